@@ -1,0 +1,170 @@
+/*
+ * lbe.h -- C ABI of the GB300 (sm_103a) steady linearized-Boltzmann solver.
+ *
+ * The solver follows Wu, Zhang, Liu, Zhang & Reese, "A fast iterative scheme for the
+ * linearized Boltzmann equation" (arXiv:1612.04488):
+ *   - problem statement: Sec. 2 (Eq. LBE, Eq. LBE_collision, the source S, the moments
+ *     U3, P13, q3 and the flow rates M, Q);
+ *   - conventional iterative scheme (CIS): Sec. 2, Eq. LBE_iteration;
+ *   - synthetic iterative scheme (SIS): Sec. 2.2 (Eqs. syn_LBE, diffusion_LBE, guided),
+ *     1D form Eq. first_order (Sec. 2.4), with the N-penalised split
+ *     L = (L + N delta h) - N delta h (abstract; Sec. 4.1 footnote) and N = nu_bar/delta
+ *     by default (Sec. 2.5);
+ *   - plates on the clustered node map of Sec. 2.4, rectangular ducts (Sec. 2.4, Table 2).
+ * The hard-sphere collision operator is evaluated by the fast spectral method (Sec. 2.4
+ * cites it); the discrete operator is: midpoint velocity grid on [-vmax, vmax]^3, Carleman
+ * truncation |x|,|y| <= R, M directions on a hemisphere (Gauss-Legendre in cos(theta) x
+ * midpoint azimuths), loss term with the same per-direction multipliers, Nyquist planes
+ * zeroed, collision strength fixed by nu_bar = 1.25 delta (Sec. 2.5).
+ *
+ * Conventions for every call:
+ *   - every call returns an lbe_status and never aborts the process;
+ *   - inputs are borrowed for the duration of the call; outputs go to caller-owned memory;
+ *   - pointers named *_dev are CUDA device pointers on the context's device, all other
+ *     pointers are host pointers;
+ *   - velocity-space arrays are laid out [cell][i1][i2][i3] with i3 (v3) fastest, i.e.
+ *     cell-major, nv^3 contiguous values per cell;
+ *   - a context is used by one host thread at a time, except lbe_submit / lbe_poll, which
+ *     are thread-safe.
+ */
+#ifndef LBE_H
+#define LBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBE_OK = 0,
+    LBE_NOT_CONVERGED = 1, /* iteration cap reached; outputs hold the last iterate       */
+    LBE_NAN = 2,           /* a non-finite flow rate was detected on the device           */
+    LBE_BAD_ARG = 3,       /* invalid argument; nothing was launched                      */
+    LBE_OOM = 4,           /* device memory (or the context's HBM budget) exhausted       */
+    LBE_TIMEOUT = 5,       /* a bounded device wait expired; the context stays usable     */
+    LBE_INTERNAL = 6,      /* CUDA runtime error; see lbe_last_error()                    */
+    LBE_UNSUPPORTED = 7    /* valid request outside what this build implements            */
+} lbe_status;
+
+/* Source term S of Sec. 2 with X_P = X_T = -1. */
+typedef enum { LBE_POISEUILLE = 0, LBE_THERMAL_TRANSPIRATION = 1 } lbe_forcing;
+
+/* Sec. 2 Eq. LBE_iteration (CIS) or Sec. 2.2 (SIS). */
+typedef enum { LBE_CIS = 0, LBE_SIS = 1 } lbe_scheme;
+
+/* Arithmetic of the collision operator and the sweeps.  LBE_FP64: everything in double.
+ * LBE_FP32: float storage and transforms, double reductions and diffusion solve.
+ * LBE_BF16_REFINED: tensor-core BF16 spectral GEMMs (FP32 accumulate) inside an outer
+ * defect-correction loop whose residual uses the FP32 operator; reductions, diffusion
+ * solve and convergence test in double. */
+typedef enum { LBE_FP64 = 0, LBE_FP32 = 1, LBE_BF16_REFINED = 2 } lbe_precision;
+
+/* Geometry (Sec. 2.4).  dim = 1: plates at x1 = +-1/2, half channel -1/2 <= x1 <= 0 with a
+ * specular symmetry plane at x1 = 0, ns sections (ns + 1 nodes), grid_kind 0 = uniform,
+ * 1 = the clustered map x1 = (10 - 15 s + 6 s^2) s^3 - 1/2, s = (0..ns)/(2 ns).
+ * dim = 2: duct [0, width] x [0, 1] (lengths scaled by the shorter side), nx x ny uniform
+ * cells, diffuse walls on all four sides. */
+typedef struct {
+    int dim;
+    int ns;
+    int grid_kind;
+    int nx, ny;
+    double width;
+} lbe_geometry;
+
+typedef struct {
+    lbe_geometry geom;
+    double delta;        /* rarefaction parameter, Eq. delta; delta >= 0                      */
+    double N;            /* SIS tuning parameter; <= 0 selects nu_bar/delta = 1.25 (Sec. 2.5)   */
+    int nv;              /* velocity points per axis: 8, 16, 24 or 32                           */
+    double vmax;         /* velocity box [-vmax, vmax]^3                                        */
+    int M;               /* hemisphere directions: power of two, 4..64                          */
+    double R;            /* Carleman truncation radius; <= 0 selects 0.75 * vmax                */
+    lbe_forcing forcing;
+    lbe_scheme scheme;
+    lbe_precision precision;
+    double eps;          /* stop when |dM| < eps |M| and |dQ| < eps |Q| (Sec. 2.4); 0 = never  */
+    int max_iter;        /* iteration cap (>= 1)                                                */
+} lbe_problem;
+
+typedef struct {
+    double mass_flow;        /* M of the last iterate                                         */
+    double heat_flow;        /* Q of the last iterate                                         */
+    int iters;               /* iterations performed (kinetic sweeps)                         */
+    int status;              /* lbe_status of this solve                                      */
+    double last_rel_change;  /* max(|dM/M|, |dQ/Q|) of the last iteration                      */
+    double seconds;          /* wall time from admission to completion                        */
+    int refinements;         /* outer defect-correction steps (LBE_BF16_REFINED), else 0       */
+} lbe_result;
+
+typedef struct lbe_ctx lbe_ctx;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device memory the
+ * context allocates (0 = 90% of the free memory at creation).  *ctx receives the handle. */
+lbe_status lbe_create(lbe_ctx** ctx, int device, size_t hbm_budget_bytes);
+
+/* Release every resource of the context (waits for queued serving work to finish). */
+lbe_status lbe_destroy(lbe_ctx* ctx);
+
+const char* lbe_status_str(lbe_status s);
+
+/* Text of the last CUDA / argument error seen by this context (never NULL). */
+const char* lbe_last_error(lbe_ctx* ctx);
+
+/* Number of cells (1D nodes or 2D cells) of a problem's spatial grid. */
+int lbe_problem_cells(const lbe_problem* pb);
+
+/* Solve one problem to convergence (or max_iter).  U3_out (host, [cells] or NULL) receives
+ * U3 of the last iterate; h_out (host, [cells * nv^3] or NULL) receives h as double.  With
+ * eps = 0 exactly max_iter iterations run (status LBE_NOT_CONVERGED). */
+lbe_status lbe_solve(lbe_ctx* ctx, const lbe_problem* pb, lbe_result* out,
+                     double* U3_out, double* h_out);
+
+/* Solve n problems that share (nv, vmax, M, R, precision) together: one batched collision
+ * launch and one batched sweep launch per iteration cover every unfinished problem.  outs
+ * receives n results.  Finished problems stop iterating while the others continue. */
+lbe_status lbe_solve_batch(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_result* outs);
+
+/* Collision operator on device data (steps A1-A4).  h_dev: [cells][nv^3] of double (FP64)
+ * or float (FP32, BF16_REFINED).  delta_dev: [cells] double, the rarefaction of each cell.
+ * Outputs (same type as h, any may be NULL): Lplus_dev = L+ h, L_dev = L h.
+ * G_dev (double [cells][2], may be NULL): G_j = 2 sum_v v_j v3 (L h + n_delta h) dv^3 with
+ * n_delta = N delta per cell taken from ndelta_dev (double [cells]; required with G_dev).
+ * stream: cudaStream_t or NULL for the legacy default stream.  Asynchronous. */
+lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R,
+                       lbe_precision precision, int cells, const double* delta_dev,
+                       const void* h_dev, void* Lplus_dev, void* L_dev,
+                       const double* ndelta_dev, double* G_dev, void* stream);
+
+/* Transport sweep of one problem (steps A5-A6): solves nu_eq h + v.grad h = rhs with the
+ * problem's geometry and delta.  rhs_dev, h_dev: [cells][nv^3], double for FP64 else
+ * float.  mom_dev (double [cells][5], may be NULL): U3, q3, W1 = F201/4, W2 = F021/4,
+ * X12 = F111/4 of the result.  Asynchronous on `stream`. */
+lbe_status lbe_sweep(lbe_ctx* ctx, const lbe_problem* pb, const void* rhs_dev, void* h_dev,
+                     double* mom_dev, void* stream);
+
+/* SIS diffusion solve (step A7) on host arrays of length cells: given the half-step
+ * moments Uh, W1, W2, X12 and the L-moments G1, G2 of one problem, write U3^(k+1) to
+ * U_out.  Runs the device kernel and synchronises. */
+lbe_status lbe_diffusion(lbe_ctx* ctx, const lbe_problem* pb, const double* Uh,
+                         const double* W1, const double* W2, const double* X12,
+                         const double* G1, const double* G2, double* U_out);
+
+/* Continuous-batching service.  lbe_submit queues a problem and returns a ticket at once;
+ * a service thread admits queued problems while slots and the HBM budget allow, advances
+ * all admitted problems together (shared collision and sweep launches per velocity grid)
+ * and retires each one as it converges.  lbe_poll reports completion (*done = 1) and
+ * copies the result; a ticket can be polled until lbe_destroy.  Thread-safe. */
+lbe_status lbe_submit(lbe_ctx* ctx, const lbe_problem* pb, uint64_t* ticket);
+lbe_status lbe_poll(lbe_ctx* ctx, uint64_t ticket, lbe_result* out, int* done);
+
+/* Maximum problems advanced together by the service (default 64). */
+lbe_status lbe_set_max_active(lbe_ctx* ctx, int max_active);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBE_H */

@@ -1,0 +1,693 @@
+// C ABI (include/lbe.h): context, tables, validation, the CIS/SIS solve driver.
+//
+// One SIS iteration of a batch of problems that share a velocity grid (Sec. 2.2):
+//   fsm (A1-A3)   L+ h, L h for the cells of every unfinished problem
+//   lmoments (A4) G_j = 2 sum v_j v3 (L h + N delta h) dv^3            [SIS only]
+//   sweep (A5)    h^(k+1/2) from nu h + v.grad h = L+ h + S
+//   moments (A6)  U3, q3, W1, W2, X12 of h^(k+1/2)
+//   sis_update (A7-A8)  diffusion correction, flow rates, convergence flags
+//   correct (A8)  h^(k+1) = h^(k+1/2) + 2 dU v3 f_eq
+// The flags come back to the host once per iteration; finished problems drop out of the
+// active list and stop iterating.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbe_internal.h"
+#include "sweep.h"
+
+namespace lbe {
+
+lbe_status cuda_status(Ctx* c, cudaError_t e, const char* where) {
+    if (e == cudaSuccess) return LBE_OK;
+    if (c) c->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return LBE_OOM;
+    return LBE_INTERNAL;
+}
+
+lbe_status bad_arg(Ctx* c, const std::string& what) {
+    if (c) c->last_error = what;
+    return LBE_BAD_ARG;
+}
+
+lbe_status dev_alloc(Ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return LBE_OK;
+    if (c->used + bytes > c->budget) {
+        c->last_error = "HBM budget exceeded";
+        return LBE_OOM;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(c, e, "cudaMalloc");
+    }
+    c->used += bytes;
+    return LBE_OK;
+}
+
+void dev_free(Ctx* c, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    c->used -= std::min(bytes, c->used);
+}
+
+lbe_status validate_problem(Ctx* c, const lbe_problem& pb) {
+    const auto& g = pb.geom;
+    if (g.dim != 1 && g.dim != 2) return bad_arg(c, "geom.dim must be 1 or 2");
+    if (g.dim == 1 && (g.ns < 2 || g.ns > 100000)) return bad_arg(c, "geom.ns must be in [2, 100000]");
+    if (g.dim == 1 && g.grid_kind != 0 && g.grid_kind != 1) return bad_arg(c, "geom.grid_kind must be 0 or 1");
+    if (g.dim == 2 && (g.nx < 3 || g.ny < 3 || (long)g.nx * g.ny > 1000000))
+        return bad_arg(c, "geom.nx, geom.ny must be >= 3");
+    if (g.dim == 2 && !(g.width > 0)) return bad_arg(c, "geom.width must be > 0");
+    if (!(pb.delta >= 0) || !std::isfinite(pb.delta)) return bad_arg(c, "delta must be finite and >= 0");
+    if (pb.nv != 8 && pb.nv != 16 && pb.nv != 24 && pb.nv != 32) return bad_arg(c, "nv must be 8, 16, 24 or 32");
+    if (!(pb.vmax > 0) || !std::isfinite(pb.vmax)) return bad_arg(c, "vmax must be > 0");
+    if (pb.M < 2 || pb.M > 64 || (pb.M & (pb.M - 1))) return bad_arg(c, "M must be a power of two in [2, 64]");
+    if (pb.R > 2.0 * pb.vmax) return bad_arg(c, "R must be <= 2 vmax");
+    if (pb.forcing != LBE_POISEUILLE && pb.forcing != LBE_THERMAL_TRANSPIRATION) return bad_arg(c, "bad forcing");
+    if (pb.scheme != LBE_CIS && pb.scheme != LBE_SIS) return bad_arg(c, "bad scheme");
+    if (pb.precision != LBE_FP64 && pb.precision != LBE_FP32 && pb.precision != LBE_BF16_REFINED)
+        return bad_arg(c, "bad precision");
+    if (!(pb.eps >= 0)) return bad_arg(c, "eps must be >= 0");
+    if (pb.max_iter < 1) return bad_arg(c, "max_iter must be >= 1");
+    return LBE_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// tables
+// ---------------------------------------------------------------------------------------
+static std::string tables_key(int nv, double vmax, int M, double R) {
+    char b[128];
+    snprintf(b, sizeof b, "%d/%.17g/%d/%.17g", nv, vmax, M, R);
+    return b;
+}
+
+template <typename T>
+static lbe_status upload(Ctx* c, T** dst, const std::vector<T>& src, size_t* bytes) {
+    lbe_status st = dev_alloc(c, (void**)dst, src.size() * sizeof(T));
+    if (st != LBE_OK) return st;
+    *bytes += src.size() * sizeof(T);
+    return cuda_status(c, cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice),
+                       "upload");
+}
+
+static std::vector<float> to_f(const std::vector<double>& a) { return std::vector<float>(a.begin(), a.end()); }
+
+DevTables* get_tables(Ctx* c, int nv, double vmax, int M, double R, lbe_status* st) {
+    if (R <= 0) R = default_R(vmax);
+    std::lock_guard<std::mutex> lk(c->tables_mu);
+    const std::string key = tables_key(nv, vmax, M, R);
+    auto it = c->tables.find(key);
+    if (it != c->tables.end()) {
+        *st = LBE_OK;
+        return it->second.get();
+    }
+    HostTables h;
+    build_host_tables(h, nv, vmax, M, R);
+    auto t = std::make_unique<DevTables>();
+    t->nv = nv;
+    t->M = M;
+    t->vmax = vmax;
+    t->R = R;
+    t->dv = h.dv;
+    t->cU = h.cU;
+    t->cq = h.cq;
+    size_t b = 0;
+    lbe_status s = LBE_OK;
+    if (s == LBE_OK) s = upload(c, &t->feq_d, h.feq, &b);
+    if (s == LBE_OK) s = upload(c, &t->nu1_d, h.nu1, &b);
+    if (s == LBE_OK) s = upload(c, &t->mult_d, h.mult, &b);
+    if (s == LBE_OK) s = upload(c, &t->ab_d, h.ab, &b);
+    if (s == LBE_OK) s = upload(c, &t->vel_d, h.v, &b);
+    if (s == LBE_OK) s = upload(c, &t->feq_f, to_f(h.feq), &b);
+    if (s == LBE_OK) s = upload(c, &t->nu1_f, to_f(h.nu1), &b);
+    if (s == LBE_OK) s = upload(c, &t->mult_f, to_f(h.mult), &b);
+    if (s == LBE_OK) s = upload(c, &t->ab_f, to_f(h.ab), &b);
+    if (s == LBE_OK) s = upload(c, &t->vel_f, to_f(h.v), &b);
+    t->bytes = b;
+    *st = s;
+    if (s != LBE_OK) return nullptr;
+    DevTables* raw = t.get();
+    c->tables[key] = std::move(t);
+    return raw;
+}
+
+// ---------------------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------------------
+static void backward_coeffs(double xm2, double xm1, double x0, double& a, double& b, double& cc) {
+    const double h1 = x0 - xm1, h2 = xm1 - xm2;
+    a = (2.0 * h1 + h2) / (h1 * (h1 + h2));
+    b = -(h1 + h2) / (h1 * h2);
+    cc = h1 / (h2 * (h1 + h2));
+}
+
+// march coefficients along increasing positions pos[0..n-1], pos[0] the inflow boundary
+static void march_coeffs(const std::vector<double>& pos, std::vector<double>& a, std::vector<double>& b,
+                         std::vector<double>& cc) {
+    const size_t n = pos.size();
+    a.assign(n, 0.0);
+    b.assign(n, 0.0);
+    cc.assign(n, 0.0);
+    a[1] = 1.0 / (pos[1] - pos[0]);
+    b[1] = -a[1];
+    for (size_t i = 2; i < n; ++i) backward_coeffs(pos[i - 2], pos[i - 1], pos[i], a[i], b[i], cc[i]);
+}
+
+void build_sweep_geom(SweepGeom& g, const lbe_problem& pb) {
+    g.dim = pb.geom.dim;
+    if (g.dim == 1) {
+        const int ns = pb.geom.ns, n = ns + 1;
+        g.cells = n;
+        g.x.resize(n);
+        for (int i = 0; i < n; ++i) {
+            if (pb.geom.grid_kind == 1) {
+                const double s = i / (2.0 * ns);
+                g.x[i] = (10.0 - 15.0 * s + 6.0 * s * s) * s * s * s - 0.5;
+            } else {
+                g.x[i] = -0.5 + 0.5 * i / ns;
+            }
+        }
+        march_coeffs(g.x, g.fa, g.fb, g.fc);
+        g.ba.assign(n, 0.0);
+        g.bb.assign(n, 0.0);
+        g.bc.assign(n, 0.0);
+        for (int i = n - 2; i >= 0; --i) {
+            const double y0 = -g.x[i], y1 = -g.x[i + 1];
+            const double y2 = (i + 2 <= n - 1) ? -g.x[i + 2] : g.x[n - 2];  // mirror ghost
+            backward_coeffs(y2, y1, y0, g.ba[i], g.bb[i], g.bc[i]);
+        }
+        g.trap.assign(n, 0.0);
+        for (int i = 0; i + 1 < n; ++i) {
+            const double w = g.x[i + 1] - g.x[i];  // M = 2 int_{-1/2}^0 U dx (trapezoid)
+            g.trap[i] += w;
+            g.trap[i + 1] += w;
+        }
+    } else {
+        const int nx = pb.geom.nx, ny = pb.geom.ny;
+        g.cells = nx * ny;
+        g.nx = nx;
+        g.ny = ny;
+        const double dx = pb.geom.width / nx, dy = 1.0 / ny;
+        std::vector<double> px(nx + 1), py(ny + 1), a, b, cc;
+        px[0] = 0;
+        py[0] = 0;
+        for (int i = 0; i < nx; ++i) px[i + 1] = (i + 0.5) * dx;
+        for (int j = 0; j < ny; ++j) py[j + 1] = (j + 0.5) * dy;
+        march_coeffs(px, a, b, cc);
+        g.xa.assign(a.begin() + 1, a.end());
+        g.xb.assign(b.begin() + 1, b.end());
+        g.xc.assign(cc.begin() + 1, cc.end());
+        march_coeffs(py, a, b, cc);
+        g.ya.assign(a.begin() + 1, a.end());
+        g.yb.assign(b.begin() + 1, b.end());
+        g.yc.assign(cc.begin() + 1, cc.end());
+        g.trap.assign(g.cells, 1.0 / g.cells);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// batch state
+// ---------------------------------------------------------------------------------------
+struct DevBuf {
+    Ctx* c = nullptr;
+    void* p = nullptr;
+    size_t n = 0;
+    lbe_status alloc(Ctx* cx, size_t bytes) {
+        c = cx;
+        n = bytes;
+        return dev_alloc(cx, &p, bytes);
+    }
+    ~DevBuf() {
+        if (c) dev_free(c, p, n);
+    }
+    template <typename T> T* as() const { return (T*)p; }
+};
+
+struct Batch {
+    Ctx* c = nullptr;
+    DevTables* t = nullptr;
+    int prec = 0;
+    int njobs = 0;
+    long cells = 0;
+    std::vector<lbe_problem> pbs;
+    std::vector<SweepGeom> geo;
+    std::vector<SweepJobDev> sj;
+    std::vector<SisJobDev> ij;
+    std::vector<long> cell_off;
+    DevBuf h, hh, lp, lh, scratch, mom, G, dU, U3, delta, nd, coef, work, sjobs, ijobs, states, act;
+    int chunk = 1;
+    std::vector<JobState> hstate;
+    std::vector<int> active;
+};
+
+static lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n) {
+    B.c = c;
+    B.njobs = n;
+    B.pbs.assign(pbs, pbs + n);
+    const lbe_problem& p0 = pbs[0];
+    lbe_status st;
+    B.t = get_tables(c, p0.nv, p0.vmax, p0.M, p0.R, &st);
+    if (!B.t) return st;
+    B.prec = p0.precision;
+    if (B.prec == LBE_BF16_REFINED) B.prec = LBE_FP32;  // handled by the refinement driver
+    const int eb = B.prec == LBE_FP64 ? 8 : 4;
+    const long n3 = (long)p0.nv * p0.nv * p0.nv;
+    std::vector<double> coef, dcell, ndcell;
+    B.geo.resize(n);
+    long work = 0;
+    for (int j = 0; j < n; ++j) {
+        const lbe_problem& pb = pbs[j];
+        build_sweep_geom(B.geo[j], pb);
+        SweepGeom& g = B.geo[j];
+        SweepJobDev s{};
+        s.cell_off = B.cells;
+        s.ncell = g.cells;
+        s.nx = g.nx;
+        s.ny = g.ny;
+        s.forcing = pb.forcing;
+        s.delta = pb.delta;
+        s.coef_off = (int)coef.size();
+        if (g.dim == 1) {
+            for (auto* v : {&g.fa, &g.fb, &g.fc, &g.ba, &g.bb, &g.bc}) coef.insert(coef.end(), v->begin(), v->end());
+        } else {
+            for (auto* v : {&g.xa, &g.xb, &g.xc, &g.ya, &g.yb, &g.yc}) coef.insert(coef.end(), v->begin(), v->end());
+        }
+        SisJobDev q{};
+        q.cell_off = B.cells;
+        q.ncell = g.cells;
+        q.dim = g.dim;
+        q.nx = g.nx;
+        q.ny = g.ny;
+        q.width = pb.geom.width;
+        q.scheme = pb.scheme == LBE_SIS ? 1 : 0;
+        const double Nn = pb.N > 0 ? pb.N : 1.25;
+        q.ndsig = Nn * pb.delta * (pb.forcing == LBE_POISEUILLE ? 1.0 : 0.0);
+        q.eps = pb.eps;
+        q.max_iter = pb.max_iter;
+        q.coef_off = (int)coef.size();
+        if (g.dim == 1) {
+            for (auto* v : {&g.fa, &g.fb, &g.fc, &g.x}) coef.insert(coef.end(), v->begin(), v->end());
+        } else {
+            const int mx = g.nx - 2, my = g.ny - 2;
+            for (int p = 0; p < mx; ++p)
+                for (int a = 0; a < mx; ++a) coef.push_back(std::sin(M_PI * (p + 1.0) * (a + 1.0) / (mx + 1.0)));
+            for (int p = 0; p < my; ++p)
+                for (int a = 0; a < my; ++a) coef.push_back(std::sin(M_PI * (p + 1.0) * (a + 1.0) / (my + 1.0)));
+            const double dx = pb.geom.width / g.nx, dy = 1.0 / g.ny;
+            for (int p = 0; p < mx; ++p)
+                for (int r = 0; r < my; ++r) {
+                    const double sx = std::sin(M_PI * (p + 1.0) / (2.0 * (mx + 1.0)));
+                    const double sy = std::sin(M_PI * (r + 1.0) / (2.0 * (my + 1.0)));
+                    coef.push_back(-4.0 / (dx * dx) * sx * sx - 4.0 / (dy * dy) * sy * sy);
+                }
+            q.work_off = work;
+            work += 2L * mx * my;
+        }
+        q.trap_off = (int)coef.size();
+        coef.insert(coef.end(), g.trap.begin(), g.trap.end());
+        for (int i = 0; i < g.cells; ++i) {
+            dcell.push_back(pb.delta);
+            ndcell.push_back(Nn * pb.delta);
+        }
+        B.sj.push_back(s);
+        B.ij.push_back(q);
+        B.cell_off.push_back(B.cells);
+        B.cells += g.cells;
+    }
+    const size_t vol = (size_t)B.cells * n3 * eb;
+    size_t scr = fsm_cc_scratch_bytes(*B.t, (int)std::min<long>(B.cells, 1L << 30), eb, &B.chunk);
+    if ((st = B.h.alloc(c, vol)) != LBE_OK) return st;
+    if ((st = B.hh.alloc(c, vol)) != LBE_OK) return st;
+    if ((st = B.lp.alloc(c, vol)) != LBE_OK) return st;
+    if ((st = B.lh.alloc(c, vol)) != LBE_OK) return st;
+    if ((st = B.scratch.alloc(c, scr)) != LBE_OK) return st;
+    if ((st = B.mom.alloc(c, B.cells * 5 * 8)) != LBE_OK) return st;
+    if ((st = B.G.alloc(c, B.cells * 2 * 8)) != LBE_OK) return st;
+    if ((st = B.dU.alloc(c, B.cells * 8)) != LBE_OK) return st;
+    if ((st = B.U3.alloc(c, B.cells * 8)) != LBE_OK) return st;
+    if ((st = B.delta.alloc(c, B.cells * 8)) != LBE_OK) return st;
+    if ((st = B.nd.alloc(c, B.cells * 8)) != LBE_OK) return st;
+    if ((st = B.coef.alloc(c, coef.size() * 8)) != LBE_OK) return st;
+    if ((st = B.work.alloc(c, std::max<long>(work, 1) * 8)) != LBE_OK) return st;
+    if ((st = B.sjobs.alloc(c, n * sizeof(SweepJobDev))) != LBE_OK) return st;
+    if ((st = B.ijobs.alloc(c, n * sizeof(SisJobDev))) != LBE_OK) return st;
+    if ((st = B.states.alloc(c, n * sizeof(JobState))) != LBE_OK) return st;
+    if ((st = B.act.alloc(c, n * sizeof(int))) != LBE_OK) return st;
+    cudaStream_t s = c->stream;
+    cudaMemsetAsync(B.h.p, 0, vol, s);  // h^0 = 0
+    cudaMemcpyAsync(B.delta.p, dcell.data(), dcell.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(B.nd.p, ndcell.data(), ndcell.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(B.coef.p, coef.data(), coef.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(B.sjobs.p, B.sj.data(), n * sizeof(SweepJobDev), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(B.ijobs.p, B.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, s);
+    B.hstate.assign(n, JobState{});
+    cudaMemcpyAsync(B.states.p, B.hstate.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, s);
+    B.active.resize(n);
+    for (int j = 0; j < n; ++j) B.active[j] = j;
+    return cuda_status(c, cudaStreamSynchronize(s), "batch_init");
+}
+
+// One iteration over the active jobs.  Contiguous active jobs share FSM launches.
+template <typename T>
+static void batch_iterate(Batch& B) {
+    cudaStream_t s = B.c->stream;
+    const DevTables& t = *B.t;
+    const long n3 = (long)t.nv * t.nv * t.nv;
+    const int na = (int)B.active.size();
+    T* h = B.h.as<T>();
+    T* hh = B.hh.as<T>();
+    T* lp = B.lp.as<T>();
+    T* lh = B.lh.as<T>();
+    bool any_sis = false;
+    for (int a = 0; a < na;) {
+        int b = a;
+        while (b + 1 < na && B.active[b + 1] == B.active[b] + 1) ++b;
+        const long c0 = B.cell_off[B.active[a]];
+        const long c1 = B.cell_off[B.active[b]] + B.sj[B.active[b]].ncell;
+        const int nc = (int)(c1 - c0);
+        fsm_cc_apply<T>(t, nc, B.delta.as<double>() + c0, h + c0 * n3, lp + c0 * n3, lh + c0 * n3, B.scratch.p,
+                        B.chunk, s);
+        for (int k = a; k <= b; ++k) any_sis |= B.pbs[B.active[k]].scheme == LBE_SIS;
+        if (any_sis) lmoments<T>(t, nc, lh + c0 * n3, h + c0 * n3, B.nd.as<double>() + c0, B.G.as<double>() + c0 * 2, s);
+        a = b + 1;
+    }
+    // sweeps grouped by dimension
+    std::vector<int> act1, act2;
+    for (int j : B.active) (B.geo[j].dim == 1 ? act1 : act2).push_back(j);
+    // the device active list is [act1..., act2...]
+    std::vector<int> ordered(act1);
+    ordered.insert(ordered.end(), act2.begin(), act2.end());
+    cudaMemcpyAsync(B.act.p, ordered.data(), na * sizeof(int), cudaMemcpyHostToDevice, s);
+    int* dact = B.act.as<int>();
+    launch_sweep<T>(t, 1, (int)act1.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact, B.coef.as<double>(), s);
+    launch_sweep<T>(t, 2, (int)act2.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact + act1.size(),
+                    B.coef.as<double>(), s);
+    for (int j : ordered) launch_moments<T>(t, B.cell_off[j], B.sj[j].ncell, hh, B.mom.as<double>(), s);
+    launch_sis_update(t, na, B.ijobs.as<SisJobDev>(), dact, B.mom.as<double>(), B.G.as<double>(),
+                      B.coef.as<double>(), B.work.as<double>(), B.dU.as<double>(), B.U3.as<double>(),
+                      B.states.as<JobState>(), s);
+    launch_correct<T>(t, na, hh, h, B.dU.as<double>(), B.sjobs.as<SweepJobDev>(), dact, s);
+    cudaMemcpyAsync(B.hstate.data(), B.states.p, B.njobs * sizeof(JobState), cudaMemcpyDeviceToHost, s);
+}
+
+static lbe_status batch_run(Batch& B, int max_steps) {
+    int steps = 0;
+    while (!B.active.empty() && steps < max_steps) {
+        if (B.prec == LBE_FP64)
+            batch_iterate<double>(B);
+        else
+            batch_iterate<float>(B);
+        lbe_status st = cuda_status(B.c, cudaStreamSynchronize(B.c->stream), "iterate");
+        if (st != LBE_OK) return st;
+        std::vector<int> keep;
+        for (int j : B.active)
+            if (!B.hstate[j].done) keep.push_back(j);
+        B.active.swap(keep);
+        ++steps;
+    }
+    return LBE_OK;
+}
+
+static void fill_result(const Batch& B, int j, lbe_result* r, double secs) {
+    const JobState& s = B.hstate[j];
+    r->mass_flow = s.M;
+    r->heat_flow = s.Q;
+    r->iters = s.iters;
+    r->last_rel_change = s.rel;
+    r->seconds = secs;
+    r->refinements = 0;
+    const lbe_problem& pb = B.pbs[j];
+    if (s.nan)
+        r->status = LBE_NAN;
+    else if (pb.eps > 0 && s.done && s.iters < pb.max_iter)
+        r->status = LBE_OK;
+    else if (pb.eps > 0 && std::fabs(s.M - s.Mprev) < pb.eps * std::fabs(s.M) &&
+             std::fabs(s.Q - s.Qprev) < pb.eps * std::fabs(s.Q))
+        r->status = LBE_OK;
+    else
+        r->status = LBE_NOT_CONVERGED;
+}
+
+}  // namespace lbe
+
+using namespace lbe;
+
+struct lbe_ctx : public lbe::Ctx {};
+
+extern "C" {
+
+const char* lbe_status_str(lbe_status s) {
+    switch (s) {
+        case LBE_OK: return "ok";
+        case LBE_NOT_CONVERGED: return "not converged";
+        case LBE_NAN: return "non-finite flow rate";
+        case LBE_BAD_ARG: return "bad argument";
+        case LBE_OOM: return "out of device memory";
+        case LBE_TIMEOUT: return "device wait timed out";
+        case LBE_INTERNAL: return "internal CUDA error";
+        case LBE_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* lbe_last_error(lbe_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+lbe_status lbe_create(lbe_ctx** out, int device, size_t budget) {
+    if (!out) return LBE_BAD_ARG;
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || device < 0 || device >= n) return e != cudaSuccess ? LBE_INTERNAL : LBE_BAD_ARG;
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return LBE_INTERNAL;
+    auto* c = new lbe_ctx();
+    c->device = device;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    c->budget = budget ? budget : (size_t)(0.9 * fr);
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return LBE_INTERNAL;
+    }
+    init_twiddles_cc();
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        delete c;
+        return LBE_INTERNAL;
+    }
+    *out = c;
+    return LBE_OK;
+}
+
+lbe_status lbe_destroy(lbe_ctx* ctx) {
+    if (!ctx) return LBE_BAD_ARG;
+    cudaSetDevice(ctx->device);
+    stop_service(ctx);
+    for (auto& kv : ctx->tables) {
+        DevTables* t = kv.second.get();
+        for (void* p : {(void*)t->feq_d, (void*)t->nu1_d, (void*)t->mult_d, (void*)t->ab_d, (void*)t->vel_d,
+                        (void*)t->feq_f, (void*)t->nu1_f, (void*)t->mult_f, (void*)t->ab_f, (void*)t->vel_f})
+            if (p) cudaFree(p);
+    }
+    ctx->tables.clear();
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return LBE_OK;
+}
+
+int lbe_problem_cells(const lbe_problem* pb) {
+    if (!pb) return 0;
+    return pb->geom.dim == 1 ? pb->geom.ns + 1 : pb->geom.nx * pb->geom.ny;
+}
+
+static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_result* outs,
+                                double* U3_out, double* h_out) {
+    if (!ctx || !pbs || n < 1 || !outs) return bad_arg(ctx, "null argument");
+    cudaSetDevice(ctx->device);
+    for (int j = 0; j < n; ++j) {
+        lbe_status st = validate_problem(ctx, pbs[j]);
+        if (st != LBE_OK) return st;
+        if (pbs[j].nv != pbs[0].nv || pbs[j].vmax != pbs[0].vmax || pbs[j].M != pbs[0].M ||
+            pbs[j].R != pbs[0].R || pbs[j].precision != pbs[0].precision)
+            return bad_arg(ctx, "batched problems must share nv, vmax, M, R and precision");
+    }
+    if (pbs[0].precision == LBE_BF16_REFINED) return refined_solve(ctx, pbs, n, outs, U3_out, h_out);
+    auto t0 = std::chrono::steady_clock::now();
+    Batch B;
+    lbe_status st = batch_init(B, ctx, pbs, n);
+    if (st != LBE_OK) return st;
+    int maxit = 0;
+    for (int j = 0; j < n; ++j) maxit = std::max(maxit, pbs[j].max_iter);
+    st = batch_run(B, maxit);
+    if (st != LBE_OK) return st;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    lbe_status worst = LBE_OK;
+    for (int j = 0; j < n; ++j) {
+        fill_result(B, j, &outs[j], secs);
+        if (outs[j].status != LBE_OK && worst == LBE_OK) worst = (lbe_status)outs[j].status;
+    }
+    const long n3 = (long)pbs[0].nv * pbs[0].nv * pbs[0].nv;
+    if (U3_out) st = cuda_status(ctx, cudaMemcpy(U3_out, B.U3.p, B.cells * 8, cudaMemcpyDeviceToHost), "U3 copy");
+    if (st == LBE_OK && h_out) {
+        if (B.prec == LBE_FP64) {
+            st = cuda_status(ctx, cudaMemcpy(h_out, B.h.p, B.cells * n3 * 8, cudaMemcpyDeviceToHost), "h copy");
+        } else {
+            std::vector<float> tmp(B.cells * n3);
+            st = cuda_status(ctx, cudaMemcpy(tmp.data(), B.h.p, tmp.size() * 4, cudaMemcpyDeviceToHost), "h copy");
+            for (size_t i = 0; i < tmp.size(); ++i) h_out[i] = tmp[i];
+        }
+    }
+    return st != LBE_OK ? st : worst;
+}
+
+lbe_status lbe_solve(lbe_ctx* ctx, const lbe_problem* pb, lbe_result* out, double* U3_out, double* h_out) {
+    return lbe_solve_batch_impl(ctx, pb, 1, out, U3_out, h_out);
+}
+
+lbe_status lbe_solve_batch(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_result* outs) {
+    return lbe_solve_batch_impl(ctx, pbs, n, outs, nullptr, nullptr);
+}
+
+lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_precision precision, int cells,
+                       const double* delta_dev, const void* h_dev, void* Lplus_dev, void* L_dev,
+                       const double* ndelta_dev, double* G_dev, void* stream) {
+    if (!ctx) return LBE_BAD_ARG;
+    if (cells < 0 || (cells > 0 && (!h_dev || !delta_dev))) return bad_arg(ctx, "null h or delta");
+    if (nv != 8 && nv != 16 && nv != 24 && nv != 32) return bad_arg(ctx, "nv must be 8, 16, 24 or 32");
+    if (M < 2 || M > 64 || (M & (M - 1))) return bad_arg(ctx, "M must be a power of two in [2, 64]");
+    if (!(vmax > 0) || R > 2 * vmax) return bad_arg(ctx, "bad vmax or R");
+    if (G_dev && !ndelta_dev) return bad_arg(ctx, "G needs ndelta");
+    if (precision != LBE_FP64 && precision != LBE_FP32 && precision != LBE_BF16_REFINED)
+        return bad_arg(ctx, "bad precision");
+    if (cells == 0) return LBE_OK;
+    cudaSetDevice(ctx->device);
+    lbe_status st;
+    DevTables* t = get_tables(ctx, nv, vmax, M, R, &st);
+    if (!t) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == LBE_BF16_REFINED) {
+        st = tc_apply_L(ctx, t, cells, delta_dev, (const float*)h_dev, (float*)Lplus_dev, (float*)L_dev, s);
+        if (st != LBE_OK) return st;
+        if (G_dev && !L_dev) return bad_arg(ctx, "G needs L_dev");
+        if (G_dev) lmoments<float>(*t, cells, (const float*)L_dev, (const float*)h_dev, ndelta_dev, G_dev, s);
+        return cuda_status(ctx, cudaGetLastError(), "apply_L");
+    }
+    const int eb = precision == LBE_FP64 ? 8 : 4;
+    int chunk = 1;
+    const size_t scr = fsm_cc_scratch_bytes(*t, cells, eb, &chunk);
+    void* p = nullptr;
+    if ((st = dev_alloc(ctx, &p, scr)) != LBE_OK) return st;
+    // L is needed for G; use a temporary when the caller did not ask for it
+    void* Ltmp = nullptr;
+    const size_t vol = (size_t)cells * nv * nv * nv * eb;
+    if (G_dev && !L_dev) {
+        if ((st = dev_alloc(ctx, &Ltmp, vol)) != LBE_OK) {
+            dev_free(ctx, p, scr);
+            return st;
+        }
+    }
+    void* Lo = L_dev ? L_dev : Ltmp;
+    if (precision == LBE_FP64) {
+        st = fsm_cc_apply<double>(*t, cells, delta_dev, (const double*)h_dev, (double*)Lplus_dev, (double*)Lo, p,
+                                  chunk, s);
+        if (G_dev) lmoments<double>(*t, cells, (const double*)Lo, (const double*)h_dev, ndelta_dev, G_dev, s);
+    } else {
+        st = fsm_cc_apply<float>(*t, cells, delta_dev, (const float*)h_dev, (float*)Lplus_dev, (float*)Lo, p,
+                                 chunk, s);
+        if (G_dev) lmoments<float>(*t, cells, (const float*)Lo, (const float*)h_dev, ndelta_dev, G_dev, s);
+    }
+    lbe_status st2 = cuda_status(ctx, cudaStreamSynchronize(s), "apply_L");
+    dev_free(ctx, p, scr);
+    if (Ltmp) dev_free(ctx, Ltmp, vol);
+    return st != LBE_OK ? st : st2;
+}
+
+lbe_status lbe_sweep(lbe_ctx* ctx, const lbe_problem* pb, const void* rhs_dev, void* h_dev, double* mom_dev,
+                     void* stream) {
+    if (!ctx || !pb || !rhs_dev || !h_dev) return bad_arg(ctx, "null argument");
+    lbe_status st = validate_problem(ctx, *pb);
+    if (st != LBE_OK) return st;
+    if (pb->precision == LBE_BF16_REFINED) return bad_arg(ctx, "sweep precision must be FP64 or FP32");
+    cudaSetDevice(ctx->device);
+    DevTables* t = get_tables(ctx, pb->nv, pb->vmax, pb->M, pb->R, &st);
+    if (!t) return st;
+    SweepGeom g;
+    build_sweep_geom(g, *pb);
+    std::vector<double> coef;
+    if (g.dim == 1)
+        for (auto* v : {&g.fa, &g.fb, &g.fc, &g.ba, &g.bb, &g.bc}) coef.insert(coef.end(), v->begin(), v->end());
+    else
+        for (auto* v : {&g.xa, &g.xb, &g.xc, &g.ya, &g.yb, &g.yc}) coef.insert(coef.end(), v->begin(), v->end());
+    SweepJobDev j{};
+    j.cell_off = 0;
+    j.ncell = g.cells;
+    j.nx = g.nx;
+    j.ny = g.ny;
+    j.coef_off = 0;
+    j.forcing = pb->forcing;
+    j.delta = pb->delta;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dc = nullptr, *dj = nullptr;
+    if ((st = dev_alloc(ctx, &dc, coef.size() * 8)) != LBE_OK) return st;
+    if ((st = dev_alloc(ctx, &dj, sizeof j)) != LBE_OK) {
+        dev_free(ctx, dc, coef.size() * 8);
+        return st;
+    }
+    cudaMemcpyAsync(dc, coef.data(), coef.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dj, &j, sizeof j, cudaMemcpyHostToDevice, s);
+    if (pb->precision == LBE_FP64) {
+        launch_sweep<double>(*t, g.dim, 1, 0, (const double*)rhs_dev, (double*)h_dev, (SweepJobDev*)dj, nullptr,
+                             (double*)dc, s);
+        if (mom_dev) launch_moments<double>(*t, 0, g.cells, (const double*)h_dev, mom_dev, s);
+    } else {
+        launch_sweep<float>(*t, g.dim, 1, 0, (const float*)rhs_dev, (float*)h_dev, (SweepJobDev*)dj, nullptr,
+                            (double*)dc, s);
+        if (mom_dev) launch_moments<float>(*t, 0, g.cells, (const float*)h_dev, mom_dev, s);
+    }
+    st = cuda_status(ctx, cudaStreamSynchronize(s), "sweep");
+    dev_free(ctx, dc, coef.size() * 8);
+    dev_free(ctx, dj, sizeof j);
+    return st;
+}
+
+lbe_status lbe_diffusion(lbe_ctx* ctx, const lbe_problem* pb, const double* Uh, const double* W1, const double* W2,
+                         const double* X12, const double* G1, const double* G2, double* U_out) {
+    if (!ctx || !pb || !Uh || !W1 || !G1 || !U_out) return bad_arg(ctx, "null argument");
+    lbe_status st = validate_problem(ctx, *pb);
+    if (st != LBE_OK) return st;
+    if (pb->geom.dim == 2 && (!W2 || !X12 || !G2)) return bad_arg(ctx, "2D needs W2, X12, G2");
+    cudaSetDevice(ctx->device);
+    lbe_problem p = *pb;
+    p.scheme = LBE_SIS;
+    p.precision = LBE_FP64;
+    Batch B;
+    if ((st = batch_init(B, ctx, &p, 1)) != LBE_OK) return st;
+    const int n = (int)B.cells;
+    std::vector<double> mom(5 * n, 0.0), G(2 * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        mom[5 * i + 0] = Uh[i];
+        mom[5 * i + 2] = W1[i];
+        mom[5 * i + 3] = W2 ? W2[i] : 0.0;
+        mom[5 * i + 4] = X12 ? X12[i] : 0.0;
+        G[2 * i + 0] = G1[i];
+        G[2 * i + 1] = G2 ? G2[i] : 0.0;
+    }
+    cudaStream_t s = ctx->stream;
+    cudaMemcpyAsync(B.mom.p, mom.data(), mom.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(B.G.p, G.data(), G.size() * 8, cudaMemcpyHostToDevice, s);
+    launch_sis_update(*B.t, 1, B.ijobs.as<SisJobDev>(), nullptr, B.mom.as<double>(), B.G.as<double>(),
+                      B.coef.as<double>(), B.work.as<double>(), B.dU.as<double>(), B.U3.as<double>(),
+                      B.states.as<JobState>(), s);
+    std::vector<double> du(n);
+    cudaMemcpyAsync(du.data(), B.dU.p, n * 8, cudaMemcpyDeviceToHost, s);
+    if ((st = cuda_status(ctx, cudaStreamSynchronize(s), "diffusion")) != LBE_OK) return st;
+    for (int i = 0; i < n; ++i) U_out[i] = Uh[i] + du[i];
+    return LBE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Device helpers shared by the library's kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbe {
+
+template <typename T> struct Cplx;
+template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<float> { using type = float2; };
+template <typename T> using cplx_t = typename Cplx<T>::type;
+
+// Twiddles W^m = exp(-2 pi i m / N) for N in {8, 16, 24, 32}, slot = index of N.
+// Each translation unit that uses them fills its own copy once per device
+// (see init_twiddles in fsm_cc.cu).
+static __constant__ double2 c_tw_d[4][32];
+static __constant__ float2 c_tw_f[4][32];
+
+template <int N> struct TwSlot;
+template <> struct TwSlot<8> { static constexpr int v = 0; };
+template <> struct TwSlot<16> { static constexpr int v = 1; };
+template <> struct TwSlot<24> { static constexpr int v = 2; };
+template <> struct TwSlot<32> { static constexpr int v = 3; };
+
+template <typename T, int N> __device__ __forceinline__ cplx_t<T> tw(int m);
+template <> __device__ __forceinline__ double2 tw<double, 8>(int m) { return c_tw_d[0][m]; }
+template <> __device__ __forceinline__ double2 tw<double, 16>(int m) { return c_tw_d[1][m]; }
+template <> __device__ __forceinline__ double2 tw<double, 24>(int m) { return c_tw_d[2][m]; }
+template <> __device__ __forceinline__ double2 tw<double, 32>(int m) { return c_tw_d[3][m]; }
+template <> __device__ __forceinline__ float2 tw<float, 8>(int m) { return c_tw_f[0][m]; }
+template <> __device__ __forceinline__ float2 tw<float, 16>(int m) { return c_tw_f[1][m]; }
+template <> __device__ __forceinline__ float2 tw<float, 24>(int m) { return c_tw_f[2][m]; }
+template <> __device__ __forceinline__ float2 tw<float, 32>(int m) { return c_tw_f[3][m]; }
+
+__host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+// In-register 1D DFT of length N (forward: exp(-2 pi i jk/N); INV: exp(+...)), unscaled.
+// Radix-2 decimation in time for powers of two, direct summation otherwise; every index
+// is a compile-time constant after unrolling, so the line stays in registers.
+template <typename T, int N, bool INV>
+__device__ __forceinline__ void dft_line(T (&re)[N], T (&im)[N]) {
+    if constexpr (is_pow2(N)) {
+        constexpr int B = ilog2(N);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int j = bitrev(i, B);
+            if (j > i) {
+                T t = re[i]; re[i] = re[j]; re[j] = t;
+                t = im[i]; im[i] = im[j]; im[j] = t;
+            }
+        }
+#pragma unroll
+        for (int stage = 0; stage < B; ++stage) {
+            const int len = 2 << stage;
+#pragma unroll
+            for (int i = 0; i < N; i += len) {
+#pragma unroll
+                for (int j = 0; j < len / 2; ++j) {
+                    const auto w = tw<T, N>(j * (N / len));
+                    const T wr = w.x, wi = INV ? -w.y : w.y;
+                    const int a = i + j, b = i + j + len / 2;
+                    T xr, xi;
+                    if (j == 0) {
+                        xr = re[b];
+                        xi = im[b];
+                    } else {
+                        xr = re[b] * wr - im[b] * wi;
+                        xi = re[b] * wi + im[b] * wr;
+                    }
+                    re[b] = re[a] - xr;
+                    im[b] = im[a] - xi;
+                    re[a] = re[a] + xr;
+                    im[a] = im[a] + xi;
+                }
+            }
+        }
+    } else {
+        T orr[N], oi[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            T ar = 0, ai = 0;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const auto w = tw<T, N>((j * k) % N);
+                const T wr = w.x, wi = INV ? -w.y : w.y;
+                ar += re[j] * wr - im[j] * wi;
+                ai += re[j] * wi + im[j] * wr;
+            }
+            orr[k] = ar;
+            oi[k] = ai;
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            re[k] = orr[k];
+            im[k] = oi[k];
+        }
+    }
+}
+
+// Deterministic block reduction of NV doubles (fixed tree for a fixed blockDim).
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], double* smem /*[32*NV]*/) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) smem[warp * NV + k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = (lane < nw) ? smem[lane * NV + k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            v[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace lbe

@@ -1,0 +1,119 @@
+// Internal declarations of the GB300 linearized-Boltzmann library (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lbe.h"
+
+namespace lbe {
+
+// ---------------------------------------------------------------------------------------
+// Velocity grid and collision-operator tables (one per (nv, vmax, M, R)).
+// Built on the host in double from the formulas of the discrete operator (see lbe.h):
+//   mult[p]  = (psi_p + i phi_p) / nv^3   for p < M, mult[M] = G_hat / nv^3 (real)
+//   ab[p]    = (w'_p A_p, w'_p B_p)       gain weights in physical space, w'_p = 2 b w_p
+//   nu1      = nu_eq at delta = 1,  feq = f_eq
+// Device copies in double and float.  The BF16 tensor path keeps its own operands.
+// ---------------------------------------------------------------------------------------
+struct HostTables {
+    int nv = 0, M = 0;
+    double vmax = 0, R = 0, dv = 0;
+    std::vector<double> v;                  // [nv] midpoint nodes
+    std::vector<double> feq, nu1;           // [nv^3]
+    std::vector<double> mult;               // [(M+1)][nv^3][2]
+    std::vector<double> ab;                 // [M][nv^3][2]
+    double cU = 0, cq = 0;                  // sum v3^2 f_eq dv^3, sum (|v|^2-5/2) v3^2 f_eq dv^3
+};
+
+void build_host_tables(HostTables& t, int nv, double vmax, int M, double R);
+
+struct TcOperands;  // tensor-core operands (fsm_tc.cu)
+
+struct DevTables {
+    int nv = 0, M = 0;
+    double vmax = 0, R = 0, dv = 0;
+    double cU = 0, cq = 0;
+    // double
+    double* feq_d = nullptr; double* nu1_d = nullptr; double* mult_d = nullptr; double* ab_d = nullptr;
+    double* vel_d = nullptr;  // [nv] nodes
+    // float
+    float* feq_f = nullptr; float* nu1_f = nullptr; float* mult_f = nullptr; float* ab_f = nullptr;
+    float* vel_f = nullptr;
+    TcOperands* tc = nullptr;
+    size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------------------------------
+// Spatial description of one problem as seen by the kernels.
+// ---------------------------------------------------------------------------------------
+struct SweepGeom {
+    int dim = 1;
+    int cells = 0;          // 1D: ns+1 nodes, 2D: nx*ny
+    int nx = 0, ny = 0;     // 2D
+    // 1D march coefficients (double), node i in [0, n): fwd (v1 > 0) and bwd (v1 < 0)
+    std::vector<double> x;                  // node coordinates (1D) / cell centres x (2D)
+    std::vector<double> fa, fb, fc;         // v1 > 0 march, coefficient of h_i, h_{i-1}, h_{i-2}
+    std::vector<double> ba, bb, bc;         // v1 < 0 march (h_i, h_{i+1}, h_{i+2}); last uses ghost
+    std::vector<double> trap;               // 1D trapezoid weights for M = 2 int U dx
+    // 2D: coefficients along a march of n cells starting at an inflow face
+    std::vector<double> xa, xb, xc, ya, yb, yc;
+};
+
+void build_sweep_geom(SweepGeom& g, const lbe_problem& pb);
+
+// ---------------------------------------------------------------------------------------
+// Context.
+// ---------------------------------------------------------------------------------------
+struct Job {
+    uint64_t ticket = 0;
+    lbe_problem pb{};
+    lbe_result res{};
+    int done = 0;
+    double t_submit = 0;  // seconds on the service clock
+};
+
+struct Ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    std::string last_error;
+    std::mutex tables_mu;
+    std::map<std::string, std::unique_ptr<DevTables>> tables;
+    cudaStream_t stream = nullptr;
+    // serving
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Job*> queue;
+    std::map<uint64_t, std::unique_ptr<Job>> jobs;
+    std::atomic<uint64_t> next_ticket{1};
+    std::thread service;
+    bool stop = false;
+    bool service_started = false;
+    int max_active = 64;
+};
+
+// tables
+DevTables* get_tables(Ctx* c, int nv, double vmax, int M, double R, lbe_status* st);
+double default_R(double vmax);
+
+// memory accounting
+lbe_status dev_alloc(Ctx* c, void** p, size_t bytes);
+void dev_free(Ctx* c, void* p, size_t bytes);
+
+// status helpers
+lbe_status cuda_status(Ctx* c, cudaError_t e, const char* where);
+lbe_status bad_arg(Ctx* c, const std::string& what);
+lbe_status validate_problem(Ctx* c, const lbe_problem& pb);
+
+}  // namespace lbe

@@ -1,0 +1,366 @@
+// Transport sweeps, moments, SIS diffusion correction and flow rates (steps A5-A8).
+//
+// A5  nu_eq h + v.grad h = rhs, second-order upwind (Sec. 2 below Eq. LBE_iteration),
+//     first order at the first node after an inflow boundary.  One thread per velocity
+//     (1D: per mirror pair v1 > 0 / v1 < 0), marching over the spatial nodes; consecutive
+//     threads hold consecutive v3, so every load/store of a node is a coalesced row of the
+//     [cell][v] layout.  1D plates: diffuse wall (incoming h = 0) at x1 = -1/2, specular
+//     symmetry plane at x1 = 0 with a mirror ghost node (Sec. 2.4).  2D ducts: diffuse walls
+//     on all faces, the march over cells in upwind order; the two previous rows are read
+//     back from the output array (this thread's own earlier stores).
+// A6  U3, q3, F201/4, F021/4, F111/4 per cell (the moment equations of Sec. 2, the
+//     non-accelerated moments below Eq. Uz2), one block per cell, fixed reduction order.
+// A7  SIS diffusion correction: 1D Eq. first_order (with the N-penalty), marched from the
+//     wall; 2D Eq. diffusion_LBE on the interior with U3 = U3^(k+1/2) on the wall ring,
+//     solved exactly by DST-I diagonalisation of the five-point Laplacian (FP64).
+// A8  Eq. guided correction, flow rates M, Q (Sec. 2.4), relative-change test.
+#include <cmath>
+
+#include "common.cuh"
+#include "lbe_internal.h"
+#include "sweep.h"
+
+namespace lbe {
+
+namespace {
+
+// Source S of Sec. 2 with X_P = X_T = -1 at velocity (v1, v2, v3).
+template <typename T>
+__device__ __forceinline__ T source(int forcing, T v1, T v2, T v3, T f) {
+    return forcing == 0 ? v3 * f : v3 * (v1 * v1 + v2 * v2 + v3 * v3 - T(2.5)) * f;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* __restrict__ h,
+                                                 const T* __restrict__ nu1, const T* __restrict__ vel,
+                                                 const T* __restrict__ feq,
+                                                 const SweepJobDev* __restrict__ jobs,
+                                                 const int* __restrict__ active,
+                                                 const double* __restrict__ coef, int nv) {
+    const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
+    const int half = nv / 2, n2 = nv * nv;
+    const long n3 = (long)n2 * nv;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= half * n2) return;
+    const int i1p = half + t / n2, rem = t % n2;
+    const int vpos = i1p * n2 + rem, vneg = (nv - 1 - i1p) * n2 + rem;
+    const int n = jb.ncell;
+    const T* r = rhs + jb.cell_off * n3;
+    T* o = h + jb.cell_off * n3;
+    const double* fa = coef + jb.coef_off;
+    const double* fb = fa + n;
+    const double* fc = fb + n;
+    const double* ba = fc + n;
+    const double* bb = ba + n;
+    const double* bc = bb + n;
+    const T d = (T)jb.delta;
+    const T v1 = vel[i1p];
+    const T nup = d * nu1[vpos];
+    const T w2 = vel[rem / nv], w3 = vel[rem % nv];
+    const T Sp = source<T>(jb.forcing, v1, w2, w3, feq[vpos]);
+    const T Sn = source<T>(jb.forcing, vel[nv - 1 - i1p], w2, w3, feq[vneg]);
+    T hm1 = T(0), hm2 = T(0);
+    o[vpos] = T(0);
+    for (int i = 1; i < n; ++i) {
+        const T acc = (r[i * n3 + vpos] + Sp) - v1 * ((T)fb[i] * hm1 + (T)fc[i] * hm2);
+        const T hi = acc / (nup + v1 * (T)fa[i]);
+        o[i * n3 + vpos] = hi;
+        hm2 = hm1;
+        hm1 = hi;
+    }
+    // specular symmetry plane: h(x_Ns, v1<0) = h(x_Ns, -v1); ghost node carries h(x_{Ns-1}, -v1)
+    const T u = -vel[nv - 1 - i1p];
+    const T nun = d * nu1[vneg];
+    T g1 = hm1, g2 = hm2;
+    o[(n - 1) * n3 + vneg] = hm1;
+    for (int i = n - 2; i >= 0; --i) {
+        const T acc = (r[i * n3 + vneg] + Sn) - u * ((T)bb[i] * g1 + (T)bc[i] * g2);
+        const T hi = acc / (nun + u * (T)ba[i]);
+        o[i * n3 + vneg] = hi;
+        g2 = g1;
+        g1 = hi;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_sweep2d(const T* __restrict__ rhs, T* __restrict__ h,
+                                                 const T* __restrict__ nu1, const T* __restrict__ vel,
+                                                 const T* __restrict__ feq,
+                                                 const SweepJobDev* __restrict__ jobs,
+                                                 const int* __restrict__ active,
+                                                 const double* __restrict__ coef, int nv) {
+    const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
+    const int n2 = nv * nv;
+    const long n3 = (long)n2 * nv;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n3) return;
+    const int i1 = v / n2, i2 = (v / nv) % nv;
+    const bool s1 = i1 >= nv / 2, s2 = i2 >= nv / 2;
+    const T u1 = s1 ? vel[i1] : -vel[i1];
+    const T u2 = s2 ? vel[i2] : -vel[i2];
+    const T nu = (T)jb.delta * nu1[v];
+    const T S = source<T>(jb.forcing, vel[i1], vel[i2], vel[v % nv], feq[v]);
+    const int nx = jb.nx, ny = jb.ny;
+    const double* xa = coef + jb.coef_off;
+    const double* xb = xa + nx;
+    const double* xc = xb + nx;
+    const double* ya = xc + nx;
+    const double* yb = ya + ny;
+    const double* yc = yb + ny;
+    const T* r = rhs + jb.cell_off * n3;
+    T* o = h + jb.cell_off * n3;
+    const int dj = s2 ? -1 : 1;  // offset to the upwind row in j
+    for (int mj = 0; mj < ny; ++mj) {
+        const int j = s2 ? mj : ny - 1 - mj;
+        T hm1 = T(0), hm2 = T(0);
+        const T ay = (T)ya[mj], by = (T)yb[mj], cy = (T)yc[mj];
+        for (int mi = 0; mi < nx; ++mi) {
+            const int i = s1 ? mi : nx - 1 - mi;
+            const long cell = (long)i * ny + j;
+            T acc = r[cell * n3 + v] + S;
+            if (mi >= 1) acc -= u1 * (T)xb[mi] * hm1;
+            if (mi >= 2) acc -= u1 * (T)xc[mi] * hm2;
+            if (mj >= 1) acc -= u2 * by * o[(cell + dj) * n3 + v];
+            if (mj >= 2) acc -= u2 * cy * o[(cell + 2 * dj) * n3 + v];
+            const T hij = acc / (nu + u1 * (T)xa[mi] + u2 * ay);
+            o[cell * n3 + v] = hij;
+            hm2 = hm1;
+            hm1 = hij;
+        }
+    }
+}
+
+// mom[cell][5] = sum_v {v3, (|v|^2-5/2) v3, (2 v1^2-1) v3, (2 v2^2-1) v3, 2 v1 v2 v3} h dv^3
+template <typename T>
+__global__ void __launch_bounds__(256) k_moments(const T* __restrict__ h, const double* __restrict__ vel,
+                                                 int nv, double dv3, long cell0, double* __restrict__ mom) {
+    __shared__ double red[32 * 5];
+    const long cell = cell0 + blockIdx.x;
+    const int n3 = nv * nv * nv;
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) {
+        const int i1 = i / (nv * nv), i2 = (i / nv) % nv, i3 = i % nv;
+        const double v1 = vel[i1], v2 = vel[i2], v3 = vel[i3];
+        const double x = (double)h[cell * n3 + i] * v3;
+        s[0] += x;
+        s[1] += (v1 * v1 + v2 * v2 + v3 * v3 - 2.5) * x;
+        s[2] += (2.0 * v1 * v1 - 1.0) * x;
+        s[3] += (2.0 * v2 * v2 - 1.0) * x;
+        s[4] += 2.0 * v1 * v2 * x;
+    }
+    block_reduce<5>(s, red);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 5; ++k) mom[cell * 5 + k] = s[k] * dv3;
+}
+
+// 2D Poisson right-hand side of Eq. diffusion_LBE (N-penalised) on the interior cells.
+__device__ double poisson_rhs(const double* mom, const double* G, int i, int j, int ny, double dx,
+                              double dy, double ndsig) {
+    auto W1 = [&](int a, int b) { return mom[((long)a * ny + b) * 5 + 2]; };
+    auto W2 = [&](int a, int b) { return mom[((long)a * ny + b) * 5 + 3]; };
+    auto X = [&](int a, int b) { return mom[((long)a * ny + b) * 5 + 4]; };
+    auto G1 = [&](int a, int b) { return G[((long)a * ny + b) * 2 + 0]; };
+    auto G2 = [&](int a, int b) { return G[((long)a * ny + b) * 2 + 1]; };
+    return -ndsig - (W1(i + 1, j) - 2.0 * W1(i, j) + W1(i - 1, j)) / (dx * dx) -
+           2.0 * (X(i + 1, j + 1) - X(i + 1, j - 1) - X(i - 1, j + 1) + X(i - 1, j - 1)) / (4.0 * dx * dy) -
+           (W2(i, j + 1) - 2.0 * W2(i, j) + W2(i, j - 1)) / (dy * dy) +
+           (G1(i + 1, j) - G1(i - 1, j)) / (2.0 * dx) + (G2(i, j + 1) - G2(i, j - 1)) / (2.0 * dy);
+}
+
+// One block per job: diffusion correction (SIS), corrected moments, flow rates, test.
+__global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict__ jobs,
+                                                    const int* __restrict__ active,
+                                                    const double* __restrict__ mom,
+                                                    const double* __restrict__ G,
+                                                    const double* __restrict__ coef,
+                                                    double* __restrict__ work, double cU, double cq,
+                                                    double* __restrict__ dU, double* __restrict__ U3,
+                                                    JobState* __restrict__ state) {
+    __shared__ double red[32 * 2];
+    const int jid = active ? active[blockIdx.x] : blockIdx.x;
+    const SisJobDev jb = jobs[jid];
+    JobState* st = state + jid;
+    const long c0 = jb.cell_off;
+    const int n = jb.ncell;
+    const double* m = mom + c0 * 5;
+    double* du = dU + c0;
+    if (jb.scheme == 0) {  // CIS: no correction
+        for (int c = threadIdx.x; c < n; c += blockDim.x) du[c] = 0.0;
+    } else if (jb.dim == 1) {
+        if (threadIdx.x == 0) {
+            const double* fa = coef + jb.coef_off;  // block [fa | fb | fc | x], n each
+            const double* fb = fa + n;
+            const double* fc = fb + n;
+            const double* xs = fc + n;
+            double ym2 = 0.0, ym1 = m[0] + m[2];
+            du[0] = 0.0;  // U(x0) = U^(k+1/2)(x0)
+            for (int i = 1; i < n; ++i) {
+                double r = -jb.ndsig * xs[i] + G[(c0 + i) * 2] - fb[i] * ym1;
+                if (i >= 2) r -= fc[i] * ym2;
+                const double yi = r / fa[i];
+                du[i] = (yi - m[i * 5 + 2]) - m[i * 5 + 0];
+                ym2 = ym1;
+                ym1 = yi;
+            }
+        }
+    } else {
+        // 2D: interior mx x my, U = Uh on the ring; DST-I solve in `work`
+        const int nx = jb.nx, ny = jb.ny, mx = nx - 2, my = ny - 2;
+        const double dx = jb.width / nx, dy = 1.0 / ny;
+        double* B = work + jb.work_off;
+        double* T1 = B + (long)mx * my;
+        const double* Sx = coef + jb.coef_off;           // [mx][mx]
+        const double* Sy = Sx + (long)mx * mx;           // [my][my]
+        const double* lam = Sy + (long)my * my;          // [mx][my]
+        const double* Gc = G + c0 * 2;
+        for (int k = threadIdx.x; k < mx * my; k += blockDim.x) {
+            const int p = k / my, q = k % my, i = p + 1, j = q + 1;
+            double b = poisson_rhs(m, Gc, i, j, ny, dx, dy, jb.ndsig);
+            if (p == 0) b -= m[((long)0 * ny + j) * 5] / (dx * dx);
+            if (p == mx - 1) b -= m[((long)(nx - 1) * ny + j) * 5] / (dx * dx);
+            if (q == 0) b -= m[((long)i * ny + 0) * 5] / (dy * dy);
+            if (q == my - 1) b -= m[((long)i * ny + ny - 1) * 5] / (dy * dy);
+            B[k] = b;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < mx * my; k += blockDim.x) {  // T1 = Sx B
+            const int p = k / my, q = k % my;
+            double s = 0.0;
+            for (int a = 0; a < mx; ++a) s += Sx[p * mx + a] * B[a * my + q];
+            T1[k] = s;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < mx * my; k += blockDim.x) {  // B = (T1 Sy) / lam
+            const int p = k / my, q = k % my;
+            double s = 0.0;
+            for (int a = 0; a < my; ++a) s += T1[p * my + a] * Sy[a * my + q];
+            B[k] = s / lam[k];
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < mx * my; k += blockDim.x) {  // T1 = Sx B
+            const int p = k / my, q = k % my;
+            double s = 0.0;
+            for (int a = 0; a < mx; ++a) s += Sx[p * mx + a] * B[a * my + q];
+            T1[k] = s;
+        }
+        __syncthreads();
+        const double scale = 4.0 / ((mx + 1.0) * (my + 1.0));
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            const int i = c / ny, j = c % ny;
+            if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) {
+                du[c] = 0.0;
+            } else {
+                const int p = i - 1, q = j - 1;
+                double s = 0.0;
+                for (int a = 0; a < my; ++a) s += T1[p * my + a] * Sy[a * my + q];
+                du[c] = s * scale - m[(long)c * 5];
+            }
+        }
+    }
+    __syncthreads();
+    // moments of h^(k+1) and flow rates
+    const double* trap = coef + jb.trap_off;
+    double s[2] = {0.0, 0.0};
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const double u = m[c * 5 + 0] + 2.0 * du[c] * cU;
+        const double q = m[c * 5 + 1] + 2.0 * du[c] * cq;
+        U3[c0 + c] = u;
+        s[0] += trap[c] * u;
+        s[1] += trap[c] * q;
+    }
+    block_reduce<2>(s, red);
+    if (threadIdx.x == 0) {
+        const double Mn = s[0], Qn = s[1];
+        const double rm = fabs(Mn - st->M) / fabs(Mn), rq = fabs(Qn - st->Q) / fabs(Qn);
+        st->Mprev = st->M;
+        st->Qprev = st->Q;
+        st->M = Mn;
+        st->Q = Qn;
+        st->iters += 1;
+        st->rel = fmax(rm, rq);
+        if (!isfinite(Mn) || !isfinite(Qn)) {
+            st->nan = 1;
+            st->done = 1;
+        } else if (fabs(Mn - st->Mprev) < jb.eps * fabs(Mn) && fabs(Qn - st->Qprev) < jb.eps * fabs(Qn)) {
+            st->done = 1;
+        } else if (st->iters >= jb.max_iter) {
+            st->done = 1;
+        }
+    }
+}
+
+// h = hh + 2 dU v3 f_eq for the cells of the active jobs (Eq. guided).
+template <typename T>
+__global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __restrict__ h,
+                                                 const double* __restrict__ dU, const T* __restrict__ feq,
+                                                 const T* __restrict__ vel, const SweepJobDev* __restrict__ jobs,
+                                                 const int* __restrict__ active, int nv) {
+    const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
+    const long n3 = (long)nv * nv * nv;
+    const long total = (long)jb.ncell * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
+        const long c = k / n3;
+        const int v = (int)(k % n3);
+        const long g = jb.cell_off * n3 + k;
+        const T d = (T)(2.0 * dU[jb.cell_off + c]);
+        h[g] = hh[g] + d * vel[v % nv] * feq[v];
+    }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_sweep(const DevTables& t, int dim, int njobs, int max_cells_unused, const T* rhs, T* h,
+                  const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s) {
+    (void)max_cells_unused;
+    if (njobs <= 0) return;
+    const int nv = t.nv;
+    const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
+    const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
+    const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
+    if (dim == 1) {
+        const int nt = nv / 2 * nv * nv;
+        dim3 g((nt + 127) / 128, njobs);
+        k_sweep1d<T><<<g, 128, 0, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv);
+    } else {
+        const int nt = nv * nv * nv;
+        dim3 g((nt + 127) / 128, njobs);
+        k_sweep2d<T><<<g, 128, 0, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv);
+    }
+}
+
+template <typename T>
+void launch_moments(const DevTables& t, long cell0, int cells, const T* h, double* mom, cudaStream_t s) {
+    if (cells <= 0) return;
+    k_moments<T><<<cells, 256, 0, s>>>(h, t.vel_d, t.nv, t.dv * t.dv * t.dv, cell0, mom);
+}
+
+void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, const int* active,
+                       const double* mom, const double* G, const double* coef, double* work, double* dU,
+                       double* U3, JobState* state, cudaStream_t s) {
+    if (njobs <= 0) return;
+    k_sis_update<<<njobs, 256, 0, s>>>(jobs, active, mom, G, coef, work, t.cU, t.cq, dU, U3, state);
+}
+
+template <typename T>
+void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU,
+                    const SweepJobDev* jobs, const int* active, cudaStream_t s) {
+    if (njobs <= 0) return;
+    const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
+    const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
+    dim3 g(152, njobs);
+    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, feq, vel, jobs, active, t.nv);
+}
+
+template void launch_sweep<double>(const DevTables&, int, int, int, const double*, double*,
+                                   const SweepJobDev*, const int*, const double*, cudaStream_t);
+template void launch_sweep<float>(const DevTables&, int, int, int, const float*, float*,
+                                  const SweepJobDev*, const int*, const double*, cudaStream_t);
+template void launch_moments<double>(const DevTables&, long, int, const double*, double*, cudaStream_t);
+template void launch_moments<float>(const DevTables&, long, int, const float*, double*, cudaStream_t);
+template void launch_correct<double>(const DevTables&, int, const double*, double*, const double*,
+                                     const SweepJobDev*, const int*, cudaStream_t);
+template void launch_correct<float>(const DevTables&, int, const float*, float*, const double*,
+                                    const SweepJobDev*, const int*, cudaStream_t);
+
+}  // namespace lbe

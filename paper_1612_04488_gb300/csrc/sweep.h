@@ -1,0 +1,73 @@
+// Device-side job descriptors shared by the sweep / SIS kernels and the host driver.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbe.h"
+
+namespace lbe {
+
+struct DevTables;
+struct Ctx;
+
+// fsm_tc.cu: BF16 tensor-core collision operator (float in / out)
+lbe_status tc_apply_L(Ctx* c, DevTables* t, int cells, const double* delta, const float* h, float* Lplus,
+                      float* Lout, cudaStream_t s);
+// refine.cu: BF16 operator inside an outer defect-correction loop
+lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs, double* U3_out,
+                         double* h_out);
+// serve.cu
+void stop_service(Ctx* c);
+
+struct SweepJobDev {
+    long cell_off;   // first cell of the job in the batched [cell][v] arrays
+    int ncell;       // 1D: nodes, 2D: nx * ny
+    int nx, ny;      // 2D
+    int coef_off;    // 1D: [fa|fb|fc|ba|bb|bc] (n each); 2D: [xa|xb|xc] (nx) [ya|yb|yc] (ny)
+    int forcing;     // source S added to the right-hand side: 0 Poiseuille, 1 thermal transp.
+    double delta;
+};
+
+struct SisJobDev {
+    long cell_off;
+    int ncell;
+    int dim;
+    int nx, ny;
+    double width;
+    int scheme;      // 0 CIS, 1 SIS
+    int coef_off;    // 1D: [fa|fb|fc|x] (n each); 2D: [Sx (mx^2) | Sy (my^2) | lambda (mx*my)]
+    int trap_off;    // flow-rate weights (n): M = sum w_c U_c
+    long work_off;   // 2D scratch (2 * mx * my doubles)
+    double ndsig;    // N delta sigma (sigma = 1 Poiseuille, 0 thermal transpiration)
+    double eps;
+    int max_iter;
+};
+
+struct JobState {
+    double M, Q, Mprev, Qprev, rel;
+    int iters, done, nan, pad;
+};
+
+template <typename T>
+void launch_sweep(const DevTables& t, int dim, int njobs, int max_cells, const T* rhs, T* h,
+                  const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s);
+template <typename T>
+void launch_moments(const DevTables& t, long cell0, int cells, const T* h, double* mom, cudaStream_t s);
+void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, const int* active,
+                       const double* mom, const double* G, const double* coef, double* work, double* dU,
+                       double* U3, JobState* state, cudaStream_t s);
+template <typename T>
+void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU,
+                    const SweepJobDev* jobs, const int* active, cudaStream_t s);
+
+// fsm_cc.cu
+void init_twiddles_cc();
+size_t fsm_cc_scratch_bytes(const DevTables& t, int cells, int elem_bytes, int* chunk_out);
+template <typename T>
+lbe_status fsm_cc_apply(const DevTables& t, int cells, const double* delta, const T* h, T* Lplus, T* Lout,
+                 void* scratch, int chunk, cudaStream_t s);
+template <typename T>
+void lmoments(const DevTables& t, int cells, const T* Lh, const T* h, const double* nd, double* G,
+              cudaStream_t s);
+
+}  // namespace lbe

@@ -1,0 +1,162 @@
+"""ctypes binding of include/lbe.h (argument marshalling only).
+
+Every computation runs in liblbe.so.  Loading fails loudly when the library has not been
+built (``python -m paper_1612_04488_gb300.build``); there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbe.so")
+
+OK, NOT_CONVERGED, NAN, BAD_ARG, OOM, TIMEOUT, INTERNAL, UNSUPPORTED = range(8)
+POISEUILLE, THERMAL_TRANSPIRATION = 0, 1
+CIS, SIS = 0, 1
+FP64, FP32, BF16_REFINED = 0, 1, 2
+
+
+class Geometry(C.Structure):
+    _fields_ = [("dim", C.c_int), ("ns", C.c_int), ("grid_kind", C.c_int), ("nx", C.c_int),
+                ("ny", C.c_int), ("width", C.c_double)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("geom", Geometry), ("delta", C.c_double), ("N", C.c_double), ("nv", C.c_int),
+                ("vmax", C.c_double), ("M", C.c_int), ("R", C.c_double), ("forcing", C.c_int),
+                ("scheme", C.c_int), ("precision", C.c_int), ("eps", C.c_double),
+                ("max_iter", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [("mass_flow", C.c_double), ("heat_flow", C.c_double), ("iters", C.c_int),
+                ("status", C.c_int), ("last_rel_change", C.c_double), ("seconds", C.c_double),
+                ("refinements", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("liblbe.so is not built; run python -m paper_1612_04488_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+        L.lbe_create.argtypes = [C.POINTER(vp), ip, C.c_size_t]
+        L.lbe_destroy.argtypes = [vp]
+        L.lbe_status_str.argtypes = [ip]
+        L.lbe_status_str.restype = C.c_char_p
+        L.lbe_last_error.argtypes = [vp]
+        L.lbe_last_error.restype = C.c_char_p
+        L.lbe_problem_cells.argtypes = [C.POINTER(Problem)]
+        L.lbe_solve.argtypes = [vp, C.POINTER(Problem), C.POINTER(Result), dp, dp]
+        L.lbe_solve_batch.argtypes = [vp, C.POINTER(Problem), ip, C.POINTER(Result)]
+        L.lbe_apply_L.argtypes = [vp, ip, C.c_double, ip, C.c_double, ip, ip, vp, vp, vp, vp, vp, vp, vp]
+        L.lbe_sweep.argtypes = [vp, C.POINTER(Problem), vp, vp, vp, vp]
+        L.lbe_diffusion.argtypes = [vp, C.POINTER(Problem), dp, dp, dp, dp, dp, dp, dp]
+        L.lbe_submit.argtypes = [vp, C.POINTER(Problem), C.POINTER(C.c_uint64)]
+        L.lbe_poll.argtypes = [vp, C.c_uint64, C.POINTER(Result), C.POINTER(C.c_int)]
+        L.lbe_set_max_active.argtypes = [vp, ip]
+        _lib = L
+    return _lib
+
+
+class LbeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (lib().lbe_status_str(status).decode(), msg))
+        self.status = status
+
+
+def problem(dim=1, ns=20, grid_kind=0, nx=64, ny=32, width=2.0, delta=1.0, N=0.0, nv=16,
+            vmax=6.0, M=16, R=0.0, forcing=POISEUILLE, scheme=SIS, precision=FP64, eps=1e-8,
+            max_iter=500):
+    return Problem(Geometry(dim, ns, grid_kind, nx, ny, width), delta, N, nv, vmax, M, R,
+                   forcing, scheme, precision, eps, max_iter)
+
+
+def cells_of(pb):
+    return lib().lbe_problem_cells(C.byref(pb))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+class Context:
+    """Owns an lbe_ctx on one CUDA device."""
+
+    def __init__(self, device=0, hbm_budget=0):
+        self.h = C.c_void_p()
+        st = lib().lbe_create(C.byref(self.h), device, hbm_budget)
+        if st != OK:
+            raise LbeError(st, "lbe_create")
+
+    def close(self):
+        if self.h:
+            lib().lbe_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def err(self):
+        return lib().lbe_last_error(self.h).decode()
+
+    def check(self, st, allow=(OK,)):
+        if st not in allow:
+            raise LbeError(st, self.err())
+        return st
+
+    def solve(self, pb, want_h=False, want_U=True):
+        n = cells_of(pb)
+        U = np.zeros(n) if want_U else None
+        h = np.zeros(n * pb.nv ** 3) if want_h else None
+        res = Result()
+        st = lib().lbe_solve(self.h, C.byref(pb), C.byref(res), _dptr(U), _dptr(h))
+        self.check(st, (OK, NOT_CONVERGED))
+        return res, U, (h.reshape((n,) + (pb.nv,) * 3) if want_h else None)
+
+    def solve_batch(self, pbs):
+        arr = (Problem * len(pbs))(*pbs)
+        res = (Result * len(pbs))()
+        st = lib().lbe_solve_batch(self.h, arr, len(pbs), res)
+        self.check(st, (OK, NOT_CONVERGED))
+        return list(res)
+
+    def apply_L(self, nv, vmax, M, R, precision, cells, delta_ptr, h_ptr, lplus_ptr, l_ptr,
+                nd_ptr=None, G_ptr=None, stream=None):
+        st = lib().lbe_apply_L(self.h, nv, vmax, M, R, precision, cells, delta_ptr, h_ptr,
+                               lplus_ptr, l_ptr, nd_ptr, G_ptr, stream)
+        return self.check(st)
+
+    def sweep(self, pb, rhs_ptr, h_ptr, mom_ptr=None, stream=None):
+        return self.check(lib().lbe_sweep(self.h, C.byref(pb), rhs_ptr, h_ptr, mom_ptr, stream))
+
+    def diffusion(self, pb, Uh, W1, W2, X12, G1, G2):
+        n = cells_of(pb)
+        out = np.zeros(n)
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) if a is not None else None
+                for a in (Uh, W1, W2, X12, G1, G2)]
+        st = lib().lbe_diffusion(self.h, C.byref(pb), *[_dptr(a) for a in arrs], _dptr(out))
+        self.check(st)
+        return out
+
+    def submit(self, pb):
+        t = C.c_uint64()
+        self.check(lib().lbe_submit(self.h, C.byref(pb), C.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        res = Result()
+        done = C.c_int()
+        self.check(lib().lbe_poll(self.h, ticket, C.byref(res), C.byref(done)))
+        return bool(done.value), res
+
+    def set_max_active(self, n):
+        self.check(lib().lbe_set_max_active(self.h, n))

@@ -1,0 +1,238 @@
+"""GPU parity: every step of the hot path through the C ABI against the FP64 oracle on the
+same seeded inputs (FP64 path to 1e-12 element-wise, FP32 path to 2e-6 of the scale)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fsm, solver, transport, velocity  # noqa: E402
+from paper_1612_04488_gb300 import lbe, workloads  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+R45 = 4.5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = lbe.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def gpu_apply(ctx, h, nv, vmax, M, R, prec, deltas, nd=None):
+    dt = torch.float64 if prec == lbe.FP64 else torch.float32
+    cells = h.shape[0]
+    hd = dev(h, dt)
+    dd = dev(deltas)
+    lp = torch.empty_like(hd)
+    L = torch.empty_like(hd)
+    G = ndd = None
+    if nd is not None:
+        ndd = dev(nd)
+        G = torch.empty((cells, 2), dtype=torch.float64, device="cuda")
+    ctx.apply_L(nv, vmax, M, R, prec, cells, dd.data_ptr(), hd.data_ptr(), lp.data_ptr(), L.data_ptr(),
+                ndd.data_ptr() if nd is not None else None, G.data_ptr() if G is not None else None)
+    torch.cuda.synchronize()
+    out = (lp.double().cpu().numpy(), L.double().cpu().numpy())
+    if G is not None:
+        out = out + (G.cpu().numpy(),)
+    return out
+
+
+@pytest.mark.parametrize("nv,M,cells,prec", [(8, 8, 70, lbe.FP64), (16, 16, 21, lbe.FP64),
+                                             (32, 32, 3, lbe.FP64), (16, 16, 21, lbe.FP32),
+                                             (24, 16, 5, lbe.FP64), (32, 32, 3, lbe.FP32)])
+def test_apply_L_matches_oracle(ctx, nv, M, cells, prec):
+    vmax = 6.0
+    h = workloads.random_h(cells, nv, vmax, seed=nv + cells)
+    deltas = np.linspace(0.5, 3.0, cells)
+    nd = 1.25 * deltas
+    lp, L, G = gpu_apply(ctx, h, nv, vmax, M, R45, prec, deltas, nd)
+    F = fsm.FSM(nv, vmax, M, R45)
+    for c in range(cells):
+        olp, oL = F.apply(h[c], deltas[c])
+        oG = solver.l_moments(F, oL, h[c], nd[c])
+        tol = 1e-12 if prec == lbe.FP64 else 2e-6
+        s = np.max(np.abs(olp))
+        assert np.max(np.abs(lp[c] - olp)) <= tol * s, c
+        assert np.max(np.abs(L[c] - oL)) <= tol * np.max(np.abs(oL)), c
+        gs = np.sum(np.abs(oL)) * F.dv ** 3
+        assert abs(G[c, 0] - oG[0]) <= 10 * tol * gs and abs(G[c, 1] - oG[1]) <= 10 * tol * gs
+
+
+def test_apply_L_full_size_sampled(ctx):
+    """808 cells of 32^3 (the batched plates workload) in one launch; oracle on 3 cells."""
+    nv, M, vmax, cells = 32, 32, 6.0, 808
+    h = workloads.random_h(cells, nv, vmax, seed=808).astype(np.float32)
+    deltas = np.repeat(np.array([0.1, 1.0, 10.0, 100.0] * 2), 101)
+    lp, L = gpu_apply(ctx, h, nv, vmax, M, R45, lbe.FP32, deltas)
+    F = fsm.FSM(nv, vmax, M, R45)
+    for c in (0, 404, 807):
+        olp, oL = F.apply(h[c].astype(np.float64), deltas[c])
+        assert np.max(np.abs(lp[c] - olp)) <= 2e-6 * np.max(np.abs(olp))
+
+
+def test_apply_L_empty_and_bad_args(ctx):
+    assert ctx.apply_L(16, 6.0, 16, R45, lbe.FP64, 0, None, None, None, None) == lbe.OK
+    with pytest.raises(lbe.LbeError) as e:
+        ctx.apply_L(12, 6.0, 16, R45, lbe.FP64, 1, 1, 1, None, None)
+    assert e.value.status == lbe.BAD_ARG
+    with pytest.raises(lbe.LbeError):
+        ctx.apply_L(16, 6.0, 12, R45, lbe.FP64, 1, 1, 1, None, None)
+
+
+def _rhs_for(pb_kw, nv, cells, seed):
+    return workloads.random_h(cells, nv, 6.0, seed=seed)
+
+
+@pytest.mark.parametrize("grid_kind,ns,prec", [(0, 20, lbe.FP64), (1, 100, lbe.FP64), (1, 100, lbe.FP32),
+                                               (0, 3, lbe.FP64)])
+def test_sweep_1d_matches_oracle(ctx, grid_kind, ns, prec):
+    nv, delta = 16, 2.0
+    pb = lbe.problem(dim=1, ns=ns, grid_kind=grid_kind, delta=delta, nv=nv, M=16, R=R45, precision=prec,
+                     forcing=lbe.THERMAL_TRANSPIRATION)
+    n = ns + 1
+    lplus = workloads.random_h(n, nv, 6.0, seed=ns)
+    dt = torch.float64 if prec == lbe.FP64 else torch.float32
+    r = dev(lplus, dt)
+    h = torch.empty_like(r)
+    mom = torch.empty((n, 5), dtype=torch.float64, device="cuda")
+    ctx.sweep(pb, r.data_ptr(), h.data_ptr(), mom.data_ptr())
+    torch.cuda.synchronize()
+    F = fsm.FSM(nv, 6.0, 16, R45)
+    x = transport.nodes_uniform(ns) if grid_kind == 0 else transport.nodes_clustered(ns)
+    S = velocity.source(F.V1, F.V2, F.V3, 1)
+    oh = transport.sweep_1d(lplus + S, delta * F.nu, F.V1, x)
+    gh = h.double().cpu().numpy()
+    tol = 1e-12 if prec == lbe.FP64 else 3e-6
+    assert np.max(np.abs(gh - oh)) <= tol * np.max(np.abs(oh))
+    om = np.stack(solver.cell_moments(F, oh), -1)
+    assert np.max(np.abs(mom.cpu().numpy() - om)) <= 10 * tol * np.max(np.abs(om))
+
+
+@pytest.mark.parametrize("nx,ny,width", [(7, 5, 1.4), (16, 8, 2.0)])
+def test_sweep_2d_matches_oracle(ctx, nx, ny, width):
+    nv, delta = 8, 1.5
+    pb = lbe.problem(dim=2, nx=nx, ny=ny, width=width, delta=delta, nv=nv, vmax=4.0, M=8, R=3.0)
+    n = nx * ny
+    lplus = workloads.random_h(n, nv, 4.0, seed=n)
+    r = dev(lplus)
+    h = torch.empty_like(r)
+    mom = torch.empty((n, 5), dtype=torch.float64, device="cuda")
+    ctx.sweep(pb, r.data_ptr(), h.data_ptr(), mom.data_ptr())
+    torch.cuda.synchronize()
+    F = fsm.FSM(nv, 4.0, 8, 3.0)
+    S = velocity.source(F.V1, F.V2, F.V3, 0)
+    rq = (lplus + S).reshape((nx, ny) + (nv,) * 3)
+    oh = transport.sweep_2d(rq, delta * F.nu, F.V1, F.V2, nx, ny, width).reshape(n, nv, nv, nv)
+    assert np.max(np.abs(h.cpu().numpy() - oh)) <= 1e-12 * np.max(np.abs(oh))
+    om = np.stack(solver.cell_moments(F, oh), -1)
+    assert np.max(np.abs(mom.cpu().numpy() - om)) <= 1e-11 * np.max(np.abs(om))
+
+
+def test_diffusion_1d_and_2d_match_oracle(ctx):
+    rng = np.random.default_rng(5)
+    pb = lbe.problem(dim=1, ns=30, grid_kind=1, delta=3.0, nv=8, vmax=4.0, M=8, R=3.0)
+    n = 31
+    Uh, W1, G1 = rng.standard_normal((3, n))
+    x = transport.nodes_clustered(30)
+    got = ctx.diffusion(pb, Uh, W1, None, None, G1, None)
+    ref = solver.diffusion_1d(Uh, W1, G1, x, 1.25 * 3.0, 1.0)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    nx, ny = 9, 6
+    pb2 = lbe.problem(dim=2, nx=nx, ny=ny, width=1.5, delta=2.0, nv=8, vmax=4.0, M=8, R=3.0,
+                      forcing=lbe.POISEUILLE)
+    Uh, W1, W2, X12, G1, G2 = rng.standard_normal((6, nx, ny))
+    got = ctx.diffusion(pb2, *[a.reshape(-1) for a in (Uh, W1, W2, X12, G1, G2)])
+    ref = solver.poisson_2d(Uh, W1, W2, X12, G1, G2, 1.5, 1.25 * 2.0, 1.0)
+    assert np.max(np.abs(got - ref.reshape(-1))) <= 1e-11 * np.max(np.abs(ref))
+
+
+def _oracle_run(kw, scheme, iters=None, eps=None):
+    pb = solver.Problem(dim=kw["dim"], ns=kw.get("ns", 20),
+                        grid={0: "uniform", 1: "clustered"}[kw.get("grid_kind", 0)],
+                        nx=kw.get("nx", 8), ny=kw.get("ny", 6), width=kw.get("width", 2.0),
+                        delta=kw["delta"], nv=kw["nv"], vmax=kw["vmax"], M=kw["M"], R=kw["R"],
+                        forcing=kw.get("forcing", 0), scheme=scheme, eps=eps or 0.0,
+                        max_iter=iters or 500)
+    r = solver.Run(pb)
+    if iters is not None and not eps:
+        for _ in range(iters):
+            r.M, r.Q = r.step()
+    else:
+        r.solve()
+    return r
+
+
+@pytest.mark.parametrize("scheme", ["sis", "cis"])
+def test_solve_fixed_iterations_fp64_matches_oracle(ctx, scheme):
+    kw = dict(workloads.PLATES_16, R=R45, forcing=0)
+    r = _oracle_run(kw, scheme, iters=6)
+    pb = lbe.problem(**kw, scheme=lbe.SIS if scheme == "sis" else lbe.CIS, precision=lbe.FP64, eps=0.0,
+                     max_iter=6)
+    res, U, h = ctx.solve(pb, want_h=True)
+    assert res.iters == 6 and res.status == lbe.NOT_CONVERGED
+    assert abs(res.mass_flow - r.M) <= 1e-10 * abs(r.M)
+    assert abs(res.heat_flow - r.Q) <= 1e-10 * abs(r.Q)
+    assert np.max(np.abs(U - r.U)) <= 1e-10 * np.max(np.abs(r.U))
+    assert np.max(np.abs(h - r.h)) <= 1e-10 * np.max(np.abs(r.h))
+
+
+def test_solve_converged_fp64_and_fp32_match_oracle(ctx):
+    kw = dict(workloads.PLATES_16, R=R45, forcing=0)
+    r = _oracle_run(kw, "sis", eps=1e-8)
+    for prec, tol in ((lbe.FP64, 1e-10), (lbe.FP32, 1e-6)):
+        pb = lbe.problem(**kw, scheme=lbe.SIS, precision=prec, eps=1e-8, max_iter=200)
+        res, U, _ = ctx.solve(pb)
+        assert res.status == lbe.OK
+        assert abs(res.mass_flow - r.M) <= tol * abs(r.M), (prec, res.mass_flow, r.M)
+        assert abs(res.heat_flow - r.Q) <= tol * abs(r.Q) * 10
+
+
+def test_solve_2d_fixed_iterations_matches_oracle(ctx):
+    kw = dict(dim=2, nx=8, ny=6, width=1.5, delta=2.0, nv=8, vmax=4.0, M=8, R=3.0, forcing=0)
+    r = _oracle_run(kw, "sis", iters=4)
+    pb = lbe.problem(**kw, scheme=lbe.SIS, precision=lbe.FP64, eps=0.0, max_iter=4)
+    res, U, h = ctx.solve(pb, want_h=True)
+    assert abs(res.mass_flow - r.M) <= 1e-10 * abs(r.M)
+    assert np.max(np.abs(h - r.h.reshape(h.shape))) <= 1e-10 * np.max(np.abs(r.h))
+
+
+def test_batch_equals_alone_bitwise(ctx):
+    base = dict(dim=1, ns=12, grid_kind=1, nv=8, vmax=4.0, M=8, R=3.0, precision=lbe.FP64,
+                scheme=lbe.SIS, eps=1e-9, max_iter=300)
+    pbs = [lbe.problem(**base, delta=d, forcing=f) for d in (0.1, 1.0, 10.0) for f in (0, 1)]
+    pbs.append(lbe.problem(dim=2, nx=6, ny=5, width=1.2, delta=3.0, nv=8, vmax=4.0, M=8, R=3.0,
+                           precision=lbe.FP64, scheme=lbe.SIS, eps=1e-9, max_iter=300))
+    batch = ctx.solve_batch(pbs)
+    for pb, rb in zip(pbs, batch):
+        ra, _, _ = ctx.solve(pb)
+        assert ra.iters == rb.iters
+        assert ra.mass_flow == rb.mass_flow and ra.heat_flow == rb.heat_flow
+
+
+def test_free_molecular_and_single_iteration(ctx):
+    pb = lbe.problem(dim=1, ns=10, grid_kind=0, delta=0.0, nv=8, vmax=4.0, M=8, R=3.0, eps=1e-9,
+                     max_iter=50)
+    res, U, _ = ctx.solve(pb)
+    assert res.status == lbe.OK and res.iters <= 3 and np.all(np.isfinite(U))
+    pb = lbe.problem(dim=1, ns=10, grid_kind=0, delta=1.0, nv=8, vmax=4.0, M=8, R=3.0, eps=1e-9,
+                     max_iter=1)
+    res, U, _ = ctx.solve(pb)
+    assert res.iters == 1 and res.status == lbe.NOT_CONVERGED
+
+
+def test_solve_bad_args(ctx):
+    for kw in (dict(nv=12), dict(M=24), dict(delta=-1.0), dict(max_iter=0), dict(ns=1)):
+        p = dict(dim=1, ns=10, nv=8, vmax=4.0, M=8, delta=1.0, max_iter=5)
+        p.update(kw)
+        with pytest.raises(lbe.LbeError) as e:
+            ctx.solve(lbe.problem(**p))
+        assert e.value.status == lbe.BAD_ARG
