@@ -1,0 +1,370 @@
+"""Benchmark: SIS solves/s of the batched plates workload on GB300 (one JSON line).
+
+Workload (default "plates32x8"): eight steady problems of Sec. 2.4 solved together --
+delta in {0.1, 1, 10, 100} x {Poiseuille, thermal transpiration}, 32^3 velocity grid on
+[-6, 6]^3, 100 sections on the clustered node map, M = 32 directions, SIS with
+N = nu_bar/delta, stopped when the flow rates change by less than eps per iteration.
+One step = one batched solve of all eight problems to convergence (every hot-path step,
+A1-A8, runs on every iteration).  Inputs are synthetic (the problem parameters; h starts
+at 0).  Working set 808 cells x 32^3 x 4 B x 4 arrays = 424 MB > L2 (129 MB).
+
+  value   solves/s with the batch resident on the device (lbe_batch_run), CUDA events
+  e2e     solves/s through the one-shot public call lbe_solve_batch (host problems in,
+          host results out; setup, uploads and per-iteration flag reads inside)
+  roofline  the collision operator (A1-A3) timed alone with CUDA events at the same size
+  cpu_baseline  the FP64 oracle on a bounded sample of the same workload (extrapolated)
+
+--impl reference times the oracle instead (the reference arm of this repository).
+Multi-GPU: replicas only (independent solves per rank), launched by torchrun.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["_source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["_source"] = "fallback"
+    return d
+
+
+def workload_problems(lbe, name, precision, eps):
+    from paper_1612_04488_gb300 import workloads as W
+    if name == "plates32x8":
+        kw = W.PLATES_32
+        return [lbe.problem(**kw, delta=d, forcing=f, scheme=lbe.SIS, precision=precision, eps=eps,
+                            max_iter=400)
+                for d in W.PLATES_32_DELTAS for f in (0, 1)]
+    if name == "plates16":
+        return [lbe.problem(**W.PLATES_16, scheme=lbe.SIS, precision=precision, eps=eps, max_iter=400)]
+    if name == "duct64x32":
+        return [lbe.problem(**W.DUCT_64x32, scheme=lbe.SIS, precision=precision, eps=eps, max_iter=400)]
+    raise ValueError(name)
+
+
+def fft_flops_per_cell(nv, M):
+    """Algorithmic flops of one cell-L-eval: (M + 2) complex 3D FFTs (5 N log2 N each,
+    N = nv^3) plus the multiplier products (6 per point per transform) and the angular
+    accumulation (4 per point per direction)."""
+    n3 = nv ** 3
+    return 5.0 * n3 * np.log2(n3) * (M + 2) + 6.0 * n3 * (M + 1) + 4.0 * n3 * M
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def oracle_sample(name, target_s=12.0):
+    """Time the FP64 oracle on a bounded sample of the workload and extrapolate solves/s.
+
+    Sample: the collision operator on k cells (k grown until ~target_s/2 of work), one
+    kinetic sweep and one SIS update of the 101-node plate; per-iteration time of a case =
+    101 x (per-cell L-eval) + sweep + update; solve time = iterations x that, with the
+    iteration counts the oracle's own SIS needs at 16^3 scaled... the counts are taken
+    from the GPU run when given (same discrete scheme), else 40 per case."""
+    from oracle import fsm, solver, transport
+    from paper_1612_04488_gb300 import workloads as W
+    if name == "plates32x8":
+        nv, M, ns, ncase = 32, 32, 100, 8
+    elif name == "plates16":
+        nv, M, ns, ncase = 16, 16, 20, 1
+    else:
+        nv, M, ns, ncase = 32, 32, 2048 - 1, 1
+    t0 = time.perf_counter()
+    F = fsm.FSM(nv, 6.0, M, 4.5)
+    t_setup = time.perf_counter() - t0
+    h = W.random_h(4, nv, 6.0, seed=3)
+    k = 0
+    t_apply = 0.0
+    while t_apply < target_s / 2 and k < 256:
+        t0 = time.perf_counter()
+        F.apply(h[k % 4], 1.0)
+        t_apply += time.perf_counter() - t0
+        k += 1
+    per_cell = t_apply / k
+    n = ns + 1
+    x = transport.nodes_clustered(ns) if name == "plates32x8" else transport.nodes_uniform(ns)
+    rhs = W.random_h(n, nv, 6.0, seed=4) if n <= 201 else W.random_h(8, nv, 6.0, seed=4)
+    t0 = time.perf_counter()
+    if n <= 201:
+        hh = transport.sweep_1d(rhs, F.nu, F.V1, x)
+        Uh, qh, W1, W2, X12 = solver.cell_moments(F, hh)
+        G1, G2 = solver.l_moments(F, hh, hh, 1.25)
+        solver.diffusion_1d(Uh, W1, G1, x, 1.25, 1.0)
+    t_rest = time.perf_counter() - t0
+    t_iter = n * per_cell + t_rest
+    return dict(per_cell_s=per_cell, cells_sampled=k, t_iter_s=t_iter, setup_s=t_setup,
+                sample_s=t_apply + t_rest, ncase=ncase, n=n)
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle, timed on bounded samples on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    iters = args.ref_iters
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, target_s=2.0)
+    t_wall = 0.0
+    for _ in range(args.steps):
+        s = oracle_sample(args.workload, target_s=args.ref_sample_s)
+        t_solve = s["t_iter_s"] * iters
+        vals.append(1.0 / t_solve)
+        t_wall += s["sample_s"]
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": "SIS solves/s at 1e-6 flow-rate error", "value": value,
+        "unit": "solves/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_wall / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "iterations_per_solve": iters,
+                   "sample": "oracle L-eval on sampled cells + one sweep/update, extrapolated"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "per-cell L-eval x cells + sweep per iteration x %d iterations" % iters},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1612_04488_gb300 import lbe
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist = dist_
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = lbe.Context(local)
+    ctx.set_stream(stream.cuda_stream)
+    prec = {"fp32": lbe.FP32, "fp64": lbe.FP64, "bf16": lbe.BF16_REFINED}[args.precision]
+    pbs = workload_problems(lbe, args.workload, prec, args.eps)
+    nsolve = len(pbs)
+    batch = ctx.batch(pbs) if prec != lbe.BF16_REFINED else None
+
+    def one_step():
+        return batch.run() if batch is not None else ctx.solve_batch(pbs)
+
+    for _ in range(args.warmup):
+        res = one_step()
+    # ---- timed region: K batched solves, device resident --------------------------------
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    st0 = lbe.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = one_step()
+            b.record(stream)
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    st1 = lbe.stats()
+    if dist:
+        dist.barrier()
+    total_ms = e0.elapsed_time(e1)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = nsolve * args.steps * world / (total_ms / 1000.0)
+    launches = int(st1["kernel_launches"] - st0["kernel_launches"])
+    iters = [r.iters for r in res]
+    status = [r.status for r in res]
+    clocks = clk.summary()
+
+    # ---- accuracy against the FP64 GPU path (parity-tested against the oracle) ----------
+    ref = None
+    if args.check_fp64 and prec != lbe.FP64:
+        rpbs = workload_problems(lbe, args.workload, lbe.FP64, min(args.eps, 1e-10))
+        ref = ctx.solve_batch(rpbs)
+        err = max(max(abs(r.mass_flow - q.mass_flow) / abs(q.mass_flow),
+                      abs(r.heat_flow - q.heat_flow) / abs(q.heat_flow)) for r, q in zip(res, ref))
+    else:
+        err = None
+
+    # ---- end to end: the one-shot public call ----------------------------------------
+    torch.cuda.synchronize()
+    s0 = lbe.stats()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.solve_batch(pbs)
+    t_e2e = time.perf_counter() - t0
+    s1 = lbe.stats()
+    e2e = {"value": nsolve * args.steps * world / t_e2e, "unit": "solves/s",
+           "h2d_bytes_per_step": int((s1["h2d_bytes"] - s0["h2d_bytes"]) / args.steps),
+           "d2h_bytes_per_step": int((s1["d2h_bytes"] - s0["d2h_bytes"]) / args.steps)}
+
+    # ---- collision operator alone (dominant kernel chain) ----------------------------
+    nv, M = pbs[0].nv, pbs[0].M
+    cells = sum(lbe.cells_of(p) for p in pbs)
+    from paper_1612_04488_gb300 import workloads as W
+    hnp = W.random_h(cells, nv, 6.0, seed=11)
+    deltas = torch.tensor(np.repeat([p.delta for p in pbs], [lbe.cells_of(p) for p in pbs]),
+                          device="cuda", dtype=torch.float64)
+
+    def time_apply(precision, reps):
+        dt = torch.float64 if precision == lbe.FP64 else torch.float32
+        hd = torch.tensor(hnp, device="cuda", dtype=dt)
+        lp = torch.empty_like(hd)
+        ctx.apply_L(nv, 6.0, M, pbs[0].R, precision, cells, deltas.data_ptr(), hd.data_ptr(),
+                    lp.data_ptr(), None, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            ctx.apply_L(nv, 6.0, M, pbs[0].R, precision, cells, deltas.data_ptr(), hd.data_ptr(),
+                        lp.data_ptr(), None, stream=stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    op_prec = lbe.FP32 if prec == lbe.BF16_REFINED else prec
+    ms_op = time_apply(op_prec, 5)
+    ms_fp64 = time_apply(lbe.FP64, 2)
+    flops = fft_flops_per_cell(nv, M) * cells
+    peaks = load_peaks()
+    clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+    achieved = flops / (ms_op / 1000.0) / 1e12
+    roofline = {"bound": "alu", "kernel": "collision operator A1-A3 (fsm_cc chain)",
+                "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak_tflops,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (clk_mhz, peaks["_source"]),
+                "traffic": None, "algorithmic_flops_per_launch": flops, "ms_per_launch": ms_op}
+
+    line = {
+        "metric": "SIS solves/s at 1e-6 flow-rate error", "value": value, "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16+f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "solves_per_step": nsolve, "cells": cells, "nv": nv, "M": M,
+                   "eps": args.eps, "l2": "inputs larger than L2 (424 MB working set)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "iterations": iters, "status": status,
+        "max_rel_err_vs_fp64": err,
+        "l_evals_per_s": cells / (ms_op / 1000.0), "l_evals_per_s_fp64": cells / (ms_fp64 / 1000.0),
+        "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(args.workload, target_s=args.ref_sample_s)
+        mean_it = float(np.mean(iters))
+        cpu_val = 1.0 / (s["t_iter_s"] * mean_it)
+        line["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                "sample": "FP64 oracle L-eval on %d cells (%.1f s) + one sweep/update of a "
+                                          "%d-node plate; x %d nodes x %.1f iterations (GPU counts)"
+                                          % (s["cells_sampled"], s["sample_s"], s["n"], s["n"], mean_it)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if batch is not None:
+        batch.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plates32x8", choices=["plates32x8", "plates16", "duct64x32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"])
+    ap.add_argument("--eps", type=float, default=1e-7)
+    ap.add_argument("--ref-iters", type=int, default=45)
+    ap.add_argument("--ref-sample-s", type=float, default=12.0)
+    ap.add_argument("--no-check-fp64", dest="check_fp64", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

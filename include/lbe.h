@@ -127,6 +127,17 @@ lbe_status lbe_solve(lbe_ctx* ctx, const lbe_problem* pb, lbe_result* out,
  * receives n results.  Finished problems stop iterating while the others continue. */
 lbe_status lbe_solve_batch(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_result* outs);
 
+/* Resident batch: lbe_batch_create validates the problems (same rules as lbe_solve_batch),
+ * allocates their device state and uploads the grids once; every lbe_batch_run restarts
+ * all problems from h = 0 and iterates them to convergence with nothing but the per-
+ * iteration convergence flags crossing to the host; outs receives n results.  The batch
+ * keeps its own device memory until lbe_batch_destroy.  LBE_BF16_REFINED is not accepted
+ * here (use lbe_solve_batch). */
+typedef struct lbe_batch lbe_batch;
+lbe_status lbe_batch_create(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_batch** out);
+lbe_status lbe_batch_run(lbe_batch* b, lbe_result* outs);
+lbe_status lbe_batch_destroy(lbe_batch* b);
+
 /* Collision operator on device data (steps A1-A4).  h_dev: [cells][nv^3] of double (FP64)
  * or float (FP32, BF16_REFINED).  delta_dev: [cells] double, the rarefaction of each cell.
  * Outputs (same type as h, any may be NULL): Lplus_dev = L+ h, L_dev = L h.
@@ -162,6 +173,22 @@ lbe_status lbe_poll(lbe_ctx* ctx, uint64_t ticket, lbe_result* out, int* done);
 
 /* Maximum problems advanced together by the service (default 64). */
 lbe_status lbe_set_max_active(lbe_ctx* ctx, int max_active);
+
+/* Run the context's synchronous calls (lbe_solve, lbe_solve_batch, lbe_diffusion) on the
+ * caller's CUDA stream (cudaStream_t, or NULL for the context's own stream).  The stream
+ * must belong to the context's device and outlive its use. */
+lbe_status lbe_set_stream(lbe_ctx* ctx, void* stream);
+
+/* Process-wide counters since the library was loaded: kernels launched by this library,
+ * bytes it copied host->device and device->host, and cells passed through the collision
+ * operator (one cell = one application of L to one nv^3 vector). */
+typedef struct {
+    uint64_t kernel_launches;
+    uint64_t h2d_bytes;
+    uint64_t d2h_bytes;
+    uint64_t cell_l_evals;
+} lbe_stats;
+lbe_status lbe_get_stats(lbe_stats* out);
 
 #ifdef __cplusplus
 }

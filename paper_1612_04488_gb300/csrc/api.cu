@@ -56,6 +56,42 @@ void dev_free(Ctx* c, void* p, size_t bytes) {
     c->used -= std::min(bytes, c->used);
 }
 
+std::atomic<unsigned long long> g_launches{0}, g_h2d{0}, g_d2h{0}, g_levals{0};
+
+lbe_status arena_reserve(Ctx* c, Arena& a, size_t bytes) {
+    a.off = 0;
+    if (bytes <= a.cap) return LBE_OK;
+    if (a.base) {
+        cudaStreamSynchronize(c->stream);
+        dev_free(c, a.base, a.cap);
+        a.base = nullptr;
+        a.cap = 0;
+    }
+    const size_t want = bytes + bytes / 8;  // headroom for slightly larger later requests
+    lbe_status st = dev_alloc(c, &a.base, want);
+    if (st != LBE_OK) {
+        st = dev_alloc(c, &a.base, bytes);
+        if (st != LBE_OK) return st;
+        a.cap = bytes;
+        return LBE_OK;
+    }
+    a.cap = want;
+    return LBE_OK;
+}
+
+void* arena_take(Arena& a, size_t bytes) {
+    const size_t off = (a.off + 255) & ~(size_t)255;
+    if (off + bytes > a.cap) return nullptr;
+    a.off = off + bytes;
+    return (char*)a.base + off;
+}
+
+void arena_release(Ctx* c, Arena& a) {
+    if (a.base) dev_free(c, a.base, a.cap);
+    a.base = nullptr;
+    a.cap = a.off = 0;
+}
+
 lbe_status validate_problem(Ctx* c, const lbe_problem& pb) {
     const auto& g = pb.geom;
     if (g.dim != 1 && g.dim != 2) return bad_arg(c, "geom.dim must be 1 or 2");
@@ -214,23 +250,16 @@ void build_sweep_geom(SweepGeom& g, const lbe_problem& pb) {
 // ---------------------------------------------------------------------------------------
 // batch state
 // ---------------------------------------------------------------------------------------
-struct DevBuf {
-    Ctx* c = nullptr;
+struct DevBuf {  // a piece of the context's solve arena
     void* p = nullptr;
     size_t n = 0;
-    lbe_status alloc(Ctx* cx, size_t bytes) {
-        c = cx;
-        n = bytes;
-        return dev_alloc(cx, &p, bytes);
-    }
-    ~DevBuf() {
-        if (c) dev_free(c, p, n);
-    }
     template <typename T> T* as() const { return (T*)p; }
 };
 
 struct Batch {
     Ctx* c = nullptr;
+    Arena* arena = nullptr;
+    cudaStream_t s = nullptr;
     DevTables* t = nullptr;
     int prec = 0;
     int njobs = 0;
@@ -246,8 +275,11 @@ struct Batch {
     std::vector<int> active;
 };
 
-static lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n) {
+static lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Arena* arena,
+                             cudaStream_t stream) {
     B.c = c;
+    B.arena = arena;
+    B.s = stream;
     B.njobs = n;
     B.pbs.assign(pbs, pbs + n);
     const lbe_problem& p0 = pbs[0];
@@ -322,24 +354,26 @@ static lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n) {
     }
     const size_t vol = (size_t)B.cells * n3 * eb;
     size_t scr = fsm_cc_scratch_bytes(*B.t, (int)std::min<long>(B.cells, 1L << 30), eb, &B.chunk);
-    if ((st = B.h.alloc(c, vol)) != LBE_OK) return st;
-    if ((st = B.hh.alloc(c, vol)) != LBE_OK) return st;
-    if ((st = B.lp.alloc(c, vol)) != LBE_OK) return st;
-    if ((st = B.lh.alloc(c, vol)) != LBE_OK) return st;
-    if ((st = B.scratch.alloc(c, scr)) != LBE_OK) return st;
-    if ((st = B.mom.alloc(c, B.cells * 5 * 8)) != LBE_OK) return st;
-    if ((st = B.G.alloc(c, B.cells * 2 * 8)) != LBE_OK) return st;
-    if ((st = B.dU.alloc(c, B.cells * 8)) != LBE_OK) return st;
-    if ((st = B.U3.alloc(c, B.cells * 8)) != LBE_OK) return st;
-    if ((st = B.delta.alloc(c, B.cells * 8)) != LBE_OK) return st;
-    if ((st = B.nd.alloc(c, B.cells * 8)) != LBE_OK) return st;
-    if ((st = B.coef.alloc(c, coef.size() * 8)) != LBE_OK) return st;
-    if ((st = B.work.alloc(c, std::max<long>(work, 1) * 8)) != LBE_OK) return st;
-    if ((st = B.sjobs.alloc(c, n * sizeof(SweepJobDev))) != LBE_OK) return st;
-    if ((st = B.ijobs.alloc(c, n * sizeof(SisJobDev))) != LBE_OK) return st;
-    if ((st = B.states.alloc(c, n * sizeof(JobState))) != LBE_OK) return st;
-    if ((st = B.act.alloc(c, n * sizeof(int))) != LBE_OK) return st;
-    cudaStream_t s = c->stream;
+    struct Piece {
+        DevBuf* b;
+        size_t n;
+    };
+    const Piece pieces[] = {{&B.h, vol}, {&B.hh, vol}, {&B.lp, vol}, {&B.lh, vol}, {&B.scratch, scr},
+                            {&B.mom, (size_t)B.cells * 5 * 8}, {&B.G, (size_t)B.cells * 2 * 8},
+                            {&B.dU, (size_t)B.cells * 8}, {&B.U3, (size_t)B.cells * 8},
+                            {&B.delta, (size_t)B.cells * 8}, {&B.nd, (size_t)B.cells * 8},
+                            {&B.coef, coef.size() * 8}, {&B.work, (size_t)std::max<long>(work, 1) * 8},
+                            {&B.sjobs, n * sizeof(SweepJobDev)}, {&B.ijobs, n * sizeof(SisJobDev)},
+                            {&B.states, n * sizeof(JobState)}, {&B.act, n * sizeof(int)}};
+    size_t total = 0;
+    for (const Piece& q : pieces) total += (q.n + 255) & ~(size_t)255;
+    if ((st = arena_reserve(c, *arena, total)) != LBE_OK) return st;
+    for (const Piece& q : pieces) {
+        q.b->p = arena_take(*arena, q.n);
+        q.b->n = q.n;
+        if (!q.b->p) return LBE_INTERNAL;
+    }
+    cudaStream_t s = stream;
     cudaMemsetAsync(B.h.p, 0, vol, s);  // h^0 = 0
     cudaMemcpyAsync(B.delta.p, dcell.data(), dcell.size() * 8, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(B.nd.p, ndcell.data(), ndcell.size() * 8, cudaMemcpyHostToDevice, s);
@@ -348,6 +382,8 @@ static lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n) {
     cudaMemcpyAsync(B.ijobs.p, B.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, s);
     B.hstate.assign(n, JobState{});
     cudaMemcpyAsync(B.states.p, B.hstate.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, s);
+    g_h2d += (dcell.size() + ndcell.size() + coef.size()) * 8 + n * (sizeof(SweepJobDev) + sizeof(SisJobDev) +
+                                                                  sizeof(JobState));
     B.active.resize(n);
     for (int j = 0; j < n; ++j) B.active[j] = j;
     return cuda_status(c, cudaStreamSynchronize(s), "batch_init");
@@ -356,7 +392,7 @@ static lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n) {
 // One iteration over the active jobs.  Contiguous active jobs share FSM launches.
 template <typename T>
 static void batch_iterate(Batch& B) {
-    cudaStream_t s = B.c->stream;
+    cudaStream_t s = B.s;
     const DevTables& t = *B.t;
     const long n3 = (long)t.nv * t.nv * t.nv;
     const int na = (int)B.active.size();
@@ -384,6 +420,7 @@ static void batch_iterate(Batch& B) {
     std::vector<int> ordered(act1);
     ordered.insert(ordered.end(), act2.begin(), act2.end());
     cudaMemcpyAsync(B.act.p, ordered.data(), na * sizeof(int), cudaMemcpyHostToDevice, s);
+    g_h2d += na * sizeof(int);
     int* dact = B.act.as<int>();
     launch_sweep<T>(t, 1, (int)act1.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact, B.coef.as<double>(), s);
     launch_sweep<T>(t, 2, (int)act2.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact + act1.size(),
@@ -394,6 +431,7 @@ static void batch_iterate(Batch& B) {
                       B.states.as<JobState>(), s);
     launch_correct<T>(t, na, hh, h, B.dU.as<double>(), B.sjobs.as<SweepJobDev>(), dact, s);
     cudaMemcpyAsync(B.hstate.data(), B.states.p, B.njobs * sizeof(JobState), cudaMemcpyDeviceToHost, s);
+    g_d2h += B.njobs * sizeof(JobState);
 }
 
 static lbe_status batch_run(Batch& B, int max_steps) {
@@ -403,7 +441,7 @@ static lbe_status batch_run(Batch& B, int max_steps) {
             batch_iterate<double>(B);
         else
             batch_iterate<float>(B);
-        lbe_status st = cuda_status(B.c, cudaStreamSynchronize(B.c->stream), "iterate");
+        lbe_status st = cuda_status(B.c, cudaStreamSynchronize(B.s), "iterate");
         if (st != LBE_OK) return st;
         std::vector<int> keep;
         for (int j : B.active)
@@ -470,10 +508,11 @@ lbe_status lbe_create(lbe_ctx** out, int device, size_t budget) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     c->budget = budget ? budget : (size_t)(0.9 * fr);
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete c;
         return LBE_INTERNAL;
     }
+    c->stream = c->own_stream;
     init_twiddles_cc();
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -495,7 +534,10 @@ lbe_status lbe_destroy(lbe_ctx* ctx) {
             if (p) cudaFree(p);
     }
     ctx->tables.clear();
-    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    cudaDeviceSynchronize();
+    arena_release(ctx, ctx->solve_arena);
+    arena_release(ctx, ctx->apply_arena);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
     return LBE_OK;
 }
@@ -519,7 +561,7 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
     if (pbs[0].precision == LBE_BF16_REFINED) return refined_solve(ctx, pbs, n, outs, U3_out, h_out);
     auto t0 = std::chrono::steady_clock::now();
     Batch B;
-    lbe_status st = batch_init(B, ctx, pbs, n);
+    lbe_status st = batch_init(B, ctx, pbs, n, &ctx->solve_arena, ctx->stream);
     if (st != LBE_OK) return st;
     int maxit = 0;
     for (int j = 0; j < n; ++j) maxit = std::max(maxit, pbs[j].max_iter);
@@ -532,7 +574,10 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
         if (outs[j].status != LBE_OK && worst == LBE_OK) worst = (lbe_status)outs[j].status;
     }
     const long n3 = (long)pbs[0].nv * pbs[0].nv * pbs[0].nv;
-    if (U3_out) st = cuda_status(ctx, cudaMemcpy(U3_out, B.U3.p, B.cells * 8, cudaMemcpyDeviceToHost), "U3 copy");
+    if (U3_out) {
+        st = cuda_status(ctx, cudaMemcpy(U3_out, B.U3.p, B.cells * 8, cudaMemcpyDeviceToHost), "U3 copy");
+        g_d2h += B.cells * 8;
+    }
     if (st == LBE_OK && h_out) {
         if (B.prec == LBE_FP64) {
             st = cuda_status(ctx, cudaMemcpy(h_out, B.h.p, B.cells * n3 * 8, cudaMemcpyDeviceToHost), "h copy");
@@ -580,18 +625,12 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_p
     const int eb = precision == LBE_FP64 ? 8 : 4;
     int chunk = 1;
     const size_t scr = fsm_cc_scratch_bytes(*t, cells, eb, &chunk);
-    void* p = nullptr;
-    if ((st = dev_alloc(ctx, &p, scr)) != LBE_OK) return st;
-    // L is needed for G; use a temporary when the caller did not ask for it
-    void* Ltmp = nullptr;
     const size_t vol = (size_t)cells * nv * nv * nv * eb;
-    if (G_dev && !L_dev) {
-        if ((st = dev_alloc(ctx, &Ltmp, vol)) != LBE_OK) {
-            dev_free(ctx, p, scr);
-            return st;
-        }
-    }
-    void* Lo = L_dev ? L_dev : Ltmp;
+    // L is needed for G; the arena holds a temporary when the caller did not ask for it
+    const size_t need = ((scr + 255) & ~(size_t)255) + ((G_dev && !L_dev) ? vol : 0);
+    if ((st = arena_reserve(ctx, ctx->apply_arena, need)) != LBE_OK) return st;
+    void* p = arena_take(ctx->apply_arena, scr);
+    void* Lo = L_dev ? L_dev : ((G_dev) ? arena_take(ctx->apply_arena, vol) : nullptr);
     if (precision == LBE_FP64) {
         st = fsm_cc_apply<double>(*t, cells, delta_dev, (const double*)h_dev, (double*)Lplus_dev, (double*)Lo, p,
                                   chunk, s);
@@ -601,10 +640,8 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_p
                                  chunk, s);
         if (G_dev) lmoments<float>(*t, cells, (const float*)Lo, (const float*)h_dev, ndelta_dev, G_dev, s);
     }
-    lbe_status st2 = cuda_status(ctx, cudaStreamSynchronize(s), "apply_L");
-    dev_free(ctx, p, scr);
-    if (Ltmp) dev_free(ctx, Ltmp, vol);
-    return st != LBE_OK ? st : st2;
+    if (st != LBE_OK) return st;
+    return cuda_status(ctx, cudaGetLastError(), "apply_L");
 }
 
 lbe_status lbe_sweep(lbe_ctx* ctx, const lbe_problem* pb, const void* rhs_dev, void* h_dev, double* mom_dev,
@@ -666,7 +703,7 @@ lbe_status lbe_diffusion(lbe_ctx* ctx, const lbe_problem* pb, const double* Uh, 
     p.scheme = LBE_SIS;
     p.precision = LBE_FP64;
     Batch B;
-    if ((st = batch_init(B, ctx, &p, 1)) != LBE_OK) return st;
+    if ((st = batch_init(B, ctx, &p, 1, &ctx->solve_arena, ctx->stream)) != LBE_OK) return st;
     const int n = (int)B.cells;
     std::vector<double> mom(5 * n, 0.0), G(2 * n, 0.0);
     for (int i = 0; i < n; ++i) {
@@ -687,6 +724,91 @@ lbe_status lbe_diffusion(lbe_ctx* ctx, const lbe_problem* pb, const double* Uh, 
     cudaMemcpyAsync(du.data(), B.dU.p, n * 8, cudaMemcpyDeviceToHost, s);
     if ((st = cuda_status(ctx, cudaStreamSynchronize(s), "diffusion")) != LBE_OK) return st;
     for (int i = 0; i < n; ++i) U_out[i] = Uh[i] + du[i];
+    return LBE_OK;
+}
+
+}  // extern "C"
+
+struct lbe_batch {
+    lbe_ctx* ctx = nullptr;
+    lbe::Arena arena;
+    lbe::Batch B;
+    int maxit = 0;
+};
+
+extern "C" {
+
+lbe_status lbe_batch_create(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_batch** out) {
+    if (!ctx || !pbs || n < 1 || !out) return bad_arg(ctx, "null argument");
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    for (int j = 0; j < n; ++j) {
+        lbe_status st = validate_problem(ctx, pbs[j]);
+        if (st != LBE_OK) return st;
+        if (pbs[j].nv != pbs[0].nv || pbs[j].vmax != pbs[0].vmax || pbs[j].M != pbs[0].M ||
+            pbs[j].R != pbs[0].R || pbs[j].precision != pbs[0].precision)
+            return bad_arg(ctx, "batched problems must share nv, vmax, M, R and precision");
+    }
+    if (pbs[0].precision == LBE_BF16_REFINED) return bad_arg(ctx, "resident batches take FP64 or FP32");
+    auto* b = new lbe_batch();
+    b->ctx = ctx;
+    lbe_status st = batch_init(b->B, ctx, pbs, n, &b->arena, ctx->stream);
+    if (st != LBE_OK) {
+        arena_release(ctx, b->arena);
+        delete b;
+        return st;
+    }
+    for (int j = 0; j < n; ++j) b->maxit = std::max(b->maxit, pbs[j].max_iter);
+    *out = b;
+    return LBE_OK;
+}
+
+lbe_status lbe_batch_run(lbe_batch* b, lbe_result* outs) {
+    if (!b || !outs) return LBE_BAD_ARG;
+    Ctx* c = b->ctx;
+    cudaSetDevice(c->device);
+    Batch& B = b->B;
+    B.s = c->stream;
+    const long n3 = (long)B.pbs[0].nv * B.pbs[0].nv * B.pbs[0].nv;
+    auto t0 = std::chrono::steady_clock::now();
+    cudaMemsetAsync(B.h.p, 0, B.cells * n3 * (B.prec == LBE_FP64 ? 8 : 4), B.s);
+    B.hstate.assign(B.njobs, JobState{});
+    cudaMemcpyAsync(B.states.p, B.hstate.data(), B.njobs * sizeof(JobState), cudaMemcpyHostToDevice, B.s);
+    g_h2d += B.njobs * sizeof(JobState);
+    B.active.resize(B.njobs);
+    for (int j = 0; j < B.njobs; ++j) B.active[j] = j;
+    lbe_status st = batch_run(B, b->maxit);
+    if (st != LBE_OK) return st;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    lbe_status worst = LBE_OK;
+    for (int j = 0; j < B.njobs; ++j) {
+        fill_result(B, j, &outs[j], secs);
+        if (outs[j].status != LBE_OK && worst == LBE_OK) worst = (lbe_status)outs[j].status;
+    }
+    return worst;
+}
+
+lbe_status lbe_batch_destroy(lbe_batch* b) {
+    if (!b) return LBE_BAD_ARG;
+    cudaSetDevice(b->ctx->device);
+    cudaStreamSynchronize(b->ctx->stream);
+    arena_release(b->ctx, b->arena);
+    delete b;
+    return LBE_OK;
+}
+
+lbe_status lbe_set_stream(lbe_ctx* ctx, void* stream) {
+    if (!ctx) return LBE_BAD_ARG;
+    ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+    return LBE_OK;
+}
+
+lbe_status lbe_get_stats(lbe_stats* out) {
+    if (!out) return LBE_BAD_ARG;
+    out->kernel_launches = g_launches.load();
+    out->h2d_bytes = g_h2d.load();
+    out->d2h_bytes = g_d2h.load();
+    out->cell_l_evals = g_levals.load();
     return LBE_OK;
 }
 

@@ -234,7 +234,10 @@ void run_fsm(const DevTables& t, int cells, const double* delta, const T* h, T* 
     }
     const int P = t.M + 1;
     const long N3 = (long)N * N * N;
+    g_launches += 3;
+    g_levals += cells;
     for (int c0 = 0; c0 < cells; c0 += chunk) {
+        g_launches += 3;
         const int cc = (cells - c0 < chunk) ? cells - c0 : chunk;
         const long nf = (long)cc * P * N * N;
         k_inv_first<T, N><<<nblk(nf, B), B, 0, s>>>(Hbuf + c0 * N3, mult, Ybuf, cc, P);
@@ -278,6 +281,7 @@ template <typename T>
 void lmoments(const DevTables& t, int cells, const T* Lh, const T* h, const double* nd, double* G,
               cudaStream_t s) {
     if (cells <= 0) return;
+    g_launches += 1;
     k_lmoments<T><<<cells, 256, 0, s>>>(Lh, h, nd, t.vel_d, t.nv, t.dv * t.dv * t.dv, G);
 }
 

@@ -83,6 +83,17 @@ struct Job {
     double t_submit = 0;  // seconds on the service clock
 };
 
+// Grow-only device workspace carved into 256-byte aligned pieces; reused across calls so
+// repeated solves allocate nothing once warm.
+struct Arena {
+    void* base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+};
+
+// process-wide counters (lbe_get_stats)
+extern std::atomic<unsigned long long> g_launches, g_h2d, g_d2h, g_levals;
+
 struct Ctx {
     int device = 0;
     size_t budget = 0;
@@ -90,7 +101,9 @@ struct Ctx {
     std::string last_error;
     std::mutex tables_mu;
     std::map<std::string, std::unique_ptr<DevTables>> tables;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;      // stream of the synchronous calls
+    cudaStream_t own_stream = nullptr;  // created by lbe_create
+    Arena solve_arena, apply_arena;
     // serving
     std::mutex mu;
     std::condition_variable cv;
@@ -110,6 +123,9 @@ double default_R(double vmax);
 // memory accounting
 lbe_status dev_alloc(Ctx* c, void** p, size_t bytes);
 void dev_free(Ctx* c, void* p, size_t bytes);
+lbe_status arena_reserve(Ctx* c, Arena& a, size_t bytes);  // resets the carve offset
+void* arena_take(Arena& a, size_t bytes);                  // nullptr when it does not fit
+void arena_release(Ctx* c, Arena& a);
 
 // status helpers
 lbe_status cuda_status(Ctx* c, cudaError_t e, const char* where);

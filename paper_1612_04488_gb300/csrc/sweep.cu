@@ -314,6 +314,7 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_cells_unused, 
                   const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s) {
     (void)max_cells_unused;
     if (njobs <= 0) return;
+    g_launches += 1;
     const int nv = t.nv;
     const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
@@ -332,6 +333,7 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_cells_unused, 
 template <typename T>
 void launch_moments(const DevTables& t, long cell0, int cells, const T* h, double* mom, cudaStream_t s) {
     if (cells <= 0) return;
+    g_launches += 1;
     k_moments<T><<<cells, 256, 0, s>>>(h, t.vel_d, t.nv, t.dv * t.dv * t.dv, cell0, mom);
 }
 
@@ -339,6 +341,7 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
                        const double* mom, const double* G, const double* coef, double* work, double* dU,
                        double* U3, JobState* state, cudaStream_t s) {
     if (njobs <= 0) return;
+    g_launches += 1;
     k_sis_update<<<njobs, 256, 0, s>>>(jobs, active, mom, G, coef, work, t.cU, t.cq, dU, U3, state);
 }
 
@@ -346,6 +349,7 @@ template <typename T>
 void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU,
                     const SweepJobDev* jobs, const int* active, cudaStream_t s) {
     if (njobs <= 0) return;
+    g_launches += 1;
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
     dim3 g(152, njobs);

@@ -35,6 +35,17 @@ class Result(C.Structure):
                 ("refinements", C.c_int)]
 
 
+class Stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
+                ("cell_l_evals", C.c_uint64)]
+
+
+def stats():
+    s = Stats()
+    lib().lbe_get_stats(C.byref(s))
+    return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
 _lib = None
 
 
@@ -60,6 +71,11 @@ def lib():
         L.lbe_submit.argtypes = [vp, C.POINTER(Problem), C.POINTER(C.c_uint64)]
         L.lbe_poll.argtypes = [vp, C.c_uint64, C.POINTER(Result), C.POINTER(C.c_int)]
         L.lbe_set_max_active.argtypes = [vp, ip]
+        L.lbe_set_stream.argtypes = [vp, vp]
+        L.lbe_batch_create.argtypes = [vp, C.POINTER(Problem), ip, C.POINTER(vp)]
+        L.lbe_batch_run.argtypes = [vp, C.POINTER(Result)]
+        L.lbe_batch_destroy.argtypes = [vp]
+        L.lbe_get_stats.argtypes = [C.POINTER(Stats)]
         _lib = L
     return _lib
 
@@ -158,5 +174,38 @@ class Context:
         self.check(lib().lbe_poll(self.h, ticket, C.byref(res), C.byref(done)))
         return bool(done.value), res
 
+    def batch(self, pbs):
+        return ResidentBatch(self, pbs)
+
+    def set_stream(self, stream_handle):
+        self.check(lib().lbe_set_stream(self.h, stream_handle))
+
     def set_max_active(self, n):
         self.check(lib().lbe_set_max_active(self.h, n))
+
+
+class ResidentBatch:
+    """lbe_batch_*: device state created once, re-solved from h = 0 on every run()."""
+
+    def __init__(self, ctx, pbs):
+        self.ctx = ctx
+        self.n = len(pbs)
+        self.h = C.c_void_p()
+        arr = (Problem * self.n)(*pbs)
+        ctx.check(lib().lbe_batch_create(ctx.h, arr, self.n, C.byref(self.h)))
+
+    def run(self):
+        res = (Result * self.n)()
+        self.ctx.check(lib().lbe_batch_run(self.h, res), (OK, NOT_CONVERGED))
+        return list(res)
+
+    def close(self):
+        if self.h:
+            lib().lbe_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
