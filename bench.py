@@ -194,6 +194,40 @@ def run_reference(args):
     return 0
 
 
+def run_op_only(args):
+    """Collision operator alone on the workload's cells (for profiling); prints timings."""
+    import torch
+
+    from paper_1612_04488_gb300 import lbe
+    from paper_1612_04488_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx = lbe.Context(0)
+    prec = {"fp32": lbe.FP32, "fp64": lbe.FP64, "bf16": lbe.BF16_REFINED}[args.precision]
+    pbs = workload_problems(lbe, args.workload, prec, args.eps)
+    nv, M = pbs[0].nv, pbs[0].M
+    cells = sum(lbe.cells_of(p) for p in pbs)
+    dt = torch.float64 if prec == lbe.FP64 else torch.float32
+    hd = torch.tensor(W.random_h(cells, nv, 6.0, seed=11), device="cuda", dtype=dt)
+    dd = torch.full((cells,), 1.0, device="cuda", dtype=torch.float64)
+    lp = torch.empty_like(hd)
+    times = []
+    for i in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.apply_L(nv, 6.0, M, pbs[0].R, prec, cells, dd.data_ptr(), hd.data_ptr(), lp.data_ptr(), None,
+                    stream=stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        if i >= args.warmup:
+            times.append(a.elapsed_time(b))
+    print(json.dumps({"op_only": True, "workload": args.workload, "precision": args.precision, "cells": cells,
+                      "ms": times, "l_evals_per_s": cells / (np.median(times) / 1000.0)}), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -360,9 +394,12 @@ def main():
     ap.add_argument("--ref-sample-s", type=float, default=12.0)
     ap.add_argument("--no-check-fp64", dest="check_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--op-only", action="store_true", help="time the collision operator alone")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.op_only:
+        return run_op_only(args)
     return run_ours(args)
 
 
