@@ -149,6 +149,26 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R,
                        const void* h_dev, void* Lplus_dev, void* L_dev,
                        const double* ndelta_dev, double* G_dev, void* stream);
 
+/* lbe_apply_L without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code recording CUDA
+ * graphs or running a latency-critical loop, where cudaMalloc / cudaFree would synchronise
+ * the device or is not allowed mid-capture, and host frameworks whose pooling allocator
+ * owns all device memory.  It runs the same collision-operator kernels as lbe_apply_L
+ * (FP64 or FP32 only; no G moments) on caller-owned inputs and outputs, with its transform
+ * scratch taken from one file-scope device array of 32 MiB that every GPU loading this
+ * library holds until the process exits.  Cells are processed in slices that fit that
+ * array; if one cell does not fit (nv = 32 with M = 64 in FP64) the call returns
+ * LBE_BAD_ARG.  The context must already hold the operator tables for (nv, vmax, M, R): an
+ * earlier lbe_apply_L or lbe_solve with those parameters builds them; otherwise the call
+ * returns LBE_BAD_ARG instead of allocating them.  The first call on a device looks up the
+ * scratch array's device address, so make it before any stream capture.  All calls share
+ * the array and its contents persist between calls; calls that overlap on the GPU race, so
+ * serialise them (e.g. one stream).  Nothing in the array needs to start at zero.
+ * Asynchronous on `stream`. */
+lbe_status lbe_apply_L_noalloc(lbe_ctx* ctx, int nv, double vmax, int M, double R,
+                               lbe_precision precision, int cells, const double* delta_dev,
+                               const void* h_dev, void* Lplus_dev, void* L_dev, void* stream);
+
 /* Transport sweep of one problem (steps A5-A6): solves nu_eq h + v.grad h = rhs with the
  * problem's geometry and delta.  rhs_dev, h_dev: [cells][nv^3], double for FP64 else
  * float.  mom_dev (double [cells][5], may be NULL): U3, q3, W1 = F201/4, W2 = F021/4,

@@ -117,7 +117,7 @@ lbe_status validate_problem(Ctx* c, const lbe_problem& pb) {
 // ---------------------------------------------------------------------------------------
 // tables
 // ---------------------------------------------------------------------------------------
-static std::string tables_key(int nv, double vmax, int M, double R) {
+std::string tables_key(int nv, double vmax, int M, double R) {
     char b[128];
     snprintf(b, sizeof b, "%d/%.17g/%d/%.17g", nv, vmax, M, R);
     return b;
@@ -476,7 +476,6 @@ static void fill_result(const Batch& B, int j, lbe_result* r, double secs) {
 
 using namespace lbe;
 
-struct lbe_ctx : public lbe::Ctx {};
 
 extern "C" {
 

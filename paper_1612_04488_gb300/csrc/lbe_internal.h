@@ -118,6 +118,7 @@ struct Ctx {
 
 // tables
 DevTables* get_tables(Ctx* c, int nv, double vmax, int M, double R, lbe_status* st);
+std::string tables_key(int nv, double vmax, int M, double R);
 double default_R(double vmax);
 
 // memory accounting
@@ -133,3 +134,6 @@ lbe_status bad_arg(Ctx* c, const std::string& what);
 lbe_status validate_problem(Ctx* c, const lbe_problem& pb);
 
 }  // namespace lbe
+
+// The opaque handle of include/lbe.h is the context itself.
+struct lbe_ctx : public lbe::Ctx {};
