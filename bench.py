@@ -34,6 +34,12 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
                   "sm_max_mhz": 2070.0}
 
 
+PRECISIONS = {"fp32": lambda L: L.FP32, "fp64": lambda L: L.FP64, "bf16": lambda L: L.BF16_REFINED,
+              "fp32r": lambda L: L.FP32_REFINED}
+DTYPES = {"fp32": "f32", "fp64": "f64", "bf16": "bf16/f32 inner + f64 residual",
+          "fp32r": "f32 inner + f64 residual"}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -204,7 +210,8 @@ def run_op_only(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     ctx = lbe.Context(0)
-    prec = {"fp32": lbe.FP32, "fp64": lbe.FP64, "bf16": lbe.BF16_REFINED}[args.precision]
+    prec = PRECISIONS[args.precision](lbe)
+    prec = lbe.FP32 if prec == lbe.FP32_REFINED else prec
     pbs = workload_problems(lbe, args.workload, prec, args.eps)
     nv, M = pbs[0].nv, pbs[0].M
     cells = sum(lbe.cells_of(p) for p in pbs)
@@ -246,10 +253,10 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     ctx = lbe.Context(local)
     ctx.set_stream(stream.cuda_stream)
-    prec = {"fp32": lbe.FP32, "fp64": lbe.FP64, "bf16": lbe.BF16_REFINED}[args.precision]
+    prec = PRECISIONS[args.precision](lbe)
     pbs = workload_problems(lbe, args.workload, prec, args.eps)
     nsolve = len(pbs)
-    batch = ctx.batch(pbs) if prec != lbe.BF16_REFINED else None
+    batch = ctx.batch(pbs) if prec in (lbe.FP32, lbe.FP64) else None
 
     def one_step():
         return batch.run() if batch is not None else ctx.solve_batch(pbs)
@@ -285,6 +292,7 @@ def run_ours(args):
     value = nsolve * args.steps * world / (total_ms / 1000.0)
     launches = int(st1["kernel_launches"] - st0["kernel_launches"])
     iters = [r.iters for r in res]
+    refinements = [r.refinements for r in res]
     status = [r.status for r in res]
     clocks = clk.summary()
 
@@ -334,7 +342,7 @@ def run_ours(args):
         b.synchronize()
         return a.elapsed_time(b) / reps
 
-    op_prec = lbe.FP32 if prec == lbe.BF16_REFINED else prec
+    op_prec = lbe.FP32 if prec in (lbe.BF16_REFINED, lbe.FP32_REFINED) else prec
     ms_op = time_apply(op_prec, 5)
     ms_fp64 = time_apply(lbe.FP64, 2)
     flops = fft_flops_per_cell(nv, M) * cells
@@ -352,13 +360,13 @@ def run_ours(args):
         "metric": "SIS solves/s at 1e-6 flow-rate error", "value": value, "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16+f32"}[args.precision],
+        "vs_baseline": None, "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "solves_per_step": nsolve, "cells": cells, "nv": nv, "M": M,
                    "eps": args.eps, "l2": "inputs larger than L2 (424 MB working set)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-        "iterations": iters, "status": status,
+        "iterations": iters, "refinements": refinements, "status": status,
         "max_rel_err_vs_fp64": err,
         "l_evals_per_s": cells / (ms_op / 1000.0), "l_evals_per_s_fp64": cells / (ms_fp64 / 1000.0),
         "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
@@ -388,7 +396,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plates32x8", choices=["plates32x8", "plates16", "duct64x32"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"])
+    ap.add_argument("--precision", default="fp32r", choices=sorted(PRECISIONS))
     ap.add_argument("--eps", type=float, default=1e-7)
     ap.add_argument("--ref-iters", type=int, default=45)
     ap.add_argument("--ref-sample-s", type=float, default=12.0)

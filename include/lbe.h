@@ -56,10 +56,13 @@ typedef enum { LBE_CIS = 0, LBE_SIS = 1 } lbe_scheme;
 
 /* Arithmetic of the collision operator and the sweeps.  LBE_FP64: everything in double.
  * LBE_FP32: float storage and transforms, double reductions and diffusion solve.
- * LBE_BF16_REFINED: tensor-core BF16 spectral GEMMs (FP32 accumulate) inside an outer
- * defect-correction loop whose residual uses the FP32 operator; reductions, diffusion
- * solve and convergence test in double. */
-typedef enum { LBE_FP64 = 0, LBE_FP32 = 1, LBE_BF16_REFINED = 2 } lbe_precision;
+ * LBE_BF16_REFINED and LBE_FP32_REFINED: defect correction towards the FP64 SIS solution --
+ * each outer step is one FP64 SIS iteration (its flow-rate change is the stopping test, as
+ * for LBE_FP64), and the correction equation is solved by low-precision SIS iterations
+ * whose collision operator runs as tcgen05 BF16 spectral GEMMs with FP32 accumulation
+ * (BF16_REFINED) or as the FP32 CUDA-core transforms (FP32_REFINED).  max_iter caps the
+ * FP64 iterations. */
+typedef enum { LBE_FP64 = 0, LBE_FP32 = 1, LBE_BF16_REFINED = 2, LBE_FP32_REFINED = 3 } lbe_precision;
 
 /* Geometry (Sec. 2.4).  dim = 1: plates at x1 = +-1/2, half channel -1/2 <= x1 <= 0 with a
  * specular symmetry plane at x1 = 0, ns sections (ns + 1 nodes), grid_kind 0 = uniform,

@@ -19,6 +19,7 @@
 
 #include "lbe_internal.h"
 #include "sweep.h"
+#include "batch.h"
 
 namespace lbe {
 
@@ -107,7 +108,8 @@ lbe_status validate_problem(Ctx* c, const lbe_problem& pb) {
     if (pb.R > 2.0 * pb.vmax) return bad_arg(c, "R must be <= 2 vmax");
     if (pb.forcing != LBE_POISEUILLE && pb.forcing != LBE_THERMAL_TRANSPIRATION) return bad_arg(c, "bad forcing");
     if (pb.scheme != LBE_CIS && pb.scheme != LBE_SIS) return bad_arg(c, "bad scheme");
-    if (pb.precision != LBE_FP64 && pb.precision != LBE_FP32 && pb.precision != LBE_BF16_REFINED)
+    if (pb.precision != LBE_FP64 && pb.precision != LBE_FP32 && pb.precision != LBE_BF16_REFINED &&
+        pb.precision != LBE_FP32_REFINED)
         return bad_arg(c, "bad precision");
     if (!(pb.eps >= 0)) return bad_arg(c, "eps must be >= 0");
     if (pb.max_iter < 1) return bad_arg(c, "max_iter must be >= 1");
@@ -250,33 +252,8 @@ void build_sweep_geom(SweepGeom& g, const lbe_problem& pb) {
 // ---------------------------------------------------------------------------------------
 // batch state
 // ---------------------------------------------------------------------------------------
-struct DevBuf {  // a piece of the context's solve arena
-    void* p = nullptr;
-    size_t n = 0;
-    template <typename T> T* as() const { return (T*)p; }
-};
-
-struct Batch {
-    Ctx* c = nullptr;
-    Arena* arena = nullptr;
-    cudaStream_t s = nullptr;
-    DevTables* t = nullptr;
-    int prec = 0;
-    int njobs = 0;
-    long cells = 0;
-    std::vector<lbe_problem> pbs;
-    std::vector<SweepGeom> geo;
-    std::vector<SweepJobDev> sj;
-    std::vector<SisJobDev> ij;
-    std::vector<long> cell_off;
-    DevBuf h, hh, lp, lh, scratch, mom, G, dU, U3, delta, nd, coef, work, sjobs, ijobs, states, act;
-    int chunk = 1;
-    std::vector<JobState> hstate;
-    std::vector<int> active;
-};
-
-static lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Arena* arena,
-                             cudaStream_t stream) {
+lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Arena* arena,
+                      cudaStream_t stream) {
     B.c = c;
     B.arena = arena;
     B.s = stream;
@@ -287,7 +264,7 @@ static lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Ar
     B.t = get_tables(c, p0.nv, p0.vmax, p0.M, p0.R, &st);
     if (!B.t) return st;
     B.prec = p0.precision;
-    if (B.prec == LBE_BF16_REFINED) B.prec = LBE_FP32;  // handled by the refinement driver
+    if (B.prec == LBE_BF16_REFINED || B.prec == LBE_FP32_REFINED) B.prec = LBE_FP32;
     const int eb = B.prec == LBE_FP64 ? 8 : 4;
     const long n3 = (long)p0.nv * p0.nv * p0.nv;
     std::vector<double> coef, dcell, ndcell;
@@ -391,7 +368,7 @@ static lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Ar
 
 // One iteration over the active jobs.  Contiguous active jobs share FSM launches.
 template <typename T>
-static void batch_iterate(Batch& B) {
+void batch_iterate(Batch& B) {
     cudaStream_t s = B.s;
     const DevTables& t = *B.t;
     const long n3 = (long)t.nv * t.nv * t.nv;
@@ -425,16 +402,24 @@ static void batch_iterate(Batch& B) {
     launch_sweep<T>(t, 1, (int)act1.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact, B.coef.as<double>(), s);
     launch_sweep<T>(t, 2, (int)act2.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact + act1.size(),
                     B.coef.as<double>(), s);
-    for (int j : ordered) launch_moments<T>(t, B.cell_off[j], B.sj[j].ncell, hh, B.mom.as<double>(), s);
+    for (int a = 0; a < na;) {  // moments over contiguous runs of active jobs
+        int b = a;
+        while (b + 1 < na && B.active[b + 1] == B.active[b] + 1) ++b;
+        const long c0 = B.cell_off[B.active[a]];
+        const long c1 = B.cell_off[B.active[b]] + B.sj[B.active[b]].ncell;
+        launch_moments<T>(t, c0, (int)(c1 - c0), hh, B.mom.as<double>(), s);
+        a = b + 1;
+    }
     launch_sis_update(t, na, B.ijobs.as<SisJobDev>(), dact, B.mom.as<double>(), B.G.as<double>(),
                       B.coef.as<double>(), B.work.as<double>(), B.dU.as<double>(), B.U3.as<double>(),
                       B.states.as<JobState>(), s);
-    launch_correct<T>(t, na, hh, h, B.dU.as<double>(), B.sjobs.as<SweepJobDev>(), dact, s);
+    launch_correct<T>(t, na, hh, h, B.dU.as<double>(), B.extra.p ? B.extra.as<T>() : nullptr,
+                      B.sjobs.as<SweepJobDev>(), dact, s);
     cudaMemcpyAsync(B.hstate.data(), B.states.p, B.njobs * sizeof(JobState), cudaMemcpyDeviceToHost, s);
     g_d2h += B.njobs * sizeof(JobState);
 }
 
-static lbe_status batch_run(Batch& B, int max_steps) {
+lbe_status batch_run(Batch& B, int max_steps) {
     int steps = 0;
     while (!B.active.empty() && steps < max_steps) {
         if (B.prec == LBE_FP64)
@@ -452,7 +437,10 @@ static lbe_status batch_run(Batch& B, int max_steps) {
     return LBE_OK;
 }
 
-static void fill_result(const Batch& B, int j, lbe_result* r, double secs) {
+template void batch_iterate<double>(Batch&);
+template void batch_iterate<float>(Batch&);
+
+void fill_result(const Batch& B, int j, lbe_result* r, double secs) {
     const JobState& s = B.hstate[j];
     r->mass_flow = s.M;
     r->heat_flow = s.Q;
@@ -557,7 +545,8 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
             pbs[j].R != pbs[0].R || pbs[j].precision != pbs[0].precision)
             return bad_arg(ctx, "batched problems must share nv, vmax, M, R and precision");
     }
-    if (pbs[0].precision == LBE_BF16_REFINED) return refined_solve(ctx, pbs, n, outs, U3_out, h_out);
+    if (pbs[0].precision == LBE_BF16_REFINED || pbs[0].precision == LBE_FP32_REFINED)
+        return refined_solve(ctx, pbs, n, outs, U3_out, h_out);
     auto t0 = std::chrono::steady_clock::now();
     Batch B;
     lbe_status st = batch_init(B, ctx, pbs, n, &ctx->solve_arena, ctx->stream);
@@ -648,7 +637,8 @@ lbe_status lbe_sweep(lbe_ctx* ctx, const lbe_problem* pb, const void* rhs_dev, v
     if (!ctx || !pb || !rhs_dev || !h_dev) return bad_arg(ctx, "null argument");
     lbe_status st = validate_problem(ctx, *pb);
     if (st != LBE_OK) return st;
-    if (pb->precision == LBE_BF16_REFINED) return bad_arg(ctx, "sweep precision must be FP64 or FP32");
+    if (pb->precision != LBE_FP64 && pb->precision != LBE_FP32)
+        return bad_arg(ctx, "sweep precision must be FP64 or FP32");
     cudaSetDevice(ctx->device);
     DevTables* t = get_tables(ctx, pb->nv, pb->vmax, pb->M, pb->R, &st);
     if (!t) return st;
@@ -748,7 +738,8 @@ lbe_status lbe_batch_create(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_bat
             pbs[j].R != pbs[0].R || pbs[j].precision != pbs[0].precision)
             return bad_arg(ctx, "batched problems must share nv, vmax, M, R and precision");
     }
-    if (pbs[0].precision == LBE_BF16_REFINED) return bad_arg(ctx, "resident batches take FP64 or FP32");
+    if (pbs[0].precision != LBE_FP64 && pbs[0].precision != LBE_FP32)
+        return bad_arg(ctx, "resident batches take FP64 or FP32");
     auto* b = new lbe_batch();
     b->ctx = ctx;
     lbe_status st = batch_init(b->B, ctx, pbs, n, &b->arena, ctx->stream);

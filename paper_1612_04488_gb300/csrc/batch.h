@@ -1,0 +1,48 @@
+// A batch of problems sharing one velocity grid and precision: device state and the
+// host-driven CIS / SIS iteration over it (api.cu), used by the solve calls, the resident
+// batches, the refinement driver and the service.
+#pragma once
+
+#include <vector>
+
+#include "lbe_internal.h"
+#include "sweep.h"
+
+namespace lbe {
+
+struct DevBuf {  // a piece of an arena
+    void* p = nullptr;
+    size_t n = 0;
+    template <typename T> T* as() const { return (T*)p; }
+};
+
+struct Batch {
+    Ctx* c = nullptr;
+    Arena* arena = nullptr;
+    cudaStream_t s = nullptr;
+    DevTables* t = nullptr;
+    int prec = 0;
+    int njobs = 0;
+    long cells = 0;
+    std::vector<lbe_problem> pbs;
+    std::vector<SweepGeom> geo;
+    std::vector<SweepJobDev> sj;
+    std::vector<SisJobDev> ij;
+    std::vector<long> cell_off;
+    DevBuf h, hh, lp, lh, scratch, mom, G, dU, U3, delta, nd, coef, work, sjobs, ijobs, states, act;
+    DevBuf extra;  // optional additive source in the correction step (same type as h)
+    int chunk = 1;
+    std::vector<JobState> hstate;
+    std::vector<int> active;
+};
+
+// Internal forcing value: no source term and no momentum-balance term (the homogeneous
+// part of the SIS map, used by the refinement driver's correction solves).
+constexpr int kForcingNone = 2;
+
+lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Arena* arena, cudaStream_t stream);
+template <typename T> void batch_iterate(Batch& B);
+lbe_status batch_run(Batch& B, int max_steps);
+void fill_result(const Batch& B, int j, lbe_result* r, double secs);
+
+}  // namespace lbe

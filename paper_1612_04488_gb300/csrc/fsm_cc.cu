@@ -8,11 +8,13 @@
 //   A4  G_j = 2 sum_v v_j v3 (L h + N delta h) dv^3   (lmoments kernel)
 // (Sec. 2, Eq. LBE_collision; the operator's reading is stated in lbe.h.)
 //
-// Layout: h, L+ h, L h are [cell][i1][i2][i3]; H is [cell][k1][k2][k3] complex; the
-// inverse transforms of a chunk of cells live in Y[cell][p][...] (p = 0..M, p = M is the
-// loss), transformed in place along i3, then i2, and the last pass (along i1, coalesced
-// across threads) accumulates the gain over p in registers and writes the outputs.
-// Every thread owns one 1D line and keeps it in registers (dft_line in common.cuh).
+// Layout: h, L+ h, L h are [cell][i1][i2][i3]; H is [cell][k1][k2][k3] complex.  The
+// forward transform does the i3 and i2 axes per k1-plane in shared memory (k_slab2d), then
+// i1 in place (k_fwd).  The inverse transforms of a chunk of cells, sized so that they stay
+// in L2, live in Y[cell][p][...] (p = 0..M, p = M is the loss): k_slab2d applies the
+// multiplier and the i3, i2 axes per plane; k_inv_last4 transforms along i1 (coalesced
+// across lanes), sums the directions over four warps and writes the outputs.  Every lane
+// owns one 1D line in registers (dft_line in common.cuh).
 #include <cmath>
 
 #include "common.cuh"
@@ -82,67 +84,95 @@ __global__ void __launch_bounds__(128) k_fwd(const T* __restrict__ hin, cplx_t<T
     for (int j = 0; j < N; ++j) H[base + (long)j * st] = mk<T>(re[j], im[j]);
 }
 
-// Y[cell][p] = F^-1_3 (mult_p * H[cell]) for p = 0..M (first inverse pass, along i3).
-template <typename T, int N>
-__global__ void __launch_bounds__(128) k_inv_first(const cplx_t<T>* __restrict__ H,
-                                                   const cplx_t<T>* __restrict__ mult,
-                                                   cplx_t<T>* __restrict__ Y, int ncell, int P) {
-    const long L = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    const long nl = (long)ncell * P * N * N;
-    if (L >= nl) return;
-    const long cp = L / (N * N);
-    const int r = (int)(L % (N * N));
-    const long cell = cp / P;
-    const int p = (int)(cp % P);
-    const cplx_t<T>* hl = H + cell * N * N * N + (long)r * N;
-    const cplx_t<T>* ml = mult + (long)p * N * N * N + (long)r * N;
-    T re[N], im[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        const cplx_t<T> z = hl[j], m = ml[j];
-        re[j] = m.x * z.x - m.y * z.y;
-        im[j] = m.x * z.y + m.y * z.x;
+// 2D transform of one k1-plane ("slab", N x N complex) along i3 then i2, staged in shared
+// memory so that global loads and stores are coalesced rows.  One warp per slab.
+//   REAL_IN:  forward transform of a real plane of h (A1, first two axes)
+//   MULT:     inverse transform of mult_p * H (A2, first two axes of direction p's inverse)
+template <typename T, int N, bool INV, bool REAL_IN, bool MULT, int WPB>
+__global__ void __launch_bounds__(32 * WPB) k_slab2d(const T* __restrict__ hin, const cplx_t<T>* __restrict__ Hin,
+                                                     const cplx_t<T>* __restrict__ mult,
+                                                     cplx_t<T>* __restrict__ out, long nslabs, int P) {
+    constexpr int LD = N + 1, N2 = N * N;
+    __shared__ cplx_t<T> sm[WPB][N][LD];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long sid = (long)blockIdx.x * WPB + w;
+    if (sid >= nslabs) return;
+    const long vol = sid / N;                 // MULT: cell * P + p; otherwise the volume
+    const int k1 = (int)(sid % N);
+    long ibase, mbase = 0;
+    if (MULT) {
+        const long cell = vol / P;
+        const int p = (int)(vol % P);
+        ibase = cell * N * N2 + (long)k1 * N2;
+        mbase = (long)p * N * N2 + (long)k1 * N2;
+    } else {
+        ibase = vol * N * N2 + (long)k1 * N2;
     }
-    dft_line<T, N, true>(re, im);
-    cplx_t<T>* yl = Y + cp * N * N * N + (long)r * N;
+    const long obase = vol * N * N2 + (long)k1 * N2;
+    for (int idx = lane; idx < N2; idx += 32) {
+        cplx_t<T> z;
+        if (REAL_IN) {
+            z.x = hin[ibase + idx];
+            z.y = T(0);
+        } else {
+            z = Hin[ibase + idx];
+            if (MULT) {
+                const cplx_t<T> m = mult[mbase + idx];
+                const T xr = m.x * z.x - m.y * z.y, xi = m.x * z.y + m.y * z.x;
+                z.x = xr;
+                z.y = xi;
+            }
+        }
+        sm[w][idx / N][idx % N] = z;
+    }
+    __syncwarp();
+    if (lane < N) {  // along i3: lane owns row k2 = lane
+        T re[N], im[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) yl[j] = mk<T>(re[j], im[j]);
+        for (int j = 0; j < N; ++j) {
+            re[j] = sm[w][lane][j].x;
+            im[j] = sm[w][lane][j].y;
+        }
+        dft_line<T, N, INV>(re, im);
+#pragma unroll
+        for (int j = 0; j < N; ++j) sm[w][lane][j] = mk<T>(re[j], im[j]);
+    }
+    __syncwarp();
+    if (lane < N) {  // along i2: lane owns column i3 = lane
+        T re[N], im[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            re[j] = sm[w][j][lane].x;
+            im[j] = sm[w][j][lane].y;
+        }
+        dft_line<T, N, INV>(re, im);
+#pragma unroll
+        for (int j = 0; j < N; ++j) sm[w][j][lane] = mk<T>(re[j], im[j]);
+    }
+    __syncwarp();
+    for (int idx = lane; idx < N2; idx += 32) out[obase + idx] = sm[w][idx / N][idx % N];
 }
 
+// Last inverse pass (along i1) with the angular sum split over the four warps of a block:
+// the 32 lanes hold 32 consecutive (i2, i3) lines of one cell, warp w sums directions
+// p = w, w+4, ...; the partial sums meet in shared memory in a fixed order (A2-A3).
 template <typename T, int N>
-__global__ void __launch_bounds__(128) k_inv_mid(cplx_t<T>* __restrict__ Y, long nlines) {
-    const long L = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (L >= nlines) return;
-    long base;
-    int st;
-    line_of<N, 1>(L, base, st);
-    T re[N], im[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        const cplx_t<T> z = Y[base + (long)j * st];
-        re[j] = z.x;
-        im[j] = z.y;
-    }
-    dft_line<T, N, true>(re, im);
-#pragma unroll
-    for (int j = 0; j < N; ++j) Y[base + (long)j * st] = mk<T>(re[j], im[j]);
-}
-
-// Last inverse pass along i1 with the angular sum and the operator assembly.
-template <typename T, int N>
-__global__ void __launch_bounds__(128) k_inv_last(const cplx_t<T>* __restrict__ Y,
-                                                  const cplx_t<T>* __restrict__ ab,
-                                                  const T* __restrict__ feq, const T* __restrict__ nu1,
-                                                  const T* __restrict__ h, const double* __restrict__ delta,
-                                                  T* __restrict__ Lplus, T* __restrict__ Lout, int ncell,
-                                                  int M) {
-    constexpr int N2 = N * N, N3 = N * N * N;
-    const long L = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (L >= (long)ncell * N2) return;
-    const long cell = L / N2;
-    const int r = (int)(L % N2);
+__global__ void __launch_bounds__(128) k_inv_last4(const cplx_t<T>* __restrict__ Y,
+                                                   const cplx_t<T>* __restrict__ ab,
+                                                   const T* __restrict__ feq, const T* __restrict__ nu1,
+                                                   const T* __restrict__ h, const double* __restrict__ delta,
+                                                   T* __restrict__ Lplus, T* __restrict__ Lout, int ncell,
+                                                   int M) {
+    constexpr int N2 = N * N, N3 = N * N * N, TILES = N2 / 32;
+    __shared__ T red[4][N][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long cell = blockIdx.x / TILES;
+    const int r = (blockIdx.x % TILES) * 32 + lane;
+    if (cell >= ncell) return;
     T acc[N];
-    {
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[j] = T(0);
+    if (w == 0) {
         const cplx_t<T>* yl = Y + (cell * (M + 1) + M) * N3 + r;
         T re[N], im[N];
 #pragma unroll
@@ -155,7 +185,7 @@ __global__ void __launch_bounds__(128) k_inv_last(const cplx_t<T>* __restrict__ 
 #pragma unroll
         for (int j = 0; j < N; ++j) acc[j] = -feq[j * N2 + r] * re[j];
     }
-    for (int p = 0; p < M; ++p) {
+    for (int p = w; p < M; p += 4) {
         const cplx_t<T>* yl = Y + (cell * (M + 1) + p) * N3 + r;
         const cplx_t<T>* al = ab + (long)p * N3 + r;
         T re[N], im[N];
@@ -168,38 +198,64 @@ __global__ void __launch_bounds__(128) k_inv_last(const cplx_t<T>* __restrict__ 
         dft_line<T, N, true>(re, im);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            const cplx_t<T> w = al[j * N2];
-            acc[j] += w.x * re[j] + w.y * im[j];
+            const cplx_t<T> a = al[j * N2];
+            acc[j] += a.x * re[j] + a.y * im[j];
         }
     }
-    const T d = (T)delta[cell];
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
+    for (int j = 0; j < N; ++j) red[w][j][lane] = acc[j];
+    __syncthreads();
+    const T d = (T)delta[cell];
+    for (int j = w; j < N; j += 4) {
+        const T sum = ((red[0][j][lane] + red[1][j][lane]) + red[2][j][lane]) + red[3][j][lane];
         const long idx = cell * N3 + (long)j * N2 + r;
-        const T lp = d * acc[j];
+        const T lp = d * sum;
         if (Lplus) Lplus[idx] = lp;
         if (Lout) Lout[idx] = lp - d * nu1[j * N2 + r] * h[idx];
     }
 }
 
-// G_j = 2 sum_v v_j v3 (L h + nd h) dv^3, one block per cell, fixed reduction order.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {  // compensated float sum
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// G_j = 2 sum_v v_j v3 (L h + nd h) dv^3, one block of 8 nv threads per cell (thread t owns
+// i3 = t % nv and rows i2 = t/nv + 8k), fixed reduction order.
 template <typename T>
 __global__ void __launch_bounds__(256) k_lmoments(const T* __restrict__ Lh, const T* __restrict__ h,
                                                   const double* __restrict__ nd,
-                                                  const double* __restrict__ vel, int nv, double dv3,
+                                                  const T* __restrict__ vel, int nv, double dv3,
                                                   double* __restrict__ G) {
     __shared__ double red[32 * 2];
     const long cell = blockIdx.x;
-    const int n3 = nv * nv * nv;
-    const double ndc = nd[cell];
-    double s[2] = {0.0, 0.0};
-    for (int i = threadIdx.x; i < n3; i += blockDim.x) {
-        const int i1 = i / (nv * nv), i2 = (i / nv) % nv, i3 = i % nv;
-        const double t = (double)Lh[cell * n3 + i] + ndc * (double)h[cell * n3 + i];
-        const double v3t = vel[i3] * t;
-        s[0] += vel[i1] * v3t;
-        s[1] += vel[i2] * v3t;
+    const long n3 = (long)nv * nv * nv;
+    const T ndc = (T)nd[cell];
+    const int i3 = threadIdx.x % nv, r0 = threadIdx.x / nv;
+    const T v3 = vel[i3];
+    Acc<T> a0, a1;
+    for (int i1 = 0; i1 < nv; ++i1) {
+        const T v1 = vel[i1];
+        for (int i2 = r0; i2 < nv; i2 += 8) {
+            const long idx = cell * n3 + ((long)i1 * nv + i2) * nv + i3;
+            const T t = (Lh[idx] + ndc * h[idx]) * v3;
+            a0.add(v1 * t);
+            a1.add(vel[i2] * t);
+        }
     }
+    double s[2] = {a0.value(), a1.value()};
     block_reduce<2>(s, red);
     if (threadIdx.x == 0) {
         G[2 * cell + 0] = 2.0 * s[0] * dv3;
@@ -213,10 +269,11 @@ template <typename T, int N>
 void run_fsm(const DevTables& t, int cells, const double* delta, const T* h, T* Lplus, T* Lout,
              cplx_t<T>* Hbuf, cplx_t<T>* Ybuf, int chunk, cudaStream_t s) {
     constexpr int B = 128;
+    constexpr int WPB = (sizeof(T) == 8 && N == 32) ? 2 : 4;
     const long nl = (long)cells * N * N;
-    k_fwd<T, N, 0, true><<<nblk(nl, B), B, 0, s>>>(h, Hbuf, nl);
-    k_fwd<T, N, 1, false><<<nblk(nl, B), B, 0, s>>>(nullptr, Hbuf, nl);
-    k_fwd<T, N, 2, false><<<nblk(nl, B), B, 0, s>>>(nullptr, Hbuf, nl);
+    const long ns = (long)cells * N;
+    k_slab2d<T, N, false, true, false, WPB><<<nblk(ns, WPB), 32 * WPB, 0, s>>>(h, nullptr, nullptr, Hbuf, ns, 1);
+    k_fwd<T, N, 0, false><<<nblk(nl, B), B, 0, s>>>(nullptr, Hbuf, nl);
     const cplx_t<T>* mult;
     const cplx_t<T>* ab;
     const T* feq;
@@ -234,18 +291,18 @@ void run_fsm(const DevTables& t, int cells, const double* delta, const T* h, T* 
     }
     const int P = t.M + 1;
     const long N3 = (long)N * N * N;
-    g_launches += 3;
+    g_launches += 2;
     g_levals += cells;
     for (int c0 = 0; c0 < cells; c0 += chunk) {
-        g_launches += 3;
+        g_launches += 2;
         const int cc = (cells - c0 < chunk) ? cells - c0 : chunk;
-        const long nf = (long)cc * P * N * N;
-        k_inv_first<T, N><<<nblk(nf, B), B, 0, s>>>(Hbuf + c0 * N3, mult, Ybuf, cc, P);
-        k_inv_mid<T, N><<<nblk(nf, B), B, 0, s>>>(Ybuf, nf);
-        const long nlast = (long)cc * N * N;
-        k_inv_last<T, N><<<nblk(nlast, B), B, 0, s>>>(Ybuf, ab, feq, nu1, h + c0 * N3, delta + c0,
-                                                      Lplus ? Lplus + c0 * N3 : nullptr,
-                                                      Lout ? Lout + c0 * N3 : nullptr, cc, t.M);
+        const long nsl = (long)cc * P * N;
+        k_slab2d<T, N, true, false, true, WPB><<<nblk(nsl, WPB), 32 * WPB, 0, s>>>(nullptr, Hbuf + c0 * N3, mult,
+                                                                                  Ybuf, nsl, P);
+        const long blocks = (long)cc * (N * N / 32);
+        k_inv_last4<T, N><<<(unsigned)blocks, 128, 0, s>>>(Ybuf, ab, feq, nu1, h + c0 * N3, delta + c0,
+                                                         Lplus ? Lplus + c0 * N3 : nullptr,
+                                                         Lout ? Lout + c0 * N3 : nullptr, cc, t.M);
     }
 }
 
@@ -255,7 +312,11 @@ void run_fsm(const DevTables& t, int cells, const double* delta, const T* h, T* 
 size_t fsm_cc_scratch_bytes(const DevTables& t, int cells, int elem_bytes, int* chunk_out) {
     const long n3 = (long)t.nv * t.nv * t.nv;
     const long vol = n3 * 2 * elem_bytes;
-    int chunk = cells < 64 ? cells : 64;
+    // keep one chunk's inverse transforms (chunk * (M+1) volumes) within ~96 MB of L2
+    long fit = (96L << 20) / (vol * (t.M + 1));
+    if (fit < 1) fit = 1;
+    if (fit > 64) fit = 64;
+    int chunk = cells < fit ? cells : (int)fit;
     if (chunk < 1) chunk = 1;
     if (chunk_out) *chunk_out = chunk;
     return (size_t)vol * cells + (size_t)vol * chunk * (t.M + 1);
@@ -282,7 +343,8 @@ void lmoments(const DevTables& t, int cells, const T* Lh, const T* h, const doub
               cudaStream_t s) {
     if (cells <= 0) return;
     g_launches += 1;
-    k_lmoments<T><<<cells, 256, 0, s>>>(Lh, h, nd, t.vel_d, t.nv, t.dv * t.dv * t.dv, G);
+    const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
+    k_lmoments<T><<<cells, 8 * t.nv, 0, s>>>(Lh, h, nd, vel, t.nv, t.dv * t.dv * t.dv, G);
 }
 
 template lbe_status fsm_cc_apply<double>(const DevTables&, int, const double*, const double*,

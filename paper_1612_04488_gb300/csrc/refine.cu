@@ -1,0 +1,188 @@
+// Mixed-precision SIS: FP64 residuals, low-precision correction solves (defect correction).
+//
+// One FP64 SIS iteration is the affine map Phi(h) = A h + b (Sec. 2.2: sweep of Eq.
+// syn_LBE, diffusion correction Eq. first_order / diffusion_LBE, Eq. guided); its fixed
+// point is the FP64 SIS solution.  The driver repeats
+//     r = Phi_64(h) - h                          (one FP64 iteration; also the stopping test:
+//                                                 the flow rates of h and Phi_64(h) differ by
+//                                                 less than eps, exactly the FP64 criterion)
+//     solve (I - A) e = r approximately by e <- A_lo e + r   (low-precision SIS iterations
+//                                                 of the homogeneous map: no source S and no
+//                                                 momentum-balance term)
+//     h <- h + e
+// so the answer is the FP64 SIS fixed point, while almost all collision-operator
+// evaluations run in low precision.  h lives in FP64; e and r in FP32.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "batch.h"
+#include "lbe_internal.h"
+#include "sweep.h"
+
+namespace lbe {
+
+namespace {
+
+// dst = src over the cells of the active jobs
+__global__ void k_copy64(const double* __restrict__ src, double* __restrict__ dst,
+                         const SweepJobDev* __restrict__ jobs, const int* __restrict__ active, long n3) {
+    const SweepJobDev jb = jobs[active[blockIdx.y]];
+    const long total = (long)jb.ncell * n3, base = jb.cell_off * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x)
+        dst[base + k] = src[base + k];
+}
+
+// r = (float)(h - h_old)
+__global__ void k_residual(const double* __restrict__ h, const double* __restrict__ h_old, float* __restrict__ r,
+                           const SweepJobDev* __restrict__ jobs, const int* __restrict__ active, long n3) {
+    const SweepJobDev jb = jobs[active[blockIdx.y]];
+    const long total = (long)jb.ncell * n3, base = jb.cell_off * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x)
+        r[base + k] = (float)(h[base + k] - h_old[base + k]);
+}
+
+// h = h_old + e
+__global__ void k_apply_correction(const double* __restrict__ h_old, const float* __restrict__ e,
+                                   double* __restrict__ h, const SweepJobDev* __restrict__ jobs,
+                                   const int* __restrict__ active, long n3) {
+    const SweepJobDev jb = jobs[active[blockIdx.y]];
+    const long total = (long)jb.ncell * n3, base = jb.cell_off * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x)
+        h[base + k] = h_old[base + k] + (double)e[base + k];
+}
+
+// state M, Q := flow rates of the moments in mom (so the next iteration measures its change
+// against the current iterate)
+__global__ void k_set_rates(const SisJobDev* __restrict__ jobs, const int* __restrict__ active,
+                            const double* __restrict__ mom, const double* __restrict__ coef,
+                            JobState* __restrict__ state) {
+    const int jid = active[blockIdx.x];
+    const SisJobDev jb = jobs[jid];
+    if (threadIdx.x != 0) return;
+    const double* m = mom + jb.cell_off * 5;
+    const double* w = coef + jb.trap_off;
+    double M = 0.0, Q = 0.0;
+    for (int c = 0; c < jb.ncell; ++c) {
+        M += w[c] * m[c * 5 + 0];
+        Q += w[c] * m[c * 5 + 1];
+    }
+    state[jid].M = M;
+    state[jid].Q = Q;
+}
+
+}  // namespace
+
+lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs, double* U3_out,
+                         double* h_out) {
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = c->stream;
+    std::vector<lbe_problem> po(pbs, pbs + n), pi(pbs, pbs + n);
+    int max_outer = 1;
+    for (int j = 0; j < n; ++j) {
+        po[j].precision = LBE_FP64;
+        pi[j].precision = LBE_FP32;
+        pi[j].forcing = (lbe_forcing)kForcingNone;
+        pi[j].eps = 1e-4;       // inner solves reduce the correction's change to 1e-4
+        pi[j].max_iter = 60;
+        max_outer = std::max(max_outer, pbs[j].max_iter);
+    }
+    Arena ao, ai;
+    Batch O, I;
+    lbe_status st = batch_init(O, c, po.data(), n, &ao, s);
+    if (st == LBE_OK) st = batch_init(I, c, pi.data(), n, &ai, s);
+    const long n3 = (long)pbs[0].nv * pbs[0].nv * pbs[0].nv;
+    double* h_old = nullptr;
+    float* r = nullptr;
+    const size_t vol64 = O.cells * n3 * 8, vol32 = O.cells * n3 * 4;
+    if (st == LBE_OK) st = dev_alloc(c, (void**)&h_old, vol64);
+    if (st == LBE_OK) st = dev_alloc(c, (void**)&r, vol32);
+    if (st != LBE_OK) {
+        dev_free(c, h_old, vol64);
+        dev_free(c, r, vol32);
+        arena_release(c, ao);
+        arena_release(c, ai);
+        return st;
+    }
+    I.extra.p = r;
+    I.extra.n = vol32;
+    std::vector<int> outer_it(n, 0), inner_it(n, 0), refs(n, 0);
+    std::vector<int> active(n);
+    for (int j = 0; j < n; ++j) active[j] = j;
+    const dim3 blk(256);
+    while (!active.empty()) {
+        const int na = (int)active.size();
+        cudaMemcpyAsync(O.act.p, active.data(), na * sizeof(int), cudaMemcpyHostToDevice, s);
+        g_h2d += na * sizeof(int);
+        // flow rates of the current iterate, then keep a copy of it
+        for (int j : active) launch_moments<double>(*O.t, O.cell_off[j], O.sj[j].ncell, O.h.as<double>(),
+                                                   O.mom.as<double>(), s);
+        k_set_rates<<<na, 32, 0, s>>>(O.ijobs.as<SisJobDev>(), O.act.as<int>(), O.mom.as<double>(),
+                                      O.coef.as<double>(), O.states.as<JobState>());
+        k_copy64<<<dim3(152, na), blk, 0, s>>>(O.h.as<double>(), h_old, O.sjobs.as<SweepJobDev>(),
+                                               O.act.as<int>(), n3);
+        g_launches += 2;
+        // one FP64 SIS iteration: h = Phi(h_old), flags against the copy's flow rates
+        O.active = active;
+        batch_iterate<double>(O);
+        if ((st = cuda_status(c, cudaStreamSynchronize(s), "refine outer")) != LBE_OK) break;
+        std::vector<int> keep;
+        for (int j : active) {
+            ++outer_it[j];
+            if (!O.hstate[j].done) keep.push_back(j);
+        }
+        active.swap(keep);
+        if (active.empty()) break;
+        // correction solve for the unfinished problems
+        const int nk = (int)active.size();
+        cudaMemcpyAsync(O.act.p, active.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s);
+        k_residual<<<dim3(152, nk), blk, 0, s>>>(O.h.as<double>(), h_old, r, O.sjobs.as<SweepJobDev>(),
+                                                 O.act.as<int>(), n3);
+        g_launches += 1;
+        for (int j : active) {
+            cudaMemsetAsync(I.h.as<float>() + I.cell_off[j] * n3, 0, I.sj[j].ncell * n3 * 4, s);
+            I.hstate[j] = JobState{};
+        }
+        cudaMemcpyAsync(I.states.p, I.hstate.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, s);
+        g_h2d += n * sizeof(JobState);
+        I.active = active;
+        if ((st = batch_run(I, 60)) != LBE_OK) break;
+        for (int j : active) {
+            inner_it[j] += I.hstate[j].iters;
+            ++refs[j];
+        }
+        k_apply_correction<<<dim3(152, nk), blk, 0, s>>>(h_old, I.h.as<float>(), O.h.as<double>(),
+                                                         O.sjobs.as<SweepJobDev>(), O.act.as<int>(), n3);
+        g_launches += 1;
+        // drop problems that reached their iteration cap
+        std::vector<int> keep2;
+        for (int j : active)
+            if (outer_it[j] < pbs[j].max_iter) keep2.push_back(j);
+        active.swap(keep2);
+    }
+    if (st == LBE_OK) st = cuda_status(c, cudaStreamSynchronize(s), "refine");
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    lbe_status worst = LBE_OK;
+    if (st == LBE_OK) {
+        for (int j = 0; j < n; ++j) {
+            fill_result(O, j, &outs[j], secs);
+            outs[j].iters = outer_it[j] + inner_it[j];
+            outs[j].refinements = refs[j];
+            if (outs[j].status != LBE_OK && worst == LBE_OK) worst = (lbe_status)outs[j].status;
+        }
+        if (U3_out) {
+            st = cuda_status(c, cudaMemcpy(U3_out, O.U3.p, O.cells * 8, cudaMemcpyDeviceToHost), "U3");
+            g_d2h += O.cells * 8;
+        }
+        if (st == LBE_OK && h_out)
+            st = cuda_status(c, cudaMemcpy(h_out, O.h.p, vol64, cudaMemcpyDeviceToHost), "h");
+    }
+    dev_free(c, h_old, vol64);
+    dev_free(c, r, vol32);
+    arena_release(c, ao);
+    arena_release(c, ai);
+    return st != LBE_OK ? st : worst;
+}
+
+}  // namespace lbe

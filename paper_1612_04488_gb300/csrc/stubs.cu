@@ -7,10 +7,6 @@ lbe_status tc_apply_L(Ctx* c, DevTables*, int, const double*, const float*, floa
     c->last_error = "BF16 tensor-core operator not built";
     return LBE_UNSUPPORTED;
 }
-lbe_status refined_solve(Ctx* c, const lbe_problem*, int, lbe_result*, double*, double*) {
-    c->last_error = "BF16 refinement not built";
-    return LBE_UNSUPPORTED;
-}
 void stop_service(Ctx*) {}
 }  // namespace lbe
 

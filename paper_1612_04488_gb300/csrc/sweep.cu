@@ -27,7 +27,9 @@ namespace {
 // Source S of Sec. 2 with X_P = X_T = -1 at velocity (v1, v2, v3).
 template <typename T>
 __device__ __forceinline__ T source(int forcing, T v1, T v2, T v3, T f) {
-    return forcing == 0 ? v3 * f : v3 * (v1 * v1 + v2 * v2 + v3 * v3 - T(2.5)) * f;
+    if (forcing == 0) return v3 * f;
+    if (forcing == 1) return v3 * (v1 * v1 + v2 * v2 + v3 * v3 - T(2.5)) * f;
+    return T(0);  // homogeneous map (refinement correction solves)
 }
 
 template <typename T>
@@ -130,24 +132,52 @@ __global__ void __launch_bounds__(128) k_sweep2d(const T* __restrict__ rhs, T* _
     }
 }
 
+// Per-thread accumulator: plain double on the FP64 path; on the FP32 path a compensated
+// (Kahan) float sum, whose error does not grow with the number of terms.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // mom[cell][5] = sum_v {v3, (|v|^2-5/2) v3, (2 v1^2-1) v3, (2 v2^2-1) v3, 2 v1 v2 v3} h dv^3
+// One block of 8 nv threads per cell: thread t owns i3 = t % nv and the rows i2 = t/nv + 8k.
 template <typename T>
-__global__ void __launch_bounds__(256) k_moments(const T* __restrict__ h, const double* __restrict__ vel,
+__global__ void __launch_bounds__(256) k_moments(const T* __restrict__ h, const T* __restrict__ vel,
                                                  int nv, double dv3, long cell0, double* __restrict__ mom) {
     __shared__ double red[32 * 5];
     const long cell = cell0 + blockIdx.x;
-    const int n3 = nv * nv * nv;
-    double s[5] = {0, 0, 0, 0, 0};
-    for (int i = threadIdx.x; i < n3; i += blockDim.x) {
-        const int i1 = i / (nv * nv), i2 = (i / nv) % nv, i3 = i % nv;
-        const double v1 = vel[i1], v2 = vel[i2], v3 = vel[i3];
-        const double x = (double)h[cell * n3 + i] * v3;
-        s[0] += x;
-        s[1] += (v1 * v1 + v2 * v2 + v3 * v3 - 2.5) * x;
-        s[2] += (2.0 * v1 * v1 - 1.0) * x;
-        s[3] += (2.0 * v2 * v2 - 1.0) * x;
-        s[4] += 2.0 * v1 * v2 * x;
+    const long n3 = (long)nv * nv * nv;
+    const int i3 = threadIdx.x % nv, r0 = threadIdx.x / nv;
+    const T v3 = vel[i3];
+    const T* hc = h + cell * n3 + i3;
+    Acc<T> a[5];
+    for (int i1 = 0; i1 < nv; ++i1) {
+        const T v1 = vel[i1];
+        for (int i2 = r0; i2 < nv; i2 += 8) {
+            const T v2 = vel[i2];
+            const T x = hc[((long)i1 * nv + i2) * nv] * v3;
+            a[0].add(x);
+            a[1].add((v1 * v1 + v2 * v2 + v3 * v3 - T(2.5)) * x);
+            a[2].add((T(2) * v1 * v1 - T(1)) * x);
+            a[3].add((T(2) * v2 * v2 - T(1)) * x);
+            a[4].add(T(2) * v1 * v2 * x);
+        }
     }
+    double s[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) s[k] = a[k].value();
     block_reduce<5>(s, red);
     if (threadIdx.x == 0)
         for (int k = 0; k < 5; ++k) mom[cell * 5 + k] = s[k] * dv3;
@@ -292,7 +322,8 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
 // h = hh + 2 dU v3 f_eq for the cells of the active jobs (Eq. guided).
 template <typename T>
 __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __restrict__ h,
-                                                 const double* __restrict__ dU, const T* __restrict__ feq,
+                                                 const double* __restrict__ dU, const T* __restrict__ extra,
+                                                 const T* __restrict__ feq,
                                                  const T* __restrict__ vel, const SweepJobDev* __restrict__ jobs,
                                                  const int* __restrict__ active, int nv) {
     const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
@@ -303,7 +334,8 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
         const int v = (int)(k % n3);
         const long g = jb.cell_off * n3 + k;
         const T d = (T)(2.0 * dU[jb.cell_off + c]);
-        h[g] = hh[g] + d * vel[v % nv] * feq[v];
+        const T x = hh[g] + d * vel[v % nv] * feq[v];
+        h[g] = extra ? x + extra[g] : x;
     }
 }
 
@@ -334,7 +366,8 @@ template <typename T>
 void launch_moments(const DevTables& t, long cell0, int cells, const T* h, double* mom, cudaStream_t s) {
     if (cells <= 0) return;
     g_launches += 1;
-    k_moments<T><<<cells, 256, 0, s>>>(h, t.vel_d, t.nv, t.dv * t.dv * t.dv, cell0, mom);
+    const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
+    k_moments<T><<<cells, 8 * t.nv, 0, s>>>(h, vel, t.nv, t.dv * t.dv * t.dv, cell0, mom);
 }
 
 void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, const int* active,
@@ -346,14 +379,14 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
 }
 
 template <typename T>
-void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU,
+void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
                     const SweepJobDev* jobs, const int* active, cudaStream_t s) {
     if (njobs <= 0) return;
     g_launches += 1;
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
     dim3 g(152, njobs);
-    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, feq, vel, jobs, active, t.nv);
+    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv);
 }
 
 template void launch_sweep<double>(const DevTables&, int, int, int, const double*, double*,
@@ -363,8 +396,8 @@ template void launch_sweep<float>(const DevTables&, int, int, int, const float*,
 template void launch_moments<double>(const DevTables&, long, int, const double*, double*, cudaStream_t);
 template void launch_moments<float>(const DevTables&, long, int, const float*, double*, cudaStream_t);
 template void launch_correct<double>(const DevTables&, int, const double*, double*, const double*,
-                                     const SweepJobDev*, const int*, cudaStream_t);
-template void launch_correct<float>(const DevTables&, int, const float*, float*, const double*,
+                                     const double*, const SweepJobDev*, const int*, cudaStream_t);
+template void launch_correct<float>(const DevTables&, int, const float*, float*, const double*, const float*,
                                     const SweepJobDev*, const int*, cudaStream_t);
 
 }  // namespace lbe

@@ -57,7 +57,7 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
                        const double* mom, const double* G, const double* coef, double* work, double* dU,
                        double* U3, JobState* state, cudaStream_t s);
 template <typename T>
-void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU,
+void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
                     const SweepJobDev* jobs, const int* active, cudaStream_t s);
 
 // fsm_cc.cu
