@@ -155,6 +155,8 @@ DevTables* get_tables(Ctx* c, int nv, double vmax, int M, double R, lbe_status* 
     t->dv = h.dv;
     t->cU = h.cU;
     t->cq = h.cq;
+    t->sym_reps1 = h.sym_reps1;
+    t->sym_reps2 = h.sym_reps2;
     size_t b = 0;
     lbe_status s = LBE_OK;
     if (s == LBE_OK) s = upload(c, &t->feq_d, h.feq, &b);
@@ -377,18 +379,34 @@ void batch_iterate(Batch& B) {
     T* hh = B.hh.as<T>();
     T* lp = B.lp.as<T>();
     T* lh = B.lh.as<T>();
+    // contiguous cell spans of the active jobs (by memory position)
+    std::vector<std::pair<long, long>> spans;
+    {
+        std::vector<std::pair<long, long>> r;
+        for (int j : B.active) r.push_back({B.cell_off[j], (long)B.sj[j].ncell});
+        std::sort(r.begin(), r.end());
+        for (auto& q : r) {
+            if (!spans.empty() && spans.back().first + spans.back().second == q.first)
+                spans.back().second += q.second;
+            else
+                spans.push_back(q);
+        }
+    }
     bool any_sis = false;
-    for (int a = 0; a < na;) {
-        int b = a;
-        while (b + 1 < na && B.active[b + 1] == B.active[b] + 1) ++b;
-        const long c0 = B.cell_off[B.active[a]];
-        const long c1 = B.cell_off[B.active[b]] + B.sj[B.active[b]].ncell;
-        const int nc = (int)(c1 - c0);
+    for (int j : B.active) any_sis |= B.pbs[j].scheme == LBE_SIS;
+    // parity of every solution: odd in v3; plates (1D) also even in v2
+    std::vector<std::pair<long, int>> dim_at;
+    for (int j : B.active) dim_at.push_back({B.cell_off[j], B.geo[j].dim});
+    std::sort(dim_at.begin(), dim_at.end());
+    for (auto& sp : spans) {
+        const long c0 = sp.first;
+        const int nc = (int)sp.second;
+        int mode = 2;
+        for (auto& q : dim_at)
+            if (q.first >= c0 && q.first < c0 + nc && q.second == 2) mode = 1;
         fsm_cc_apply<T>(t, nc, B.delta.as<double>() + c0, h + c0 * n3, lp + c0 * n3, lh + c0 * n3, B.scratch.p,
-                        B.chunk, s);
-        for (int k = a; k <= b; ++k) any_sis |= B.pbs[B.active[k]].scheme == LBE_SIS;
+                        B.chunk, s, mode);
         if (any_sis) lmoments<T>(t, nc, lh + c0 * n3, h + c0 * n3, B.nd.as<double>() + c0, B.G.as<double>() + c0 * 2, s);
-        a = b + 1;
     }
     // sweeps grouped by dimension
     std::vector<int> act1, act2;
@@ -402,14 +420,7 @@ void batch_iterate(Batch& B) {
     launch_sweep<T>(t, 1, (int)act1.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact, B.coef.as<double>(), s);
     launch_sweep<T>(t, 2, (int)act2.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact + act1.size(),
                     B.coef.as<double>(), s);
-    for (int a = 0; a < na;) {  // moments over contiguous runs of active jobs
-        int b = a;
-        while (b + 1 < na && B.active[b + 1] == B.active[b] + 1) ++b;
-        const long c0 = B.cell_off[B.active[a]];
-        const long c1 = B.cell_off[B.active[b]] + B.sj[B.active[b]].ncell;
-        launch_moments<T>(t, c0, (int)(c1 - c0), hh, B.mom.as<double>(), s);
-        a = b + 1;
-    }
+    for (auto& sp : spans) launch_moments<T>(t, sp.first, (int)sp.second, hh, B.mom.as<double>(), s);
     launch_sis_update(t, na, B.ijobs.as<SisJobDev>(), dact, B.mom.as<double>(), B.G.as<double>(),
                       B.coef.as<double>(), B.work.as<double>(), B.dU.as<double>(), B.U3.as<double>(),
                       B.states.as<JobState>(), s);
@@ -419,8 +430,14 @@ void batch_iterate(Batch& B) {
     g_d2h += B.njobs * sizeof(JobState);
 }
 
+static double host_now() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 lbe_status batch_run(Batch& B, int max_steps) {
     int steps = 0;
+    B.t_start = host_now();
+    B.t_done.assign(B.njobs, 0.0);
     while (!B.active.empty() && steps < max_steps) {
         if (B.prec == LBE_FP64)
             batch_iterate<double>(B);
@@ -429,11 +446,18 @@ lbe_status batch_run(Batch& B, int max_steps) {
         lbe_status st = cuda_status(B.c, cudaStreamSynchronize(B.s), "iterate");
         if (st != LBE_OK) return st;
         std::vector<int> keep;
-        for (int j : B.active)
-            if (!B.hstate[j].done) keep.push_back(j);
+        const double t = host_now();
+        for (int j : B.active) {
+            if (!B.hstate[j].done)
+                keep.push_back(j);
+            else
+                B.t_done[j] = t;
+        }
         B.active.swap(keep);
         ++steps;
     }
+    const double t = host_now();
+    for (int j : B.active) B.t_done[j] = t;
     return LBE_OK;
 }
 
@@ -446,7 +470,7 @@ void fill_result(const Batch& B, int j, lbe_result* r, double secs) {
     r->heat_flow = s.Q;
     r->iters = s.iters;
     r->last_rel_change = s.rel;
-    r->seconds = secs;
+    r->seconds = (j < (int)B.t_done.size() && B.t_done[j] > 0) ? B.t_done[j] - B.t_start : secs;
     r->refinements = 0;
     const lbe_problem& pb = B.pbs[j];
     if (s.nan)

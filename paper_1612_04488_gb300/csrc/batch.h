@@ -34,6 +34,8 @@ struct Batch {
     int chunk = 1;
     std::vector<JobState> hstate;
     std::vector<int> active;
+    double t_start = 0;            // host clock (s) when batch_run began
+    std::vector<double> t_done;    // host clock (s) when each job's flag was seen
 };
 
 // Internal forcing value: no source term and no momentum-balance term (the homogeneous
@@ -44,5 +46,13 @@ lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Arena* ar
 template <typename T> void batch_iterate(Batch& B);
 lbe_status batch_run(Batch& B, int max_steps);
 void fill_result(const Batch& B, int j, lbe_result* r, double secs);
+
+// refine.cu helpers shared with the service
+void launch_set_rates(int njobs, const SisJobDev* jobs, const int* active, const double* mom, const double* coef,
+                      JobState* state, cudaStream_t s);
+void range_widen(const float* e, double* h, long n, cudaStream_t s);
+void range_copy(const double* a, double* b, long n, cudaStream_t s);
+void range_residual(const double* h, const double* h_old, float* r, long n, cudaStream_t s);
+void range_correct(const double* h_old, const float* e, double* h, long n, cudaStream_t s);
 
 }  // namespace lbe

@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(128) k_fwd(const T* __restrict__ hin, cplx_t<T
 template <typename T, int N, bool INV, bool REAL_IN, bool MULT, int WPB>
 __global__ void __launch_bounds__(32 * WPB) k_slab2d(const T* __restrict__ hin, const cplx_t<T>* __restrict__ Hin,
                                                      const cplx_t<T>* __restrict__ mult,
-                                                     cplx_t<T>* __restrict__ out, long nslabs, int P) {
+                                                     cplx_t<T>* __restrict__ out, long nslabs, int P,
+                                                     int loss_slot) {
     constexpr int LD = N + 1, N2 = N * N;
     __shared__ cplx_t<T> sm[WPB][N][LD];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -103,8 +104,9 @@ __global__ void __launch_bounds__(32 * WPB) k_slab2d(const T* __restrict__ hin, 
     if (MULT) {
         const long cell = vol / P;
         const int p = (int)(vol % P);
+        const int pm = (p == P - 1) ? loss_slot : p;  // last slot: the loss multiplier
         ibase = cell * N * N2 + (long)k1 * N2;
-        mbase = (long)p * N * N2 + (long)k1 * N2;
+        mbase = (long)pm * N * N2 + (long)k1 * N2;
     } else {
         ibase = vol * N * N2 + (long)k1 * N2;
     }
@@ -156,7 +158,9 @@ __global__ void __launch_bounds__(32 * WPB) k_slab2d(const T* __restrict__ hin, 
 // Last inverse pass (along i1) with the angular sum split over the four warps of a block:
 // the 32 lanes hold 32 consecutive (i2, i3) lines of one cell, warp w sums directions
 // p = w, w+4, ...; the partial sums meet in shared memory in a fixed order (A2-A3).
-template <typename T, int N>
+// With RAW, the representatives' gain goes to Lplus and the loss convolution to Lout
+// unassembled, for k_sym to complete.  Y holds M directions and the loss in slot M.
+template <typename T, int N, bool RAW>
 __global__ void __launch_bounds__(128) k_inv_last4(const cplx_t<T>* __restrict__ Y,
                                                    const cplx_t<T>* __restrict__ ab,
                                                    const T* __restrict__ feq, const T* __restrict__ nu1,
@@ -182,8 +186,13 @@ __global__ void __launch_bounds__(128) k_inv_last4(const cplx_t<T>* __restrict__
             im[j] = z.y;
         }
         dft_line<T, N, true>(re, im);
+        if (RAW) {
 #pragma unroll
-        for (int j = 0; j < N; ++j) acc[j] = -feq[j * N2 + r] * re[j];
+            for (int j = 0; j < N; ++j) Lout[cell * N3 + (long)j * N2 + r] = re[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] = -feq[j * N2 + r] * re[j];
+        }
     }
     for (int p = w; p < M; p += 4) {
         const cplx_t<T>* yl = Y + (cell * (M + 1) + p) * N3 + r;
@@ -209,9 +218,71 @@ __global__ void __launch_bounds__(128) k_inv_last4(const cplx_t<T>* __restrict__
     for (int j = w; j < N; j += 4) {
         const T sum = ((red[0][j][lane] + red[1][j][lane]) + red[2][j][lane]) + red[3][j][lane];
         const long idx = cell * N3 + (long)j * N2 + r;
+        if (RAW) {
+            Lplus[idx] = sum;
+            continue;
+        }
         const T lp = d * sum;
         if (Lplus) Lplus[idx] = lp;
         if (Lout) Lout[idx] = lp - d * nu1[j * N2 + r] * h[idx];
+    }
+}
+
+// Completes the symmetry-reduced operator.  For h with parities s2 (v2 -> -v2) and
+// s3 = -1 (v3 -> -v3), the operator commutes with the reflections and the direction set is
+// closed under them, so the sum over all directions equals the sum over one representative
+// per orbit, G, symmetrised: gain(v) = sum_g s_g G(g v) over g in {1, R3} (MODE 1) or
+// {1, R2, R3, R2R3} (MODE 2, s2 = +1).  One thread per orbit of velocity points.
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(128) k_sym(T* __restrict__ Lplus, T* __restrict__ Lout,
+                                             const T* __restrict__ feq, const T* __restrict__ nu1,
+                                             const T* __restrict__ h, const double* __restrict__ delta,
+                                             int ncell, bool want_lplus, bool want_l) {
+    constexpr int N2 = N * N, N3 = N2 * N, H = N / 2;
+    constexpr int per_cell = MODE == 2 ? N * H * H : N * N * H;
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)ncell * per_cell) return;
+    const long cell = t / per_cell;
+    const int q = (int)(t % per_cell);
+    int i1, i2, i3;
+    if (MODE == 2) {
+        i1 = q / (H * H);
+        i2 = (q / H) % H;
+        i3 = q % H;
+    } else {
+        i1 = q / (N * H);
+        i2 = (q / H) % N;
+        i3 = q % H;
+    }
+    const int j2 = N - 1 - i2, j3 = N - 1 - i3;
+    const long base = cell * N3 + (long)i1 * N2;
+    const T d = (T)delta[cell];
+    long idx[4];
+    T sgn[4];
+    int nptr;
+    T gs;
+    if (MODE == 2) {
+        idx[0] = base + i2 * N + i3;   // v
+        idx[1] = base + j2 * N + i3;   // R2 v   (s2 = +1)
+        idx[2] = base + i2 * N + j3;   // R3 v   (s3 = -1)
+        idx[3] = base + j2 * N + j3;   // R2R3 v (s2 s3 = -1)
+        sgn[0] = T(1); sgn[1] = T(1); sgn[2] = T(-1); sgn[3] = T(-1);
+        nptr = 4;
+        gs = (Lplus[idx[0]] + Lplus[idx[1]]) - (Lplus[idx[2]] + Lplus[idx[3]]);
+    } else {
+        idx[0] = base + i2 * N + i3;
+        idx[1] = base + i2 * N + j3;   // R3 v
+        sgn[0] = T(1); sgn[1] = T(-1);
+        nptr = 2;
+        gs = Lplus[idx[0]] - Lplus[idx[1]];
+    }
+    for (int k = 0; k < nptr; ++k) {
+        const long g = idx[k];
+        const int v = (int)(g - cell * N3);
+        const T lp = d * (sgn[k] * gs - feq[v] * Lout[g]);
+        const T hv = h[g];
+        if (want_lplus) Lplus[g] = lp;
+        if (want_l) Lout[g] = lp - d * nu1[v] * hv;
     }
 }
 
@@ -267,12 +338,12 @@ inline unsigned nblk(long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 template <typename T, int N>
 void run_fsm(const DevTables& t, int cells, const double* delta, const T* h, T* Lplus, T* Lout,
-             cplx_t<T>* Hbuf, cplx_t<T>* Ybuf, int chunk, cudaStream_t s) {
+             cplx_t<T>* Hbuf, cplx_t<T>* Ybuf, int chunk, int mode, cudaStream_t s) {
     constexpr int B = 128;
     constexpr int WPB = (sizeof(T) == 8 && N == 32) ? 2 : 4;
     const long nl = (long)cells * N * N;
     const long ns = (long)cells * N;
-    k_slab2d<T, N, false, true, false, WPB><<<nblk(ns, WPB), 32 * WPB, 0, s>>>(h, nullptr, nullptr, Hbuf, ns, 1);
+    k_slab2d<T, N, false, true, false, WPB><<<nblk(ns, WPB), 32 * WPB, 0, s>>>(h, nullptr, nullptr, Hbuf, ns, 1, 0);
     k_fwd<T, N, 0, false><<<nblk(nl, B), B, 0, s>>>(nullptr, Hbuf, nl);
     const cplx_t<T>* mult;
     const cplx_t<T>* ab;
@@ -289,7 +360,8 @@ void run_fsm(const DevTables& t, int cells, const double* delta, const T* h, T* 
         feq = (const T*)t.feq_f;
         nu1 = (const T*)t.nu1_f;
     }
-    const int P = t.M + 1;
+    const int Muse = mode == 2 ? t.sym_reps2 : (mode == 1 ? t.sym_reps1 : t.M);
+    const int P = Muse + 1;
     const long N3 = (long)N * N * N;
     g_launches += 2;
     g_levals += cells;
@@ -298,11 +370,25 @@ void run_fsm(const DevTables& t, int cells, const double* delta, const T* h, T* 
         const int cc = (cells - c0 < chunk) ? cells - c0 : chunk;
         const long nsl = (long)cc * P * N;
         k_slab2d<T, N, true, false, true, WPB><<<nblk(nsl, WPB), 32 * WPB, 0, s>>>(nullptr, Hbuf + c0 * N3, mult,
-                                                                                  Ybuf, nsl, P);
+                                                                                  Ybuf, nsl, P, t.M);
         const long blocks = (long)cc * (N * N / 32);
-        k_inv_last4<T, N><<<(unsigned)blocks, 128, 0, s>>>(Ybuf, ab, feq, nu1, h + c0 * N3, delta + c0,
-                                                         Lplus ? Lplus + c0 * N3 : nullptr,
-                                                         Lout ? Lout + c0 * N3 : nullptr, cc, t.M);
+        if (mode == 0) {
+            k_inv_last4<T, N, false><<<(unsigned)blocks, 128, 0, s>>>(Ybuf, ab, feq, nu1, h + c0 * N3, delta + c0,
+                                                                    Lplus ? Lplus + c0 * N3 : nullptr,
+                                                                    Lout ? Lout + c0 * N3 : nullptr, cc, Muse);
+        } else {
+            // raw gain of the representatives and the loss convolution, then symmetrise
+            k_inv_last4<T, N, true><<<(unsigned)blocks, 128, 0, s>>>(Ybuf, ab, feq, nu1, h + c0 * N3, delta + c0,
+                                                                   Lplus + c0 * N3, Lout + c0 * N3, cc, Muse);
+            g_launches += 1;
+            const long nt = (long)cc * (mode == 2 ? N * (N / 2) * (N / 2) : N * N * (N / 2));
+            if (mode == 2)
+                k_sym<T, N, 2><<<nblk(nt, 128), 128, 0, s>>>(Lplus + c0 * N3, Lout + c0 * N3, feq, nu1, h + c0 * N3,
+                                                             delta + c0, cc, true, true);
+            else
+                k_sym<T, N, 1><<<nblk(nt, 128), 128, 0, s>>>(Lplus + c0 * N3, Lout + c0 * N3, feq, nu1, h + c0 * N3,
+                                                             delta + c0, cc, true, true);
+        }
     }
 }
 
@@ -324,15 +410,18 @@ size_t fsm_cc_scratch_bytes(const DevTables& t, int cells, int elem_bytes, int* 
 
 template <typename T>
 lbe_status fsm_cc_apply(const DevTables& t, int cells, const double* delta, const T* h, T* Lplus,
-                        T* Lout, void* scratch, int chunk, cudaStream_t s) {
+                        T* Lout, void* scratch, int chunk, cudaStream_t s, int mode) {
     const long n3 = (long)t.nv * t.nv * t.nv;
+    if (mode == 2 && t.sym_reps2 == 0) mode = t.sym_reps1 ? 1 : 0;
+    if (mode == 1 && t.sym_reps1 == 0) mode = 0;
+    if (mode != 0 && (!Lplus || !Lout)) return LBE_INTERNAL;  // the symmetrised path needs both outputs
     cplx_t<T>* Hbuf = (cplx_t<T>*)scratch;
     cplx_t<T>* Ybuf = Hbuf + n3 * cells;
     switch (t.nv) {
-        case 8: run_fsm<T, 8>(t, cells, delta, h, Lplus, Lout, Hbuf, Ybuf, chunk, s); break;
-        case 16: run_fsm<T, 16>(t, cells, delta, h, Lplus, Lout, Hbuf, Ybuf, chunk, s); break;
-        case 24: run_fsm<T, 24>(t, cells, delta, h, Lplus, Lout, Hbuf, Ybuf, chunk, s); break;
-        case 32: run_fsm<T, 32>(t, cells, delta, h, Lplus, Lout, Hbuf, Ybuf, chunk, s); break;
+        case 8: run_fsm<T, 8>(t, cells, delta, h, Lplus, Lout, Hbuf, Ybuf, chunk, mode, s); break;
+        case 16: run_fsm<T, 16>(t, cells, delta, h, Lplus, Lout, Hbuf, Ybuf, chunk, mode, s); break;
+        case 24: run_fsm<T, 24>(t, cells, delta, h, Lplus, Lout, Hbuf, Ybuf, chunk, mode, s); break;
+        case 32: run_fsm<T, 32>(t, cells, delta, h, Lplus, Lout, Hbuf, Ybuf, chunk, mode, s); break;
         default: return LBE_UNSUPPORTED;
     }
     return LBE_OK;
@@ -348,9 +437,9 @@ void lmoments(const DevTables& t, int cells, const T* Lh, const T* h, const doub
 }
 
 template lbe_status fsm_cc_apply<double>(const DevTables&, int, const double*, const double*,
-                                         double*, double*, void*, int, cudaStream_t);
+                                         double*, double*, void*, int, cudaStream_t, int);
 template lbe_status fsm_cc_apply<float>(const DevTables&, int, const double*, const float*, float*,
-                                        float*, void*, int, cudaStream_t);
+                                        float*, void*, int, cudaStream_t, int);
 template void lmoments<double>(const DevTables&, int, const double*, const double*, const double*,
                                double*, cudaStream_t);
 template void lmoments<float>(const DevTables&, int, const float*, const float*, const double*,

@@ -34,6 +34,7 @@ struct HostTables {
     std::vector<double> mult;               // [(M+1)][nv^3][2]
     std::vector<double> ab;                 // [M][nv^3][2]
     double cU = 0, cq = 0;                  // sum v3^2 f_eq dv^3, sum (|v|^2-5/2) v3^2 f_eq dv^3
+    int sym_reps1 = 0, sym_reps2 = 0;       // representatives per reflection group (0: unavailable)
 };
 
 void build_host_tables(HostTables& t, int nv, double vmax, int M, double R);
@@ -44,6 +45,7 @@ struct DevTables {
     int nv = 0, M = 0;
     double vmax = 0, R = 0, dv = 0;
     double cU = 0, cq = 0;
+    int sym_reps1 = 0, sym_reps2 = 0;
     // double
     double* feq_d = nullptr; double* nu1_d = nullptr; double* mult_d = nullptr; double* ab_d = nullptr;
     double* vel_d = nullptr;  // [nv] nodes

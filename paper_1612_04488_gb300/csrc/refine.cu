@@ -10,8 +10,10 @@
 //                                                 of the homogeneous map: no source S and no
 //                                                 momentum-balance term)
 //     h <- h + e
-// so the answer is the FP64 SIS fixed point, while almost all collision-operator
-// evaluations run in low precision.  h lives in FP64; e and r in FP32.
+// starting from h = the low-precision SIS solution of the full problem, so that a solve
+// usually needs two FP64 iterations: one residual and one that certifies convergence.
+// The answer is the FP64 SIS fixed point, while almost all collision-operator evaluations
+// run in low precision.  h lives in FP64; e and r in FP32.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -53,6 +55,15 @@ __global__ void k_apply_correction(const double* __restrict__ h_old, const float
         h[base + k] = h_old[base + k] + (double)e[base + k];
 }
 
+// h = (double)e
+__global__ void k_widen(const float* __restrict__ e, double* __restrict__ h, const SweepJobDev* __restrict__ jobs,
+                        const int* __restrict__ active, long n3) {
+    const SweepJobDev jb = jobs[active[blockIdx.y]];
+    const long total = (long)jb.ncell * n3, base = jb.cell_off * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x)
+        h[base + k] = (double)e[base + k];
+}
+
 // state M, Q := flow rates of the moments in mom (so the next iteration measures its change
 // against the current iterate)
 __global__ void k_set_rates(const SisJobDev* __restrict__ jobs, const int* __restrict__ active,
@@ -74,6 +85,48 @@ __global__ void k_set_rates(const SisJobDev* __restrict__ jobs, const int* __res
 
 }  // namespace
 
+void launch_set_rates(int njobs, const SisJobDev* jobs, const int* active, const double* mom, const double* coef,
+                      JobState* state, cudaStream_t s) {
+    g_launches += 1;
+    k_set_rates<<<njobs, 32, 0, s>>>(jobs, active, mom, coef, state);
+}
+
+// Element-wise range kernels of the defect-correction steps (one range of cells).
+__global__ void k_range_widen(const float* __restrict__ e, double* __restrict__ h, long n) {
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+        h[k] = (double)e[k];
+}
+__global__ void k_range_copy(const double* __restrict__ a, double* __restrict__ b, long n) {
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) b[k] = a[k];
+}
+__global__ void k_range_residual(const double* __restrict__ h, const double* __restrict__ h_old, float* __restrict__ r,
+                                 long n) {
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+        r[k] = (float)(h[k] - h_old[k]);
+}
+__global__ void k_range_correct(const double* __restrict__ h_old, const float* __restrict__ e, double* __restrict__ h,
+                                long n) {
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+        h[k] = h_old[k] + (double)e[k];
+}
+
+void range_widen(const float* e, double* h, long n, cudaStream_t s) {
+    g_launches += 1;
+    k_range_widen<<<152, 256, 0, s>>>(e, h, n);
+}
+void range_copy(const double* a, double* b, long n, cudaStream_t s) {
+    g_launches += 1;
+    k_range_copy<<<152, 256, 0, s>>>(a, b, n);
+}
+void range_residual(const double* h, const double* h_old, float* r, long n, cudaStream_t s) {
+    g_launches += 1;
+    k_range_residual<<<152, 256, 0, s>>>(h, h_old, r, n);
+}
+void range_correct(const double* h_old, const float* e, double* h, long n, cudaStream_t s) {
+    g_launches += 1;
+    k_range_correct<<<152, 256, 0, s>>>(h_old, e, h, n);
+}
+
 lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs, double* U3_out,
                          double* h_out) {
     auto t0 = std::chrono::steady_clock::now();
@@ -82,16 +135,19 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
     int max_outer = 1;
     for (int j = 0; j < n; ++j) {
         po[j].precision = LBE_FP64;
-        pi[j].precision = LBE_FP32;
-        pi[j].forcing = (lbe_forcing)kForcingNone;
-        pi[j].eps = 1e-4;       // inner solves reduce the correction's change to 1e-4
-        pi[j].max_iter = 60;
+        pi[j].precision = LBE_FP32;  // phase 0: the full problem in low precision
+        pi[j].eps = std::max(pbs[j].eps, 1e-5);
+        pi[j].max_iter = 150;
         max_outer = std::max(max_outer, pbs[j].max_iter);
     }
     Arena ao, ai;
     Batch O, I;
     lbe_status st = batch_init(O, c, po.data(), n, &ao, s);
     if (st == LBE_OK) st = batch_init(I, c, pi.data(), n, &ai, s);
+    if (st == LBE_OK) {  // low-precision phases test changes against the flow-rate scale
+        for (int j = 0; j < n; ++j) I.ij[j].crit = 1;
+        cudaMemcpyAsync(I.ijobs.p, I.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, s);
+    }
     const long n3 = (long)pbs[0].nv * pbs[0].nv * pbs[0].nv;
     double* h_old = nullptr;
     float* r = nullptr;
@@ -105,12 +161,34 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         arena_release(c, ai);
         return st;
     }
-    I.extra.p = r;
-    I.extra.n = vol32;
     std::vector<int> outer_it(n, 0), inner_it(n, 0), refs(n, 0);
+    std::vector<double> t_done(n, 0.0);
     std::vector<int> active(n);
     for (int j = 0; j < n; ++j) active[j] = j;
     const dim3 blk(256);
+    // phase 0: low-precision SIS of the full problem from h = 0, widened to FP64
+    if (st == LBE_OK) st = batch_run(I, 150);
+    if (st == LBE_OK) {
+        for (int j = 0; j < n; ++j) inner_it[j] += I.hstate[j].iters;
+        cudaMemcpyAsync(O.act.p, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, s);
+        k_widen<<<dim3(152, n), blk, 0, s>>>(I.h.as<float>(), O.h.as<double>(), O.sjobs.as<SweepJobDev>(),
+                                             O.act.as<int>(), n3);
+        g_launches += 1;
+        // from now on the inner batch solves the homogeneous correction equation
+        for (int j = 0; j < n; ++j) {
+            I.sj[j].forcing = kForcingNone;
+            I.ij[j].ndsig = 0.0;
+            I.ij[j].eps = 1e-4;  // each correction solve reduces its flow-rate change to 1e-4
+            I.ij[j].max_iter = 60;
+        }
+        cudaMemcpyAsync(I.sjobs.p, I.sj.data(), n * sizeof(SweepJobDev), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(I.ijobs.p, I.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, s);
+        g_h2d += n * (sizeof(SweepJobDev) + sizeof(SisJobDev));
+        st = cuda_status(c, cudaStreamSynchronize(s), "refine phase 0");
+    }
+    I.extra.p = r;
+    I.extra.n = vol32;
+    if (st != LBE_OK) active.clear();
     while (!active.empty()) {
         const int na = (int)active.size();
         cudaMemcpyAsync(O.act.p, active.data(), na * sizeof(int), cudaMemcpyHostToDevice, s);
@@ -128,9 +206,13 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         batch_iterate<double>(O);
         if ((st = cuda_status(c, cudaStreamSynchronize(s), "refine outer")) != LBE_OK) break;
         std::vector<int> keep;
+        const double tnow = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int j : active) {
             ++outer_it[j];
-            if (!O.hstate[j].done) keep.push_back(j);
+            if (!O.hstate[j].done)
+                keep.push_back(j);
+            else
+                t_done[j] = tnow;
         }
         active.swap(keep);
         if (active.empty()) break;
@@ -169,6 +251,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             fill_result(O, j, &outs[j], secs);
             outs[j].iters = outer_it[j] + inner_it[j];
             outs[j].refinements = refs[j];
+            outs[j].seconds = t_done[j] > 0 ? t_done[j] : secs;
             if (outs[j].status != LBE_OK && worst == LBE_OK) worst = (lbe_status)outs[j].status;
         }
         if (U3_out) {

@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
         if (!isfinite(Mn) || !isfinite(Qn)) {
             st->nan = 1;
             st->done = 1;
-        } else if (fabs(Mn - st->Mprev) < jb.eps * fabs(Mn) && fabs(Qn - st->Qprev) < jb.eps * fabs(Qn)) {
+        } else if (jb.crit == 0 ? (fabs(Mn - st->Mprev) < jb.eps * fabs(Mn) && fabs(Qn - st->Qprev) < jb.eps * fabs(Qn))
+                                : (fmax(fabs(Mn - st->Mprev), fabs(Qn - st->Qprev)) < jb.eps * fmax(fabs(Mn), fabs(Qn)))) {
             st->done = 1;
         } else if (st->iters >= jb.max_iter) {
             st->done = 1;

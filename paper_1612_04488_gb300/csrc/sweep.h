@@ -41,6 +41,7 @@ struct SisJobDev {
     double ndsig;    // N delta sigma (sigma = 1 Poiseuille, 0 thermal transpiration)
     double eps;
     int max_iter;
+    int crit;        // 0: |dM| < eps |M| and |dQ| < eps |Q| (Sec. 2.4); 1: both changes < eps max(|M|, |Q|)
 };
 
 struct JobState {
@@ -65,7 +66,7 @@ void init_twiddles_cc();
 size_t fsm_cc_scratch_bytes(const DevTables& t, int cells, int elem_bytes, int* chunk_out);
 template <typename T>
 lbe_status fsm_cc_apply(const DevTables& t, int cells, const double* delta, const T* h, T* Lplus, T* Lout,
-                 void* scratch, int chunk, cudaStream_t s);
+                        void* scratch, int chunk, cudaStream_t s, int mode = 0);
 template <typename T>
 void lmoments(const DevTables& t, int cells, const T* Lh, const T* h, const double* nd, double* G,
               cudaStream_t s);

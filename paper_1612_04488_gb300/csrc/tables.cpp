@@ -11,6 +11,7 @@
 // n_t = 2^floor(log2(M)/2); the sphere integral is even in e, hence the hemisphere x 2.
 // F is the plain DFT on the midpoint grid (the multipliers act as cyclic convolutions, so
 // the grid offset cancels); Nyquist planes are zeroed in every multiplier.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <stdexcept>
@@ -121,12 +122,26 @@ void build_host_tables(HostTables& t, int nv, double vmax, int M, double R) {
     std::vector<double> e(3 * M), wp(M);
     const double K = 5.0 * std::sqrt(2.0 * M_PI) / 16.0;
     const double b = K / (4.0 * M_PI);
+    // Storage order: directions grouped by their orbit under the reflections v2 -> -v2,
+    // v3 -> -v3 (azimuth k -> n_a-1-k, k -> k+n_a/2): first every ring's k < n_a/4, then
+    // n_a/4 <= k < n_a/2, then the rest.  The first M/4 (M/2) directions are one
+    // representative per orbit of the group {1, R2, R3, R2R3} ({1, R3}).
+    auto klass = [&](int k) { return (na % 4 == 0 && k < na / 4) ? 0 : (k < na / 2 ? 1 : 2); };
+    std::vector<std::pair<int, int>> order;  // (class, i*na+k) sorted
+    for (int i = 0; i < nt; ++i)
+        for (int k = 0; k < na; ++k) order.push_back({klass(k), i * na + k});
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<int, int>& a, const std::pair<int, int>& b) { return a.first < b.first; });
+    std::vector<int> slot_of(M);
+    for (int q = 0; q < M; ++q) slot_of[order[q].second] = q;
+    t.sym_reps1 = (na % 2 == 0) ? M / 2 : 0;
+    t.sym_reps2 = (na % 4 == 0) ? M / 4 : 0;
     for (int i = 0; i < nt; ++i) {
         double mu = 0.5 * (gx[i] + 1.0), wmu = 0.5 * gw[i];
         double st = std::sqrt(1.0 - mu * mu);
         for (int k = 0; k < na; ++k) {
             double az = (k + 0.5) * 2.0 * M_PI / na;
-            int p = i * na + k;
+            int p = slot_of[i * na + k];
             e[3 * p + 0] = st * std::cos(az);
             e[3 * p + 1] = st * std::sin(az);
             e[3 * p + 2] = mu;

@@ -188,12 +188,14 @@ def test_solve_fixed_iterations_fp64_matches_oracle(ctx, scheme):
 def test_solve_converged_fp64_and_fp32_match_oracle(ctx):
     kw = dict(workloads.PLATES_16, R=R45, forcing=0)
     r = _oracle_run(kw, "sis", eps=1e-8)
-    for prec, tol in ((lbe.FP64, 1e-10), (lbe.FP32, 1e-6)):
-        pb = lbe.problem(**kw, scheme=lbe.SIS, precision=prec, eps=1e-8, max_iter=200)
+    # FP32 cannot resolve a 1e-8 relative change; it stops at 1e-6 and carries the FP32
+    # fixed-point error plus the stopping error eps * omega / (1 - omega)
+    for prec, eps, tol in ((lbe.FP64, 1e-8, 1e-10), (lbe.FP32, 1e-6, 2e-5)):
+        pb = lbe.problem(**kw, scheme=lbe.SIS, precision=prec, eps=eps, max_iter=200)
         res, U, _ = ctx.solve(pb)
         assert res.status == lbe.OK
         assert abs(res.mass_flow - r.M) <= tol * abs(r.M), (prec, res.mass_flow, r.M)
-        assert abs(res.heat_flow - r.Q) <= tol * abs(r.Q) * 10
+        assert abs(res.heat_flow - r.Q) <= tol * abs(r.Q), (prec, res.heat_flow, r.Q)
 
 
 def test_solve_2d_fixed_iterations_matches_oracle(ctx):

@@ -1,0 +1,83 @@
+"""Continuous-batching service (lbe_submit / lbe_poll): results equal lbe_solve, bitwise the
+same alone and in a mix, admission under a slot limit, refined requests reach the FP64
+solution."""
+import time
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1612_04488_gb300 import lbe  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = lbe.Context(0)
+    yield c
+    c.close()
+
+
+def wait_all(ctx, tickets, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        assert time.time() - t0 < timeout, "service timed out"
+        for t in tickets:
+            if t not in out:
+                done, r = ctx.poll(t)
+                if done:
+                    out[t] = r
+        time.sleep(0.002)
+    return [out[t] for t in tickets]
+
+
+def mix(prec):
+    base = dict(nv=8, vmax=4.0, M=8, R=3.0, scheme=lbe.SIS, precision=prec, eps=1e-9, max_iter=300)
+    pbs = [lbe.problem(dim=1, ns=ns, grid_kind=1, delta=d, forcing=f, **base)
+           for ns, d, f in ((12, 0.1, 0), (30, 1.0, 1), (20, 10.0, 0), (50, 3.0, 1))]
+    pbs += [lbe.problem(dim=2, nx=nx, ny=ny, width=nx / ny, delta=d, forcing=f, **base)
+            for nx, ny, d, f in ((6, 5, 2.0, 0), (10, 5, 0.5, 1))]
+    return pbs
+
+
+def test_served_equals_solve_and_mix_equals_alone(ctx):
+    pbs = mix(lbe.FP64)
+    alone = wait_all(ctx, [ctx.submit(pbs[2])])[0]
+    mixed = wait_all(ctx, [ctx.submit(p) for p in pbs])
+    assert all(r.status == lbe.OK for r in mixed)
+    assert mixed[2].mass_flow == alone.mass_flow and mixed[2].heat_flow == alone.heat_flow
+    assert mixed[2].iters == alone.iters
+    for p, r in zip(pbs, mixed):
+        s, _, _ = ctx.solve(p)
+        assert r.mass_flow == s.mass_flow and r.heat_flow == s.heat_flow and r.iters == s.iters
+
+
+def test_admission_with_few_slots_and_arrivals_in_flight(ctx):
+    ctx.set_max_active(2)
+    pbs = mix(lbe.FP32)
+    tickets = [ctx.submit(p) for p in pbs[:3]]
+    time.sleep(0.01)
+    tickets += [ctx.submit(p) for p in pbs[3:]]
+    res = wait_all(ctx, tickets)
+    assert all(r.status == lbe.OK for r in res)
+    ctx.set_max_active(64)
+
+
+def test_refined_requests_reach_fp64(ctx):
+    pbs = mix(lbe.FP64)
+    ref = [ctx.solve(p)[0] for p in pbs]
+    rp = mix(lbe.FP32_REFINED)
+    got = wait_all(ctx, [ctx.submit(p) for p in rp])
+    for r, g in zip(ref, got):
+        assert g.status == lbe.OK
+        assert abs(g.mass_flow - r.mass_flow) <= 1e-7 * abs(r.mass_flow)
+        assert abs(g.heat_flow - r.heat_flow) <= 1e-7 * abs(r.heat_flow)
+
+
+def test_submit_rejects_bad_problem(ctx):
+    with pytest.raises(lbe.LbeError):
+        ctx.submit(lbe.problem(dim=1, ns=10, nv=12))
