@@ -379,33 +379,43 @@ void batch_iterate(Batch& B) {
     T* hh = B.hh.as<T>();
     T* lp = B.lp.as<T>();
     T* lh = B.lh.as<T>();
-    // contiguous cell spans of the active jobs (by memory position)
-    std::vector<std::pair<long, long>> spans;
+    // contiguous cell spans of the active jobs (by memory position), never mixing plates
+    // and ducts: each problem's operator uses its own parity group (plates: odd in v3 and
+    // even in v2; ducts: odd in v3), so its arithmetic does not depend on its neighbours
+    struct Span {
+        long c0, n;
+        int dim;
+    };
+    std::vector<Span> spans;
     {
-        std::vector<std::pair<long, long>> r;
-        for (int j : B.active) r.push_back({B.cell_off[j], (long)B.sj[j].ncell});
-        std::sort(r.begin(), r.end());
+        std::vector<Span> r;
+        for (int j : B.active) r.push_back({B.cell_off[j], (long)B.sj[j].ncell, B.geo[j].dim});
+        std::sort(r.begin(), r.end(), [](const Span& a, const Span& b) { return a.c0 < b.c0; });
         for (auto& q : r) {
-            if (!spans.empty() && spans.back().first + spans.back().second == q.first)
-                spans.back().second += q.second;
+            if (!spans.empty() && spans.back().c0 + spans.back().n == q.c0 && spans.back().dim == q.dim)
+                spans.back().n += q.n;
             else
                 spans.push_back(q);
         }
     }
     bool any_sis = false;
     for (int j : B.active) any_sis |= B.pbs[j].scheme == LBE_SIS;
-    // parity of every solution: odd in v3; plates (1D) also even in v2
-    std::vector<std::pair<long, int>> dim_at;
-    for (int j : B.active) dim_at.push_back({B.cell_off[j], B.geo[j].dim});
-    std::sort(dim_at.begin(), dim_at.end());
     for (auto& sp : spans) {
-        const long c0 = sp.first;
-        const int nc = (int)sp.second;
-        int mode = 2;
-        for (auto& q : dim_at)
-            if (q.first >= c0 && q.first < c0 + nc && q.second == 2) mode = 1;
-        fsm_cc_apply<T>(t, nc, B.delta.as<double>() + c0, h + c0 * n3, lp + c0 * n3, lh + c0 * n3, B.scratch.p,
-                        B.chunk, s, mode);
+        const long c0 = sp.c0;
+        const int nc = (int)sp.n;
+        const int mode = sp.dim == 1 ? 2 : 1;
+        if (sizeof(T) == 8 && B.base_h) {
+            // L h = L_64(h_base) + L_32(h - h_base): the increment is small, so FP32 suffices
+            const long o = c0 * n3, nn = (long)nc * n3;
+            range_sub_f32((const double*)(h + o), B.base_h + o, B.inc_h + o, nn, s);
+            fsm_cc_apply<float>(t, nc, B.delta.as<double>() + c0, B.inc_h + o, B.inc_lp + o, B.inc_lh + o,
+                                B.inc_scratch, B.inc_chunk, s, mode);
+            range_add_f64(B.base_lp + o, B.inc_lp + o, (double*)(lp + o), nn, s);
+            range_add_f64(B.base_lh + o, B.inc_lh + o, (double*)(lh + o), nn, s);
+        } else {
+            fsm_cc_apply<T>(t, nc, B.delta.as<double>() + c0, h + c0 * n3, lp + c0 * n3, lh + c0 * n3,
+                            B.scratch.p, B.chunk, s, mode);
+        }
         if (any_sis) lmoments<T>(t, nc, lh + c0 * n3, h + c0 * n3, B.nd.as<double>() + c0, B.G.as<double>() + c0 * 2, s);
     }
     // sweeps grouped by dimension
@@ -420,7 +430,7 @@ void batch_iterate(Batch& B) {
     launch_sweep<T>(t, 1, (int)act1.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact, B.coef.as<double>(), s);
     launch_sweep<T>(t, 2, (int)act2.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact + act1.size(),
                     B.coef.as<double>(), s);
-    for (auto& sp : spans) launch_moments<T>(t, sp.first, (int)sp.second, hh, B.mom.as<double>(), s);
+    for (auto& sp : spans) launch_moments<T>(t, sp.c0, (int)sp.n, hh, B.mom.as<double>(), s);
     launch_sis_update(t, na, B.ijobs.as<SisJobDev>(), dact, B.mom.as<double>(), B.G.as<double>(),
                       B.coef.as<double>(), B.work.as<double>(), B.dU.as<double>(), B.U3.as<double>(),
                       B.states.as<JobState>(), s);

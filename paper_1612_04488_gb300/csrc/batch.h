@@ -31,6 +31,17 @@ struct Batch {
     std::vector<long> cell_off;
     DevBuf h, hh, lp, lh, scratch, mom, G, dU, U3, delta, nd, coef, work, sjobs, ijobs, states, act;
     DevBuf extra;  // optional additive source in the correction step (same type as h)
+    // Increment mode (FP64 batches of the refinement driver): the collision operator of h is
+    // base_lp / base_lh (FP64 operator of base_h, computed once) plus the FP32 operator of
+    // the increment h - base_h.  Unset: the operator runs in the batch's own arithmetic.
+    const double* base_h = nullptr;
+    const double* base_lp = nullptr;
+    const double* base_lh = nullptr;
+    float* inc_h = nullptr;
+    float* inc_lp = nullptr;
+    float* inc_lh = nullptr;
+    void* inc_scratch = nullptr;
+    int inc_chunk = 1;
     int chunk = 1;
     std::vector<JobState> hstate;
     std::vector<int> active;
@@ -54,5 +65,7 @@ void range_widen(const float* e, double* h, long n, cudaStream_t s);
 void range_copy(const double* a, double* b, long n, cudaStream_t s);
 void range_residual(const double* h, const double* h_old, float* r, long n, cudaStream_t s);
 void range_correct(const double* h_old, const float* e, double* h, long n, cudaStream_t s);
+void range_sub_f32(const double* h, const double* base, float* out, long n, cudaStream_t s);
+void range_add_f64(const double* base, const float* inc, double* out, long n, cudaStream_t s);
 
 }  // namespace lbe

@@ -110,6 +110,25 @@ __global__ void k_range_correct(const double* __restrict__ h_old, const float* _
         h[k] = h_old[k] + (double)e[k];
 }
 
+__global__ void k_range_sub_f32(const double* __restrict__ h, const double* __restrict__ b, float* __restrict__ o,
+                                long n) {
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+        o[k] = (float)(h[k] - b[k]);
+}
+__global__ void k_range_add_f64(const double* __restrict__ b, const float* __restrict__ inc, double* __restrict__ o,
+                                long n) {
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+        o[k] = b[k] + (double)inc[k];
+}
+void range_sub_f32(const double* h, const double* base, float* out, long n, cudaStream_t s) {
+    g_launches += 1;
+    k_range_sub_f32<<<304, 256, 0, s>>>(h, base, out, n);
+}
+void range_add_f64(const double* base, const float* inc, double* out, long n, cudaStream_t s) {
+    g_launches += 1;
+    k_range_add_f64<<<304, 256, 0, s>>>(base, inc, out, n);
+}
+
 void range_widen(const float* e, double* h, long n, cudaStream_t s) {
     g_launches += 1;
     k_range_widen<<<152, 256, 0, s>>>(e, h, n);
@@ -149,20 +168,40 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         cudaMemcpyAsync(I.ijobs.p, I.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, s);
     }
     const long n3 = (long)pbs[0].nv * pbs[0].nv * pbs[0].nv;
-    double* h_old = nullptr;
-    float* r = nullptr;
     const size_t vol64 = O.cells * n3 * 8, vol32 = O.cells * n3 * 4;
-    if (st == LBE_OK) st = dev_alloc(c, (void**)&h_old, vol64);
-    if (st == LBE_OK) st = dev_alloc(c, (void**)&r, vol32);
+    int inc_chunk = 1;
+    const size_t inc_scr = st == LBE_OK ? fsm_cc_scratch_bytes(*O.t, (int)O.cells, 4, &inc_chunk) : 0;
+    // h_old, r, base_h, base_lp, base_lh, inc_h, inc_lp, inc_lh, FP32 operator scratch
+    Arena aw;
+    double *h_old = nullptr, *base_h = nullptr, *base_lp = nullptr, *base_lh = nullptr;
+    float *r = nullptr, *inc_h = nullptr, *inc_lp = nullptr, *inc_lh = nullptr;
+    void* inc_scratch = nullptr;
+    if (st == LBE_OK) {
+        const size_t pad = 256;
+        st = arena_reserve(c, aw, 4 * (vol64 + pad) + 4 * (vol32 + pad) + inc_scr + pad);
+    }
+    if (st == LBE_OK) {
+        h_old = (double*)arena_take(aw, vol64);
+        base_h = (double*)arena_take(aw, vol64);
+        base_lp = (double*)arena_take(aw, vol64);
+        base_lh = (double*)arena_take(aw, vol64);
+        r = (float*)arena_take(aw, vol32);
+        inc_h = (float*)arena_take(aw, vol32);
+        inc_lp = (float*)arena_take(aw, vol32);
+        inc_lh = (float*)arena_take(aw, vol32);
+        inc_scratch = arena_take(aw, inc_scr);
+        if (!inc_scratch) st = LBE_INTERNAL;
+    }
     if (st != LBE_OK) {
-        dev_free(c, h_old, vol64);
-        dev_free(c, r, vol32);
+        arena_release(c, aw);
         arena_release(c, ao);
         arena_release(c, ai);
         return st;
     }
     std::vector<int> outer_it(n, 0), inner_it(n, 0), refs(n, 0);
     std::vector<double> t_done(n, 0.0);
+    std::vector<double> prev_rel(n, 1e300);
+    std::vector<char> rebase(n, 0);
     std::vector<int> active(n);
     for (int j = 0; j < n; ++j) active[j] = j;
     const dim3 blk(256);
@@ -178,12 +217,28 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         for (int j = 0; j < n; ++j) {
             I.sj[j].forcing = kForcingNone;
             I.ij[j].ndsig = 0.0;
-            I.ij[j].eps = 1e-4;  // each correction solve reduces its flow-rate change to 1e-4
-            I.ij[j].max_iter = 60;
+            I.ij[j].eps = 1e-6;  // each correction solve reduces its flow-rate change to 1e-6
+            I.ij[j].max_iter = 30;  // or runs 30 SIS iterations (omega <= 0.6: error x 2e-7)
         }
         cudaMemcpyAsync(I.sjobs.p, I.sj.data(), n * sizeof(SweepJobDev), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(I.ijobs.p, I.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, s);
         g_h2d += n * (sizeof(SweepJobDev) + sizeof(SisJobDev));
+        // the one FP64 collision-operator evaluation of the solve: at h0 = the FP32 solution;
+        // every later FP64 iteration adds the FP32 operator of the increment h - h0
+        range_copy(O.h.as<double>(), base_h, O.cells * n3, s);
+        for (int j = 0; j < n; ++j) {
+            const long o = O.cell_off[j] * n3;
+            fsm_cc_apply<double>(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o, base_lp + o,
+                                 base_lh + o, O.scratch.p, O.chunk, s, O.geo[j].dim == 1 ? 2 : 1);
+        }
+        O.base_h = base_h;
+        O.base_lp = base_lp;
+        O.base_lh = base_lh;
+        O.inc_h = inc_h;
+        O.inc_lp = inc_lp;
+        O.inc_lh = inc_lh;
+        O.inc_scratch = inc_scratch;
+        O.inc_chunk = inc_chunk;
         st = cuda_status(c, cudaStreamSynchronize(s), "refine phase 0");
     }
     I.extra.p = r;
@@ -213,6 +268,11 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
                 keep.push_back(j);
             else
                 t_done[j] = tnow;
+            // the increment's FP32 error (~1e-7 |h - h0|) is the floor of this scheme; when the
+            // change stalls near it, re-centre: evaluate the FP64 operator at the next iterate
+            const double rel = O.hstate[j].rel;
+            rebase[j] = (rel > 0.5 * prev_rel[j] && rel < 1e-7) ? 1 : 0;
+            prev_rel[j] = rel;
         }
         active.swap(keep);
         if (active.empty()) break;
@@ -229,7 +289,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         cudaMemcpyAsync(I.states.p, I.hstate.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, s);
         g_h2d += n * sizeof(JobState);
         I.active = active;
-        if ((st = batch_run(I, 60)) != LBE_OK) break;
+        if ((st = batch_run(I, 30)) != LBE_OK) break;
         for (int j : active) {
             inner_it[j] += I.hstate[j].iters;
             ++refs[j];
@@ -237,6 +297,13 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         k_apply_correction<<<dim3(152, nk), blk, 0, s>>>(h_old, I.h.as<float>(), O.h.as<double>(),
                                                          O.sjobs.as<SweepJobDev>(), O.act.as<int>(), n3);
         g_launches += 1;
+        for (int j : active) {
+            if (!rebase[j]) continue;
+            const long o = O.cell_off[j] * n3;
+            range_copy(O.h.as<double>() + o, base_h + o, (long)O.sj[j].ncell * n3, s);
+            fsm_cc_apply<double>(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o, base_lp + o,
+                                 base_lh + o, O.scratch.p, O.chunk, s, O.geo[j].dim == 1 ? 2 : 1);
+        }
         // drop problems that reached their iteration cap
         std::vector<int> keep2;
         for (int j : active)
@@ -261,8 +328,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         if (st == LBE_OK && h_out)
             st = cuda_status(c, cudaMemcpy(h_out, O.h.p, vol64, cudaMemcpyDeviceToHost), "h");
     }
-    dev_free(c, h_old, vol64);
-    dev_free(c, r, vol32);
+    arena_release(c, aw);
     arena_release(c, ao);
     arena_release(c, ai);
     return st != LBE_OK ? st : worst;

@@ -68,6 +68,10 @@ struct Bucket {
     std::vector<SJob*> slot_job;
     std::vector<std::pair<long, long>> free_ranges;  // (offset, length), sorted by offset
     DevBuf aux;  // FP32 buckets: additive source r; FP64 buckets: copy of h before an iteration
+    // FP64 buckets of refined requests: operator of h as base (FP64, once per request) plus
+    // the FP32 operator of the increment (see Batch)
+    bool inc = false;
+    DevBuf base_h, base_lp, base_lh, inc_h, inc_lp, inc_lh, inc_scratch;
 };
 
 size_t coef_len(const SweepGeom& g) {
@@ -103,15 +107,17 @@ void give_range(Bucket& b, long off, long n) {
     b.free_ranges.swap(m);
 }
 
-std::string bucket_key(const lbe_problem& pb, int prec) {
+std::string bucket_key(const lbe_problem& pb, int prec, bool inc) {
     char k[160];
     const double R = pb.R > 0 ? pb.R : default_R(pb.vmax);
-    snprintf(k, sizeof k, "%d/%.17g/%d/%.17g/%d", pb.nv, pb.vmax, pb.M, R, prec);
+    snprintf(k, sizeof k, "%d/%.17g/%d/%.17g/%d/%d", pb.nv, pb.vmax, pb.M, R, prec, inc ? 1 : 0);
     return k;
 }
 
 // Buffers of a bucket: the batch layout of batch_init, sized by capacity instead of jobs.
-lbe_status bucket_create(Ctx* c, Bucket& b, const lbe_problem& pb, int prec, long cap_cells, int slots) {
+lbe_status bucket_create(Ctx* c, Bucket& b, const lbe_problem& pb, int prec, long cap_cells, int slots,
+                         bool inc) {
+    b.inc = inc;
     b.nv = pb.nv;
     b.M = pb.M;
     b.vmax = pb.vmax;
@@ -154,14 +160,28 @@ lbe_status bucket_create(Ctx* c, Bucket& b, const lbe_problem& pb, int prec, lon
                             {&B.coef, b.coef_per_slot * slots * 8}, {&B.work, b.work_per_slot * slots * 8},
                             {&B.sjobs, slots * sizeof(SweepJobDev)}, {&B.ijobs, slots * sizeof(SisJobDev)},
                             {&B.states, slots * sizeof(JobState)}, {&B.act, slots * sizeof(int)},
-                            {&b.aux, vol}};
+                            {&b.aux, vol},
+                            {&b.base_h, inc ? vol : 0}, {&b.base_lp, inc ? vol : 0}, {&b.base_lh, inc ? vol : 0},
+                            {&b.inc_h, inc ? vol / 2 : 0}, {&b.inc_lp, inc ? vol / 2 : 0},
+                            {&b.inc_lh, inc ? vol / 2 : 0},
+                            {&b.inc_scratch, inc ? fsm_cc_scratch_bytes(*B.t, (int)cap_cells, 4, &B.inc_chunk) : 0}};
     size_t total = 0;
     for (const Piece& q : pieces) total += (q.n + 255) & ~(size_t)255;
     if ((st = arena_reserve(c, b.arena, total)) != LBE_OK) return st;
     for (const Piece& q : pieces) {
+        if (q.n == 0) continue;
         q.d->p = arena_take(b.arena, q.n);
         q.d->n = q.n;
         if (!q.d->p) return LBE_INTERNAL;
+    }
+    if (inc) {
+        B.base_h = b.base_h.as<double>();
+        B.base_lp = b.base_lp.as<double>();
+        B.base_lh = b.base_lh.as<double>();
+        B.inc_h = b.inc_h.as<float>();
+        B.inc_lp = b.inc_lp.as<float>();
+        B.inc_lh = b.inc_lh.as<float>();
+        B.inc_scratch = b.inc_scratch.p;
     }
     if (prec != LBE_FP64) {
         B.extra = b.aux;  // zero outside correction solves
@@ -259,9 +279,9 @@ void slot_set_correction(Bucket& b, int s) {
     Batch& B = b.B;
     B.sj[s].forcing = kForcingNone;
     B.ij[s].ndsig = 0.0;
-    B.ij[s].eps = 1e-4;
+    B.ij[s].eps = 1e-6;
     B.ij[s].crit = 1;
-    B.ij[s].max_iter = 60;
+    B.ij[s].max_iter = 30;
     B.hstate[s] = JobState{};
     cudaStream_t st = b.stream;
     cudaMemcpyAsync(B.sjobs.as<SweepJobDev>() + s, &B.sj[s], sizeof(SweepJobDev), cudaMemcpyHostToDevice, st);
@@ -286,14 +306,14 @@ static Bucket* find_bucket(Service& sv, const std::string& key) {
     return nullptr;
 }
 
-static Bucket* get_bucket(Service& sv, Ctx* c, const lbe_problem& pb, int prec, lbe_status* st) {
-    const std::string key = bucket_key(pb, prec);
+static Bucket* get_bucket(Service& sv, Ctx* c, const lbe_problem& pb, int prec, bool inc, lbe_status* st) {
+    const std::string key = bucket_key(pb, prec, inc);
     Bucket* b = find_bucket(sv, key);
     *st = LBE_OK;
     if (b) return b;
     auto nb = std::make_unique<Bucket>();
     nb->key = key;
-    *st = bucket_create(c, *nb, pb, prec, sv.cap_cells_default, c->max_active);
+    *st = bucket_create(c, *nb, pb, prec, sv.cap_cells_default, c->max_active, inc);
     if (*st != LBE_OK) {
         if (nb->stream) cudaStreamDestroy(nb->stream);
         arena_release(c, nb->arena);
@@ -358,8 +378,8 @@ static void service_main(Ctx* c) {
             const bool refined = pb.precision == LBE_FP32_REFINED || pb.precision == LBE_BF16_REFINED;
             const int cells = lbe_problem_cells(&pb);
             lbe_status st;
-            Bucket* F = get_bucket(sv, c, pb, refined ? LBE_FP32 : pb.precision, &st);
-            Bucket* D = (F && refined) ? get_bucket(sv, c, pb, LBE_FP64, &st) : nullptr;
+            Bucket* F = get_bucket(sv, c, pb, refined ? LBE_FP32 : pb.precision, false, &st);
+            Bucket* D = (F && refined) ? get_bucket(sv, c, pb, LBE_FP64, true, &st) : nullptr;
             if (!F || (refined && !D)) {
                 if (live.empty()) {  // nothing will free memory: fail the request
                     std::lock_guard<std::mutex> lk(c->mu);
@@ -447,6 +467,13 @@ static void service_main(Ctx* c) {
                     cudaStream_t ds = D->stream;
                     if (sj->phase == 1) {
                         range_widen(e, h, n, ds);
+                        // the request's one FP64 collision-operator evaluation, at h0
+                        const long o = D->B.cell_off[sj->ds] * n3;
+                        range_copy(h, D->base_h.as<double>() + o, n, ds);
+                        fsm_cc_apply<double>(*D->B.t, D->B.sj[sj->ds].ncell, D->B.delta.as<double>() + D->B.cell_off[sj->ds],
+                                             D->base_h.as<double>() + o, D->base_lp.as<double>() + o,
+                                             D->base_lh.as<double>() + o, D->B.scratch.p, D->B.chunk, ds,
+                                             D->B.geo[sj->ds].dim == 1 ? 2 : 1);
                         // the FP32 flow rates of h start the FP64 change test
                         D->B.hstate[sj->ds] = JobState{};
                         D->B.hstate[sj->ds].M = js.M;

@@ -63,8 +63,11 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
     const T Sn = source<T>(jb.forcing, vel[nv - 1 - i1p], w2, w3, feq[vneg]);
     T hm1 = T(0), hm2 = T(0);
     o[vpos] = T(0);
+    T rn = n > 1 ? r[1 * n3 + vpos] : T(0);  // rhs of the next node is loaded one step ahead
     for (int i = 1; i < n; ++i) {
-        const T acc = (r[i * n3 + vpos] + Sp) - v1 * ((T)fb[i] * hm1 + (T)fc[i] * hm2);
+        const T ri = rn;
+        if (i + 1 < n) rn = r[(i + 1) * n3 + vpos];
+        const T acc = (ri + Sp) - v1 * ((T)fb[i] * hm1 + (T)fc[i] * hm2);
         const T hi = acc / (nup + v1 * (T)fa[i]);
         o[i * n3 + vpos] = hi;
         hm2 = hm1;
@@ -75,8 +78,11 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
     const T nun = d * nu1[vneg];
     T g1 = hm1, g2 = hm2;
     o[(n - 1) * n3 + vneg] = hm1;
+    T rb = n > 1 ? r[(n - 2) * n3 + vneg] : T(0);
     for (int i = n - 2; i >= 0; --i) {
-        const T acc = (r[i * n3 + vneg] + Sn) - u * ((T)bb[i] * g1 + (T)bc[i] * g2);
+        const T ri = rb;
+        if (i > 0) rb = r[(i - 1) * n3 + vneg];
+        const T acc = (ri + Sn) - u * ((T)bb[i] * g1 + (T)bc[i] * g2);
         const T hi = acc / (nun + u * (T)ba[i]);
         o[i * n3 + vneg] = hi;
         g2 = g1;
@@ -217,20 +223,38 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
     if (jb.scheme == 0) {  // CIS: no correction
         for (int c = threadIdx.x; c < n; c += blockDim.x) du[c] = 0.0;
     } else if (jb.dim == 1) {
-        if (threadIdx.x == 0) {
-            const double* fa = coef + jb.coef_off;  // block [fa | fb | fc | x], n each
-            const double* fb = fa + n;
-            const double* fc = fb + n;
-            const double* xs = fc + n;
-            double ym2 = 0.0, ym1 = m[0] + m[2];
-            du[0] = 0.0;  // U(x0) = U^(k+1/2)(x0)
-            for (int i = 1; i < n; ++i) {
-                double r = -jb.ndsig * xs[i] + G[(c0 + i) * 2] - fb[i] * ym1;
-                if (i >= 2) r -= fc[i] * ym2;
-                const double yi = r / fa[i];
-                du[i] = (yi - m[i * 5 + 2]) - m[i * 5 + 0];
-                ym2 = ym1;
-                ym1 = yi;
+        // the march is serial: the block stages 256 nodes at a time in shared memory and
+        // thread 0 walks them
+        __shared__ double sfa[256], sfb[256], sfc[256], srhs[256], sW[256], sU[256];
+        const double* fa = coef + jb.coef_off;  // block [fa | fb | fc | x], n each
+        const double* fb = fa + n;
+        const double* fc = fb + n;
+        const double* xs = fc + n;
+        double ym2 = 0.0, ym1 = m[0] + m[2];
+        if (threadIdx.x == 0) du[0] = 0.0;  // U(x0) = U^(k+1/2)(x0)
+        for (int w0 = 1; w0 < n; w0 += 256) {
+            const int i = w0 + threadIdx.x;
+            __syncthreads();
+            if (i < n) {
+                sfa[threadIdx.x] = fa[i];
+                sfb[threadIdx.x] = fb[i];
+                sfc[threadIdx.x] = fc[i];
+                srhs[threadIdx.x] = -jb.ndsig * xs[i] + G[(c0 + i) * 2];
+                sW[threadIdx.x] = m[i * 5 + 2];
+                sU[threadIdx.x] = m[i * 5 + 0];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int wn = min(256, n - w0);
+                for (int k = 0; k < wn; ++k) {
+                    const int ii = w0 + k;
+                    double r = srhs[k] - sfb[k] * ym1;
+                    if (ii >= 2) r -= sfc[k] * ym2;
+                    const double yi = r / sfa[k];
+                    du[ii] = (yi - sW[k]) - sU[k];
+                    ym2 = ym1;
+                    ym1 = yi;
+                }
             }
         }
     } else {
@@ -320,7 +344,7 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
     }
 }
 
-// h = hh + 2 dU v3 f_eq for the cells of the active jobs (Eq. guided).
+// h = hh + 2 dU v3 f_eq (+ extra) for the cells of the active jobs (Eq. guided).
 template <typename T>
 __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __restrict__ h,
                                                  const double* __restrict__ dU, const T* __restrict__ extra,
@@ -328,15 +352,17 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
                                                  const T* __restrict__ vel, const SweepJobDev* __restrict__ jobs,
                                                  const int* __restrict__ active, int nv) {
     const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
-    const long n3 = (long)nv * nv * nv;
-    const long total = (long)jb.ncell * n3;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-        const long c = k / n3;
-        const int v = (int)(k % n3);
-        const long g = jb.cell_off * n3 + k;
+    const int n3 = nv * nv * nv;
+    for (int c = blockIdx.x; c < jb.ncell; c += gridDim.x) {
+        const long g0 = (jb.cell_off + c) * (long)n3;
         const T d = (T)(2.0 * dU[jb.cell_off + c]);
-        const T x = hh[g] + d * vel[v % nv] * feq[v];
-        h[g] = extra ? x + extra[g] : x;
+        const T* src = hh + g0;
+        T* dst = h + g0;
+        const T* ex = extra ? extra + g0 : nullptr;
+        for (int v = threadIdx.x; v < n3; v += blockDim.x) {
+            const T x = src[v] + d * vel[v % nv] * feq[v];
+            dst[v] = ex ? x + ex[v] : x;
+        }
     }
 }
 
@@ -386,7 +412,7 @@ void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const doub
     g_launches += 1;
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
-    dim3 g(152, njobs);
+    dim3 g(304, njobs);
     k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv);
 }
 
