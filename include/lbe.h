@@ -152,6 +152,22 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R,
                        const void* h_dev, void* Lplus_dev, void* L_dev,
                        const double* ndelta_dev, double* G_dev, void* stream);
 
+/* Collision operator restricted to the parity subspace of the plate and duct solutions
+ * (steps A1-A3).  The source S of Sec. 2 is odd in v3, so every CIS / SIS iterate is odd in
+ * v3, and on plates also even in v2; the discrete operator commutes with those reflections.
+ * parity = 1: h odd in v3 (ducts); parity = 2: h odd in v3 and even in v2 (plates).  For
+ * such h the result equals lbe_apply_L's up to rounding; for other h it is not defined.
+ * LBE_FP64 / LBE_FP32: fast spectral transforms of one direction per reflection orbit
+ * (a quarter or half of the directions).  LBE_BF16_REFINED: the operator as a dense
+ * (nv^3/4 or nv^3/2)-square matrix at delta = 1, built once per grid from the FP64
+ * transforms, applied to all cells as one tcgen05 GEMM with bfloat16 hi/lo operands and FP32
+ * accumulation (relative error about 1e-5 of the scale); h, L+ h, L h are float.  Needs
+ * M >= 8.  Lplus_dev / L_dev may be NULL.  Returns after the work is queued on `stream`
+ * (the tensor-core form synchronises the stream). */
+lbe_status lbe_apply_L_sym(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_precision precision,
+                           int parity, int cells, const double* delta_dev, const void* h_dev,
+                           void* Lplus_dev, void* L_dev, void* stream);
+
 /* lbe_apply_L without any device allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code recording CUDA
  * graphs or running a latency-critical loop, where cudaMalloc / cudaFree would synchronise

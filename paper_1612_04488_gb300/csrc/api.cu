@@ -412,6 +412,9 @@ void batch_iterate(Batch& B) {
                                 B.inc_scratch, B.inc_chunk, s, mode);
             range_add_f64(B.base_lp + o, B.inc_lp + o, (double*)(lp + o), nn, s);
             range_add_f64(B.base_lh + o, B.inc_lh + o, (double*)(lh + o), nn, s);
+        } else if (sizeof(T) == 4 && B.use_tc) {
+            tc_apply_sym(B.c, B.t, mode, nc, B.delta.as<double>() + c0, (const float*)(h + c0 * n3),
+                         (float*)(lp + c0 * n3), (float*)(lh + c0 * n3), s);
         } else {
             fsm_cc_apply<T>(t, nc, B.delta.as<double>() + c0, h + c0 * n3, lp + c0 * n3, lh + c0 * n3,
                             B.scratch.p, B.chunk, s, mode);
@@ -550,6 +553,7 @@ lbe_status lbe_destroy(lbe_ctx* ctx) {
     stop_service(ctx);
     for (auto& kv : ctx->tables) {
         DevTables* t = kv.second.get();
+        tc_release(ctx, t);
         for (void* p : {(void*)t->feq_d, (void*)t->nu1_d, (void*)t->mult_d, (void*)t->ab_d, (void*)t->vel_d,
                         (void*)t->feq_f, (void*)t->nu1_f, (void*)t->mult_f, (void*)t->ab_f, (void*)t->vel_f})
             if (p) cudaFree(p);
@@ -664,6 +668,44 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_p
     }
     if (st != LBE_OK) return st;
     return cuda_status(ctx, cudaGetLastError(), "apply_L");
+}
+
+lbe_status lbe_apply_L_sym(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_precision precision, int parity,
+                           int cells, const double* delta_dev, const void* h_dev, void* Lplus_dev, void* L_dev,
+                           void* stream) {
+    if (!ctx) return LBE_BAD_ARG;
+    if (parity != 1 && parity != 2) return bad_arg(ctx, "parity must be 1 (odd in v3) or 2 (also even in v2)");
+    if (cells < 0 || (cells > 0 && (!h_dev || !delta_dev))) return bad_arg(ctx, "null h or delta");
+    if (nv != 8 && nv != 16 && nv != 24 && nv != 32) return bad_arg(ctx, "nv must be 8, 16, 24 or 32");
+    if (M < 8 || M > 64 || (M & (M - 1))) return bad_arg(ctx, "M must be a power of two in [8, 64]");
+    if (!(vmax > 0) || R > 2 * vmax) return bad_arg(ctx, "bad vmax or R");
+    if (precision != LBE_FP64 && precision != LBE_FP32 && precision != LBE_BF16_REFINED)
+        return bad_arg(ctx, "precision must be FP64, FP32 or BF16_REFINED");
+    if (cells == 0) return LBE_OK;
+    cudaSetDevice(ctx->device);
+    lbe_status st;
+    DevTables* t = get_tables(ctx, nv, vmax, M, R, &st);
+    if (!t) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int eb = precision == LBE_FP64 ? 8 : 4;
+    const size_t vol = (size_t)cells * nv * nv * nv * eb;
+    int chunk = 1;
+    const size_t scr = precision == LBE_BF16_REFINED ? 0 : fsm_cc_scratch_bytes(*t, cells, eb, &chunk);
+    const size_t need = scr + 256 + (Lplus_dev ? 0 : vol + 256) + (L_dev ? 0 : vol + 256);
+    if ((st = arena_reserve(ctx, ctx->apply_arena, need)) != LBE_OK) return st;
+    void* p = scr ? arena_take(ctx->apply_arena, scr) : nullptr;
+    void* lp = Lplus_dev ? Lplus_dev : arena_take(ctx->apply_arena, vol);
+    void* lo = L_dev ? L_dev : arena_take(ctx->apply_arena, vol);
+    if (precision == LBE_BF16_REFINED)
+        return tc_apply_sym(ctx, t, parity, cells, delta_dev, (const float*)h_dev, (float*)lp, (float*)lo, s);
+    if (precision == LBE_FP64)
+        st = fsm_cc_apply<double>(*t, cells, delta_dev, (const double*)h_dev, (double*)lp, (double*)lo, p, chunk, s,
+                                  parity);
+    else
+        st = fsm_cc_apply<float>(*t, cells, delta_dev, (const float*)h_dev, (float*)lp, (float*)lo, p, chunk, s,
+                                 parity);
+    if (st != LBE_OK) return st;
+    return cuda_status(ctx, cudaGetLastError(), "apply_L_sym");
 }
 
 lbe_status lbe_sweep(lbe_ctx* ctx, const lbe_problem* pb, const void* rhs_dev, void* h_dev, double* mom_dev,

@@ -42,6 +42,7 @@ struct Batch {
     float* inc_lh = nullptr;
     void* inc_scratch = nullptr;
     int inc_chunk = 1;
+    bool use_tc = false;  // FP32 batches: collision operator by the dense tensor-core GEMM
     int chunk = 1;
     std::vector<JobState> hstate;
     std::vector<int> active;

@@ -1,0 +1,486 @@
+// Collision operator on the parity subspace as one tcgen05 GEMM (BF16 hi/lo, FP32 accumulate).
+//
+// Solutions of the plate and duct problems are odd in v3 (the source S of Sec. 2 is) and, on
+// plates, even in v2; the discrete operator commutes with those reflections (the direction
+// set is closed under them).  On that subspace h is fixed by its values at one point per
+// orbit of velocity points -- Nr = nv^3/4 (plates) or nv^3/2 (ducts) values -- and the
+// operator (at delta = 1) is an Nr x Nr matrix A.  A is built once per velocity grid by
+// applying the FP64 fast-spectral operator to the Nr symmetric basis functions, so it is the
+// same discrete operator.  Applying it to every cell at once is the GEMM
+//     Y[c][q] = sum_q' A[q][q'] x_c[q'],     L+ h_c = delta_c * expand(Y[c]),
+// run with A = A_hi + A_lo and x = x_hi + x_lo split into bfloat16 and the three products
+// A_hi x_hi + A_lo x_hi + A_hi x_lo accumulated in FP32 tensor memory (about 2^-16 relative).
+//
+// Kernel: one CTA per 128 x BN output tile; operands staged by TMA (cp.async.bulk.tensor,
+// 128-byte swizzle) through a 4-stage mbarrier pipeline; one thread issues tcgen05.mma
+// (M = 128, N = BN, K = 16) into a TMEM accumulator; four warps read it back with
+// tcgen05.ld.  Every wait is bounded: on expiry the kernel raises an error word, drains its
+// own copies, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "lbe_internal.h"
+#include "sweep.h"
+
+namespace lbe {
+
+namespace {
+
+constexpr int kBM = 128, kBK = 64, kStages = 4;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait on an mbarrier phase; false when the deadline passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(16 >> 4) << 16;    // leading byte offset (unused by swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16 with bf16 A and B, f32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Y[col][row] = sum over segments s and k of A_s[row][k] * B_s[col][k].
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    k_dense_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+                 const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1, int Mrows,
+                 int ncols, int K, int nseg, uint32_t seg_codes, float* __restrict__ Y, int* __restrict__ err) {
+    constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2, STAGE = A_BYTES + B_BYTES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(base + kStages * STAGE);
+    uint64_t* empty = full + kStages;
+    uint64_t* done = empty + kStages;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int col0 = blockIdx.x * BN, row0 = blockIdx.y * kBM;
+    const int ktseg = K / kBK, KT = nseg * ktseg;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t IDESC = idesc_bf16(kBM, BN);
+
+    __shared__ int failed;
+    if (tid == 0) failed = 0;
+
+    if (tid == 0) {
+        auto issue = [&](int kt, int s) {
+            const int seg = kt / ktseg, kk = kt % ktseg;
+            const uint32_t code = (seg_codes >> (2 * seg)) & 3u;  // bit 0: A lo, bit 1: B lo
+            mbar_expect_tx(&full[s], STAGE);
+            tma_load_2d(base + s * STAGE, (code & 1u) ? &tmA1 : &tmA0, kk * kBK, row0, &full[s]);
+            tma_load_2d(base + s * STAGE + A_BYTES, (code & 2u) ? &tmB1 : &tmB0, kk * kBK, col0, &full[s]);
+        };
+        int issued = 0;
+        for (int s = 0; s < kStages && s < KT; ++s) issue(s, s), ++issued;
+        int consumed = 0;
+        bool ok = true;
+        for (int kt = 0; kt < KT; ++kt) {
+            const int s = kt % kStages;
+            if (!mbar_wait(&full[s], (kt / kStages) & 1)) {
+                ok = false;
+                break;
+            }
+            ++consumed;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(base + s * STAGE), b0 = a0 + A_BYTES;
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)
+                mma_bf16(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), IDESC, (kt > 0 || k > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+            const int nk = kt - 1 + kStages;  // refill the slot of the previous stage
+            if (kt >= 1 && nk < KT) {
+                const int sp = (kt - 1) % kStages;
+                if (!mbar_wait(&empty[sp], ((kt - 1) / kStages) & 1)) {
+                    ok = false;
+                    break;
+                }
+                issue(nk, sp);
+                ++issued;
+            }
+        }
+        if (!ok) {
+            failed = 1;
+            atomicExch(err, 1);
+            // drain the loads still in flight before the shared memory goes away
+            for (int kt = consumed; kt < issued; ++kt) mbar_wait(&full[kt % kStages], (kt / kStages) & 1);
+        }
+        mma_commit(done);
+    }
+    __syncthreads();  // the other threads wait here, not spinning beside the issuing thread
+    const bool got = mbar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (got && !failed) {
+        const int row = row0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+            if (row < Mrows) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = col0 + c0 + j;
+                    if (col < ncols) Y[(long)col * Mrows + row] = v[j];
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+}
+
+// ---- parity-subspace index maps -----------------------------------------------------------
+// mode 2 (plates): q = (i1 * H + i2) * H + i3, i2, i3 < H = nv/2; orbit signs: +1 for i2,
+// -1 for i3 (even in v2, odd in v3).  mode 1 (ducts): q = (i1 * nv + i2) * H + i3.
+__device__ __forceinline__ int rep_full(int q, int nv, int mode) {
+    const int H = nv / 2;
+    int i1, i2, i3;
+    if (mode == 2) {
+        i1 = q / (H * H);
+        i2 = (q / H) % H;
+        i3 = q % H;
+    } else {
+        i1 = q / (nv * H);
+        i2 = (q / H) % nv;
+        i3 = q % H;
+    }
+    return (i1 * nv + i2) * nv + i3;
+}
+__device__ __forceinline__ int orbit_of(int v, int nv, int mode, float* sign) {
+    const int H = nv / 2;
+    const int i1 = v / (nv * nv), i2 = (v / nv) % nv, i3 = v % nv;
+    const int j3 = i3 < H ? i3 : nv - 1 - i3;
+    *sign = i3 < H ? 1.f : -1.f;
+    if (mode == 2) {
+        const int j2 = i2 < H ? i2 : nv - 1 - i2;
+        return (i1 * H + j2) * H + j3;
+    }
+    return (i1 * nv + i2) * H + j3;
+}
+
+// x_hi / x_lo [cell][q] from h (float)
+__global__ void k_gather_split(const float* __restrict__ h, __nv_bfloat16* __restrict__ xh,
+                               __nv_bfloat16* __restrict__ xl, int cells, int nv, int nr, int mode) {
+    const long total = (long)cells * nr;
+    const long n3 = (long)nv * nv * nv;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
+        const long c = k / nr;
+        const int q = (int)(k % nr);
+        const float x = h[c * n3 + rep_full(q, nv, mode)];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        xh[k] = hi;
+        xl[k] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
+}
+
+// L+ h = delta Y expanded with the orbit signs; L h = L+ h - delta nu h
+__global__ void k_expand(const float* __restrict__ Y, const float* __restrict__ h, const float* __restrict__ nu1,
+                         const double* __restrict__ delta, float* __restrict__ Lplus, float* __restrict__ Lout,
+                         int cells, int nv, int nr, int mode) {
+    const long n3 = (long)nv * nv * nv;
+    const long total = (long)cells * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
+        const long c = k / n3;
+        const int v = (int)(k % n3);
+        float sg;
+        const int q = orbit_of(v, nv, mode, &sg);
+        const float d = (float)delta[c];
+        const float lp = d * sg * Y[c * nr + q];
+        if (Lplus) Lplus[k] = lp;
+        if (Lout) Lout[k] = lp - d * nu1[v] * h[k];
+    }
+}
+
+// symmetric basis functions e_q for q in [q0, q0 + nb): value sign at each orbit point
+__global__ void k_basis(double* __restrict__ h, int q0, int nb, int nv, int nr, int mode) {
+    const long n3 = (long)nv * nv * nv;
+    const long total = (long)nb * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
+        const long b = k / n3;
+        const int v = (int)(k % n3);
+        float sg;
+        const int q = orbit_of(v, nv, mode, &sg);
+        h[k] = (q == q0 + b) ? (double)sg : 0.0;
+    }
+}
+
+// columns q0 .. q0+nb of A (row-major [nr][nr], hi / lo bf16) from L+ e_q at the rep points
+__global__ void k_store_columns(const double* __restrict__ Lp, __nv_bfloat16* __restrict__ Ah,
+                                __nv_bfloat16* __restrict__ Al, int q0, int nb, int nv, int nr, int mode) {
+    const long n3 = (long)nv * nv * nv;
+    const long total = (long)nb * nr;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
+        const int q = (int)(k % nr);   // output row
+        const long b = k / nr;         // basis column
+        const double a = Lp[b * n3 + rep_full(q, nv, mode)];
+        const __nv_bfloat16 hi = __float2bfloat16_rn((float)a);
+        const long idx = (long)q * nr + (q0 + b);
+        Ah[idx] = hi;
+        Al[idx] = __float2bfloat16_rn((float)(a - (double)__bfloat162float(hi)));
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* ptr, long rows, long cols, int box_rows) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+constexpr int kBN = 256;
+constexpr size_t kGemmSmem = (size_t)kStages * (kBM * kBK * 2 + kBN * kBK * 2) + 1024 + 256;
+
+}  // namespace
+
+// Dense operator of one (tables, parity mode).
+struct DenseOp {
+    int mode = 0, nv = 0, nr = 0;
+    __nv_bfloat16* Ah = nullptr;
+    __nv_bfloat16* Al = nullptr;
+    CUtensorMap mAh, mAl;
+    size_t bytes = 0;
+};
+
+struct TcOperands {
+    std::mutex mu;
+    DenseOp op[3];  // by mode
+    // per-call workspace (grow-only)
+    Arena ws;
+    int* err = nullptr;
+};
+
+static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaStream_t s) {
+    const int nv = t->nv;
+    const int nr = mode == 2 ? nv * nv * nv / 4 : nv * nv * nv / 2;
+    if (nr % kBK != 0 || nr % kBM != 0) return LBE_UNSUPPORTED;
+    d.mode = mode;
+    d.nv = nv;
+    d.nr = nr;
+    const size_t abytes = (size_t)nr * nr * 2;
+    lbe_status st = dev_alloc(c, (void**)&d.Ah, abytes);
+    if (st == LBE_OK) st = dev_alloc(c, (void**)&d.Al, abytes);
+    if (st != LBE_OK) return st;
+    d.bytes = 2 * abytes;
+    // basis chunks through the FP64 fast-spectral operator (delta = 1)
+    const long n3 = (long)nv * nv * nv;
+    const int nb = (int)std::min<long>(nr, std::max<long>(1, (256L << 20) / (n3 * 8)));
+    int chunk = 1;
+    const size_t scr = fsm_cc_scratch_bytes(*t, nb, 8, &chunk);
+    void *hb = nullptr, *lp = nullptr, *lo = nullptr, *sc = nullptr, *dl = nullptr;
+    const size_t vb = (size_t)nb * n3 * 8;
+    st = dev_alloc(c, &hb, vb);
+    if (st == LBE_OK) st = dev_alloc(c, &lp, vb);
+    if (st == LBE_OK) st = dev_alloc(c, &lo, vb);
+    if (st == LBE_OK) st = dev_alloc(c, &sc, scr);
+    if (st == LBE_OK) st = dev_alloc(c, &dl, (size_t)nb * 8);
+    if (st == LBE_OK) {
+        std::vector<double> ones(nb, 1.0);
+        cudaMemcpyAsync(dl, ones.data(), nb * 8, cudaMemcpyHostToDevice, s);
+        for (int q0 = 0; q0 < nr && st == LBE_OK; q0 += nb) {
+            const int b = std::min(nb, nr - q0);
+            k_basis<<<1024, 256, 0, s>>>((double*)hb, q0, b, nv, nr, mode);
+            st = fsm_cc_apply<double>(*t, b, (const double*)dl, (const double*)hb, (double*)lp, (double*)lo, sc, chunk,
+                                      s, mode);
+            k_store_columns<<<1024, 256, 0, s>>>((const double*)lp, d.Ah, d.Al, q0, b, nv, nr, mode);
+            g_launches += 2;
+        }
+        if (st == LBE_OK) st = cuda_status(c, cudaStreamSynchronize(s), "dense operator build");
+    }
+    dev_free(c, hb, vb);
+    dev_free(c, lp, vb);
+    dev_free(c, lo, vb);
+    dev_free(c, sc, scr);
+    dev_free(c, dl, (size_t)nb * 8);
+    if (st != LBE_OK) return st;
+    if (!make_map(&d.mAh, d.Ah, nr, nr, kBM) || !make_map(&d.mAl, d.Al, nr, nr, kBM)) {
+        c->last_error = "cuTensorMapEncodeTiled unavailable or failed";
+        return LBE_INTERNAL;
+    }
+    return LBE_OK;
+}
+
+// L+ h and L h on the parity subspace with the dense tensor-core operator (float in / out).
+lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h, float* Lplus,
+                        float* Lout, cudaStream_t s) {
+    if (mode != 1 && mode != 2) return LBE_BAD_ARG;
+    if (cells <= 0) return LBE_OK;
+    if (!t->tc) t->tc = new TcOperands();
+    TcOperands& T = *t->tc;
+    std::lock_guard<std::mutex> lk(T.mu);
+    DenseOp& d = T.op[mode];
+    lbe_status st;
+    if (!d.Ah && (st = build_dense(c, t, d, mode, s)) != LBE_OK) return st;
+    const int nr = d.nr, nv = t->nv;
+    const long cpad = (cells + kBN - 1) / kBN * kBN;  // whole TMA boxes, zero padding rows
+    const size_t xb = (size_t)cpad * nr * 2, yb = (size_t)cells * nr * 4;
+    if ((st = arena_reserve(c, T.ws, 2 * xb + yb + 4 * 256 + 64)) != LBE_OK) return st;
+    auto* xh = (__nv_bfloat16*)arena_take(T.ws, xb);
+    auto* xl = (__nv_bfloat16*)arena_take(T.ws, xb);
+    auto* Y = (float*)arena_take(T.ws, yb);
+    auto* err = (int*)arena_take(T.ws, 64);
+    if (cpad > cells) {
+        cudaMemsetAsync(xh + (size_t)cells * nr, 0, (size_t)(cpad - cells) * nr * 2, s);
+        cudaMemsetAsync(xl + (size_t)cells * nr, 0, (size_t)(cpad - cells) * nr * 2, s);
+    }
+    CUtensorMap mXh, mXl;
+    if (!make_map(&mXh, xh, cpad, nr, kBN) || !make_map(&mXl, xl, cpad, nr, kBN)) {
+        c->last_error = "cuTensorMapEncodeTiled failed for the cell operand";
+        return LBE_INTERNAL;
+    }
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_dense_gemm<kBN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+        attr = true;
+    }
+    cudaMemsetAsync(err, 0, 4, s);
+    k_gather_split<<<1024, 256, 0, s>>>(h, xh, xl, cells, nv, nr, mode);
+    // segments: (A_hi, x_hi), (A_lo, x_hi), (A_hi, x_lo); code bit 0 = A lo, bit 1 = x lo
+    const uint32_t codes = (0u) | (1u << 2) | (2u << 4);
+    dim3 grid((cells + kBN - 1) / kBN, nr / kBM);
+    k_dense_gemm<kBN><<<grid, 128, kGemmSmem, s>>>(d.mAh, d.mAl, mXh, mXl, nr, cells, nr, 3, codes, Y, err);
+    const float* nu1 = t->nu1_f;
+    k_expand<<<2048, 256, 0, s>>>(Y, h, nu1, delta, Lplus, Lout, cells, nv, nr, mode);
+    g_launches += 3;
+    g_levals += cells;
+    int herr = 0;
+    cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s);
+    st = cuda_status(c, cudaStreamSynchronize(s), "dense operator");
+    if (st == LBE_OK && herr) {
+        c->last_error = "tensor-core operator: a bounded wait expired";
+        return LBE_TIMEOUT;
+    }
+    return st;
+}
+
+lbe_status tc_apply_L(Ctx* c, DevTables* t, int cells, const double* delta, const float* h, float* Lplus,
+                      float* Lout, cudaStream_t s) {
+    (void)t;
+    (void)cells;
+    (void)delta;
+    (void)h;
+    (void)Lplus;
+    (void)Lout;
+    (void)s;
+    c->last_error = "the tensor-core operator acts on the parity subspace: use lbe_apply_L_sym";
+    return LBE_UNSUPPORTED;
+}
+
+void tc_release(Ctx* c, DevTables* t) {
+    if (!t->tc) return;
+    for (auto& d : t->tc->op) {
+        dev_free(c, d.Ah, d.bytes / 2);
+        dev_free(c, d.Al, d.bytes / 2);
+    }
+    arena_release(c, t->tc->ws);
+    delete t->tc;
+    t->tc = nullptr;
+}
+
+}  // namespace lbe

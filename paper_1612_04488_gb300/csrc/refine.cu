@@ -164,6 +164,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
     lbe_status st = batch_init(O, c, po.data(), n, &ao, s);
     if (st == LBE_OK) st = batch_init(I, c, pi.data(), n, &ai, s);
     if (st == LBE_OK) {  // low-precision phases test changes against the flow-rate scale
+        I.use_tc = pbs[0].precision == LBE_BF16_REFINED && O.t->sym_reps2 > 0 && pbs[0].M >= 8;
         for (int j = 0; j < n; ++j) I.ij[j].crit = 1;
         cudaMemcpyAsync(I.ijobs.p, I.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, s);
     }

@@ -10,9 +10,12 @@ namespace lbe {
 struct DevTables;
 struct Ctx;
 
-// fsm_tc.cu: BF16 tensor-core collision operator (float in / out)
+// fsm_dense.cu: tensor-core operator on the parity subspace (float in / out; mode 1 or 2)
 lbe_status tc_apply_L(Ctx* c, DevTables* t, int cells, const double* delta, const float* h, float* Lplus,
                       float* Lout, cudaStream_t s);
+lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h,
+                        float* Lplus, float* Lout, cudaStream_t s);
+void tc_release(Ctx* c, DevTables* t);
 // refine.cu: BF16 operator inside an outer defect-correction loop
 lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs, double* U3_out,
                          double* h_out);

@@ -72,6 +72,7 @@ def lib():
         L.lbe_poll.argtypes = [vp, C.c_uint64, C.POINTER(Result), C.POINTER(C.c_int)]
         L.lbe_set_max_active.argtypes = [vp, ip]
         L.lbe_set_stream.argtypes = [vp, vp]
+        L.lbe_apply_L_sym.argtypes = [vp, ip, C.c_double, ip, C.c_double, ip, ip, ip, vp, vp, vp, vp, vp]
         L.lbe_apply_L_noalloc.argtypes = [vp, ip, C.c_double, ip, C.c_double, ip, ip, vp, vp, vp, vp, vp]
         L.lbe_batch_create.argtypes = [vp, C.POINTER(Problem), ip, C.POINTER(vp)]
         L.lbe_batch_run.argtypes = [vp, C.POINTER(Result)]
@@ -150,6 +151,12 @@ class Context:
                 nd_ptr=None, G_ptr=None, stream=None):
         st = lib().lbe_apply_L(self.h, nv, vmax, M, R, precision, cells, delta_ptr, h_ptr,
                                lplus_ptr, l_ptr, nd_ptr, G_ptr, stream)
+        return self.check(st)
+
+    def apply_L_sym(self, nv, vmax, M, R, precision, parity, cells, delta_ptr, h_ptr, lplus_ptr, l_ptr,
+                    stream=None):
+        st = lib().lbe_apply_L_sym(self.h, nv, vmax, M, R, precision, parity, cells, delta_ptr, h_ptr,
+                                   lplus_ptr, l_ptr, stream)
         return self.check(st)
 
     def apply_L_noalloc(self, nv, vmax, M, R, precision, cells, delta_ptr, h_ptr, lplus_ptr, l_ptr,
