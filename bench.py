@@ -201,7 +201,8 @@ def run_reference(args):
 
 
 def run_op_only(args):
-    """Collision operator alone on the workload's cells (for profiling); prints timings."""
+    """Collision operator alone on the workload's cells (for profiling); prints timings.
+    bf16: the tensor-core parity-subspace operator; fp32 / fp64: the full fast-spectral one."""
     import torch
 
     from paper_1612_04488_gb300 import lbe
@@ -216,15 +217,23 @@ def run_op_only(args):
     nv, M = pbs[0].nv, pbs[0].M
     cells = sum(lbe.cells_of(p) for p in pbs)
     dt = torch.float64 if prec == lbe.FP64 else torch.float32
-    hd = torch.tensor(W.random_h(cells, nv, 6.0, seed=11), device="cuda", dtype=dt)
+    h = W.random_h(cells, nv, 6.0, seed=11)
+    h = 0.5 * (h + h[:, :, ::-1, :])
+    hd = torch.tensor(h, device="cuda", dtype=dt)
     dd = torch.full((cells,), 1.0, device="cuda", dtype=torch.float64)
     lp = torch.empty_like(hd)
+    lo = torch.empty_like(hd)
+    parity = 2 if pbs[0].geom.dim == 1 else 1
     times = []
     for i in range(args.warmup + args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        ctx.apply_L(nv, 6.0, M, pbs[0].R, prec, cells, dd.data_ptr(), hd.data_ptr(), lp.data_ptr(), None,
-                    stream=stream.cuda_stream)
+        if prec == lbe.BF16_REFINED:
+            ctx.apply_L_sym(nv, 6.0, M, pbs[0].R, prec, parity, cells, dd.data_ptr(), hd.data_ptr(), lp.data_ptr(),
+                            lo.data_ptr(), stream=stream.cuda_stream)
+        else:
+            ctx.apply_L(nv, 6.0, M, pbs[0].R, prec, cells, dd.data_ptr(), hd.data_ptr(), lp.data_ptr(), None,
+                        stream=stream.cuda_stream)
         b.record(stream)
         b.synchronize()
         if i >= args.warmup:
@@ -389,43 +398,69 @@ def run_ours(args):
            "h2d_bytes_per_step": int((s1["h2d_bytes"] - s0["h2d_bytes"]) / args.steps),
            "d2h_bytes_per_step": int((s1["d2h_bytes"] - s0["d2h_bytes"]) / args.steps)}
 
-    # ---- collision operator alone (dominant kernel chain) ----------------------------
+    # ---- collision operator alone (dominant kernel) ------------------------------------
     nv, M = pbs[0].nv, pbs[0].M
     cells = sum(lbe.cells_of(p) for p in pbs)
     from paper_1612_04488_gb300 import workloads as W
     hnp = W.random_h(cells, nv, 6.0, seed=11)
+    hnp = 0.5 * (hnp + hnp[:, :, ::-1, :])  # plate parity: odd in v3, even in v2
     deltas = torch.tensor(np.repeat([p.delta for p in pbs], [lbe.cells_of(p) for p in pbs]),
                           device="cuda", dtype=torch.float64)
+    parity = 2 if pbs[0].geom.dim == 1 else 1
 
-    def time_apply(precision, reps):
+    def time_apply(precision, reps, sym):
         dt = torch.float64 if precision == lbe.FP64 else torch.float32
         hd = torch.tensor(hnp, device="cuda", dtype=dt)
         lp = torch.empty_like(hd)
-        ctx.apply_L(nv, 6.0, M, pbs[0].R, precision, cells, deltas.data_ptr(), hd.data_ptr(),
-                    lp.data_ptr(), None, stream=stream.cuda_stream)
+        lo = torch.empty_like(hd)
+
+        def call():
+            if sym:
+                ctx.apply_L_sym(nv, 6.0, M, pbs[0].R, precision, parity, cells, deltas.data_ptr(), hd.data_ptr(),
+                                lp.data_ptr(), lo.data_ptr(), stream=stream.cuda_stream)
+            else:
+                ctx.apply_L(nv, 6.0, M, pbs[0].R, precision, cells, deltas.data_ptr(), hd.data_ptr(),
+                            lp.data_ptr(), None, stream=stream.cuda_stream)
+        call()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(reps):
-            ctx.apply_L(nv, 6.0, M, pbs[0].R, precision, cells, deltas.data_ptr(), hd.data_ptr(),
-                        lp.data_ptr(), None, stream=stream.cuda_stream)
+            call()
         b.record(stream)
         b.synchronize()
         return a.elapsed_time(b) / reps
 
-    op_prec = lbe.FP32 if prec in (lbe.BF16_REFINED, lbe.FP32_REFINED) else prec
-    ms_op = time_apply(op_prec, 5)
-    ms_fp64 = time_apply(lbe.FP64, 2)
-    flops = fft_flops_per_cell(nv, M) * cells
     peaks = load_peaks()
-    clk_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak_tflops = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
-    achieved = flops / (ms_op / 1000.0) / 1e12
-    roofline = {"bound": "alu", "kernel": "collision operator A1-A3 (fsm_cc chain)",
-                "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak_tflops,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (clk_mhz, peaks["_source"]),
-                "traffic": None, "algorithmic_flops_per_launch": flops, "ms_per_launch": ms_op}
+    ms_fp64 = time_apply(lbe.FP64, 2, False)
+    ms_fp64_sym = time_apply(lbe.FP64, 2, True)
+    ms_fp32_sym = time_apply(lbe.FP32, 5, True)
+    alg_flops = fft_flops_per_cell(nv, M) * cells
+    if prec == lbe.BF16_REFINED:
+        ms_op = time_apply(lbe.BF16_REFINED, 5, True)
+        nr = nv ** 3 // (4 if parity == 2 else 2)
+        exec_flops = 3 * 2.0 * nr * nr * cells
+        peak = peaks.get("bf16_tflops", 1900.0)
+        achieved = exec_flops / (ms_op / 1000.0) / 1e12
+        roofline = {"bound": "tensor", "kernel": "k_dense_gemm (tcgen05 BF16 hi/lo x3, FP32 accumulate) "
+                                                 "+ gather/expand, timed as one lbe_apply_L_sym call",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": "bf16_tflops (burst, %s)" % peaks["_source"], "traffic": None,
+                    "executed_flops_per_launch": exec_flops, "algorithmic_flops_per_launch": alg_flops,
+                    "algorithmic_tflops": alg_flops / (ms_op / 1000.0) / 1e12, "ms_per_launch": ms_op}
+    else:
+        ms_op = ms_fp32_sym if prec != lbe.FP64 else ms_fp64_sym
+        clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+        lanes = 128 if prec != lbe.FP64 else 2
+        peak = 152 * lanes * 2 * clk_mhz * 1e6 / 1e12
+        sym_flops = (5.0 * nv ** 3 * np.log2(nv ** 3) * (M // (4 if parity == 2 else 2) + 2)) * cells
+        achieved = sym_flops / (ms_op / 1000.0) / 1e12
+        roofline = {"bound": "alu", "kernel": "fast spectral transforms (fsm_cc chain, symmetry-reduced)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": "152 SMs x %d lanes x 2 x %.0f MHz" % (lanes, clk_mhz), "traffic": None,
+                    "algorithmic_flops_per_launch": sym_flops, "ms_per_launch": ms_op}
+    l_evals = {"op": cells / (ms_op / 1000.0), "fp32_fft_sym": cells / (ms_fp32_sym / 1000.0),
+               "fp64_fft_sym": cells / (ms_fp64_sym / 1000.0), "fp64_fft_full": cells / (ms_fp64 / 1000.0)}
 
     line = {
         "metric": "SIS solves/s at 1e-6 flow-rate error", "value": value, "unit": "solves/s",
@@ -440,7 +475,7 @@ def run_ours(args):
                        "what": "per solve, batch start to that solve's convergence"},
         "iterations": iters, "refinements": refinements, "status": status,
         "max_rel_err_vs_fp64": err,
-        "l_evals_per_s": cells / (ms_op / 1000.0), "l_evals_per_s_fp64": cells / (ms_fp64 / 1000.0),
+        "l_evals_per_s": l_evals["op"], "l_evals_per_s_fp64": l_evals["fp64_fft_full"], "l_evals_detail": l_evals,
         "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -468,7 +503,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plates32x8", choices=["plates32x8", "plates16", "duct64x32"])
-    ap.add_argument("--precision", default="fp32r", choices=sorted(PRECISIONS))
+    ap.add_argument("--precision", default="bf16", choices=sorted(PRECISIONS))
     ap.add_argument("--eps", type=float, default=1e-7)
     ap.add_argument("--ref-iters", type=int, default=45)
     ap.add_argument("--ref-sample-s", type=float, default=12.0)

@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "batch.h"
@@ -202,6 +204,11 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
     std::vector<int> outer_it(n, 0), inner_it(n, 0), refs(n, 0);
     std::vector<double> t_done(n, 0.0);
     std::vector<double> prev_rel(n, 1e300);
+    // problems whose last correction did not cut the change by 10x continue with plain FP64
+    // SIS steps (the low-precision correction map has reached its precision floor)
+    std::vector<char> plain(n, 0);
+    std::vector<double> rel_before(n, 0.0);
+    const bool trace = std::getenv("LBE_TRACE") != nullptr;  // per-step progress on stderr
     std::vector<char> rebase(n, 0);
     std::vector<int> active(n);
     for (int j = 0; j < n; ++j) active[j] = j;
@@ -271,39 +278,71 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
                 t_done[j] = tnow;
             // the increment's FP32 error (~1e-7 |h - h0|) is the floor of this scheme; when the
             // change stalls near it, re-centre: evaluate the FP64 operator at the next iterate
-            const double rel = O.hstate[j].rel;
-            rebase[j] = (rel > 0.5 * prev_rel[j] && rel < 1e-7) ? 1 : 0;
+            const double rel = O.hstate[j].rel, pr = prev_rel[j];
+            rebase[j] = (rel > 0.5 * pr && rel < 1e-7) ? 1 : 0;
             prev_rel[j] = rel;
+            if (!plain[j] && refs[j] >= 1 && rel > 0.1 * rel_before[j]) plain[j] = 1;
+            rel_before[j] = rel;
+            if (plain[j] && rel > 0.9 * pr) rebase[j] = 1;  // plain steps stalled: exact FP64 operator
+            if (trace) {
+                const long o = O.cell_off[j] * n3, nn = (long)O.sj[j].ncell * n3;
+                std::vector<double> hh(nn), hb(nn);
+                cudaMemcpy(hh.data(), h_old + o, nn * 8, cudaMemcpyDeviceToHost);
+                cudaMemcpy(hb.data(), base_h + o, nn * 8, cudaMemcpyDeviceToHost);
+                double dmax = 0, hmax = 0;
+                for (long k = 0; k < nn; ++k) {
+                    dmax = std::max(dmax, std::fabs(hh[k] - hb[k]));
+                    hmax = std::max(hmax, std::fabs(hh[k]));
+                }
+                fprintf(stderr, "lbe refine: problem %d outer %d M %.17g Q %.17g rel %.3e |h-h0|/|h| %.3e%s%s\n", j,
+                        outer_it[j], O.hstate[j].M, O.hstate[j].Q, rel, dmax / hmax, rebase[j] ? " re-centre" : "",
+                        plain[j] ? " plain" : "");
+            }
         }
         active.swap(keep);
         if (active.empty()) break;
-        // correction solve for the unfinished problems
-        const int nk = (int)active.size();
-        cudaMemcpyAsync(O.act.p, active.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s);
-        k_residual<<<dim3(152, nk), blk, 0, s>>>(O.h.as<double>(), h_old, r, O.sjobs.as<SweepJobDev>(),
-                                                 O.act.as<int>(), n3);
-        g_launches += 1;
-        for (int j : active) {
-            cudaMemsetAsync(I.h.as<float>() + I.cell_off[j] * n3, 0, I.sj[j].ncell * n3 * 4, s);
-            I.hstate[j] = JobState{};
-        }
-        cudaMemcpyAsync(I.states.p, I.hstate.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, s);
-        g_h2d += n * sizeof(JobState);
-        I.active = active;
-        if ((st = batch_run(I, 30)) != LBE_OK) break;
-        for (int j : active) {
-            inner_it[j] += I.hstate[j].iters;
-            ++refs[j];
-        }
-        k_apply_correction<<<dim3(152, nk), blk, 0, s>>>(h_old, I.h.as<float>(), O.h.as<double>(),
-                                                         O.sjobs.as<SweepJobDev>(), O.act.as<int>(), n3);
-        g_launches += 1;
-        for (int j : active) {
+        // correction solve for the unfinished problems (plain ones keep h = Phi(h_old))
+        std::vector<int> corr, rb_plain;
+        for (int j : active) (plain[j] ? rb_plain : corr).push_back(j);
+        for (int j : rb_plain) {
             if (!rebase[j]) continue;
             const long o = O.cell_off[j] * n3;
             range_copy(O.h.as<double>() + o, base_h + o, (long)O.sj[j].ncell * n3, s);
             fsm_cc_apply<double>(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o, base_lp + o,
                                  base_lh + o, O.scratch.p, O.chunk, s, O.geo[j].dim == 1 ? 2 : 1);
+        }
+        if (!corr.empty()) {
+            const int nk = (int)corr.size();
+            cudaMemcpyAsync(O.act.p, corr.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s);
+            k_residual<<<dim3(152, nk), blk, 0, s>>>(O.h.as<double>(), h_old, r, O.sjobs.as<SweepJobDev>(),
+                                                     O.act.as<int>(), n3);
+            g_launches += 1;
+            for (int j : corr) {
+                cudaMemsetAsync(I.h.as<float>() + I.cell_off[j] * n3, 0, I.sj[j].ncell * n3 * 4, s);
+                I.hstate[j] = JobState{};
+            }
+            cudaMemcpyAsync(I.states.p, I.hstate.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, s);
+            g_h2d += n * sizeof(JobState);
+            I.active = corr;
+            if ((st = batch_run(I, 30)) != LBE_OK) break;
+            for (int j : corr) {
+                inner_it[j] += I.hstate[j].iters;
+                ++refs[j];
+                if (trace)
+                    fprintf(stderr, "lbe refine: problem %d correction %d inner iterations %d Me %.3e Qe %.3e rel %.3e\n",
+                            j, refs[j], I.hstate[j].iters, I.hstate[j].M, I.hstate[j].Q, I.hstate[j].rel);
+            }
+            cudaMemcpyAsync(O.act.p, corr.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s);
+            k_apply_correction<<<dim3(152, nk), blk, 0, s>>>(h_old, I.h.as<float>(), O.h.as<double>(),
+                                                             O.sjobs.as<SweepJobDev>(), O.act.as<int>(), n3);
+            g_launches += 1;
+            for (int j : corr) {
+                if (!rebase[j]) continue;
+                const long o = O.cell_off[j] * n3;
+                range_copy(O.h.as<double>() + o, base_h + o, (long)O.sj[j].ncell * n3, s);
+                fsm_cc_apply<double>(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o,
+                                     base_lp + o, base_lh + o, O.scratch.p, O.chunk, s, O.geo[j].dim == 1 ? 2 : 1);
+            }
         }
         // drop problems that reached their iteration cap
         std::vector<int> keep2;

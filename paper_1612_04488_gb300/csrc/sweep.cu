@@ -344,7 +344,15 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
     }
 }
 
-// h = hh + 2 dU v3 f_eq (+ extra) for the cells of the active jobs (Eq. guided).
+// h = P(hh + extra) + 2 dU v3 f_eq for the cells of the active jobs (Eq. guided), where P
+// projects onto the parity group of the solution: plates odd in v3 and even in v2, ducts odd
+// in v3 (the sources X_P v3 f_eq and X_T (c^2 - 5/2) v3 f_eq have it, and transport and the
+// collision operator preserve it).  The exact iterates never leave that subspace, but
+// rounding does (the FFT of the loss term is not mirror-exact), and outside it sits the
+// density mode, which the diffusion correction does not accelerate and which the discrete
+// operator, conserving mass only to quadrature accuracy, leaves at |lambda| ~ 1 for large
+// delta: seeded at FP32 rounding it would never decay.  One thread per orbit, so the
+// projection moves no extra bytes.
 template <typename T>
 __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __restrict__ h,
                                                  const double* __restrict__ dU, const T* __restrict__ extra,
@@ -352,16 +360,50 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
                                                  const T* __restrict__ vel, const SweepJobDev* __restrict__ jobs,
                                                  const int* __restrict__ active, int nv) {
     const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
-    const int n3 = nv * nv * nv;
+    const int n3 = nv * nv * nv, hv = nv / 2;
+    const bool plates = jb.ny == 0;  // 1D: orbits {1, R2, R3, R2R3}; 2D: {1, R3}
+    const int norb = plates ? n3 / 4 : n3 / 2;
     for (int c = blockIdx.x; c < jb.ncell; c += gridDim.x) {
         const long g0 = (jb.cell_off + c) * (long)n3;
         const T d = (T)(2.0 * dU[jb.cell_off + c]);
         const T* src = hh + g0;
         T* dst = h + g0;
         const T* ex = extra ? extra + g0 : nullptr;
-        for (int v = threadIdx.x; v < n3; v += blockDim.x) {
-            const T x = src[v] + d * vel[v % nv] * feq[v];
-            dst[v] = ex ? x + ex[v] : x;
+        for (int r = threadIdx.x; r < norb; r += blockDim.x) {
+            const int i3 = r % hv;
+            int i1, i2;
+            if (plates) {
+                i2 = (r / hv) % hv;
+                i1 = r / (hv * hv);
+            } else {
+                i2 = (r / hv) % nv;
+                i1 = r / (hv * nv);
+            }
+            const int va = (i1 * nv + i2) * nv + i3;        // v3 < 0 half
+            const int vc = (i1 * nv + i2) * nv + nv - 1 - i3;  // R3
+            T xa = src[va], xc = src[vc];
+            if (ex) {
+                xa += ex[va];
+                xc += ex[vc];
+            }
+            if (plates) {
+                const int vb = (i1 * nv + nv - 1 - i2) * nv + i3;           // R2
+                const int vd = (i1 * nv + nv - 1 - i2) * nv + nv - 1 - i3;  // R2 R3
+                T xb = src[vb], xd = src[vd];
+                if (ex) {
+                    xb += ex[vb];
+                    xd += ex[vd];
+                }
+                const T y = (T)0.25 * ((xa + xb) - (xc + xd)) + d * vel[i3] * feq[va];
+                dst[va] = y;
+                dst[vb] = y;
+                dst[vc] = -y;
+                dst[vd] = -y;
+            } else {
+                const T y = (T)0.5 * (xa - xc) + d * vel[i3] * feq[va];
+                dst[va] = y;
+                dst[vc] = -y;
+            }
         }
     }
 }

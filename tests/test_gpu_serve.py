@@ -35,8 +35,8 @@ def wait_all(ctx, tickets, timeout=120.0):
     return [out[t] for t in tickets]
 
 
-def mix(prec):
-    base = dict(nv=8, vmax=4.0, M=8, R=3.0, scheme=lbe.SIS, precision=prec, eps=1e-9, max_iter=300)
+def mix(prec, eps=1e-9):
+    base = dict(nv=8, vmax=4.0, M=8, R=3.0, scheme=lbe.SIS, precision=prec, eps=eps, max_iter=300)
     pbs = [lbe.problem(dim=1, ns=ns, grid_kind=1, delta=d, forcing=f, **base)
            for ns, d, f in ((12, 0.1, 0), (30, 1.0, 1), (20, 10.0, 0), (50, 3.0, 1))]
     pbs += [lbe.problem(dim=2, nx=nx, ny=ny, width=nx / ny, delta=d, forcing=f, **base)
@@ -58,13 +58,15 @@ def test_served_equals_solve_and_mix_equals_alone(ctx):
 
 def test_admission_with_few_slots_and_arrivals_in_flight(ctx):
     ctx.set_max_active(2)
-    pbs = mix(lbe.FP32)
-    tickets = [ctx.submit(p) for p in pbs[:3]]
-    time.sleep(0.01)
-    tickets += [ctx.submit(p) for p in pbs[3:]]
-    res = wait_all(ctx, tickets)
-    assert all(r.status == lbe.OK for r in res)
-    ctx.set_max_active(64)
+    try:
+        pbs = mix(lbe.FP32, eps=1e-6)  # the relative-change test FP32 arithmetic can meet
+        tickets = [ctx.submit(p) for p in pbs[:3]]
+        time.sleep(0.01)
+        tickets += [ctx.submit(p) for p in pbs[3:]]
+        res = wait_all(ctx, tickets)
+    finally:
+        ctx.set_max_active(64)
+    assert all(r.status == lbe.OK for r in res), [(r.status, r.iters, r.last_rel_change) for r in res]
 
 
 def test_refined_requests_reach_fp64(ctx):
@@ -73,7 +75,7 @@ def test_refined_requests_reach_fp64(ctx):
     rp = mix(lbe.FP32_REFINED)
     got = wait_all(ctx, [ctx.submit(p) for p in rp])
     for r, g in zip(ref, got):
-        assert g.status == lbe.OK
+        assert g.status == lbe.OK, (g.status, g.iters, g.refinements, g.mass_flow, r.mass_flow)
         assert abs(g.mass_flow - r.mass_flow) <= 1e-7 * abs(r.mass_flow)
         assert abs(g.heat_flow - r.heat_flow) <= 1e-7 * abs(r.heat_flow)
 
