@@ -202,7 +202,9 @@ def run_reference(args):
 
 def run_op_only(args):
     """Collision operator alone on the workload's cells (for profiling); prints timings.
-    bf16: the tensor-core parity-subspace operator; fp32 / fp64: the full fast-spectral one."""
+    bf16: the tensor-core parity-subspace operator; fp32 / fp64: the fast-spectral one, over
+    all directions or, with --sym, over one direction per reflection orbit (as the solves run
+    it)."""
     import torch
 
     from paper_1612_04488_gb300 import lbe
@@ -228,7 +230,7 @@ def run_op_only(args):
     for i in range(args.warmup + args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        if prec == lbe.BF16_REFINED:
+        if prec == lbe.BF16_REFINED or args.sym:
             ctx.apply_L_sym(nv, 6.0, M, pbs[0].R, prec, parity, cells, dd.data_ptr(), hd.data_ptr(), lp.data_ptr(),
                             lo.data_ptr(), stream=stream.cuda_stream)
         else:
@@ -350,6 +352,7 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms, solve_ms = [], []
     with Clocks(local) as clk:
+        torch.cuda.nvtx.range_push("timed")  # lets a profiler select exactly these launches
         e0.record(stream)
         for _ in range(args.steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -361,6 +364,7 @@ def run_ours(args):
             solve_ms += [1000.0 * r.seconds for r in res]
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     st1 = lbe.stats()
     if dist:
         dist.barrier()
@@ -510,6 +514,7 @@ def main():
     ap.add_argument("--no-check-fp64", dest="check_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--op-only", action="store_true", help="time the collision operator alone")
+    ap.add_argument("--sym", action="store_true", help="--op-only: parity-reduced fast-spectral operator")
     ap.add_argument("--serve", action="store_true", help="serving stream with Poisson arrivals")
     ap.add_argument("--requests", type=int, default=64)
     args = ap.parse_args()
