@@ -61,8 +61,19 @@ typedef enum { LBE_CIS = 0, LBE_SIS = 1 } lbe_scheme;
  * for LBE_FP64), and the correction equation is solved by low-precision SIS iterations
  * whose collision operator runs as tcgen05 BF16 spectral GEMMs with FP32 accumulation
  * (BF16_REFINED) or as the FP32 CUDA-core transforms (FP32_REFINED).  max_iter caps the
- * FP64 iterations. */
-typedef enum { LBE_FP64 = 0, LBE_FP32 = 1, LBE_BF16_REFINED = 2, LBE_FP32_REFINED = 3 } lbe_precision;
+ * FP64 iterations.  Their FP64 collision-operator evaluations run in LBE_DF32 arithmetic.
+ * LBE_DF32 (the operator entry points lbe_apply_L and lbe_apply_L_sym only): data in double,
+ * arithmetic in double-float -- each value the unevaluated sum of two floats, about 2^-44
+ * relative per operation, on the FP32 pipes, which this GPU issues at many times its FP64
+ * rate; results agree with LBE_FP64 to about 1e-13 of their scale.  Values below the float
+ * range (|x| < 1e-38, the far tails of f_eq) are flushed to zero. */
+typedef enum {
+    LBE_FP64 = 0,
+    LBE_FP32 = 1,
+    LBE_BF16_REFINED = 2,
+    LBE_FP32_REFINED = 3,
+    LBE_DF32 = 4
+} lbe_precision;
 
 /* Geometry (Sec. 2.4).  dim = 1: plates at x1 = +-1/2, half channel -1/2 <= x1 <= 0 with a
  * specular symmetry plane at x1 = 0, ns sections (ns + 1 nodes), grid_kind 0 = uniform,
@@ -141,8 +152,8 @@ lbe_status lbe_batch_create(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_bat
 lbe_status lbe_batch_run(lbe_batch* b, lbe_result* outs);
 lbe_status lbe_batch_destroy(lbe_batch* b);
 
-/* Collision operator on device data (steps A1-A4).  h_dev: [cells][nv^3] of double (FP64)
- * or float (FP32, BF16_REFINED).  delta_dev: [cells] double, the rarefaction of each cell.
+/* Collision operator on device data (steps A1-A4).  h_dev: [cells][nv^3] of double (FP64,
+ * DF32) or float (FP32, BF16_REFINED).  delta_dev: [cells] double, the rarefaction of each cell.
  * Outputs (same type as h, any may be NULL): Lplus_dev = L+ h, L_dev = L h.
  * G_dev (double [cells][2], may be NULL): G_j = 2 sum_v v_j v3 (L h + n_delta h) dv^3 with
  * n_delta = N delta per cell taken from ndelta_dev (double [cells]; required with G_dev).
@@ -157,9 +168,9 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R,
  * v3, and on plates also even in v2; the discrete operator commutes with those reflections.
  * parity = 1: h odd in v3 (ducts); parity = 2: h odd in v3 and even in v2 (plates).  For
  * such h the result equals lbe_apply_L's up to rounding; for other h it is not defined.
- * LBE_FP64 / LBE_FP32: fast spectral transforms of one direction per reflection orbit
- * (a quarter or half of the directions).  LBE_BF16_REFINED: the operator as a dense
- * (nv^3/4 or nv^3/2)-square matrix at delta = 1, built once per grid from the FP64
+ * LBE_FP64 / LBE_DF32 / LBE_FP32: fast spectral transforms of one direction per reflection
+ * orbit (a quarter or half of the directions).  LBE_BF16_REFINED: the operator as a dense
+ * (nv^3/4 or nv^3/2)-square matrix at delta = 1, built once per grid from the DF32
  * transforms, applied to all cells as one tcgen05 GEMM with bfloat16 hi/lo operands and FP32
  * accumulation (relative error about 1e-5 of the scale); h, L+ h, L h are float.  Needs
  * M >= 8.  Lplus_dev / L_dev may be NULL.  Returns after the work is queued on `stream`

@@ -135,6 +135,15 @@ static lbe_status upload(Ctx* c, T** dst, const std::vector<T>& src, size_t* byt
 }
 
 static std::vector<float> to_f(const std::vector<double>& a) { return std::vector<float>(a.begin(), a.end()); }
+// each double as the float pair (hi, lo) with hi = fl(x), lo = fl(x - hi)
+static std::vector<float> to_df(const std::vector<double>& a) {
+    std::vector<float> o(2 * a.size());
+    for (size_t i = 0; i < a.size(); ++i) {
+        o[2 * i] = (float)a[i];
+        o[2 * i + 1] = (float)(a[i] - (double)o[2 * i]);
+    }
+    return o;
+}
 
 DevTables* get_tables(Ctx* c, int nv, double vmax, int M, double R, lbe_status* st) {
     if (R <= 0) R = default_R(vmax);
@@ -169,6 +178,10 @@ DevTables* get_tables(Ctx* c, int nv, double vmax, int M, double R, lbe_status* 
     if (s == LBE_OK) s = upload(c, &t->mult_f, to_f(h.mult), &b);
     if (s == LBE_OK) s = upload(c, &t->ab_f, to_f(h.ab), &b);
     if (s == LBE_OK) s = upload(c, &t->vel_f, to_f(h.v), &b);
+    if (s == LBE_OK) s = upload(c, &t->feq_x, to_df(h.feq), &b);
+    if (s == LBE_OK) s = upload(c, &t->nu1_x, to_df(h.nu1), &b);
+    if (s == LBE_OK) s = upload(c, &t->mult_x, to_df(h.mult), &b);
+    if (s == LBE_OK) s = upload(c, &t->ab_x, to_df(h.ab), &b);
     t->bytes = b;
     *st = s;
     if (s != LBE_OK) return nullptr;
@@ -303,7 +316,12 @@ lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Arena* ar
         q.max_iter = pb.max_iter;
         q.coef_off = (int)coef.size();
         if (g.dim == 1) {
-            for (auto* v : {&g.fa, &g.fb, &g.fc, &g.x}) coef.insert(coef.end(), v->begin(), v->end());
+            {
+            // the march divides by fa at every node: store 1/fa (block [1/fa | fb | fc | x])
+            std::vector<double> ifa(g.fa.size());
+            for (size_t i = 0; i < ifa.size(); ++i) ifa[i] = g.fa[i] != 0.0 ? 1.0 / g.fa[i] : 0.0;
+            for (auto* v : {&ifa, &g.fb, &g.fc, &g.x}) coef.insert(coef.end(), v->begin(), v->end());
+        }
         } else {
             const int mx = g.nx - 2, my = g.ny - 2;
             for (int p = 0; p < mx; ++p)
@@ -413,8 +431,12 @@ void batch_iterate(Batch& B) {
             range_add_f64(B.base_lp + o, B.inc_lp + o, (double*)(lp + o), nn, s);
             range_add_f64(B.base_lh + o, B.inc_lh + o, (double*)(lh + o), nn, s);
         } else if (sizeof(T) == 4 && B.use_tc) {
-            tc_apply_sym(B.c, B.t, mode, nc, B.delta.as<double>() + c0, (const float*)(h + c0 * n3),
-                         (float*)(lp + c0 * n3), (float*)(lh + c0 * n3), s);
+            // L+ h and the L-moments in one pass; L h itself is not stored
+            const lbe_status ts = tc_apply_sym(B.c, B.t, mode, nc, B.delta.as<double>() + c0, (const float*)(h + c0 * n3),
+                                               (float*)(lp + c0 * n3), nullptr, s, false, B.nd.as<double>() + c0,
+                                               B.G.as<double>() + c0 * 2);
+            if (ts != LBE_OK && B.op_status == LBE_OK) B.op_status = ts;
+            continue;
         } else {
             fsm_cc_apply<T>(t, nc, B.delta.as<double>() + c0, h + c0 * n3, lp + c0 * n3, lh + c0 * n3,
                             B.scratch.p, B.chunk, s, mode);
@@ -430,8 +452,11 @@ void batch_iterate(Batch& B) {
     cudaMemcpyAsync(B.act.p, ordered.data(), na * sizeof(int), cudaMemcpyHostToDevice, s);
     g_h2d += na * sizeof(int);
     int* dact = B.act.as<int>();
-    launch_sweep<T>(t, 1, (int)act1.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact, B.coef.as<double>(), s);
-    launch_sweep<T>(t, 2, (int)act2.size(), 0, lp, hh, B.sjobs.as<SweepJobDev>(), dact + act1.size(),
+    int mc1 = 0, mc2 = 0;  // largest coefficient block of a job (shared-memory staging)
+    for (int j : act1) mc1 = std::max(mc1, 6 * B.sj[j].ncell);
+    for (int j : act2) mc2 = std::max(mc2, 3 * (B.sj[j].nx + B.sj[j].ny));
+    launch_sweep<T>(t, 1, (int)act1.size(), mc1, lp, hh, B.sjobs.as<SweepJobDev>(), dact, B.coef.as<double>(), s);
+    launch_sweep<T>(t, 2, (int)act2.size(), mc2, lp, hh, B.sjobs.as<SweepJobDev>(), dact + act1.size(),
                     B.coef.as<double>(), s);
     for (auto& sp : spans) launch_moments<T>(t, sp.c0, (int)sp.n, hh, B.mom.as<double>(), s);
     launch_sis_update(t, na, B.ijobs.as<SisJobDev>(), dact, B.mom.as<double>(), B.G.as<double>(),
@@ -457,6 +482,8 @@ lbe_status batch_run(Batch& B, int max_steps) {
         else
             batch_iterate<float>(B);
         lbe_status st = cuda_status(B.c, cudaStreamSynchronize(B.s), "iterate");
+        if (st == LBE_OK && B.use_tc) st = tc_check(B.c, B.t);
+        if (st == LBE_OK) st = B.op_status;
         if (st != LBE_OK) return st;
         std::vector<int> keep;
         const double t = host_now();
@@ -555,7 +582,8 @@ lbe_status lbe_destroy(lbe_ctx* ctx) {
         DevTables* t = kv.second.get();
         tc_release(ctx, t);
         for (void* p : {(void*)t->feq_d, (void*)t->nu1_d, (void*)t->mult_d, (void*)t->ab_d, (void*)t->vel_d,
-                        (void*)t->feq_f, (void*)t->nu1_f, (void*)t->mult_f, (void*)t->ab_f, (void*)t->vel_f})
+                        (void*)t->feq_f, (void*)t->nu1_f, (void*)t->mult_f, (void*)t->ab_f, (void*)t->vel_f,
+                        (void*)t->feq_x, (void*)t->nu1_x, (void*)t->mult_x, (void*)t->ab_x})
             if (p) cudaFree(p);
     }
     ctx->tables.clear();
@@ -633,7 +661,7 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_p
     if (M < 2 || M > 64 || (M & (M - 1))) return bad_arg(ctx, "M must be a power of two in [2, 64]");
     if (!(vmax > 0) || R > 2 * vmax) return bad_arg(ctx, "bad vmax or R");
     if (G_dev && !ndelta_dev) return bad_arg(ctx, "G needs ndelta");
-    if (precision != LBE_FP64 && precision != LBE_FP32 && precision != LBE_BF16_REFINED)
+    if (precision != LBE_FP64 && precision != LBE_FP32 && precision != LBE_BF16_REFINED && precision != LBE_DF32)
         return bad_arg(ctx, "bad precision");
     if (cells == 0) return LBE_OK;
     cudaSetDevice(ctx->device);
@@ -648,7 +676,8 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_p
         if (G_dev) lmoments<float>(*t, cells, (const float*)L_dev, (const float*)h_dev, ndelta_dev, G_dev, s);
         return cuda_status(ctx, cudaGetLastError(), "apply_L");
     }
-    const int eb = precision == LBE_FP64 ? 8 : 4;
+    const bool wide = precision == LBE_FP64 || precision == LBE_DF32;  // double data
+    const int eb = wide ? 8 : 4;
     int chunk = 1;
     const size_t scr = fsm_cc_scratch_bytes(*t, cells, eb, &chunk);
     const size_t vol = (size_t)cells * nv * nv * nv * eb;
@@ -657,9 +686,12 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_p
     if ((st = arena_reserve(ctx, ctx->apply_arena, need)) != LBE_OK) return st;
     void* p = arena_take(ctx->apply_arena, scr);
     void* Lo = L_dev ? L_dev : ((G_dev) ? arena_take(ctx->apply_arena, vol) : nullptr);
-    if (precision == LBE_FP64) {
-        st = fsm_cc_apply<double>(*t, cells, delta_dev, (const double*)h_dev, (double*)Lplus_dev, (double*)Lo, p,
-                                  chunk, s);
+    if (wide) {
+        st = precision == LBE_FP64
+                 ? fsm_cc_apply<double>(*t, cells, delta_dev, (const double*)h_dev, (double*)Lplus_dev, (double*)Lo,
+                                        p, chunk, s)
+                 : fsm_df_apply(*t, cells, delta_dev, (const double*)h_dev, (double*)Lplus_dev, (double*)Lo, p,
+                                chunk, s);
         if (G_dev) lmoments<double>(*t, cells, (const double*)Lo, (const double*)h_dev, ndelta_dev, G_dev, s);
     } else {
         st = fsm_cc_apply<float>(*t, cells, delta_dev, (const float*)h_dev, (float*)Lplus_dev, (float*)Lo, p,
@@ -679,15 +711,15 @@ lbe_status lbe_apply_L_sym(lbe_ctx* ctx, int nv, double vmax, int M, double R, l
     if (nv != 8 && nv != 16 && nv != 24 && nv != 32) return bad_arg(ctx, "nv must be 8, 16, 24 or 32");
     if (M < 8 || M > 64 || (M & (M - 1))) return bad_arg(ctx, "M must be a power of two in [8, 64]");
     if (!(vmax > 0) || R > 2 * vmax) return bad_arg(ctx, "bad vmax or R");
-    if (precision != LBE_FP64 && precision != LBE_FP32 && precision != LBE_BF16_REFINED)
-        return bad_arg(ctx, "precision must be FP64, FP32 or BF16_REFINED");
+    if (precision != LBE_FP64 && precision != LBE_FP32 && precision != LBE_BF16_REFINED && precision != LBE_DF32)
+        return bad_arg(ctx, "precision must be FP64, FP32, DF32 or BF16_REFINED");
     if (cells == 0) return LBE_OK;
     cudaSetDevice(ctx->device);
     lbe_status st;
     DevTables* t = get_tables(ctx, nv, vmax, M, R, &st);
     if (!t) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const int eb = precision == LBE_FP64 ? 8 : 4;
+    const int eb = (precision == LBE_FP64 || precision == LBE_DF32) ? 8 : 4;
     const size_t vol = (size_t)cells * nv * nv * nv * eb;
     int chunk = 1;
     const size_t scr = precision == LBE_BF16_REFINED ? 0 : fsm_cc_scratch_bytes(*t, cells, eb, &chunk);
@@ -701,6 +733,8 @@ lbe_status lbe_apply_L_sym(lbe_ctx* ctx, int nv, double vmax, int M, double R, l
     if (precision == LBE_FP64)
         st = fsm_cc_apply<double>(*t, cells, delta_dev, (const double*)h_dev, (double*)lp, (double*)lo, p, chunk, s,
                                   parity);
+    else if (precision == LBE_DF32)
+        st = fsm_df_apply(*t, cells, delta_dev, (const double*)h_dev, (double*)lp, (double*)lo, p, chunk, s, parity);
     else
         st = fsm_cc_apply<float>(*t, cells, delta_dev, (const float*)h_dev, (float*)lp, (float*)lo, p, chunk, s,
                                  parity);
@@ -747,7 +781,8 @@ lbe_status lbe_sweep(lbe_ctx* ctx, const lbe_problem* pb, const void* rhs_dev, v
                              (double*)dc, s);
         if (mom_dev) launch_moments<double>(*t, 0, g.cells, (const double*)h_dev, mom_dev, s);
     } else {
-        launch_sweep<float>(*t, g.dim, 1, 0, (const float*)rhs_dev, (float*)h_dev, (SweepJobDev*)dj, nullptr,
+        launch_sweep<float>(*t, g.dim, 1, (int)coef.size(), (const float*)rhs_dev, (float*)h_dev, (SweepJobDev*)dj,
+                            nullptr,
                             (double*)dc, s);
         if (mom_dev) launch_moments<float>(*t, 0, g.cells, (const float*)h_dev, mom_dev, s);
     }

@@ -6,9 +6,53 @@
 
 namespace lbe {
 
+// Double-float: the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi) / 2, about
+// 2^-44 relative per operation -- FP64-class accuracy from the FP32 pipes, which on this GPU
+// issue many times the FP64 rate.  Built from the error-free transformations TwoSum (Knuth),
+// Fast2Sum (Dekker; |a| >= |b|) and the FMA form of TwoProduct; every step is an explicitly
+// rounded intrinsic so that no contraction or reassociation can remove an error term.
+// Addition is the cheap variant (error relative to |a| + |b|), which suits transforms and
+// sums whose error is measured against the size of their inputs.
+struct dfloat {
+    float hi, lo;
+    dfloat() = default;
+    __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ dfloat(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+    __host__ __device__ constexpr dfloat(int x) : hi((float)x), lo(0.f) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+struct dfloat2 {
+    dfloat x, y;
+};
+
+__device__ __forceinline__ dfloat df_fast2sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfloat df_twosum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return dfloat(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+    const dfloat s = df_twosum(a.hi, b.hi);
+    return df_fast2sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast2sum(p, e);
+}
+__device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
+
 template <typename T> struct Cplx;
 template <> struct Cplx<double> { using type = double2; };
 template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<dfloat> { using type = dfloat2; };
 template <typename T> using cplx_t = typename Cplx<T>::type;
 
 // Twiddles W^m = exp(-2 pi i m / N) for N in {8, 16, 24, 32}, slot = index of N.
@@ -16,6 +60,7 @@ template <typename T> using cplx_t = typename Cplx<T>::type;
 // (see init_twiddles in fsm_cc.cu).
 static __constant__ double2 c_tw_d[4][32];
 static __constant__ float2 c_tw_f[4][32];
+static __constant__ dfloat2 c_tw_df[4][32];
 
 template <int N> struct TwSlot;
 template <> struct TwSlot<8> { static constexpr int v = 0; };
@@ -32,6 +77,10 @@ template <> __device__ __forceinline__ float2 tw<float, 8>(int m) { return c_tw_
 template <> __device__ __forceinline__ float2 tw<float, 16>(int m) { return c_tw_f[1][m]; }
 template <> __device__ __forceinline__ float2 tw<float, 24>(int m) { return c_tw_f[2][m]; }
 template <> __device__ __forceinline__ float2 tw<float, 32>(int m) { return c_tw_f[3][m]; }
+template <> __device__ __forceinline__ dfloat2 tw<dfloat, 8>(int m) { return c_tw_df[0][m]; }
+template <> __device__ __forceinline__ dfloat2 tw<dfloat, 16>(int m) { return c_tw_df[1][m]; }
+template <> __device__ __forceinline__ dfloat2 tw<dfloat, 24>(int m) { return c_tw_df[2][m]; }
+template <> __device__ __forceinline__ dfloat2 tw<dfloat, 32>(int m) { return c_tw_df[3][m]; }
 
 __host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }

@@ -16,6 +16,7 @@
 // across lanes), sums the directions over four warps and writes the outputs.  Every lane
 // owns one 1D line in registers (dft_line in common.cuh).
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "lbe_internal.h"
@@ -25,15 +26,18 @@ namespace lbe {
 void init_twiddles_cc() {
     double2 hd[4][32];
     float2 hf[4][32];
+    dfloat2 hx[4][32];
     const int ns[4] = {8, 16, 24, 32};
     for (int s = 0; s < 4; ++s)
         for (int m = 0; m < 32; ++m) {
             double a = -2.0 * M_PI * (m % ns[s]) / ns[s];
             hd[s][m] = make_double2(std::cos(a), std::sin(a));
             hf[s][m] = make_float2((float)std::cos(a), (float)std::sin(a));
+            hx[s][m] = dfloat2{dfloat(std::cos(a)), dfloat(std::sin(a))};
         }
     cudaMemcpyToSymbol(c_tw_d, hd, sizeof(hd));
     cudaMemcpyToSymbol(c_tw_f, hf, sizeof(hf));
+    cudaMemcpyToSymbol(c_tw_df, hx, sizeof(hx));
 }
 
 namespace {
@@ -41,6 +45,7 @@ namespace {
 template <typename T> __device__ __forceinline__ cplx_t<T> mk(T a, T b);
 template <> __device__ __forceinline__ double2 mk<double>(double a, double b) { return make_double2(a, b); }
 template <> __device__ __forceinline__ float2 mk<float>(float a, float b) { return make_float2(a, b); }
+template <> __device__ __forceinline__ dfloat2 mk<dfloat>(dfloat a, dfloat b) { return dfloat2{a, b}; }
 
 // Line L of a batch of volumes along AXIS: first element offset and stride.
 template <int N, int AXIS>
@@ -88,8 +93,8 @@ __global__ void __launch_bounds__(128) k_fwd(const T* __restrict__ hin, cplx_t<T
 // memory so that global loads and stores are coalesced rows.  One warp per slab.
 //   REAL_IN:  forward transform of a real plane of h (A1, first two axes)
 //   MULT:     inverse transform of mult_p * H (A2, first two axes of direction p's inverse)
-template <typename T, int N, bool INV, bool REAL_IN, bool MULT, int WPB>
-__global__ void __launch_bounds__(32 * WPB) k_slab2d(const T* __restrict__ hin, const cplx_t<T>* __restrict__ Hin,
+template <typename T, int N, bool INV, bool REAL_IN, bool MULT, int WPB, typename TIN = T>
+__global__ void __launch_bounds__(32 * WPB) k_slab2d(const TIN* __restrict__ hin, const cplx_t<T>* __restrict__ Hin,
                                                      const cplx_t<T>* __restrict__ mult,
                                                      cplx_t<T>* __restrict__ out, long nslabs, int P,
                                                      int loss_slot) {
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(32 * WPB) k_slab2d(const T* __restrict__ hin, 
     for (int idx = lane; idx < N2; idx += 32) {
         cplx_t<T> z;
         if (REAL_IN) {
-            z.x = hin[ibase + idx];
+            z.x = T(hin[ibase + idx]);
             z.y = T(0);
         } else {
             z = Hin[ibase + idx];
@@ -160,11 +165,11 @@ __global__ void __launch_bounds__(32 * WPB) k_slab2d(const T* __restrict__ hin, 
 // p = w, w+4, ...; the partial sums meet in shared memory in a fixed order (A2-A3).
 // With RAW, the representatives' gain goes to Lplus and the loss convolution to Lout
 // unassembled, for k_sym to complete.  Y holds M directions and the loss in slot M.
-template <typename T, int N, bool RAW>
+template <typename T, int N, bool RAW, typename TIN = T>
 __global__ void __launch_bounds__(128) k_inv_last4(const cplx_t<T>* __restrict__ Y,
                                                    const cplx_t<T>* __restrict__ ab,
                                                    const T* __restrict__ feq, const T* __restrict__ nu1,
-                                                   const T* __restrict__ h, const double* __restrict__ delta,
+                                                   const TIN* __restrict__ h, const double* __restrict__ delta,
                                                    T* __restrict__ Lplus, T* __restrict__ Lout, int ncell,
                                                    int M) {
     constexpr int N2 = N * N, N3 = N * N * N, TILES = N2 / 32;
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(128) k_inv_last4(const cplx_t<T>* __restrict__
         }
         const T lp = d * sum;
         if (Lplus) Lplus[idx] = lp;
-        if (Lout) Lout[idx] = lp - d * nu1[j * N2 + r] * h[idx];
+        if (Lout) Lout[idx] = lp - d * nu1[j * N2 + r] * T(h[idx]);
     }
 }
 
@@ -233,10 +238,10 @@ __global__ void __launch_bounds__(128) k_inv_last4(const cplx_t<T>* __restrict__
 // closed under them, so the sum over all directions equals the sum over one representative
 // per orbit, G, symmetrised: gain(v) = sum_g s_g G(g v) over g in {1, R3} (MODE 1) or
 // {1, R2, R3, R2R3} (MODE 2, s2 = +1).  One thread per orbit of velocity points.
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, typename TIN = T>
 __global__ void __launch_bounds__(128) k_sym(T* __restrict__ Lplus, T* __restrict__ Lout,
                                              const T* __restrict__ feq, const T* __restrict__ nu1,
-                                             const T* __restrict__ h, const double* __restrict__ delta,
+                                             const TIN* __restrict__ h, const double* __restrict__ delta,
                                              int ncell, bool want_lplus, bool want_l) {
     constexpr int N2 = N * N, N3 = N2 * N, H = N / 2;
     constexpr int per_cell = MODE == 2 ? N * H * H : N * N * H;
@@ -280,7 +285,7 @@ __global__ void __launch_bounds__(128) k_sym(T* __restrict__ Lplus, T* __restric
         const long g = idx[k];
         const int v = (int)(g - cell * N3);
         const T lp = d * (sgn[k] * gs - feq[v] * Lout[g]);
-        const T hv = h[g];
+        const T hv = T(h[g]);
         if (want_lplus) Lplus[g] = lp;
         if (want_l) Lout[g] = lp - d * nu1[v] * hv;
     }
@@ -336,24 +341,30 @@ __global__ void __launch_bounds__(256) k_lmoments(const T* __restrict__ Lh, cons
 
 inline unsigned nblk(long n, int b) { return (unsigned)((n + b - 1) / b); }
 
-template <typename T, int N>
-void run_fsm(const DevTables& t, int cells, const double* delta, const T* h, T* Lplus, T* Lout,
+template <typename T, int N, typename TH = T>
+void run_fsm(const DevTables& t, int cells, const double* delta, const TH* h, T* Lplus, T* Lout,
              cplx_t<T>* Hbuf, cplx_t<T>* Ybuf, int chunk, int mode, cudaStream_t s) {
     constexpr int B = 128;
     constexpr int WPB = (sizeof(T) == 8 && N == 32) ? 2 : 4;
     const long nl = (long)cells * N * N;
     const long ns = (long)cells * N;
-    k_slab2d<T, N, false, true, false, WPB><<<nblk(ns, WPB), 32 * WPB, 0, s>>>(h, nullptr, nullptr, Hbuf, ns, 1, 0);
+    k_slab2d<T, N, false, true, false, WPB, TH><<<nblk(ns, WPB), 32 * WPB, 0, s>>>(h, nullptr, nullptr, Hbuf, ns, 1,
+                                                                                 0);
     k_fwd<T, N, 0, false><<<nblk(nl, B), B, 0, s>>>(nullptr, Hbuf, nl);
     const cplx_t<T>* mult;
     const cplx_t<T>* ab;
     const T* feq;
     const T* nu1;
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (std::is_same<T, double>::value) {
         mult = (const cplx_t<T>*)t.mult_d;
         ab = (const cplx_t<T>*)t.ab_d;
         feq = (const T*)t.feq_d;
         nu1 = (const T*)t.nu1_d;
+    } else if constexpr (std::is_same<T, dfloat>::value) {
+        mult = (const cplx_t<T>*)t.mult_x;
+        ab = (const cplx_t<T>*)t.ab_x;
+        feq = (const T*)t.feq_x;
+        nu1 = (const T*)t.nu1_x;
     } else {
         mult = (const cplx_t<T>*)t.mult_f;
         ab = (const cplx_t<T>*)t.ab_f;
@@ -369,24 +380,24 @@ void run_fsm(const DevTables& t, int cells, const double* delta, const T* h, T* 
         g_launches += 2;
         const int cc = (cells - c0 < chunk) ? cells - c0 : chunk;
         const long nsl = (long)cc * P * N;
-        k_slab2d<T, N, true, false, true, WPB><<<nblk(nsl, WPB), 32 * WPB, 0, s>>>(nullptr, Hbuf + c0 * N3, mult,
+        k_slab2d<T, N, true, false, true, WPB, T><<<nblk(nsl, WPB), 32 * WPB, 0, s>>>(nullptr, Hbuf + c0 * N3, mult,
                                                                                   Ybuf, nsl, P, t.M);
         const long blocks = (long)cc * (N * N / 32);
         if (mode == 0) {
-            k_inv_last4<T, N, false><<<(unsigned)blocks, 128, 0, s>>>(Ybuf, ab, feq, nu1, h + c0 * N3, delta + c0,
+            k_inv_last4<T, N, false, TH><<<(unsigned)blocks, 128, 0, s>>>(Ybuf, ab, feq, nu1, h + c0 * N3, delta + c0,
                                                                     Lplus ? Lplus + c0 * N3 : nullptr,
                                                                     Lout ? Lout + c0 * N3 : nullptr, cc, Muse);
         } else {
             // raw gain of the representatives and the loss convolution, then symmetrise
-            k_inv_last4<T, N, true><<<(unsigned)blocks, 128, 0, s>>>(Ybuf, ab, feq, nu1, h + c0 * N3, delta + c0,
+            k_inv_last4<T, N, true, TH><<<(unsigned)blocks, 128, 0, s>>>(Ybuf, ab, feq, nu1, h + c0 * N3, delta + c0,
                                                                    Lplus + c0 * N3, Lout + c0 * N3, cc, Muse);
             g_launches += 1;
             const long nt = (long)cc * (mode == 2 ? N * (N / 2) * (N / 2) : N * N * (N / 2));
             if (mode == 2)
-                k_sym<T, N, 2><<<nblk(nt, 128), 128, 0, s>>>(Lplus + c0 * N3, Lout + c0 * N3, feq, nu1, h + c0 * N3,
+                k_sym<T, N, 2, TH><<<nblk(nt, 128), 128, 0, s>>>(Lplus + c0 * N3, Lout + c0 * N3, feq, nu1, h + c0 * N3,
                                                              delta + c0, cc, true, true);
             else
-                k_sym<T, N, 1><<<nblk(nt, 128), 128, 0, s>>>(Lplus + c0 * N3, Lout + c0 * N3, feq, nu1, h + c0 * N3,
+                k_sym<T, N, 1, TH><<<nblk(nt, 128), 128, 0, s>>>(Lplus + c0 * N3, Lout + c0 * N3, feq, nu1, h + c0 * N3,
                                                              delta + c0, cc, true, true);
         }
     }
@@ -424,6 +435,44 @@ lbe_status fsm_cc_apply(const DevTables& t, int cells, const double* delta, cons
         case 32: run_fsm<T, 32>(t, cells, delta, h, Lplus, Lout, Hbuf, Ybuf, chunk, mode, s); break;
         default: return LBE_UNSUPPORTED;
     }
+    return LBE_OK;
+}
+
+namespace {
+// in place: the 8 bytes of a double-float become the double hi + lo
+__global__ void k_df_to_double(double* __restrict__ x, long n) {
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const dfloat v = reinterpret_cast<const dfloat*>(x)[k];
+        x[k] = (double)v;
+    }
+}
+}  // namespace
+
+// The operator in double-float arithmetic on double data: h is read as double and rounded to
+// a double-float on load; Lplus and Lout (double arrays) first receive double-floats, which
+// a last pass widens in place.  Scratch as for the double path (8-byte elements).
+lbe_status fsm_df_apply(const DevTables& t, int cells, const double* delta, const double* h, double* Lplus,
+                        double* Lout, void* scratch, int chunk, cudaStream_t s, int mode) {
+    const long n3 = (long)t.nv * t.nv * t.nv;
+    if (mode == 2 && t.sym_reps2 == 0) mode = t.sym_reps1 ? 1 : 0;
+    if (mode == 1 && t.sym_reps1 == 0) mode = 0;
+    if (mode != 0 && (!Lplus || !Lout)) return LBE_INTERNAL;
+    if (!t.mult_x) return LBE_INTERNAL;
+    auto* Hbuf = (dfloat2*)scratch;
+    dfloat2* Ybuf = Hbuf + n3 * cells;
+    auto* lp = reinterpret_cast<dfloat*>(Lplus);
+    auto* lo = reinterpret_cast<dfloat*>(Lout);
+    switch (t.nv) {
+        case 8: run_fsm<dfloat, 8, double>(t, cells, delta, h, lp, lo, Hbuf, Ybuf, chunk, mode, s); break;
+        case 16: run_fsm<dfloat, 16, double>(t, cells, delta, h, lp, lo, Hbuf, Ybuf, chunk, mode, s); break;
+        case 24: run_fsm<dfloat, 24, double>(t, cells, delta, h, lp, lo, Hbuf, Ybuf, chunk, mode, s); break;
+        case 32: run_fsm<dfloat, 32, double>(t, cells, delta, h, lp, lo, Hbuf, Ybuf, chunk, mode, s); break;
+        default: return LBE_UNSUPPORTED;
+    }
+    const long n = (long)cells * n3;
+    if (Lplus) k_df_to_double<<<608, 256, 0, s>>>(Lplus, n);
+    if (Lout) k_df_to_double<<<608, 256, 0, s>>>(Lout, n);
+    g_launches += (Lplus ? 1 : 0) + (Lout ? 1 : 0);
     return LBE_OK;
 }
 

@@ -5,8 +5,8 @@
 // set is closed under them).  On that subspace h is fixed by its values at one point per
 // orbit of velocity points -- Nr = nv^3/4 (plates) or nv^3/2 (ducts) values -- and the
 // operator (at delta = 1) is an Nr x Nr matrix A.  A is built once per velocity grid by
-// applying the FP64 fast-spectral operator to the Nr symmetric basis functions, so it is the
-// same discrete operator.  Applying it to every cell at once is the GEMM
+// applying the fast-spectral operator in double-float arithmetic (FP64-class) to the Nr
+// symmetric basis functions, so it is the same discrete operator.  Applying it to every cell at once is the GEMM
 //     Y[c][q] = sum_q' A[q][q'] x_c[q'],     L+ h_c = delta_c * expand(Y[c]),
 // run with A = A_hi + A_lo and x = x_hi + x_lo split into bfloat16 and the three products
 // A_hi x_hi + A_lo x_hi + A_hi x_lo accumulated in FP32 tensor memory (about 2^-16 relative).
@@ -26,6 +26,7 @@
 #include <mutex>
 #include <vector>
 
+#include "common.cuh"
 #include "lbe_internal.h"
 #include "sweep.h"
 
@@ -33,7 +34,18 @@ namespace lbe {
 
 namespace {
 
-constexpr int kBM = 128, kBK = 64, kStages = 4;
+constexpr int kBM = 128, kBK = 32;
+constexpr int kSmemMax = 232448;  // opt-in dynamic shared memory per block
+constexpr int kTmemCols = 256;    // accumulator columns allocated (power of two >= BN)
+
+// Pipeline depth for a BN-wide tile: as many 32-deep K stages (A_hi, A_lo, x_hi, x_lo) as
+// shared memory holds (max 8).
+template <int BN>
+struct GemmCfg {
+    static constexpr int STAGE = 2 * kBM * kBK * 2 + 2 * BN * kBK * 2;
+    static constexpr int STAGES = (kSmemMax - 1280) / STAGE < 8 ? (kSmemMax - 1280) / STAGE : 8;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 + 256;
+};
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -93,14 +105,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 32 bf16), 8-row groups
+// 512 B apart.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)(16 >> 4) << 16;    // leading byte offset (unused by swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-    d |= (uint64_t)1 << 46;            // descriptor version
-    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    d |= (uint64_t)(16 >> 4) << 16;   // leading byte offset (unused by swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;           // descriptor version
+    d |= (uint64_t)4 << 61;           // 64-byte swizzle
     return d;
 }
 
@@ -109,13 +122,17 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Y[col][row] = sum over segments s and k of A_s[row][k] * B_s[col][k].
+// Y_z[col][row] = sum over k in K-split z of (A_hi + A_lo)[row][k] (x_hi + x_lo)[col][k], without
+// the A_lo x_lo term.  A stage holds one 32-deep K slice of all four operands, so A_hi is staged
+// once for its two products: per stage 16 KB of A and 2 BN x 64 B of x feed 3 x 2 x 128 x BN x 32
+// flops.
 template <int BN>
 __global__ void __launch_bounds__(128, 1)
-    k_dense_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
-                 const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1, int Mrows,
-                 int ncols, int K, int nseg, uint32_t seg_codes, float* __restrict__ Y, int* __restrict__ err) {
-    constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2, STAGE = A_BYTES + B_BYTES;
+    k_dense_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                 const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl, int Mrows,
+                 int ncols, int K, float* __restrict__ Y, int* __restrict__ err) {
+    constexpr int A_BYTES = kBM * kBK * 2, X_BYTES = BN * kBK * 2, STAGE = 2 * A_BYTES + 2 * X_BYTES;
+    constexpr int kStages = GemmCfg<BN>::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(base + kStages * STAGE);
@@ -124,7 +141,10 @@ __global__ void __launch_bounds__(128, 1)
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int col0 = blockIdx.x * BN, row0 = blockIdx.y * kBM;
-    const int ktseg = K / kBK, KT = nseg * ktseg;
+    const int KTall = K / kBK, ksplit = gridDim.z;
+    const int kt0 = (int)((long)KTall * blockIdx.z / ksplit), kt1 = (int)((long)KTall * (blockIdx.z + 1) / ksplit);
+    const int KT = kt1 - kt0;
+    float* Yz = Y + (size_t)blockIdx.z * ncols * Mrows;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -136,7 +156,7 @@ __global__ void __launch_bounds__(128, 1)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(BN));
+                     "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -149,12 +169,14 @@ __global__ void __launch_bounds__(128, 1)
     if (tid == 0) failed = 0;
 
     if (tid == 0) {
-        auto issue = [&](int kt, int s) {
-            const int seg = kt / ktseg, kk = kt % ktseg;
-            const uint32_t code = (seg_codes >> (2 * seg)) & 3u;  // bit 0: A lo, bit 1: B lo
+        auto issue = [&](int kt, int s) {  // slice kt of this CTA's K range into stage s
+            const int x = (kt0 + kt) * kBK;
+            uint8_t* st = base + s * STAGE;
             mbar_expect_tx(&full[s], STAGE);
-            tma_load_2d(base + s * STAGE, (code & 1u) ? &tmA1 : &tmA0, kk * kBK, row0, &full[s]);
-            tma_load_2d(base + s * STAGE + A_BYTES, (code & 2u) ? &tmB1 : &tmB0, kk * kBK, col0, &full[s]);
+            tma_load_2d(st, &tmAh, x, row0, &full[s]);
+            tma_load_2d(st + A_BYTES, &tmAl, x, row0, &full[s]);
+            tma_load_2d(st + 2 * A_BYTES, &tmXh, x, col0, &full[s]);
+            tma_load_2d(st + 2 * A_BYTES + X_BYTES, &tmXl, x, col0, &full[s]);
         };
         int issued = 0;
         for (int s = 0; s < kStages && s < KT; ++s) issue(s, s), ++issued;
@@ -168,10 +190,14 @@ __global__ void __launch_bounds__(128, 1)
             }
             ++consumed;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(base + s * STAGE), b0 = a0 + A_BYTES;
+            const uint32_t ah = smem_u32(base + s * STAGE), al = ah + A_BYTES, xh = al + A_BYTES, xl = xh + X_BYTES;
 #pragma unroll
-            for (int k = 0; k < kBK / 16; ++k)
-                mma_bf16(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), IDESC, (kt > 0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < kBK / 16; ++k) {
+                const uint32_t o = 32 * k;  // 16 bf16 along K inside the 64-byte swizzled row
+                mma_bf16(tmem, sdesc_sw64(ah + o), sdesc_sw64(xh + o), IDESC, (kt > 0 || k > 0) ? 1u : 0u);
+                mma_bf16(tmem, sdesc_sw64(al + o), sdesc_sw64(xh + o), IDESC, 1u);
+                mma_bf16(tmem, sdesc_sw64(ah + o), sdesc_sw64(xl + o), IDESC, 1u);
+            }
             mma_commit(&empty[s]);
             const int nk = kt - 1 + kStages;  // refill the slot of the previous stage
             if (kt >= 1 && nk < KT) {
@@ -196,7 +222,7 @@ __global__ void __launch_bounds__(128, 1)
     const bool got = mbar_wait(done, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
-    if (got && !failed) {
+    if (got && !failed && KT > 0) {
         const int row = row0 + warp * 32 + lane;
         for (int c0 = 0; c0 < BN; c0 += 32) {
             float v[32];
@@ -205,16 +231,16 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int col = col0 + c0 + j;
-                    if (col < ncols) Y[(long)col * Mrows + row] = v[j];
+                    if (col < ncols) Yz[(long)col * Mrows + row] = v[j];
                 }
             }
         }
-    } else if (tid == 0) {
+    } else if (tid == 0 && KT > 0) {
         atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 // ---- parity-subspace index maps -----------------------------------------------------------
@@ -264,7 +290,7 @@ __global__ void k_gather_split(const float* __restrict__ h, __nv_bfloat16* __res
 // L+ h = delta Y expanded with the orbit signs; L h = L+ h - delta nu h
 __global__ void k_expand(const float* __restrict__ Y, const float* __restrict__ h, const float* __restrict__ nu1,
                          const double* __restrict__ delta, float* __restrict__ Lplus, float* __restrict__ Lout,
-                         int cells, int nv, int nr, int mode) {
+                         int cells, int nv, int nr, int mode, int ks) {
     const long n3 = (long)nv * nv * nv;
     const long total = (long)cells * n3;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
@@ -273,10 +299,82 @@ __global__ void k_expand(const float* __restrict__ Y, const float* __restrict__ 
         float sg;
         const int q = orbit_of(v, nv, mode, &sg);
         const float d = (float)delta[c];
-        const float lp = d * sg * Y[c * nr + q];
+        float y = Y[c * nr + q];
+        for (int z = 1; z < ks; ++z) y += Y[((long)z * cells + c) * nr + q];
+        const float lp = d * sg * y;
         if (Lplus) Lplus[k] = lp;
         if (Lout) Lout[k] = lp - d * nu1[v] * h[k];
     }
+}
+
+// k_expand fused with the L-moments of an SIS iteration: one block of 8 NV threads per
+// cell stages the cell's Nr outputs in shared memory, writes L+ h (and L h when asked for),
+// and sums G_j = 2 sum_v v_j v3 (L h + N delta h) dv^3 (j = 1, 2) without storing L h.
+template <int NV, int MODE>
+__global__ void __launch_bounds__(8 * NV) k_expand_g(const float* __restrict__ Y, const float* __restrict__ h,
+                                                     const float* __restrict__ nu1, const float* __restrict__ vel,
+                                                     const double* __restrict__ delta, const double* __restrict__ nd,
+                                                     float* __restrict__ Lplus, float* __restrict__ Lout,
+                                                     double* __restrict__ G, int nr, double dv3, int cells, int ks) {
+    extern __shared__ float sY[];
+    __shared__ double red[32 * 2];
+    constexpr int H = NV / 2;
+    constexpr long n3 = (long)NV * NV * NV;
+    const long c = blockIdx.x;
+    for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+        float y = Y[c * nr + q];
+        for (int z = 1; z < ks; ++z) y += Y[((long)z * cells + c) * nr + q];
+        sY[q] = y;
+    }
+    __syncthreads();
+    const float d = (float)delta[c], ndc = (float)nd[c];
+    const int i3 = threadIdx.x % NV, r0 = threadIdx.x / NV;
+    const int j3 = i3 < H ? i3 : NV - 1 - i3;
+    const float s3 = i3 < H ? d : -d;
+    const float v3 = vel[i3];
+    float a0 = 0.f, c0 = 0.f, a1 = 0.f, c1 = 0.f;  // compensated sums of v1 t and v2 t
+    auto kahan = [](float& sum, float& comp, float x) {
+        const float y = x - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    };
+    for (int i1 = 0; i1 < NV; ++i1) {
+        const float v1 = vel[i1];
+#pragma unroll
+        for (int k = 0; k < NV / 8; ++k) {
+            const int i2 = r0 + 8 * k;
+            const int q = MODE == 2 ? (i1 * H + (i2 < H ? i2 : NV - 1 - i2)) * H + j3 : (i1 * NV + i2) * H + j3;
+            const int v = (i1 * NV + i2) * NV + i3;
+            const long g = c * n3 + v;
+            const float lp = s3 * sY[q];
+            Lplus[g] = lp;
+            const float hv = h[g];
+            const float lo = lp - d * nu1[v] * hv;
+            if (Lout) Lout[g] = lo;
+            const float t = (lo + ndc * hv) * v3;
+            kahan(a0, c0, v1 * t);
+            kahan(a1, c1, vel[i2] * t);
+        }
+    }
+    double sm[2] = {(double)a0 - (double)c0, (double)a1 - (double)c1};
+    block_reduce<2>(sm, red);
+    if (threadIdx.x == 0) {
+        G[2 * c + 0] = 2.0 * sm[0] * dv3;
+        G[2 * c + 1] = 2.0 * sm[1] * dv3;
+    }
+}
+
+template <int NV, int MODE>
+void launch_expand_g(int cells, const float* Y, const float* h, const float* nu1, const float* vel,
+                     const double* delta, const double* nd, float* Lplus, float* Lout, double* G, int nr, double dv3,
+                     int ks, cudaStream_t s) {
+    static std::once_flag once;
+    const int smem = nr * 4;
+    std::call_once(once, [smem] {
+        cudaFuncSetAttribute(k_expand_g<NV, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+    k_expand_g<NV, MODE><<<cells, 8 * NV, smem, s>>>(Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nr, dv3, cells, ks);
 }
 
 // symmetric basis functions e_q for q in [q0, q0 + nb): value sign at each orbit point
@@ -330,12 +428,40 @@ bool make_map(CUtensorMap* m, const void* ptr, long rows, long cols, int box_row
     cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-constexpr int kBN = 256;
-constexpr size_t kGemmSmem = (size_t)kStages * (kBM * kBK * 2 + kBN * kBK * 2) + 1024 + 256;
+// Column tile for a call: the cells split evenly over ceil(cells / 256) tiles, rounded up to
+// the next instantiated width (808 cells: 4 x 224 = 896 columns instead of 4 x 256).
+constexpr int kWidths[] = {64, 128, 160, 192, 224, 256};
+int pick_bn(int cells) {
+    const int nct = (cells + 255) / 256, per = (cells + nct - 1) / nct;
+    for (int w : kWidths)
+        if (w >= per) return w;
+    return 256;
+}
+
+template <int BN>
+void launch_gemm(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1, int nr,
+                 int cells, int ksplit, float* Y, int* err, cudaStream_t s) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_dense_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GemmCfg<BN>::SMEM);
+    });
+    dim3 grid((cells + BN - 1) / BN, nr / kBM, ksplit);
+    k_dense_gemm<BN><<<grid, 128, GemmCfg<BN>::SMEM, s>>>(a0, a1, b0, b1, nr, cells, nr, Y, err);
+}
+
+// K-split for launches with fewer tiles than SMs: the partial products land in separate
+// slices of Y and the expand kernels add them in a fixed order.
+int pick_ksplit(int cells, int bn, int nr) {
+    const int ctas = (cells + bn - 1) / bn * (nr / kBM);
+    int ks = ctas >= 152 ? 1 : 152 / ctas;
+    ks = ks < 1 ? 1 : (ks > 4 ? 4 : ks);
+    while (ks > 1 && nr / kBK < 4 * ks) --ks;
+    return ks;
+}
 
 }  // namespace
 
@@ -353,7 +479,8 @@ struct TcOperands {
     DenseOp op[3];  // by mode
     // per-call workspace (grow-only)
     Arena ws;
-    int* err = nullptr;
+    int* err_dev = nullptr;   // bounded-wait failure word of the GEMM (sticky until read)
+    int* err_host = nullptr;  // pinned copy, valid after the stream's next synchronisation
 };
 
 static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaStream_t s) {
@@ -386,7 +513,7 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
         for (int q0 = 0; q0 < nr && st == LBE_OK; q0 += nb) {
             const int b = std::min(nb, nr - q0);
             k_basis<<<1024, 256, 0, s>>>((double*)hb, q0, b, nv, nr, mode);
-            st = fsm_cc_apply<double>(*t, b, (const double*)dl, (const double*)hb, (double*)lp, (double*)lo, sc, chunk,
+            st = fsm_df_apply(*t, b, (const double*)dl, (const double*)hb, (double*)lp, (double*)lo, sc, chunk,
                                       s, mode);
             k_store_columns<<<1024, 256, 0, s>>>((const double*)lp, d.Ah, d.Al, q0, b, nv, nr, mode);
             g_launches += 2;
@@ -407,8 +534,10 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
 }
 
 // L+ h and L h on the parity subspace with the dense tensor-core operator (float in / out).
+// sync = false leaves the stream running: the GEMM's failure word is copied to pinned host
+// memory behind it and tc_check reads it after the caller's own synchronisation.
 lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h, float* Lplus,
-                        float* Lout, cudaStream_t s) {
+                        float* Lout, cudaStream_t s, bool sync, const double* nd, double* G) {
     if (mode != 1 && mode != 2) return LBE_BAD_ARG;
     if (cells <= 0) return LBE_OK;
     if (!t->tc) t->tc = new TcOperands();
@@ -417,46 +546,71 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     DenseOp& d = T.op[mode];
     lbe_status st;
     if (!d.Ah && (st = build_dense(c, t, d, mode, s)) != LBE_OK) return st;
+    if (!T.err_dev) {
+        if ((st = dev_alloc(c, (void**)&T.err_dev, 256)) != LBE_OK) return st;
+        if (cudaMallocHost((void**)&T.err_host, sizeof(int)) != cudaSuccess) {
+            c->last_error = "pinned host word for the tensor-core operator";
+            return LBE_OOM;
+        }
+        *T.err_host = 0;
+        cudaMemsetAsync(T.err_dev, 0, sizeof(int), s);
+    }
     const int nr = d.nr, nv = t->nv;
-    const long cpad = (cells + kBN - 1) / kBN * kBN;  // whole TMA boxes, zero padding rows
-    const size_t xb = (size_t)cpad * nr * 2, yb = (size_t)cells * nr * 4;
-    if ((st = arena_reserve(c, T.ws, 2 * xb + yb + 4 * 256 + 64)) != LBE_OK) return st;
+    const int bn = pick_bn(cells);
+    const long cpad = (cells + bn - 1) / bn * bn;  // whole TMA boxes, zero padding rows
+    const int ks = pick_ksplit(cells, bn, nr);
+    const size_t xb = (size_t)cpad * nr * 2, yb = (size_t)ks * cells * nr * 4;
+    if ((st = arena_reserve(c, T.ws, 2 * xb + yb + 3 * 256)) != LBE_OK) return st;
     auto* xh = (__nv_bfloat16*)arena_take(T.ws, xb);
     auto* xl = (__nv_bfloat16*)arena_take(T.ws, xb);
     auto* Y = (float*)arena_take(T.ws, yb);
-    auto* err = (int*)arena_take(T.ws, 64);
     if (cpad > cells) {
         cudaMemsetAsync(xh + (size_t)cells * nr, 0, (size_t)(cpad - cells) * nr * 2, s);
         cudaMemsetAsync(xl + (size_t)cells * nr, 0, (size_t)(cpad - cells) * nr * 2, s);
     }
     CUtensorMap mXh, mXl;
-    if (!make_map(&mXh, xh, cpad, nr, kBN) || !make_map(&mXl, xl, cpad, nr, kBN)) {
+    if (!make_map(&mXh, xh, cpad, nr, bn) || !make_map(&mXl, xl, cpad, nr, bn)) {
         c->last_error = "cuTensorMapEncodeTiled failed for the cell operand";
         return LBE_INTERNAL;
     }
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_dense_gemm<kBN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
-        attr = true;
-    }
-    cudaMemsetAsync(err, 0, 4, s);
     k_gather_split<<<1024, 256, 0, s>>>(h, xh, xl, cells, nv, nr, mode);
-    // segments: (A_hi, x_hi), (A_lo, x_hi), (A_hi, x_lo); code bit 0 = A lo, bit 1 = x lo
-    const uint32_t codes = (0u) | (1u << 2) | (2u << 4);
-    dim3 grid((cells + kBN - 1) / kBN, nr / kBM);
-    k_dense_gemm<kBN><<<grid, 128, kGemmSmem, s>>>(d.mAh, d.mAl, mXh, mXl, nr, cells, nr, 3, codes, Y, err);
+    switch (bn) {
+        case 64: launch_gemm<64>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
+        case 128: launch_gemm<128>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
+        case 160: launch_gemm<160>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
+        case 192: launch_gemm<192>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
+        case 224: launch_gemm<224>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
+        default: launch_gemm<256>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
+    }
     const float* nu1 = t->nu1_f;
-    k_expand<<<2048, 256, 0, s>>>(Y, h, nu1, delta, Lplus, Lout, cells, nv, nr, mode);
+    if (G) {  // L+ h and the SIS L-moments in one pass
+        const float* vel = t->vel_f;
+        const double dv3 = t->dv * t->dv * t->dv;
+        const bool p2 = mode == 2;
+        switch (nv) {
+            case 8: (p2 ? launch_expand_g<8, 2> : launch_expand_g<8, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nr, dv3, ks, s); break;
+            case 16: (p2 ? launch_expand_g<16, 2> : launch_expand_g<16, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nr, dv3, ks, s); break;
+            case 24: (p2 ? launch_expand_g<24, 2> : launch_expand_g<24, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nr, dv3, ks, s); break;
+            default: (p2 ? launch_expand_g<32, 2> : launch_expand_g<32, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nr, dv3, ks, s); break;
+        }
+    } else {
+        k_expand<<<2048, 256, 0, s>>>(Y, h, nu1, delta, Lplus, Lout, cells, nv, nr, mode, ks);
+    }
     g_launches += 3;
     g_levals += cells;
-    int herr = 0;
-    cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(T.err_host, T.err_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (!sync) return cuda_status(c, cudaGetLastError(), "dense operator launch");
     st = cuda_status(c, cudaStreamSynchronize(s), "dense operator");
-    if (st == LBE_OK && herr) {
-        c->last_error = "tensor-core operator: a bounded wait expired";
-        return LBE_TIMEOUT;
-    }
-    return st;
+    return st != LBE_OK ? st : tc_check(c, t);
+}
+
+// Reads (and clears) the GEMM's failure word; valid once the stream has been synchronised.
+lbe_status tc_check(Ctx* c, DevTables* t) {
+    if (!t->tc || !t->tc->err_host || !*t->tc->err_host) return LBE_OK;
+    *t->tc->err_host = 0;
+    cudaMemset(t->tc->err_dev, 0, sizeof(int));
+    c->last_error = "tensor-core operator: a bounded wait expired";
+    return LBE_TIMEOUT;
 }
 
 lbe_status tc_apply_L(Ctx* c, DevTables* t, int cells, const double* delta, const float* h, float* Lplus,
@@ -479,6 +633,8 @@ void tc_release(Ctx* c, DevTables* t) {
         dev_free(c, d.Al, d.bytes / 2);
     }
     arena_release(c, t->tc->ws);
+    dev_free(c, t->tc->err_dev, 256);
+    if (t->tc->err_host) cudaFreeHost(t->tc->err_host);
     delete t->tc;
     t->tc = nullptr;
 }

@@ -52,6 +52,8 @@ struct DevTables {
     // float
     float* feq_f = nullptr; float* nu1_f = nullptr; float* mult_f = nullptr; float* ab_f = nullptr;
     float* vel_f = nullptr;
+    // double-float (hi, lo float pairs; complex tables as re.hi, re.lo, im.hi, im.lo)
+    float* feq_x = nullptr; float* nu1_x = nullptr; float* mult_x = nullptr; float* ab_x = nullptr;
     TcOperands* tc = nullptr;
     size_t bytes = 0;
 };

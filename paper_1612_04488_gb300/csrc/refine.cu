@@ -13,7 +13,9 @@
 // starting from h = the low-precision SIS solution of the full problem, so that a solve
 // usually needs two FP64 iterations: one residual and one that certifies convergence.
 // The answer is the FP64 SIS fixed point, while almost all collision-operator evaluations
-// run in low precision.  h lives in FP64; e and r in FP32.
+// run in low precision.  h lives in FP64; e and r in FP32.  The FP64-class operator
+// evaluations (at the base point h0 and when it is re-centred) run in double-float
+// arithmetic (pairs of floats, ~2^-44 relative), which this GPU issues far faster than FP64.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -231,12 +233,12 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         cudaMemcpyAsync(I.sjobs.p, I.sj.data(), n * sizeof(SweepJobDev), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(I.ijobs.p, I.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, s);
         g_h2d += n * (sizeof(SweepJobDev) + sizeof(SisJobDev));
-        // the one FP64 collision-operator evaluation of the solve: at h0 = the FP32 solution;
-        // every later FP64 iteration adds the FP32 operator of the increment h - h0
+        // the one FP64-class collision-operator evaluation of the solve: at h0 = the FP32
+        // solution; every later FP64 iteration adds the FP32 operator of the increment h - h0
         range_copy(O.h.as<double>(), base_h, O.cells * n3, s);
         for (int j = 0; j < n; ++j) {
             const long o = O.cell_off[j] * n3;
-            fsm_cc_apply<double>(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o, base_lp + o,
+            fsm_df_apply(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o, base_lp + o,
                                  base_lh + o, O.scratch.p, O.chunk, s, O.geo[j].dim == 1 ? 2 : 1);
         }
         O.base_h = base_h;
@@ -283,7 +285,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             prev_rel[j] = rel;
             if (!plain[j] && refs[j] >= 1 && rel > 0.1 * rel_before[j]) plain[j] = 1;
             rel_before[j] = rel;
-            if (plain[j] && rel > 0.9 * pr) rebase[j] = 1;  // plain steps stalled: exact FP64 operator
+            if (plain[j] && rel > 0.9 * pr) rebase[j] = 1;  // plain steps stalled: re-centre the operator
             if (trace) {
                 const long o = O.cell_off[j] * n3, nn = (long)O.sj[j].ncell * n3;
                 std::vector<double> hh(nn), hb(nn);
@@ -308,7 +310,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             if (!rebase[j]) continue;
             const long o = O.cell_off[j] * n3;
             range_copy(O.h.as<double>() + o, base_h + o, (long)O.sj[j].ncell * n3, s);
-            fsm_cc_apply<double>(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o, base_lp + o,
+            fsm_df_apply(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o, base_lp + o,
                                  base_lh + o, O.scratch.p, O.chunk, s, O.geo[j].dim == 1 ? 2 : 1);
         }
         if (!corr.empty()) {
@@ -340,7 +342,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
                 if (!rebase[j]) continue;
                 const long o = O.cell_off[j] * n3;
                 range_copy(O.h.as<double>() + o, base_h + o, (long)O.sj[j].ncell * n3, s);
-                fsm_cc_apply<double>(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o,
+                fsm_df_apply(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o,
                                      base_lp + o, base_lh + o, O.scratch.p, O.chunk, s, O.geo[j].dim == 1 ? 2 : 1);
             }
         }

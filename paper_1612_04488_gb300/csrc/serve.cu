@@ -236,7 +236,12 @@ void slot_install(Bucket& b, int s, const lbe_problem& pb, long off, int phase) 
     ij.max_iter = pb.max_iter;
     ij.coef_off = (int)(s * b.coef_per_slot + coef.size());
     if (g.dim == 1) {
-        for (auto* v : {&g.fa, &g.fb, &g.fc, &g.x}) coef.insert(coef.end(), v->begin(), v->end());
+        {
+            // the march divides by fa at every node: store 1/fa (block [1/fa | fb | fc | x])
+            std::vector<double> ifa(g.fa.size());
+            for (size_t i = 0; i < ifa.size(); ++i) ifa[i] = g.fa[i] != 0.0 ? 1.0 / g.fa[i] : 0.0;
+            for (auto* v : {&ifa, &g.fb, &g.fc, &g.x}) coef.insert(coef.end(), v->begin(), v->end());
+        }
     } else {
         const int mx = g.nx - 2, my = g.ny - 2;
         for (int p = 0; p < mx; ++p)
@@ -470,7 +475,7 @@ static void service_main(Ctx* c) {
                         // the request's one FP64 collision-operator evaluation, at h0
                         const long o = D->B.cell_off[sj->ds] * n3;
                         range_copy(h, D->base_h.as<double>() + o, n, ds);
-                        fsm_cc_apply<double>(*D->B.t, D->B.sj[sj->ds].ncell, D->B.delta.as<double>() + D->B.cell_off[sj->ds],
+                        fsm_df_apply(*D->B.t, D->B.sj[sj->ds].ncell, D->B.delta.as<double>() + D->B.cell_off[sj->ds],
                                              D->base_h.as<double>() + o, D->base_lp.as<double>() + o,
                                              D->base_lh.as<double>() + o, D->B.scratch.p, D->B.chunk, ds,
                                              D->B.geo[sj->ds].dim == 1 ? 2 : 1);

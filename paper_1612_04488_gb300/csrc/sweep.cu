@@ -32,29 +32,36 @@ __device__ __forceinline__ T source(int forcing, T v1, T v2, T v3, T f) {
     return T(0);  // homogeneous map (refinement correction solves)
 }
 
+constexpr int kPre = 8;  // prefetch depth of the sweeps (nodes)
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* __restrict__ h,
                                                  const T* __restrict__ nu1, const T* __restrict__ vel,
                                                  const T* __restrict__ feq,
                                                  const SweepJobDev* __restrict__ jobs,
                                                  const int* __restrict__ active,
-                                                 const double* __restrict__ coef, int nv) {
+                                                 const double* __restrict__ coef, int nv, int staged) {
+    extern __shared__ __align__(16) unsigned char sweep_smem[];
     const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
     const int half = nv / 2, n2 = nv * nv;
     const long n3 = (long)n2 * nv;
+    const int n = jb.ncell;
+    // march coefficients [fa|fb|fc|ba|bb|bc] (n each): with `staged`, converted to T once per
+    // block into shared memory (a double-to-float conversion per node and thread would
+    // otherwise run at the FP64 rate)
+    const double* cg = coef + jb.coef_off;
+    T* sc = reinterpret_cast<T*>(sweep_smem);
+    if (staged) {
+        for (int k = threadIdx.x; k < 6 * n; k += blockDim.x) sc[k] = (T)cg[k];
+        __syncthreads();
+    }
+    auto C = [&](int a, int i) -> T { return staged ? sc[a * n + i] : (T)cg[a * n + i]; };
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= half * n2) return;
     const int i1p = half + t / n2, rem = t % n2;
     const int vpos = i1p * n2 + rem, vneg = (nv - 1 - i1p) * n2 + rem;
-    const int n = jb.ncell;
     const T* r = rhs + jb.cell_off * n3;
     T* o = h + jb.cell_off * n3;
-    const double* fa = coef + jb.coef_off;
-    const double* fb = fa + n;
-    const double* fc = fb + n;
-    const double* ba = fc + n;
-    const double* bb = ba + n;
-    const double* bc = bb + n;
     const T d = (T)jb.delta;
     const T v1 = vel[i1p];
     const T nup = d * nu1[vpos];
@@ -63,30 +70,64 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
     const T Sn = source<T>(jb.forcing, vel[nv - 1 - i1p], w2, w3, feq[vneg]);
     T hm1 = T(0), hm2 = T(0);
     o[vpos] = T(0);
-    T rn = n > 1 ? r[1 * n3 + vpos] : T(0);  // rhs of the next node is loaded one step ahead
-    for (int i = 1; i < n; ++i) {
-        const T ri = rn;
-        if (i + 1 < n) rn = r[(i + 1) * n3 + vpos];
-        const T acc = (ri + Sp) - v1 * ((T)fb[i] * hm1 + (T)fc[i] * hm2);
-        const T hi = acc / (nup + v1 * (T)fa[i]);
-        o[i * n3 + vpos] = hi;
-        hm2 = hm1;
-        hm1 = hi;
+    // the right-hand sides of the next kPre nodes are in flight while a node is solved, and
+    // their reciprocal diagonals are formed off the march's dependent chain (which is then
+    // three multiply-adds per node)
+    T rb[kPre], ib[kPre];
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+        const int i = 1 + k;
+        rb[k] = i < n ? r[(long)i * n3 + vpos] : T(0);
+        ib[k] = i < n ? T(1) / (nup + v1 * C(0, i)) : T(0);
+    }
+    for (int i0 = 1; i0 < n; i0 += kPre) {
+#pragma unroll
+        for (int k = 0; k < kPre; ++k) {
+            const int i = i0 + k;
+            if (i < n) {
+                const T ri = rb[k], inv = ib[k];
+                const int j = i + kPre;
+                if (j < n) {
+                    rb[k] = r[(long)j * n3 + vpos];
+                    ib[k] = T(1) / (nup + v1 * C(0, j));
+                }
+                const T acc = (ri + Sp) - v1 * (C(1, i) * hm1 + C(2, i) * hm2);
+                const T hi = acc * inv;
+                o[(long)i * n3 + vpos] = hi;
+                hm2 = hm1;
+                hm1 = hi;
+            }
+        }
     }
     // specular symmetry plane: h(x_Ns, v1<0) = h(x_Ns, -v1); ghost node carries h(x_{Ns-1}, -v1)
     const T u = -vel[nv - 1 - i1p];
     const T nun = d * nu1[vneg];
     T g1 = hm1, g2 = hm2;
-    o[(n - 1) * n3 + vneg] = hm1;
-    T rb = n > 1 ? r[(n - 2) * n3 + vneg] : T(0);
-    for (int i = n - 2; i >= 0; --i) {
-        const T ri = rb;
-        if (i > 0) rb = r[(i - 1) * n3 + vneg];
-        const T acc = (ri + Sn) - u * ((T)bb[i] * g1 + (T)bc[i] * g2);
-        const T hi = acc / (nun + u * (T)ba[i]);
-        o[i * n3 + vneg] = hi;
-        g2 = g1;
-        g1 = hi;
+    o[(long)(n - 1) * n3 + vneg] = hm1;
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+        const int i = n - 2 - k;
+        rb[k] = i >= 0 ? r[(long)i * n3 + vneg] : T(0);
+        ib[k] = i >= 0 ? T(1) / (nun + u * C(3, i)) : T(0);
+    }
+    for (int i0 = n - 2; i0 >= 0; i0 -= kPre) {
+#pragma unroll
+        for (int k = 0; k < kPre; ++k) {
+            const int i = i0 - k;
+            if (i >= 0) {
+                const T ri = rb[k], inv = ib[k];
+                const int j = i - kPre;
+                if (j >= 0) {
+                    rb[k] = r[(long)j * n3 + vneg];
+                    ib[k] = T(1) / (nun + u * C(3, j));
+                }
+                const T acc = (ri + Sn) - u * (C(4, i) * g1 + C(5, i) * g2);
+                const T hi = acc * inv;
+                o[(long)i * n3 + vneg] = hi;
+                g2 = g1;
+                g1 = hi;
+            }
+        }
     }
 }
 
@@ -96,10 +137,21 @@ __global__ void __launch_bounds__(128) k_sweep2d(const T* __restrict__ rhs, T* _
                                                  const T* __restrict__ feq,
                                                  const SweepJobDev* __restrict__ jobs,
                                                  const int* __restrict__ active,
-                                                 const double* __restrict__ coef, int nv) {
+                                                 const double* __restrict__ coef, int nv, int staged) {
+    extern __shared__ __align__(16) unsigned char sweep_smem[];
     const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
     const int n2 = nv * nv;
     const long n3 = (long)n2 * nv;
+    const int nx = jb.nx, ny = jb.ny;
+    // [xa|xb|xc] (nx each) [ya|yb|yc] (ny each), staged as in the 1D sweep
+    const double* cg = coef + jb.coef_off;
+    T* sc = reinterpret_cast<T*>(sweep_smem);
+    if (staged) {
+        for (int k = threadIdx.x; k < 3 * (nx + ny); k += blockDim.x) sc[k] = (T)cg[k];
+        __syncthreads();
+    }
+    auto CX = [&](int a, int i) -> T { return staged ? sc[a * nx + i] : (T)cg[a * nx + i]; };
+    auto CY = [&](int a, int j) -> T { return staged ? sc[3 * nx + a * ny + j] : (T)cg[3 * nx + a * ny + j]; };
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n3) return;
     const int i1 = v / n2, i2 = (v / nv) % nv;
@@ -108,32 +160,43 @@ __global__ void __launch_bounds__(128) k_sweep2d(const T* __restrict__ rhs, T* _
     const T u2 = s2 ? vel[i2] : -vel[i2];
     const T nu = (T)jb.delta * nu1[v];
     const T S = source<T>(jb.forcing, vel[i1], vel[i2], vel[v % nv], feq[v]);
-    const int nx = jb.nx, ny = jb.ny;
-    const double* xa = coef + jb.coef_off;
-    const double* xb = xa + nx;
-    const double* xc = xb + nx;
-    const double* ya = xc + nx;
-    const double* yb = ya + ny;
-    const double* yc = yb + ny;
     const T* r = rhs + jb.cell_off * n3;
     T* o = h + jb.cell_off * n3;
     const int dj = s2 ? -1 : 1;  // offset to the upwind row in j
     for (int mj = 0; mj < ny; ++mj) {
         const int j = s2 ? mj : ny - 1 - mj;
         T hm1 = T(0), hm2 = T(0);
-        const T ay = (T)ya[mj], by = (T)yb[mj], cy = (T)yc[mj];
-        for (int mi = 0; mi < nx; ++mi) {
-            const int i = s1 ? mi : nx - 1 - mi;
-            const long cell = (long)i * ny + j;
-            T acc = r[cell * n3 + v] + S;
-            if (mi >= 1) acc -= u1 * (T)xb[mi] * hm1;
-            if (mi >= 2) acc -= u1 * (T)xc[mi] * hm2;
-            if (mj >= 1) acc -= u2 * by * o[(cell + dj) * n3 + v];
-            if (mj >= 2) acc -= u2 * cy * o[(cell + 2 * dj) * n3 + v];
-            const T hij = acc / (nu + u1 * (T)xa[mi] + u2 * ay);
-            o[cell * n3 + v] = hij;
-            hm2 = hm1;
-            hm1 = hij;
+        const T ay = CY(0, mj), by = CY(1, mj), cy = CY(2, mj);
+        auto cell_of = [&](int m) { return (long)(s1 ? m : nx - 1 - m) * ny + j; };
+        T buf[kPre], ib[kPre];
+        const T diag = nu + u2 * ay;
+#pragma unroll
+        for (int k = 0; k < kPre; ++k) {
+            buf[k] = k < nx ? r[cell_of(k) * n3 + v] : T(0);
+            ib[k] = k < nx ? T(1) / (diag + u1 * CX(0, k)) : T(0);
+        }
+        for (int m0 = 0; m0 < nx; m0 += kPre) {
+#pragma unroll
+            for (int k = 0; k < kPre; ++k) {
+                const int mi = m0 + k;
+                if (mi < nx) {
+                    const long cell = cell_of(mi);
+                    T acc = buf[k] + S;
+                    const T inv = ib[k];
+                    if (mi + kPre < nx) {
+                        buf[k] = r[cell_of(mi + kPre) * n3 + v];
+                        ib[k] = T(1) / (diag + u1 * CX(0, mi + kPre));
+                    }
+                    if (mi >= 1) acc -= u1 * CX(1, mi) * hm1;
+                    if (mi >= 2) acc -= u1 * CX(2, mi) * hm2;
+                    if (mj >= 1) acc -= u2 * by * o[(cell + dj) * n3 + v];
+                    if (mj >= 2) acc -= u2 * cy * o[(cell + 2 * dj) * n3 + v];
+                    const T hij = acc * inv;
+                    o[cell * n3 + v] = hij;
+                    hm2 = hm1;
+                    hm1 = hij;
+                }
+            }
         }
     }
 }
@@ -158,32 +221,43 @@ template <> struct Acc<float> {
 };
 
 // mom[cell][5] = sum_v {v3, (|v|^2-5/2) v3, (2 v1^2-1) v3, (2 v2^2-1) v3, 2 v1 v2 v3} h dv^3
-// One block of 8 nv threads per cell: thread t owns i3 = t % nv and the rows i2 = t/nv + 8k.
-template <typename T>
-__global__ void __launch_bounds__(256) k_moments(const T* __restrict__ h, const T* __restrict__ vel,
-                                                 int nv, double dv3, long cell0, double* __restrict__ mom) {
+// One block of 8 NV threads per cell: thread t owns i3 = t % NV and the rows i2 = t/NV + 8k.
+// v3 is fixed per thread, so it is factored out: the thread sums h, (v1^2 + v2^2) h, v1^2 h,
+// v2^2 h and v1 v2 h, and combines them with v3 once (five multiply-adds per value).
+template <typename T, int NV>
+__global__ void __launch_bounds__(8 * NV) k_moments(const T* __restrict__ h, const T* __restrict__ vel,
+                                                    double dv3, long cell0, double* __restrict__ mom) {
     __shared__ double red[32 * 5];
+    constexpr int R = NV / 8;  // rows per thread and plane
     const long cell = cell0 + blockIdx.x;
-    const long n3 = (long)nv * nv * nv;
-    const int i3 = threadIdx.x % nv, r0 = threadIdx.x / nv;
+    constexpr long n3 = (long)NV * NV * NV;
+    const int i3 = threadIdx.x % NV, r0 = threadIdx.x / NV;
     const T v3 = vel[i3];
+    T v2s[R], v2v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        v2v[k] = vel[r0 + 8 * k];
+        v2s[k] = v2v[k] * v2v[k];
+    }
     const T* hc = h + cell * n3 + i3;
     Acc<T> a[5];
-    for (int i1 = 0; i1 < nv; ++i1) {
-        const T v1 = vel[i1];
-        for (int i2 = r0; i2 < nv; i2 += 8) {
-            const T v2 = vel[i2];
-            const T x = hc[((long)i1 * nv + i2) * nv] * v3;
-            a[0].add(x);
-            a[1].add((v1 * v1 + v2 * v2 + v3 * v3 - T(2.5)) * x);
-            a[2].add((T(2) * v1 * v1 - T(1)) * x);
-            a[3].add((T(2) * v2 * v2 - T(1)) * x);
-            a[4].add(T(2) * v1 * v2 * x);
+    for (int i1 = 0; i1 < NV; ++i1) {
+        const T v1 = vel[i1], v1s = v1 * v1;
+        T x[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) x[k] = hc[((long)i1 * NV + r0 + 8 * k) * NV];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            a[0].add(x[k]);
+            a[1].add((v1s + v2s[k]) * x[k]);
+            a[2].add(v1s * x[k]);
+            a[3].add(v2s[k] * x[k]);
+            a[4].add(v1 * v2v[k] * x[k]);
         }
     }
-    double s[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) s[k] = a[k].value();
+    const double w3 = (double)v3, s0 = a[0].value();
+    double s[5] = {w3 * s0, w3 * (a[1].value() + (w3 * w3 - 2.5) * s0), w3 * (2.0 * a[2].value() - s0),
+                   w3 * (2.0 * a[3].value() - s0), 2.0 * w3 * a[4].value()};
     block_reduce<5>(s, red);
     if (threadIdx.x == 0)
         for (int k = 0; k < 5; ++k) mom[cell * 5 + k] = s[k] * dv3;
@@ -226,7 +300,7 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
         // the march is serial: the block stages 256 nodes at a time in shared memory and
         // thread 0 walks them
         __shared__ double sfa[256], sfb[256], sfc[256], srhs[256], sW[256], sU[256];
-        const double* fa = coef + jb.coef_off;  // block [fa | fb | fc | x], n each
+        const double* fa = coef + jb.coef_off;  // block [1/fa | fb | fc | x], n each
         const double* fb = fa + n;
         const double* fc = fb + n;
         const double* xs = fc + n;
@@ -250,7 +324,7 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
                     const int ii = w0 + k;
                     double r = srhs[k] - sfb[k] * ym1;
                     if (ii >= 2) r -= sfc[k] * ym2;
-                    const double yi = r / sfa[k];
+                    const double yi = r * sfa[k];
                     du[ii] = (yi - sW[k]) - sU[k];
                     ym2 = ym1;
                     ym1 = yi;
@@ -411,10 +485,13 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
 }  // namespace
 
 template <typename T>
-void launch_sweep(const DevTables& t, int dim, int njobs, int max_cells_unused, const T* rhs, T* h,
+void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T* rhs, T* h,
                   const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s) {
-    (void)max_cells_unused;
     if (njobs <= 0) return;
+    // float sweeps stage the coefficients when the largest job's fit in 48 KB
+    const size_t sbytes = (size_t)max_coef * sizeof(T);
+    const int staged = (sizeof(T) == 4 && max_coef > 0 && sbytes <= 48 * 1024) ? 1 : 0;
+    const size_t smem = staged ? sbytes : 0;
     g_launches += 1;
     const int nv = t.nv;
     const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
@@ -423,11 +500,11 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_cells_unused, 
     if (dim == 1) {
         const int nt = nv / 2 * nv * nv;
         dim3 g((nt + 127) / 128, njobs);
-        k_sweep1d<T><<<g, 128, 0, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv);
+        k_sweep1d<T><<<g, 128, smem, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv, staged);
     } else {
         const int nt = nv * nv * nv;
         dim3 g((nt + 127) / 128, njobs);
-        k_sweep2d<T><<<g, 128, 0, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv);
+        k_sweep2d<T><<<g, 128, smem, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv, staged);
     }
 }
 
@@ -436,7 +513,13 @@ void launch_moments(const DevTables& t, long cell0, int cells, const T* h, doubl
     if (cells <= 0) return;
     g_launches += 1;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
-    k_moments<T><<<cells, 8 * t.nv, 0, s>>>(h, vel, t.nv, t.dv * t.dv * t.dv, cell0, mom);
+    const double dv3 = t.dv * t.dv * t.dv;
+    switch (t.nv) {
+        case 8: k_moments<T, 8><<<cells, 64, 0, s>>>(h, vel, dv3, cell0, mom); break;
+        case 16: k_moments<T, 16><<<cells, 128, 0, s>>>(h, vel, dv3, cell0, mom); break;
+        case 24: k_moments<T, 24><<<cells, 192, 0, s>>>(h, vel, dv3, cell0, mom); break;
+        default: k_moments<T, 32><<<cells, 256, 0, s>>>(h, vel, dv3, cell0, mom); break;
+    }
 }
 
 void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, const int* active,

@@ -14,7 +14,9 @@ struct Ctx;
 lbe_status tc_apply_L(Ctx* c, DevTables* t, int cells, const double* delta, const float* h, float* Lplus,
                       float* Lout, cudaStream_t s);
 lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h,
-                        float* Lplus, float* Lout, cudaStream_t s);
+                        float* Lplus, float* Lout, cudaStream_t s, bool sync = true, const double* nd = nullptr,
+                        double* G = nullptr);
+lbe_status tc_check(Ctx* c, DevTables* t);
 void tc_release(Ctx* c, DevTables* t);
 // refine.cu: BF16 operator inside an outer defect-correction loop
 lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs, double* U3_out,
@@ -53,7 +55,7 @@ struct JobState {
 };
 
 template <typename T>
-void launch_sweep(const DevTables& t, int dim, int njobs, int max_cells, const T* rhs, T* h,
+void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T* rhs, T* h,
                   const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s);
 template <typename T>
 void launch_moments(const DevTables& t, long cell0, int cells, const T* h, double* mom, cudaStream_t s);
@@ -70,6 +72,9 @@ size_t fsm_cc_scratch_bytes(const DevTables& t, int cells, int elem_bytes, int* 
 template <typename T>
 lbe_status fsm_cc_apply(const DevTables& t, int cells, const double* delta, const T* h, T* Lplus, T* Lout,
                         void* scratch, int chunk, cudaStream_t s, int mode = 0);
+// the same operator in double-float arithmetic on double data (scratch as for double)
+lbe_status fsm_df_apply(const DevTables& t, int cells, const double* delta, const double* h, double* Lplus,
+                        double* Lout, void* scratch, int chunk, cudaStream_t s, int mode = 0);
 template <typename T>
 void lmoments(const DevTables& t, int cells, const T* Lh, const T* h, const double* nd, double* G,
               cudaStream_t s);

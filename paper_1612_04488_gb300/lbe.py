@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "liblbe.so")
 OK, NOT_CONVERGED, NAN, BAD_ARG, OOM, TIMEOUT, INTERNAL, UNSUPPORTED = range(8)
 POISEUILLE, THERMAL_TRANSPIRATION = 0, 1
 CIS, SIS = 0, 1
-FP64, FP32, BF16_REFINED, FP32_REFINED = 0, 1, 2, 3
+FP64, FP32, BF16_REFINED, FP32_REFINED, DF32 = 0, 1, 2, 3, 4
 
 
 class Geometry(C.Structure):

@@ -32,11 +32,13 @@ def parity_h(cells, nv, parity, seed):
 @pytest.mark.parametrize("nv,M,parity,cells,prec,tol", [
     (16, 16, 2, 21, lbe.FP64, 1e-12), (16, 16, 1, 9, lbe.FP64, 1e-12), (32, 32, 2, 3, lbe.FP64, 1e-12),
     (24, 16, 2, 4, lbe.FP64, 1e-12), (32, 32, 1, 3, lbe.FP32, 3e-6), (16, 16, 2, 300, lbe.BF16_REFINED, 2e-4),
-    (32, 32, 2, 40, lbe.BF16_REFINED, 2e-4), (16, 16, 1, 70, lbe.BF16_REFINED, 2e-4)])
+    (32, 32, 2, 40, lbe.BF16_REFINED, 2e-4), (16, 16, 1, 70, lbe.BF16_REFINED, 2e-4),
+    (16, 16, 2, 21, lbe.DF32, 1e-12), (16, 16, 1, 9, lbe.DF32, 1e-12), (32, 32, 2, 3, lbe.DF32, 1e-12),
+    (24, 16, 2, 4, lbe.DF32, 1e-12)])
 def test_apply_L_sym_matches_oracle(ctx, nv, M, parity, cells, prec, tol):
     h = parity_h(cells, nv, parity, seed=cells + nv)
     deltas = np.linspace(0.3, 30.0, cells)
-    dt = torch.float64 if prec == lbe.FP64 else torch.float32
+    dt = torch.float64 if prec in (lbe.FP64, lbe.DF32) else torch.float32
     hd = torch.tensor(h, device="cuda", dtype=dt)
     dd = torch.tensor(deltas, device="cuda")
     lp = torch.full_like(hd, float("nan"))
@@ -50,6 +52,37 @@ def test_apply_L_sym_matches_oracle(ctx, nv, M, parity, cells, prec, tol):
         olp, oL = F.apply(hh[c], deltas[c])
         assert np.max(np.abs(lp[c] - olp)) <= tol * np.max(np.abs(olp)), c
         assert np.max(np.abs(L[c] - oL)) <= tol * np.max(np.abs(oL)), c
+
+
+@pytest.mark.parametrize("nv,M,cells", [(16, 16, 7), (8, 8, 33), (32, 16, 2)])
+def test_apply_L_df32_matches_oracle(ctx, nv, M, cells):
+    """The full operator (all M directions, no parity assumed) in double-float arithmetic,
+    with the L-moments, against the FP64 oracle."""
+    rng = np.random.default_rng(nv + cells)
+    h = workloads.random_h(cells, nv, 6.0, seed=nv * cells)
+    h = h + 0.1 * rng.standard_normal(h.shape) * np.abs(h).max()   # no parity at all
+    deltas = np.linspace(0.5, 50.0, cells)
+    nd = 1.25 * deltas
+    hd = torch.tensor(h, device="cuda", dtype=torch.float64)
+    dd = torch.tensor(deltas, device="cuda")
+    ndd = torch.tensor(nd, device="cuda")
+    lp = torch.full_like(hd, float("nan"))
+    L = torch.full_like(hd, float("nan"))
+    G = torch.zeros((cells, 2), device="cuda", dtype=torch.float64)
+    ctx.apply_L(nv, 6.0, M, 4.5, lbe.DF32, cells, dd.data_ptr(), hd.data_ptr(), lp.data_ptr(), L.data_ptr(),
+                ndd.data_ptr(), G.data_ptr())
+    torch.cuda.synchronize()
+    lp, L, G = lp.cpu().numpy(), L.cpu().numpy(), G.cpu().numpy()
+    F = fsm.FSM(nv, 6.0, M, 4.5)
+    V1, V2, V3 = F.V1, F.V2, F.V3
+    for c in sorted({0, cells // 2, cells - 1}):
+        olp, oL = F.apply(h[c], deltas[c])
+        assert np.max(np.abs(lp[c] - olp)) <= 1e-12 * np.max(np.abs(olp)), c
+        assert np.max(np.abs(L[c] - oL)) <= 1e-12 * np.max(np.abs(oL)), c
+        w = 2.0 * (oL + nd[c] * h[c]) * V3 * F.dv ** 3
+        for j, Vj in ((0, V1), (1, V2)):
+            ref = np.sum(Vj * w)
+            assert abs(G[c, j] - ref) <= 1e-11 * np.sum(np.abs(Vj * w)), (c, j)
 
 
 def test_bf16_refined_solve_reaches_fp64(ctx):
