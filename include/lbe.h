@@ -231,14 +231,22 @@ lbe_status lbe_set_stream(lbe_ctx* ctx, void* stream);
 
 /* Process-wide counters since the library was loaded: kernels launched by this library,
  * bytes it copied host->device and device->host, and cells passed through the collision
- * operator (one cell = one application of L to one nv^3 vector). */
+ * operator (one cell = one application of L to one nv^3 vector).  With kernel timing on
+ * (lbe_set_kernel_timing), every tensor-core GEMM launched by lbe_apply_L_sym is bracketed
+ * by CUDA events on its stream: dense_gemm_timed counts those launches and dense_gemm_ms
+ * sums their durations. */
 typedef struct {
     uint64_t kernel_launches;
     uint64_t h2d_bytes;
     uint64_t d2h_bytes;
     uint64_t cell_l_evals;
+    uint64_t dense_gemm_timed;
+    double dense_gemm_ms;
 } lbe_stats;
 lbe_status lbe_get_stats(lbe_stats* out);
+
+/* Process-wide switch (0 = off, the default) for the event timing described above. */
+lbe_status lbe_set_kernel_timing(int on);
 
 #ifdef __cplusplus
 }

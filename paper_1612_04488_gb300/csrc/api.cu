@@ -58,6 +58,20 @@ void dev_free(Ctx* c, void* p, size_t bytes) {
 }
 
 std::atomic<unsigned long long> g_launches{0}, g_h2d{0}, g_d2h{0}, g_levals{0};
+std::atomic<int> g_time_kernels{0};
+static std::mutex g_time_mu;
+static unsigned long long g_gemm_n = 0;
+static double g_gemm_ms = 0.0;
+void add_gemm_time(double ms) {
+    std::lock_guard<std::mutex> lk(g_time_mu);
+    ++g_gemm_n;
+    g_gemm_ms += ms;
+}
+void get_gemm_time(unsigned long long* n, double* ms) {
+    std::lock_guard<std::mutex> lk(g_time_mu);
+    *n = g_gemm_n;
+    *ms = g_gemm_ms;
+}
 
 lbe_status arena_reserve(Ctx* c, Arena& a, size_t bytes) {
     a.off = 0;
@@ -910,6 +924,16 @@ lbe_status lbe_get_stats(lbe_stats* out) {
     out->h2d_bytes = g_h2d.load();
     out->d2h_bytes = g_d2h.load();
     out->cell_l_evals = g_levals.load();
+    unsigned long long n = 0;
+    double ms = 0.0;
+    get_gemm_time(&n, &ms);
+    out->dense_gemm_timed = n;
+    out->dense_gemm_ms = ms;
+    return LBE_OK;
+}
+
+lbe_status lbe_set_kernel_timing(int on) {
+    g_time_kernels.store(on ? 1 : 0);
     return LBE_OK;
 }
 

@@ -574,6 +574,11 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         return LBE_INTERNAL;
     }
     k_gather_split<<<1024, 256, 0, s>>>(h, xh, xl, cells, nv, nr, mode);
+    // optional event timing of the GEMM alone (public synchronous calls only)
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    const bool timed = sync && g_time_kernels.load() != 0 && cudaEventCreate(&ev[0]) == cudaSuccess &&
+                       cudaEventCreate(&ev[1]) == cudaSuccess;
+    if (timed) cudaEventRecord(ev[0], s);
     switch (bn) {
         case 64: launch_gemm<64>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
         case 128: launch_gemm<128>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
@@ -582,6 +587,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         case 224: launch_gemm<224>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
         default: launch_gemm<256>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
     }
+    if (timed) cudaEventRecord(ev[1], s);
     const float* nu1 = t->nu1_f;
     if (G) {  // L+ h and the SIS L-moments in one pass
         const float* vel = t->vel_f;
@@ -601,6 +607,12 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     cudaMemcpyAsync(T.err_host, T.err_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (!sync) return cuda_status(c, cudaGetLastError(), "dense operator launch");
     st = cuda_status(c, cudaStreamSynchronize(s), "dense operator");
+    if (ev[0]) {
+        float ms = 0.f;
+        if (timed && st == LBE_OK && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) add_gemm_time(ms);
+        cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+    }
     return st != LBE_OK ? st : tc_check(c, t);
 }
 

@@ -97,6 +97,10 @@ struct Arena {
 
 // process-wide counters (lbe_get_stats)
 extern std::atomic<unsigned long long> g_launches, g_h2d, g_d2h, g_levals;
+// optional event timing of the tensor-core GEMM (lbe_set_kernel_timing)
+extern std::atomic<int> g_time_kernels;
+void add_gemm_time(double ms);
+void get_gemm_time(unsigned long long* n, double* ms);
 
 struct Ctx {
     int device = 0;

@@ -34,13 +34,21 @@ __device__ __forceinline__ T source(int forcing, T v1, T v2, T v3, T f) {
 
 constexpr int kPre = 8;  // prefetch depth of the sweeps (nodes)
 
+// 4-byte asynchronous copy global -> shared (completes through cp.async.wait_group)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* __restrict__ h,
                                                  const T* __restrict__ nu1, const T* __restrict__ vel,
                                                  const T* __restrict__ feq,
                                                  const SweepJobDev* __restrict__ jobs,
                                                  const int* __restrict__ active,
-                                                 const double* __restrict__ coef, int nv, int staged) {
+                                                 const double* __restrict__ coef, int nv, int staged,
+                                                 int async_rhs) {
     extern __shared__ __align__(16) unsigned char sweep_smem[];
     const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
     const int half = nv / 2, n2 = nv * nv;
@@ -70,6 +78,45 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
     const T Sn = source<T>(jb.forcing, vel[nv - 1 - i1p], w2, w3, feq[vneg]);
     T hm1 = T(0), hm2 = T(0);
     o[vpos] = T(0);
+    if constexpr (sizeof(T) == 4) {
+        if (async_rhs) {
+            // every right-hand side of this thread's two columns goes in flight at once
+            // (cp.async, 4 bytes each, after the staged coefficients); the thread waits for its
+            // own copies only, so no barrier is needed.  Layout [column][node][thread].
+            T* cp = sc + 6 * n;
+            T* cn = cp + (long)n * blockDim.x;
+            const int tx = threadIdx.x;
+            for (int i = 1; i < n; ++i) cp_async4(cp + i * blockDim.x + tx, r + (long)i * n3 + vpos);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            for (int i = 0; i + 1 < n; ++i) cp_async4(cn + i * blockDim.x + tx, r + (long)i * n3 + vneg);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+#pragma unroll 4
+            for (int i = 1; i < n; ++i) {
+                const T inv = T(1) / (nup + v1 * C(0, i));
+                const T acc = (cp[i * blockDim.x + tx] + Sp) - v1 * (C(1, i) * hm1 + C(2, i) * hm2);
+                const T hi = acc * inv;
+                o[(long)i * n3 + vpos] = hi;
+                hm2 = hm1;
+                hm1 = hi;
+            }
+            const T u = -vel[nv - 1 - i1p];
+            const T nun = d * nu1[vneg];
+            T g1 = hm1, g2 = hm2;
+            o[(long)(n - 1) * n3 + vneg] = hm1;
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll 4
+            for (int i = n - 2; i >= 0; --i) {
+                const T inv = T(1) / (nun + u * C(3, i));
+                const T acc = (cn[i * blockDim.x + tx] + Sn) - u * (C(4, i) * g1 + C(5, i) * g2);
+                const T hi = acc * inv;
+                o[(long)i * n3 + vneg] = hi;
+                g2 = g1;
+                g1 = hi;
+            }
+            return;
+        }
+    }
     // the right-hand sides of the next kPre nodes are in flight while a node is solved, and
     // their reciprocal diagonals are formed off the march's dependent chain (which is then
     // three multiply-adds per node)
@@ -488,10 +535,24 @@ template <typename T>
 void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T* rhs, T* h,
                   const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s) {
     if (njobs <= 0) return;
-    // float sweeps stage the coefficients when the largest job's fit in 48 KB
+    // float sweeps stage the coefficients when the largest job's fit in 48 KB; 1D float sweeps
+    // also stage every right-hand side of their columns when that fits in 200 KB
     const size_t sbytes = (size_t)max_coef * sizeof(T);
     const int staged = (sizeof(T) == 4 && max_coef > 0 && sbytes <= 48 * 1024) ? 1 : 0;
-    const size_t smem = staged ? sbytes : 0;
+    size_t smem = staged ? sbytes : 0;
+    int async_rhs = 0;
+    if (dim == 1 && staged) {
+        const size_t full = sbytes + 2 * (size_t)(max_coef / 6) * 128 * sizeof(T);
+        if (full <= 200 * 1024) {
+            async_rhs = 1;
+            smem = full;
+            static bool attr = false;  // opt-in shared memory beyond 48 KB (float instance)
+            if (!attr) {
+                cudaFuncSetAttribute(k_sweep1d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                attr = true;
+            }
+        }
+    }
     g_launches += 1;
     const int nv = t.nv;
     const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
@@ -500,7 +561,7 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
     if (dim == 1) {
         const int nt = nv / 2 * nv * nv;
         dim3 g((nt + 127) / 128, njobs);
-        k_sweep1d<T><<<g, 128, smem, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv, staged);
+        k_sweep1d<T><<<g, 128, smem, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv, staged, async_rhs);
     } else {
         const int nt = nv * nv * nv;
         dim3 g((nt + 127) / 128, njobs);

@@ -37,13 +37,17 @@ class Result(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
-                ("cell_l_evals", C.c_uint64)]
+                ("cell_l_evals", C.c_uint64), ("dense_gemm_timed", C.c_uint64), ("dense_gemm_ms", C.c_double)]
 
 
 def stats():
     s = Stats()
     lib().lbe_get_stats(C.byref(s))
     return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+def set_kernel_timing(on):
+    lib().lbe_set_kernel_timing(1 if on else 0)
 
 
 _lib = None
