@@ -35,9 +35,9 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 
 
 PRECISIONS = {"fp32": lambda L: L.FP32, "fp64": lambda L: L.FP64, "bf16": lambda L: L.BF16_REFINED,
-              "fp32r": lambda L: L.FP32_REFINED}
+              "fp32r": lambda L: L.FP32_REFINED, "df32": lambda L: L.DF32}
 DTYPES = {"fp32": "f32", "fp64": "f64", "bf16": "bf16/f32 inner + f64 residual",
-          "fp32r": "f32 inner + f64 residual"}
+          "fp32r": "f32 inner + f64 residual", "df32": "f32 pairs (operator only)"}
 
 
 def load_peaks():
@@ -218,7 +218,7 @@ def run_op_only(args):
     pbs = workload_problems(lbe, args.workload, prec, args.eps)
     nv, M = pbs[0].nv, pbs[0].M
     cells = sum(lbe.cells_of(p) for p in pbs)
-    dt = torch.float64 if prec == lbe.FP64 else torch.float32
+    dt = torch.float64 if prec in (lbe.FP64, lbe.DF32) else torch.float32
     h = W.random_h(cells, nv, 6.0, seed=11)
     h = 0.5 * (h + h[:, :, ::-1, :])
     hd = torch.tensor(h, device="cuda", dtype=dt)

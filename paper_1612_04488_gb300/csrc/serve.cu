@@ -72,6 +72,7 @@ struct Bucket {
     // the FP32 operator of the increment (see Batch)
     bool inc = false;
     DevBuf base_h, base_lp, base_lh, inc_h, inc_lp, inc_lh, inc_scratch;
+    lbe_status failed = LBE_OK;  // an operator launch of the last iteration failed
 };
 
 size_t coef_len(const SweepGeom& g) {
@@ -107,10 +108,10 @@ void give_range(Bucket& b, long off, long n) {
     b.free_ranges.swap(m);
 }
 
-std::string bucket_key(const lbe_problem& pb, int prec, bool inc) {
+std::string bucket_key(const lbe_problem& pb, int prec, bool inc, bool tc) {
     char k[160];
     const double R = pb.R > 0 ? pb.R : default_R(pb.vmax);
-    snprintf(k, sizeof k, "%d/%.17g/%d/%.17g/%d/%d", pb.nv, pb.vmax, pb.M, R, prec, inc ? 1 : 0);
+    snprintf(k, sizeof k, "%d/%.17g/%d/%.17g/%d/%d/%d", pb.nv, pb.vmax, pb.M, R, prec, inc ? 1 : 0, tc ? 1 : 0);
     return k;
 }
 
@@ -284,7 +285,7 @@ void slot_set_correction(Bucket& b, int s) {
     Batch& B = b.B;
     B.sj[s].forcing = kForcingNone;
     B.ij[s].ndsig = 0.0;
-    B.ij[s].eps = 1e-6;
+    B.ij[s].eps = 1e-4;
     B.ij[s].crit = 1;
     B.ij[s].max_iter = 30;
     B.hstate[s] = JobState{};
@@ -311,8 +312,10 @@ static Bucket* find_bucket(Service& sv, const std::string& key) {
     return nullptr;
 }
 
-static Bucket* get_bucket(Service& sv, Ctx* c, const lbe_problem& pb, int prec, bool inc, lbe_status* st) {
-    const std::string key = bucket_key(pb, prec, inc);
+// tc: an FP32 bucket whose collision operator is the tensor-core GEMM (BF16-refined requests)
+static Bucket* get_bucket(Service& sv, Ctx* c, const lbe_problem& pb, int prec, bool inc, lbe_status* st,
+                          bool tc = false) {
+    const std::string key = bucket_key(pb, prec, inc, tc);
     Bucket* b = find_bucket(sv, key);
     *st = LBE_OK;
     if (b) return b;
@@ -324,6 +327,7 @@ static Bucket* get_bucket(Service& sv, Ctx* c, const lbe_problem& pb, int prec, 
         arena_release(c, nb->arena);
         return nullptr;
     }
+    nb->B.use_tc = tc;
     b = nb.get();
     sv.buckets.push_back(std::move(nb));
     return b;
@@ -383,7 +387,8 @@ static void service_main(Ctx* c) {
             const bool refined = pb.precision == LBE_FP32_REFINED || pb.precision == LBE_BF16_REFINED;
             const int cells = lbe_problem_cells(&pb);
             lbe_status st;
-            Bucket* F = get_bucket(sv, c, pb, refined ? LBE_FP32 : pb.precision, false, &st);
+            const bool tc = pb.precision == LBE_BF16_REFINED && pb.M >= 8;
+            Bucket* F = get_bucket(sv, c, pb, refined ? LBE_FP32 : pb.precision, false, &st, tc);
             Bucket* D = (F && refined) ? get_bucket(sv, c, pb, LBE_FP64, true, &st) : nullptr;
             if (!F || (refined && !D)) {
                 if (live.empty()) {  // nothing will free memory: fail the request
@@ -443,7 +448,13 @@ static void service_main(Ctx* c) {
                 batch_iterate<float>(b.B);
             ran.push_back(&b);
         }
-        for (Bucket* b : ran) cudaStreamSynchronize(b->stream);
+        for (Bucket* b : ran) {
+            lbe_status st = cuda_status(c, cudaStreamSynchronize(b->stream), "service iterate");
+            if (st == LBE_OK && b->B.use_tc) st = tc_check(c, b->B.t);
+            if (st == LBE_OK) st = b->B.op_status;
+            b->B.op_status = LBE_OK;
+            if (st != LBE_OK) b->failed = st;
+        }
         // ---- retire finished problems, advance refined ones ------------------------------
         const double t = now_s();
         std::vector<std::unique_ptr<SJob>> keep;
@@ -451,6 +462,20 @@ static void service_main(Ctx* c) {
             SJob* sj = up.get();
             const long n3 = (long)sj->j->pb.nv * sj->j->pb.nv * sj->j->pb.nv;
             bool done = false;
+            const lbe_status bad = (sj->F && sj->F->failed != LBE_OK)   ? sj->F->failed
+                                   : (sj->D && sj->D->failed != LBE_OK) ? sj->D->failed
+                                                                        : LBE_OK;
+            if (bad != LBE_OK) {  // a launch of one of its buckets failed: the request fails
+                {
+                    std::lock_guard<std::mutex> lk(c->mu);
+                    sj->j->res = lbe_result{};
+                    sj->j->res.status = bad;
+                    sj->j->done = 1;
+                }
+                if (sj->F) release(sj->F, sj->fs);
+                if (sj->D) release(sj->D, sj->ds);
+                continue;
+            }
             if (sj->phase == 0) {
                 const JobState& js = sj->F->B.hstate[sj->fs];
                 if (std::find(sj->F->B.active.begin(), sj->F->B.active.end(), sj->fs) != sj->F->B.active.end() &&
@@ -525,6 +550,7 @@ static void service_main(Ctx* c) {
             if (!done) keep.push_back(std::move(up));
         }
         live.swap(keep);
+        for (auto& b : sv.buckets) b->failed = LBE_OK;  // its requests have been failed
     }
     for (auto& b : sv.buckets) {
         cudaStreamSynchronize(b->stream);

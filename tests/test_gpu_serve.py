@@ -69,10 +69,11 @@ def test_admission_with_few_slots_and_arrivals_in_flight(ctx):
     assert all(r.status == lbe.OK for r in res), [(r.status, r.iters, r.last_rel_change) for r in res]
 
 
-def test_refined_requests_reach_fp64(ctx):
+@pytest.mark.parametrize("prec", [lbe.FP32_REFINED, lbe.BF16_REFINED])
+def test_refined_requests_reach_fp64(ctx, prec):
     pbs = mix(lbe.FP64)
     ref = [ctx.solve(p)[0] for p in pbs]
-    rp = mix(lbe.FP32_REFINED)
+    rp = mix(prec)
     got = wait_all(ctx, [ctx.submit(p) for p in rp])
     for r, g in zip(ref, got):
         assert g.status == lbe.OK, (g.status, g.iters, g.refinements, g.mass_flow, r.mass_flow)
