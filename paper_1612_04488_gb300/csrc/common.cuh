@@ -112,14 +112,36 @@ __device__ __forceinline__ void dft_line(T (&re)[N], T (&im)[N]) {
             for (int i = 0; i < N; i += len) {
 #pragma unroll
                 for (int j = 0; j < len / 2; ++j) {
-                    const auto w = tw<T, N>(j * (N / len));
-                    const T wr = w.x, wi = INV ? -w.y : w.y;
+                    // m is a compile-time constant after unrolling: W^0 = 1, W^(N/4) = -i
+                    // (+i inverse) are exact swaps, W^(N/8) and W^(3N/8) = (+-1 - i) sqrt(1/2)
+                    // take two real products; the rest is the general complex product
+                    const int m = j * (N / len);
                     const int a = i + j, b = i + j + len / 2;
                     T xr, xi;
-                    if (j == 0) {
+                    if (m == 0) {
                         xr = re[b];
                         xi = im[b];
+                    } else if (4 * m == N) {
+                        if (INV) {
+                            xr = -im[b];
+                            xi = re[b];
+                        } else {
+                            xr = im[b];
+                            xi = -re[b];
+                        }
+                    } else if (8 * m == N || 8 * m == 3 * N) {
+                        const T c = tw<T, N>(N / 8).x;  // sqrt(1/2)
+                        const T s = re[b] + im[b], d = im[b] - re[b];
+                        if (8 * m == N) {  // forward (1 - i) c, inverse (1 + i) c
+                            xr = INV ? -(c * d) : c * s;
+                            xi = INV ? c * s : c * d;
+                        } else {           // forward (-1 - i) c, inverse (-1 + i) c
+                            xr = INV ? -(c * s) : c * d;
+                            xi = INV ? -(c * d) : -(c * s);
+                        }
                     } else {
+                        const auto w = tw<T, N>(m);
+                        const T wr = w.x, wi = INV ? -w.y : w.y;
                         xr = re[b] * wr - im[b] * wi;
                         xi = re[b] * wi + im[b] * wr;
                     }

@@ -15,6 +15,7 @@
 // multiplier and the i3, i2 axes per plane; k_inv_last4 transforms along i1 (coalesced
 // across lanes), sums the directions over four warps and writes the outputs.  Every lane
 // owns one 1D line in registers (dft_line in common.cuh).
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -376,6 +377,9 @@ void run_fsm(const DevTables& t, int cells, const double* delta, const TH* h, T*
     const long N3 = (long)N * N * N;
     g_launches += 2;
     g_levals += cells;
+    // the scratch holds chunk * (M + 1) inverse-transform volumes; the parity-reduced forms
+    // use P of them per cell, so the same scratch (and L2 footprint) takes more cells per chunk
+    chunk = std::min(cells, std::max(chunk, chunk * (t.M + 1) / P));
     for (int c0 = 0; c0 < cells; c0 += chunk) {
         g_launches += 2;
         const int cc = (cells - c0 < chunk) ? cells - c0 : chunk;
