@@ -172,7 +172,8 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R,
  * orbit (a quarter or half of the directions).  LBE_BF16_REFINED: the operator as a dense
  * (nv^3/4 or nv^3/2)-square matrix at delta = 1, built once per grid from the DF32
  * transforms, applied to all cells as one tcgen05 GEMM with bfloat16 hi/lo operands and FP32
- * accumulation (relative error about 1e-5 of the scale); h, L+ h, L h are float.  Needs
+ * accumulation (relative error about 1e-5 of the scale); h, L+ h, L h are float, h 8-byte
+ * aligned.  Needs
  * M >= 8.  Lplus_dev / L_dev may be NULL.  Returns after the work is queued on `stream`
  * (the tensor-core form synchronises the stream). */
 lbe_status lbe_apply_L_sym(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_precision precision,

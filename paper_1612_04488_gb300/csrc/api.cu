@@ -742,8 +742,10 @@ lbe_status lbe_apply_L_sym(lbe_ctx* ctx, int nv, double vmax, int M, double R, l
     void* p = scr ? arena_take(ctx->apply_arena, scr) : nullptr;
     void* lp = Lplus_dev ? Lplus_dev : arena_take(ctx->apply_arena, vol);
     void* lo = L_dev ? L_dev : arena_take(ctx->apply_arena, vol);
-    if (precision == LBE_BF16_REFINED)
+    if (precision == LBE_BF16_REFINED) {
+        if ((uintptr_t)h_dev % 8 != 0) return bad_arg(ctx, "h_dev must be 8-byte aligned for the tensor-core form");
         return tc_apply_sym(ctx, t, parity, cells, delta_dev, (const float*)h_dev, (float*)lp, (float*)lo, s);
+    }
     if (precision == LBE_FP64)
         st = fsm_cc_apply<double>(*t, cells, delta_dev, (const double*)h_dev, (double*)lp, (double*)lo, p, chunk, s,
                                   parity);

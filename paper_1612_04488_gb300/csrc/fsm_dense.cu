@@ -272,18 +272,27 @@ __device__ __forceinline__ int orbit_of(int v, int nv, int mode, float* sign) {
     return (i1 * nv + i2) * H + j3;
 }
 
-// x_hi / x_lo [cell][q] from h (float)
-__global__ void k_gather_split(const float* __restrict__ h, __nv_bfloat16* __restrict__ xh,
-                               __nv_bfloat16* __restrict__ xl, int cells, int nv, int nr, int mode) {
-    const long total = (long)cells * nr;
-    const long n3 = (long)nv * nv * nv;
+// x_hi / x_lo [cell][q] from h (float) with the grid and parity known at compile time: each
+// thread takes two neighbouring representatives (i3, i3 + 1; H is even), one float2 load and
+// one bf16x2 store per operand.
+template <int NV, int MODE>
+__global__ void __launch_bounds__(256) k_gather_split_t(const float* __restrict__ h, __nv_bfloat162* __restrict__ xh,
+                                                        __nv_bfloat162* __restrict__ xl, int cells) {
+    constexpr int H = NV / 2;
+    constexpr int NR = MODE == 2 ? NV * H * H : NV * NV * H;
+    constexpr long N3 = (long)NV * NV * NV;
+    const long total = (long)cells * (NR / 2);
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-        const long c = k / nr;
-        const int q = (int)(k % nr);
-        const float x = h[c * n3 + rep_full(q, nv, mode)];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        const long c = k / (NR / 2);
+        const int q = 2 * (int)(k % (NR / 2));
+        const int i3 = q % H;
+        const int i2 = MODE == 2 ? (q / H) % H : (q / H) % NV;
+        const int i1 = MODE == 2 ? q / (H * H) : q / (NV * H);
+        const float2 x = *reinterpret_cast<const float2*>(h + c * N3 + (i1 * NV + i2) * NV + i3);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(x.x, x.y);
+        const float2 hf = __bfloat1622float2(hi);
         xh[k] = hi;
-        xl[k] = __float2bfloat16_rn(x - __bfloat162float(hi));
+        xl[k] = __floats2bfloat162_rn(x.x - hf.x, x.y - hf.y);
     }
 }
 
@@ -573,7 +582,17 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         c->last_error = "cuTensorMapEncodeTiled failed for the cell operand";
         return LBE_INTERNAL;
     }
-    k_gather_split<<<1024, 256, 0, s>>>(h, xh, xl, cells, nv, nr, mode);
+    {
+        auto* xh2 = reinterpret_cast<__nv_bfloat162*>(xh);
+        auto* xl2 = reinterpret_cast<__nv_bfloat162*>(xl);
+        const bool p2 = mode == 2;
+        switch (nv) {
+            case 8: (p2 ? k_gather_split_t<8, 2> : k_gather_split_t<8, 1>)<<<1216, 256, 0, s>>>(h, xh2, xl2, cells); break;
+            case 16: (p2 ? k_gather_split_t<16, 2> : k_gather_split_t<16, 1>)<<<1216, 256, 0, s>>>(h, xh2, xl2, cells); break;
+            case 24: (p2 ? k_gather_split_t<24, 2> : k_gather_split_t<24, 1>)<<<1216, 256, 0, s>>>(h, xh2, xl2, cells); break;
+            default: (p2 ? k_gather_split_t<32, 2> : k_gather_split_t<32, 1>)<<<1216, 256, 0, s>>>(h, xh2, xl2, cells); break;
+        }
+    }
     // optional event timing of the GEMM alone (public synchronous calls only)
     cudaEvent_t ev[2] = {nullptr, nullptr};
     const bool timed = sync && g_time_kernels.load() != 0 && cudaEventCreate(&ev[0]) == cudaSuccess &&

@@ -259,8 +259,20 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         cudaMemcpyAsync(O.act.p, active.data(), na * sizeof(int), cudaMemcpyHostToDevice, s);
         g_h2d += na * sizeof(int);
         // flow rates of the current iterate, then keep a copy of it
-        for (int j : active) launch_moments<double>(*O.t, O.cell_off[j], O.sj[j].ncell, O.h.as<double>(),
-                                                   O.mom.as<double>(), s);
+        {  // one launch per contiguous run of active problems' cells
+            std::vector<std::pair<long, long>> runs;
+            for (int j : active) runs.push_back({O.cell_off[j], (long)O.sj[j].ncell});
+            std::sort(runs.begin(), runs.end());
+            std::vector<std::pair<long, long>> merged;
+            for (auto& r : runs) {
+                if (!merged.empty() && merged.back().first + merged.back().second == r.first)
+                    merged.back().second += r.second;
+                else
+                    merged.push_back(r);
+            }
+            for (auto& r : merged)
+                launch_moments<double>(*O.t, r.first, (int)r.second, O.h.as<double>(), O.mom.as<double>(), s);
+        }
         k_set_rates<<<na, 32, 0, s>>>(O.ijobs.as<SisJobDev>(), O.act.as<int>(), O.mom.as<double>(),
                                       O.coef.as<double>(), O.states.as<JobState>());
         k_copy64<<<dim3(152, na), blk, 0, s>>>(O.h.as<double>(), h_old, O.sjobs.as<SweepJobDev>(),

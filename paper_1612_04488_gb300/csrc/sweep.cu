@@ -269,8 +269,9 @@ template <> struct Acc<float> {
 
 // mom[cell][5] = sum_v {v3, (|v|^2-5/2) v3, (2 v1^2-1) v3, (2 v2^2-1) v3, 2 v1 v2 v3} h dv^3
 // One block of 8 NV threads per cell: thread t owns i3 = t % NV and the rows i2 = t/NV + 8k.
-// v3 is fixed per thread, so it is factored out: the thread sums h, (v1^2 + v2^2) h, v1^2 h,
-// v2^2 h and v1 v2 h, and combines them with v3 once (five multiply-adds per value).
+// v3 is fixed per thread and v2 per row, so they are factored out: per row the thread sums
+// h, v1^2 h and v1 h over i1 and combines them with v2 and v3 once (the FP64 pipe is the
+// limit of the double instance).
 template <typename T, int NV>
 __global__ void __launch_bounds__(8 * NV) k_moments(const T* __restrict__ h, const T* __restrict__ vel,
                                                     double dv3, long cell0, double* __restrict__ mom) {
@@ -286,8 +287,10 @@ __global__ void __launch_bounds__(8 * NV) k_moments(const T* __restrict__ h, con
         v2v[k] = vel[r0 + 8 * k];
         v2s[k] = v2v[k] * v2v[k];
     }
+    // per row i2 the thread sums h, v1^2 h and v1 h over i1 (three operations per value);
+    // the v2 and v3 factors are applied once afterwards
     const T* hc = h + cell * n3 + i3;
-    Acc<T> a[5];
+    Acc<T> S0[R], S1[R], S4[R];
     for (int i1 = 0; i1 < NV; ++i1) {
         const T v1 = vel[i1], v1s = v1 * v1;
         T x[R];
@@ -295,16 +298,23 @@ __global__ void __launch_bounds__(8 * NV) k_moments(const T* __restrict__ h, con
         for (int k = 0; k < R; ++k) x[k] = hc[((long)i1 * NV + r0 + 8 * k) * NV];
 #pragma unroll
         for (int k = 0; k < R; ++k) {
-            a[0].add(x[k]);
-            a[1].add((v1s + v2s[k]) * x[k]);
-            a[2].add(v1s * x[k]);
-            a[3].add(v2s[k] * x[k]);
-            a[4].add(v1 * v2v[k] * x[k]);
+            S0[k].add(x[k]);
+            S1[k].add(v1s * x[k]);
+            S4[k].add(v1 * x[k]);
         }
     }
-    const double w3 = (double)v3, s0 = a[0].value();
-    double s[5] = {w3 * s0, w3 * (a[1].value() + (w3 * w3 - 2.5) * s0), w3 * (2.0 * a[2].value() - s0),
-                   w3 * (2.0 * a[3].value() - s0), 2.0 * w3 * a[4].value()};
+    double a0 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;  // sums of h, v1^2 h, v2^2 h, v1 v2 h
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const double s0 = S0[k].value();
+        a0 += s0;
+        a2 += S1[k].value();
+        a3 += (double)v2s[k] * s0;
+        a4 += (double)v2v[k] * S4[k].value();
+    }
+    const double w3 = (double)v3;
+    double s[5] = {w3 * a0, w3 * (a2 + a3 + (w3 * w3 - 2.5) * a0), w3 * (2.0 * a2 - a0), w3 * (2.0 * a3 - a0),
+                   2.0 * w3 * a4};
     block_reduce<5>(s, red);
     if (threadIdx.x == 0)
         for (int k = 0; k < 5; ++k) mom[cell * 5 + k] = s[k] * dv3;
