@@ -508,7 +508,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "solves_per_step": nsolve, "cells": cells, "nv": nv, "M": M,
-                   "eps": args.eps, "l2": "inputs larger than L2 (424 MB working set)",
+                   "eps": args.eps,
+                   "l2": "inputs larger than L2 (h, L+h, h half-step: %d MB in FP32)" % (3 * cells * nv ** 3 * 4 // 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single"},
         "latency_ms": {"p50": float(np.percentile(solve_ms, 50)), "p99": float(np.percentile(solve_ms, 99)),
                        "what": "per solve, batch start to that solve's convergence"},
