@@ -200,6 +200,22 @@ lbe_status lbe_apply_L_noalloc(lbe_ctx* ctx, int nv, double vmax, int M, double 
                                lbe_precision precision, int cells, const double* delta_dev,
                                const void* h_dev, void* Lplus_dev, void* L_dev, void* stream);
 
+/* Convergence factor of the CIS or the SIS for one Fourier mode (Sec. 2.3): a system periodic
+ * in x1 with the mode exp(2 pi i x1), whose error obeys, per iteration, the CIS map
+ * e <- L+(e) / (nu_eq + 2 pi i v1) (Eq. conv_iteration), or for the SIS that half step
+ * followed by U3 = (-2 pi i A1 - 4 pi^2 A2) / (4 pi^2) with A1 = 2 int v1 v3 (L e + N delta e),
+ * A2 = int (2 v1^2 - 1) v3 e_half, and the correction of Eq. guided.  Runs the power iteration
+ * e_{k+1} = P map(e_k) / |e_k|, P the projection onto functions odd in v3 (the parity of the
+ * plate and duct errors; rounding would otherwise seed even, density-type modes that the SIS
+ * does not accelerate), from e0 (host, double [2][nv^3]: real part, then imaginary
+ * part) with the FP64 collision operator, and writes ratios[k] = |e_{k+1}| (host, double
+ * [iters]); the ratios converge to omega, the modulus of the dominant eigenvalue (the paper
+ * fits U3(k) = U_inf + C exp(-lambda k), omega = exp(-lambda)).  N <= 0 selects 1.25.  The
+ * start vector is the caller's, so runs are reproducible.  Synchronous on the context's
+ * stream. */
+lbe_status lbe_fourier_omega(lbe_ctx* ctx, int nv, double vmax, int M, double R, double delta, double N,
+                             lbe_scheme scheme, int iters, const double* e0, double* ratios);
+
 /* Transport sweep of one problem (steps A5-A6): solves nu_eq h + v.grad h = rhs with the
  * problem's geometry and delta.  rhs_dev, h_dev: [cells][nv^3], double for FP64 else
  * float.  mom_dev (double [cells][5], may be NULL): U3, q3, W1 = F201/4, W2 = F021/4,

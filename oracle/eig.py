@@ -60,3 +60,19 @@ def omega(step, F, iters=60, seed=0):
         e = step(e) / n0
         r = np.sqrt(np.sum(np.abs(e) ** 2))
     return float(r)
+
+
+def power_ratios(step, e0, iters, odd_v3=True):
+    """Power iteration from a given start vector: e_{k+1} = P step(e_k) / |e_k|, returning the
+    ratios |e_{k+1}| (they converge to the modulus of the dominant eigenvalue).  With odd_v3,
+    P projects onto functions odd in v3 (the parity of the plate and duct errors), so that
+    rounding cannot seed the even, density-type modes that the SIS does not accelerate."""
+    e = np.asarray(e0).astype(complex)
+    out = []
+    for _ in range(iters):
+        n0 = np.sqrt(np.sum(np.abs(e) ** 2))
+        e = step(e) / n0
+        if odd_v3:
+            e = 0.5 * (e - e[..., ::-1])
+        out.append(float(np.sqrt(np.sum(np.abs(e) ** 2))))
+    return np.array(out)

@@ -72,6 +72,7 @@ def lib():
         L.lbe_apply_L.argtypes = [vp, ip, C.c_double, ip, C.c_double, ip, ip, vp, vp, vp, vp, vp, vp, vp]
         L.lbe_sweep.argtypes = [vp, C.POINTER(Problem), vp, vp, vp, vp]
         L.lbe_diffusion.argtypes = [vp, C.POINTER(Problem), dp, dp, dp, dp, dp, dp, dp]
+        L.lbe_fourier_omega.argtypes = [vp, ip, C.c_double, ip, C.c_double, C.c_double, C.c_double, ip, ip, dp, dp]
         L.lbe_submit.argtypes = [vp, C.POINTER(Problem), C.POINTER(C.c_uint64)]
         L.lbe_poll.argtypes = [vp, C.c_uint64, C.POINTER(Result), C.POINTER(C.c_int)]
         L.lbe_set_max_active.argtypes = [vp, ip]
@@ -171,6 +172,19 @@ class Context:
 
     def sweep(self, pb, rhs_ptr, h_ptr, mom_ptr=None, stream=None):
         return self.check(lib().lbe_sweep(self.h, C.byref(pb), rhs_ptr, h_ptr, mom_ptr, stream))
+
+    def fourier_omega(self, nv, vmax, M, R, delta, N, scheme, iters, e0):
+        """Power-iteration ratios of the CIS / SIS Fourier-mode error map (lbe_fourier_omega);
+        e0: complex or real array of nv^3 values (the start vector)."""
+        e0 = np.asarray(e0).reshape(-1)
+        buf = np.ascontiguousarray(np.concatenate([e0.real, e0.imag if np.iscomplexobj(e0) else 0 * e0.real]),
+                                   dtype=np.float64)
+        out = np.zeros(iters)
+        st = lib().lbe_fourier_omega(self.h, nv, vmax, M, R, delta, N, scheme, iters,
+                                     buf.ctypes.data_as(C.POINTER(C.c_double)),
+                                     out.ctypes.data_as(C.POINTER(C.c_double)))
+        self.check(st)
+        return out
 
     def diffusion(self, pb, Uh, W1, W2, X12, G1, G2):
         n = cells_of(pb)

@@ -27,6 +27,17 @@ def random_h(cells, nv, vmax, seed, odd_v3=True):
     return h
 
 
+
+def fourier_start(nv, vmax, seed):
+    """Start vector of the Fourier-mode power iteration: v3 exp(-|v|^2) (1 + 0.3 n) with n a
+    standard-normal field even in v3, so the vector is odd in v3 (real, shape (nv, nv, nv))."""
+    rng = np.random.default_rng(seed)
+    v = -vmax + (np.arange(nv) + 0.5) * (2.0 * vmax / nv)
+    V1, V2, V3 = np.meshgrid(v, v, v, indexing="ij")
+    n = rng.standard_normal((nv, nv, nv))
+    n = 0.5 * (n + n[..., ::-1])
+    return V3 * np.exp(-(V1 * V1 + V2 * V2 + V3 * V3)) * (1.0 + 0.3 * n)
+
 # Plates, 16^3, 20 uniform sections, delta = 1, M = 16 (small case the oracle finishes in
 # seconds).
 PLATES_16 = dict(dim=1, ns=20, grid_kind=0, delta=1.0, nv=16, vmax=6.0, M=16)

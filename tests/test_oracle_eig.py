@@ -32,3 +32,14 @@ def test_P12_lbe_cis_vs_sis_eigenvalues(F16):
     assert om[100.0][0] > 0.99
     assert om[10.0][1] < 0.5 * om[10.0][0]
     assert 0.45 < om[100.0][1] < 0.7
+
+
+def test_power_ratios_from_given_start_reach_bgk_closed_form(F16):
+    """The start-vector form of the power iteration (used to compare with the GPU driver)
+    converges to the same BGK closed-form eigenvalue as P11."""
+    from paper_1612_04488_gb300 import workloads
+    d = 10.0
+    ex = quad(lambda v: d * d * np.exp(-v * v) / np.sqrt(np.pi) / (d * d + 4 * np.pi ** 2 * v * v),
+              -np.inf, np.inf)[0]
+    r = eig.power_ratios(lambda e: eig.bgk_cis_map(F16, e, d), workloads.fourier_start(16, 6.0, seed=2), 15)
+    assert abs(r[-1] - ex) < 2e-3 * ex, (r[-1], ex)
