@@ -187,7 +187,7 @@ def run_reference(args):
     value = float(np.median(vals))
     line = {
         "impl": "reference", "metric": "SIS solves/s at 1e-6 flow-rate error", "value": value,
-        "unit": "solves/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * t_wall / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "iterations_per_solve": iters,

@@ -199,4 +199,35 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], double* smem /*[32
     __syncthreads();
 }
 
+// The same fixed-tree block reduction in double-float arithmetic: FP64-class sums that stay
+// on the FP32 pipes (for kernels whose data are float).
+template <int NV>
+__device__ __forceinline__ void block_reduce_df(dfloat (&v)[NV], dfloat* smem /*[32*NV]*/) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const dfloat w(__shfl_down_sync(0xffffffffu, v[k].hi, o), __shfl_down_sync(0xffffffffu, v[k].lo, o));
+            v[k] = v[k] + w;
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) smem[warp * NV + k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            dfloat s = (lane < nw) ? smem[lane * NV + k] : dfloat(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const dfloat w(__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o));
+                s = s + w;
+            }
+            v[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
 }  // namespace lbe

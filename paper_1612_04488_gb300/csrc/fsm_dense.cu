@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(8 * NV) k_expand_g(const float* __restrict__ Y
                                                      float* __restrict__ Lplus, float* __restrict__ Lout,
                                                      double* __restrict__ G, int nr, double dv3, int cells, int ks) {
     extern __shared__ float sY[];
-    __shared__ double red[32 * 2];
+    __shared__ dfloat redx[32 * 2];
     constexpr int H = NV / 2;
     constexpr long n3 = (long)NV * NV * NV;
     const long c = blockIdx.x;
@@ -366,11 +366,11 @@ __global__ void __launch_bounds__(8 * NV) k_expand_g(const float* __restrict__ Y
             kahan(a1, c1, vel[i2] * t);
         }
     }
-    double sm[2] = {(double)a0 - (double)c0, (double)a1 - (double)c1};
-    block_reduce<2>(sm, red);
+    dfloat sm[2] = {df_fast2sum(a0, -c0), df_fast2sum(a1, -c1)};  // reduced in double-float
+    block_reduce_df<2>(sm, redx);
     if (threadIdx.x == 0) {
-        G[2 * c + 0] = 2.0 * sm[0] * dv3;
-        G[2 * c + 1] = 2.0 * sm[1] * dv3;
+        G[2 * c + 0] = 2.0 * (double)sm[0] * dv3;
+        G[2 * c + 1] = 2.0 * (double)sm[1] * dv3;
     }
 }
 

@@ -265,6 +265,7 @@ template <> struct Acc<float> {
         s = t;
     }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+    __device__ __forceinline__ dfloat pair() const { return df_fast2sum(s, -c); }  // s - c
 };
 
 // mom[cell][5] = sum_v {v3, (|v|^2-5/2) v3, (2 v1^2-1) v3, (2 v2^2-1) v3, 2 v1 v2 v3} h dv^3
@@ -303,21 +304,42 @@ __global__ void __launch_bounds__(8 * NV) k_moments(const T* __restrict__ h, con
             S4[k].add(v1 * x[k]);
         }
     }
-    double a0 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;  // sums of h, v1^2 h, v2^2 h, v1 v2 h
+    if constexpr (sizeof(T) == 4) {
+        // float data: combine and reduce in double-float (the FP64 pipe is a small fraction of
+        // the FP32 one here, and a double tail would cost more than the sums themselves)
+        __shared__ dfloat redx[32 * 5];
+        dfloat a0(0), a2(0), a3(0), a4(0);  // sums of h, v1^2 h, v2^2 h, v1 v2 h
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const double s0 = S0[k].value();
-        a0 += s0;
-        a2 += S1[k].value();
-        a3 += (double)v2s[k] * s0;
-        a4 += (double)v2v[k] * S4[k].value();
+        for (int k = 0; k < R; ++k) {
+            const dfloat s0 = S0[k].pair(), s4 = S4[k].pair();
+            a0 = a0 + s0;
+            a2 = a2 + S1[k].pair();
+            a3 = a3 + dfloat((float)v2s[k], 0.f) * s0;
+            a4 = a4 + dfloat((float)v2v[k], 0.f) * s4;
+        }
+        const dfloat w3((float)v3, 0.f), w3s = w3 * w3;
+        dfloat s[5] = {w3 * a0, w3 * ((a2 + a3) + (w3s - dfloat(2.5f, 0.f)) * a0), w3 * ((a2 + a2) - a0),
+                       w3 * ((a3 + a3) - a0), (w3 + w3) * a4};
+        block_reduce_df<5>(s, redx);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 5; ++k) mom[cell * 5 + k] = (double)s[k] * dv3;
+    } else {
+        double a0 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;  // sums of h, v1^2 h, v2^2 h, v1 v2 h
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const double s0 = S0[k].value();
+            a0 += s0;
+            a2 += S1[k].value();
+            a3 += (double)v2s[k] * s0;
+            a4 += (double)v2v[k] * S4[k].value();
+        }
+        const double w3 = (double)v3;
+        double s[5] = {w3 * a0, w3 * (a2 + a3 + (w3 * w3 - 2.5) * a0), w3 * (2.0 * a2 - a0),
+                       w3 * (2.0 * a3 - a0), 2.0 * w3 * a4};
+        block_reduce<5>(s, red);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 5; ++k) mom[cell * 5 + k] = s[k] * dv3;
     }
-    const double w3 = (double)v3;
-    double s[5] = {w3 * a0, w3 * (a2 + a3 + (w3 * w3 - 2.5) * a0), w3 * (2.0 * a2 - a0), w3 * (2.0 * a3 - a0),
-                   2.0 * w3 * a4};
-    block_reduce<5>(s, red);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 5; ++k) mom[cell * 5 + k] = s[k] * dv3;
 }
 
 // 2D Poisson right-hand side of Eq. diffusion_LBE (N-penalised) on the interior cells.
