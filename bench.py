@@ -320,7 +320,7 @@ def run_serve(args):
 # `bench.py --op-only` (plates32x8, 808 cells; profiles/k_dense_gemm_plates32x8.md), valid
 # only while the kernel's source is the one captured: the digest covers the kernel and its
 # stage configuration.
-GEMM_TRAFFIC = {"plates32x8": {"cells": 808, "bytes": 346168576, "digest": "62ddcfbf2f872fc0"}}
+GEMM_TRAFFIC = {"plates32x8": {"cells": 808, "bytes": 412313088, "digest": "3e69fb6a96f1d27e"}}
 
 
 def gemm_source_digest():

@@ -22,6 +22,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -126,11 +127,19 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // the A_lo x_lo term.  A stage holds one 32-deep K slice of all four operands, so A_hi is staged
 // once for its two products: per stage 16 KB of A and 2 BN x 64 B of x feed 3 x 2 x 128 x BN x 32
 // flops.
+// One CTA per work item: a 128 x BN output tile and a range of its K slices.  slot < 0: the
+// item covers all of K and stores its tile into Y; slot >= 0: a part of a split tile, stored
+// whole into partial slot `slot` of P ([slot][BN][128]) for k_gemm_fixup to add up.
+struct GemmWork {
+    int col0, row0, kt0, kt1, slot;
+};
+
 template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_dense_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                  const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl, int Mrows,
-                 int ncols, int K, float* __restrict__ Y, int* __restrict__ err) {
+                 int ncols, const GemmWork* __restrict__ work, float* __restrict__ Y, float* __restrict__ P,
+                 int* __restrict__ err) {
     constexpr int A_BYTES = kBM * kBK * 2, X_BYTES = BN * kBK * 2, STAGE = 2 * A_BYTES + 2 * X_BYTES;
     constexpr int kStages = GemmCfg<BN>::STAGES;
     extern __shared__ uint8_t smem_raw[];
@@ -140,11 +149,9 @@ __global__ void __launch_bounds__(128, 1)
     uint64_t* done = empty + kStages;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int col0 = blockIdx.x * BN, row0 = blockIdx.y * kBM;
-    const int KTall = K / kBK, ksplit = gridDim.z;
-    const int kt0 = (int)((long)KTall * blockIdx.z / ksplit), kt1 = (int)((long)KTall * (blockIdx.z + 1) / ksplit);
-    const int KT = kt1 - kt0;
-    float* Yz = Y + (size_t)blockIdx.z * ncols * Mrows;
+    const GemmWork wk = work[blockIdx.x];
+    const int col0 = wk.col0, row0 = wk.row0, kt0 = wk.kt0;
+    const int KT = wk.kt1 - wk.kt0;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -223,15 +230,19 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (got && !failed && KT > 0) {
-        const int row = row0 + warp * 32 + lane;
+        const int r = warp * 32 + lane, row = row0 + r;
         for (int c0 = 0; c0 < BN; c0 += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-            if (row < Mrows) {
+            if (wk.slot >= 0) {
+                float* pt = P + (size_t)wk.slot * BN * kBM;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) pt[(c0 + j) * kBM + r] = v[j];
+            } else if (row < Mrows) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int col = col0 + c0 + j;
-                    if (col < ncols) Yz[(long)col * Mrows + row] = v[j];
+                    if (col < ncols) Y[(long)col * Mrows + row] = v[j];
                 }
             }
         }
@@ -451,25 +462,83 @@ int pick_bn(int cells) {
     return 256;
 }
 
+// A split tile: its S parts sit in partial slots slot0 .. slot0 + S - 1.
+struct GemmFix {
+    int col0, row0, slot0, nparts;
+};
+
+// Y tile = sum of its parts, added in slot order (deterministic).  blockIdx.y picks the split
+// tile; each thread adds four consecutive rows of one column (float4: the tile's rows start at
+// a multiple of 128 and Nr is a multiple of 128, so the four rows are in range together).
+template <int BN>
+__global__ void __launch_bounds__(256) k_gemm_fixup(const GemmFix* __restrict__ fix, const float* __restrict__ P,
+                                                    float* __restrict__ Y, int Mrows, int ncols) {
+    const GemmFix f = fix[blockIdx.y];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;  // float4 index within the tile
+    if (q >= BN * kBM / 4) return;
+    const int c = (4 * q) / kBM, r = (4 * q) % kBM;
+    const int col = f.col0 + c;
+    if (col >= ncols) return;
+    const float4* p4 = reinterpret_cast<const float4*>(P);
+    const size_t per = (size_t)BN * kBM / 4;
+    float4 acc = p4[(size_t)f.slot0 * per + q];
+    for (int p = 1; p < f.nparts; ++p) {
+        const float4 v = p4[(size_t)(f.slot0 + p) * per + q];
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+    }
+    *reinterpret_cast<float4*>(Y + (long)col * Mrows + f.row0 + r) = acc;
+}
+
+// Work list of one launch shape.  With T tiles on 152 SMs, the first floor(T / 152) * 152
+// tiles run whole (entire waves); each remaining tile is split into S K-ranges, so the last
+// partial wave becomes S times as many shorter items (S = 4 for a tail, up to 4 when there
+// are fewer tiles than SMs, keeping at least 8 K slices per item).
+struct GemmPlan {
+    std::vector<GemmWork> work;
+    std::vector<GemmFix> fix;
+    int slots = 0;
+};
+
+GemmPlan make_plan(int cells, int bn, int nr) {
+    constexpr int P = 152;
+    GemmPlan pl;
+    const int nct = (cells + bn - 1) / bn, nrt = nr / kBM, T = nct * nrt, KT = nr / kBK;
+    int W, S;
+    if (T >= P) {
+        W = T / P * P;
+        S = 4;
+    } else {
+        W = 0;
+        S = std::max(1, std::min(4, P / T));
+    }
+    while (S > 1 && KT / S < 8) --S;
+    if (S == 1) W = T;
+    for (int t = 0; t < T; ++t) {
+        const int col0 = (t % nct) * bn, row0 = (t / nct) * kBM;
+        if (t < W) {
+            pl.work.push_back({col0, row0, 0, KT, -1});
+            continue;
+        }
+        const int slot0 = pl.slots;
+        for (int p = 0; p < S; ++p) pl.work.push_back({col0, row0, KT * p / S, KT * (p + 1) / S, pl.slots++});
+        pl.fix.push_back({col0, row0, slot0, S});
+    }
+    return pl;
+}
+
 template <int BN>
 void launch_gemm(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1, int nr,
-                 int cells, int ksplit, float* Y, int* err, cudaStream_t s) {
+                 int cells, int nwork, const GemmWork* work, int nfix, const GemmFix* fix, float* Y, float* P,
+                 int* err, cudaStream_t s) {
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_dense_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GemmCfg<BN>::SMEM);
     });
-    dim3 grid((cells + BN - 1) / BN, nr / kBM, ksplit);
-    k_dense_gemm<BN><<<grid, 128, GemmCfg<BN>::SMEM, s>>>(a0, a1, b0, b1, nr, cells, nr, Y, err);
-}
-
-// K-split for launches with fewer tiles than SMs: the partial products land in separate
-// slices of Y and the expand kernels add them in a fixed order.
-int pick_ksplit(int cells, int bn, int nr) {
-    const int ctas = (cells + bn - 1) / bn * (nr / kBM);
-    int ks = ctas >= 152 ? 1 : 152 / ctas;
-    ks = ks < 1 ? 1 : (ks > 4 ? 4 : ks);
-    while (ks > 1 && nr / kBK < 4 * ks) --ks;
-    return ks;
+    k_dense_gemm<BN><<<nwork, 128, GemmCfg<BN>::SMEM, s>>>(a0, a1, b0, b1, nr, cells, work, Y, P, err);
+    if (nfix > 0) k_gemm_fixup<BN><<<dim3((BN * kBM / 4 + 255) / 256, nfix), 256, 0, s>>>(fix, P, Y, nr, cells);
 }
 
 }  // namespace
@@ -483,9 +552,17 @@ struct DenseOp {
     size_t bytes = 0;
 };
 
+// Work list of one launch shape on the device (built once per (cells, BN, Nr)).
+struct DevPlan {
+    GemmWork* work = nullptr;
+    GemmFix* fix = nullptr;
+    int nwork = 0, nfix = 0, slots = 0;
+};
+
 struct TcOperands {
     std::mutex mu;
     DenseOp op[3];  // by mode
+    std::map<long long, DevPlan> plans;
     // per-call workspace (grow-only)
     Arena ws;
     int* err_dev = nullptr;   // bounded-wait failure word of the GEMM (sticky until read)
@@ -567,12 +644,30 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     const int nr = d.nr, nv = t->nv;
     const int bn = pick_bn(cells);
     const long cpad = (cells + bn - 1) / bn * bn;  // whole TMA boxes, zero padding rows
-    const int ks = pick_ksplit(cells, bn, nr);
-    const size_t xb = (size_t)cpad * nr * 2, yb = (size_t)ks * cells * nr * 4;
-    if ((st = arena_reserve(c, T.ws, 2 * xb + yb + 3 * 256)) != LBE_OK) return st;
+    const int ks = 1;  // Y holds whole tiles (split tiles are added up by k_gemm_fixup)
+    const long long pkey = ((long long)cells << 32) | ((long long)bn << 20) | nr;
+    auto pit = T.plans.find(pkey);
+    if (pit == T.plans.end()) {
+        const GemmPlan pl = make_plan(cells, bn, nr);
+        DevPlan dp;
+        dp.nwork = (int)pl.work.size();
+        dp.nfix = (int)pl.fix.size();
+        dp.slots = pl.slots;
+        if ((st = dev_alloc(c, (void**)&dp.work, pl.work.size() * sizeof(GemmWork))) != LBE_OK) return st;
+        if (dp.nfix && (st = dev_alloc(c, (void**)&dp.fix, pl.fix.size() * sizeof(GemmFix))) != LBE_OK) return st;
+        cudaMemcpyAsync(dp.work, pl.work.data(), pl.work.size() * sizeof(GemmWork), cudaMemcpyHostToDevice, s);
+        if (dp.nfix) cudaMemcpyAsync(dp.fix, pl.fix.data(), pl.fix.size() * sizeof(GemmFix), cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);  // the host vectors go out of scope
+        pit = T.plans.emplace(pkey, dp).first;
+    }
+    const DevPlan& plan = pit->second;
+    const size_t xb = (size_t)cpad * nr * 2, yb = (size_t)cells * nr * 4;
+    const size_t pb = (size_t)plan.slots * bn * kBM * 4;
+    if ((st = arena_reserve(c, T.ws, 2 * xb + yb + pb + 4 * 256)) != LBE_OK) return st;
     auto* xh = (__nv_bfloat16*)arena_take(T.ws, xb);
     auto* xl = (__nv_bfloat16*)arena_take(T.ws, xb);
     auto* Y = (float*)arena_take(T.ws, yb);
+    auto* Pp = pb ? (float*)arena_take(T.ws, pb) : nullptr;
     if (cpad > cells) {
         cudaMemsetAsync(xh + (size_t)cells * nr, 0, (size_t)(cpad - cells) * nr * 2, s);
         cudaMemsetAsync(xl + (size_t)cells * nr, 0, (size_t)(cpad - cells) * nr * 2, s);
@@ -599,12 +694,12 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
                        cudaEventCreate(&ev[1]) == cudaSuccess;
     if (timed) cudaEventRecord(ev[0], s);
     switch (bn) {
-        case 64: launch_gemm<64>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
-        case 128: launch_gemm<128>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
-        case 160: launch_gemm<160>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
-        case 192: launch_gemm<192>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
-        case 224: launch_gemm<224>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
-        default: launch_gemm<256>(d.mAh, d.mAl, mXh, mXl, nr, cells, ks, Y, T.err_dev, s); break;
+        case 64: launch_gemm<64>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
+        case 128: launch_gemm<128>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
+        case 160: launch_gemm<160>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
+        case 192: launch_gemm<192>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
+        case 224: launch_gemm<224>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
+        default: launch_gemm<256>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
     }
     if (timed) cudaEventRecord(ev[1], s);
     const float* nu1 = t->nu1_f;
@@ -664,6 +759,10 @@ void tc_release(Ctx* c, DevTables* t) {
         dev_free(c, d.Al, d.bytes / 2);
     }
     arena_release(c, t->tc->ws);
+    for (auto& kv : t->tc->plans) {
+        dev_free(c, kv.second.work, kv.second.nwork * sizeof(GemmWork));
+        if (kv.second.fix) dev_free(c, kv.second.fix, kv.second.nfix * sizeof(GemmFix));
+    }
     dev_free(c, t->tc->err_dev, 256);
     if (t->tc->err_host) cudaFreeHost(t->tc->err_host);
     delete t->tc;
