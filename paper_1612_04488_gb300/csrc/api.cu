@@ -440,8 +440,14 @@ void batch_iterate(Batch& B) {
             // L h = L_64(h_base) + L_32(h - h_base): the increment is small, so FP32 suffices
             const long o = c0 * n3, nn = (long)nc * n3;
             range_sub_f32((const double*)(h + o), B.base_h + o, B.inc_h + o, nn, s);
-            fsm_cc_apply<float>(t, nc, B.delta.as<double>() + c0, B.inc_h + o, B.inc_lp + o, B.inc_lh + o,
-                                B.inc_scratch, B.inc_chunk, s, mode);
+            if (B.inc_tc) {  // BF16-refined: the increment through the tensor-core operator
+                const lbe_status ts = tc_apply_sym(B.c, B.t, mode, nc, B.delta.as<double>() + c0, B.inc_h + o,
+                                                   B.inc_lp + o, B.inc_lh + o, s, false);
+                if (ts != LBE_OK && B.op_status == LBE_OK) B.op_status = ts;
+            } else {
+                fsm_cc_apply<float>(t, nc, B.delta.as<double>() + c0, B.inc_h + o, B.inc_lp + o, B.inc_lh + o,
+                                    B.inc_scratch, B.inc_chunk, s, mode);
+            }
             range_add_f64(B.base_lp + o, B.inc_lp + o, (double*)(lp + o), nn, s);
             range_add_f64(B.base_lh + o, B.inc_lh + o, (double*)(lh + o), nn, s);
         } else if (sizeof(T) == 4 && B.use_tc) {

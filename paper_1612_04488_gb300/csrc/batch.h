@@ -43,6 +43,7 @@ struct Batch {
     void* inc_scratch = nullptr;
     int inc_chunk = 1;
     bool use_tc = false;  // FP32 batches: collision operator by the dense tensor-core GEMM
+    bool inc_tc = false;  // FP64 batches in increment mode: the increment's operator by that GEMM
     lbe_status op_status = LBE_OK;  // first failure of an operator launch inside an iteration
     int chunk = 1;
     std::vector<JobState> hstate;

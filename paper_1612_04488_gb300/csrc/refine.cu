@@ -245,6 +245,8 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         O.base_lp = base_lp;
         O.base_lh = base_lh;
         O.inc_h = inc_h;
+        O.inc_tc = I.use_tc;  // BF16-refined: the increment h - h0 (~1e-4 of h) takes the
+                              // tensor-core operator too; its 2^-16 error is ~1e-9 of h
         O.inc_lp = inc_lp;
         O.inc_lh = inc_lh;
         O.inc_scratch = inc_scratch;
@@ -282,6 +284,8 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         O.active = active;
         batch_iterate<double>(O);
         if ((st = cuda_status(c, cudaStreamSynchronize(s), "refine outer")) != LBE_OK) break;
+        if (O.inc_tc && (st = tc_check(c, O.t)) != LBE_OK) break;
+        if ((st = O.op_status) != LBE_OK) break;
         std::vector<int> keep;
         const double tnow = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int j : active) {
