@@ -563,8 +563,9 @@ struct TcOperands {
     std::mutex mu;
     DenseOp op[3];  // by mode
     std::map<long long, DevPlan> plans;
-    // per-call workspace (grow-only)
-    Arena ws;
+    // per-call workspace (grow-only), one per stream: callers on different streams (the
+    // service's buckets) run concurrently and must not share operands or partial tiles
+    std::map<cudaStream_t, Arena> ws;
     int* err_dev = nullptr;   // bounded-wait failure word of the GEMM (sticky until read)
     int* err_host = nullptr;  // pinned copy, valid after the stream's next synchronisation
 };
@@ -663,11 +664,12 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     const DevPlan& plan = pit->second;
     const size_t xb = (size_t)cpad * nr * 2, yb = (size_t)cells * nr * 4;
     const size_t pb = (size_t)plan.slots * bn * kBM * 4;
-    if ((st = arena_reserve(c, T.ws, 2 * xb + yb + pb + 4 * 256)) != LBE_OK) return st;
-    auto* xh = (__nv_bfloat16*)arena_take(T.ws, xb);
-    auto* xl = (__nv_bfloat16*)arena_take(T.ws, xb);
-    auto* Y = (float*)arena_take(T.ws, yb);
-    auto* Pp = pb ? (float*)arena_take(T.ws, pb) : nullptr;
+    Arena& ws = T.ws[s];
+    if ((st = arena_reserve(c, ws, 2 * xb + yb + pb + 4 * 256)) != LBE_OK) return st;
+    auto* xh = (__nv_bfloat16*)arena_take(ws, xb);
+    auto* xl = (__nv_bfloat16*)arena_take(ws, xb);
+    auto* Y = (float*)arena_take(ws, yb);
+    auto* Pp = pb ? (float*)arena_take(ws, pb) : nullptr;
     if (cpad > cells) {
         cudaMemsetAsync(xh + (size_t)cells * nr, 0, (size_t)(cpad - cells) * nr * 2, s);
         cudaMemsetAsync(xl + (size_t)cells * nr, 0, (size_t)(cpad - cells) * nr * 2, s);
@@ -758,7 +760,7 @@ void tc_release(Ctx* c, DevTables* t) {
         dev_free(c, d.Ah, d.bytes / 2);
         dev_free(c, d.Al, d.bytes / 2);
     }
-    arena_release(c, t->tc->ws);
+    for (auto& kv : t->tc->ws) arena_release(c, kv.second);
     for (auto& kv : t->tc->plans) {
         dev_free(c, kv.second.work, kv.second.nwork * sizeof(GemmWork));
         if (kv.second.fix) dev_free(c, kv.second.fix, kv.second.nfix * sizeof(GemmFix));

@@ -312,7 +312,8 @@ static Bucket* find_bucket(Service& sv, const std::string& key) {
     return nullptr;
 }
 
-// tc: an FP32 bucket whose collision operator is the tensor-core GEMM (BF16-refined requests)
+// tc: BF16-refined requests -- an FP32 bucket whose collision operator is the tensor-core
+// GEMM, or an FP64 increment-mode bucket whose increments go through that GEMM
 static Bucket* get_bucket(Service& sv, Ctx* c, const lbe_problem& pb, int prec, bool inc, lbe_status* st,
                           bool tc = false) {
     const std::string key = bucket_key(pb, prec, inc, tc);
@@ -327,7 +328,10 @@ static Bucket* get_bucket(Service& sv, Ctx* c, const lbe_problem& pb, int prec, 
         arena_release(c, nb->arena);
         return nullptr;
     }
-    nb->B.use_tc = tc;
+    if (prec == LBE_FP64)
+        nb->B.inc_tc = tc && inc;
+    else
+        nb->B.use_tc = tc;
     b = nb.get();
     sv.buckets.push_back(std::move(nb));
     return b;
@@ -389,7 +393,8 @@ static void service_main(Ctx* c) {
             lbe_status st;
             const bool tc = pb.precision == LBE_BF16_REFINED && pb.M >= 8;
             Bucket* F = get_bucket(sv, c, pb, refined ? LBE_FP32 : pb.precision, false, &st, tc);
-            Bucket* D = (F && refined) ? get_bucket(sv, c, pb, LBE_FP64, true, &st) : nullptr;
+            // the FP64 bucket of a BF16-refined request evaluates increments on the tensor cores too
+            Bucket* D = (F && refined) ? get_bucket(sv, c, pb, LBE_FP64, true, &st, tc) : nullptr;
             if (!F || (refined && !D)) {
                 if (live.empty()) {  // nothing will free memory: fail the request
                     std::lock_guard<std::mutex> lk(c->mu);
@@ -450,7 +455,7 @@ static void service_main(Ctx* c) {
         }
         for (Bucket* b : ran) {
             lbe_status st = cuda_status(c, cudaStreamSynchronize(b->stream), "service iterate");
-            if (st == LBE_OK && b->B.use_tc) st = tc_check(c, b->B.t);
+            if (st == LBE_OK && (b->B.use_tc || b->B.inc_tc)) st = tc_check(c, b->B.t);
             if (st == LBE_OK) st = b->B.op_status;
             b->B.op_status = LBE_OK;
             if (st != LBE_OK) b->failed = st;
