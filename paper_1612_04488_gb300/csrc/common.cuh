@@ -34,9 +34,12 @@ __device__ __forceinline__ dfloat df_twosum(float a, float b) {
     const float bb = __fsub_rn(s, a);
     return dfloat(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
 }
+// The results of + and * are left unnormalised (|lo| may reach a few ulps of hi): the next
+// TwoSum / TwoProduct is exact whatever the split, so the pair keeps the same information
+// and the renormalising Fast2Sum is saved; widening to double adds the parts exactly.
 __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
     const dfloat s = df_twosum(a.hi, b.hi);
-    return df_fast2sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+    return dfloat(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
 __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
@@ -45,7 +48,7 @@ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
     float e = __fmaf_rn(a.hi, b.hi, -p);
     e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
-    return df_fast2sum(p, e);
+    return dfloat(p, e);
 }
 __device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
 
