@@ -236,10 +236,17 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         // the one FP64-class collision-operator evaluation of the solve: at h0 = the FP32
         // solution; every later FP64 iteration adds the FP32 operator of the increment h - h0
         range_copy(O.h.as<double>(), base_h, O.cells * n3, s);
-        for (int j = 0; j < n; ++j) {
-            const long o = O.cell_off[j] * n3;
-            fsm_df_apply(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o, base_lp + o,
-                                 base_lh + o, O.scratch.p, O.chunk, s, O.geo[j].dim == 1 ? 2 : 1);
+        // one call per run of consecutive problems of one geometry (plates: parity mode 2,
+        // ducts: mode 1); the problems' cells are contiguous in batch order
+        for (int j0 = 0; j0 < n;) {
+            int j1 = j0 + 1;
+            long cells = O.sj[j0].ncell;
+            while (j1 < n && O.geo[j1].dim == O.geo[j0].dim && O.cell_off[j1] == O.cell_off[j0] + cells)
+                cells += O.sj[j1++].ncell;
+            const long o = O.cell_off[j0] * n3;
+            fsm_df_apply(*O.t, (int)cells, O.delta.as<double>() + O.cell_off[j0], base_h + o, base_lp + o,
+                         base_lh + o, O.scratch.p, O.chunk, s, O.geo[j0].dim == 1 ? 2 : 1);
+            j0 = j1;
         }
         O.base_h = base_h;
         O.base_lp = base_lp;
