@@ -106,6 +106,36 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// One W-column chunk of a CTA's accumulator row r: into partial slot `slot` of P, or into Y.
+template <int BN, int W>
+__device__ __forceinline__ void emit_chunk(const float (&v)[W], int c0, int r, int row, int col0, int slot, int Mrows,
+                                           int ncols, float* __restrict__ Y, float* __restrict__ P) {
+    if (slot >= 0) {
+        float* pt = P + (size_t)slot * BN * kBM;
+#pragma unroll
+        for (int j = 0; j < W; ++j) pt[(c0 + j) * kBM + r] = v[j];
+    } else if (row < Mrows) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int col = col0 + c0 + j;
+            if (col < ncols) Y[(long)col * Mrows + row] = v[j];
+        }
+    }
+}
+
 // Shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 32 bf16), 8-row groups
 // 512 B apart.
 __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
@@ -231,20 +261,15 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     if (got && !failed && KT > 0) {
         const int r = warp * 32 + lane, row = row0 + r;
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = 0; c0 + 32 <= BN; c0 += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-            if (wk.slot >= 0) {
-                float* pt = P + (size_t)wk.slot * BN * kBM;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) pt[(c0 + j) * kBM + r] = v[j];
-            } else if (row < Mrows) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = col0 + c0 + j;
-                    if (col < ncols) Y[(long)col * Mrows + row] = v[j];
-                }
-            }
+            emit_chunk<BN, 32>(v, c0, r, row, col0, wk.slot, Mrows, ncols, Y, P);
+        }
+        if constexpr (BN % 32 == 16) {  // last 16 columns
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (BN - 16), v);
+            emit_chunk<BN, 16>(v, BN - 16, r, row, col0, wk.slot, Mrows, ncols, Y, P);
         }
     } else if (tid == 0 && KT > 0) {
         atomicExch(err, 1);
@@ -453,8 +478,8 @@ bool make_map(CUtensorMap* m, const void* ptr, long rows, long cols, int box_row
 }
 
 // Column tile for a call: the cells split evenly over ceil(cells / 256) tiles, rounded up to
-// the next instantiated width (808 cells: 4 x 224 = 896 columns instead of 4 x 256).
-constexpr int kWidths[] = {64, 128, 160, 192, 224, 256};
+// the next instantiated width (808 cells: 4 x 208 = 832 columns instead of 4 x 256).
+constexpr int kWidths[] = {64, 128, 160, 192, 208, 224, 256};
 int pick_bn(int cells) {
     const int nct = (cells + 255) / 256, per = (cells + nct - 1) / nct;
     for (int w : kWidths)
@@ -700,6 +725,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         case 128: launch_gemm<128>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
         case 160: launch_gemm<160>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
         case 192: launch_gemm<192>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
+        case 208: launch_gemm<208>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
         case 224: launch_gemm<224>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
         default: launch_gemm<256>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
     }
