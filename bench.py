@@ -6,12 +6,14 @@ delta in {0.1, 1, 10, 100} x {Poiseuille, thermal transpiration}, 32^3 velocity 
 N = nu_bar/delta, stopped when the flow rates change by less than eps per iteration.
 One step = one batched solve of all eight problems to convergence (every hot-path step,
 A1-A8, runs on every iteration).  Inputs are synthetic (the problem parameters; h starts
-at 0).  Working set 808 cells x 32^3 x 4 B x 4 arrays = 424 MB > L2 (129 MB).
+at 0).  Working set: 808 cells x 32^3 x 4 B per array (106 MB) over several arrays, plus
+the 268 MB operator matrix, well above L2 (129 MB).
 
   value   solves/s with the batch resident on the device (lbe_batch_run), CUDA events
   e2e     solves/s through the one-shot public call lbe_solve_batch (host problems in,
           host results out; setup, uploads and per-iteration flag reads inside)
-  roofline  the collision operator (A1-A3) timed alone with CUDA events at the same size
+  roofline  the tensor-core GEMM of the collision operator (A1-A3), timed alone with CUDA
+          events on its own stream at the same size; traffic from an ncu capture
   cpu_baseline  the FP64 oracle on a bounded sample of the same workload (extrapolated)
 
 --impl reference times the oracle instead (the reference arm of this repository).
@@ -339,6 +341,20 @@ def gemm_traffic(workload, cells):
     return t["bytes"]
 
 
+def replica_throughput(local_ms, units_per_rank, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: every rank processed units_per_rank units;
+    the job took as long as its slowest rank (max over ranks).  Returns (units/s, slowest ms)."""
+    import torch
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    slowest = float(t.item())
+    return units_per_rank * world / (slowest / 1000.0), slowest
+
+
 def run_ours(args):
     import torch
 
@@ -391,12 +407,7 @@ def run_ours(args):
     st1 = lbe.stats()
     if dist:
         dist.barrier()
-    total_ms = e0.elapsed_time(e1)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = nsolve * args.steps * world / (total_ms / 1000.0)
+    value, total_ms = replica_throughput(e0.elapsed_time(e1), nsolve * args.steps, dist, "cuda")
     launches = int(st1["kernel_launches"] - st0["kernel_launches"])
     iters = [r.iters for r in res]
     refinements = [r.refinements for r in res]
