@@ -61,11 +61,14 @@ typedef enum { LBE_CIS = 0, LBE_SIS = 1 } lbe_scheme;
  * for LBE_FP64), and the correction equation is solved by low-precision SIS iterations
  * whose collision operator runs as tcgen05 BF16 spectral GEMMs with FP32 accumulation
  * (BF16_REFINED) or as the FP32 CUDA-core transforms (FP32_REFINED).  max_iter caps the
- * FP64 iterations.  Their FP64 collision-operator evaluations run in LBE_DF32 arithmetic.
+ * FP64 iterations.  The FP64 iterations evaluate the operator as L(h0) + L(h - h0): L(h0)
+ * once per solve (and when re-centred) in LBE_DF32 arithmetic, the small increment h - h0
+ * with the same low-precision operator as the correction solves.
  * LBE_DF32 (the operator entry points lbe_apply_L and lbe_apply_L_sym only): data in double,
  * arithmetic in double-float -- each value the unevaluated sum of two floats, about 2^-44
  * relative per operation, on the FP32 pipes, which this GPU issues at many times its FP64
- * rate; results agree with LBE_FP64 to about 1e-13 of their scale.  Values below the float
+ * rate; results agree with LBE_FP64 to about 1e-13 of their scale (pairs are left
+ * unnormalised between operations, which loses nothing).  Values below the float
  * range (|x| < 1e-38, the far tails of f_eq) are flushed to zero. */
 typedef enum {
     LBE_FP64 = 0,
