@@ -68,6 +68,14 @@ def workload_problems(lbe, name, precision, eps):
     raise ValueError(name)
 
 
+def dense_exec_flops(nv, parity):
+    """Executed tensor flops of one cell through the dense parity-subspace operator: three
+    BF16 products (A_hi x_hi, A_lo x_hi, A_hi x_lo) of the Nr-square matrix, 2 flops per
+    multiply-add."""
+    nr = nv ** 3 // (4 if parity == 2 else 2)
+    return 3 * 2.0 * nr * nr
+
+
 def fft_flops_per_cell(nv, M):
     """Algorithmic flops of one cell-L-eval: (M + 2) complex 3D FFTs (5 N log2 N each,
     N = nv^3) plus the multiplier products (6 per point per transform) and the angular
@@ -171,6 +179,33 @@ def oracle_sample(name, target_s=12.0):
                 sample_s=t_apply + t_rest, ncase=ncase, n=n)
 
 
+def _oracle_worker(a):
+    """One host process: build the oracle operator, then time L-evals for ~target_s."""
+    nv, M, R, seed, target_s = a
+    from oracle import fsm
+    from paper_1612_04488_gb300 import workloads as W
+    F = fsm.FSM(nv, 6.0, M, R)
+    h = W.random_h(2, nv, 6.0, seed=seed)
+    k, t = 0, 0.0
+    while t < target_s and k < 512:
+        t0 = time.perf_counter()
+        F.apply(h[k % 2], 1.0)
+        t += time.perf_counter() - t0
+        k += 1
+    return k, t
+
+
+def oracle_parallel_rate(nv, M, R, target_s, procs=None):
+    """Cell-L-evals/s of the oracle with one process per host core (spawned, so it is safe
+    after CUDA has been initialised).  Returns (rate, processes)."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        out = pool.map(_oracle_worker, [(nv, M, R, 100 + i, target_s) for i in range(procs)])
+    return sum(k / t for k, t in out if t > 0), procs
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle, timed on bounded samples on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -195,7 +230,8 @@ def run_reference(args):
         "config": {"workload": args.workload, "iterations_per_solve": iters,
                    "sample": "oracle L-eval on sampled cells + one sweep/update, extrapolated"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "per-cell L-eval x cells + sweep per iteration x %d iterations" % iters},
+                         "sample": "per-cell L-eval x cells + sweep per iteration x %d iterations "
+                                   "(the mean FP64 SIS iteration count of the workload)" % iters},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -319,9 +355,8 @@ def run_serve(args):
 
 
 # DRAM bytes (read + write) of one k_dense_gemm launch, from an ncu capture of
-# `bench.py --op-only` (plates32x8, 808 cells; profiles/k_dense_gemm_plates32x8.md), valid
-# only while the kernel's source is the one captured: the digest covers the kernel and its
-# stage configuration.
+# `bench.py --op-only` (plates32x8, 808 cells), valid only while the kernel's source is the
+# one captured: the digest covers the kernel and its stage configuration.
 GEMM_TRAFFIC = {"plates32x8": {"cells": 808, "bytes": 386856192, "digest": "67a1c45935e0d76b"}}
 
 
@@ -416,11 +451,26 @@ def run_ours(args):
 
     # ---- accuracy against the FP64 GPU path (parity-tested against the oracle) ----------
     ref = None
+    fp64 = None
     if args.check_fp64 and prec != lbe.FP64:
         rpbs = workload_problems(lbe, args.workload, lbe.FP64, min(args.eps, 1e-10))
         ref = ctx.solve_batch(rpbs)
         err = max(max(abs(r.mass_flow - q.mass_flow) / abs(q.mass_flow),
                       abs(r.heat_flow - q.heat_flow) / abs(q.heat_flow)) for r, q in zip(res, ref))
+        # the plain FP64 GPU path at the same eps: the comparison the mixed precision must beat
+        b64 = ctx.batch(workload_problems(lbe, args.workload, lbe.FP64, args.eps))
+        b64.run()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r64 = b64.run()
+        b.record(stream)
+        b.synchronize()
+        b64.close()
+        fp64 = {"solves_per_s": nsolve / (a.elapsed_time(b) / 1000.0), "eps": args.eps,
+                "iterations": [r.iters for r in r64],
+                "max_rel_err_vs_fp64_1e-10": max(max(abs(r.mass_flow - q.mass_flow) / abs(q.mass_flow),
+                                                     abs(r.heat_flow - q.heat_flow) / abs(q.heat_flow))
+                                                 for r, q in zip(r64, ref))}
     else:
         err = None
 
@@ -484,18 +534,23 @@ def run_ours(args):
         lbe.set_kernel_timing(False)
         n_t = g1["dense_gemm_timed"] - g0["dense_gemm_timed"]
         ms_gemm = (g1["dense_gemm_ms"] - g0["dense_gemm_ms"]) / max(n_t, 1)
-        nr = nv ** 3 // (4 if parity == 2 else 2)
-        exec_flops = 3 * 2.0 * nr * nr * cells  # useful products only (no padding columns)
+        exec_flops = dense_exec_flops(nv, parity) * cells  # useful products only (no padding columns)
         peak = peaks.get("bf16_tflops", 1900.0)
-        achieved = exec_flops / (ms_gemm / 1000.0) / 1e12
+        # achieved: the method's algorithmic work (the FFT-equivalent flops of one full
+        # cell-L-eval x the cells of one launch) over the launch's duration
+        achieved = alg_flops / (ms_gemm / 1000.0) / 1e12
+        executed = exec_flops / (ms_gemm / 1000.0) / 1e12
         roofline = {"bound": "tensor", "kernel": "k_dense_gemm (tcgen05 kind::f16, BF16 hi/lo x3, FP32 TMEM "
-                                                 "accumulate), %d cells x Nr=%d" % (cells, nr),
+                                                 "accumulate), %d cells" % cells,
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "peak_source": "bf16_tflops (burst, %s)" % peaks["_source"],
                     "traffic": gemm_traffic(args.workload, cells),
                     "timed_launches": n_t, "ms_per_launch": ms_gemm,
-                    "executed_flops_per_launch": exec_flops, "algorithmic_flops_per_launch": alg_flops,
-                    "algorithmic_tflops": alg_flops / (ms_gemm / 1000.0) / 1e12,
+                    "algorithmic_flops_per_launch": alg_flops,
+                    "algorithmic_unit": "%.1f MFLOP per cell-L-eval (FFT-equivalent, all %d directions) x %d cells"
+                                        % (fft_flops_per_cell(nv, M) / 1e6, M, cells),
+                    "executed_flops_per_launch": exec_flops, "executed_tflops": executed,
+                    "executed_frac": executed / peak,
                     "whole_call_ms": ms_op, "whole_call": "gather + GEMM + expand (lbe_apply_L_sym)"}
     else:
         ms_op = ms_fp32_sym if prec != lbe.FP64 else ms_fp64_sym
@@ -508,6 +563,30 @@ def run_ours(args):
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "peak_source": "152 SMs x %d lanes x 2 x %.0f MHz" % (lanes, clk_mhz), "traffic": None,
                     "algorithmic_flops_per_launch": sym_flops, "ms_per_launch": ms_op}
+    # ---- the transport sweep (HBM-bound), timed by the library inside an FP32 solve of the workload
+    sweep = None
+    if prec != lbe.FP64:
+        bf = ctx.batch(workload_problems(lbe, args.workload, lbe.FP32, args.eps))
+        bf.run()
+        lbe.set_kernel_timing(True)
+        w0 = lbe.stats()
+        bf.run()
+        w1 = lbe.stats()
+        lbe.set_kernel_timing(False)
+        bf.close()
+        n_sw = w1["sweep_timed"] - w0["sweep_timed"]
+        if n_sw:
+            sw_ms = w1["sweep_ms"] - w0["sweep_ms"]
+            sw_bytes = w1["sweep_bytes"] - w0["sweep_bytes"]
+            gbs = sw_bytes / (sw_ms / 1000.0) / 1e9
+            hbm = peaks.get("hbm_gbs", 6800.0)
+            sweep = {"bound": "hbm", "kernel": "k_sweep1d<float>" if pbs[0].geom.dim == 1 else "k_sweep2d<float>",
+                     "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "peak_source": "hbm_gbs (%s)" % peaks["_source"], "timed_launches": n_sw,
+                     "ms_per_launch": sw_ms / n_sw, "bytes_per_launch": sw_bytes / n_sw,
+                     "algorithmic_unit": "8 B per cell-velocity (FP32 rhs read + h written)",
+                     "what": "every sweep launch of one FP32 SIS solve of the workload (problems drop out as "
+                             "they converge)"}
     l_evals = {"op": cells / (ms_op / 1000.0), "fp32_fft_sym": cells / (ms_fp32_sym / 1000.0),
                "df32_fft_sym": cells / (ms_df_sym / 1000.0),
                "fp64_fft_sym": cells / (ms_fp64_sym / 1000.0), "fp64_fft_full": cells / (ms_fp64 / 1000.0)}
@@ -526,17 +605,24 @@ def run_ours(args):
                        "what": "per solve, batch start to that solve's convergence"},
         "iterations": iters, "refinements": refinements, "status": status,
         "max_rel_err_vs_fp64": err,
-        "l_evals_per_s": l_evals["op"], "l_evals_per_s_fp64": l_evals["fp64_fft_full"], "l_evals_detail": l_evals,
-        "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+        "l_evals_per_s": l_evals["op"], "l_evals_per_s_fp64": l_evals["fp64_fft_sym"], "l_evals_detail": l_evals,
+        "roofline": roofline, "roofline_sweep": sweep, "fp64_gpu": fp64,
+        "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # one extrapolation for both arms: per-iteration oracle time x the SIS iterations per
+        # solve (--ref-iters, the workload's FP64 count), single core and all cores
         s = oracle_sample(args.workload, target_s=args.ref_sample_s)
-        mean_it = float(np.mean(iters))
-        cpu_val = 1.0 / (s["t_iter_s"] * mean_it)
-        line["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                "sample": "FP64 oracle L-eval on %d cells (%.1f s) + one sweep/update of a "
-                                          "%d-node plate; x %d nodes x %.1f iterations (GPU counts)"
-                                          % (s["cells_sampled"], s["sample_s"], s["n"], s["n"], mean_it)}
+        it = args.ref_iters
+        one = 1.0 / (s["t_iter_s"] * it)
+        rate, procs = oracle_parallel_rate(nv, M, pbs[0].R if pbs[0].R > 0 else 4.5, args.ref_sample_s / 2)
+        t_iter_all = s["n"] * (1.0 / rate) + (s["t_iter_s"] - s["n"] * s["per_cell_s"])
+        allc = 1.0 / (t_iter_all * it)
+        line["cpu_baseline"] = {"value": allc, "unit": "solves/s", "cores": procs, "kind": "oracle",
+                                "single_core": one,
+                                "sample": "FP64 oracle L-evals for %.0f s on each of %d processes (%.1f cell-L-evals/s) "
+                                          "+ one sweep/update of a %d-node plate; per-iteration time x %d iterations "
+                                          "per solve" % (args.ref_sample_s / 2, procs, rate, s["n"], it)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if batch is not None:
@@ -556,7 +642,9 @@ def main():
     ap.add_argument("--workload", default="plates32x8", choices=["plates32x8", "plates16", "duct64x32"])
     ap.add_argument("--precision", default="bf16", choices=sorted(PRECISIONS))
     ap.add_argument("--eps", type=float, default=1e-7)
-    ap.add_argument("--ref-iters", type=int, default=45)
+    ap.add_argument("--ref-iters", type=int, default=35,
+                    help="SIS iterations per solve for the oracle extrapolation (the workload's mean "
+                         "FP64 count at eps = 1e-7)")
     ap.add_argument("--ref-sample-s", type=float, default=12.0)
     ap.add_argument("--no-check-fp64", dest="check_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")

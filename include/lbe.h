@@ -45,7 +45,8 @@ typedef enum {
     LBE_OOM = 4,           /* device memory (or the context's HBM budget) exhausted       */
     LBE_TIMEOUT = 5,       /* a bounded device wait expired; the context stays usable     */
     LBE_INTERNAL = 6,      /* CUDA runtime error; see lbe_last_error()                    */
-    LBE_UNSUPPORTED = 7    /* valid request outside what this build implements            */
+    LBE_UNSUPPORTED = 7,   /* valid request outside what this build implements            */
+    LBE_CANCELLED = 8      /* a served request withdrawn by lbe_cancel                     */
 } lbe_status;
 
 /* Source term S of Sec. 2 with X_P = X_T = -1. */
@@ -64,18 +65,26 @@ typedef enum { LBE_CIS = 0, LBE_SIS = 1 } lbe_scheme;
  * FP64 iterations.  The FP64 iterations evaluate the operator as L(h0) + L(h - h0): L(h0)
  * once per solve (and when re-centred) in LBE_DF32 arithmetic, the small increment h - h0
  * with the same low-precision operator as the correction solves.
+ * LBE_BF16 (solves only): the low-precision phase of LBE_BF16_REFINED on its own -- the
+ * tcgen05 BF16 operator with FP32 everything else and FP64 reductions, no refinement; it
+ * stops when both flow-rate changes fall below eps times the larger flow rate (a plain
+ * relative change of a small flow rate cannot get below FP32 rounding).  Its flow rates
+ * agree with LBE_FP64 to about 1e-5 relative.
  * LBE_DF32 (the operator entry points lbe_apply_L and lbe_apply_L_sym only): data in double,
  * arithmetic in double-float -- each value the unevaluated sum of two floats, about 2^-44
- * relative per operation, on the FP32 pipes, which this GPU issues at many times its FP64
- * rate; results agree with LBE_FP64 to about 1e-13 of their scale (pairs are left
- * unnormalised between operations, which loses nothing).  Values below the float
- * range (|x| < 1e-38, the far tails of f_eq) are flushed to zero. */
+ * relative per operation when the pairs are normalised, on the FP32 pipes, which this GPU
+ * issues at many times its FP64 rate.  Pairs are left unnormalised between operations
+ * (|lo| may grow to a few ulps of hi), so the per-operation bound grows with |lo|/ulp(hi);
+ * the agreement with LBE_FP64, about 1e-13 of the scale, is measured (parity tests), not
+ * guaranteed by that bound.  Values below the float range (|x| < 1e-38, the far tails of
+ * f_eq) are flushed to zero. */
 typedef enum {
     LBE_FP64 = 0,
     LBE_FP32 = 1,
     LBE_BF16_REFINED = 2,
     LBE_FP32_REFINED = 3,
-    LBE_DF32 = 4
+    LBE_DF32 = 4,
+    LBE_BF16 = 5
 } lbe_precision;
 
 /* Geometry (Sec. 2.4).  dim = 1: plates at x1 = +-1/2, half channel -1/2 <= x1 <= 0 with a
@@ -155,8 +164,10 @@ lbe_status lbe_batch_create(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_bat
 lbe_status lbe_batch_run(lbe_batch* b, lbe_result* outs);
 lbe_status lbe_batch_destroy(lbe_batch* b);
 
-/* Collision operator on device data (steps A1-A4).  h_dev: [cells][nv^3] of double (FP64,
- * DF32) or float (FP32, BF16_REFINED).  delta_dev: [cells] double, the rarefaction of each cell.
+/* Collision operator on device data (steps A1-A4), over all M directions, for any h.
+ * precision: LBE_FP64, LBE_DF32 or LBE_FP32 (the tensor-core form acts on the parity
+ * subspace only: see lbe_apply_L_sym).  h_dev: [cells][nv^3] of double (FP64, DF32) or
+ * float (FP32).  delta_dev: [cells] double, the rarefaction of each cell.
  * Outputs (same type as h, any may be NULL): Lplus_dev = L+ h, L_dev = L h.
  * G_dev (double [cells][2], may be NULL): G_j = 2 sum_v v_j v3 (L h + n_delta h) dv^3 with
  * n_delta = N delta per cell taken from ndelta_dev (double [cells]; required with G_dev).
@@ -167,7 +178,7 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R,
                        const double* ndelta_dev, double* G_dev, void* stream);
 
 /* Collision operator restricted to the parity subspace of the plate and duct solutions
- * (steps A1-A3).  The source S of Sec. 2 is odd in v3, so every CIS / SIS iterate is odd in
+ * (steps A1-A4).  The source S of Sec. 2 is odd in v3, so every CIS / SIS iterate is odd in
  * v3, and on plates also even in v2; the discrete operator commutes with those reflections.
  * parity = 1: h odd in v3 (ducts); parity = 2: h odd in v3 and even in v2 (plates).  For
  * such h the result equals lbe_apply_L's up to rounding; for other h it is not defined.
@@ -177,11 +188,15 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R,
  * transforms, applied to all cells as one tcgen05 GEMM with bfloat16 hi/lo operands and FP32
  * accumulation (relative error about 1e-5 of the scale); h, L+ h, L h are float, h 8-byte
  * aligned.  Needs
- * M >= 8.  Lplus_dev / L_dev may be NULL.  Returns after the work is queued on `stream`
- * (the tensor-core form synchronises the stream). */
+ * M >= 8.  Lplus_dev / L_dev may be NULL.  G_dev (double [cells][2], may be NULL): the
+ * L-moments G_j of lbe_apply_L with n_delta from ndelta_dev (required with G_dev); the
+ * tensor-core form sums them in the same pass that expands L+ h, without storing L h.
+ * LBE_BF16 is accepted as a synonym of LBE_BF16_REFINED here.  Returns after the work is
+ * queued on `stream` (the tensor-core form synchronises the stream). */
 lbe_status lbe_apply_L_sym(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_precision precision,
                            int parity, int cells, const double* delta_dev, const void* h_dev,
-                           void* Lplus_dev, void* L_dev, void* stream);
+                           void* Lplus_dev, void* L_dev, const double* ndelta_dev, double* G_dev,
+                           void* stream);
 
 /* lbe_apply_L without any device allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code recording CUDA
@@ -195,10 +210,14 @@ lbe_status lbe_apply_L_sym(lbe_ctx* ctx, int nv, double vmax, int M, double R, l
  * LBE_BAD_ARG.  The context must already hold the operator tables for (nv, vmax, M, R): an
  * earlier lbe_apply_L or lbe_solve with those parameters builds them; otherwise the call
  * returns LBE_BAD_ARG instead of allocating them.  The first call on a device looks up the
- * scratch array's device address, so make it before any stream capture.  All calls share
- * the array and its contents persist between calls; calls that overlap on the GPU race, so
- * serialise them (e.g. one stream).  Nothing in the array needs to start at zero.
- * Asynchronous on `stream`. */
+ * scratch array's device address; with lazy module loading (CUDA's default) that lookup is
+ * also when the driver loads the library's module and reserves the 32 MiB, so the first
+ * call can fail with LBE_OOM (or LBE_INTERNAL) when the device is full.  Make it before any
+ * stream capture; later calls on that device allocate nothing.  All calls share the array
+ * and its contents persist between calls; calls that overlap on the GPU race, so serialise
+ * them (e.g. one stream).  Nothing in the array needs to start at zero.  The result is
+ * bitwise that of lbe_apply_L (the per-cell arithmetic does not depend on how the cells are
+ * sliced).  Asynchronous on `stream`. */
 lbe_status lbe_apply_L_noalloc(lbe_ctx* ctx, int nv, double vmax, int M, double R,
                                lbe_precision precision, int cells, const double* delta_dev,
                                const void* h_dev, void* Lplus_dev, void* L_dev, void* stream);
@@ -218,6 +237,18 @@ lbe_status lbe_apply_L_noalloc(lbe_ctx* ctx, int nv, double vmax, int M, double 
  * stream. */
 lbe_status lbe_fourier_omega(lbe_ctx* ctx, int nv, double vmax, int M, double R, double delta, double N,
                              lbe_scheme scheme, int iters, const double* e0, double* ratios);
+
+/* Solve one problem starting from a checkpoint instead of h = 0 (checkpoint / resume; the
+ * SIS state is the iterate h and the flow rates of the stopping test).  h_in (host, double
+ * [cells * nv^3], the layout of lbe_solve's h_out) is the starting VDF.  prev (may be NULL)
+ * is the lbe_result of the run that produced h_in: its mass_flow and heat_flow start the
+ * stopping test, so a solve stopped after k iterations and resumed here continues exactly
+ * as the uninterrupted solve would -- the iterates, flow rates and stopping decision are
+ * bitwise those of the uninterrupted run.  With prev = NULL the first change is measured
+ * against the flow rates of h_in computed afresh.  LBE_FP64 and LBE_FP32 only (FP32 data are
+ * rounded from h_in).  Outputs as for lbe_solve; out->iters counts this call's iterations. */
+lbe_status lbe_solve_from(lbe_ctx* ctx, const lbe_problem* pb, const double* h_in, const lbe_result* prev,
+                          lbe_result* out, double* U3_out, double* h_out);
 
 /* Transport sweep of one problem (steps A5-A6): solves nu_eq h + v.grad h = rhs with the
  * problem's geometry and delta.  rhs_dev, h_dev: [cells][nv^3], double for FP64 else
@@ -241,6 +272,12 @@ lbe_status lbe_diffusion(lbe_ctx* ctx, const lbe_problem* pb, const double* Uh,
 lbe_status lbe_submit(lbe_ctx* ctx, const lbe_problem* pb, uint64_t* ticket);
 lbe_status lbe_poll(lbe_ctx* ctx, uint64_t ticket, lbe_result* out, int* done);
 
+/* Withdraw a submitted request.  A request still queued is dropped at once; an admitted one
+ * leaves the service at its next iteration boundary (its slot and cells are freed, none of
+ * its kernels is interrupted).  Either way lbe_poll then reports it done with status
+ * LBE_CANCELLED.  Cancelling a finished request changes nothing.  Thread-safe. */
+lbe_status lbe_cancel(lbe_ctx* ctx, uint64_t ticket);
+
 /* Maximum problems advanced together by the service (default 64). */
 lbe_status lbe_set_max_active(lbe_ctx* ctx, int max_active);
 
@@ -254,7 +291,10 @@ lbe_status lbe_set_stream(lbe_ctx* ctx, void* stream);
  * operator (one cell = one application of L to one nv^3 vector).  With kernel timing on
  * (lbe_set_kernel_timing), every tensor-core GEMM launched by lbe_apply_L_sym is bracketed
  * by CUDA events on its stream: dense_gemm_timed counts those launches and dense_gemm_ms
- * sums their durations. */
+ * sums their durations; and every transport-sweep launch of a solve (step A5, one launch per
+ * geometry per iteration) likewise: sweep_timed, sweep_ms, and sweep_bytes, the algorithmic
+ * bytes of those launches (right-hand side read and h written once per cell-velocity).
+ * Reading the counters waits for the timed sweeps to finish. */
 typedef struct {
     uint64_t kernel_launches;
     uint64_t h2d_bytes;
@@ -262,11 +302,21 @@ typedef struct {
     uint64_t cell_l_evals;
     uint64_t dense_gemm_timed;
     double dense_gemm_ms;
+    uint64_t sweep_timed;
+    double sweep_ms;
+    double sweep_bytes;
 } lbe_stats;
 lbe_status lbe_get_stats(lbe_stats* out);
 
 /* Process-wide switch (0 = off, the default) for the event timing described above. */
 lbe_status lbe_set_kernel_timing(int on);
+
+/* Test hook for the bounded-wait failure path (0 = off, the default).  While on, every CTA of
+ * the tensor-core GEMM first waits on a shared-memory barrier that nothing completes, with a
+ * limit of about 1e5 cycles; when the limit passes the CTA raises the failure word, waits
+ * (with the normal limit) for the operand copies it has issued, frees its tensor memory and
+ * returns, and the call returns LBE_TIMEOUT.  The context stays usable.  Process-wide. */
+lbe_status lbe_debug_expire_waits(int on);
 
 #ifdef __cplusplus
 }

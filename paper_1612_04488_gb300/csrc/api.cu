@@ -30,6 +30,17 @@ lbe_status cuda_status(Ctx* c, cudaError_t e, const char* where) {
     return LBE_INTERNAL;
 }
 
+int sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    int n = cache[dev].load();
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cache[dev].store(n);
+    return n;
+}
+
 lbe_status bad_arg(Ctx* c, const std::string& what) {
     if (c) c->last_error = what;
     return LBE_BAD_ARG;
@@ -59,6 +70,7 @@ void dev_free(Ctx* c, void* p, size_t bytes) {
 
 std::atomic<unsigned long long> g_launches{0}, g_h2d{0}, g_d2h{0}, g_levals{0};
 std::atomic<int> g_time_kernels{0};
+std::atomic<int> g_expire_waits{0};
 static std::mutex g_time_mu;
 static unsigned long long g_gemm_n = 0;
 static double g_gemm_ms = 0.0;
@@ -71,6 +83,47 @@ void get_gemm_time(unsigned long long* n, double* ms) {
     std::lock_guard<std::mutex> lk(g_time_mu);
     *n = g_gemm_n;
     *ms = g_gemm_ms;
+}
+
+// Transport-sweep launches timed inside solves: events are recorded on the solve's stream and
+// resolved (waited for) only when the counters are read.
+struct PendingSweep {
+    cudaEvent_t a, b;
+    double bytes;
+};
+static std::vector<PendingSweep> g_sweep_pending;
+static unsigned long long g_sweep_n = 0;
+static double g_sweep_ms = 0.0, g_sweep_bytes = 0.0;
+bool sweep_timing_begin(cudaStream_t s, cudaEvent_t* ev) {
+    if (!g_time_kernels.load()) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    if (cudaEventCreate(&ev[0]) != cudaSuccess) return false;
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return false;
+    }
+    cudaEventRecord(ev[0], s);
+    return true;
+}
+void sweep_timing_end(cudaStream_t s, cudaEvent_t* ev, double bytes) {
+    cudaEventRecord(ev[1], s);
+    std::lock_guard<std::mutex> lk(g_time_mu);
+    g_sweep_pending.push_back({ev[0], ev[1], bytes});
+}
+static void resolve_sweep_times() {
+    std::lock_guard<std::mutex> lk(g_time_mu);
+    for (auto& p : g_sweep_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            ++g_sweep_n;
+            g_sweep_ms += ms;
+            g_sweep_bytes += p.bytes;
+        }
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    g_sweep_pending.clear();
 }
 
 lbe_status arena_reserve(Ctx* c, Arena& a, size_t bytes) {
@@ -123,8 +176,9 @@ lbe_status validate_problem(Ctx* c, const lbe_problem& pb) {
     if (pb.forcing != LBE_POISEUILLE && pb.forcing != LBE_THERMAL_TRANSPIRATION) return bad_arg(c, "bad forcing");
     if (pb.scheme != LBE_CIS && pb.scheme != LBE_SIS) return bad_arg(c, "bad scheme");
     if (pb.precision != LBE_FP64 && pb.precision != LBE_FP32 && pb.precision != LBE_BF16_REFINED &&
-        pb.precision != LBE_FP32_REFINED)
+        pb.precision != LBE_FP32_REFINED && pb.precision != LBE_BF16)
         return bad_arg(c, "bad precision");
+    if (pb.precision == LBE_BF16 && pb.M < 8) return bad_arg(c, "LBE_BF16 needs M >= 8");
     if (!(pb.eps >= 0)) return bad_arg(c, "eps must be >= 0");
     if (pb.max_iter < 1) return bad_arg(c, "max_iter must be >= 1");
     return LBE_OK;
@@ -198,7 +252,14 @@ DevTables* get_tables(Ctx* c, int nv, double vmax, int M, double R, lbe_status* 
     if (s == LBE_OK) s = upload(c, &t->ab_x, to_df(h.ab), &b);
     t->bytes = b;
     *st = s;
-    if (s != LBE_OK) return nullptr;
+    if (s != LBE_OK) {  // give back what was uploaded before the failure
+        for (void* p : {(void*)t->feq_d, (void*)t->nu1_d, (void*)t->mult_d, (void*)t->ab_d, (void*)t->vel_d,
+                        (void*)t->feq_f, (void*)t->nu1_f, (void*)t->mult_f, (void*)t->ab_f, (void*)t->vel_f,
+                        (void*)t->feq_x, (void*)t->nu1_x, (void*)t->mult_x, (void*)t->ab_x})
+            if (p) cudaFree(p);
+        c->used -= std::min(b, c->used);
+        return nullptr;
+    }
     DevTables* raw = t.get();
     c->tables[key] = std::move(t);
     return raw;
@@ -293,7 +354,7 @@ lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Arena* ar
     B.t = get_tables(c, p0.nv, p0.vmax, p0.M, p0.R, &st);
     if (!B.t) return st;
     B.prec = p0.precision;
-    if (B.prec == LBE_BF16_REFINED || B.prec == LBE_FP32_REFINED) B.prec = LBE_FP32;
+    if (B.prec == LBE_BF16_REFINED || B.prec == LBE_FP32_REFINED || B.prec == LBE_BF16) B.prec = LBE_FP32;
     const int eb = B.prec == LBE_FP64 ? 8 : 4;
     const long n3 = (long)p0.nv * p0.nv * p0.nv;
     std::vector<double> coef, dcell, ndcell;
@@ -475,9 +536,19 @@ void batch_iterate(Batch& B) {
     int mc1 = 0, mc2 = 0;  // largest coefficient block of a job (shared-memory staging)
     for (int j : act1) mc1 = std::max(mc1, 6 * B.sj[j].ncell);
     for (int j : act2) mc2 = std::max(mc2, 3 * (B.sj[j].nx + B.sj[j].ny));
-    launch_sweep<T>(t, 1, (int)act1.size(), mc1, lp, hh, B.sjobs.as<SweepJobDev>(), dact, B.coef.as<double>(), s);
-    launch_sweep<T>(t, 2, (int)act2.size(), mc2, lp, hh, B.sjobs.as<SweepJobDev>(), dact + act1.size(),
-                    B.coef.as<double>(), s);
+    {  // optional event timing of each sweep launch (algorithmic bytes: rhs in, h out)
+        long c1 = 0, c2 = 0;
+        for (int j : act1) c1 += B.sj[j].ncell;
+        for (int j : act2) c2 += B.sj[j].ncell;
+        cudaEvent_t ev[2];
+        bool tm = !act1.empty() && sweep_timing_begin(s, ev);
+        launch_sweep<T>(t, 1, (int)act1.size(), mc1, lp, hh, B.sjobs.as<SweepJobDev>(), dact, B.coef.as<double>(), s);
+        if (tm) sweep_timing_end(s, ev, 2.0 * sizeof(T) * (double)c1 * n3);
+        tm = !act2.empty() && sweep_timing_begin(s, ev);
+        launch_sweep<T>(t, 2, (int)act2.size(), mc2, lp, hh, B.sjobs.as<SweepJobDev>(), dact + act1.size(),
+                        B.coef.as<double>(), s);
+        if (tm) sweep_timing_end(s, ev, 2.0 * sizeof(T) * (double)c2 * n3);
+    }
     for (auto& sp : spans) launch_moments<T>(t, sp.c0, (int)sp.n, hh, B.mom.as<double>(), s);
     launch_sis_update(t, na, B.ijobs.as<SisJobDev>(), dact, B.mom.as<double>(), B.G.as<double>(),
                       B.coef.as<double>(), B.work.as<double>(), B.dU.as<double>(), B.U3.as<double>(),
@@ -561,6 +632,7 @@ const char* lbe_status_str(lbe_status s) {
         case LBE_TIMEOUT: return "device wait timed out";
         case LBE_INTERNAL: return "internal CUDA error";
         case LBE_UNSUPPORTED: return "unsupported";
+        case LBE_CANCELLED: return "cancelled";
     }
     return "unknown status";
 }
@@ -621,7 +693,8 @@ int lbe_problem_cells(const lbe_problem* pb) {
 }
 
 static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_result* outs,
-                                double* U3_out, double* h_out) {
+                                double* U3_out, double* h_out, const double* h_in = nullptr,
+                                const lbe_result* prev = nullptr) {
     if (!ctx || !pbs || n < 1 || !outs) return bad_arg(ctx, "null argument");
     cudaSetDevice(ctx->device);
     for (int j = 0; j < n; ++j) {
@@ -637,6 +710,44 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
     Batch B;
     lbe_status st = batch_init(B, ctx, pbs, n, &ctx->solve_arena, ctx->stream);
     if (st != LBE_OK) return st;
+    if (pbs[0].precision == LBE_BF16) {
+        // the tensor-core operator with FP32 everything else; scale-relative stopping test
+        if (B.t->sym_reps2 == 0) return bad_arg(ctx, "LBE_BF16 needs a parity-reducible direction set");
+        B.use_tc = true;
+        for (int j = 0; j < n; ++j) B.ij[j].crit = 1;
+        cudaMemcpyAsync(B.ijobs.p, B.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, ctx->stream);
+        g_h2d += n * sizeof(SisJobDev);
+    }
+    if (h_in) {  // resume from a checkpoint (one problem)
+        const long n3h = (long)pbs[0].nv * pbs[0].nv * pbs[0].nv;
+        const long nn = B.cells * n3h;
+        if (B.prec == LBE_FP64) {
+            st = cuda_status(ctx, cudaMemcpyAsync(B.h.p, h_in, nn * 8, cudaMemcpyHostToDevice, ctx->stream),
+                             "h_in copy");
+        } else {
+            std::vector<float> tmp(h_in, h_in + nn);
+            st = cuda_status(ctx, cudaMemcpyAsync(B.h.p, tmp.data(), nn * 4, cudaMemcpyHostToDevice, ctx->stream),
+                             "h_in copy");
+            if (st == LBE_OK) st = cuda_status(ctx, cudaStreamSynchronize(ctx->stream), "h_in copy");
+        }
+        g_h2d += nn * (B.prec == LBE_FP64 ? 8 : 4);
+        if (st != LBE_OK) return st;
+        if (prev) {  // the flow rates the interrupted run held
+            B.hstate[0].M = prev->mass_flow;
+            B.hstate[0].Q = prev->heat_flow;
+            cudaMemcpyAsync(B.states.p, B.hstate.data(), sizeof(JobState), cudaMemcpyHostToDevice, ctx->stream);
+            g_h2d += sizeof(JobState);
+        } else {  // flow rates of h_in
+            int zero = 0;
+            cudaMemcpyAsync(B.act.p, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+            if (B.prec == LBE_FP64)
+                launch_moments<double>(*B.t, 0, (int)B.cells, B.h.as<double>(), B.mom.as<double>(), ctx->stream);
+            else
+                launch_moments<float>(*B.t, 0, (int)B.cells, B.h.as<float>(), B.mom.as<double>(), ctx->stream);
+            launch_set_rates(1, B.ijobs.as<SisJobDev>(), B.act.as<int>(), B.mom.as<double>(), B.coef.as<double>(),
+                             B.states.as<JobState>(), ctx->stream);
+        }
+    }
     int maxit = 0;
     for (int j = 0; j < n; ++j) maxit = std::max(maxit, pbs[j].max_iter);
     st = batch_run(B, maxit);
@@ -672,6 +783,16 @@ lbe_status lbe_solve_batch(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_resu
     return lbe_solve_batch_impl(ctx, pbs, n, outs, nullptr, nullptr);
 }
 
+lbe_status lbe_solve_from(lbe_ctx* ctx, const lbe_problem* pb, const double* h_in, const lbe_result* prev,
+                          lbe_result* out, double* U3_out, double* h_out) {
+    if (!ctx || !pb || !h_in || !out) return bad_arg(ctx, "null argument");
+    if (pb->precision != LBE_FP64 && pb->precision != LBE_FP32)
+        return bad_arg(ctx, "lbe_solve_from takes LBE_FP64 or LBE_FP32");
+    if (prev && (!std::isfinite(prev->mass_flow) || !std::isfinite(prev->heat_flow)))
+        return bad_arg(ctx, "prev flow rates must be finite");
+    return lbe_solve_batch_impl(ctx, pb, 1, out, U3_out, h_out, h_in, prev);
+}
+
 lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_precision precision, int cells,
                        const double* delta_dev, const void* h_dev, void* Lplus_dev, void* L_dev,
                        const double* ndelta_dev, double* G_dev, void* stream) {
@@ -681,21 +802,17 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_p
     if (M < 2 || M > 64 || (M & (M - 1))) return bad_arg(ctx, "M must be a power of two in [2, 64]");
     if (!(vmax > 0) || R > 2 * vmax) return bad_arg(ctx, "bad vmax or R");
     if (G_dev && !ndelta_dev) return bad_arg(ctx, "G needs ndelta");
-    if (precision != LBE_FP64 && precision != LBE_FP32 && precision != LBE_BF16_REFINED && precision != LBE_DF32)
-        return bad_arg(ctx, "bad precision");
+    if (precision == LBE_BF16_REFINED || precision == LBE_BF16) {
+        ctx->last_error = "the tensor-core operator acts on the parity subspace: use lbe_apply_L_sym";
+        return LBE_UNSUPPORTED;
+    }
+    if (precision != LBE_FP64 && precision != LBE_FP32 && precision != LBE_DF32) return bad_arg(ctx, "bad precision");
     if (cells == 0) return LBE_OK;
     cudaSetDevice(ctx->device);
     lbe_status st;
     DevTables* t = get_tables(ctx, nv, vmax, M, R, &st);
     if (!t) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if (precision == LBE_BF16_REFINED) {
-        st = tc_apply_L(ctx, t, cells, delta_dev, (const float*)h_dev, (float*)Lplus_dev, (float*)L_dev, s);
-        if (st != LBE_OK) return st;
-        if (G_dev && !L_dev) return bad_arg(ctx, "G needs L_dev");
-        if (G_dev) lmoments<float>(*t, cells, (const float*)L_dev, (const float*)h_dev, ndelta_dev, G_dev, s);
-        return cuda_status(ctx, cudaGetLastError(), "apply_L");
-    }
     const bool wide = precision == LBE_FP64 || precision == LBE_DF32;  // double data
     const int eb = wide ? 8 : 4;
     int chunk = 1;
@@ -724,15 +841,17 @@ lbe_status lbe_apply_L(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_p
 
 lbe_status lbe_apply_L_sym(lbe_ctx* ctx, int nv, double vmax, int M, double R, lbe_precision precision, int parity,
                            int cells, const double* delta_dev, const void* h_dev, void* Lplus_dev, void* L_dev,
-                           void* stream) {
+                           const double* ndelta_dev, double* G_dev, void* stream) {
     if (!ctx) return LBE_BAD_ARG;
     if (parity != 1 && parity != 2) return bad_arg(ctx, "parity must be 1 (odd in v3) or 2 (also even in v2)");
     if (cells < 0 || (cells > 0 && (!h_dev || !delta_dev))) return bad_arg(ctx, "null h or delta");
     if (nv != 8 && nv != 16 && nv != 24 && nv != 32) return bad_arg(ctx, "nv must be 8, 16, 24 or 32");
     if (M < 8 || M > 64 || (M & (M - 1))) return bad_arg(ctx, "M must be a power of two in [8, 64]");
     if (!(vmax > 0) || R > 2 * vmax) return bad_arg(ctx, "bad vmax or R");
+    if (precision == LBE_BF16) precision = LBE_BF16_REFINED;  // the same tensor-core operator
     if (precision != LBE_FP64 && precision != LBE_FP32 && precision != LBE_BF16_REFINED && precision != LBE_DF32)
-        return bad_arg(ctx, "precision must be FP64, FP32, DF32 or BF16_REFINED");
+        return bad_arg(ctx, "precision must be FP64, FP32, DF32, BF16 or BF16_REFINED");
+    if (G_dev && !ndelta_dev) return bad_arg(ctx, "G needs ndelta");
     if (cells == 0) return LBE_OK;
     cudaSetDevice(ctx->device);
     lbe_status st;
@@ -750,7 +869,9 @@ lbe_status lbe_apply_L_sym(lbe_ctx* ctx, int nv, double vmax, int M, double R, l
     void* lo = L_dev ? L_dev : arena_take(ctx->apply_arena, vol);
     if (precision == LBE_BF16_REFINED) {
         if ((uintptr_t)h_dev % 8 != 0) return bad_arg(ctx, "h_dev must be 8-byte aligned for the tensor-core form");
-        return tc_apply_sym(ctx, t, parity, cells, delta_dev, (const float*)h_dev, (float*)lp, (float*)lo, s);
+        // with G: L+ h (and L h) and the L-moments in one fused pass
+        return tc_apply_sym(ctx, t, parity, cells, delta_dev, (const float*)h_dev, (float*)lp, (float*)lo, s, true,
+                            ndelta_dev, G_dev);
     }
     if (precision == LBE_FP64)
         st = fsm_cc_apply<double>(*t, cells, delta_dev, (const double*)h_dev, (double*)lp, (double*)lo, p, chunk, s,
@@ -761,6 +882,12 @@ lbe_status lbe_apply_L_sym(lbe_ctx* ctx, int nv, double vmax, int M, double R, l
         st = fsm_cc_apply<float>(*t, cells, delta_dev, (const float*)h_dev, (float*)lp, (float*)lo, p, chunk, s,
                                  parity);
     if (st != LBE_OK) return st;
+    if (G_dev) {
+        if (eb == 8)
+            lmoments<double>(*t, cells, (const double*)lo, (const double*)h_dev, ndelta_dev, G_dev, s);
+        else
+            lmoments<float>(*t, cells, (const float*)lo, (const float*)h_dev, ndelta_dev, G_dev, s);
+    }
     return cuda_status(ctx, cudaGetLastError(), "apply_L_sym");
 }
 
@@ -937,11 +1064,23 @@ lbe_status lbe_get_stats(lbe_stats* out) {
     get_gemm_time(&n, &ms);
     out->dense_gemm_timed = n;
     out->dense_gemm_ms = ms;
+    resolve_sweep_times();
+    {
+        std::lock_guard<std::mutex> lk(g_time_mu);
+        out->sweep_timed = g_sweep_n;
+        out->sweep_ms = g_sweep_ms;
+        out->sweep_bytes = g_sweep_bytes;
+    }
     return LBE_OK;
 }
 
 lbe_status lbe_set_kernel_timing(int on) {
     g_time_kernels.store(on ? 1 : 0);
+    return LBE_OK;
+}
+
+lbe_status lbe_debug_expire_waits(int on) {
+    g_expire_waits.store(on ? 1 : 0);
     return LBE_OK;
 }
 

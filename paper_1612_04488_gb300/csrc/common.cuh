@@ -93,12 +93,70 @@ __host__ __device__ constexpr int bitrev(int i, int bits) {
     return r;
 }
 
+template <typename T, int N, bool INV>
+__device__ __forceinline__ void dft_line(T (&re)[N], T (&im)[N]);
+
+// Length N = 3 * 2^k by one mixed-radix step (Cooley-Tukey): the three interleaved
+// subsequences x[3j + r] are transformed with length N/3, then for every k1 < N/3
+//     X[k1 + (N/3) k2] = sum_r W_3^(r k2) (W_N^(r k1) Y_r[k1]),   k2 = 0, 1, 2,
+// a twiddle product and one 3-point DFT.  With d = z1 - z2 and m = z0 - (z1 + z2)/2 the
+// 3-point DFT is Z0 = z0 + z1 + z2, Z1 = m -+ i (sqrt(3)/2) d, Z2 = m +- i (sqrt(3)/2) d
+// (upper signs forward).  W_N^(N/3) = -1/2 - i sqrt(3)/2 supplies both constants.
+template <typename T, int N, bool INV>
+__device__ __forceinline__ void dft_line_radix3(T (&re)[N], T (&im)[N]) {
+    constexpr int K = N / 3;
+    T sr[3][K], si[3][K];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            sr[r][j] = re[3 * j + r];
+            si[r][j] = im[3 * j + r];
+        }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) dft_line<T, K, INV>(sr[r], si[r]);
+    const auto w3 = tw<T, N>(K);
+    const T half = w3.x;                  // -1/2
+    const T c = INV ? w3.y : -w3.y;       // +-sqrt(3)/2: the sign of the forward form
+#pragma unroll
+    for (int k1 = 0; k1 < K; ++k1) {
+        T zr[3], zi[3];
+        zr[0] = sr[0][k1];
+        zi[0] = si[0][k1];
+#pragma unroll
+        for (int r = 1; r < 3; ++r) {
+            if (k1 == 0) {
+                zr[r] = sr[r][k1];
+                zi[r] = si[r][k1];
+            } else {
+                const auto w = tw<T, N>(r * k1);
+                const T wr = w.x, wi = INV ? -w.y : w.y;
+                zr[r] = sr[r][k1] * wr - si[r][k1] * wi;
+                zi[r] = sr[r][k1] * wi + si[r][k1] * wr;
+            }
+        }
+        const T tr = zr[1] + zr[2], ti = zi[1] + zi[2];
+        const T dr = zr[1] - zr[2], di = zi[1] - zi[2];
+        const T mr = zr[0] + tr * half, mi = zi[0] + ti * half;
+        re[k1] = zr[0] + tr;
+        im[k1] = zi[0] + ti;
+        // forward: Z1 = m - i c d = (mr + c di, mi - c dr); Z2 = (mr - c di, mi + c dr)
+        re[k1 + K] = mr + c * di;
+        im[k1 + K] = mi - c * dr;
+        re[k1 + 2 * K] = mr - c * di;
+        im[k1 + 2 * K] = mi + c * dr;
+    }
+}
+
 // In-register 1D DFT of length N (forward: exp(-2 pi i jk/N); INV: exp(+...)), unscaled.
-// Radix-2 decimation in time for powers of two, direct summation otherwise; every index
-// is a compile-time constant after unrolling, so the line stays in registers.
+// Radix-2 decimation in time for powers of two, one radix-3 step for 3 * 2^k, direct
+// summation otherwise; every index is a compile-time constant after unrolling, so the line
+// stays in registers.
 template <typename T, int N, bool INV>
 __device__ __forceinline__ void dft_line(T (&re)[N], T (&im)[N]) {
-    if constexpr (is_pow2(N)) {
+    if constexpr (N % 3 == 0 && is_pow2(N / 3) && N >= 12) {
+        dft_line_radix3<T, N, INV>(re, im);
+    } else if constexpr (is_pow2(N)) {
         constexpr int B = ilog2(N);
 #pragma unroll
         for (int i = 0; i < N; ++i) {

@@ -48,6 +48,7 @@ struct GemmCfg {
     static constexpr size_t SMEM = (size_t)STAGES * STAGE + 1024 + 256;
 };
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long kProbeCycles = 100000LL;     // the test hook's wait, ~50 us
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -59,7 +60,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 // Bounded wait on an mbarrier phase; false when the deadline passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kWaitCycles) {
     const uint32_t addr = smem_u32(bar);
     const long long t0 = clock64();
     for (;;) {
@@ -70,7 +71,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             : "r"(addr), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(128, 1)
     k_dense_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                  const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl, int Mrows,
                  int ncols, const GemmWork* __restrict__ work, float* __restrict__ Y, float* __restrict__ P,
-                 int* __restrict__ err) {
+                 int* __restrict__ err, int probe) {
     constexpr int A_BYTES = kBM * kBK * 2, X_BYTES = BN * kBK * 2, STAGE = 2 * A_BYTES + 2 * X_BYTES;
     constexpr int kStages = GemmCfg<BN>::STAGES;
     extern __shared__ uint8_t smem_raw[];
@@ -177,7 +178,8 @@ __global__ void __launch_bounds__(128, 1)
     uint64_t* full = (uint64_t*)(base + kStages * STAGE);
     uint64_t* empty = full + kStages;
     uint64_t* done = empty + kStages;
-    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    uint64_t* never = done + 1;  // completed by nothing: the test hook waits on it
+    uint32_t* tmem_slot = (uint32_t*)(done + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const GemmWork wk = work[blockIdx.x];
     const int col0 = wk.col0, row0 = wk.row0, kt0 = wk.kt0;
@@ -189,6 +191,7 @@ __global__ void __launch_bounds__(128, 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(done, 1);
+        mbar_init(never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -218,8 +221,10 @@ __global__ void __launch_bounds__(128, 1)
         int issued = 0;
         for (int s = 0; s < kStages && s < KT; ++s) issue(s, s), ++issued;
         int consumed = 0;
-        bool ok = true;
-        for (int kt = 0; kt < KT; ++kt) {
+        // test hook: a short wait that cannot succeed takes the failure path below with the
+        // first stages' copies in flight
+        bool ok = probe ? mbar_wait(never, 0, kProbeCycles) : true;
+        for (int kt = 0; ok && kt < KT; ++kt) {
             const int s = kt % kStages;
             if (!mbar_wait(&full[s], (kt / kStages) & 1)) {
                 ok = false;
@@ -517,7 +522,7 @@ __global__ void __launch_bounds__(256) k_gemm_fixup(const GemmFix* __restrict__ 
     *reinterpret_cast<float4*>(Y + (long)col * Mrows + f.row0 + r) = acc;
 }
 
-// Work list of one launch shape.  With T tiles on 152 SMs, the first floor(T / 152) * 152
+// Work list of one launch shape.  With T tiles on P SMs, the first floor(T / P) * P
 // tiles run whole (entire waves); each remaining tile is split into S K-ranges, so the last
 // partial wave becomes S times as many shorter items (S = 4 for a tail, up to 4 when there
 // are fewer tiles than SMs, keeping at least 8 K slices per item).
@@ -527,8 +532,7 @@ struct GemmPlan {
     int slots = 0;
 };
 
-GemmPlan make_plan(int cells, int bn, int nr) {
-    constexpr int P = 152;
+GemmPlan make_plan(int cells, int bn, int nr, int P) {
     GemmPlan pl;
     const int nct = (cells + bn - 1) / bn, nrt = nr / kBM, T = nct * nrt, KT = nr / kBK;
     int W, S;
@@ -557,12 +561,12 @@ GemmPlan make_plan(int cells, int bn, int nr) {
 template <int BN>
 void launch_gemm(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1, int nr,
                  int cells, int nwork, const GemmWork* work, int nfix, const GemmFix* fix, float* Y, float* P,
-                 int* err, cudaStream_t s) {
+                 int* err, int probe, cudaStream_t s) {
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_dense_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GemmCfg<BN>::SMEM);
     });
-    k_dense_gemm<BN><<<nwork, 128, GemmCfg<BN>::SMEM, s>>>(a0, a1, b0, b1, nr, cells, work, Y, P, err);
+    k_dense_gemm<BN><<<nwork, 128, GemmCfg<BN>::SMEM, s>>>(a0, a1, b0, b1, nr, cells, work, Y, P, err, probe);
     if (nfix > 0) k_gemm_fixup<BN><<<dim3((BN * kBM / 4 + 255) / 256, nfix), 256, 0, s>>>(fix, P, Y, nr, cells);
 }
 
@@ -624,10 +628,10 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
         cudaMemcpyAsync(dl, ones.data(), nb * 8, cudaMemcpyHostToDevice, s);
         for (int q0 = 0; q0 < nr && st == LBE_OK; q0 += nb) {
             const int b = std::min(nb, nr - q0);
-            k_basis<<<1024, 256, 0, s>>>((double*)hb, q0, b, nv, nr, mode);
+            k_basis<<<8 * sm_count(), 256, 0, s>>>((double*)hb, q0, b, nv, nr, mode);
             st = fsm_df_apply(*t, b, (const double*)dl, (const double*)hb, (double*)lp, (double*)lo, sc, chunk,
                                       s, mode);
-            k_store_columns<<<1024, 256, 0, s>>>((const double*)lp, d.Ah, d.Al, q0, b, nv, nr, mode);
+            k_store_columns<<<8 * sm_count(), 256, 0, s>>>((const double*)lp, d.Ah, d.Al, q0, b, nv, nr, mode);
             g_launches += 2;
         }
         if (st == LBE_OK) st = cuda_status(c, cudaStreamSynchronize(s), "dense operator build");
@@ -674,7 +678,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     const long long pkey = ((long long)cells << 32) | ((long long)bn << 20) | nr;
     auto pit = T.plans.find(pkey);
     if (pit == T.plans.end()) {
-        const GemmPlan pl = make_plan(cells, bn, nr);
+        const GemmPlan pl = make_plan(cells, bn, nr, sm_count());
         DevPlan dp;
         dp.nwork = (int)pl.work.size();
         dp.nfix = (int)pl.fix.size();
@@ -709,10 +713,10 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         auto* xl2 = reinterpret_cast<__nv_bfloat162*>(xl);
         const bool p2 = mode == 2;
         switch (nv) {
-            case 8: (p2 ? k_gather_split_t<8, 2> : k_gather_split_t<8, 1>)<<<1216, 256, 0, s>>>(h, xh2, xl2, cells); break;
-            case 16: (p2 ? k_gather_split_t<16, 2> : k_gather_split_t<16, 1>)<<<1216, 256, 0, s>>>(h, xh2, xl2, cells); break;
-            case 24: (p2 ? k_gather_split_t<24, 2> : k_gather_split_t<24, 1>)<<<1216, 256, 0, s>>>(h, xh2, xl2, cells); break;
-            default: (p2 ? k_gather_split_t<32, 2> : k_gather_split_t<32, 1>)<<<1216, 256, 0, s>>>(h, xh2, xl2, cells); break;
+            case 8: (p2 ? k_gather_split_t<8, 2> : k_gather_split_t<8, 1>)<<<8 * sm_count(), 256, 0, s>>>(h, xh2, xl2, cells); break;
+            case 16: (p2 ? k_gather_split_t<16, 2> : k_gather_split_t<16, 1>)<<<8 * sm_count(), 256, 0, s>>>(h, xh2, xl2, cells); break;
+            case 24: (p2 ? k_gather_split_t<24, 2> : k_gather_split_t<24, 1>)<<<8 * sm_count(), 256, 0, s>>>(h, xh2, xl2, cells); break;
+            default: (p2 ? k_gather_split_t<32, 2> : k_gather_split_t<32, 1>)<<<8 * sm_count(), 256, 0, s>>>(h, xh2, xl2, cells); break;
         }
     }
     // optional event timing of the GEMM alone (public synchronous calls only)
@@ -720,14 +724,15 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     const bool timed = sync && g_time_kernels.load() != 0 && cudaEventCreate(&ev[0]) == cudaSuccess &&
                        cudaEventCreate(&ev[1]) == cudaSuccess;
     if (timed) cudaEventRecord(ev[0], s);
+    const int probe = g_expire_waits.load();
     switch (bn) {
-        case 64: launch_gemm<64>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
-        case 128: launch_gemm<128>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
-        case 160: launch_gemm<160>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
-        case 192: launch_gemm<192>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
-        case 208: launch_gemm<208>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
-        case 224: launch_gemm<224>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
-        default: launch_gemm<256>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, s); break;
+        case 64: launch_gemm<64>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        case 128: launch_gemm<128>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        case 160: launch_gemm<160>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        case 192: launch_gemm<192>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        case 208: launch_gemm<208>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        case 224: launch_gemm<224>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        default: launch_gemm<256>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
     }
     if (timed) cudaEventRecord(ev[1], s);
     const float* nu1 = t->nu1_f;
@@ -742,7 +747,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
             default: (p2 ? launch_expand_g<32, 2> : launch_expand_g<32, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nr, dv3, ks, s); break;
         }
     } else {
-        k_expand<<<2048, 256, 0, s>>>(Y, h, nu1, delta, Lplus, Lout, cells, nv, nr, mode, ks);
+        k_expand<<<16 * sm_count(), 256, 0, s>>>(Y, h, nu1, delta, Lplus, Lout, cells, nv, nr, mode, ks);
     }
     g_launches += 3;
     g_levals += cells;
@@ -765,19 +770,6 @@ lbe_status tc_check(Ctx* c, DevTables* t) {
     cudaMemset(t->tc->err_dev, 0, sizeof(int));
     c->last_error = "tensor-core operator: a bounded wait expired";
     return LBE_TIMEOUT;
-}
-
-lbe_status tc_apply_L(Ctx* c, DevTables* t, int cells, const double* delta, const float* h, float* Lplus,
-                      float* Lout, cudaStream_t s) {
-    (void)t;
-    (void)cells;
-    (void)delta;
-    (void)h;
-    (void)Lplus;
-    (void)Lout;
-    (void)s;
-    c->last_error = "the tensor-core operator acts on the parity subspace: use lbe_apply_L_sym";
-    return LBE_UNSUPPORTED;
 }
 
 void tc_release(Ctx* c, DevTables* t) {

@@ -84,6 +84,7 @@ struct Job {
     lbe_problem pb{};
     lbe_result res{};
     int done = 0;
+    std::atomic<int> cancel{0};  // set by lbe_cancel; the service retires the job at its next boundary
     double t_submit = 0;  // seconds on the service clock
 };
 
@@ -99,8 +100,13 @@ struct Arena {
 extern std::atomic<unsigned long long> g_launches, g_h2d, g_d2h, g_levals;
 // optional event timing of the tensor-core GEMM (lbe_set_kernel_timing)
 extern std::atomic<int> g_time_kernels;
+// test hook of the GEMM's bounded waits (lbe_debug_expire_waits)
+extern std::atomic<int> g_expire_waits;
 void add_gemm_time(double ms);
 void get_gemm_time(unsigned long long* n, double* ms);
+// the same for the transport-sweep launches of the solves (false: timing off or capturing)
+bool sweep_timing_begin(cudaStream_t s, cudaEvent_t* ev);
+void sweep_timing_end(cudaStream_t s, cudaEvent_t* ev, double bytes);
 
 struct Ctx {
     int device = 0;
@@ -135,6 +141,10 @@ void dev_free(Ctx* c, void* p, size_t bytes);
 lbe_status arena_reserve(Ctx* c, Arena& a, size_t bytes);  // resets the carve offset
 void* arena_take(Arena& a, size_t bytes);                  // nullptr when it does not fit
 void arena_release(Ctx* c, Arena& a);
+
+// streaming multiprocessors of the current device (queried once per device); grid-stride
+// kernels launch a multiple of it
+int sm_count();
 
 // status helpers
 lbe_status cuda_status(Ctx* c, cudaError_t e, const char* where);

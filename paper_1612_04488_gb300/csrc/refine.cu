@@ -126,28 +126,28 @@ __global__ void k_range_add_f64(const double* __restrict__ b, const float* __res
 }
 void range_sub_f32(const double* h, const double* base, float* out, long n, cudaStream_t s) {
     g_launches += 1;
-    k_range_sub_f32<<<304, 256, 0, s>>>(h, base, out, n);
+    k_range_sub_f32<<<2 * sm_count(), 256, 0, s>>>(h, base, out, n);
 }
 void range_add_f64(const double* base, const float* inc, double* out, long n, cudaStream_t s) {
     g_launches += 1;
-    k_range_add_f64<<<304, 256, 0, s>>>(base, inc, out, n);
+    k_range_add_f64<<<2 * sm_count(), 256, 0, s>>>(base, inc, out, n);
 }
 
 void range_widen(const float* e, double* h, long n, cudaStream_t s) {
     g_launches += 1;
-    k_range_widen<<<152, 256, 0, s>>>(e, h, n);
+    k_range_widen<<<sm_count(), 256, 0, s>>>(e, h, n);
 }
 void range_copy(const double* a, double* b, long n, cudaStream_t s) {
     g_launches += 1;
-    k_range_copy<<<152, 256, 0, s>>>(a, b, n);
+    k_range_copy<<<sm_count(), 256, 0, s>>>(a, b, n);
 }
 void range_residual(const double* h, const double* h_old, float* r, long n, cudaStream_t s) {
     g_launches += 1;
-    k_range_residual<<<152, 256, 0, s>>>(h, h_old, r, n);
+    k_range_residual<<<sm_count(), 256, 0, s>>>(h, h_old, r, n);
 }
 void range_correct(const double* h_old, const float* e, double* h, long n, cudaStream_t s) {
     g_launches += 1;
-    k_range_correct<<<152, 256, 0, s>>>(h_old, e, h, n);
+    k_range_correct<<<sm_count(), 256, 0, s>>>(h_old, e, h, n);
 }
 
 lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs, double* U3_out,
@@ -220,7 +220,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
     if (st == LBE_OK) {
         for (int j = 0; j < n; ++j) inner_it[j] += I.hstate[j].iters;
         cudaMemcpyAsync(O.act.p, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, s);
-        k_widen<<<dim3(152, n), blk, 0, s>>>(I.h.as<float>(), O.h.as<double>(), O.sjobs.as<SweepJobDev>(),
+        k_widen<<<dim3(sm_count(), n), blk, 0, s>>>(I.h.as<float>(), O.h.as<double>(), O.sjobs.as<SweepJobDev>(),
                                              O.act.as<int>(), n3);
         g_launches += 1;
         // from now on the inner batch solves the homogeneous correction equation
@@ -284,7 +284,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         }
         k_set_rates<<<na, 32, 0, s>>>(O.ijobs.as<SisJobDev>(), O.act.as<int>(), O.mom.as<double>(),
                                       O.coef.as<double>(), O.states.as<JobState>());
-        k_copy64<<<dim3(152, na), blk, 0, s>>>(O.h.as<double>(), h_old, O.sjobs.as<SweepJobDev>(),
+        k_copy64<<<dim3(sm_count(), na), blk, 0, s>>>(O.h.as<double>(), h_old, O.sjobs.as<SweepJobDev>(),
                                                O.act.as<int>(), n3);
         g_launches += 2;
         // one FP64 SIS iteration: h = Phi(h_old), flags against the copy's flow rates
@@ -339,7 +339,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         if (!corr.empty()) {
             const int nk = (int)corr.size();
             cudaMemcpyAsync(O.act.p, corr.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s);
-            k_residual<<<dim3(152, nk), blk, 0, s>>>(O.h.as<double>(), h_old, r, O.sjobs.as<SweepJobDev>(),
+            k_residual<<<dim3(sm_count(), nk), blk, 0, s>>>(O.h.as<double>(), h_old, r, O.sjobs.as<SweepJobDev>(),
                                                      O.act.as<int>(), n3);
             g_launches += 1;
             for (int j : corr) {
@@ -358,7 +358,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
                             j, refs[j], I.hstate[j].iters, I.hstate[j].M, I.hstate[j].Q, I.hstate[j].rel);
             }
             cudaMemcpyAsync(O.act.p, corr.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s);
-            k_apply_correction<<<dim3(152, nk), blk, 0, s>>>(h_old, I.h.as<float>(), O.h.as<double>(),
+            k_apply_correction<<<dim3(sm_count(), nk), blk, 0, s>>>(h_old, I.h.as<float>(), O.h.as<double>(),
                                                              O.sjobs.as<SweepJobDev>(), O.act.as<int>(), n3);
             g_launches += 1;
             for (int j : corr) {

@@ -36,6 +36,7 @@ namespace {
 
 constexpr int kMaxSlotCellsX = 128;  // service geometry limits (per-slot coefficient regions)
 constexpr int kMaxSlotNs = 1024;
+constexpr long kBucketCells = 4096;  // cells of one bucket's pool (a request must fit in one)
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -301,7 +302,7 @@ void slot_set_correction(Bucket& b, int s) {
 struct Service {
     Ctx* c;
     std::vector<std::unique_ptr<Bucket>> buckets;
-    long cap_cells_default = 4096;
+    long cap_cells_default = kBucketCells;
 };
 
 }  // namespace
@@ -387,6 +388,13 @@ static void service_main(Ctx* c) {
         // ---- admit, in arrival order, while slots and cells allow -----------------------
         std::vector<Job*> still;
         for (Job* j : pending) {
+            if (j->cancel.load()) {  // withdrawn before admission
+                std::lock_guard<std::mutex> lk(c->mu);
+                j->res = lbe_result{};
+                j->res.status = LBE_CANCELLED;
+                j->done = 1;
+                continue;
+            }
             const lbe_problem& pb = j->pb;
             const bool refined = pb.precision == LBE_FP32_REFINED || pb.precision == LBE_BF16_REFINED;
             const int cells = lbe_problem_cells(&pb);
@@ -470,11 +478,12 @@ static void service_main(Ctx* c) {
             const lbe_status bad = (sj->F && sj->F->failed != LBE_OK)   ? sj->F->failed
                                    : (sj->D && sj->D->failed != LBE_OK) ? sj->D->failed
                                                                         : LBE_OK;
-            if (bad != LBE_OK) {  // a launch of one of its buckets failed: the request fails
+            const bool cancelled = sj->j->cancel.load() != 0;
+            if (bad != LBE_OK || cancelled) {  // a launch of its buckets failed, or it was withdrawn
                 {
                     std::lock_guard<std::mutex> lk(c->mu);
                     sj->j->res = lbe_result{};
-                    sj->j->res.status = bad;
+                    sj->j->res.status = bad != LBE_OK ? bad : LBE_CANCELLED;
                     sj->j->done = 1;
                 }
                 if (sj->F) release(sj->F, sj->fs);
@@ -588,6 +597,8 @@ lbe_status lbe_submit(lbe_ctx* ctx, const lbe_problem* pb, uint64_t* ticket) {
     if ((pb->geom.dim == 1 && pb->geom.ns > kMaxSlotNs) ||
         (pb->geom.dim == 2 && (pb->geom.nx > kMaxSlotCellsX || pb->geom.ny > kMaxSlotCellsX)))
         return bad_arg(ctx, "service geometry limit: ns <= 1024, nx, ny <= 128");
+    if (lbe_problem_cells(pb) > kBucketCells)
+        return bad_arg(ctx, "service limit: at most 4096 cells per request");
     auto job = std::make_unique<Job>();
     job->pb = *pb;
     job->t_submit = now_s();
@@ -612,6 +623,25 @@ lbe_status lbe_poll(lbe_ctx* ctx, uint64_t ticket, lbe_result* out, int* done) {
     if (it == ctx->jobs.end()) return bad_arg(ctx, "unknown ticket");
     *done = it->second->done;
     if (*done) *out = it->second->res;
+    return LBE_OK;
+}
+
+lbe_status lbe_cancel(lbe_ctx* ctx, uint64_t ticket) {
+    if (!ctx) return LBE_BAD_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->jobs.find(ticket);
+    if (it == ctx->jobs.end()) return bad_arg(ctx, "unknown ticket");
+    Job* j = it->second.get();
+    if (j->done) return LBE_OK;
+    j->cancel.store(1);
+    auto q = std::find(ctx->queue.begin(), ctx->queue.end(), j);
+    if (q != ctx->queue.end()) {  // not yet seen by the service
+        ctx->queue.erase(q);
+        j->res = lbe_result{};
+        j->res.status = LBE_CANCELLED;
+        j->done = 1;
+    }
+    ctx->cv.notify_all();
     return LBE_OK;
 }
 

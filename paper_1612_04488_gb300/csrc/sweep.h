@@ -11,8 +11,6 @@ struct DevTables;
 struct Ctx;
 
 // fsm_dense.cu: tensor-core operator on the parity subspace (float in / out; mode 1 or 2)
-lbe_status tc_apply_L(Ctx* c, DevTables* t, int cells, const double* delta, const float* h, float* Lplus,
-                      float* Lout, cudaStream_t s);
 lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h,
                         float* Lplus, float* Lout, cudaStream_t s, bool sync = true, const double* nd = nullptr,
                         double* G = nullptr);

@@ -11,10 +11,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbe.so")
 
-OK, NOT_CONVERGED, NAN, BAD_ARG, OOM, TIMEOUT, INTERNAL, UNSUPPORTED = range(8)
+OK, NOT_CONVERGED, NAN, BAD_ARG, OOM, TIMEOUT, INTERNAL, UNSUPPORTED, CANCELLED = range(9)
 POISEUILLE, THERMAL_TRANSPIRATION = 0, 1
 CIS, SIS = 0, 1
-FP64, FP32, BF16_REFINED, FP32_REFINED, DF32 = 0, 1, 2, 3, 4
+FP64, FP32, BF16_REFINED, FP32_REFINED, DF32, BF16 = 0, 1, 2, 3, 4, 5
 
 
 class Geometry(C.Structure):
@@ -37,7 +37,8 @@ class Result(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
-                ("cell_l_evals", C.c_uint64), ("dense_gemm_timed", C.c_uint64), ("dense_gemm_ms", C.c_double)]
+                ("cell_l_evals", C.c_uint64), ("dense_gemm_timed", C.c_uint64), ("dense_gemm_ms", C.c_double),
+                ("sweep_timed", C.c_uint64), ("sweep_ms", C.c_double), ("sweep_bytes", C.c_double)]
 
 
 def stats():
@@ -48,6 +49,11 @@ def stats():
 
 def set_kernel_timing(on):
     lib().lbe_set_kernel_timing(1 if on else 0)
+
+
+def debug_expire_waits(on):
+    """Test hook: the tensor-core GEMM's first pipeline wait runs out (lbe_debug_expire_waits)."""
+    lib().lbe_debug_expire_waits(1 if on else 0)
 
 
 _lib = None
@@ -77,12 +83,15 @@ def lib():
         L.lbe_poll.argtypes = [vp, C.c_uint64, C.POINTER(Result), C.POINTER(C.c_int)]
         L.lbe_set_max_active.argtypes = [vp, ip]
         L.lbe_set_stream.argtypes = [vp, vp]
-        L.lbe_apply_L_sym.argtypes = [vp, ip, C.c_double, ip, C.c_double, ip, ip, ip, vp, vp, vp, vp, vp]
+        L.lbe_apply_L_sym.argtypes = [vp, ip, C.c_double, ip, C.c_double, ip, ip, ip, vp, vp, vp, vp, vp, vp, vp]
         L.lbe_apply_L_noalloc.argtypes = [vp, ip, C.c_double, ip, C.c_double, ip, ip, vp, vp, vp, vp, vp]
         L.lbe_batch_create.argtypes = [vp, C.POINTER(Problem), ip, C.POINTER(vp)]
         L.lbe_batch_run.argtypes = [vp, C.POINTER(Result)]
         L.lbe_batch_destroy.argtypes = [vp]
         L.lbe_get_stats.argtypes = [C.POINTER(Stats)]
+        L.lbe_solve_from.argtypes = [vp, C.POINTER(Problem), dp, C.POINTER(Result), C.POINTER(Result), dp, dp]
+        L.lbe_cancel.argtypes = [vp, C.c_uint64]
+        L.lbe_debug_expire_waits.argtypes = [ip]
         _lib = L
     return _lib
 
@@ -145,6 +154,20 @@ class Context:
         self.check(st, (OK, NOT_CONVERGED))
         return res, U, (h.reshape((n,) + (pb.nv,) * 3) if want_h else None)
 
+    def solve_from(self, pb, h_in, prev=None, want_h=False, want_U=True):
+        """lbe_solve_from: resume a solve from the iterate h_in (and the flow rates of prev)."""
+        n = cells_of(pb)
+        hin = np.ascontiguousarray(h_in, dtype=np.float64).reshape(-1)
+        if hin.size != n * pb.nv ** 3:
+            raise ValueError("h_in must hold cells * nv^3 values")
+        U = np.zeros(n) if want_U else None
+        h = np.zeros(n * pb.nv ** 3) if want_h else None
+        res = Result()
+        st = lib().lbe_solve_from(self.h, C.byref(pb), _dptr(hin), C.byref(prev) if prev is not None else None,
+                                  C.byref(res), _dptr(U), _dptr(h))
+        self.check(st, (OK, NOT_CONVERGED))
+        return res, U, (h.reshape((n,) + (pb.nv,) * 3) if want_h else None)
+
     def solve_batch(self, pbs):
         arr = (Problem * len(pbs))(*pbs)
         res = (Result * len(pbs))()
@@ -159,9 +182,9 @@ class Context:
         return self.check(st)
 
     def apply_L_sym(self, nv, vmax, M, R, precision, parity, cells, delta_ptr, h_ptr, lplus_ptr, l_ptr,
-                    stream=None):
+                    nd_ptr=None, G_ptr=None, stream=None):
         st = lib().lbe_apply_L_sym(self.h, nv, vmax, M, R, precision, parity, cells, delta_ptr, h_ptr,
-                                   lplus_ptr, l_ptr, stream)
+                                   lplus_ptr, l_ptr, nd_ptr, G_ptr, stream)
         return self.check(st)
 
     def apply_L_noalloc(self, nv, vmax, M, R, precision, cells, delta_ptr, h_ptr, lplus_ptr, l_ptr,
@@ -199,6 +222,9 @@ class Context:
         t = C.c_uint64()
         self.check(lib().lbe_submit(self.h, C.byref(pb), C.byref(t)))
         return t.value
+
+    def cancel(self, ticket):
+        self.check(lib().lbe_cancel(self.h, ticket))
 
     def poll(self, ticket):
         res = Result()

@@ -3,7 +3,8 @@
 Callers that cannot allocate device memory (graph capture, latency-critical loops, host
 frameworks that own every device byte) get the same operator with scratch taken from a
 fixed 32 MiB device array.  Two calls in a row must both reproduce the allocating entry
-point, including cell counts that need several scratch slices with a ragged last one."""
+point bit for bit, including cell counts that need several scratch slices with a ragged
+last one."""
 import numpy as np
 import pytest
 
@@ -23,9 +24,8 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("nv,M,cells,prec,tol", [(32, 32, 10, lbe.FP32, 1e-6), (16, 16, 70, lbe.FP64, 1e-12),
-                                                 (32, 32, 2, lbe.FP64, 1e-12)])
-def test_noalloc_matches_allocating_entry_point(ctx, nv, M, cells, prec, tol):
+@pytest.mark.parametrize("nv,M,cells,prec", [(32, 32, 10, lbe.FP32), (16, 16, 70, lbe.FP64), (32, 32, 2, lbe.FP64)])
+def test_noalloc_matches_allocating_entry_point(ctx, nv, M, cells, prec):
     dt = torch.float64 if prec == lbe.FP64 else torch.float32
     h = torch.tensor(workloads.random_h(cells, nv, 6.0, seed=cells), device="cuda", dtype=dt)
     d = torch.linspace(0.3, 30.0, cells, device="cuda", dtype=torch.float64)
@@ -39,11 +39,9 @@ def test_noalloc_matches_allocating_entry_point(ctx, nv, M, cells, prec, tol):
         ctx.apply_L_noalloc(nv, 6.0, M, 4.5, prec, cells, d.data_ptr(), h.data_ptr(), out_p.data_ptr(),
                             out_l.data_ptr())
         torch.cuda.synchronize()
-        sp = ref_p.abs().max().item()
-        sl = ref_l.abs().max().item()
+        # the same kernels on the same per-cell data: the slicing of the cells changes nothing
         assert torch.isfinite(out_p).all() and torch.isfinite(out_l).all()
-        assert (out_p - ref_p).abs().max().item() <= tol * sp
-        assert (out_l - ref_l).abs().max().item() <= tol * sl
+        assert torch.equal(out_p, ref_p) and torch.equal(out_l, ref_l)
 
 
 def test_noalloc_rejects_oversize_and_unprepared(ctx):
