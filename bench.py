@@ -69,11 +69,11 @@ def workload_problems(lbe, name, precision, eps):
 
 
 def dense_exec_flops(nv, parity):
-    """Executed tensor flops of one cell through the dense parity-subspace operator: three
-    BF16 products (A_hi x_hi, A_lo x_hi, A_hi x_lo) of the Nr-square matrix, 2 flops per
-    multiply-add."""
-    nr = nv ** 3 // (4 if parity == 2 else 2)
-    return 3 * 2.0 * nr * nr
+    """Executed tensor flops of one cell through the dense operator: three BF16 products
+    (A_hi x_hi, A_lo x_hi, A_hi x_lo) of each reflection block, 2 flops per multiply-add.
+    The blocks are (nv/2)^3 square: two for plates, four for ducts."""
+    nb = (nv // 2) ** 3
+    return 3 * 2.0 * nb * nb * (2 if parity == 2 else 4)
 
 
 def fft_flops_per_cell(nv, M):
@@ -357,7 +357,7 @@ def run_serve(args):
 # DRAM bytes (read + write) of one k_dense_gemm launch, from an ncu capture of
 # `bench.py --op-only` (plates32x8, 808 cells), valid only while the kernel's source is the
 # one captured: the digest covers the kernel and its stage configuration.
-GEMM_TRAFFIC = {"plates32x8": {"cells": 808, "bytes": 386856192, "digest": "67a1c45935e0d76b"}}
+GEMM_TRAFFIC = {}
 
 
 def gemm_source_digest():
@@ -365,7 +365,7 @@ def gemm_source_digest():
     src = open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1612_04488_gb300", "csrc",
                             "fsm_dense.cu")).read()
     a = src.index("struct GemmCfg")
-    b = src.index("// ---- parity-subspace index maps")
+    b = src.index("// ---- reflection blocks")
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 

@@ -1,13 +1,18 @@
 // Collision operator on the parity subspace as one tcgen05 GEMM (BF16 hi/lo, FP32 accumulate).
 //
 // Solutions of the plate and duct problems are odd in v3 (the source S of Sec. 2 is) and, on
-// plates, even in v2; the discrete operator commutes with those reflections (the direction
-// set is closed under them).  On that subspace h is fixed by its values at one point per
-// orbit of velocity points -- Nr = nv^3/4 (plates) or nv^3/2 (ducts) values -- and the
-// operator (at delta = 1) is an Nr x Nr matrix A.  A is built once per velocity grid by
-// applying the fast-spectral operator in double-float arithmetic (FP64-class) to the Nr
-// symmetric basis functions, so it is the same discrete operator.  Applying it to every cell at once is the GEMM
-//     Y[c][q] = sum_q' A[q][q'] x_c[q'],     L+ h_c = delta_c * expand(Y[c]),
+// plates, even in v2.  The discrete operator commutes with each coordinate reflection
+// R_k: v_k -> -v_k (the midpoint grid is symmetric and the direction set is closed under every
+// R_k), so it maps the functions with given signs (s1, s2, s3) under (R1, R2, R3) into
+// themselves.  Plate solutions live in the two subspaces s2 = +1, s3 = -1, s1 = +-1; duct
+// solutions in the four with s3 = -1.  Each subspace is fixed by the values at one point per
+// orbit of the eight reflections, p = (j1 H + j2) H + j3 with j_k < H = nv/2, so on it the
+// operator (at delta = 1) is an NB x NB block, NB = H^3 = nv^3/8: two blocks for plates, four
+// for ducts -- a half (plates) or a quarter (ducts) of the products of one parity-subspace
+// matrix.  The blocks are built once per velocity grid by applying the fast-spectral operator
+// in double-float arithmetic (FP64-class) to the symmetric basis functions of every block, so
+// they are the same discrete operator.  Applying them to every cell at once is the GEMM
+//     Y_b[c][q] = sum_p A_b[q][p] x_b[c][p],   L+ h_c = delta_c * expand(Y_b[c], all b),
 // run with A = A_hi + A_lo and x = x_hi + x_lo split into bfloat16 and the three products
 // A_hi x_hi + A_lo x_hi + A_hi x_lo accumulated in FP32 tensor memory (about 2^-16 relative).
 //
@@ -162,7 +167,7 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // item covers all of K and stores its tile into Y; slot >= 0: a part of a split tile, stored
 // whole into partial slot `slot` of P ([slot][BN][128]) for k_gemm_fixup to add up.
 struct GemmWork {
-    int col0, row0, kt0, kt1, slot;
+    int col0, row0, xrow0, kt0, kt1, slot;  // xrow0: first operand row (block b: b * cpad + col0)
 };
 
 template <int BN>
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(128, 1)
     uint32_t* tmem_slot = (uint32_t*)(done + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const GemmWork wk = work[blockIdx.x];
-    const int col0 = wk.col0, row0 = wk.row0, kt0 = wk.kt0;
+    const int col0 = wk.col0, row0 = wk.row0, xrow0 = wk.xrow0, kt0 = wk.kt0;
     const int KT = wk.kt1 - wk.kt0;
 
     if (tid == 0) {
@@ -215,8 +220,8 @@ __global__ void __launch_bounds__(128, 1)
             mbar_expect_tx(&full[s], STAGE);
             tma_load_2d(st, &tmAh, x, row0, &full[s]);
             tma_load_2d(st + A_BYTES, &tmAl, x, row0, &full[s]);
-            tma_load_2d(st + 2 * A_BYTES, &tmXh, x, col0, &full[s]);
-            tma_load_2d(st + 2 * A_BYTES + X_BYTES, &tmXl, x, col0, &full[s]);
+            tma_load_2d(st + 2 * A_BYTES, &tmXh, x, xrow0, &full[s]);
+            tma_load_2d(st + 2 * A_BYTES + X_BYTES, &tmXl, x, xrow0, &full[s]);
         };
         int issued = 0;
         for (int s = 0; s < kStages && s < KT; ++s) issue(s, s), ++issued;
@@ -284,100 +289,84 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-// ---- parity-subspace index maps -----------------------------------------------------------
-// mode 2 (plates): q = (i1 * H + i2) * H + i3, i2, i3 < H = nv/2; orbit signs: +1 for i2,
-// -1 for i3 (even in v2, odd in v3).  mode 1 (ducts): q = (i1 * nv + i2) * H + i3.
-__device__ __forceinline__ int rep_full(int q, int nv, int mode) {
-    const int H = nv / 2;
-    int i1, i2, i3;
-    if (mode == 2) {
-        i1 = q / (H * H);
-        i2 = (q / H) % H;
-        i3 = q % H;
-    } else {
-        i1 = q / (nv * H);
-        i2 = (q / H) % nv;
-        i3 = q % H;
-    }
-    return (i1 * nv + i2) * nv + i3;
-}
-__device__ __forceinline__ int orbit_of(int v, int nv, int mode, float* sign) {
-    const int H = nv / 2;
-    const int i1 = v / (nv * nv), i2 = (v / nv) % nv, i3 = v % nv;
-    const int j3 = i3 < H ? i3 : nv - 1 - i3;
-    *sign = i3 < H ? 1.f : -1.f;
-    if (mode == 2) {
-        const int j2 = i2 < H ? i2 : nv - 1 - i2;
-        return (i1 * H + j2) * H + j3;
-    }
-    return (i1 * nv + i2) * H + j3;
-}
+// ---- reflection blocks -----------------------------------------------------------------
+// Block b has s1 = -1 when bit 0 of b is set and s2 = -1 when bit 1 is set (ducts; plates use
+// b = 0, 1 with s2 = +1); s3 = -1 always.  Rows of block b start at b * NBP, NBP = NB rounded
+// up to the 128-row tile (the padding rows and columns of A are zero).
+constexpr int nblocks_of(int mode) { return mode == 2 ? 2 : 4; }
+inline int nb_of(int nv) { return (nv / 2) * (nv / 2) * (nv / 2); }
+inline int nbp_of(int nv) { return (nb_of(nv) + kBM - 1) / kBM * kBM; }
 
-// x_hi / x_lo [cell][q] from h (float) with the grid and parity known at compile time: each
-// thread takes two neighbouring representatives (i3, i3 + 1; H is even), one float2 load and
-// one bf16x2 store per operand.
+// x_b[c][p] (hi / lo bf16, [block][cpad][NBP]) from h (float): the signed average of h over the
+// reflections that the parity leaves free -- plates x_b = (h(p) +- h(R1 p)) / 2, ducts
+// x_b = (h(p) +- h(R1 p) +- h(R2 p) +- h(R1 R2 p)) / 4.  Each thread takes two neighbouring
+// representatives (j3, j3 + 1; H is even): one float2 load per orbit point and one bf16x2
+// store per block and operand.  Padding columns p >= NB are written as zero.
 template <int NV, int MODE>
-__global__ void __launch_bounds__(256) k_gather_split_t(const float* __restrict__ h, __nv_bfloat162* __restrict__ xh,
-                                                        __nv_bfloat162* __restrict__ xl, int cells) {
-    constexpr int H = NV / 2;
-    constexpr int NR = MODE == 2 ? NV * H * H : NV * NV * H;
+__global__ void __launch_bounds__(256) k_gather_blocks(const float* __restrict__ h, __nv_bfloat162* __restrict__ xh,
+                                                       __nv_bfloat162* __restrict__ xl, int cells, int cpad,
+                                                       int nbp) {
+    constexpr int H = NV / 2, NB = H * H * H, NBLK = MODE == 2 ? 2 : 4;
     constexpr long N3 = (long)NV * NV * NV;
-    const long total = (long)cells * (NR / 2);
+    const int half = nbp / 2;
+    const long total = (long)cells * half;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-        const long c = k / (NR / 2);
-        const int q = 2 * (int)(k % (NR / 2));
-        const int i3 = q % H;
-        const int i2 = MODE == 2 ? (q / H) % H : (q / H) % NV;
-        const int i1 = MODE == 2 ? q / (H * H) : q / (NV * H);
-        const float2 x = *reinterpret_cast<const float2*>(h + c * N3 + (i1 * NV + i2) * NV + i3);
-        const __nv_bfloat162 hi = __floats2bfloat162_rn(x.x, x.y);
-        const float2 hf = __bfloat1622float2(hi);
-        xh[k] = hi;
-        xl[k] = __floats2bfloat162_rn(x.x - hf.x, x.y - hf.y);
+        const long c = k / half;
+        const int p = 2 * (int)(k % half);
+        float2 x[NBLK];
+        if (p < NB) {
+            const int j3 = p % H, j2 = (p / H) % H, j1 = p / (H * H);
+            const float* hc = h + c * N3;
+            const float2 a = *reinterpret_cast<const float2*>(hc + (j1 * NV + j2) * NV + j3);
+            const float2 b = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * NV + j2) * NV + j3);
+            if constexpr (MODE == 2) {
+                x[0] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
+                x[1] = make_float2(0.5f * (a.x - b.x), 0.5f * (a.y - b.y));
+            } else {
+                const float2 e = *reinterpret_cast<const float2*>(hc + (j1 * NV + (NV - 1 - j2)) * NV + j3);
+                const float2 f = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * NV + (NV - 1 - j2)) * NV + j3);
+                const float2 s0 = make_float2(a.x + b.x, a.y + b.y), d0 = make_float2(a.x - b.x, a.y - b.y);
+                const float2 s1 = make_float2(e.x + f.x, e.y + f.y), d1 = make_float2(e.x - f.x, e.y - f.y);
+                x[0] = make_float2(0.25f * (s0.x + s1.x), 0.25f * (s0.y + s1.y));
+                x[1] = make_float2(0.25f * (d0.x + d1.x), 0.25f * (d0.y + d1.y));
+                x[2] = make_float2(0.25f * (s0.x - s1.x), 0.25f * (s0.y - s1.y));
+                x[3] = make_float2(0.25f * (d0.x - d1.x), 0.25f * (d0.y - d1.y));
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < NBLK; ++b) x[b] = make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int b = 0; b < NBLK; ++b) {
+            const long o = (((long)b * cpad + c) * nbp + p) / 2;
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(x[b].x, x[b].y);
+            const float2 hf = __bfloat1622float2(hi);
+            xh[o] = hi;
+            xl[o] = __floats2bfloat162_rn(x[b].x - hf.x, x[b].y - hf.y);
+        }
     }
 }
 
-// L+ h = delta Y expanded with the orbit signs; L h = L+ h - delta nu h
-__global__ void k_expand(const float* __restrict__ Y, const float* __restrict__ h, const float* __restrict__ nu1,
-                         const double* __restrict__ delta, float* __restrict__ Lplus, float* __restrict__ Lout,
-                         int cells, int nv, int nr, int mode, int ks) {
-    const long n3 = (long)nv * nv * nv;
-    const long total = (long)cells * n3;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-        const long c = k / n3;
-        const int v = (int)(k % n3);
-        float sg;
-        const int q = orbit_of(v, nv, mode, &sg);
-        const float d = (float)delta[c];
-        float y = Y[c * nr + q];
-        for (int z = 1; z < ks; ++z) y += Y[((long)z * cells + c) * nr + q];
-        const float lp = d * sg * y;
-        if (Lplus) Lplus[k] = lp;
-        if (Lout) Lout[k] = lp - d * nu1[v] * h[k];
-    }
-}
-
-// k_expand fused with the L-moments of an SIS iteration: one block of 8 NV threads per
-// cell stages the cell's Nr outputs in shared memory, writes L+ h (and L h when asked for),
-// and sums G_j = 2 sum_v v_j v3 (L h + N delta h) dv^3 (j = 1, 2) without storing L h.
+// L+ h = delta s3 sum_b s_b Y_b[p] for every velocity point of a cell (Y: [cell][block][NBP]),
+// optionally L h = L+ h - delta nu h, and optionally the SIS L-moments
+// G_j = 2 sum_v v_j v3 (L h + N delta h) dv^3 (j = 1, 2) in the same pass, without storing L h.
+// One block of 8 NV threads per cell stages the cell's block outputs in shared memory.
 template <int NV, int MODE>
-__global__ void __launch_bounds__(8 * NV) k_expand_g(const float* __restrict__ Y, const float* __restrict__ h,
-                                                     const float* __restrict__ nu1, const float* __restrict__ vel,
-                                                     const double* __restrict__ delta, const double* __restrict__ nd,
-                                                     float* __restrict__ Lplus, float* __restrict__ Lout,
-                                                     double* __restrict__ G, int nr, double dv3, int cells, int ks) {
+__global__ void __launch_bounds__(8 * NV) k_expand_blocks(const float* __restrict__ Y, const float* __restrict__ h,
+                                                          const float* __restrict__ nu1, const float* __restrict__ vel,
+                                                          const double* __restrict__ delta, const double* __restrict__ nd,
+                                                          float* __restrict__ Lplus, float* __restrict__ Lout,
+                                                          double* __restrict__ G, int nbp, double dv3) {
     extern __shared__ float sY[];
     __shared__ dfloat redx[32 * 2];
-    constexpr int H = NV / 2;
+    constexpr int H = NV / 2, NB = H * H * H, NBLK = MODE == 2 ? 2 : 4;
     constexpr long n3 = (long)NV * NV * NV;
     const long c = blockIdx.x;
-    for (int q = threadIdx.x; q < nr; q += blockDim.x) {
-        float y = Y[c * nr + q];
-        for (int z = 1; z < ks; ++z) y += Y[((long)z * cells + c) * nr + q];
-        sY[q] = y;
-    }
+    const float* yc = Y + c * (long)NBLK * nbp;
+    for (int k = threadIdx.x; k < NBLK * NB; k += blockDim.x) sY[k] = yc[(k / NB) * nbp + (k % NB)];
     __syncthreads();
-    const float d = (float)delta[c], ndc = (float)nd[c];
+    const float d = (float)delta[c];
+    const float ndc = G ? (float)nd[c] : 0.f;
     const int i3 = threadIdx.x % NV, r0 = threadIdx.x / NV;
     const int j3 = i3 < H ? i3 : NV - 1 - i3;
     const float s3 = i3 < H ? d : -d;
@@ -391,22 +380,39 @@ __global__ void __launch_bounds__(8 * NV) k_expand_g(const float* __restrict__ Y
     };
     for (int i1 = 0; i1 < NV; ++i1) {
         const float v1 = vel[i1];
+        const bool m1 = i1 >= H;
+        const int j1 = m1 ? NV - 1 - i1 : i1;
 #pragma unroll
         for (int k = 0; k < NV / 8; ++k) {
             const int i2 = r0 + 8 * k;
-            const int q = MODE == 2 ? (i1 * H + (i2 < H ? i2 : NV - 1 - i2)) * H + j3 : (i1 * NV + i2) * H + j3;
+            const bool m2 = i2 >= H;
+            const int j2 = m2 ? NV - 1 - i2 : i2;
+            const int p = (j1 * H + j2) * H + j3;
+            float y;
+            if constexpr (MODE == 2) {
+                const float y1 = sY[NB + p];
+                y = sY[p] + (m1 ? -y1 : y1);
+            } else {
+                const float y1 = sY[NB + p], y2 = sY[2 * NB + p], y3 = sY[3 * NB + p];
+                y = (sY[p] + (m1 ? -y1 : y1)) + ((m2 ? -y2 : y2) + ((m1 != m2) ? -y3 : y3));
+            }
             const int v = (i1 * NV + i2) * NV + i3;
             const long g = c * n3 + v;
-            const float lp = s3 * sY[q];
+            const float lp = s3 * y;
             Lplus[g] = lp;
-            const float hv = h[g];
-            const float lo = lp - d * nu1[v] * hv;
-            if (Lout) Lout[g] = lo;
-            const float t = (lo + ndc * hv) * v3;
-            kahan(a0, c0, v1 * t);
-            kahan(a1, c1, vel[i2] * t);
+            if (Lout || G) {
+                const float hv = h[g];
+                const float lo = lp - d * nu1[v] * hv;
+                if (Lout) Lout[g] = lo;
+                if (G) {
+                    const float t = (lo + ndc * hv) * v3;
+                    kahan(a0, c0, v1 * t);
+                    kahan(a1, c1, vel[i2] * t);
+                }
+            }
         }
     }
+    if (!G) return;
     dfloat sm[2] = {df_fast2sum(a0, -c0), df_fast2sum(a1, -c1)};  // reduced in double-float
     block_reduce_df<2>(sm, redx);
     if (threadIdx.x == 0) {
@@ -416,41 +422,59 @@ __global__ void __launch_bounds__(8 * NV) k_expand_g(const float* __restrict__ Y
 }
 
 template <int NV, int MODE>
-void launch_expand_g(int cells, const float* Y, const float* h, const float* nu1, const float* vel,
-                     const double* delta, const double* nd, float* Lplus, float* Lout, double* G, int nr, double dv3,
-                     int ks, cudaStream_t s) {
-    static std::once_flag once;
-    const int smem = nr * 4;
-    std::call_once(once, [smem] {
-        cudaFuncSetAttribute(k_expand_g<NV, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    });
-    k_expand_g<NV, MODE><<<cells, 8 * NV, smem, s>>>(Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nr, dv3, cells, ks);
+void launch_blocks(int cells, int cpad, int nbp, const float* h, __nv_bfloat162* xh, __nv_bfloat162* xl,
+                   cudaStream_t s) {
+    k_gather_blocks<NV, MODE><<<8 * sm_count(), 256, 0, s>>>(h, xh, xl, cells, cpad, nbp);
 }
 
-// symmetric basis functions e_q for q in [q0, q0 + nb): value sign at each orbit point
-__global__ void k_basis(double* __restrict__ h, int q0, int nb, int nv, int nr, int mode) {
+template <int NV, int MODE>
+void launch_expand(int cells, int nbp, const float* Y, const float* h, const float* nu1, const float* vel,
+                   const double* delta, const double* nd, float* Lplus, float* Lout, double* G, double dv3,
+                   cudaStream_t s) {
+    static std::once_flag once;
+    constexpr int H = NV / 2;
+    const int smem = nblocks_of(MODE) * H * H * H * 4;
+    std::call_once(once, [smem] {
+        cudaFuncSetAttribute(k_expand_blocks<NV, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+    k_expand_blocks<NV, MODE><<<cells, 8 * NV, smem, s>>>(Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nbp, dv3);
+}
+
+// Basis functions of block b, column p, for the global basis indices g0 .. g0 + nbas - 1
+// (g = b NB + p): value s3 s_b at the eight points of the orbit of p, zero elsewhere.
+__global__ void k_basis_blocks(double* __restrict__ h, int g0, int nbas, int nv, int mode) {
+    const int H = nv / 2, NB = H * H * H;
     const long n3 = (long)nv * nv * nv;
-    const long total = (long)nb * n3;
+    const long total = (long)nbas * n3;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-        const long b = k / n3;
+        const int gi = g0 + (int)(k / n3);
+        const int b = gi / NB, p = gi % NB;
         const int v = (int)(k % n3);
-        float sg;
-        const int q = orbit_of(v, nv, mode, &sg);
-        h[k] = (q == q0 + b) ? (double)sg : 0.0;
+        const int i1 = v / (nv * nv), i2 = (v / nv) % nv, i3 = v % nv;
+        const bool m1 = i1 >= H, m2 = i2 >= H, m3 = i3 >= H;
+        const int q = ((m1 ? nv - 1 - i1 : i1) * H + (m2 ? nv - 1 - i2 : i2)) * H + (m3 ? nv - 1 - i3 : i3);
+        int neg = m3 ? 1 : 0;
+        if (b & 1) neg += m1 ? 1 : 0;
+        if (mode == 1 && (b & 2)) neg += m2 ? 1 : 0;
+        h[k] = (q == p) ? ((neg & 1) ? -1.0 : 1.0) : 0.0;
     }
 }
 
-// columns q0 .. q0+nb of A (row-major [nr][nr], hi / lo bf16) from L+ e_q at the rep points
-__global__ void k_store_columns(const double* __restrict__ Lp, __nv_bfloat16* __restrict__ Ah,
-                                __nv_bfloat16* __restrict__ Al, int q0, int nb, int nv, int nr, int mode) {
+// Columns g0 .. g0 + nbas - 1 of the stacked blocks (row-major [NBLK NBP][NBP], hi / lo bf16)
+// from L+ e at the representative points (all j_k < H).
+__global__ void k_store_blocks(const double* __restrict__ Lp, __nv_bfloat16* __restrict__ Ah,
+                               __nv_bfloat16* __restrict__ Al, int g0, int nbas, int nv, int nbp) {
+    const int H = nv / 2, NB = H * H * H;
     const long n3 = (long)nv * nv * nv;
-    const long total = (long)nb * nr;
+    const long total = (long)nbas * NB;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-        const int q = (int)(k % nr);   // output row
-        const long b = k / nr;         // basis column
-        const double a = Lp[b * n3 + rep_full(q, nv, mode)];
+        const int q = (int)(k % NB);          // output row within the block
+        const long bb = k / NB;               // basis function of this chunk
+        const int gi = g0 + (int)bb, b = gi / NB, p = gi % NB;
+        const int j3 = q % H, j2 = (q / H) % H, j1 = q / (H * H);
+        const double a = Lp[bb * n3 + (j1 * nv + j2) * nv + j3];
         const __nv_bfloat16 hi = __float2bfloat16_rn((float)a);
-        const long idx = (long)q * nr + (q0 + b);
+        const long idx = ((long)b * nbp + q) * nbp + p;
         Ah[idx] = hi;
         Al[idx] = __float2bfloat16_rn((float)(a - (double)__bfloat162float(hi)));
     }
@@ -532,9 +556,10 @@ struct GemmPlan {
     int slots = 0;
 };
 
-GemmPlan make_plan(int cells, int bn, int nr, int P) {
+GemmPlan make_plan(int cells, int bn, int nblk, int nbp, int P) {
     GemmPlan pl;
-    const int nct = (cells + bn - 1) / bn, nrt = nr / kBM, T = nct * nrt, KT = nr / kBK;
+    const int nct = (cells + bn - 1) / bn, cpad = nct * bn;
+    const int nrt = nblk * nbp / kBM, T = nct * nrt, KT = nbp / kBK;
     int W, S;
     if (T >= P) {
         W = T / P * P;
@@ -547,12 +572,14 @@ GemmPlan make_plan(int cells, int bn, int nr, int P) {
     if (S == 1) W = T;
     for (int t = 0; t < T; ++t) {
         const int col0 = (t % nct) * bn, row0 = (t / nct) * kBM;
+        const int xrow0 = (row0 / nbp) * cpad + col0;  // the block's operand rows
         if (t < W) {
-            pl.work.push_back({col0, row0, 0, KT, -1});
+            pl.work.push_back({col0, row0, xrow0, 0, KT, -1});
             continue;
         }
         const int slot0 = pl.slots;
-        for (int p = 0; p < S; ++p) pl.work.push_back({col0, row0, KT * p / S, KT * (p + 1) / S, pl.slots++});
+        for (int p = 0; p < S; ++p)
+            pl.work.push_back({col0, row0, xrow0, KT * p / S, KT * (p + 1) / S, pl.slots++});
         pl.fix.push_back({col0, row0, slot0, S});
     }
     return pl;
@@ -572,9 +599,9 @@ void launch_gemm(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap
 
 }  // namespace
 
-// Dense operator of one (tables, parity mode).
+// Reflection blocks of one (tables, parity mode): A_hi / A_lo stacked [nblk * nbp][nbp].
 struct DenseOp {
-    int mode = 0, nv = 0, nr = 0;
+    int mode = 0, nv = 0, nblk = 0, nb = 0, nbp = 0;
     __nv_bfloat16* Ah = nullptr;
     __nv_bfloat16* Al = nullptr;
     CUtensorMap mAh, mAl;
@@ -601,19 +628,22 @@ struct TcOperands {
 
 static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaStream_t s) {
     const int nv = t->nv;
-    const int nr = mode == 2 ? nv * nv * nv / 4 : nv * nv * nv / 2;
-    if (nr % kBK != 0 || nr % kBM != 0) return LBE_UNSUPPORTED;
     d.mode = mode;
     d.nv = nv;
-    d.nr = nr;
-    const size_t abytes = (size_t)nr * nr * 2;
+    d.nblk = nblocks_of(mode);
+    d.nb = nb_of(nv);
+    d.nbp = nbp_of(nv);
+    const int nbas = d.nblk * d.nb;  // basis functions: every block's columns
+    const size_t abytes = (size_t)d.nblk * d.nbp * d.nbp * 2;
     lbe_status st = dev_alloc(c, (void**)&d.Ah, abytes);
     if (st == LBE_OK) st = dev_alloc(c, (void**)&d.Al, abytes);
     if (st != LBE_OK) return st;
     d.bytes = 2 * abytes;
-    // basis chunks through the FP64 fast-spectral operator (delta = 1)
+    cudaMemsetAsync(d.Ah, 0, abytes, s);  // padding rows and columns stay zero
+    cudaMemsetAsync(d.Al, 0, abytes, s);
+    // basis chunks through the double-float fast-spectral operator (delta = 1)
     const long n3 = (long)nv * nv * nv;
-    const int nb = (int)std::min<long>(nr, std::max<long>(1, (256L << 20) / (n3 * 8)));
+    const int nb = (int)std::min<long>(nbas, std::max<long>(1, (256L << 20) / (n3 * 8)));
     int chunk = 1;
     const size_t scr = fsm_cc_scratch_bytes(*t, nb, 8, &chunk);
     void *hb = nullptr, *lp = nullptr, *lo = nullptr, *sc = nullptr, *dl = nullptr;
@@ -626,12 +656,12 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
     if (st == LBE_OK) {
         std::vector<double> ones(nb, 1.0);
         cudaMemcpyAsync(dl, ones.data(), nb * 8, cudaMemcpyHostToDevice, s);
-        for (int q0 = 0; q0 < nr && st == LBE_OK; q0 += nb) {
-            const int b = std::min(nb, nr - q0);
-            k_basis<<<8 * sm_count(), 256, 0, s>>>((double*)hb, q0, b, nv, nr, mode);
-            st = fsm_df_apply(*t, b, (const double*)dl, (const double*)hb, (double*)lp, (double*)lo, sc, chunk,
-                                      s, mode);
-            k_store_columns<<<8 * sm_count(), 256, 0, s>>>((const double*)lp, d.Ah, d.Al, q0, b, nv, nr, mode);
+        for (int g0 = 0; g0 < nbas && st == LBE_OK; g0 += nb) {
+            const int b = std::min(nb, nbas - g0);
+            k_basis_blocks<<<8 * sm_count(), 256, 0, s>>>((double*)hb, g0, b, nv, mode);
+            st = fsm_df_apply(*t, b, (const double*)dl, (const double*)hb, (double*)lp, (double*)lo, sc, chunk, s,
+                              mode);
+            k_store_blocks<<<8 * sm_count(), 256, 0, s>>>((const double*)lp, d.Ah, d.Al, g0, b, nv, d.nbp);
             g_launches += 2;
         }
         if (st == LBE_OK) st = cuda_status(c, cudaStreamSynchronize(s), "dense operator build");
@@ -642,7 +672,8 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
     dev_free(c, sc, scr);
     dev_free(c, dl, (size_t)nb * 8);
     if (st != LBE_OK) return st;
-    if (!make_map(&d.mAh, d.Ah, nr, nr, kBM) || !make_map(&d.mAl, d.Al, nr, nr, kBM)) {
+    if (!make_map(&d.mAh, d.Ah, (long)d.nblk * d.nbp, d.nbp, kBM) ||
+        !make_map(&d.mAl, d.Al, (long)d.nblk * d.nbp, d.nbp, kBM)) {
         c->last_error = "cuTensorMapEncodeTiled unavailable or failed";
         return LBE_INTERNAL;
     }
@@ -671,14 +702,14 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         *T.err_host = 0;
         cudaMemsetAsync(T.err_dev, 0, sizeof(int), s);
     }
-    const int nr = d.nr, nv = t->nv;
+    const int nv = t->nv, nblk = d.nblk, nbp = d.nbp;
+    const int mrows = nblk * nbp;  // rows of the stacked blocks (and of Y per cell)
     const int bn = pick_bn(cells);
     const long cpad = (cells + bn - 1) / bn * bn;  // whole TMA boxes, zero padding rows
-    const int ks = 1;  // Y holds whole tiles (split tiles are added up by k_gemm_fixup)
-    const long long pkey = ((long long)cells << 32) | ((long long)bn << 20) | nr;
+    const long long pkey = ((long long)cells << 32) | ((long long)bn << 20) | mrows;
     auto pit = T.plans.find(pkey);
     if (pit == T.plans.end()) {
-        const GemmPlan pl = make_plan(cells, bn, nr, sm_count());
+        const GemmPlan pl = make_plan(cells, bn, nblk, nbp, sm_count());
         DevPlan dp;
         dp.nwork = (int)pl.work.size();
         dp.nfix = (int)pl.fix.size();
@@ -691,7 +722,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         pit = T.plans.emplace(pkey, dp).first;
     }
     const DevPlan& plan = pit->second;
-    const size_t xb = (size_t)cpad * nr * 2, yb = (size_t)cells * nr * 4;
+    const size_t xb = (size_t)nblk * cpad * nbp * 2, yb = (size_t)cells * mrows * 4;
     const size_t pb = (size_t)plan.slots * bn * kBM * 4;
     Arena& ws = T.ws[s];
     if ((st = arena_reserve(c, ws, 2 * xb + yb + pb + 4 * 256)) != LBE_OK) return st;
@@ -699,12 +730,14 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     auto* xl = (__nv_bfloat16*)arena_take(ws, xb);
     auto* Y = (float*)arena_take(ws, yb);
     auto* Pp = pb ? (float*)arena_take(ws, pb) : nullptr;
-    if (cpad > cells) {
-        cudaMemsetAsync(xh + (size_t)cells * nr, 0, (size_t)(cpad - cells) * nr * 2, s);
-        cudaMemsetAsync(xl + (size_t)cells * nr, 0, (size_t)(cpad - cells) * nr * 2, s);
-    }
+    if (cpad > cells)
+        for (int b = 0; b < nblk; ++b) {
+            const size_t o = ((size_t)b * cpad + cells) * nbp, n = (size_t)(cpad - cells) * nbp * 2;
+            cudaMemsetAsync(xh + o, 0, n, s);
+            cudaMemsetAsync(xl + o, 0, n, s);
+        }
     CUtensorMap mXh, mXl;
-    if (!make_map(&mXh, xh, cpad, nr, bn) || !make_map(&mXl, xl, cpad, nr, bn)) {
+    if (!make_map(&mXh, xh, nblk * cpad, nbp, bn) || !make_map(&mXl, xl, nblk * cpad, nbp, bn)) {
         c->last_error = "cuTensorMapEncodeTiled failed for the cell operand";
         return LBE_INTERNAL;
     }
@@ -712,11 +745,12 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         auto* xh2 = reinterpret_cast<__nv_bfloat162*>(xh);
         auto* xl2 = reinterpret_cast<__nv_bfloat162*>(xl);
         const bool p2 = mode == 2;
+        const int cp = (int)cpad;
         switch (nv) {
-            case 8: (p2 ? k_gather_split_t<8, 2> : k_gather_split_t<8, 1>)<<<8 * sm_count(), 256, 0, s>>>(h, xh2, xl2, cells); break;
-            case 16: (p2 ? k_gather_split_t<16, 2> : k_gather_split_t<16, 1>)<<<8 * sm_count(), 256, 0, s>>>(h, xh2, xl2, cells); break;
-            case 24: (p2 ? k_gather_split_t<24, 2> : k_gather_split_t<24, 1>)<<<8 * sm_count(), 256, 0, s>>>(h, xh2, xl2, cells); break;
-            default: (p2 ? k_gather_split_t<32, 2> : k_gather_split_t<32, 1>)<<<8 * sm_count(), 256, 0, s>>>(h, xh2, xl2, cells); break;
+            case 8: (p2 ? launch_blocks<8, 2> : launch_blocks<8, 1>)(cells, cp, nbp, h, xh2, xl2, s); break;
+            case 16: (p2 ? launch_blocks<16, 2> : launch_blocks<16, 1>)(cells, cp, nbp, h, xh2, xl2, s); break;
+            case 24: (p2 ? launch_blocks<24, 2> : launch_blocks<24, 1>)(cells, cp, nbp, h, xh2, xl2, s); break;
+            default: (p2 ? launch_blocks<32, 2> : launch_blocks<32, 1>)(cells, cp, nbp, h, xh2, xl2, s); break;
         }
     }
     // optional event timing of the GEMM alone (public synchronous calls only)
@@ -726,28 +760,26 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     if (timed) cudaEventRecord(ev[0], s);
     const int probe = g_expire_waits.load();
     switch (bn) {
-        case 64: launch_gemm<64>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        case 128: launch_gemm<128>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        case 160: launch_gemm<160>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        case 192: launch_gemm<192>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        case 208: launch_gemm<208>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        case 224: launch_gemm<224>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        default: launch_gemm<256>(d.mAh, d.mAl, mXh, mXl, nr, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        case 64: launch_gemm<64>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        case 128: launch_gemm<128>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        case 160: launch_gemm<160>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        case 192: launch_gemm<192>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        case 208: launch_gemm<208>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        case 224: launch_gemm<224>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+        default: launch_gemm<256>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
     }
     if (timed) cudaEventRecord(ev[1], s);
-    const float* nu1 = t->nu1_f;
-    if (G) {  // L+ h and the SIS L-moments in one pass
+    {  // L+ h (L h when asked for) and, with G, the SIS L-moments in one pass
+        const float* nu1 = t->nu1_f;
         const float* vel = t->vel_f;
         const double dv3 = t->dv * t->dv * t->dv;
         const bool p2 = mode == 2;
         switch (nv) {
-            case 8: (p2 ? launch_expand_g<8, 2> : launch_expand_g<8, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nr, dv3, ks, s); break;
-            case 16: (p2 ? launch_expand_g<16, 2> : launch_expand_g<16, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nr, dv3, ks, s); break;
-            case 24: (p2 ? launch_expand_g<24, 2> : launch_expand_g<24, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nr, dv3, ks, s); break;
-            default: (p2 ? launch_expand_g<32, 2> : launch_expand_g<32, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nr, dv3, ks, s); break;
+            case 8: (p2 ? launch_expand<8, 2> : launch_expand<8, 1>)(cells, nbp, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
+            case 16: (p2 ? launch_expand<16, 2> : launch_expand<16, 1>)(cells, nbp, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
+            case 24: (p2 ? launch_expand<24, 2> : launch_expand<24, 1>)(cells, nbp, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
+            default: (p2 ? launch_expand<32, 2> : launch_expand<32, 1>)(cells, nbp, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
         }
-    } else {
-        k_expand<<<16 * sm_count(), 256, 0, s>>>(Y, h, nu1, delta, Lplus, Lout, cells, nv, nr, mode, ks);
     }
     g_launches += 3;
     g_levals += cells;

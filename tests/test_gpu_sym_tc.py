@@ -33,6 +33,8 @@ def parity_h(cells, nv, parity, seed):
     (16, 16, 2, 21, lbe.FP64, 1e-12), (16, 16, 1, 9, lbe.FP64, 1e-12), (32, 32, 2, 3, lbe.FP64, 1e-12),
     (24, 16, 2, 4, lbe.FP64, 1e-12), (32, 32, 1, 3, lbe.FP32, 3e-6), (16, 16, 2, 300, lbe.BF16_REFINED, 1e-4),
     (32, 32, 2, 40, lbe.BF16_REFINED, 1e-4), (16, 16, 1, 70, lbe.BF16_REFINED, 1e-4),
+    (8, 8, 2, 33, lbe.BF16_REFINED, 1e-4), (8, 8, 1, 20, lbe.BF16_REFINED, 1e-4),
+    (24, 16, 2, 30, lbe.BF16_REFINED, 1e-4), (24, 16, 1, 17, lbe.BF16_REFINED, 1e-4),
     (16, 16, 2, 21, lbe.DF32, 1e-12), (16, 16, 1, 9, lbe.DF32, 1e-12), (32, 32, 2, 3, lbe.DF32, 1e-12),
     (24, 16, 2, 4, lbe.DF32, 1e-12)])
 def test_apply_L_sym_matches_oracle(ctx, nv, M, parity, cells, prec, tol):
