@@ -70,10 +70,14 @@ def workload_problems(lbe, name, precision, eps):
 
 def dense_exec_flops(nv, parity):
     """Executed tensor flops of one cell through the dense operator: three BF16 products
-    (A_hi x_hi, A_lo x_hi, A_hi x_lo) of each reflection block, 2 flops per multiply-add.
-    The blocks are (nv/2)^3 square: two for plates, four for ducts."""
-    nb = (nv // 2) ** 3
-    return 3 * 2.0 * nb * nb * (2 if parity == 2 else 4)
+    (A_hi x_hi, A_lo x_hi, A_hi x_lo) of each sub-block, 2 flops per multiply-add.  The
+    sub-blocks: the reflection blocks ((nv/2)^3 square) that the v1 <-> v2 transposition maps
+    to others, and the even and odd halves (H^2 (H +- 1) / 2 square, H = nv/2) of those it maps
+    to themselves -- plates {even, odd, whole}, ducts {even, odd, whole, whole, even, odd}."""
+    H = nv // 2
+    nf, ns, na = H ** 3, H * H * (H + 1) // 2, H * H * (H - 1) // 2
+    sizes = [ns, na, nf] if parity == 2 else [ns, na, nf, nf, ns, na]
+    return 3 * 2.0 * sum(n * n for n in sizes)
 
 
 def fft_flops_per_cell(nv, M):
@@ -365,7 +369,7 @@ def gemm_source_digest():
     src = open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1612_04488_gb300", "csrc",
                             "fsm_dense.cu")).read()
     a = src.index("struct GemmCfg")
-    b = src.index("// ---- reflection blocks")
+    b = src.index("// ---- reflection blocks and their transposition halves")
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
@@ -606,7 +610,7 @@ def run_ours(args):
         "iterations": iters, "refinements": refinements, "status": status,
         "max_rel_err_vs_fp64": err,
         "l_evals_per_s": l_evals["op"], "l_evals_per_s_fp64": l_evals["fp64_fft_sym"], "l_evals_detail": l_evals,
-        "roofline": roofline, "roofline_sweep": sweep, "fp64_gpu": fp64,
+        "roofline": roofline, "roofline_sweep": sweep, "fp64_gpu": fp64, "autotuner": ctx.tuning_report(),
         "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -311,6 +311,13 @@ lbe_status lbe_get_stats(lbe_stats* out);
 /* Process-wide switch (0 = off, the default) for the event timing described above. */
 lbe_status lbe_set_kernel_timing(int on);
 
+/* The autotuner's decisions in this context, one text line each (for logs and benchmark
+ * records): launch choices measured at first use, e.g. the schedule of the 1D float transport
+ * sweep per (grid, number of problems, nodes) class.  Every schedule computes the same bits, so
+ * the choices change speed only.  buf (host, cap bytes) receives a NUL-terminated string;
+ * LBE_BAD_ARG if it does not fit (the text is then truncated). */
+lbe_status lbe_tuning_report(lbe_ctx* ctx, char* buf, size_t cap);
+
 /* Test hook for the bounded-wait failure path (0 = off, the default).  While on, every CTA of
  * the tensor-core GEMM first waits on a shared-memory barrier that nothing completes, with a
  * limit of about 1e5 cycles; when the limit passes the CTA raises the failure word, waits

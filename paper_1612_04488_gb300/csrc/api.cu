@@ -234,6 +234,7 @@ DevTables* get_tables(Ctx* c, int nv, double vmax, int M, double R, lbe_status* 
     t->cq = h.cq;
     t->sym_reps1 = h.sym_reps1;
     t->sym_reps2 = h.sym_reps2;
+    t->tuning = new Tuning();
     size_t b = 0;
     lbe_status s = LBE_OK;
     if (s == LBE_OK) s = upload(c, &t->feq_d, h.feq, &b);
@@ -258,6 +259,7 @@ DevTables* get_tables(Ctx* c, int nv, double vmax, int M, double R, lbe_status* 
                         (void*)t->feq_x, (void*)t->nu1_x, (void*)t->mult_x, (void*)t->ab_x})
             if (p) cudaFree(p);
         c->used -= std::min(b, c->used);
+        delete t->tuning;
         return nullptr;
     }
     DevTables* raw = t.get();
@@ -463,7 +465,7 @@ lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Arena* ar
 
 // One iteration over the active jobs.  Contiguous active jobs share FSM launches.
 template <typename T>
-void batch_iterate(Batch& B) {
+void batch_iterate(Batch& B, bool upload, bool read) {
     cudaStream_t s = B.s;
     const DevTables& t = *B.t;
     const long n3 = (long)t.nv * t.nv * t.nv;
@@ -530,8 +532,10 @@ void batch_iterate(Batch& B) {
     // the device active list is [act1..., act2...]
     std::vector<int> ordered(act1);
     ordered.insert(ordered.end(), act2.begin(), act2.end());
-    cudaMemcpyAsync(B.act.p, ordered.data(), na * sizeof(int), cudaMemcpyHostToDevice, s);
-    g_h2d += na * sizeof(int);
+    if (upload) {
+        cudaMemcpyAsync(B.act.p, ordered.data(), na * sizeof(int), cudaMemcpyHostToDevice, s);
+        g_h2d += na * sizeof(int);
+    }
     int* dact = B.act.as<int>();
     int mc1 = 0, mc2 = 0;  // largest coefficient block of a job (shared-memory staging)
     for (int j : act1) mc1 = std::max(mc1, 6 * B.sj[j].ncell);
@@ -554,24 +558,113 @@ void batch_iterate(Batch& B) {
                       B.coef.as<double>(), B.work.as<double>(), B.dU.as<double>(), B.U3.as<double>(),
                       B.states.as<JobState>(), s);
     launch_correct<T>(t, na, hh, h, B.dU.as<double>(), B.extra.p ? B.extra.as<T>() : nullptr,
-                      B.sjobs.as<SweepJobDev>(), dact, s);
-    cudaMemcpyAsync(B.hstate.data(), B.states.p, B.njobs * sizeof(JobState), cudaMemcpyDeviceToHost, s);
-    g_d2h += B.njobs * sizeof(JobState);
+                      B.sjobs.as<SweepJobDev>(), dact, s, B.states.as<JobState>());
+    if (read) {
+        cudaMemcpyAsync(B.hstate.data(), B.states.p, B.njobs * sizeof(JobState), cudaMemcpyDeviceToHost, s);
+        g_d2h += B.njobs * sizeof(JobState);
+    }
 }
 
 static double host_now() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Iterations that can be queued before the next convergence check without passing any
+// problem's predicted convergence: from the last two changes of each active problem (its
+// contraction per iteration) the iterations it still needs, the smallest of them, at most 8.
+// Queued iterations leave finished problems untouched (JobState::skip), so a wrong guess
+// only costs the extra iterations of the problems still running.
+static int predict_chunk(const Batch& B, int left) {
+    int k = 8;
+    for (int j : B.active) {
+        const JobState& st = B.hstate[j];
+        if (st.iters < 3) return 1;
+        const SisJobDev& q = B.ij[j];
+        const double dM = std::fabs(st.M - st.Mprev), dQ = std::fabs(st.Q - st.Qprev);
+        const double rel = q.crit == 0 ? std::max(dM / std::fabs(st.M), dQ / std::fabs(st.Q))
+                                       : std::max(dM, dQ) / std::max(std::fabs(st.M), std::fabs(st.Q));
+        if (!(rel > 0) || !std::isfinite(rel) || q.eps <= 0) {
+            if (q.eps > 0) return 1;
+        } else {
+            const double om = std::min(0.95, std::max(0.05, B.omega.size() > (size_t)j ? B.omega[j] : 0.9));
+            const double need = std::log(q.eps / rel) / std::log(om);
+            k = std::min(k, std::max(1, (int)std::floor(need)));
+        }
+        k = std::min(k, std::max(1, q.max_iter - st.iters));
+    }
+    return std::max(1, std::min(k, left));
+}
+
+template <typename T>
+static void run_chunk(Batch& B, int K) {
+    // the first iteration uploads the active list and runs uncaptured, which also warms every
+    // workspace the iteration uses; the rest replay it as a CUDA graph
+    batch_iterate<T>(B, true, K == 1);
+    if (K == 1) return;
+    const int rest = K - 1;
+    bool use_graph = B.graphs_ok && rest >= 2 && B.s != nullptr && B.s != cudaStreamLegacy &&
+                     B.s != cudaStreamPerThread;
+    if (use_graph && (!B.graph || B.graph_key != B.active)) {
+        if (B.graph) {
+            cudaGraphExecDestroy(B.graph);
+            B.graph = nullptr;
+        }
+        const unsigned long long l0 = g_launches.load(), e0 = g_levals.load();
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(B.s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            batch_iterate<T>(B, false, false);
+            ok = cudaStreamEndCapture(B.s, &g) == cudaSuccess && g != nullptr;
+        }
+        if (ok) ok = cudaGraphInstantiate(&B.graph, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        B.graph_launches = g_launches.load() - l0;
+        B.graph_levals = g_levals.load() - e0;
+        g_launches -= B.graph_launches;  // counted per replay below
+        g_levals -= B.graph_levals;
+        if (!ok) {
+            cudaGetLastError();
+            if (B.graph) cudaGraphExecDestroy(B.graph);
+            B.graph = nullptr;
+            B.graphs_ok = false;
+            B.op_status = LBE_OK;
+            use_graph = false;
+        } else {
+            B.graph_key = B.active;
+        }
+    }
+    if (use_graph) {
+        for (int k = 0; k < rest; ++k) {
+            cudaGraphLaunch(B.graph, B.s);
+            g_launches += B.graph_launches;
+            g_levals += B.graph_levals;
+        }
+        cudaMemcpyAsync(B.hstate.data(), B.states.p, B.njobs * sizeof(JobState), cudaMemcpyDeviceToHost, B.s);
+        g_d2h += B.njobs * sizeof(JobState);
+    } else {
+        for (int k = 0; k < rest; ++k) batch_iterate<T>(B, false, k == rest - 1);
+    }
+}
+
 lbe_status batch_run(Batch& B, int max_steps) {
+    // a graph holds the workspace addresses of its capture; other calls between two runs may
+    // have moved them, so every run captures afresh
+    if (B.graph) {
+        cudaGraphExecDestroy(B.graph);
+        B.graph = nullptr;
+    }
+    B.graph_key.clear();
     int steps = 0;
     B.t_start = host_now();
     B.t_done.assign(B.njobs, 0.0);
+    B.omega.assign(B.njobs, 0.9);
+    std::vector<double> last(B.njobs, 0.0);
     while (!B.active.empty() && steps < max_steps) {
+        const int K = predict_chunk(B, max_steps - steps);
         if (B.prec == LBE_FP64)
-            batch_iterate<double>(B);
+            run_chunk<double>(B, K);
         else
-            batch_iterate<float>(B);
+            run_chunk<float>(B, K);
         lbe_status st = cuda_status(B.c, cudaStreamSynchronize(B.s), "iterate");
         if (st == LBE_OK && B.use_tc) st = tc_check(B.c, B.t);
         if (st == LBE_OK) st = B.op_status;
@@ -579,21 +672,26 @@ lbe_status batch_run(Batch& B, int max_steps) {
         std::vector<int> keep;
         const double t = host_now();
         for (int j : B.active) {
-            if (!B.hstate[j].done)
+            const JobState& js = B.hstate[j];
+            // contraction per iteration from successive relative changes
+            if (last[j] > 0 && js.rel > 0 && std::isfinite(js.rel))
+                B.omega[j] = std::pow(js.rel / last[j], 1.0 / K);
+            last[j] = js.rel;
+            if (!js.done)
                 keep.push_back(j);
             else
                 B.t_done[j] = t;
         }
         B.active.swap(keep);
-        ++steps;
+        steps += K;
     }
     const double t = host_now();
     for (int j : B.active) B.t_done[j] = t;
     return LBE_OK;
 }
 
-template void batch_iterate<double>(Batch&);
-template void batch_iterate<float>(Batch&);
+template void batch_iterate<double>(Batch&, bool, bool);
+template void batch_iterate<float>(Batch&, bool, bool);
 
 void fill_result(const Batch& B, int j, lbe_result* r, double secs) {
     const JobState& s = B.hstate[j];
@@ -673,6 +771,8 @@ lbe_status lbe_destroy(lbe_ctx* ctx) {
     for (auto& kv : ctx->tables) {
         DevTables* t = kv.second.get();
         tc_release(ctx, t);
+        delete t->tuning;
+        t->tuning = nullptr;
         for (void* p : {(void*)t->feq_d, (void*)t->nu1_d, (void*)t->mult_d, (void*)t->ab_d, (void*)t->vel_d,
                         (void*)t->feq_f, (void*)t->nu1_f, (void*)t->mult_f, (void*)t->ab_f, (void*)t->vel_f,
                         (void*)t->feq_x, (void*)t->nu1_x, (void*)t->mult_x, (void*)t->ab_x})
@@ -682,6 +782,7 @@ lbe_status lbe_destroy(lbe_ctx* ctx) {
     cudaDeviceSynchronize();
     arena_release(ctx, ctx->solve_arena);
     arena_release(ctx, ctx->apply_arena);
+    for (auto& a : ctx->refine_arena) arena_release(ctx, a);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
     return LBE_OK;
@@ -1077,6 +1178,22 @@ lbe_status lbe_get_stats(lbe_stats* out) {
 lbe_status lbe_set_kernel_timing(int on) {
     g_time_kernels.store(on ? 1 : 0);
     return LBE_OK;
+}
+
+lbe_status lbe_tuning_report(lbe_ctx* ctx, char* buf, size_t cap) {
+    if (!ctx || !buf || cap == 0) return LBE_BAD_ARG;
+    std::string out;
+    std::lock_guard<std::mutex> lk(ctx->tables_mu);
+    for (auto& kv : ctx->tables) {
+        Tuning* tu = kv.second->tuning;
+        if (!tu) continue;
+        std::lock_guard<std::mutex> lk2(tu->mu);
+        for (auto& line : tu->log) out += line + "\n";
+    }
+    const size_t n = std::min(out.size(), cap - 1);
+    memcpy(buf, out.data(), n);
+    buf[n] = 0;
+    return out.size() < cap ? LBE_OK : LBE_BAD_ARG;
 }
 
 lbe_status lbe_debug_expire_waits(int on) {

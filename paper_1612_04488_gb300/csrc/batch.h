@@ -50,6 +50,19 @@ struct Batch {
     std::vector<int> active;
     double t_start = 0;            // host clock (s) when batch_run began
     std::vector<double> t_done;    // host clock (s) when each job's flag was seen
+    std::vector<double> omega;     // observed contraction per iteration of each job's change
+    // One iteration over a fixed active set captured as a CUDA graph (batch_run replays it
+    // between convergence checks); re-captured when the active set changes.
+    cudaGraphExec_t graph = nullptr;
+    std::vector<int> graph_key;
+    unsigned long long graph_launches = 0, graph_levals = 0;  // counters of one replay
+    bool graphs_ok = true;          // false after a failed capture (then iterations are queued plainly)
+    Batch() = default;
+    Batch(const Batch&) = delete;
+    Batch& operator=(const Batch&) = delete;
+    ~Batch() {
+        if (graph) cudaGraphExecDestroy(graph);
+    }
 };
 
 // Internal forcing value: no source term and no momentum-balance term (the homogeneous
@@ -57,7 +70,10 @@ struct Batch {
 constexpr int kForcingNone = 2;
 
 lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Arena* arena, cudaStream_t stream);
-template <typename T> void batch_iterate(Batch& B);
+// One iteration over B.active.  upload: copy the active list to the device first (it has not
+// changed since the previous iteration otherwise); read: copy the convergence states back to
+// B.hstate at the end (the host waits for that copy).
+template <typename T> void batch_iterate(Batch& B, bool upload = true, bool read = true);
 lbe_status batch_run(Batch& B, int max_steps);
 void fill_result(const Batch& B, int j, lbe_result* r, double secs);
 

@@ -25,6 +25,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -289,87 +290,173 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-// ---- reflection blocks -----------------------------------------------------------------
+// ---- reflection blocks and their transposition halves ------------------------------------
 // Block b has s1 = -1 when bit 0 of b is set and s2 = -1 when bit 1 is set (ducts; plates use
-// b = 0, 1 with s2 = +1); s3 = -1 always.  Rows of block b start at b * NBP, NBP = NB rounded
-// up to the 128-row tile (the padding rows and columns of A are zero).
-constexpr int nblocks_of(int mode) { return mode == 2 ? 2 : 4; }
-inline int nb_of(int nv) { return (nv / 2) * (nv / 2) * (nv / 2); }
-inline int nbp_of(int nv) { return (nb_of(nv) + kBM - 1) / kBM * kBM; }
+// b = 0, 1 with s2 = +1); s3 = -1 always.  The operator also commutes with the transposition
+// T: (v1, v2) -> (v2, v1) (the cubic grid is symmetric and the direction set is closed under it:
+// T maps azimuth phi to pi/2 - phi, a midpoint azimuth when their number is a multiple of 4,
+// i.e. M >= 8).  T maps the blocks with s1 = s2 (b = 0, and b = 3 for ducts) into themselves,
+// and there they split once more into functions even and odd under T, indexed by the unordered
+// pairs (a <= b) or (a < b) of (j1, j2) times j3:
+//     ts(a, b) = b (b + 1) / 2 + a,   ta(a, b) = b (b - 1) / 2 + a.
+// So the GEMM runs over sub-blocks: plates {S0, A0, F1}, ducts {S0, A0, F1, F2, S3, A3} (F: a
+// whole block, S / A: the even / odd half of one), (nv/2)^3 (H + 1) / (2 H) and
+// (nv/2)^3 (H - 1) / (2 H) square for the halves -- three quarters of the products of the
+// blocks.  Every sub-block is padded to the 128-row tile (padding rows and columns of A are
+// zero); its rows start at roff in the stacked A, and its cell operands at rows k * cpad of X,
+// npmax columns wide.
+struct SubLayout {
+    int count = 0;
+    int kind[6] = {};  // 0 whole block, 1 even half, 2 odd half
+    int blk[6] = {};
+    int n[6] = {};     // logical size
+    int np[6] = {};    // padded size
+    int roff[6] = {};  // first row in the stacked A
+    int soff[6] = {};  // first value in a cell's compact output (expand)
+    int rows = 0, npmax = 0;
+};
+__host__ __device__ constexpr int pad128(int n) { return (n + 127) / 128 * 128; }
+__host__ __device__ constexpr SubLayout sub_layout(int nv, int mode) {
+    SubLayout L;
+    const int H = nv / 2, nf = H * H * H, ns = H * (H + 1) / 2 * H, na = H * (H - 1) / 2 * H;
+    const int kinds_p[3] = {1, 2, 0}, blks_p[3] = {0, 0, 1};
+    const int kinds_d[6] = {1, 2, 0, 0, 1, 2}, blks_d[6] = {0, 0, 1, 2, 3, 3};
+    L.count = mode == 2 ? 3 : 6;
+    int r = 0, so = 0;
+    for (int k = 0; k < L.count; ++k) {
+        L.kind[k] = mode == 2 ? kinds_p[k] : kinds_d[k];
+        L.blk[k] = mode == 2 ? blks_p[k] : blks_d[k];
+        L.n[k] = L.kind[k] == 0 ? nf : (L.kind[k] == 1 ? ns : na);
+        L.np[k] = pad128(L.n[k]);
+        L.roff[k] = r;
+        L.soff[k] = so;
+        r += L.np[k];
+        so += L.n[k];
+        if (L.np[k] > L.npmax) L.npmax = L.np[k];
+    }
+    L.rows = r;
+    return L;
+}
+__host__ __device__ constexpr int ts_idx(int a, int b) { return b * (b + 1) / 2 + a; }
+__host__ __device__ constexpr int ta_idx(int a, int b) { return b * (b - 1) / 2 + a; }
+// sign of block b at a velocity point in the mirror halves m1, m2, m3
+__host__ __device__ inline bool blk_neg(int b, int mode, bool m1, bool m2, bool m3) {
+    int neg = m3 ? 1 : 0;
+    if (b & 1) neg += m1 ? 1 : 0;
+    if (mode == 1 && (b & 2)) neg += m2 ? 1 : 0;
+    return neg & 1;
+}
 
-// x_b[c][p] (hi / lo bf16, [block][cpad][NBP]) from h (float): the signed average of h over the
-// reflections that the parity leaves free -- plates x_b = (h(p) +- h(R1 p)) / 2, ducts
-// x_b = (h(p) +- h(R1 p) +- h(R2 p) +- h(R1 R2 p)) / 4.  Each thread takes two neighbouring
-// representatives (j3, j3 + 1; H is even): one float2 load per orbit point and one bf16x2
-// store per block and operand.  Padding columns p >= NB are written as zero.
+// x of every sub-block (hi / lo bf16, [sub-block][cpad][npmax]) from h (float).  Block
+// coefficients: the signed average of h over the reflections that the parity leaves free --
+// plates x_b = (h(p) +- h(R1 p)) / 2, ducts x_b = (h(p) +- h(R1 p) +- h(R2 p) +- h(R1 R2 p)) / 4;
+// halves: (x_b(a, b) +- x_b(b, a)) / 2.  Each thread takes one unordered pair a <= b of (j1, j2)
+// and two neighbouring j3 (H is even): float2 loads of both orders' orbit points, bf16x2
+// stores.  A second loop writes the padding columns of every sub-block as zero.
 template <int NV, int MODE>
-__global__ void __launch_bounds__(256) k_gather_blocks(const float* __restrict__ h, __nv_bfloat162* __restrict__ xh,
-                                                       __nv_bfloat162* __restrict__ xl, int cells, int cpad,
-                                                       int nbp) {
-    constexpr int H = NV / 2, NB = H * H * H, NBLK = MODE == 2 ? 2 : 4;
+__global__ void __launch_bounds__(256) k_gather_sub(const float* __restrict__ h, __nv_bfloat162* __restrict__ xh,
+                                                    __nv_bfloat162* __restrict__ xl, int cells, int cpad) {
+    constexpr int H = NV / 2, NBLK = MODE == 2 ? 2 : 4, NPAIR = H * (H + 1) / 2;
+    constexpr SubLayout L = sub_layout(NV, MODE);
     constexpr long N3 = (long)NV * NV * NV;
-    const int half = nbp / 2;
-    const long total = (long)cells * half;
+    const long total = (long)cells * NPAIR * (H / 2);
+    auto put = [&](int k, long c, int idx, float2 v) {
+        const long o = (((long)k * cpad + c) * L.npmax + idx) / 2;
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
+        const float2 hf = __bfloat1622float2(hi);
+        xh[o] = hi;
+        xl[o] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+    };
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-        const long c = k / half;
-        const int p = 2 * (int)(k % half);
-        float2 x[NBLK];
-        if (p < NB) {
-            const int j3 = p % H, j2 = (p / H) % H, j1 = p / (H * H);
-            const float* hc = h + c * N3;
-            const float2 a = *reinterpret_cast<const float2*>(hc + (j1 * NV + j2) * NV + j3);
-            const float2 b = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * NV + j2) * NV + j3);
+        const long c = k / (NPAIR * (H / 2));
+        const int r = (int)(k % (NPAIR * (H / 2)));
+        const int t = r / (H / 2), j3 = 2 * (r % (H / 2));
+        int bb = 0;
+        while ((bb + 1) * (bb + 2) / 2 <= t) ++bb;
+        const int aa = t - bb * (bb + 1) / 2;  // aa <= bb
+        const float* hc = h + c * N3;
+        float2 x[2][NBLK];  // [order: (aa, bb), (bb, aa)][block]
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            const int j1 = o ? bb : aa, j2 = o ? aa : bb;
+            const float2 p0 = *reinterpret_cast<const float2*>(hc + (j1 * NV + j2) * NV + j3);
+            const float2 p1 = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * NV + j2) * NV + j3);
             if constexpr (MODE == 2) {
-                x[0] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
-                x[1] = make_float2(0.5f * (a.x - b.x), 0.5f * (a.y - b.y));
+                x[o][0] = make_float2(0.5f * (p0.x + p1.x), 0.5f * (p0.y + p1.y));
+                x[o][1] = make_float2(0.5f * (p0.x - p1.x), 0.5f * (p0.y - p1.y));
             } else {
-                const float2 e = *reinterpret_cast<const float2*>(hc + (j1 * NV + (NV - 1 - j2)) * NV + j3);
-                const float2 f = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * NV + (NV - 1 - j2)) * NV + j3);
-                const float2 s0 = make_float2(a.x + b.x, a.y + b.y), d0 = make_float2(a.x - b.x, a.y - b.y);
-                const float2 s1 = make_float2(e.x + f.x, e.y + f.y), d1 = make_float2(e.x - f.x, e.y - f.y);
-                x[0] = make_float2(0.25f * (s0.x + s1.x), 0.25f * (s0.y + s1.y));
-                x[1] = make_float2(0.25f * (d0.x + d1.x), 0.25f * (d0.y + d1.y));
-                x[2] = make_float2(0.25f * (s0.x - s1.x), 0.25f * (s0.y - s1.y));
-                x[3] = make_float2(0.25f * (d0.x - d1.x), 0.25f * (d0.y - d1.y));
+                const float2 p2 = *reinterpret_cast<const float2*>(hc + (j1 * NV + (NV - 1 - j2)) * NV + j3);
+                const float2 p3 = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * NV + (NV - 1 - j2)) * NV + j3);
+                const float2 s0 = make_float2(p0.x + p1.x, p0.y + p1.y), d0 = make_float2(p0.x - p1.x, p0.y - p1.y);
+                const float2 s1 = make_float2(p2.x + p3.x, p2.y + p3.y), d1 = make_float2(p2.x - p3.x, p2.y - p3.y);
+                x[o][0] = make_float2(0.25f * (s0.x + s1.x), 0.25f * (s0.y + s1.y));
+                x[o][1] = make_float2(0.25f * (d0.x + d1.x), 0.25f * (d0.y + d1.y));
+                x[o][2] = make_float2(0.25f * (s0.x - s1.x), 0.25f * (s0.y - s1.y));
+                x[o][3] = make_float2(0.25f * (d0.x - d1.x), 0.25f * (d0.y - d1.y));
             }
-        } else {
-#pragma unroll
-            for (int b = 0; b < NBLK; ++b) x[b] = make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int b = 0; b < NBLK; ++b) {
-            const long o = (((long)b * cpad + c) * nbp + p) / 2;
-            const __nv_bfloat162 hi = __floats2bfloat162_rn(x[b].x, x[b].y);
-            const float2 hf = __bfloat1622float2(hi);
-            xh[o] = hi;
-            xl[o] = __floats2bfloat162_rn(x[b].x - hf.x, x[b].y - hf.y);
+        for (int q = 0; q < L.count; ++q) {
+            const int b = L.blk[q];
+            if (L.kind[q] == 0) {
+                put(q, c, (aa * H + bb) * H + j3, x[0][b]);
+                if (aa != bb) put(q, c, (bb * H + aa) * H + j3, x[1][b]);
+            } else if (L.kind[q] == 1) {
+                const float2 v = aa == bb ? x[0][b]
+                                          : make_float2(0.5f * (x[0][b].x + x[1][b].x), 0.5f * (x[0][b].y + x[1][b].y));
+                put(q, c, ts_idx(aa, bb) * H + j3, v);
+            } else if (aa != bb) {
+                put(q, c, ta_idx(aa, bb) * H + j3,
+                    make_float2(0.5f * (x[0][b].x - x[1][b].x), 0.5f * (x[0][b].y - x[1][b].y)));
+            }
         }
+    }
+    // padding columns
+    int npad = 0;
+#pragma unroll
+    for (int q = 0; q < L.count; ++q) npad += (L.np[q] - L.n[q]) / 2;
+    const long ptotal = (long)cells * npad;
+    const __nv_bfloat162 z = __floats2bfloat162_rn(0.f, 0.f);
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < ptotal; k += (long)gridDim.x * blockDim.x) {
+        const long c = k / npad;
+        int r = (int)(k % npad), q = 0;
+        while (r >= (L.np[q] - L.n[q]) / 2) {
+            r -= (L.np[q] - L.n[q]) / 2;
+            ++q;
+        }
+        const long o = (((long)q * cpad + c) * L.npmax + L.n[q] + 2 * r) / 2;
+        xh[o] = z;
+        xl[o] = z;
     }
 }
 
-// L+ h = delta s3 sum_b s_b Y_b[p] for every velocity point of a cell (Y: [cell][block][NBP]),
+// L+ h = delta s3 sum_b s_b y_b for every velocity point of a cell, y_b from the block's whole
+// output or from its two halves (y_b(j1, j2) = Ys(a, b) +- Ya(a, b), + for j1 <= j2);
 // optionally L h = L+ h - delta nu h, and optionally the SIS L-moments
 // G_j = 2 sum_v v_j v3 (L h + N delta h) dv^3 (j = 1, 2) in the same pass, without storing L h.
-// One block of 8 NV threads per cell stages the cell's block outputs in shared memory.
+// One block of 8 NV threads per cell stages the cell's sub-block outputs in shared memory.
 template <int NV, int MODE>
-__global__ void __launch_bounds__(8 * NV) k_expand_blocks(const float* __restrict__ Y, const float* __restrict__ h,
-                                                          const float* __restrict__ nu1, const float* __restrict__ vel,
-                                                          const double* __restrict__ delta, const double* __restrict__ nd,
-                                                          float* __restrict__ Lplus, float* __restrict__ Lout,
-                                                          double* __restrict__ G, int nbp, double dv3) {
+__global__ void __launch_bounds__(8 * NV) k_expand_sub(const float* __restrict__ Y, const float* __restrict__ h,
+                                                       const float* __restrict__ nu1, const float* __restrict__ vel,
+                                                       const double* __restrict__ delta, const double* __restrict__ nd,
+                                                       float* __restrict__ Lplus, float* __restrict__ Lout,
+                                                       double* __restrict__ G, double dv3) {
     extern __shared__ float sY[];
     __shared__ dfloat redx[32 * 2];
-    constexpr int H = NV / 2, NB = H * H * H, NBLK = MODE == 2 ? 2 : 4;
+    constexpr int H = NV / 2, NBLK = MODE == 2 ? 2 : 4;
+    constexpr SubLayout L = sub_layout(NV, MODE);
     constexpr long n3 = (long)NV * NV * NV;
     const long c = blockIdx.x;
-    const float* yc = Y + c * (long)NBLK * nbp;
-    for (int k = threadIdx.x; k < NBLK * NB; k += blockDim.x) sY[k] = yc[(k / NB) * nbp + (k % NB)];
+    const float* yc = Y + c * (long)L.rows;
+#pragma unroll
+    for (int q = 0; q < L.count; ++q)
+        for (int k = threadIdx.x; k < L.n[q]; k += blockDim.x) sY[L.soff[q] + k] = yc[L.roff[q] + k];
     __syncthreads();
     const float d = (float)delta[c];
     const float ndc = G ? (float)nd[c] : 0.f;
     const int i3 = threadIdx.x % NV, r0 = threadIdx.x / NV;
-    const int j3 = i3 < H ? i3 : NV - 1 - i3;
-    const float s3 = i3 < H ? d : -d;
+    const bool m3 = i3 >= H;
+    const int j3 = m3 ? NV - 1 - i3 : i3;
     const float v3 = vel[i3];
     float a0 = 0.f, c0 = 0.f, a1 = 0.f, c1 = 0.f;  // compensated sums of v1 t and v2 t
     auto kahan = [](float& sum, float& comp, float x) {
@@ -387,18 +474,26 @@ __global__ void __launch_bounds__(8 * NV) k_expand_blocks(const float* __restric
             const int i2 = r0 + 8 * k;
             const bool m2 = i2 >= H;
             const int j2 = m2 ? NV - 1 - i2 : i2;
-            const int p = (j1 * H + j2) * H + j3;
-            float y;
-            if constexpr (MODE == 2) {
-                const float y1 = sY[NB + p];
-                y = sY[p] + (m1 ? -y1 : y1);
-            } else {
-                const float y1 = sY[NB + p], y2 = sY[2 * NB + p], y3 = sY[3 * NB + p];
-                y = (sY[p] + (m1 ? -y1 : y1)) + ((m2 ? -y2 : y2) + ((m1 != m2) ? -y3 : y3));
+            const int aa = j1 <= j2 ? j1 : j2, bb = j1 <= j2 ? j2 : j1;
+            float yb[NBLK];
+#pragma unroll
+            for (int q = 0; q < L.count; ++q) {
+                const int b = L.blk[q];
+                if (L.kind[q] == 0) {
+                    yb[b] = sY[L.soff[q] + (j1 * H + j2) * H + j3];
+                } else if (L.kind[q] == 1) {
+                    yb[b] = sY[L.soff[q] + ts_idx(aa, bb) * H + j3];
+                } else if (aa != bb) {
+                    const float ya = sY[L.soff[q] + ta_idx(aa, bb) * H + j3];
+                    yb[b] += j1 < j2 ? ya : -ya;
+                }
             }
+            float y = 0.f;
+#pragma unroll
+            for (int b = 0; b < NBLK; ++b) y += blk_neg(b, MODE, m1, m2, false) ? -yb[b] : yb[b];
             const int v = (i1 * NV + i2) * NV + i3;
             const long g = c * n3 + v;
-            const float lp = s3 * y;
+            const float lp = (m3 ? -d : d) * y;
             Lplus[g] = lp;
             if (Lout || G) {
                 const float hv = h[g];
@@ -422,59 +517,89 @@ __global__ void __launch_bounds__(8 * NV) k_expand_blocks(const float* __restric
 }
 
 template <int NV, int MODE>
-void launch_blocks(int cells, int cpad, int nbp, const float* h, __nv_bfloat162* xh, __nv_bfloat162* xl,
-                   cudaStream_t s) {
-    k_gather_blocks<NV, MODE><<<8 * sm_count(), 256, 0, s>>>(h, xh, xl, cells, cpad, nbp);
+void launch_gather(int cells, int cpad, const float* h, __nv_bfloat162* xh, __nv_bfloat162* xl, cudaStream_t s) {
+    k_gather_sub<NV, MODE><<<8 * sm_count(), 256, 0, s>>>(h, xh, xl, cells, cpad);
 }
 
 template <int NV, int MODE>
-void launch_expand(int cells, int nbp, const float* Y, const float* h, const float* nu1, const float* vel,
-                   const double* delta, const double* nd, float* Lplus, float* Lout, double* G, double dv3,
-                   cudaStream_t s) {
+void launch_expand(int cells, const float* Y, const float* h, const float* nu1, const float* vel, const double* delta,
+                   const double* nd, float* Lplus, float* Lout, double* G, double dv3, cudaStream_t s) {
     static std::once_flag once;
     constexpr int H = NV / 2;
-    const int smem = nblocks_of(MODE) * H * H * H * 4;
+    const int smem = (MODE == 2 ? 2 : 4) * H * H * H * 4;
     std::call_once(once, [smem] {
-        cudaFuncSetAttribute(k_expand_blocks<NV, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_expand_sub<NV, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     });
-    k_expand_blocks<NV, MODE><<<cells, 8 * NV, smem, s>>>(Y, h, nu1, vel, delta, nd, Lplus, Lout, G, nbp, dv3);
+    k_expand_sub<NV, MODE><<<cells, 8 * NV, smem, s>>>(Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3);
 }
 
-// Basis functions of block b, column p, for the global basis indices g0 .. g0 + nbas - 1
-// (g = b NB + p): value s3 s_b at the eight points of the orbit of p, zero elsewhere.
-__global__ void k_basis_blocks(double* __restrict__ h, int g0, int nbas, int nv, int mode) {
-    const int H = nv / 2, NB = H * H * H;
+// Column col of sub-block q: its canonical (a, b, j3) -- (j1, j2, j3) of a whole block, or the
+// unordered pair of a half.
+__host__ __device__ inline void sub_column(const SubLayout& L, int q, int col, int H, int* pa, int* pb, int* p3) {
+    *p3 = col % H;
+    const int t = col / H;
+    if (L.kind[q] == 0) {
+        *pa = t / H;
+        *pb = t % H;
+        return;
+    }
+    int b = L.kind[q] == 1 ? 0 : 1;
+    if (L.kind[q] == 1)
+        while ((b + 1) * (b + 2) / 2 <= t) ++b;
+    else
+        while ((b + 1) * b / 2 <= t) ++b;
+    *pb = b;
+    *pa = t - (L.kind[q] == 1 ? b * (b + 1) / 2 : b * (b - 1) / 2);
+}
+
+// Basis functions for the global columns g0 .. g0 + nbas - 1 (sub-block by sub-block): the
+// block-b function of the orbit of (a, b, j3) (value s3 s_b on its eight points), for a half
+// plus (even) or minus (odd) that of (b, a, j3).
+__global__ void k_basis_sub(double* __restrict__ h, int g0, int nbas, int nv, int mode) {
+    const SubLayout L = sub_layout(nv, mode);
+    const int H = nv / 2;
     const long n3 = (long)nv * nv * nv;
     const long total = (long)nbas * n3;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-        const int gi = g0 + (int)(k / n3);
-        const int b = gi / NB, p = gi % NB;
+        int gi = g0 + (int)(k / n3), q = 0;
+        while (gi >= L.n[q]) gi -= L.n[q++];
+        int pa, pb, p3;
+        sub_column(L, q, gi, H, &pa, &pb, &p3);
         const int v = (int)(k % n3);
         const int i1 = v / (nv * nv), i2 = (v / nv) % nv, i3 = v % nv;
         const bool m1 = i1 >= H, m2 = i2 >= H, m3 = i3 >= H;
-        const int q = ((m1 ? nv - 1 - i1 : i1) * H + (m2 ? nv - 1 - i2 : i2)) * H + (m3 ? nv - 1 - i3 : i3);
-        int neg = m3 ? 1 : 0;
-        if (b & 1) neg += m1 ? 1 : 0;
-        if (mode == 1 && (b & 2)) neg += m2 ? 1 : 0;
-        h[k] = (q == p) ? ((neg & 1) ? -1.0 : 1.0) : 0.0;
+        const int j1 = m1 ? nv - 1 - i1 : i1, j2 = m2 ? nv - 1 - i2 : i2, j3 = m3 ? nv - 1 - i3 : i3;
+        double val = 0.0;
+        if (j3 == p3) {
+            const double sg = blk_neg(L.blk[q], mode, m1, m2, m3) ? -1.0 : 1.0;
+            if (j1 == pa && j2 == pb) val += sg;
+            if (L.kind[q] != 0 && pa != pb && j1 == pb && j2 == pa) val += L.kind[q] == 1 ? sg : -sg;
+        }
+        h[k] = val;
     }
 }
 
-// Columns g0 .. g0 + nbas - 1 of the stacked blocks (row-major [NBLK NBP][NBP], hi / lo bf16)
-// from L+ e at the representative points (all j_k < H).
-__global__ void k_store_blocks(const double* __restrict__ Lp, __nv_bfloat16* __restrict__ Ah,
-                               __nv_bfloat16* __restrict__ Al, int g0, int nbas, int nv, int nbp) {
-    const int H = nv / 2, NB = H * H * H;
+// Columns g0 .. g0 + nbas - 1 of the stacked sub-blocks (row-major [rows][npmax], hi / lo
+// bf16) from L+ e at the representative point of each output row.
+__global__ void k_store_sub(const double* __restrict__ Lp, __nv_bfloat16* __restrict__ Ah,
+                            __nv_bfloat16* __restrict__ Al, int g0, int nbas, int nv, int mode) {
+    const SubLayout L = sub_layout(nv, mode);
+    const int H = nv / 2;
     const long n3 = (long)nv * nv * nv;
-    const long total = (long)nbas * NB;
+    int nmax = 0;
+    for (int q = 0; q < L.count; ++q) nmax = L.n[q] > nmax ? L.n[q] : nmax;
+    const long total = (long)nbas * nmax;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-        const int q = (int)(k % NB);          // output row within the block
-        const long bb = k / NB;               // basis function of this chunk
-        const int gi = g0 + (int)bb, b = gi / NB, p = gi % NB;
-        const int j3 = q % H, j2 = (q / H) % H, j1 = q / (H * H);
-        const double a = Lp[bb * n3 + (j1 * nv + j2) * nv + j3];
+        const long bb = k / nmax;  // basis function of this chunk
+        const int row = (int)(k % nmax);
+        int col = g0 + (int)bb, q = 0;
+        while (col >= L.n[q]) col -= L.n[q++];
+        if (row >= L.n[q]) continue;
+        int qa, qb, q3;
+        sub_column(L, q, row, H, &qa, &qb, &q3);
+        const double a = Lp[bb * n3 + (qa * nv + qb) * nv + q3];
         const __nv_bfloat16 hi = __float2bfloat16_rn((float)a);
-        const long idx = ((long)b * nbp + q) * nbp + p;
+        const long idx = (long)(L.roff[q] + row) * L.npmax + col;
         Ah[idx] = hi;
         Al[idx] = __float2bfloat16_rn((float)(a - (double)__bfloat162float(hi)));
     }
@@ -556,10 +681,23 @@ struct GemmPlan {
     int slots = 0;
 };
 
-GemmPlan make_plan(int cells, int bn, int nblk, int nbp, int P) {
+GemmPlan make_plan(int cells, int bn, const SubLayout& L, int P) {
     GemmPlan pl;
     const int nct = (cells + bn - 1) / bn, cpad = nct * bn;
-    const int nrt = nblk * nbp / kBM, T = nct * nrt, KT = nbp / kBK;
+    const int nrt = L.rows / kBM, T = nct * nrt;
+    // tiles, deepest first (the sub-blocks differ in K), so that the last wave holds the
+    // shortest ones
+    struct Tile {
+        int col0, row0, xrow0, kt;
+    };
+    std::vector<Tile> tiles;
+    for (int t = 0; t < T; ++t) {
+        const int col0 = (t % nct) * bn, row0 = (t / nct) * kBM;
+        int q = 0;
+        while (q + 1 < L.count && row0 >= L.roff[q + 1]) ++q;
+        tiles.push_back({col0, row0, q * cpad + col0, L.np[q] / kBK});  // the sub-block's operand rows, depth
+    }
+    std::stable_sort(tiles.begin(), tiles.end(), [](const Tile& a, const Tile& b) { return a.kt > b.kt; });
     int W, S;
     if (T >= P) {
         W = T / P * P;
@@ -568,19 +706,20 @@ GemmPlan make_plan(int cells, int bn, int nblk, int nbp, int P) {
         W = 0;
         S = std::max(1, std::min(4, P / T));
     }
-    while (S > 1 && KT / S < 8) --S;
+    int ktmin = 1 << 30;
+    for (int q = 0; q < L.count; ++q) ktmin = std::min(ktmin, L.np[q] / kBK);
+    while (S > 1 && ktmin / S < 4) --S;
     if (S == 1) W = T;
     for (int t = 0; t < T; ++t) {
-        const int col0 = (t % nct) * bn, row0 = (t / nct) * kBM;
-        const int xrow0 = (row0 / nbp) * cpad + col0;  // the block's operand rows
+        const Tile& u = tiles[t];
         if (t < W) {
-            pl.work.push_back({col0, row0, xrow0, 0, KT, -1});
+            pl.work.push_back({u.col0, u.row0, u.xrow0, 0, u.kt, -1});
             continue;
         }
         const int slot0 = pl.slots;
         for (int p = 0; p < S; ++p)
-            pl.work.push_back({col0, row0, xrow0, KT * p / S, KT * (p + 1) / S, pl.slots++});
-        pl.fix.push_back({col0, row0, slot0, S});
+            pl.work.push_back({u.col0, u.row0, u.xrow0, u.kt * p / S, u.kt * (p + 1) / S, pl.slots++});
+        pl.fix.push_back({u.col0, u.row0, slot0, S});
     }
     return pl;
 }
@@ -599,9 +738,10 @@ void launch_gemm(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap
 
 }  // namespace
 
-// Reflection blocks of one (tables, parity mode): A_hi / A_lo stacked [nblk * nbp][nbp].
+// Sub-blocks of one (tables, parity mode): A_hi / A_lo stacked [L.rows][L.npmax].
 struct DenseOp {
-    int mode = 0, nv = 0, nblk = 0, nb = 0, nbp = 0;
+    int mode = 0, nv = 0;
+    SubLayout L;
     __nv_bfloat16* Ah = nullptr;
     __nv_bfloat16* Al = nullptr;
     CUtensorMap mAh, mAl;
@@ -630,11 +770,10 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
     const int nv = t->nv;
     d.mode = mode;
     d.nv = nv;
-    d.nblk = nblocks_of(mode);
-    d.nb = nb_of(nv);
-    d.nbp = nbp_of(nv);
-    const int nbas = d.nblk * d.nb;  // basis functions: every block's columns
-    const size_t abytes = (size_t)d.nblk * d.nbp * d.nbp * 2;
+    d.L = sub_layout(nv, mode);
+    int nbas = 0;  // basis functions: every sub-block's columns
+    for (int q = 0; q < d.L.count; ++q) nbas += d.L.n[q];
+    const size_t abytes = (size_t)d.L.rows * d.L.npmax * 2;
     lbe_status st = dev_alloc(c, (void**)&d.Ah, abytes);
     if (st == LBE_OK) st = dev_alloc(c, (void**)&d.Al, abytes);
     if (st != LBE_OK) return st;
@@ -658,10 +797,10 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
         cudaMemcpyAsync(dl, ones.data(), nb * 8, cudaMemcpyHostToDevice, s);
         for (int g0 = 0; g0 < nbas && st == LBE_OK; g0 += nb) {
             const int b = std::min(nb, nbas - g0);
-            k_basis_blocks<<<8 * sm_count(), 256, 0, s>>>((double*)hb, g0, b, nv, mode);
+            k_basis_sub<<<8 * sm_count(), 256, 0, s>>>((double*)hb, g0, b, nv, mode);
             st = fsm_df_apply(*t, b, (const double*)dl, (const double*)hb, (double*)lp, (double*)lo, sc, chunk, s,
                               mode);
-            k_store_blocks<<<8 * sm_count(), 256, 0, s>>>((const double*)lp, d.Ah, d.Al, g0, b, nv, d.nbp);
+            k_store_sub<<<8 * sm_count(), 256, 0, s>>>((const double*)lp, d.Ah, d.Al, g0, b, nv, mode);
             g_launches += 2;
         }
         if (st == LBE_OK) st = cuda_status(c, cudaStreamSynchronize(s), "dense operator build");
@@ -672,8 +811,7 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
     dev_free(c, sc, scr);
     dev_free(c, dl, (size_t)nb * 8);
     if (st != LBE_OK) return st;
-    if (!make_map(&d.mAh, d.Ah, (long)d.nblk * d.nbp, d.nbp, kBM) ||
-        !make_map(&d.mAl, d.Al, (long)d.nblk * d.nbp, d.nbp, kBM)) {
+    if (!make_map(&d.mAh, d.Ah, d.L.rows, d.L.npmax, kBM) || !make_map(&d.mAl, d.Al, d.L.rows, d.L.npmax, kBM)) {
         c->last_error = "cuTensorMapEncodeTiled unavailable or failed";
         return LBE_INTERNAL;
     }
@@ -702,14 +840,14 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         *T.err_host = 0;
         cudaMemsetAsync(T.err_dev, 0, sizeof(int), s);
     }
-    const int nv = t->nv, nblk = d.nblk, nbp = d.nbp;
-    const int mrows = nblk * nbp;  // rows of the stacked blocks (and of Y per cell)
+    const int nv = t->nv, nsub = d.L.count, npmax = d.L.npmax;
+    const int mrows = d.L.rows;  // rows of the stacked sub-blocks (and of Y per cell)
     const int bn = pick_bn(cells);
     const long cpad = (cells + bn - 1) / bn * bn;  // whole TMA boxes, zero padding rows
     const long long pkey = ((long long)cells << 32) | ((long long)bn << 20) | mrows;
     auto pit = T.plans.find(pkey);
     if (pit == T.plans.end()) {
-        const GemmPlan pl = make_plan(cells, bn, nblk, nbp, sm_count());
+        const GemmPlan pl = make_plan(cells, bn, d.L, sm_count());
         DevPlan dp;
         dp.nwork = (int)pl.work.size();
         dp.nfix = (int)pl.fix.size();
@@ -722,7 +860,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         pit = T.plans.emplace(pkey, dp).first;
     }
     const DevPlan& plan = pit->second;
-    const size_t xb = (size_t)nblk * cpad * nbp * 2, yb = (size_t)cells * mrows * 4;
+    const size_t xb = (size_t)nsub * cpad * npmax * 2, yb = (size_t)cells * mrows * 4;
     const size_t pb = (size_t)plan.slots * bn * kBM * 4;
     Arena& ws = T.ws[s];
     if ((st = arena_reserve(c, ws, 2 * xb + yb + pb + 4 * 256)) != LBE_OK) return st;
@@ -731,13 +869,13 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     auto* Y = (float*)arena_take(ws, yb);
     auto* Pp = pb ? (float*)arena_take(ws, pb) : nullptr;
     if (cpad > cells)
-        for (int b = 0; b < nblk; ++b) {
-            const size_t o = ((size_t)b * cpad + cells) * nbp, n = (size_t)(cpad - cells) * nbp * 2;
+        for (int q = 0; q < nsub; ++q) {
+            const size_t o = ((size_t)q * cpad + cells) * npmax, n = (size_t)(cpad - cells) * npmax * 2;
             cudaMemsetAsync(xh + o, 0, n, s);
             cudaMemsetAsync(xl + o, 0, n, s);
         }
     CUtensorMap mXh, mXl;
-    if (!make_map(&mXh, xh, nblk * cpad, nbp, bn) || !make_map(&mXl, xl, nblk * cpad, nbp, bn)) {
+    if (!make_map(&mXh, xh, nsub * cpad, npmax, bn) || !make_map(&mXl, xl, nsub * cpad, npmax, bn)) {
         c->last_error = "cuTensorMapEncodeTiled failed for the cell operand";
         return LBE_INTERNAL;
     }
@@ -747,10 +885,10 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         const bool p2 = mode == 2;
         const int cp = (int)cpad;
         switch (nv) {
-            case 8: (p2 ? launch_blocks<8, 2> : launch_blocks<8, 1>)(cells, cp, nbp, h, xh2, xl2, s); break;
-            case 16: (p2 ? launch_blocks<16, 2> : launch_blocks<16, 1>)(cells, cp, nbp, h, xh2, xl2, s); break;
-            case 24: (p2 ? launch_blocks<24, 2> : launch_blocks<24, 1>)(cells, cp, nbp, h, xh2, xl2, s); break;
-            default: (p2 ? launch_blocks<32, 2> : launch_blocks<32, 1>)(cells, cp, nbp, h, xh2, xl2, s); break;
+            case 8: (p2 ? launch_gather<8, 2> : launch_gather<8, 1>)(cells, cp, h, xh2, xl2, s); break;
+            case 16: (p2 ? launch_gather<16, 2> : launch_gather<16, 1>)(cells, cp, h, xh2, xl2, s); break;
+            case 24: (p2 ? launch_gather<24, 2> : launch_gather<24, 1>)(cells, cp, h, xh2, xl2, s); break;
+            default: (p2 ? launch_gather<32, 2> : launch_gather<32, 1>)(cells, cp, h, xh2, xl2, s); break;
         }
     }
     // optional event timing of the GEMM alone (public synchronous calls only)
@@ -775,10 +913,10 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         const double dv3 = t->dv * t->dv * t->dv;
         const bool p2 = mode == 2;
         switch (nv) {
-            case 8: (p2 ? launch_expand<8, 2> : launch_expand<8, 1>)(cells, nbp, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
-            case 16: (p2 ? launch_expand<16, 2> : launch_expand<16, 1>)(cells, nbp, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
-            case 24: (p2 ? launch_expand<24, 2> : launch_expand<24, 1>)(cells, nbp, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
-            default: (p2 ? launch_expand<32, 2> : launch_expand<32, 1>)(cells, nbp, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
+            case 8: (p2 ? launch_expand<8, 2> : launch_expand<8, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
+            case 16: (p2 ? launch_expand<16, 2> : launch_expand<16, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
+            case 24: (p2 ? launch_expand<24, 2> : launch_expand<24, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
+            default: (p2 ? launch_expand<32, 2> : launch_expand<32, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
         }
     }
     g_launches += 3;

@@ -39,7 +39,16 @@ struct HostTables {
 
 void build_host_tables(HostTables& t, int nv, double vmax, int M, double R);
 
-struct TcOperands;  // tensor-core operands (fsm_tc.cu)
+struct TcOperands;  // tensor-core operands (fsm_dense.cu)
+
+// Launch choices made by measurement at first use (the autotuner): the schedule of the 1D
+// float transport sweep per (grid, problems, nodes) class.  Every choice computes the same
+// bits, so tuning changes speed only.
+struct Tuning {
+    std::mutex mu;
+    std::map<long long, int> sweep;  // key -> schedule (0 staged, 1 register ring)
+    std::vector<std::string> log;    // one line per decision (lbe_tuning_report)
+};
 
 struct DevTables {
     int nv = 0, M = 0;
@@ -55,6 +64,7 @@ struct DevTables {
     // double-float (hi, lo float pairs; complex tables as re.hi, re.lo, im.hi, im.lo)
     float* feq_x = nullptr; float* nu1_x = nullptr; float* mult_x = nullptr; float* ab_x = nullptr;
     TcOperands* tc = nullptr;
+    Tuning* tuning = nullptr;
     size_t bytes = 0;
 };
 
@@ -118,6 +128,7 @@ struct Ctx {
     cudaStream_t stream = nullptr;      // stream of the synchronous calls
     cudaStream_t own_stream = nullptr;  // created by lbe_create
     Arena solve_arena, apply_arena;
+    Arena refine_arena[3];  // refined solves: FP64 batch, low-precision batch, work buffers
     // serving
     std::mutex mu;
     std::condition_variable cv;

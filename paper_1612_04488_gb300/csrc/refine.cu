@@ -163,7 +163,9 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         pi[j].max_iter = 150;
         max_outer = std::max(max_outer, pbs[j].max_iter);
     }
-    Arena ao, ai;
+    // the context's grow-only arenas: a warm context allocates nothing per solve
+    Arena& ao = c->refine_arena[0];
+    Arena& ai = c->refine_arena[1];
     Batch O, I;
     lbe_status st = batch_init(O, c, po.data(), n, &ao, s);
     if (st == LBE_OK) st = batch_init(I, c, pi.data(), n, &ai, s);
@@ -177,7 +179,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
     int inc_chunk = 1;
     const size_t inc_scr = st == LBE_OK ? fsm_cc_scratch_bytes(*O.t, (int)O.cells, 4, &inc_chunk) : 0;
     // h_old, r, base_h, base_lp, base_lh, inc_h, inc_lp, inc_lh, FP32 operator scratch
-    Arena aw;
+    Arena& aw = c->refine_arena[2];
     double *h_old = nullptr, *base_h = nullptr, *base_lp = nullptr, *base_lh = nullptr;
     float *r = nullptr, *inc_h = nullptr, *inc_lp = nullptr, *inc_lh = nullptr;
     void* inc_scratch = nullptr;
@@ -197,12 +199,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         inc_scratch = arena_take(aw, inc_scr);
         if (!inc_scratch) st = LBE_INTERNAL;
     }
-    if (st != LBE_OK) {
-        arena_release(c, aw);
-        arena_release(c, ao);
-        arena_release(c, ai);
-        return st;
-    }
+    if (st != LBE_OK) return st;
     std::vector<int> outer_it(n, 0), inner_it(n, 0), refs(n, 0);
     std::vector<double> t_done(n, 0.0);
     std::vector<double> prev_rel(n, 1e300);
@@ -393,9 +390,6 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         if (st == LBE_OK && h_out)
             st = cuda_status(c, cudaMemcpy(h_out, O.h.p, vol64, cudaMemcpyDeviceToHost), "h");
     }
-    arena_release(c, aw);
-    arena_release(c, ao);
-    arena_release(c, ai);
     return st != LBE_OK ? st : worst;
 }
 

@@ -14,7 +14,10 @@
 //     wall; 2D Eq. diffusion_LBE on the interior with U3 = U3^(k+1/2) on the wall ring,
 //     solved exactly by DST-I diagonalisation of the five-point Laplacian (FP64).
 // A8  Eq. guided correction, flow rates M, Q (Sec. 2.4), relative-change test.
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <mutex>
 
 #include "common.cuh"
 #include "lbe_internal.h"
@@ -41,22 +44,59 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
                  : "memory");
 }
 
+// Explicitly rounded arithmetic of the march (no contraction into fused multiply-adds), so
+// that every schedule of the same march gives the same bits.
+template <typename T> struct Rn;
+template <> struct Rn<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float rcp(float x) { return __fdiv_rn(1.0f, x); }
+};
+template <> struct Rn<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double rcp(double x) { return __ddiv_rn(1.0, x); }
+};
+// one node of the second-order upwind march: h_i = (rhs_i + S - u (b h_(i-1) + c h_(i-2))) inv,
+// inv = 1 / (nu + u a)
 template <typename T>
+__device__ __forceinline__ T march_node(T r, T S, T u, T b, T c, T hm1, T hm2, T inv) {
+    using R = Rn<T>;
+    return R::mul(R::sub(R::add(r, S), R::mul(u, R::add(R::mul(b, hm1), R::mul(c, hm2)))), inv);
+}
+template <typename T>
+__device__ __forceinline__ T march_inv(T nu, T u, T a) {
+    using R = Rn<T>;
+    return R::rcp(R::add(nu, R::mul(u, a)));
+}
+
+// 1D sweep (plates): one thread per mirror pair (v1 > 0, v1 < 0) of velocities, marching the
+// nodes wall -> symmetry plane for v1 > 0, then back for v1 < 0 starting from the specular
+// reflection.  Two schedules of the same arithmetic:
+//   SCHED 0  (float) every right-hand side of the thread's two columns is copied to shared
+//            memory up front (cp.async, 4 bytes each), so all loads are in flight at once;
+//            ~1 KB of shared memory per node and block limits residency to a few blocks per SM;
+//   SCHED 1  a register ring: the right-hand sides of the next RING nodes are in flight while a
+//            node is solved, no shared memory beyond the coefficients, so the SM holds as many
+//            threads as the registers allow.
+// The march coefficients [fa|fb|fc|ba|bb|bc] (n each) are converted to T once per block into
+// shared memory when `staged` (a double-to-float conversion per node and thread would run at
+// the FP64 rate).
+constexpr int kRing = 16;
+template <typename T, int SCHED>
 __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* __restrict__ h,
                                                  const T* __restrict__ nu1, const T* __restrict__ vel,
                                                  const T* __restrict__ feq,
                                                  const SweepJobDev* __restrict__ jobs,
                                                  const int* __restrict__ active,
-                                                 const double* __restrict__ coef, int nv, int staged,
-                                                 int async_rhs) {
+                                                 const double* __restrict__ coef, int nv, int staged) {
     extern __shared__ __align__(16) unsigned char sweep_smem[];
     const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
     const int half = nv / 2, n2 = nv * nv;
     const long n3 = (long)n2 * nv;
     const int n = jb.ncell;
-    // march coefficients [fa|fb|fc|ba|bb|bc] (n each): with `staged`, converted to T once per
-    // block into shared memory (a double-to-float conversion per node and thread would
-    // otherwise run at the FP64 rate)
     const double* cg = coef + jb.coef_off;
     T* sc = reinterpret_cast<T*>(sweep_smem);
     if (staged) {
@@ -76,103 +116,80 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
     const T w2 = vel[rem / nv], w3 = vel[rem % nv];
     const T Sp = source<T>(jb.forcing, v1, w2, w3, feq[vpos]);
     const T Sn = source<T>(jb.forcing, vel[nv - 1 - i1p], w2, w3, feq[vneg]);
-    T hm1 = T(0), hm2 = T(0);
-    o[vpos] = T(0);
-    if constexpr (sizeof(T) == 4) {
-        if (async_rhs) {
-            // every right-hand side of this thread's two columns goes in flight at once
-            // (cp.async, 4 bytes each, after the staged coefficients); the thread waits for its
-            // own copies only, so no barrier is needed.  Layout [column][node][thread].
-            T* cp = sc + 6 * n;
-            T* cn = cp + (long)n * blockDim.x;
-            const int tx = threadIdx.x;
-            for (int i = 1; i < n; ++i) cp_async4(cp + i * blockDim.x + tx, r + (long)i * n3 + vpos);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            for (int i = 0; i + 1 < n; ++i) cp_async4(cn + i * blockDim.x + tx, r + (long)i * n3 + vneg);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-#pragma unroll 4
-            for (int i = 1; i < n; ++i) {
-                const T inv = T(1) / (nup + v1 * C(0, i));
-                const T acc = (cp[i * blockDim.x + tx] + Sp) - v1 * (C(1, i) * hm1 + C(2, i) * hm2);
-                const T hi = acc * inv;
-                o[(long)i * n3 + vpos] = hi;
-                hm2 = hm1;
-                hm1 = hi;
-            }
-            const T u = -vel[nv - 1 - i1p];
-            const T nun = d * nu1[vneg];
-            T g1 = hm1, g2 = hm2;
-            o[(long)(n - 1) * n3 + vneg] = hm1;
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-#pragma unroll 4
-            for (int i = n - 2; i >= 0; --i) {
-                const T inv = T(1) / (nun + u * C(3, i));
-                const T acc = (cn[i * blockDim.x + tx] + Sn) - u * (C(4, i) * g1 + C(5, i) * g2);
-                const T hi = acc * inv;
-                o[(long)i * n3 + vneg] = hi;
-                g2 = g1;
-                g1 = hi;
-            }
-            return;
-        }
-    }
-    // the right-hand sides of the next kPre nodes are in flight while a node is solved, and
-    // their reciprocal diagonals are formed off the march's dependent chain (which is then
-    // three multiply-adds per node)
-    T rb[kPre], ib[kPre];
-#pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-        const int i = 1 + k;
-        rb[k] = i < n ? r[(long)i * n3 + vpos] : T(0);
-        ib[k] = i < n ? T(1) / (nup + v1 * C(0, i)) : T(0);
-    }
-    for (int i0 = 1; i0 < n; i0 += kPre) {
-#pragma unroll
-        for (int k = 0; k < kPre; ++k) {
-            const int i = i0 + k;
-            if (i < n) {
-                const T ri = rb[k], inv = ib[k];
-                const int j = i + kPre;
-                if (j < n) {
-                    rb[k] = r[(long)j * n3 + vpos];
-                    ib[k] = T(1) / (nup + v1 * C(0, j));
-                }
-                const T acc = (ri + Sp) - v1 * (C(1, i) * hm1 + C(2, i) * hm2);
-                const T hi = acc * inv;
-                o[(long)i * n3 + vpos] = hi;
-                hm2 = hm1;
-                hm1 = hi;
-            }
-        }
-    }
-    // specular symmetry plane: h(x_Ns, v1<0) = h(x_Ns, -v1); ghost node carries h(x_{Ns-1}, -v1)
     const T u = -vel[nv - 1 - i1p];
     const T nun = d * nu1[vneg];
-    T g1 = hm1, g2 = hm2;
-    o[(long)(n - 1) * n3 + vneg] = hm1;
+    T hm1 = T(0), hm2 = T(0);
+    o[vpos] = T(0);
+    if constexpr (SCHED == 0) {
+        // every right-hand side of this thread's two columns goes in flight at once (after the
+        // staged coefficients); the thread waits for its own copies only, so no barrier is
+        // needed.  Layout [column][node][thread].
+        T* cp = sc + 6 * n;
+        T* cn = cp + (long)n * blockDim.x;
+        const int tx = threadIdx.x;
+        for (int i = 1; i < n; ++i) cp_async4(cp + i * blockDim.x + tx, r + (long)i * n3 + vpos);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        for (int i = 0; i + 1 < n; ++i) cp_async4(cn + i * blockDim.x + tx, r + (long)i * n3 + vneg);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+#pragma unroll 4
+        for (int i = 1; i < n; ++i) {
+            const T hi = march_node(cp[i * blockDim.x + tx], Sp, v1, C(1, i), C(2, i), hm1, hm2,
+                                    march_inv(nup, v1, C(0, i)));
+            o[(long)i * n3 + vpos] = hi;
+            hm2 = hm1;
+            hm1 = hi;
+        }
+        // specular symmetry plane: h(x_Ns, v1 < 0) = h(x_Ns, -v1); the ghost node carries
+        // h(x_(Ns-1), -v1)
+        T g1 = hm1, g2 = hm2;
+        o[(long)(n - 1) * n3 + vneg] = hm1;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll 4
+        for (int i = n - 2; i >= 0; --i) {
+            const T hi = march_node(cn[i * blockDim.x + tx], Sn, u, C(4, i), C(5, i), g1, g2,
+                                    march_inv(nun, u, C(3, i)));
+            o[(long)i * n3 + vneg] = hi;
+            g2 = g1;
+            g1 = hi;
+        }
+    } else {
+        T rb[kRing];
 #pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-        const int i = n - 2 - k;
-        rb[k] = i >= 0 ? r[(long)i * n3 + vneg] : T(0);
-        ib[k] = i >= 0 ? T(1) / (nun + u * C(3, i)) : T(0);
-    }
-    for (int i0 = n - 2; i0 >= 0; i0 -= kPre) {
+        for (int k = 0; k < kRing; ++k) rb[k] = 1 + k < n ? r[(long)(1 + k) * n3 + vpos] : T(0);
+        for (int i0 = 1; i0 < n; i0 += kRing) {
 #pragma unroll
-        for (int k = 0; k < kPre; ++k) {
-            const int i = i0 - k;
-            if (i >= 0) {
-                const T ri = rb[k], inv = ib[k];
-                const int j = i - kPre;
-                if (j >= 0) {
-                    rb[k] = r[(long)j * n3 + vneg];
-                    ib[k] = T(1) / (nun + u * C(3, j));
+            for (int k = 0; k < kRing; ++k) {
+                const int i = i0 + k;
+                if (i < n) {
+                    const T ri = rb[k];
+                    if (i + kRing < n) rb[k] = r[(long)(i + kRing) * n3 + vpos];
+                    const T hi = march_node(ri, Sp, v1, C(1, i), C(2, i), hm1, hm2, march_inv(nup, v1, C(0, i)));
+                    o[(long)i * n3 + vpos] = hi;
+                    hm2 = hm1;
+                    hm1 = hi;
                 }
-                const T acc = (ri + Sn) - u * (C(4, i) * g1 + C(5, i) * g2);
-                const T hi = acc * inv;
-                o[(long)i * n3 + vneg] = hi;
-                g2 = g1;
-                g1 = hi;
+            }
+        }
+        T g1 = hm1, g2 = hm2;
+        o[(long)(n - 1) * n3 + vneg] = hm1;
+#pragma unroll
+        for (int k = 0; k < kRing; ++k) {
+            const int i = n - 2 - k;
+            rb[k] = i >= 0 ? r[(long)i * n3 + vneg] : T(0);
+        }
+        for (int i0 = n - 2; i0 >= 0; i0 -= kRing) {
+#pragma unroll
+            for (int k = 0; k < kRing; ++k) {
+                const int i = i0 - k;
+                if (i >= 0) {
+                    const T ri = rb[k];
+                    if (i - kRing >= 0) rb[k] = r[(long)(i - kRing) * n3 + vneg];
+                    const T hi = march_node(ri, Sn, u, C(4, i), C(5, i), g1, g2, march_inv(nun, u, C(3, i)));
+                    o[(long)i * n3 + vneg] = hi;
+                    g2 = g1;
+                    g1 = hi;
+                }
             }
         }
     }
@@ -369,6 +386,11 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
     const int jid = active ? active[blockIdx.x] : blockIdx.x;
     const SisJobDev jb = jobs[jid];
     JobState* st = state + jid;
+    if (st->done) {  // finished before this iteration: state, U3 and h stay as they are
+        if (threadIdx.x == 0) st->skip = 1;
+        return;
+    }
+    if (threadIdx.x == 0) st->skip = 0;
     const long c0 = jb.cell_off;
     const int n = jb.ncell;
     const double* m = mom + c0 * 5;
@@ -511,8 +533,11 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
                                                  const double* __restrict__ dU, const T* __restrict__ extra,
                                                  const T* __restrict__ feq,
                                                  const T* __restrict__ vel, const SweepJobDev* __restrict__ jobs,
-                                                 const int* __restrict__ active, int nv) {
-    const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
+                                                 const int* __restrict__ active, int nv,
+                                                 const JobState* __restrict__ state) {
+    const int jid = active ? active[blockIdx.y] : blockIdx.y;
+    if (state && state[jid].skip) return;  // finished before this iteration
+    const SweepJobDev jb = jobs[jid];
     const int n3 = nv * nv * nv, hv = nv / 2;
     const bool plates = jb.ny == 0;  // 1D: orbits {1, R2, R3, R2R3}; 2D: {1, R3}
     const int norb = plates ? n3 / 4 : n3 / 2;
@@ -564,37 +589,83 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
 }  // namespace
 
 template <typename T>
-void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T* rhs, T* h,
-                  const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s) {
-    if (njobs <= 0) return;
-    // float sweeps stage the coefficients when the largest job's fit in 48 KB; 1D float sweeps
-    // also stage every right-hand side of their columns when that fits in 200 KB
-    const size_t sbytes = (size_t)max_coef * sizeof(T);
-    const int staged = (sizeof(T) == 4 && max_coef > 0 && sbytes <= 48 * 1024) ? 1 : 0;
-    size_t smem = staged ? sbytes : 0;
-    int async_rhs = 0;
-    if (dim == 1 && staged) {
-        const size_t full = sbytes + 2 * (size_t)(max_coef / 6) * 128 * sizeof(T);
-        if (full <= 200 * 1024) {
-            async_rhs = 1;
-            smem = full;
-            static bool attr = false;  // opt-in shared memory beyond 48 KB (float instance)
-            if (!attr) {
-                cudaFuncSetAttribute(k_sweep1d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                attr = true;
-            }
-        }
-    }
-    g_launches += 1;
-    const int nv = t.nv;
+static void sweep1d_sched(int sched, const DevTables& t, dim3 g, size_t smem_coef, size_t smem_full, int staged,
+                          const T* rhs, T* h, const SweepJobDev* jobs, const int* active, const double* coef,
+                          cudaStream_t s) {
     const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
+    if (sched == 0)
+        k_sweep1d<T, 0><<<g, 128, smem_full, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged);
+    else
+        k_sweep1d<T, 1><<<g, 128, smem_coef, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged);
+}
+
+template <typename T>
+void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T* rhs, T* h,
+                  const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s) {
+    if (njobs <= 0) return;
+    // float sweeps stage the coefficients when the largest job's fit in 48 KB
+    const size_t sbytes = (size_t)max_coef * sizeof(T);
+    const int staged = (sizeof(T) == 4 && max_coef > 0 && sbytes <= 48 * 1024) ? 1 : 0;
+    const size_t smem = staged ? sbytes : 0;
+    g_launches += 1;
+    const int nv = t.nv;
     if (dim == 1) {
         const int nt = nv / 2 * nv * nv;
         dim3 g((nt + 127) / 128, njobs);
-        k_sweep1d<T><<<g, 128, smem, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv, staged, async_rhs);
+        // 1D float sweeps can also stage every right-hand side of their columns (schedule 0)
+        // when that fits in 200 KB; which schedule is faster is measured at first use
+        const size_t full = sbytes + 2 * (size_t)(max_coef / 6) * 128 * sizeof(T);
+        int sched = 1;
+        if (sizeof(T) == 4 && staged && full <= 200 * 1024 && t.tuning) {
+            static std::once_flag attr;  // opt-in shared memory beyond 48 KB (float instance)
+            std::call_once(attr, [] {
+                cudaFuncSetAttribute(k_sweep1d<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            });
+            int jb = 1;
+            while (jb < njobs) jb *= 2;  // problems and nodes classes: the next power of two
+            int nb = 1;
+            while (nb < max_coef / 6) nb *= 2;
+            const long long key = ((long long)nv << 40) | ((long long)jb << 20) | nb;
+            std::lock_guard<std::mutex> lk(t.tuning->mu);
+            auto it = t.tuning->sweep.find(key);
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            const bool capturing = cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+            if (it != t.tuning->sweep.end()) {
+                sched = it->second;
+            } else if (capturing) {
+                sched = 0;
+            } else {
+                // both schedules twice, alternating; each writes the same h (same arithmetic)
+                cudaEvent_t ev[5];
+                for (auto& e : ev) cudaEventCreate(&e);
+                cudaEventRecord(ev[0], s);
+                for (int k = 0; k < 4; ++k) {
+                    sweep1d_sched<T>(k & 1, t, g, smem, full, staged, rhs, h, jobs, active, coef, s);
+                    cudaEventRecord(ev[k + 1], s);
+                }
+                cudaEventSynchronize(ev[4]);
+                float ms[4] = {0, 0, 0, 0};
+                for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
+                for (auto& e : ev) cudaEventDestroy(e);
+                const float t0 = std::min(ms[0], ms[2]), t1 = std::min(ms[1], ms[3]);
+                sched = t1 <= t0 ? 1 : 0;
+                t.tuning->sweep[key] = sched;
+                char line[200];
+                snprintf(line, sizeof line,
+                         "sweep1d<float> nv=%d problems<=%d nodes<=%d: %s (staged %.1f us, register ring %.1f us)", nv,
+                         jb, nb, sched ? "register ring" : "staged", 1000.0f * t0, 1000.0f * t1);
+                t.tuning->log.push_back(line);
+                g_launches += 3;
+                return;
+            }
+        }
+        sweep1d_sched<T>(sched, t, g, smem, full, staged, rhs, h, jobs, active, coef, s);
     } else {
+        const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
+        const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
+        const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
         const int nt = nv * nv * nv;
         dim3 g((nt + 127) / 128, njobs);
         k_sweep2d<T><<<g, 128, smem, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv, staged);
@@ -625,13 +696,13 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
 
 template <typename T>
 void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
-                    const SweepJobDev* jobs, const int* active, cudaStream_t s) {
+                    const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state) {
     if (njobs <= 0) return;
     g_launches += 1;
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
-    dim3 g(304, njobs);
-    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv);
+    dim3 g(2 * sm_count(), njobs);
+    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state);
 }
 
 template void launch_sweep<double>(const DevTables&, int, int, int, const double*, double*,
@@ -641,8 +712,8 @@ template void launch_sweep<float>(const DevTables&, int, int, int, const float*,
 template void launch_moments<double>(const DevTables&, long, int, const double*, double*, cudaStream_t);
 template void launch_moments<float>(const DevTables&, long, int, const float*, double*, cudaStream_t);
 template void launch_correct<double>(const DevTables&, int, const double*, double*, const double*,
-                                     const double*, const SweepJobDev*, const int*, cudaStream_t);
+                                     const double*, const SweepJobDev*, const int*, cudaStream_t, const JobState*);
 template void launch_correct<float>(const DevTables&, int, const float*, float*, const double*, const float*,
-                                    const SweepJobDev*, const int*, cudaStream_t);
+                                    const SweepJobDev*, const int*, cudaStream_t, const JobState*);
 
 }  // namespace lbe

@@ -47,9 +47,12 @@ struct SisJobDev {
     int crit;        // 0: |dM| < eps |M| and |dQ| < eps |Q| (Sec. 2.4); 1: both changes < eps max(|M|, |Q|)
 };
 
+// Convergence state of one problem.  skip = 1 while an iteration passes over a problem that
+// was already done when the iteration began (the update and the correction leave it untouched,
+// so iterations can be queued ahead of the host's convergence check).
 struct JobState {
     double M, Q, Mprev, Qprev, rel;
-    int iters, done, nan, pad;
+    int iters, done, nan, skip;
 };
 
 template <typename T>
@@ -62,7 +65,7 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
                        double* U3, JobState* state, cudaStream_t s);
 template <typename T>
 void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
-                    const SweepJobDev* jobs, const int* active, cudaStream_t s);
+                    const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state = nullptr);
 
 // fsm_cc.cu
 void init_twiddles_cc();

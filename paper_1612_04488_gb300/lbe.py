@@ -92,6 +92,7 @@ def lib():
         L.lbe_solve_from.argtypes = [vp, C.POINTER(Problem), dp, C.POINTER(Result), C.POINTER(Result), dp, dp]
         L.lbe_cancel.argtypes = [vp, C.c_uint64]
         L.lbe_debug_expire_waits.argtypes = [ip]
+        L.lbe_tuning_report.argtypes = [vp, C.c_char_p, C.c_size_t]
         _lib = L
     return _lib
 
@@ -222,6 +223,12 @@ class Context:
         t = C.c_uint64()
         self.check(lib().lbe_submit(self.h, C.byref(pb), C.byref(t)))
         return t.value
+
+    def tuning_report(self):
+        """The autotuner's decisions (lbe_tuning_report), one line each."""
+        buf = C.create_string_buffer(1 << 16)
+        lib().lbe_tuning_report(self.h, buf, len(buf))
+        return [l for l in buf.value.decode().split("\n") if l]
 
     def cancel(self, ticket):
         self.check(lib().lbe_cancel(self.h, ticket))

@@ -84,3 +84,43 @@ def test_refined_requests_reach_fp64(ctx, prec):
 def test_submit_rejects_bad_problem(ctx):
     with pytest.raises(lbe.LbeError):
         ctx.submit(lbe.problem(dim=1, ns=10, nv=12))
+
+
+def test_serving_stream_at_workload_sizes(ctx):
+    """Requests of the serving stream at their own sizes (velocity grids 24^3 and 32^3, M = 32,
+    plates of 50-200 sections and ducts up to 80 x 40 cells, delta log-uniform on [0.01, 100]),
+    BF16-refined, submitted while others are on the GPU: every result reaches the FP64 solution
+    of its problem to 1e-7, and a request served in the mix agrees with the same request served
+    alone to 1e-7 (the tensor-core GEMM's K split depends on the bucket's cells, so the last bits
+    may differ)."""
+    from paper_1612_04488_gb300 import workloads
+    reqs = workloads.serving_requests(n=256, seed=20261203)
+    # two of each kind: plates and ducts at 24^3 and 32^3
+    pick, seen = [], {}
+    for r in reqs:
+        k = (r["dim"], r["nv"])
+        if seen.get(k, 0) < 2 and (r["dim"] == 1 or r["nx"] * r["ny"] <= 1600):
+            seen[k] = seen.get(k, 0) + 1
+            pick.append(r)
+    assert len(pick) == 8
+
+    def pb(r, prec, eps):
+        geo = {k: r[k] for k in ("dim", "ns", "grid_kind", "nx", "ny", "width") if k in r}
+        return lbe.problem(**geo, delta=r["delta"], nv=r["nv"], vmax=r["vmax"], M=r["M"], R=4.5, forcing=r["forcing"],
+                           scheme=lbe.SIS, precision=prec, eps=eps, max_iter=400)
+
+    ctx.set_max_active(64)
+    tickets = []
+    for i, r in enumerate(pick):  # arrivals spread while earlier requests run
+        tickets.append(ctx.submit(pb(r, lbe.BF16_REFINED, 1e-9)))
+        time.sleep(0.02)
+    got = wait_all(ctx, tickets, timeout=600.0)
+    alone = wait_all(ctx, [ctx.submit(pb(pick[0], lbe.BF16_REFINED, 1e-9))], timeout=600.0)[0]
+    for r, g in zip(pick, got):
+        ref, _, _ = ctx.solve(pb(r, lbe.FP64, 1e-9))
+        info = (r, g.status, g.refinements, g.mass_flow, ref.mass_flow, g.heat_flow, ref.heat_flow)
+        assert g.status == lbe.OK and ref.status == lbe.OK, info
+        assert abs(g.mass_flow - ref.mass_flow) <= 1e-7 * abs(ref.mass_flow), info
+        assert abs(g.heat_flow - ref.heat_flow) <= 1e-7 * abs(ref.heat_flow), info
+    assert abs(alone.mass_flow - got[0].mass_flow) <= 1e-7 * abs(got[0].mass_flow)
+    assert abs(alone.heat_flow - got[0].heat_flow) <= 1e-7 * abs(got[0].heat_flow)
