@@ -7,14 +7,24 @@ N = nu_bar/delta, stopped when the flow rates change by less than eps per iterat
 One step = one batched solve of all eight problems to convergence (every hot-path step,
 A1-A8, runs on every iteration).  Inputs are synthetic (the problem parameters; h starts
 at 0).  Working set: 808 cells x 32^3 x 4 B per array (106 MB) over several arrays, plus
-the 268 MB operator matrix, well above L2 (129 MB).
+the 134 MB of tensor-core operator blocks, well above L2 (129 MB).
 
-  value   solves/s with the batch resident on the device (lbe_batch_run), CUDA events
-  e2e     solves/s through the one-shot public call lbe_solve_batch (host problems in,
-          host results out; setup, uploads and per-iteration flag reads inside)
-  roofline  the tensor-core GEMM of the collision operator (A1-A3), timed alone with CUDA
-          events on its own stream at the same size; traffic from an ncu capture
-  cpu_baseline  the FP64 oracle on a bounded sample of the same workload (extrapolated)
+  value     solves/s of one batched solve per step (BF16-refined: lbe_solve_batch; FP32 / FP64:
+            the resident batch, lbe_batch_run), CUDA events on the calling stream
+  e2e       solves/s through the one-shot public call lbe_solve_batch (host problems in,
+            host results out; setup, uploads and convergence-flag reads inside)
+  roofline  the tensor-core GEMM of the collision operator (A1-A3), timed alone by the library
+            with CUDA events on its own stream at the same size: the method's algorithmic
+            flops (FFT-equivalent) over its duration, executed flops beside them
+  roofline_sweep  the transport sweep (A5) of an FP32 solve of the workload, every launch
+            timed by the library: algorithmic bytes over duration against HBM
+  fp64_gpu  the plain FP64 GPU path at the same eps (the comparison the mixed precision beats)
+  duct64x32 the 64 x 32 duct (2048 cells, 32^3) solved in the same precision
+  serving   the 256-request serving stream: saturated solves/s and p50 / p99 latency with
+            Poisson arrivals (the line's latency_ms)
+  autotuner the launch choices measured at first use
+  cpu_baseline  the FP64 oracle on a bounded sample of the same workload (extrapolated), on
+            one core and on all host cores
 
 --impl reference times the oracle instead (the reference arm of this repository).
 Multi-GPU: replicas only (independent solves per rank), launched by torchrun.
@@ -288,26 +298,19 @@ def run_op_only(args):
     return 0
 
 
-def run_serve(args):
-    """Serving stream: mixed plates/ducts, nv in {24, 32}, delta log-uniform on [0.01, 100],
-    submitted to the continuous-batching service.  Phase 1 submits everything at t = 0
-    (saturated throughput); phase 2 replays the stream with Poisson arrivals at 0.8x that
-    rate and reports per-request latency (submit to result)."""
-    import torch
-
-    from paper_1612_04488_gb300 import lbe
+def serve_stream(ctx, lbe, prec, eps, requests):
+    """The serving stream (workload "serve256"): mixed plates / ducts, nv in {24, 32}, delta
+    log-uniform on [0.01, 100], submitted to the continuous-batching service.  Phase 1 submits
+    everything at t = 0 (saturated throughput); phase 2 replays the stream with Poisson
+    arrivals at 0.8x that rate and measures per-request latency (submit to result)."""
     from paper_1612_04488_gb300 import workloads as W
-
-    torch.cuda.set_device(0)
-    ctx = lbe.Context(0)
-    prec = PRECISIONS[args.precision](lbe)
 
     def to_pb(r):
         geo = {k: r[k] for k in ("dim", "ns", "grid_kind", "nx", "ny", "width") if k in r}
         return lbe.problem(**geo, delta=r["delta"], nv=r["nv"], vmax=r["vmax"], M=r["M"], forcing=r["forcing"],
-                           scheme=lbe.SIS, precision=prec, eps=args.eps, max_iter=400)
+                           scheme=lbe.SIS, precision=prec, eps=eps, max_iter=400)
 
-    reqs = W.serving_requests(n=args.requests, seed=20261203)
+    reqs = W.serving_requests(n=requests, seed=20261203)
     pbs = [to_pb(r) for r in reqs]
 
     def run_stream(arrivals):
@@ -333,7 +336,7 @@ def run_serve(args):
         return wall, lat, res
 
     # warm-up: build the tables of both grids and the buckets
-    warm = [pbs[k] for k in range(len(pbs)) if k < 4]
+    warm = pbs[:4]
     tk = [ctx.submit(p) for p in warm]
     while not all(ctx.poll(t)[0] for t in tk):
         time.sleep(0.001)
@@ -343,16 +346,31 @@ def run_serve(args):
     rate = 0.8 * rate_sat
     arr = np.cumsum(rng.exponential(1.0 / rate, size=len(pbs)))
     wall, lat, res = run_stream(list(arr))
-    bad = sum(1 for r in res if r.status != lbe.OK)
-    line = {"metric": "serving: solves/s and per-request latency (Poisson arrivals)",
-            "value": len(pbs) / wall, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
-            "saturated_solves_per_s": rate_sat, "arrival_rate": rate,
-            "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)), "p99": 1000 * float(np.percentile(lat, 99))},
+    bad = sum(1 for r in res + res_sat if r.status != lbe.OK)
+    return {"workload": "serve%d" % requests, "requests": len(pbs), "failed": bad,
+            "solves_per_s": len(pbs) / wall, "saturated_solves_per_s": rate_sat, "arrival_rate": rate,
+            "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)), "p99": 1000 * float(np.percentile(lat, 99)),
+                           "what": "Poisson arrivals at 0.8x the saturated rate, submit to result"},
             "latency_saturated_ms": {"p50": 1000 * float(np.percentile(lat_sat, 50)),
                                      "p99": 1000 * float(np.percentile(lat_sat, 99))},
-            "requests": len(pbs), "failed": bad, "dtype": DTYPES[args.precision], "data": "synthetic",
-            "config": {"workload": "serving stream: plates 50-200 sections / ducts 20x20-80x40, nv 24/32, "
-                                   "delta log-uniform [0.01, 100], M = 32", "eps": args.eps}}
+            "mix": "plates 50-200 sections / ducts 20x20-80x40, nv 24/32, delta log-uniform [0.01, 100], M = 32",
+            "eps": eps}
+
+
+def run_serve(args):
+    """The serving stream alone (--serve), one JSON line."""
+    import torch
+
+    from paper_1612_04488_gb300 import lbe
+
+    torch.cuda.set_device(0)
+    ctx = lbe.Context(0)
+    prec = PRECISIONS[args.precision](lbe)
+    sv = serve_stream(ctx, lbe, prec, args.eps, args.requests)
+    line = {"metric": "serving: solves/s and per-request latency (Poisson arrivals)",
+            "value": sv["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": DTYPES[args.precision], "data": "synthetic", "config": {"workload": sv["workload"]},
+            "serving": sv}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -605,14 +623,31 @@ def run_ours(args):
                    "eps": args.eps,
                    "l2": "inputs larger than L2 (h, L+h, h half-step: %d MB in FP32)" % (3 * cells * nv ** 3 * 4 // 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "latency_ms": {"p50": float(np.percentile(solve_ms, 50)), "p99": float(np.percentile(solve_ms, 99)),
-                       "what": "per solve, batch start to that solve's convergence"},
+        "batch_latency_ms": {"p50": float(np.percentile(solve_ms, 50)), "p99": float(np.percentile(solve_ms, 99)),
+                             "what": "per solve, batch start to that solve's convergence"},
         "iterations": iters, "refinements": refinements, "status": status,
         "max_rel_err_vs_fp64": err,
         "l_evals_per_s": l_evals["op"], "l_evals_per_s_fp64": l_evals["fp64_fft_sym"], "l_evals_detail": l_evals,
         "roofline": roofline, "roofline_sweep": sweep, "fp64_gpu": fp64, "autotuner": ctx.tuning_report(),
         "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
     }
+    # ---- the other workloads on the same line: the 64 x 32 duct (2048 cells, one solve) and
+    # the serving stream (per-request p50 / p99 latency) ------------------------------------
+    if args.workload == "plates32x8" and not args.no_extra:
+        dpbs = workload_problems(lbe, "duct64x32", prec, args.eps)
+        ctx.solve_batch(dpbs)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dres = [ctx.solve_batch(dpbs)[0] for _ in range(2)]
+        b.record(stream)
+        b.synchronize()
+        line["duct64x32"] = {"solves_per_s": 2.0 / (a.elapsed_time(b) / 1000.0), "cells": 2048,
+                             "iterations": dres[-1].iters, "refinements": dres[-1].refinements,
+                             "status": dres[-1].status}
+        sctx = lbe.Context(local)
+        line["serving"] = serve_stream(sctx, lbe, prec, args.eps, args.requests)
+        line["latency_ms"] = dict(line["serving"]["latency_ms"], workload=line["serving"]["workload"])
+        sctx.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # one extrapolation for both arms: per-iteration oracle time x the SIS iterations per
         # solve (--ref-iters, the workload's FP64 count), single core and all cores
@@ -655,7 +690,8 @@ def main():
     ap.add_argument("--op-only", action="store_true", help="time the collision operator alone")
     ap.add_argument("--sym", action="store_true", help="--op-only: parity-reduced fast-spectral operator")
     ap.add_argument("--serve", action="store_true", help="serving stream with Poisson arrivals")
-    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--no-extra", action="store_true", help="skip the duct and serving entries of the line")
     args = ap.parse_args()
     if args.serve:
         return run_serve(args)

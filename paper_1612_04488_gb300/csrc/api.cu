@@ -436,6 +436,7 @@ lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Arena* ar
                             {&B.mom, (size_t)B.cells * 5 * 8}, {&B.G, (size_t)B.cells * 2 * 8},
                             {&B.dU, (size_t)B.cells * 8}, {&B.U3, (size_t)B.cells * 8},
                             {&B.delta, (size_t)B.cells * 8}, {&B.nd, (size_t)B.cells * 8},
+                            {&B.hmom, (size_t)B.cells * 2 * 8},
                             {&B.coef, coef.size() * 8}, {&B.work, (size_t)std::max<long>(work, 1) * 8},
                             {&B.sjobs, n * sizeof(SweepJobDev)}, {&B.ijobs, n * sizeof(SisJobDev)},
                             {&B.states, n * sizeof(JobState)}, {&B.act, n * sizeof(int)}};
@@ -449,6 +450,7 @@ lbe_status batch_init(Batch& B, Ctx* c, const lbe_problem* pbs, int n, Arena* ar
     }
     cudaStream_t s = stream;
     cudaMemsetAsync(B.h.p, 0, vol, s);  // h^0 = 0
+    cudaMemsetAsync(B.hmom.p, 0, B.hmom.n, s);
     cudaMemcpyAsync(B.delta.p, dcell.data(), dcell.size() * 8, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(B.nd.p, ndcell.data(), ndcell.size() * 8, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(B.coef.p, coef.data(), coef.size() * 8, cudaMemcpyHostToDevice, s);
@@ -517,7 +519,7 @@ void batch_iterate(Batch& B, bool upload, bool read) {
             // L+ h and the L-moments in one pass; L h itself is not stored
             const lbe_status ts = tc_apply_sym(B.c, B.t, mode, nc, B.delta.as<double>() + c0, (const float*)(h + c0 * n3),
                                                (float*)(lp + c0 * n3), nullptr, s, false, B.nd.as<double>() + c0,
-                                               B.G.as<double>() + c0 * 2);
+                                               B.G.as<double>() + c0 * 2, B.hmom.as<double>() + c0 * 2);
             if (ts != LBE_OK && B.op_status == LBE_OK) B.op_status = ts;
             continue;
         } else {
@@ -558,7 +560,8 @@ void batch_iterate(Batch& B, bool upload, bool read) {
                       B.coef.as<double>(), B.work.as<double>(), B.dU.as<double>(), B.U3.as<double>(),
                       B.states.as<JobState>(), s);
     launch_correct<T>(t, na, hh, h, B.dU.as<double>(), B.extra.p ? B.extra.as<T>() : nullptr,
-                      B.sjobs.as<SweepJobDev>(), dact, s, B.states.as<JobState>());
+                      B.sjobs.as<SweepJobDev>(), dact, s, B.states.as<JobState>(),
+                      (sizeof(T) == 4 && B.use_tc) ? B.hmom.as<double>() : nullptr, B.nd.as<double>());
     if (read) {
         cudaMemcpyAsync(B.hstate.data(), B.states.p, B.njobs * sizeof(JobState), cudaMemcpyDeviceToHost, s);
         g_d2h += B.njobs * sizeof(JobState);
@@ -1027,8 +1030,8 @@ lbe_status lbe_sweep(lbe_ctx* ctx, const lbe_problem* pb, const void* rhs_dev, v
     cudaMemcpyAsync(dc, coef.data(), coef.size() * 8, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dj, &j, sizeof j, cudaMemcpyHostToDevice, s);
     if (pb->precision == LBE_FP64) {
-        launch_sweep<double>(*t, g.dim, 1, 0, (const double*)rhs_dev, (double*)h_dev, (SweepJobDev*)dj, nullptr,
-                             (double*)dc, s);
+        launch_sweep<double>(*t, g.dim, 1, (int)coef.size(), (const double*)rhs_dev, (double*)h_dev,
+                             (SweepJobDev*)dj, nullptr, (double*)dc, s);
         if (mom_dev) launch_moments<double>(*t, 0, g.cells, (const double*)h_dev, mom_dev, s);
     } else {
         launch_sweep<float>(*t, g.dim, 1, (int)coef.size(), (const float*)rhs_dev, (float*)h_dev, (SweepJobDev*)dj,
@@ -1123,6 +1126,7 @@ lbe_status lbe_batch_run(lbe_batch* b, lbe_result* outs) {
     const long n3 = (long)B.pbs[0].nv * B.pbs[0].nv * B.pbs[0].nv;
     auto t0 = std::chrono::steady_clock::now();
     cudaMemsetAsync(B.h.p, 0, B.cells * n3 * (B.prec == LBE_FP64 ? 8 : 4), B.s);
+    cudaMemsetAsync(B.hmom.p, 0, B.hmom.n, B.s);
     B.hstate.assign(B.njobs, JobState{});
     cudaMemcpyAsync(B.states.p, B.hstate.data(), B.njobs * sizeof(JobState), cudaMemcpyHostToDevice, B.s);
     g_h2d += B.njobs * sizeof(JobState);

@@ -31,6 +31,9 @@ struct Batch {
     std::vector<long> cell_off;
     DevBuf h, hh, lp, lh, scratch, mom, G, dU, U3, delta, nd, coef, work, sjobs, ijobs, states, act;
     DevBuf extra;  // optional additive source in the correction step (same type as h)
+    // [cells][2]: the h part of the SIS L-moments of the current h, summed by the correction
+    // step (tensor-core batches); zero wherever h is reset to zero
+    DevBuf hmom;
     // Increment mode (FP64 batches of the refinement driver): the collision operator of h is
     // base_lp / base_lh (FP64 operator of base_h, computed once) plus the FP32 operator of
     // the increment h - base_h.  Unset: the operator runs in the batch's own arithmetic.

@@ -34,9 +34,12 @@ __device__ __forceinline__ dfloat df_twosum(float a, float b) {
     const float bb = __fsub_rn(s, a);
     return dfloat(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
 }
-// The results of + and * are left unnormalised (|lo| may reach a few ulps of hi): the next
-// TwoSum / TwoProduct is exact whatever the split, so the pair keeps the same information
-// and the renormalising Fast2Sum is saved; widening to double adds the parts exactly.
+// The results of + and * are left unnormalised (|lo| may reach a few ulps of hi), which saves
+// the renormalising Fast2Sum.  TwoSum / TwoProduct of the hi parts stay exact whatever the
+// split, but the lo terms are rounded together, so the per-operation error bound grows with
+// |lo| / ulp(hi) beyond the ~2^-44 of normalised pairs; the agreement of the transforms with
+// FP64 (about 1e-13 of the scale) is measured by the parity tests, not implied by this bound.
+// Widening to double adds the parts exactly.
 __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
     const dfloat s = df_twosum(a.hi, b.hi);
     return dfloat(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));

@@ -434,13 +434,16 @@ __global__ void __launch_bounds__(256) k_gather_sub(const float* __restrict__ h,
 // output or from its two halves (y_b(j1, j2) = Ys(a, b) +- Ya(a, b), + for j1 <= j2);
 // optionally L h = L+ h - delta nu h, and optionally the SIS L-moments
 // G_j = 2 sum_v v_j v3 (L h + N delta h) dv^3 (j = 1, 2) in the same pass, without storing L h.
+// With hm (the h part of G summed when h was written, see launch_correct) and no L h wanted,
+// G_j = 2 sum_v v_j v3 L+ h dv^3 + hm_j and h is not read at all.
 // One block of 8 NV threads per cell stages the cell's sub-block outputs in shared memory.
 template <int NV, int MODE>
 __global__ void __launch_bounds__(8 * NV) k_expand_sub(const float* __restrict__ Y, const float* __restrict__ h,
                                                        const float* __restrict__ nu1, const float* __restrict__ vel,
                                                        const double* __restrict__ delta, const double* __restrict__ nd,
                                                        float* __restrict__ Lplus, float* __restrict__ Lout,
-                                                       double* __restrict__ G, double dv3) {
+                                                       double* __restrict__ G, double dv3,
+                                                       const double* __restrict__ hm) {
     extern __shared__ float sY[];
     __shared__ dfloat redx[32 * 2];
     constexpr int H = NV / 2, NBLK = MODE == 2 ? 2 : 4;
@@ -495,7 +498,13 @@ __global__ void __launch_bounds__(8 * NV) k_expand_sub(const float* __restrict__
             const long g = c * n3 + v;
             const float lp = (m3 ? -d : d) * y;
             Lplus[g] = lp;
-            if (Lout || G) {
+            if (hm && !Lout) {
+                if (G) {
+                    const float t = lp * v3;
+                    kahan(a0, c0, v1 * t);
+                    kahan(a1, c1, vel[i2] * t);
+                }
+            } else if (Lout || G) {
                 const float hv = h[g];
                 const float lo = lp - d * nu1[v] * hv;
                 if (Lout) Lout[g] = lo;
@@ -511,8 +520,9 @@ __global__ void __launch_bounds__(8 * NV) k_expand_sub(const float* __restrict__
     dfloat sm[2] = {df_fast2sum(a0, -c0), df_fast2sum(a1, -c1)};  // reduced in double-float
     block_reduce_df<2>(sm, redx);
     if (threadIdx.x == 0) {
-        G[2 * c + 0] = 2.0 * (double)sm[0] * dv3;
-        G[2 * c + 1] = 2.0 * (double)sm[1] * dv3;
+        const bool add = hm && !Lout;
+        G[2 * c + 0] = 2.0 * (double)sm[0] * dv3 + (add ? hm[2 * c + 0] : 0.0);
+        G[2 * c + 1] = 2.0 * (double)sm[1] * dv3 + (add ? hm[2 * c + 1] : 0.0);
     }
 }
 
@@ -523,14 +533,15 @@ void launch_gather(int cells, int cpad, const float* h, __nv_bfloat162* xh, __nv
 
 template <int NV, int MODE>
 void launch_expand(int cells, const float* Y, const float* h, const float* nu1, const float* vel, const double* delta,
-                   const double* nd, float* Lplus, float* Lout, double* G, double dv3, cudaStream_t s) {
+                   const double* nd, float* Lplus, float* Lout, double* G, double dv3, const double* hm,
+                   cudaStream_t s) {
     static std::once_flag once;
     constexpr int H = NV / 2;
     const int smem = (MODE == 2 ? 2 : 4) * H * H * H * 4;
     std::call_once(once, [smem] {
         cudaFuncSetAttribute(k_expand_sub<NV, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     });
-    k_expand_sub<NV, MODE><<<cells, 8 * NV, smem, s>>>(Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3);
+    k_expand_sub<NV, MODE><<<cells, 8 * NV, smem, s>>>(Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, hm);
 }
 
 // Column col of sub-block q: its canonical (a, b, j3) -- (j1, j2, j3) of a whole block, or the
@@ -822,7 +833,7 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
 // sync = false leaves the stream running: the GEMM's failure word is copied to pinned host
 // memory behind it and tc_check reads it after the caller's own synchronisation.
 lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h, float* Lplus,
-                        float* Lout, cudaStream_t s, bool sync, const double* nd, double* G) {
+                        float* Lout, cudaStream_t s, bool sync, const double* nd, double* G, const double* hm) {
     if (mode != 1 && mode != 2) return LBE_BAD_ARG;
     if (cells <= 0) return LBE_OK;
     if (!t->tc) t->tc = new TcOperands();
@@ -913,10 +924,10 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         const double dv3 = t->dv * t->dv * t->dv;
         const bool p2 = mode == 2;
         switch (nv) {
-            case 8: (p2 ? launch_expand<8, 2> : launch_expand<8, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
-            case 16: (p2 ? launch_expand<16, 2> : launch_expand<16, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
-            case 24: (p2 ? launch_expand<24, 2> : launch_expand<24, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
-            default: (p2 ? launch_expand<32, 2> : launch_expand<32, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, s); break;
+            case 8: (p2 ? launch_expand<8, 2> : launch_expand<8, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, hm, s); break;
+            case 16: (p2 ? launch_expand<16, 2> : launch_expand<16, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, hm, s); break;
+            case 24: (p2 ? launch_expand<24, 2> : launch_expand<24, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, hm, s); break;
+            default: (p2 ? launch_expand<32, 2> : launch_expand<32, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, hm, s); break;
         }
     }
     g_launches += 3;

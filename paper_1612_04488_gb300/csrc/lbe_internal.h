@@ -46,7 +46,7 @@ struct TcOperands;  // tensor-core operands (fsm_dense.cu)
 // bits, so tuning changes speed only.
 struct Tuning {
     std::mutex mu;
-    std::map<long long, int> sweep;  // key -> schedule (0 staged, 1 register ring)
+    std::map<long long, int> sweep;  // key -> schedule (0 staged, 1 register ring, 2 shared ring)
     std::vector<std::string> log;    // one line per decision (lbe_tuning_report)
 };
 

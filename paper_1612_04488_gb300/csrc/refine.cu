@@ -341,6 +341,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             g_launches += 1;
             for (int j : corr) {
                 cudaMemsetAsync(I.h.as<float>() + I.cell_off[j] * n3, 0, I.sj[j].ncell * n3 * 4, s);
+                cudaMemsetAsync(I.hmom.as<double>() + I.cell_off[j] * 2, 0, I.sj[j].ncell * 2 * 8, s);
                 I.hstate[j] = JobState{};
             }
             cudaMemcpyAsync(I.states.p, I.hstate.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, s);

@@ -159,6 +159,7 @@ lbe_status bucket_create(Ctx* c, Bucket& b, const lbe_problem& pb, int prec, lon
                             {&B.mom, (size_t)cap_cells * 5 * 8}, {&B.G, (size_t)cap_cells * 2 * 8},
                             {&B.dU, (size_t)cap_cells * 8}, {&B.U3, (size_t)cap_cells * 8},
                             {&B.delta, (size_t)cap_cells * 8}, {&B.nd, (size_t)cap_cells * 8},
+                            {&B.hmom, (size_t)cap_cells * 2 * 8},
                             {&B.coef, b.coef_per_slot * slots * 8}, {&B.work, b.work_per_slot * slots * 8},
                             {&B.sjobs, slots * sizeof(SweepJobDev)}, {&B.ijobs, slots * sizeof(SisJobDev)},
                             {&B.states, slots * sizeof(JobState)}, {&B.act, slots * sizeof(int)},
@@ -277,6 +278,7 @@ void slot_install(Bucket& b, int s, const lbe_problem& pb, long off, int phase) 
     const long n3 = (long)pb.nv * pb.nv * pb.nv;
     const int eb = b.prec == LBE_FP64 ? 8 : 4;
     cudaMemsetAsync((char*)B.h.p + off * n3 * eb, 0, (size_t)g.cells * n3 * eb, st);
+    cudaMemsetAsync(B.hmom.as<double>() + off * 2, 0, (size_t)g.cells * 2 * 8, st);
     if (b.prec != LBE_FP64) cudaMemsetAsync((char*)b.aux.p + off * n3 * eb, 0, (size_t)g.cells * n3 * eb, st);
 }
 
@@ -297,6 +299,7 @@ void slot_set_correction(Bucket& b, int s) {
     g_h2d += sizeof(SweepJobDev) + sizeof(SisJobDev) + sizeof(JobState);
     const long n3 = (long)b.nv * b.nv * b.nv;
     cudaMemsetAsync(B.h.as<float>() + B.cell_off[s] * n3, 0, (size_t)B.sj[s].ncell * n3 * 4, st);
+    cudaMemsetAsync(B.hmom.as<double>() + B.cell_off[s] * 2, 0, (size_t)B.sj[s].ncell * 2 * 8, st);
 }
 
 struct Service {

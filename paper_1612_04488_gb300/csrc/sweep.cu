@@ -51,25 +51,70 @@ template <> struct Rn<float> {
     static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-    static __device__ __forceinline__ float rcp(float x) { return __fdiv_rn(1.0f, x); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 };
 template <> struct Rn<double> {
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-    static __device__ __forceinline__ double rcp(double x) { return __ddiv_rn(1.0, x); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    // 1/x without the FP64 divide (the FP64 pipe is this GPU's narrow one): the float reciprocal
+    // of x (relative error <= 2^-23 after rounding x to float) refined by two Newton steps
+    // r <- r + r (1 - x r), each squaring the error: 2^-46, then the double rounding level
+    // (within an ulp or two of the correctly rounded 1/x).  Outside the float range, the divide.
+    static __device__ __forceinline__ double rcp(double x) {
+        const float xf = (float)x;
+        const float ax = fabsf(xf);
+        if (!(ax > 1e-30f && ax < 1e30f)) return __ddiv_rn(1.0, x);
+        double r = (double)__frcp_rn(xf);
+        r = __fma_rn(r, __fma_rn(-x, r, 1.0), r);
+        r = __fma_rn(r, __fma_rn(-x, r, 1.0), r);
+        return r;
+    }
 };
 // one node of the second-order upwind march: h_i = (rhs_i + S - u (b h_(i-1) + c h_(i-2))) inv,
-// inv = 1 / (nu + u a)
+// inv = 1 / (nu + u a), in fused multiply-adds
 template <typename T>
 __device__ __forceinline__ T march_node(T r, T S, T u, T b, T c, T hm1, T hm2, T inv) {
     using R = Rn<T>;
-    return R::mul(R::sub(R::add(r, S), R::mul(u, R::add(R::mul(b, hm1), R::mul(c, hm2)))), inv);
+    return R::mul(R::fma(-u, R::fma(b, hm1, R::mul(c, hm2)), R::add(r, S)), inv);
 }
 template <typename T>
 __device__ __forceinline__ T march_inv(T nu, T u, T a) {
     using R = Rn<T>;
-    return R::rcp(R::add(nu, R::mul(u, a)));
+    return R::rcp(R::fma(u, a, nu));
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)));
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// bounded wait for the phase `parity` of an mbarrier (~2 s); false when the deadline passed
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_addr(bar);
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > 4000000000LL) return false;
+    }
+}
+// one contiguous global -> shared copy by the bulk-copy (TMA) engine, completing on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
 }
 
 // 1D sweep (plates): one thread per mirror pair (v1 > 0, v1 < 0) of velocities, marching the
@@ -80,7 +125,10 @@ __device__ __forceinline__ T march_inv(T nu, T u, T a) {
 //            ~1 KB of shared memory per node and block limits residency to a few blocks per SM;
 //   SCHED 1  a register ring: the right-hand sides of the next RING nodes are in flight while a
 //            node is solved, no shared memory beyond the coefficients, so the SM holds as many
-//            threads as the registers allow.
+//            threads as the registers allow;
+//   SCHED 2  (float; n2 a multiple of 128) a ring of node rows in shared memory filled by the
+//            bulk-copy (TMA) engine, 512 bytes per node and column, one mbarrier per half ring:
+//            up to 32 nodes in flight per block at 16 KB of shared memory.
 // The march coefficients [fa|fb|fc|ba|bb|bc] (n each) are converted to T once per block into
 // shared memory when `staged` (a double-to-float conversion per node and thread would run at
 // the FP64 rate).
@@ -153,6 +201,81 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
             g2 = g1;
             g1 = hi;
         }
+    } else if constexpr (SCHED == 2) {
+        // The block's 128 velocities are contiguous in both columns (n2 is a multiple of 128),
+        // so each node is one 512-byte row per column, copied by the bulk-copy engine into a
+        // ring of two halves of HR rows in shared memory.  The two columns form one stream of
+        // 2 (n - 1) rows: forward nodes 1 .. n-1, then backward nodes n-2 .. 0.  Half k sits
+        // in slot k & 1, completes on that slot's mbarrier (its use number k >> 1 gives the
+        // phase), and is refilled with half k + 2 once every thread has read it.
+        constexpr int HR = 16;
+        const int tx = threadIdx.x;
+        const int P = 2 * (n - 1), nh = (P + HR - 1) / HR;
+        T* ring = reinterpret_cast<T*>(sweep_smem + ((6 * n * sizeof(T) + 15) / 16) * 16);
+        uint64_t* bar = reinterpret_cast<uint64_t*>(ring + 2 * HR * 128);
+        const long cpos0 = vpos - tx, cneg0 = vneg - tx;  // the block's first velocity per column
+        int issued = 0, landed = 0;  // halves issued (thread 0) / seen complete by every thread
+        auto issue = [&](int k) {  // thread 0: rows of half k
+            if (k >= nh) return;
+            issued = k + 1;
+            const int cnt = min(HR, P - k * HR);
+            uint64_t* bk = bar + (k & 1);
+            mbar_expect(bk, (uint32_t)(cnt * 128 * sizeof(T)));
+            for (int q = 0; q < cnt; ++q) {
+                const int p = k * HR + q;
+                const long src = p < n - 1 ? (long)(p + 1) * n3 + cpos0 : (long)(n - 2 - (p - (n - 1))) * n3 + cneg0;
+                bulk_g2s(ring + ((k & 1) * HR + q) * 128, r + src, 128 * sizeof(T), bk);
+            }
+        };
+        if (tx == 0) {
+            mbar_init1(&bar[0]);
+            mbar_init1(&bar[1]);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (tx == 0) {
+            issue(0);
+            issue(1);
+        }
+        T g1 = T(0), g2 = T(0);
+        for (int p = 0; p < P; ++p) {
+            const int k = p / HR;
+            if (p % HR == 0) {  // every thread saw half k land, or all give up together
+                const bool ok = mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1));
+                if (!__syncthreads_and(ok)) break;
+                landed = k + 1;
+            }
+            const T x = ring[((k & 1) * HR + p % HR) * 128 + tx];
+            if (p < n - 1) {
+                const int i = p + 1;
+                const T hi = march_node(x, Sp, v1, C(1, i), C(2, i), hm1, hm2, march_inv(nup, v1, C(0, i)));
+                o[(long)i * n3 + vpos] = hi;
+                hm2 = hm1;
+                hm1 = hi;
+                if (i == n - 1) {  // specular symmetry plane, then the backward march
+                    g1 = hm1;
+                    g2 = hm2;
+                    o[(long)(n - 1) * n3 + vneg] = hm1;
+                }
+            } else {
+                const int i = n - 2 - (p - (n - 1));
+                const T hi = march_node(x, Sn, u, C(4, i), C(5, i), g1, g2, march_inv(nun, u, C(3, i)));
+                o[(long)i * n3 + vneg] = hi;
+                g2 = g1;
+                g1 = hi;
+            }
+            if (p % HR == HR - 1 && p + 1 < P) {  // half k read by every thread: refill its slot
+                __syncthreads();
+                if (tx == 0) {
+                    // order the block's reads of the slot before the copy engine's writes
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(k + 2);
+                }
+            }
+        }
+        // after a failed wait: the copies still in flight land before the block leaves
+        if (tx == 0)
+            for (int k = landed; k < issued; ++k) mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1));
     } else {
         T rb[kRing];
 #pragma unroll
@@ -227,40 +350,130 @@ __global__ void __launch_bounds__(128) k_sweep2d(const T* __restrict__ rhs, T* _
     const T* r = rhs + jb.cell_off * n3;
     T* o = h + jb.cell_off * n3;
     const int dj = s2 ? -1 : 1;  // offset to the upwind row in j
+    // the right-hand side and the two upwind-row values (this thread's own outputs of the two
+    // previous rows) of the next D cells are in flight while a cell is solved
+    constexpr int D = sizeof(T) == 4 ? 16 : 8;
     for (int mj = 0; mj < ny; ++mj) {
         const int j = s2 ? mj : ny - 1 - mj;
         T hm1 = T(0), hm2 = T(0);
         const T ay = CY(0, mj), by = CY(1, mj), cy = CY(2, mj);
         auto cell_of = [&](int m) { return (long)(s1 ? m : nx - 1 - m) * ny + j; };
-        T buf[kPre], ib[kPre];
+        T buf[D], y1[D], y2[D];
         const T diag = nu + u2 * ay;
+        auto fetch = [&](int k, int m) {
+            const long cell = cell_of(m);
+            buf[k] = r[cell * n3 + v];
+            y1[k] = mj >= 1 ? o[(cell + dj) * n3 + v] : T(0);
+            y2[k] = mj >= 2 ? o[(cell + 2 * dj) * n3 + v] : T(0);
+        };
 #pragma unroll
-        for (int k = 0; k < kPre; ++k) {
-            buf[k] = k < nx ? r[cell_of(k) * n3 + v] : T(0);
-            ib[k] = k < nx ? T(1) / (diag + u1 * CX(0, k)) : T(0);
-        }
-        for (int m0 = 0; m0 < nx; m0 += kPre) {
+        for (int k = 0; k < D; ++k)
+            if (k < nx) fetch(k, k);
+        for (int m0 = 0; m0 < nx; m0 += D) {
 #pragma unroll
-            for (int k = 0; k < kPre; ++k) {
+            for (int k = 0; k < D; ++k) {
                 const int mi = m0 + k;
                 if (mi < nx) {
                     const long cell = cell_of(mi);
                     T acc = buf[k] + S;
-                    const T inv = ib[k];
-                    if (mi + kPre < nx) {
-                        buf[k] = r[cell_of(mi + kPre) * n3 + v];
-                        ib[k] = T(1) / (diag + u1 * CX(0, mi + kPre));
-                    }
+                    const T w1 = y1[k], w2 = y2[k];
+                    if (mi + D < nx) fetch(k, mi + D);
+                    const T inv = Rn<T>::rcp(diag + u1 * CX(0, mi));
                     if (mi >= 1) acc -= u1 * CX(1, mi) * hm1;
                     if (mi >= 2) acc -= u1 * CX(2, mi) * hm2;
-                    if (mj >= 1) acc -= u2 * by * o[(cell + dj) * n3 + v];
-                    if (mj >= 2) acc -= u2 * cy * o[(cell + 2 * dj) * n3 + v];
+                    if (mj >= 1) acc -= u2 * by * w1;
+                    if (mj >= 2) acc -= u2 * cy * w2;
                     const T hij = acc * inv;
                     o[cell * n3 + v] = hij;
                     hm2 = hm1;
                     hm1 = hij;
                 }
             }
+        }
+    }
+}
+
+// 2D sweep as a wavefront.  For one velocity the upwind march over the nx x ny cells is a
+// recurrence in both directions, but the cells of one anti-diagonal (march indices
+// mi + mj = d) are independent.  A block takes 32 consecutive velocities (one per lane) and
+// strips of WR rows (march order in y): warp w owns row mj = base + w and at step d solves
+// its cell mi = d - w, with its own two previous cells in x in registers and the two cells
+// below it in y from the warps w - 1, w - 2 of the previous steps through a 3-slot ring in
+// shared memory (one barrier per step); the last two rows of a strip are kept for the first
+// two warps of the next.  Loads and stores are coalesced rows of 32 velocities.  Each
+// warp's next right-hand sides are prefetched D cells ahead in a register queue.  The
+// arithmetic is that of the per-velocity march.
+template <typename T, int WR>
+__global__ void __launch_bounds__(32 * WR) k_sweep2d_wave(const T* __restrict__ rhs, T* __restrict__ h,
+                                                          const T* __restrict__ nu1, const T* __restrict__ vel,
+                                                          const T* __restrict__ feq,
+                                                          const SweepJobDev* __restrict__ jobs,
+                                                          const int* __restrict__ active,
+                                                          const double* __restrict__ coef, int nv) {
+    constexpr int D = 8;
+    extern __shared__ __align__(16) unsigned char sweep_smem[];
+    const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
+    const int n2 = nv * nv;
+    const long n3 = (long)n2 * nv;
+    const int nx = jb.nx, ny = jb.ny;
+    T* cxs = reinterpret_cast<T*>(sweep_smem);  // [xa|xb|xc] (nx each)
+    T* cys = cxs + 3 * nx;                       // [ya|yb|yc] (ny each)
+    T* ring = cys + 3 * ny;                      // [3][WR][32]
+    T* prev = ring + 3 * WR * 32;                // [2][nx][32]: rows base - 2, base - 1
+    const double* cg = coef + jb.coef_off;
+    for (int k = threadIdx.x; k < 3 * (nx + ny); k += blockDim.x) cxs[k] = (T)cg[k];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = blockIdx.x * 32 + lane;
+    const bool vok = v < n3;
+    const int vv = vok ? v : 0;
+    const int i1 = vv / n2, i2 = (vv / nv) % nv;
+    const bool s1 = i1 >= nv / 2, s2 = i2 >= nv / 2;
+    const T u1 = s1 ? vel[i1] : -vel[i1];
+    const T u2 = s2 ? vel[i2] : -vel[i2];
+    const T nu = (T)jb.delta * nu1[vv];
+    const T S = source<T>(jb.forcing, vel[i1], vel[i2], vel[vv % nv], feq[vv]);
+    const T* r = rhs + jb.cell_off * n3;
+    T* o = h + jb.cell_off * n3;
+    __syncthreads();
+    for (int base = 0; base < ny; base += WR) {
+        const int mj = base + w;
+        const bool rowok = vok && mj < ny;
+        const int j = s2 ? mj : ny - 1 - mj;
+        const T ay = rowok ? cys[mj] : T(0), by = rowok ? cys[ny + mj] : T(0), cy = rowok ? cys[2 * ny + mj] : T(0);
+        const T diag = nu + u2 * ay;
+        auto cell_of = [&](int m) { return (long)(s1 ? m : nx - 1 - m) * ny + j; };
+        T q[D];  // right-hand sides of cells mi .. mi + D - 1 of this row
+#pragma unroll
+        for (int k = 0; k < D; ++k) q[k] = (rowok && k < nx) ? r[cell_of(k) * n3 + v] : T(0);
+        T hm1 = T(0), hm2 = T(0);
+        const int nsteps = nx + WR - 1;
+        for (int d = 0; d < nsteps; ++d) {
+            const int mi = d - w;
+            if (rowok && mi >= 0 && mi < nx) {
+                const T rq = q[0];
+#pragma unroll
+                for (int k = 0; k + 1 < D; ++k) q[k] = q[k + 1];
+                q[D - 1] = mi + D < nx ? r[cell_of(mi + D) * n3 + v] : T(0);
+                T w1 = T(0), w2 = T(0);  // h at (mi, mj - 1), (mi, mj - 2)
+                if (mj >= 1) w1 = w >= 1 ? ring[(((d - 1) % 3) * WR + w - 1) * 32 + lane] : prev[(nx + mi) * 32 + lane];
+                if (mj >= 2)
+                    w2 = w >= 2 ? ring[(((d - 2) % 3) * WR + w - 2) * 32 + lane]
+                                : prev[((w == 1 ? nx : 0) + mi) * 32 + lane];
+                T acc = rq + S;
+                const T inv = Rn<T>::rcp(diag + u1 * cxs[mi]);
+                if (mi >= 1) acc -= u1 * cxs[nx + mi] * hm1;
+                if (mi >= 2) acc -= u1 * cxs[2 * nx + mi] * hm2;
+                if (mj >= 1) acc -= u2 * by * w1;
+                if (mj >= 2) acc -= u2 * cy * w2;
+                const T hij = acc * inv;
+                o[cell_of(mi) * n3 + v] = hij;
+                ring[((d % 3) * WR + w) * 32 + lane] = hij;
+                if (w == WR - 2) prev[mi * 32 + lane] = hij;
+                if (w == WR - 1) prev[(nx + mi) * 32 + lane] = hij;
+                hm2 = hm1;
+                hm1 = hij;
+            }
+            __syncthreads();
         }
     }
 }
@@ -534,7 +747,10 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
                                                  const T* __restrict__ feq,
                                                  const T* __restrict__ vel, const SweepJobDev* __restrict__ jobs,
                                                  const int* __restrict__ active, int nv,
-                                                 const JobState* __restrict__ state) {
+                                                 const JobState* __restrict__ state, double* __restrict__ hm,
+                                                 const double* __restrict__ nd, const T* __restrict__ nu1,
+                                                 double dv3) {
+    __shared__ dfloat redx[32 * 2];
     const int jid = active ? active[blockIdx.y] : blockIdx.y;
     if (state && state[jid].skip) return;  // finished before this iteration
     const SweepJobDev jb = jobs[jid];
@@ -547,6 +763,14 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
         const T* src = hh + g0;
         T* dst = h + g0;
         const T* ex = extra ? extra + g0 : nullptr;
+        const float ndc = hm ? (float)nd[jb.cell_off + c] : 0.f, dl = (float)jb.delta;
+        float a0 = 0.f, c0 = 0.f, a1 = 0.f, c1 = 0.f;  // compensated sums of the two moments
+        auto kahan = [](float& sum, float& comp, float x) {
+            const float y = x - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        };
         for (int r = threadIdx.x; r < norb; r += blockDim.x) {
             const int i3 = r % hv;
             int i1, i2;
@@ -577,10 +801,31 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
                 dst[vb] = y;
                 dst[vc] = -y;
                 dst[vd] = -y;
+                if (hm) {  // v3 h is the same at the four points; v2 flips sign under R2
+                    const float wa = ndc - dl * (float)nu1[va], wb = ndc - dl * (float)nu1[vb];
+                    const float wc = ndc - dl * (float)nu1[vc], wd = ndc - dl * (float)nu1[vd];
+                    const float t = (float)vel[i3] * (float)y;
+                    kahan(a0, c0, (float)vel[i1] * t * ((wa + wb) + (wc + wd)));
+                    kahan(a1, c1, (float)vel[i2] * t * ((wa - wb) + (wc - wd)));
+                }
             } else {
                 const T y = (T)0.5 * (xa - xc) + d * vel[i3] * feq[va];
                 dst[va] = y;
                 dst[vc] = -y;
+                if (hm) {
+                    const float w = (ndc - dl * (float)nu1[va]) + (ndc - dl * (float)nu1[vc]);
+                    const float t = (float)vel[i3] * (float)y * w;
+                    kahan(a0, c0, (float)vel[i1] * t);
+                    kahan(a1, c1, (float)vel[i2] * t);
+                }
+            }
+        }
+        if (hm) {
+            dfloat sm[2] = {df_fast2sum(a0, -c0), df_fast2sum(a1, -c1)};
+            block_reduce_df<2>(sm, redx);
+            if (threadIdx.x == 0) {
+                hm[2 * (jb.cell_off + c) + 0] = 2.0 * (double)sm[0] * dv3;
+                hm[2 * (jb.cell_off + c) + 1] = 2.0 * (double)sm[1] * dv3;
             }
         }
     }
@@ -597,6 +842,9 @@ static void sweep1d_sched(int sched, const DevTables& t, dim3 g, size_t smem_coe
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
     if (sched == 0)
         k_sweep1d<T, 0><<<g, 128, smem_full, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged);
+    else if (sched == 2)
+        k_sweep1d<T, 2><<<g, 128, (smem_coef + 15) / 16 * 16 + 2 * 16 * 128 * sizeof(T) + 16, s>>>(
+            rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged);
     else
         k_sweep1d<T, 1><<<g, 128, smem_coef, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged);
 }
@@ -618,7 +866,7 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
         // when that fits in 200 KB; which schedule is faster is measured at first use
         const size_t full = sbytes + 2 * (size_t)(max_coef / 6) * 128 * sizeof(T);
         int sched = 1;
-        if (sizeof(T) == 4 && staged && full <= 200 * 1024 && t.tuning) {
+        if (sizeof(T) == 4 && staged && full <= 200 * 1024 && t.tuning && (uintptr_t)rhs % 16 == 0) {
             static std::once_flag attr;  // opt-in shared memory beyond 48 KB (float instance)
             std::call_once(attr, [] {
                 cudaFuncSetAttribute(k_sweep1d<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -637,27 +885,34 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
             } else if (capturing) {
                 sched = 0;
             } else {
-                // both schedules twice, alternating; each writes the same h (same arithmetic)
-                cudaEvent_t ev[5];
-                for (auto& e : ev) cudaEventCreate(&e);
+                // every schedule twice, in turn; each writes the same h (same arithmetic).  The
+                // bulk-copy ring needs whole 128-velocity rows per block (nv = 16, 32).
+                const int NS = (nv * nv) % 128 == 0 ? 3 : 2;
+                cudaEvent_t ev[7];
+                for (int k = 0; k <= 2 * NS; ++k) cudaEventCreate(&ev[k]);
                 cudaEventRecord(ev[0], s);
-                for (int k = 0; k < 4; ++k) {
-                    sweep1d_sched<T>(k & 1, t, g, smem, full, staged, rhs, h, jobs, active, coef, s);
+                for (int k = 0; k < 2 * NS; ++k) {
+                    sweep1d_sched<T>(k % NS, t, g, smem, full, staged, rhs, h, jobs, active, coef, s);
                     cudaEventRecord(ev[k + 1], s);
                 }
-                cudaEventSynchronize(ev[4]);
-                float ms[4] = {0, 0, 0, 0};
-                for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
-                for (auto& e : ev) cudaEventDestroy(e);
-                const float t0 = std::min(ms[0], ms[2]), t1 = std::min(ms[1], ms[3]);
-                sched = t1 <= t0 ? 1 : 0;
+                cudaEventSynchronize(ev[2 * NS]);
+                float ms[6] = {};
+                for (int k = 0; k < 2 * NS; ++k) cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
+                for (int k = 0; k <= 2 * NS; ++k) cudaEventDestroy(ev[k]);
+                float best[3] = {0.f, 0.f, 0.f};
+                for (int q = 0; q < NS; ++q) best[q] = std::min(ms[q], ms[q + NS]);
+                sched = 0;
+                for (int q = 1; q < NS; ++q)
+                    if (best[q] < best[sched]) sched = q;
                 t.tuning->sweep[key] = sched;
-                char line[200];
+                static const char* names[3] = {"staged", "register ring", "bulk-copy ring"};
+                char line[240];
                 snprintf(line, sizeof line,
-                         "sweep1d<float> nv=%d problems<=%d nodes<=%d: %s (staged %.1f us, register ring %.1f us)", nv,
-                         jb, nb, sched ? "register ring" : "staged", 1000.0f * t0, 1000.0f * t1);
+                         "sweep1d<float> nv=%d problems<=%d nodes<=%d: %s (staged %.1f us, register ring %.1f us, "
+                         "bulk-copy ring %.1f us)",
+                         nv, jb, nb, names[sched], 1000.0f * best[0], 1000.0f * best[1], 1000.0f * best[2]);
                 t.tuning->log.push_back(line);
-                g_launches += 3;
+                g_launches += 2 * NS - 1;
                 return;
             }
         }
@@ -666,9 +921,23 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
         const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
         const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
         const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
+        // the wavefront: blocks of 32 velocities x 16 rows; shared memory holds the
+        // coefficients, the 3-step ring and the strip's last two rows
+        constexpr int WR = 16;
         const int nt = nv * nv * nv;
-        dim3 g((nt + 127) / 128, njobs);
-        k_sweep2d<T><<<g, 128, smem, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv, staged);
+        const int mcx = max_coef / 3;  // largest nx + ny of the launch's jobs
+        const size_t sm2 = (size_t)(3 * mcx + 3 * WR * 32 + 2 * mcx * 32) * sizeof(T);
+        static std::once_flag attr;
+        std::call_once(attr, [] {
+            cudaFuncSetAttribute(k_sweep2d_wave<T, WR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        });
+        if (sm2 <= 160 * 1024) {
+            dim3 g((nt + 31) / 32, njobs);
+            k_sweep2d_wave<T, WR><<<g, 32 * WR, sm2, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv);
+        } else {
+            dim3 g((nt + 127) / 128, njobs);
+            k_sweep2d<T><<<g, 128, smem, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv, staged);
+        }
     }
 }
 
@@ -696,13 +965,16 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
 
 template <typename T>
 void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
-                    const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state) {
+                    const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state, double* hm,
+                    const double* nd) {
     if (njobs <= 0) return;
     g_launches += 1;
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
     dim3 g(2 * sm_count(), njobs);
-    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state);
+    const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
+    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1,
+                                   t.dv * t.dv * t.dv);
 }
 
 template void launch_sweep<double>(const DevTables&, int, int, int, const double*, double*,
@@ -712,8 +984,10 @@ template void launch_sweep<float>(const DevTables&, int, int, int, const float*,
 template void launch_moments<double>(const DevTables&, long, int, const double*, double*, cudaStream_t);
 template void launch_moments<float>(const DevTables&, long, int, const float*, double*, cudaStream_t);
 template void launch_correct<double>(const DevTables&, int, const double*, double*, const double*,
-                                     const double*, const SweepJobDev*, const int*, cudaStream_t, const JobState*);
+                                     const double*, const SweepJobDev*, const int*, cudaStream_t, const JobState*,
+                                     double*, const double*);
 template void launch_correct<float>(const DevTables&, int, const float*, float*, const double*, const float*,
-                                    const SweepJobDev*, const int*, cudaStream_t, const JobState*);
+                                    const SweepJobDev*, const int*, cudaStream_t, const JobState*, double*,
+                                    const double*);
 
 }  // namespace lbe

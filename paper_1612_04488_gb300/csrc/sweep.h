@@ -11,9 +11,11 @@ struct DevTables;
 struct Ctx;
 
 // fsm_dense.cu: tensor-core operator on the parity subspace (float in / out; mode 1 or 2)
+// hm (may be NULL): per cell the h part of G (launch_correct); with it and without Lout the
+// expand reads no h.
 lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h,
                         float* Lplus, float* Lout, cudaStream_t s, bool sync = true, const double* nd = nullptr,
-                        double* G = nullptr);
+                        double* G = nullptr, const double* hm = nullptr);
 lbe_status tc_check(Ctx* c, DevTables* t);
 void tc_release(Ctx* c, DevTables* t);
 // refine.cu: BF16 operator inside an outer defect-correction loop
@@ -63,9 +65,13 @@ void launch_moments(const DevTables& t, long cell0, int cells, const T* h, doubl
 void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, const int* active,
                        const double* mom, const double* G, const double* coef, double* work, double* dU,
                        double* U3, JobState* state, cudaStream_t s);
+// hm (may be NULL; [cells][2] double): per cell the L-moment part carried by the new h,
+// Gh_j = 2 sum_v v_j v3 (N delta - delta nu) h dv^3 (j = 1, 2), with N delta per cell from nd --
+// the tensor-core operator adds it to 2 sum v_j v3 L+ h dv^3 instead of reading h again.
 template <typename T>
 void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
-                    const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state = nullptr);
+                    const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state = nullptr,
+                    double* hm = nullptr, const double* nd = nullptr);
 
 // fsm_cc.cu
 void init_twiddles_cc();
