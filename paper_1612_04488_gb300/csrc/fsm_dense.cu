@@ -98,6 +98,32 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
+// A tile slice copied into the same shared-memory offset of every CTA in `mask` (cluster
+// multicast); each destination's mbarrier at the offset of `bar` receives its bytes.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+        "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+// arrive, when this CTA's issued MMAs are done, on the mbarrier at the offset of `bar` in
+// every CTA of `mask`
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "h"(mask)
+                 : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
     asm volatile(
@@ -167,6 +193,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // One CTA per work item: a 128 x BN output tile and a range of its K slices.  slot < 0: the
 // item covers all of K and stores its tile into Y; slot >= 0: a part of a split tile, stored
 // whole into partial slot `slot` of P ([slot][BN][128]) for k_gemm_fixup to add up.
+// With cs > 1 the launch is a cluster of cs CTAs whose items share the row tile and the K
+// range (neighbouring column tiles): each CTA copies 128 / cs rows of every A slice and
+// multicasts them to all, so A crosses from L2 once per cluster; a stage is refilled only
+// when every CTA of the cluster has consumed it (each CTA's MMA commit arrives on the stage's
+// empty barrier in all of them).  The arithmetic is that of cs = 1.
 struct GemmWork {
     int col0, row0, xrow0, kt0, kt1, slot;  // xrow0: first operand row (block b: b * cpad + col0)
 };
@@ -176,7 +207,7 @@ __global__ void __launch_bounds__(128, 1)
     k_dense_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                  const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl, int Mrows,
                  int ncols, const GemmWork* __restrict__ work, float* __restrict__ Y, float* __restrict__ P,
-                 int* __restrict__ err, int probe) {
+                 int* __restrict__ err, int probe, int cs) {
     constexpr int A_BYTES = kBM * kBK * 2, X_BYTES = BN * kBK * 2, STAGE = 2 * A_BYTES + 2 * X_BYTES;
     constexpr int kStages = GemmCfg<BN>::STAGES;
     extern __shared__ uint8_t smem_raw[];
@@ -190,11 +221,13 @@ __global__ void __launch_bounds__(128, 1)
     const GemmWork wk = work[blockIdx.x];
     const int col0 = wk.col0, row0 = wk.row0, xrow0 = wk.xrow0, kt0 = wk.kt0;
     const int KT = wk.kt1 - wk.kt0;
+    const uint32_t rank = cs > 1 ? cluster_rank() : 0u;
+    const uint16_t cmask = (uint16_t)((1u << cs) - 1u);
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], (uint32_t)cs);
         }
         mbar_init(done, 1);
         mbar_init(never, 1);
@@ -207,6 +240,7 @@ __global__ void __launch_bounds__(128, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if (cs > 1) cluster_sync_all();  // every CTA's barriers exist before any multicast lands
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     constexpr uint32_t IDESC = idesc_bf16(kBM, BN);
@@ -218,9 +252,15 @@ __global__ void __launch_bounds__(128, 1)
         auto issue = [&](int kt, int s) {  // slice kt of this CTA's K range into stage s
             const int x = (kt0 + kt) * kBK;
             uint8_t* st = base + s * STAGE;
-            mbar_expect_tx(&full[s], STAGE);
-            tma_load_2d(st, &tmAh, x, row0, &full[s]);
-            tma_load_2d(st + A_BYTES, &tmAl, x, row0, &full[s]);
+            mbar_expect_tx(&full[s], STAGE);  // the whole stage lands here, A from every CTA
+            if (cs == 1) {
+                tma_load_2d(st, &tmAh, x, row0, &full[s]);
+                tma_load_2d(st + A_BYTES, &tmAl, x, row0, &full[s]);
+            } else {
+                const int rows = kBM / cs, off = (int)rank * rows;  // this CTA's slice of the A rows
+                tma_load_2d_mc(st + off * kBK * 2, &tmAh, x, row0 + off, &full[s], cmask);
+                tma_load_2d_mc(st + A_BYTES + off * kBK * 2, &tmAl, x, row0 + off, &full[s], cmask);
+            }
             tma_load_2d(st + 2 * A_BYTES, &tmXh, x, xrow0, &full[s]);
             tma_load_2d(st + 2 * A_BYTES + X_BYTES, &tmXl, x, xrow0, &full[s]);
         };
@@ -246,7 +286,10 @@ __global__ void __launch_bounds__(128, 1)
                 mma_bf16(tmem, sdesc_sw64(al + o), sdesc_sw64(xh + o), IDESC, 1u);
                 mma_bf16(tmem, sdesc_sw64(ah + o), sdesc_sw64(xl + o), IDESC, 1u);
             }
-            mma_commit(&empty[s]);
+            if (cs > 1)
+                mma_commit_mc(&empty[s], cmask);
+            else
+                mma_commit(&empty[s]);
             const int nk = kt - 1 + kStages;  // refill the slot of the previous stage
             if (kt >= 1 && nk < KT) {
                 const int sp = (kt - 1) % kStages;
@@ -288,6 +331,7 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    if (cs > 1) cluster_sync_all();  // no CTA leaves while its peers may still signal it
 }
 
 // ---- reflection blocks and their transposition halves ------------------------------------
@@ -682,33 +726,39 @@ __global__ void __launch_bounds__(256) k_gemm_fixup(const GemmFix* __restrict__ 
     *reinterpret_cast<float4*>(Y + (long)col * Mrows + f.row0 + r) = acc;
 }
 
-// Work list of one launch shape.  With T tiles on P SMs, the first floor(T / P) * P
-// tiles run whole (entire waves); each remaining tile is split into S K-ranges, so the last
-// partial wave becomes S times as many shorter items (S = 4 for a tail, up to 4 when there
-// are fewer tiles than SMs, keeping at least 8 K slices per item).
+// Work list of one launch shape.  Tiles go in groups of G neighbouring column tiles of one
+// row tile (G = 4, 2 or 1, whichever divides the column tiles), deepest sub-blocks first.  With
+// T tiles on P SMs, the groups within the first floor(T / P) * P tiles run whole (entire
+// waves); each remaining tile is split into S K-ranges, so the last partial wave becomes S
+// times as many shorter items (S = 4 for a tail, up to 4 when there are fewer tiles than SMs,
+// keeping at least 4 K slices per item).  The G members of a group (and of each of its K
+// parts) are consecutive items with the same row tile and K range, so any cluster size that
+// divides G can take them together; the items, and so the arithmetic, do not depend on it.
 struct GemmPlan {
-    std::vector<GemmWork> work;
+    std::vector<GemmWork> work;     // cluster order: the group's members consecutive per K part
+    std::vector<GemmWork> work_t;   // tile order: each tile's K parts consecutive (cluster size 1)
     std::vector<GemmFix> fix;
     int slots = 0;
+    int group = 1;
 };
 
 GemmPlan make_plan(int cells, int bn, const SubLayout& L, int P) {
     GemmPlan pl;
     const int nct = (cells + bn - 1) / bn, cpad = nct * bn;
+    const int G = nct % 4 == 0 ? 4 : (nct % 2 == 0 ? 2 : 1);
+    pl.group = G;
     const int nrt = L.rows / kBM, T = nct * nrt;
-    // tiles, deepest first (the sub-blocks differ in K), so that the last wave holds the
-    // shortest ones
-    struct Tile {
-        int col0, row0, xrow0, kt;
+    struct Group {
+        int row0, q, kt, cg;
     };
-    std::vector<Tile> tiles;
-    for (int t = 0; t < T; ++t) {
-        const int col0 = (t % nct) * bn, row0 = (t / nct) * kBM;
+    std::vector<Group> groups;
+    for (int rt = 0; rt < nrt; ++rt) {
+        const int row0 = rt * kBM;
         int q = 0;
         while (q + 1 < L.count && row0 >= L.roff[q + 1]) ++q;
-        tiles.push_back({col0, row0, q * cpad + col0, L.np[q] / kBK});  // the sub-block's operand rows, depth
+        for (int cg = 0; cg < nct / G; ++cg) groups.push_back({row0, q, L.np[q] / kBK, cg});
     }
-    std::stable_sort(tiles.begin(), tiles.end(), [](const Tile& a, const Tile& b) { return a.kt > b.kt; });
+    std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.kt > b.kt; });
     int W, S;
     if (T >= P) {
         W = T / P * P;
@@ -720,31 +770,73 @@ GemmPlan make_plan(int cells, int bn, const SubLayout& L, int P) {
     int ktmin = 1 << 30;
     for (int q = 0; q < L.count; ++q) ktmin = std::min(ktmin, L.np[q] / kBK);
     while (S > 1 && ktmin / S < 4) --S;
-    if (S == 1) W = T;
-    for (int t = 0; t < T; ++t) {
-        const Tile& u = tiles[t];
-        if (t < W) {
-            pl.work.push_back({u.col0, u.row0, u.xrow0, 0, u.kt, -1});
+    const int Wg = S == 1 ? (int)groups.size() : W / G;  // whole groups
+    for (int gi = 0; gi < (int)groups.size(); ++gi) {
+        const Group& u = groups[gi];
+        if (gi < Wg) {
+            for (int m = 0; m < G; ++m) {
+                const int col0 = (u.cg * G + m) * bn;
+                pl.work.push_back({col0, u.row0, u.q * cpad + col0, 0, u.kt, -1});
+                pl.work_t.push_back(pl.work.back());
+            }
             continue;
         }
-        const int slot0 = pl.slots;
+        const int base = pl.slots;  // tile m's parts sit in slots base + m S .. base + m S + S - 1
         for (int p = 0; p < S; ++p)
-            pl.work.push_back({u.col0, u.row0, u.xrow0, u.kt * p / S, u.kt * (p + 1) / S, pl.slots++});
-        pl.fix.push_back({u.col0, u.row0, slot0, S});
+            for (int m = 0; m < G; ++m) {
+                const int col0 = (u.cg * G + m) * bn;
+                pl.work.push_back({col0, u.row0, u.q * cpad + col0, u.kt * p / S, u.kt * (p + 1) / S, base + m * S + p});
+            }
+        for (int m = 0; m < G; ++m)
+            for (int p = 0; p < S; ++p) {
+                const int col0 = (u.cg * G + m) * bn;
+                pl.work_t.push_back({col0, u.row0, u.q * cpad + col0, u.kt * p / S, u.kt * (p + 1) / S, base + m * S + p});
+            }
+        for (int m = 0; m < G; ++m) pl.fix.push_back({(u.cg * G + m) * bn, u.row0, base + m * S, S});
+        pl.slots += G * S;
     }
     return pl;
 }
 
+// Number of positions where the float arrays a and b differ bitwise (atomic count).
+__global__ void k_count_diff(const float* __restrict__ a, const float* __restrict__ b, long n, int* __restrict__ out) {
+    int c = 0;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x)
+        c += __float_as_uint(a[k]) != __float_as_uint(b[k]) ? 1 : 0;
+    if (c) atomicAdd(out, c);
+}
+
+// The GEMM (cluster size cs; cs = 1 an ordinary launch) and, when fix is set, the fix-up of
+// the split tiles.  Returns the launch error.
 template <int BN>
-void launch_gemm(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1, int nr,
-                 int cells, int nwork, const GemmWork* work, int nfix, const GemmFix* fix, float* Y, float* P,
-                 int* err, int probe, cudaStream_t s) {
+cudaError_t launch_gemm(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
+                        int nr, int cells, int nwork, const GemmWork* work, int nfix, const GemmFix* fix, float* Y,
+                        float* P, int* err, int probe, int cs, cudaStream_t s) {
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_dense_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GemmCfg<BN>::SMEM);
     });
-    k_dense_gemm<BN><<<nwork, 128, GemmCfg<BN>::SMEM, s>>>(a0, a1, b0, b1, nr, cells, work, Y, P, err, probe);
+    if (cs == 1) {
+        k_dense_gemm<BN><<<nwork, 128, GemmCfg<BN>::SMEM, s>>>(a0, a1, b0, b1, nr, cells, work, Y, P, err, probe, 1);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nwork);
+        cfg.blockDim = dim3(128);
+        cfg.dynamicSmemBytes = GemmCfg<BN>::SMEM;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const cudaError_t e =
+            cudaLaunchKernelEx(&cfg, k_dense_gemm<BN>, a0, a1, b0, b1, nr, cells, work, Y, P, err, probe, cs);
+        if (e != cudaSuccess) return e;
+    }
     if (nfix > 0) k_gemm_fixup<BN><<<dim3((BN * kBM / 4 + 255) / 256, nfix), 256, 0, s>>>(fix, P, Y, nr, cells);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -755,21 +847,26 @@ struct DenseOp {
     SubLayout L;
     __nv_bfloat16* Ah = nullptr;
     __nv_bfloat16* Al = nullptr;
-    CUtensorMap mAh, mAl;
+    CUtensorMap mAh[3], mAl[3];  // boxes of 128, 64 and 32 rows (cluster sizes 1, 2 and 4)
     size_t bytes = 0;
 };
 
 // Work list of one launch shape on the device (built once per (cells, BN, Nr)).
 struct DevPlan {
-    GemmWork* work = nullptr;
+    GemmWork* work = nullptr;    // cluster order
+    GemmWork* work_t = nullptr;  // tile order (cluster size 1)
     GemmFix* fix = nullptr;
     int nwork = 0, nfix = 0, slots = 0;
+    int group = 1;  // column tiles per group (the largest cluster the items allow)
+    int cs = 0;     // cluster size chosen by the autotuner (0: not yet measured)
 };
 
 struct TcOperands {
     std::mutex mu;
     DenseOp op[3];  // by mode
     std::map<long long, DevPlan> plans;
+    // cluster size chosen per launch class (rows, tile width, column-tile group): tuned once
+    std::map<long long, int> cs_choice;
     // per-call workspace (grow-only), one per stream: callers on different streams (the
     // service's buckets) run concurrently and must not share operands or partial tiles
     std::map<cudaStream_t, Arena> ws;
@@ -822,7 +919,11 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
     dev_free(c, sc, scr);
     dev_free(c, dl, (size_t)nb * 8);
     if (st != LBE_OK) return st;
-    if (!make_map(&d.mAh, d.Ah, d.L.rows, d.L.npmax, kBM) || !make_map(&d.mAl, d.Al, d.L.rows, d.L.npmax, kBM)) {
+    bool maps = true;
+    for (int k = 0; k < 3; ++k)
+        maps = maps && make_map(&d.mAh[k], d.Ah, d.L.rows, d.L.npmax, kBM >> k) &&
+               make_map(&d.mAl[k], d.Al, d.L.rows, d.L.npmax, kBM >> k);
+    if (!maps) {
         c->last_error = "cuTensorMapEncodeTiled unavailable or failed";
         return LBE_INTERNAL;
     }
@@ -863,14 +964,17 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         dp.nwork = (int)pl.work.size();
         dp.nfix = (int)pl.fix.size();
         dp.slots = pl.slots;
+        dp.group = pl.group;
         if ((st = dev_alloc(c, (void**)&dp.work, pl.work.size() * sizeof(GemmWork))) != LBE_OK) return st;
+        if ((st = dev_alloc(c, (void**)&dp.work_t, pl.work_t.size() * sizeof(GemmWork))) != LBE_OK) return st;
+        cudaMemcpyAsync(dp.work_t, pl.work_t.data(), pl.work_t.size() * sizeof(GemmWork), cudaMemcpyHostToDevice, s);
         if (dp.nfix && (st = dev_alloc(c, (void**)&dp.fix, pl.fix.size() * sizeof(GemmFix))) != LBE_OK) return st;
         cudaMemcpyAsync(dp.work, pl.work.data(), pl.work.size() * sizeof(GemmWork), cudaMemcpyHostToDevice, s);
         if (dp.nfix) cudaMemcpyAsync(dp.fix, pl.fix.data(), pl.fix.size() * sizeof(GemmFix), cudaMemcpyHostToDevice, s);
         cudaStreamSynchronize(s);  // the host vectors go out of scope
         pit = T.plans.emplace(pkey, dp).first;
     }
-    const DevPlan& plan = pit->second;
+    DevPlan& plan = pit->second;
     const size_t xb = (size_t)nsub * cpad * npmax * 2, yb = (size_t)cells * mrows * 4;
     const size_t pb = (size_t)plan.slots * bn * kBM * 4;
     Arena& ws = T.ws[s];
@@ -906,16 +1010,114 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     cudaEvent_t ev[2] = {nullptr, nullptr};
     const bool timed = sync && g_time_kernels.load() != 0 && cudaEventCreate(&ev[0]) == cudaSuccess &&
                        cudaEventCreate(&ev[1]) == cudaSuccess;
-    if (timed) cudaEventRecord(ev[0], s);
     const int probe = g_expire_waits.load();
-    switch (bn) {
-        case 64: launch_gemm<64>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        case 128: launch_gemm<128>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        case 160: launch_gemm<160>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        case 192: launch_gemm<192>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        case 208: launch_gemm<208>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        case 224: launch_gemm<224>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
-        default: launch_gemm<256>(d.mAh, d.mAl, mXh, mXl, mrows, cells, plan.nwork, plan.work, plan.nfix, plan.fix, Y, Pp, T.err_dev, probe, s); break;
+    auto gemm = [&](int cs, bool with_fix) -> cudaError_t {
+        const int k = cs == 4 ? 2 : (cs == 2 ? 1 : 0);
+        const int nf = with_fix ? plan.nfix : 0;
+        switch (bn) {
+            case 64: return launch_gemm<64>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            case 128: return launch_gemm<128>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            case 160: return launch_gemm<160>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            case 192: return launch_gemm<192>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            case 208: return launch_gemm<208>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            case 224: return launch_gemm<224>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            default: return launch_gemm<256>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+        }
+    };
+    const long long cs_key = ((long long)mrows << 20) | ((long long)bn << 8) | plan.group;
+    if (plan.cs == 0) {
+        auto it = T.cs_choice.find(cs_key);
+        if (it != T.cs_choice.end()) plan.cs = it->second;
+    }
+    if (plan.cs == 0) {
+        // autotuner: each cluster size the work list allows, twice in turn (every one computes
+        // the same Y); a size that cannot launch is skipped
+        cudaStreamCaptureStatus cs_ = cudaStreamCaptureStatusNone;
+        const bool capturing = cudaStreamIsCapturing(s, &cs_) != cudaSuccess || cs_ != cudaStreamCaptureStatusNone;
+        std::vector<int> cand{1};
+        for (int c : {2, 4})
+            if (plan.group % c == 0) cand.push_back(c);
+        if (capturing || cand.size() == 1 || probe) {
+            if (!capturing && !probe) plan.cs = 1;
+        } else {
+            // every candidate runs with the fix-up and must reproduce the cluster-1 result bit
+            // for bit (they share the work list); one that does not is never chosen
+            std::vector<float> best(cand.size(), 1e30f);
+            float* yref = nullptr;
+            int* ndiff = nullptr;
+            const size_t ny = (size_t)cells * mrows;
+            const bool verify = dev_alloc(c, (void**)&yref, ny * 4) == LBE_OK &&
+                                dev_alloc(c, (void**)&ndiff, 256) == LBE_OK;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int rep = 0; rep < 2; ++rep)
+                for (size_t i = 0; i < cand.size(); ++i) {
+                    if (best[i] >= 2e30f) continue;
+                    cudaEventRecord(e0, s);
+                    if (gemm(cand[i], true) != cudaSuccess) {
+                        cudaGetLastError();
+                        best[i] = 3e30f;
+                        continue;
+                    }
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    int werr = 0;  // a bounded wait expired: drop the candidate, clear the word
+                    cudaMemcpy(&werr, T.err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+                    if (werr) {
+                        cudaMemset(T.err_dev, 0, sizeof(int));
+                        best[i] = 5e30f;
+                        continue;
+                    }
+                    if (verify && rep == 0) {
+                        if (i == 0) {
+                            cudaMemcpyAsync(yref, Y, ny * 4, cudaMemcpyDeviceToDevice, s);
+                        } else {
+                            int nd = 0;
+                            cudaMemsetAsync(ndiff, 0, sizeof(int), s);
+                            k_count_diff<<<4 * sm_count(), 256, 0, s>>>(yref, Y, (long)ny, ndiff);
+                            cudaMemcpyAsync(&nd, ndiff, sizeof(int), cudaMemcpyDeviceToHost, s);
+                            cudaStreamSynchronize(s);
+                            if (nd != 0) {
+                                best[i] = 4e30f;
+                                continue;
+                            }
+                        }
+                    }
+                    best[i] = std::min(best[i], ms);
+                }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (yref) dev_free(c, yref, ny * 4);
+            if (ndiff) dev_free(c, ndiff, 256);
+            size_t bi = 0;
+            for (size_t i = 1; i < cand.size(); ++i)
+                if (best[i] < best[bi]) bi = i;
+            plan.cs = cand[bi];
+            T.cs_choice[cs_key] = plan.cs;
+            if (t->tuning) {
+                char line[256];
+                int n = snprintf(line, sizeof line, "dense_gemm<%d> cells=%d rows=%d: cluster %d (", bn, cells, mrows,
+                                 plan.cs);
+                for (size_t i = 0; i < cand.size() && n < (int)sizeof line; ++i)
+                    n += best[i] < 1e29f ? snprintf(line + n, sizeof line - n, "%scluster %d %.1f us", i ? ", " : "",
+                                                    cand[i], 1000.0f * best[i])
+                                         : snprintf(line + n, sizeof line - n, "%scluster %d %s", i ? ", " : "", cand[i],
+                                                    best[i] >= 5e30f   ? "wait expired"
+                                                    : best[i] >= 4e30f ? "differed"
+                                                                       : "did not launch");
+                if (n < (int)sizeof line) snprintf(line + n, sizeof line - n, ")");
+                std::lock_guard<std::mutex> lk2(t->tuning->mu);
+                t->tuning->log.push_back(line);
+            }
+        }
+    }
+    {
+        if (timed) cudaEventRecord(ev[0], s);
+        const cudaError_t ge = gemm(plan.cs > 0 ? plan.cs : 1, true);
+        if (ge != cudaSuccess) return cuda_status(c, ge, "dense operator GEMM launch");
     }
     if (timed) cudaEventRecord(ev[1], s);
     {  // L+ h (L h when asked for) and, with G, the SIS L-moments in one pass
@@ -962,6 +1164,7 @@ void tc_release(Ctx* c, DevTables* t) {
     for (auto& kv : t->tc->ws) arena_release(c, kv.second);
     for (auto& kv : t->tc->plans) {
         dev_free(c, kv.second.work, kv.second.nwork * sizeof(GemmWork));
+        dev_free(c, kv.second.work_t, kv.second.nwork * sizeof(GemmWork));
         if (kv.second.fix) dev_free(c, kv.second.fix, kv.second.nfix * sizeof(GemmFix));
     }
     dev_free(c, t->tc->err_dev, 256);
