@@ -245,8 +245,11 @@ lbe_status lbe_fourier_omega(lbe_ctx* ctx, int nv, double vmax, int M, double R,
  * stopping test, so a solve stopped after k iterations and resumed here continues exactly
  * as the uninterrupted solve would -- the iterates, flow rates and stopping decision are
  * bitwise those of the uninterrupted run.  With prev = NULL the first change is measured
- * against the flow rates of h_in computed afresh.  LBE_FP64 and LBE_FP32 only (FP32 data are
- * rounded from h_in).  Outputs as for lbe_solve; out->iters counts this call's iterations. */
+ * against the flow rates of h_in computed afresh.  LBE_FP64, LBE_FP32 and LBE_BF16 (FP32 data
+ * are rounded from h_in; LBE_BF16 plates keep one value per orbit of the v2 and v3 reflections,
+ * taken from h_in at v2 < 0, v3 < 0).  The refined precisions are rejected (LBE_BAD_ARG): their
+ * state also holds the FP64 base point of the defect correction.  Outputs as for lbe_solve;
+ * out->iters counts this call's iterations. */
 lbe_status lbe_solve_from(lbe_ctx* ctx, const lbe_problem* pb, const double* h_in, const lbe_result* prev,
                           lbe_result* out, double* U3_out, double* h_out);
 

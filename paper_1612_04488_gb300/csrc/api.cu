@@ -519,7 +519,8 @@ void batch_iterate(Batch& B, bool upload, bool read) {
             // L+ h and the L-moments in one pass; L h itself is not stored
             const lbe_status ts = tc_apply_sym(B.c, B.t, mode, nc, B.delta.as<double>() + c0, (const float*)(h + c0 * n3),
                                                (float*)(lp + c0 * n3), nullptr, s, false, B.nd.as<double>() + c0,
-                                               B.G.as<double>() + c0 * 2, B.hmom.as<double>() + c0 * 2);
+                                               B.G.as<double>() + c0 * 2, B.hmom.as<double>() + c0 * 2,
+                                               B.quarter() && sp.dim == 1);
             if (ts != LBE_OK && B.op_status == LBE_OK) B.op_status = ts;
             continue;
         } else {
@@ -548,20 +549,24 @@ void batch_iterate(Batch& B, bool upload, bool read) {
         for (int j : act2) c2 += B.sj[j].ncell;
         cudaEvent_t ev[2];
         bool tm = !act1.empty() && sweep_timing_begin(s, ev);
-        launch_sweep<T>(t, 1, (int)act1.size(), mc1, lp, hh, B.sjobs.as<SweepJobDev>(), dact, B.coef.as<double>(), s);
-        if (tm) sweep_timing_end(s, ev, 2.0 * sizeof(T) * (double)c1 * n3);
+        const int q1 = B.quarter() ? 1 : 0;  // plates in the orbit layout: a quarter of each cell
+        launch_sweep<T>(t, 1, (int)act1.size(), mc1, lp, hh, B.sjobs.as<SweepJobDev>(), dact, B.coef.as<double>(), s,
+                        q1);
+        if (tm) sweep_timing_end(s, ev, 2.0 * sizeof(T) * (double)c1 * (q1 ? n3 / 4 : n3));
         tm = !act2.empty() && sweep_timing_begin(s, ev);
         launch_sweep<T>(t, 2, (int)act2.size(), mc2, lp, hh, B.sjobs.as<SweepJobDev>(), dact + act1.size(),
                         B.coef.as<double>(), s);
         if (tm) sweep_timing_end(s, ev, 2.0 * sizeof(T) * (double)c2 * n3);
     }
-    for (auto& sp : spans) launch_moments<T>(t, sp.c0, (int)sp.n, hh, B.mom.as<double>(), s);
+    for (auto& sp : spans)
+        launch_moments<T>(t, sp.c0, (int)sp.n, hh, B.mom.as<double>(), s, B.quarter() && sp.dim == 1);
     launch_sis_update(t, na, B.ijobs.as<SisJobDev>(), dact, B.mom.as<double>(), B.G.as<double>(),
                       B.coef.as<double>(), B.work.as<double>(), B.dU.as<double>(), B.U3.as<double>(),
                       B.states.as<JobState>(), s);
     launch_correct<T>(t, na, hh, h, B.dU.as<double>(), B.extra.p ? B.extra.as<T>() : nullptr,
                       B.sjobs.as<SweepJobDev>(), dact, s, B.states.as<JobState>(),
-                      (sizeof(T) == 4 && B.use_tc) ? B.hmom.as<double>() : nullptr, B.nd.as<double>());
+                      (sizeof(T) == 4 && B.use_tc) ? B.hmom.as<double>() : nullptr, B.nd.as<double>(),
+                      B.quarter() ? 1 : 0);
     if (read) {
         cudaMemcpyAsync(B.hstate.data(), B.states.p, B.njobs * sizeof(JobState), cudaMemcpyDeviceToHost, s);
         g_d2h += B.njobs * sizeof(JobState);
@@ -796,6 +801,31 @@ int lbe_problem_cells(const lbe_problem* pb) {
     return pb->geom.dim == 1 ? pb->geom.ns + 1 : pb->geom.nx * pb->geom.ny;
 }
 
+// Host conversion between the full velocity grid and the orbit layout (sweep.h) of `cells`
+// cells: pack keeps the orbit representatives (i2, i3 < nv / 2), unpack restores the R2 and R3
+// images (even in v2, odd in v3).
+static void orbit_pack(int nv, long cells, const double* full, float* q) {
+    const int H = nv / 2;
+    const long n3 = (long)nv * nv * nv;
+    for (long c = 0; c < cells; ++c)
+        for (int i1 = 0; i1 < nv; ++i1)
+            for (int j2 = 0; j2 < H; ++j2)
+                for (int j3 = 0; j3 < H; ++j3)
+                    q[c * n3 + ((long)i1 * H + j2) * H + j3] = (float)full[c * n3 + ((long)i1 * nv + j2) * nv + j3];
+}
+static void orbit_unpack(int nv, long cells, const float* q, double* full) {
+    const int H = nv / 2;
+    const long n3 = (long)nv * nv * nv;
+    for (long c = 0; c < cells; ++c)
+        for (int i1 = 0; i1 < nv; ++i1)
+            for (int i2 = 0; i2 < nv; ++i2)
+                for (int i3 = 0; i3 < nv; ++i3) {
+                    const int j2 = i2 < H ? i2 : nv - 1 - i2, j3 = i3 < H ? i3 : nv - 1 - i3;
+                    const double v = q[c * n3 + ((long)i1 * H + j2) * H + j3];
+                    full[c * n3 + ((long)i1 * nv + i2) * nv + i3] = i3 < H ? v : -v;
+                }
+}
+
 static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_result* outs,
                                 double* U3_out, double* h_out, const double* h_in = nullptr,
                                 const lbe_result* prev = nullptr) {
@@ -830,12 +860,20 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
                              "h_in copy");
         } else {
             std::vector<float> tmp(h_in, h_in + nn);
+            if (B.quarter() && B.geo[0].dim == 1) orbit_pack(pbs[0].nv, B.cells, h_in, tmp.data());
             st = cuda_status(ctx, cudaMemcpyAsync(B.h.p, tmp.data(), nn * 4, cudaMemcpyHostToDevice, ctx->stream),
                              "h_in copy");
             if (st == LBE_OK) st = cuda_status(ctx, cudaStreamSynchronize(ctx->stream), "h_in copy");
         }
         g_h2d += nn * (B.prec == LBE_FP64 ? 8 : 4);
         if (st != LBE_OK) return st;
+        if (B.use_tc) {  // the h part of the L-moments, which the correction step keeps per cell
+            int zero = 0;
+            cudaMemcpyAsync(B.act.p, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+            launch_correct<float>(*B.t, 1, nullptr, B.h.as<float>(), nullptr, nullptr, B.sjobs.as<SweepJobDev>(),
+                                  B.act.as<int>(), ctx->stream, nullptr, B.hmom.as<double>(), B.nd.as<double>(),
+                                  B.quarter() ? 1 : 0);
+        }
         if (prev) {  // the flow rates the interrupted run held
             B.hstate[0].M = prev->mass_flow;
             B.hstate[0].Q = prev->heat_flow;
@@ -847,7 +885,8 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
             if (B.prec == LBE_FP64)
                 launch_moments<double>(*B.t, 0, (int)B.cells, B.h.as<double>(), B.mom.as<double>(), ctx->stream);
             else
-                launch_moments<float>(*B.t, 0, (int)B.cells, B.h.as<float>(), B.mom.as<double>(), ctx->stream);
+                launch_moments<float>(*B.t, 0, (int)B.cells, B.h.as<float>(), B.mom.as<double>(), ctx->stream,
+                                      B.quarter() && B.geo[0].dim == 1);
             launch_set_rates(1, B.ijobs.as<SisJobDev>(), B.act.as<int>(), B.mom.as<double>(), B.coef.as<double>(),
                              B.states.as<JobState>(), ctx->stream);
         }
@@ -874,6 +913,11 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
             std::vector<float> tmp(B.cells * n3);
             st = cuda_status(ctx, cudaMemcpy(tmp.data(), B.h.p, tmp.size() * 4, cudaMemcpyDeviceToHost), "h copy");
             for (size_t i = 0; i < tmp.size(); ++i) h_out[i] = tmp[i];
+            if (B.quarter())
+                for (int j = 0; j < n; ++j)
+                    if (B.geo[j].dim == 1)
+                        orbit_unpack(pbs[0].nv, B.sj[j].ncell, tmp.data() + B.cell_off[j] * n3,
+                                     h_out + B.cell_off[j] * n3);
         }
     }
     return st != LBE_OK ? st : worst;
@@ -890,8 +934,8 @@ lbe_status lbe_solve_batch(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_resu
 lbe_status lbe_solve_from(lbe_ctx* ctx, const lbe_problem* pb, const double* h_in, const lbe_result* prev,
                           lbe_result* out, double* U3_out, double* h_out) {
     if (!ctx || !pb || !h_in || !out) return bad_arg(ctx, "null argument");
-    if (pb->precision != LBE_FP64 && pb->precision != LBE_FP32)
-        return bad_arg(ctx, "lbe_solve_from takes LBE_FP64 or LBE_FP32");
+    if (pb->precision != LBE_FP64 && pb->precision != LBE_FP32 && pb->precision != LBE_BF16)
+        return bad_arg(ctx, "lbe_solve_from takes LBE_FP64, LBE_FP32 or LBE_BF16");
     if (prev && (!std::isfinite(prev->mass_flow) || !std::isfinite(prev->heat_flow)))
         return bad_arg(ctx, "prev flow rates must be finite");
     return lbe_solve_batch_impl(ctx, pb, 1, out, U3_out, h_out, h_in, prev);

@@ -46,6 +46,9 @@ struct Batch {
     void* inc_scratch = nullptr;
     int inc_chunk = 1;
     bool use_tc = false;  // FP32 batches: collision operator by the dense tensor-core GEMM
+    // plates (1D problems) of a tensor-core batch keep h, the operator output and the sweep
+    // output in the orbit layout (sweep.h): a quarter of each cell's velocity points
+    bool quarter() const { return use_tc; }
     bool inc_tc = false;  // FP64 batches in increment mode: the increment's operator by that GEMM
     lbe_status op_status = LBE_OK;  // first failure of an operator launch inside an iteration
     int chunk = 1;
@@ -89,5 +92,9 @@ void range_residual(const double* h, const double* h_old, float* r, long n, cuda
 void range_correct(const double* h_old, const float* e, double* h, long n, cudaStream_t s);
 void range_sub_f32(const double* h, const double* base, float* out, long n, cudaStream_t s);
 void range_add_f64(const double* base, const float* inc, double* out, long n, cudaStream_t s);
+// the same steps for `cells` plate cells whose FP32 side is in the orbit layout (sweep.h)
+void range_widen_q(const float* e, double* h, long cells, int nv, cudaStream_t s);
+void range_correct_q(const double* h_old, const float* e, double* h, long cells, int nv, cudaStream_t s);
+void range_residual_q(const double* h, const double* h_old, float* r, long cells, int nv, cudaStream_t s);
 
 }  // namespace lbe

@@ -397,10 +397,14 @@ __host__ __device__ inline bool blk_neg(int b, int mode, bool m1, bool m2, bool 
 // halves: (x_b(a, b) +- x_b(b, a)) / 2.  Each thread takes one unordered pair a <= b of (j1, j2)
 // and two neighbouring j3 (H is even): float2 loads of both orders' orbit points, bf16x2
 // stores.  A second loop writes the padding columns of every sub-block as zero.
+// quarter (plates): h in the orbit layout, where the points read (i2, i3 < nv / 2) are stored
+// at (i1 nv / 2 + i2) nv / 2 + i3.
 template <int NV, int MODE>
 __global__ void __launch_bounds__(256) k_gather_sub(const float* __restrict__ h, __nv_bfloat162* __restrict__ xh,
-                                                    __nv_bfloat162* __restrict__ xl, int cells, int cpad) {
+                                                    __nv_bfloat162* __restrict__ xl, int cells, int cpad,
+                                                    int quarter) {
     constexpr int H = NV / 2, NBLK = MODE == 2 ? 2 : 4, NPAIR = H * (H + 1) / 2;
+    const int rs = MODE == 2 && quarter ? H : NV;  // row length and rows per plane of the data
     constexpr SubLayout L = sub_layout(NV, MODE);
     constexpr long N3 = (long)NV * NV * NV;
     const long total = (long)cells * NPAIR * (H / 2);
@@ -423,8 +427,8 @@ __global__ void __launch_bounds__(256) k_gather_sub(const float* __restrict__ h,
 #pragma unroll
         for (int o = 0; o < 2; ++o) {
             const int j1 = o ? bb : aa, j2 = o ? aa : bb;
-            const float2 p0 = *reinterpret_cast<const float2*>(hc + (j1 * NV + j2) * NV + j3);
-            const float2 p1 = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * NV + j2) * NV + j3);
+            const float2 p0 = *reinterpret_cast<const float2*>(hc + (j1 * rs + j2) * rs + j3);
+            const float2 p1 = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * rs + j2) * rs + j3);
             if constexpr (MODE == 2) {
                 x[o][0] = make_float2(0.5f * (p0.x + p1.x), 0.5f * (p0.y + p1.y));
                 x[o][1] = make_float2(0.5f * (p0.x - p1.x), 0.5f * (p0.y - p1.y));
@@ -570,9 +574,74 @@ __global__ void __launch_bounds__(8 * NV) k_expand_sub(const float* __restrict__
     }
 }
 
+// The plate expand in the orbit layout: L+ h at the stored quarter only (i2, i3 < nv / 2, where
+// the R2 and R3 signs are +1), and G_1 = 2 sum_v v1 v3 L+ h dv^3 + hm_1 as four times the
+// quarter's sum (v1 v3 L+ h is even under R2 and R3); G_2's summand is odd under R2, so
+// G_2 = hm_2.  The per-point arithmetic is that of k_expand_sub.
+template <int NV>
+__global__ void __launch_bounds__(8 * NV) k_expand_q(const float* __restrict__ Y, const float* __restrict__ vel,
+                                                     const double* __restrict__ delta, float* __restrict__ Lplus,
+                                                     double* __restrict__ G, double dv3,
+                                                     const double* __restrict__ hm) {
+    extern __shared__ float sY[];
+    __shared__ dfloat redx[32 * 2];
+    constexpr int H = NV / 2;
+    constexpr SubLayout L = sub_layout(NV, 2);  // S0, A0 (block 0), F1 (block 1)
+    constexpr long n3 = (long)NV * NV * NV;
+    const long c = blockIdx.x;
+    const float* yc = Y + c * (long)L.rows;
+#pragma unroll
+    for (int q = 0; q < L.count; ++q)
+        for (int k = threadIdx.x; k < L.n[q]; k += blockDim.x) sY[L.soff[q] + k] = yc[L.roff[q] + k];
+    __syncthreads();
+    const float d = (float)delta[c];
+    float a0 = 0.f, c0 = 0.f;  // compensated sum of v1 v3 L+ h
+    for (int p = threadIdx.x; p < NV * H * H; p += blockDim.x) {
+        const int i1 = p / (H * H), j2 = (p / H) % H, j3 = p % H;
+        const bool m1 = i1 >= H;
+        const int j1 = m1 ? NV - 1 - i1 : i1;
+        const int aa = j1 <= j2 ? j1 : j2, bb = j1 <= j2 ? j2 : j1;
+        float y0 = sY[L.soff[0] + ts_idx(aa, bb) * H + j3];
+        if (aa != bb) {
+            const float ya = sY[L.soff[1] + ta_idx(aa, bb) * H + j3];
+            y0 += j1 < j2 ? ya : -ya;
+        }
+        const float y1 = sY[L.soff[2] + (j1 * H + j2) * H + j3];
+        const float lp = d * (m1 ? y0 - y1 : y0 + y1);
+        Lplus[c * n3 + p] = lp;
+        if (G) {
+            const float t = lp * vel[j3];
+            const float x = vel[i1] * t - c0;
+            const float u = a0 + x;
+            c0 = (u - a0) - x;
+            a0 = u;
+        }
+    }
+    if (!G) return;
+    dfloat sm[2] = {df_fast2sum(a0, -c0), dfloat(0)};
+    block_reduce_df<2>(sm, redx);
+    if (threadIdx.x == 0) {
+        G[2 * c + 0] = 8.0 * (double)sm[0] * dv3 + hm[2 * c + 0];
+        G[2 * c + 1] = hm[2 * c + 1];
+    }
+}
+
 template <int NV, int MODE>
-void launch_gather(int cells, int cpad, const float* h, __nv_bfloat162* xh, __nv_bfloat162* xl, cudaStream_t s) {
-    k_gather_sub<NV, MODE><<<8 * sm_count(), 256, 0, s>>>(h, xh, xl, cells, cpad);
+void launch_gather(int cells, int cpad, const float* h, __nv_bfloat162* xh, __nv_bfloat162* xl, cudaStream_t s,
+                   int quarter) {
+    k_gather_sub<NV, MODE><<<8 * sm_count(), 256, 0, s>>>(h, xh, xl, cells, cpad, quarter);
+}
+
+template <int NV>
+void launch_expand_q(int cells, const float* Y, const float* vel, const double* delta, float* Lplus, double* G,
+                     double dv3, const double* hm, cudaStream_t s) {
+    static std::once_flag once;
+    constexpr int H = NV / 2;
+    const int smem = 2 * H * H * H * 4;
+    std::call_once(once, [smem] {
+        cudaFuncSetAttribute(k_expand_q<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+    k_expand_q<NV><<<cells, 8 * NV, smem, s>>>(Y, vel, delta, Lplus, G, dv3, hm);
 }
 
 template <int NV, int MODE>
@@ -934,8 +1003,10 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
 // sync = false leaves the stream running: the GEMM's failure word is copied to pinned host
 // memory behind it and tc_check reads it after the caller's own synchronisation.
 lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h, float* Lplus,
-                        float* Lout, cudaStream_t s, bool sync, const double* nd, double* G, const double* hm) {
+                        float* Lout, cudaStream_t s, bool sync, const double* nd, double* G, const double* hm,
+                        bool quarter) {
     if (mode != 1 && mode != 2) return LBE_BAD_ARG;
+    if (quarter && (mode != 2 || Lout || (G && !hm))) return LBE_BAD_ARG;
     if (cells <= 0) return LBE_OK;
     if (!t->tc) t->tc = new TcOperands();
     TcOperands& T = *t->tc;
@@ -998,12 +1069,12 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         auto* xh2 = reinterpret_cast<__nv_bfloat162*>(xh);
         auto* xl2 = reinterpret_cast<__nv_bfloat162*>(xl);
         const bool p2 = mode == 2;
-        const int cp = (int)cpad;
+        const int cp = (int)cpad, qf = quarter ? 1 : 0;
         switch (nv) {
-            case 8: (p2 ? launch_gather<8, 2> : launch_gather<8, 1>)(cells, cp, h, xh2, xl2, s); break;
-            case 16: (p2 ? launch_gather<16, 2> : launch_gather<16, 1>)(cells, cp, h, xh2, xl2, s); break;
-            case 24: (p2 ? launch_gather<24, 2> : launch_gather<24, 1>)(cells, cp, h, xh2, xl2, s); break;
-            default: (p2 ? launch_gather<32, 2> : launch_gather<32, 1>)(cells, cp, h, xh2, xl2, s); break;
+            case 8: (p2 ? launch_gather<8, 2> : launch_gather<8, 1>)(cells, cp, h, xh2, xl2, s, qf); break;
+            case 16: (p2 ? launch_gather<16, 2> : launch_gather<16, 1>)(cells, cp, h, xh2, xl2, s, qf); break;
+            case 24: (p2 ? launch_gather<24, 2> : launch_gather<24, 1>)(cells, cp, h, xh2, xl2, s, qf); break;
+            default: (p2 ? launch_gather<32, 2> : launch_gather<32, 1>)(cells, cp, h, xh2, xl2, s, qf); break;
         }
     }
     // optional event timing of the GEMM alone (public synchronous calls only)
@@ -1125,7 +1196,13 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         const float* vel = t->vel_f;
         const double dv3 = t->dv * t->dv * t->dv;
         const bool p2 = mode == 2;
-        switch (nv) {
+        if (quarter) switch (nv) {
+                case 8: launch_expand_q<8>(cells, Y, vel, delta, Lplus, G, dv3, hm, s); break;
+                case 16: launch_expand_q<16>(cells, Y, vel, delta, Lplus, G, dv3, hm, s); break;
+                case 24: launch_expand_q<24>(cells, Y, vel, delta, Lplus, G, dv3, hm, s); break;
+                default: launch_expand_q<32>(cells, Y, vel, delta, Lplus, G, dv3, hm, s); break;
+            }
+        else switch (nv) {
             case 8: (p2 ? launch_expand<8, 2> : launch_expand<8, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, hm, s); break;
             case 16: (p2 ? launch_expand<16, 2> : launch_expand<16, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, hm, s); break;
             case 24: (p2 ? launch_expand<24, 2> : launch_expand<24, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, hm, s); break;

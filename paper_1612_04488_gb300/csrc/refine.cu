@@ -31,6 +31,67 @@ namespace lbe {
 
 namespace {
 
+// Orbit layout (sweep.h) index of the full-grid point f of a cell, and whether the point is the
+// R3 image (negated); and the full-grid index of the representative of orbit q.
+__device__ __forceinline__ long orbit_of(long f, int nv, bool* neg) {
+    const int H = nv / 2;
+    const int i3 = (int)(f % nv), i2 = (int)((f / nv) % nv), i1 = (int)(f / ((long)nv * nv));
+    *neg = i3 >= H;
+    const int j2 = i2 < H ? i2 : nv - 1 - i2, j3 = i3 < H ? i3 : nv - 1 - i3;
+    return ((long)i1 * H + j2) * H + j3;
+}
+__device__ __forceinline__ long full_of(long q, int nv) {
+    const int H = nv / 2;
+    const int j3 = (int)(q % H), j2 = (int)((q / H) % H), i1 = (int)(q / ((long)H * H));
+    return ((long)i1 * nv + j2) * nv + j3;
+}
+
+}  // namespace
+
+// The element-wise steps between the FP64 iterate and the FP32 correction of a range of cells
+// whose FP32 side is in the orbit layout (plates of a tensor-core batch).
+__global__ void k_range_widen_q(const float* __restrict__ e, double* __restrict__ h, long cells, int nv) {
+    const long n3 = (long)nv * nv * nv, n = cells * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const long f = k % n3;
+        bool neg;
+        const double v = (double)e[k - f + orbit_of(f, nv, &neg)];
+        h[k] = neg ? -v : v;
+    }
+}
+__global__ void k_range_correct_q(const double* __restrict__ h_old, const float* __restrict__ e,
+                                  double* __restrict__ h, long cells, int nv) {
+    const long n3 = (long)nv * nv * nv, n = cells * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const long f = k % n3;
+        bool neg;
+        const double v = (double)e[k - f + orbit_of(f, nv, &neg)];
+        h[k] = h_old[k] + (neg ? -v : v);
+    }
+}
+__global__ void k_range_residual_q(const double* __restrict__ h, const double* __restrict__ h_old,
+                                   float* __restrict__ r, long cells, int nv) {
+    const long n3 = (long)nv * nv * nv, nq = n3 / 4, n = cells * nq;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const long c = k / nq, q = k % nq, f = c * n3 + full_of(q, nv);
+        r[c * n3 + q] = (float)(h[f] - h_old[f]);
+    }
+}
+void range_widen_q(const float* e, double* h, long cells, int nv, cudaStream_t s) {
+    g_launches += 1;
+    k_range_widen_q<<<sm_count(), 256, 0, s>>>(e, h, cells, nv);
+}
+void range_correct_q(const double* h_old, const float* e, double* h, long cells, int nv, cudaStream_t s) {
+    g_launches += 1;
+    k_range_correct_q<<<sm_count(), 256, 0, s>>>(h_old, e, h, cells, nv);
+}
+void range_residual_q(const double* h, const double* h_old, float* r, long cells, int nv, cudaStream_t s) {
+    g_launches += 1;
+    k_range_residual_q<<<sm_count(), 256, 0, s>>>(h, h_old, r, cells, nv);
+}
+
+namespace {
+
 // dst = src over the cells of the active jobs
 __global__ void k_copy64(const double* __restrict__ src, double* __restrict__ dst,
                          const SweepJobDev* __restrict__ jobs, const int* __restrict__ active, long n3) {
@@ -40,32 +101,63 @@ __global__ void k_copy64(const double* __restrict__ src, double* __restrict__ ds
         dst[base + k] = src[base + k];
 }
 
-// r = (float)(h - h_old)
+// r = (float)(h - h_old); r of a plate in the orbit layout when quarter (h is exactly even in
+// v2 and odd in v3: the FP64 correction step projects onto that subspace)
 __global__ void k_residual(const double* __restrict__ h, const double* __restrict__ h_old, float* __restrict__ r,
-                           const SweepJobDev* __restrict__ jobs, const int* __restrict__ active, long n3) {
+                           const SweepJobDev* __restrict__ jobs, const int* __restrict__ active, int nv,
+                           int quarter) {
     const SweepJobDev jb = jobs[active[blockIdx.y]];
-    const long total = (long)jb.ncell * n3, base = jb.cell_off * n3;
+    const long n3 = (long)nv * nv * nv, base = jb.cell_off * n3;
+    if (quarter && jb.ny == 0) {
+        const long nq = n3 / 4, total = (long)jb.ncell * nq;
+        for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
+            const long c = k / nq, q = k % nq, f = base + c * n3 + full_of(q, nv);
+            r[base + c * n3 + q] = (float)(h[f] - h_old[f]);
+        }
+        return;
+    }
+    const long total = (long)jb.ncell * n3;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x)
         r[base + k] = (float)(h[base + k] - h_old[base + k]);
 }
 
-// h = h_old + e
+// h = h_old + e (e of a plate in the orbit layout when quarter)
 __global__ void k_apply_correction(const double* __restrict__ h_old, const float* __restrict__ e,
                                    double* __restrict__ h, const SweepJobDev* __restrict__ jobs,
-                                   const int* __restrict__ active, long n3) {
+                                   const int* __restrict__ active, int nv, int quarter) {
     const SweepJobDev jb = jobs[active[blockIdx.y]];
-    const long total = (long)jb.ncell * n3, base = jb.cell_off * n3;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x)
-        h[base + k] = h_old[base + k] + (double)e[base + k];
+    const long n3 = (long)nv * nv * nv, total = (long)jb.ncell * n3, base = jb.cell_off * n3;
+    const bool q = quarter && jb.ny == 0;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
+        double v;
+        if (q) {
+            const long f = k % n3;
+            bool neg;
+            v = (double)e[base + k - f + orbit_of(f, nv, &neg)];
+            if (neg) v = -v;
+        } else {
+            v = (double)e[base + k];
+        }
+        h[base + k] = h_old[base + k] + v;
+    }
 }
 
-// h = (double)e
+// h = (double)e (e of a plate in the orbit layout when quarter)
 __global__ void k_widen(const float* __restrict__ e, double* __restrict__ h, const SweepJobDev* __restrict__ jobs,
-                        const int* __restrict__ active, long n3) {
+                        const int* __restrict__ active, int nv, int quarter) {
     const SweepJobDev jb = jobs[active[blockIdx.y]];
-    const long total = (long)jb.ncell * n3, base = jb.cell_off * n3;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x)
-        h[base + k] = (double)e[base + k];
+    const long n3 = (long)nv * nv * nv, total = (long)jb.ncell * n3, base = jb.cell_off * n3;
+    const bool q = quarter && jb.ny == 0;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
+        if (q) {
+            const long f = k % n3;
+            bool neg;
+            const double v = (double)e[base + k - f + orbit_of(f, nv, &neg)];
+            h[base + k] = neg ? -v : v;
+        } else {
+            h[base + k] = (double)e[base + k];
+        }
+    }
 }
 
 // state M, Q := flow rates of the moments in mom (so the next iteration measures its change
@@ -218,7 +310,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         for (int j = 0; j < n; ++j) inner_it[j] += I.hstate[j].iters;
         cudaMemcpyAsync(O.act.p, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, s);
         k_widen<<<dim3(sm_count(), n), blk, 0, s>>>(I.h.as<float>(), O.h.as<double>(), O.sjobs.as<SweepJobDev>(),
-                                             O.act.as<int>(), n3);
+                                                   O.act.as<int>(), pbs[0].nv, I.quarter() ? 1 : 0);
         g_launches += 1;
         // from now on the inner batch solves the homogeneous correction equation
         for (int j = 0; j < n; ++j) {
@@ -337,7 +429,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             const int nk = (int)corr.size();
             cudaMemcpyAsync(O.act.p, corr.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s);
             k_residual<<<dim3(sm_count(), nk), blk, 0, s>>>(O.h.as<double>(), h_old, r, O.sjobs.as<SweepJobDev>(),
-                                                     O.act.as<int>(), n3);
+                                                           O.act.as<int>(), pbs[0].nv, I.quarter() ? 1 : 0);
             g_launches += 1;
             for (int j : corr) {
                 cudaMemsetAsync(I.h.as<float>() + I.cell_off[j] * n3, 0, I.sj[j].ncell * n3 * 4, s);
@@ -357,7 +449,8 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             }
             cudaMemcpyAsync(O.act.p, corr.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s);
             k_apply_correction<<<dim3(sm_count(), nk), blk, 0, s>>>(h_old, I.h.as<float>(), O.h.as<double>(),
-                                                             O.sjobs.as<SweepJobDev>(), O.act.as<int>(), n3);
+                                                                   O.sjobs.as<SweepJobDev>(), O.act.as<int>(),
+                                                                   pbs[0].nv, I.quarter() ? 1 : 0);
             g_launches += 1;
             for (int j : corr) {
                 if (!rebase[j]) continue;

@@ -512,8 +512,14 @@ static void service_main(Ctx* c) {
                     double* hold = D->aux.as<double>() + D->B.cell_off[sj->ds] * n3;
                     const float* e = F->B.h.as<float>() + F->B.cell_off[sj->fs] * n3;
                     cudaStream_t ds = D->stream;
+                    // plates of a tensor-core bucket: e in the orbit layout
+                    const bool q = F->B.quarter() && F->B.geo[sj->fs].dim == 1;
+                    const long nc = F->B.sj[sj->fs].ncell;
                     if (sj->phase == 1) {
-                        range_widen(e, h, n, ds);
+                        if (q)
+                            range_widen_q(e, h, nc, F->nv, ds);
+                        else
+                            range_widen(e, h, n, ds);
                         // the request's one FP64 collision-operator evaluation, at h0
                         const long o = D->B.cell_off[sj->ds] * n3;
                         range_copy(h, D->base_h.as<double>() + o, n, ds);
@@ -528,7 +534,10 @@ static void service_main(Ctx* c) {
                         cudaMemcpyAsync(D->B.states.as<JobState>() + sj->ds, &D->B.hstate[sj->ds], sizeof(JobState),
                                         cudaMemcpyHostToDevice, ds);
                     } else {
-                        range_correct(hold, e, h, n, ds);
+                        if (q)
+                            range_correct_q(hold, e, h, nc, F->nv, ds);
+                        else
+                            range_correct(hold, e, h, n, ds);
                         ++sj->refs;
                         // flow rates of the corrected h for the next change test
                         launch_moments<double>(*D->B.t, D->B.cell_off[sj->ds], D->B.sj[sj->ds].ncell,
@@ -557,7 +566,10 @@ static void service_main(Ctx* c) {
                     const double* h = D->B.h.as<double>() + D->B.cell_off[sj->ds] * n3;
                     const double* hold = D->aux.as<double>() + D->B.cell_off[sj->ds] * n3;
                     float* r = F->aux.as<float>() + F->B.cell_off[sj->fs] * n3;
-                    range_residual(h, hold, r, n, D->stream);
+                    if (F->B.quarter() && F->B.geo[sj->fs].dim == 1)
+                        range_residual_q(h, hold, r, D->B.sj[sj->ds].ncell, F->nv, D->stream);
+                    else
+                        range_residual(h, hold, r, n, D->stream);
                     cudaStreamSynchronize(D->stream);
                     slot_set_correction(*F, sj->fs);
                     cudaStreamSynchronize(F->stream);

@@ -126,7 +126,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 //   SCHED 1  a register ring: the right-hand sides of the next RING nodes are in flight while a
 //            node is solved, no shared memory beyond the coefficients, so the SM holds as many
 //            threads as the registers allow;
-//   SCHED 2  (float; n2 a multiple of 128) a ring of node rows in shared memory filled by the
+//   SCHED 2  (float; W a multiple of 128) a ring of node rows in shared memory filled by the
 //            bulk-copy (TMA) engine, 512 bytes per node and column, one mbarrier per half ring:
 //            up to 32 nodes in flight per block at 16 KB of shared memory.
 // The march coefficients [fa|fb|fc|ba|bb|bc] (n each) are converted to T once per block into
@@ -139,10 +139,14 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
                                                  const T* __restrict__ feq,
                                                  const SweepJobDev* __restrict__ jobs,
                                                  const int* __restrict__ active,
-                                                 const double* __restrict__ coef, int nv, int staged) {
+                                                 const double* __restrict__ coef, int nv, int staged,
+                                                 int quarter) {
     extern __shared__ __align__(16) unsigned char sweep_smem[];
     const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
     const int half = nv / 2, n2 = nv * nv;
+    // velocities per i1 plane of the data: the whole plane, or in the orbit layout the quarter
+    // (j2, j3 < nv / 2) that represents it
+    const int W = quarter ? half * half : n2;
     const long n3 = (long)n2 * nv;
     const int n = jb.ncell;
     const double* cg = coef + jb.coef_off;
@@ -153,19 +157,21 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
     }
     auto C = [&](int a, int i) -> T { return staged ? sc[a * n + i] : (T)cg[a * n + i]; };
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= half * n2) return;
-    const int i1p = half + t / n2, rem = t % n2;
-    const int vpos = i1p * n2 + rem, vneg = (nv - 1 - i1p) * n2 + rem;
+    if (t >= half * W) return;
+    const int i1p = half + t / W, rem = t % W;
+    const int vpos = i1p * W + rem, vneg = (nv - 1 - i1p) * W + rem;  // in the data
+    const int i2 = quarter ? rem / half : rem / nv, i3 = quarter ? rem % half : rem % nv;
+    const int fpos = (i1p * nv + i2) * nv + i3, fneg = ((nv - 1 - i1p) * nv + i2) * nv + i3;  // in the tables
     const T* r = rhs + jb.cell_off * n3;
     T* o = h + jb.cell_off * n3;
     const T d = (T)jb.delta;
     const T v1 = vel[i1p];
-    const T nup = d * nu1[vpos];
-    const T w2 = vel[rem / nv], w3 = vel[rem % nv];
-    const T Sp = source<T>(jb.forcing, v1, w2, w3, feq[vpos]);
-    const T Sn = source<T>(jb.forcing, vel[nv - 1 - i1p], w2, w3, feq[vneg]);
+    const T nup = d * nu1[fpos];
+    const T w2 = vel[i2], w3 = vel[i3];
+    const T Sp = source<T>(jb.forcing, v1, w2, w3, feq[fpos]);
+    const T Sn = source<T>(jb.forcing, vel[nv - 1 - i1p], w2, w3, feq[fneg]);
     const T u = -vel[nv - 1 - i1p];
-    const T nun = d * nu1[vneg];
+    const T nun = d * nu1[fneg];
     T hm1 = T(0), hm2 = T(0);
     o[vpos] = T(0);
     if constexpr (SCHED == 0) {
@@ -202,7 +208,7 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
             g1 = hi;
         }
     } else if constexpr (SCHED == 2) {
-        // The block's 128 velocities are contiguous in both columns (n2 is a multiple of 128),
+        // The block's 128 velocities are contiguous in both columns (W is a multiple of 128),
         // so each node is one 512-byte row per column, copied by the bulk-copy engine into a
         // ring of two halves of HR rows in shared memory.  The two columns form one stream of
         // 2 (n - 1) rows: forward nodes 1 .. n-1, then backward nodes n-2 .. 0.  Half k sits
@@ -572,6 +578,44 @@ __global__ void __launch_bounds__(8 * NV) k_moments(const T* __restrict__ h, con
     }
 }
 
+// The same moments of a plate cell in the orbit layout (h[i1][j2][j3], j2, j3 < nv / 2, one
+// value per orbit {1, R2, R3, R2 R3} of the parity odd in v3 and even in v2).  The first four
+// integrands are even under both reflections, so each is four times its sum over the stored
+// quarter; 2 v1 v2 v3 h is odd under R2 and sums to zero.  One thread per (j2, j3), the block
+// rounded up to whole warps.
+template <int NV>
+__global__ void __launch_bounds__(256) k_moments_q(const float* __restrict__ h, const float* __restrict__ vel,
+                                                   double dv3, long cell0, double* __restrict__ mom) {
+    __shared__ dfloat redx[32 * 4];
+    constexpr int H = NV / 2;
+    constexpr long n3 = (long)NV * NV * NV;
+    const long cell = cell0 + blockIdx.x;
+    const int p = threadIdx.x;
+    dfloat s[4] = {dfloat(0), dfloat(0), dfloat(0), dfloat(0)};
+    if (p < H * H) {
+        const int j2 = p / H, j3 = p % H;
+        const float* hc = h + cell * n3 + p;
+        Acc<float> S0, S1;  // sums of h and v1^2 h over i1
+        for (int i1 = 0; i1 < NV; ++i1) {
+            const float v1 = vel[i1], x = hc[(long)i1 * H * H];
+            S0.add(x);
+            S1.add(v1 * v1 * x);
+        }
+        const float v2 = vel[j2];
+        const dfloat a0 = S0.pair(), a2 = S1.pair(), a3 = dfloat(v2 * v2, 0.f) * a0;
+        const dfloat w3(vel[j3], 0.f), w3s = w3 * w3;
+        s[0] = w3 * a0;
+        s[1] = w3 * ((a2 + a3) + (w3s - dfloat(2.5f, 0.f)) * a0);
+        s[2] = w3 * ((a2 + a2) - a0);
+        s[3] = w3 * ((a3 + a3) - a0);
+    }
+    block_reduce_df<4>(s, redx);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 4; ++k) mom[cell * 5 + k] = 4.0 * (double)s[k] * dv3;
+        mom[cell * 5 + 4] = 0.0;
+    }
+}
+
 // 2D Poisson right-hand side of Eq. diffusion_LBE (N-penalised) on the interior cells.
 __device__ double poisson_rhs(const double* mom, const double* G, int i, int j, int ny, double dx,
                               double dy, double ndsig) {
@@ -740,7 +784,9 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
 // density mode, which the diffusion correction does not accelerate and which the discrete
 // operator, conserving mass only to quadrature accuracy, leaves at |lambda| ~ 1 for large
 // delta: seeded at FP32 rounding it would never decay.  One thread per orbit, so the
-// projection moves no extra bytes.
+// projection moves no extra bytes.  quarter: plates in the orbit layout (one value per orbit,
+// at the orbit's index), where the projection is the identity.  hh = NULL: only hm, of the h
+// already stored (a solve resumed from a checkpoint), with the same arithmetic.
 template <typename T>
 __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __restrict__ h,
                                                  const double* __restrict__ dU, const T* __restrict__ extra,
@@ -749,7 +795,7 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
                                                  const int* __restrict__ active, int nv,
                                                  const JobState* __restrict__ state, double* __restrict__ hm,
                                                  const double* __restrict__ nd, const T* __restrict__ nu1,
-                                                 double dv3) {
+                                                 double dv3, int quarter) {
     __shared__ dfloat redx[32 * 2];
     const int jid = active ? active[blockIdx.y] : blockIdx.y;
     if (state && state[jid].skip) return;  // finished before this iteration
@@ -757,10 +803,11 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
     const int n3 = nv * nv * nv, hv = nv / 2;
     const bool plates = jb.ny == 0;  // 1D: orbits {1, R2, R3, R2R3}; 2D: {1, R3}
     const int norb = plates ? n3 / 4 : n3 / 2;
+    const bool only_hm = hh == nullptr;  // hm of the stored h alone (a resumed solve); h unchanged
     for (int c = blockIdx.x; c < jb.ncell; c += gridDim.x) {
         const long g0 = (jb.cell_off + c) * (long)n3;
-        const T d = (T)(2.0 * dU[jb.cell_off + c]);
-        const T* src = hh + g0;
+        const T d = only_hm ? T(0) : (T)(2.0 * dU[jb.cell_off + c]);
+        const T* src = only_hm ? nullptr : hh + g0;
         T* dst = h + g0;
         const T* ex = extra ? extra + g0 : nullptr;
         const float ndc = hm ? (float)nd[jb.cell_off + c] : 0.f, dl = (float)jb.delta;
@@ -783,41 +830,49 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
             }
             const int va = (i1 * nv + i2) * nv + i3;        // v3 < 0 half
             const int vc = (i1 * nv + i2) * nv + nv - 1 - i3;  // R3
-            T xa = src[va], xc = src[vc];
-            if (ex) {
-                xa += ex[va];
-                xc += ex[vc];
-            }
-            if (plates) {
-                const int vb = (i1 * nv + nv - 1 - i2) * nv + i3;           // R2
-                const int vd = (i1 * nv + nv - 1 - i2) * nv + nv - 1 - i3;  // R2 R3
-                T xb = src[vb], xd = src[vd];
-                if (ex) {
-                    xb += ex[vb];
-                    xd += ex[vd];
-                }
-                const T y = (T)0.25 * ((xa + xb) - (xc + xd)) + d * vel[i3] * feq[va];
-                dst[va] = y;
-                dst[vb] = y;
-                dst[vc] = -y;
-                dst[vd] = -y;
-                if (hm) {  // v3 h is the same at the four points; v2 flips sign under R2
-                    const float wa = ndc - dl * (float)nu1[va], wb = ndc - dl * (float)nu1[vb];
-                    const float wc = ndc - dl * (float)nu1[vc], wd = ndc - dl * (float)nu1[vd];
-                    const float t = (float)vel[i3] * (float)y;
-                    kahan(a0, c0, (float)vel[i1] * t * ((wa + wb) + (wc + wd)));
-                    kahan(a1, c1, (float)vel[i2] * t * ((wa - wb) + (wc - wd)));
-                }
+            const int vb = (i1 * nv + nv - 1 - i2) * nv + i3;           // R2 (plates)
+            const int vd = (i1 * nv + nv - 1 - i2) * nv + nv - 1 - i3;  // R2 R3 (plates)
+            T y;
+            if (only_hm) {
+                y = plates && quarter ? dst[r] : dst[va];
+            } else if (plates && quarter) {  // orbit layout: the orbit's one stored value, at index r
+                y = (ex ? src[r] + ex[r] : src[r]) + d * vel[i3] * feq[va];
+                dst[r] = y;
             } else {
-                const T y = (T)0.5 * (xa - xc) + d * vel[i3] * feq[va];
-                dst[va] = y;
-                dst[vc] = -y;
-                if (hm) {
-                    const float w = (ndc - dl * (float)nu1[va]) + (ndc - dl * (float)nu1[vc]);
-                    const float t = (float)vel[i3] * (float)y * w;
-                    kahan(a0, c0, (float)vel[i1] * t);
-                    kahan(a1, c1, (float)vel[i2] * t);
+                T xa = src[va], xc = src[vc];
+                if (ex) {
+                    xa += ex[va];
+                    xc += ex[vc];
                 }
+                if (plates) {
+                    T xb = src[vb], xd = src[vd];
+                    if (ex) {
+                        xb += ex[vb];
+                        xd += ex[vd];
+                    }
+                    y = (T)0.25 * ((xa + xb) - (xc + xd)) + d * vel[i3] * feq[va];
+                    dst[va] = y;
+                    dst[vb] = y;
+                    dst[vc] = -y;
+                    dst[vd] = -y;
+                } else {
+                    y = (T)0.5 * (xa - xc) + d * vel[i3] * feq[va];
+                    dst[va] = y;
+                    dst[vc] = -y;
+                }
+            }
+            if (!hm) continue;
+            if (plates) {  // v3 h is the same at the four points; v2 flips sign under R2
+                const float wa = ndc - dl * (float)nu1[va], wb = ndc - dl * (float)nu1[vb];
+                const float wc = ndc - dl * (float)nu1[vc], wd = ndc - dl * (float)nu1[vd];
+                const float t = (float)vel[i3] * (float)y;
+                kahan(a0, c0, (float)vel[i1] * t * ((wa + wb) + (wc + wd)));
+                kahan(a1, c1, (float)vel[i2] * t * ((wa - wb) + (wc - wd)));
+            } else {
+                const float w = (ndc - dl * (float)nu1[va]) + (ndc - dl * (float)nu1[vc]);
+                const float t = (float)vel[i3] * (float)y * w;
+                kahan(a0, c0, (float)vel[i1] * t);
+                kahan(a1, c1, (float)vel[i2] * t);
             }
         }
         if (hm) {
@@ -836,22 +891,24 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
 template <typename T>
 static void sweep1d_sched(int sched, const DevTables& t, dim3 g, size_t smem_coef, size_t smem_full, int staged,
                           const T* rhs, T* h, const SweepJobDev* jobs, const int* active, const double* coef,
-                          cudaStream_t s) {
+                          cudaStream_t s, int quarter) {
     const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
     if (sched == 0)
-        k_sweep1d<T, 0><<<g, 128, smem_full, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged);
+        k_sweep1d<T, 0><<<g, 128, smem_full, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged,
+                                                   quarter);
     else if (sched == 2)
         k_sweep1d<T, 2><<<g, 128, (smem_coef + 15) / 16 * 16 + 2 * 16 * 128 * sizeof(T) + 16, s>>>(
-            rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged);
+            rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged, quarter);
     else
-        k_sweep1d<T, 1><<<g, 128, smem_coef, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged);
+        k_sweep1d<T, 1><<<g, 128, smem_coef, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged,
+                                                   quarter);
 }
 
 template <typename T>
 void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T* rhs, T* h,
-                  const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s) {
+                  const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s, int quarter) {
     if (njobs <= 0) return;
     // float sweeps stage the coefficients when the largest job's fit in 48 KB
     const size_t sbytes = (size_t)max_coef * sizeof(T);
@@ -860,7 +917,8 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
     g_launches += 1;
     const int nv = t.nv;
     if (dim == 1) {
-        const int nt = nv / 2 * nv * nv;
+        const int W = quarter ? nv / 2 * (nv / 2) : nv * nv;  // velocities per i1 plane of the data
+        const int nt = nv / 2 * W;
         dim3 g((nt + 127) / 128, njobs);
         // 1D float sweeps can also stage every right-hand side of their columns (schedule 0)
         // when that fits in 200 KB; which schedule is faster is measured at first use
@@ -875,7 +933,7 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
             while (jb < njobs) jb *= 2;  // problems and nodes classes: the next power of two
             int nb = 1;
             while (nb < max_coef / 6) nb *= 2;
-            const long long key = ((long long)nv << 40) | ((long long)jb << 20) | nb;
+            const long long key = ((long long)quarter << 50) | ((long long)nv << 40) | ((long long)jb << 20) | nb;
             std::lock_guard<std::mutex> lk(t.tuning->mu);
             auto it = t.tuning->sweep.find(key);
             cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -886,13 +944,13 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
                 sched = 0;
             } else {
                 // every schedule twice, in turn; each writes the same h (same arithmetic).  The
-                // bulk-copy ring needs whole 128-velocity rows per block (nv = 16, 32).
-                const int NS = (nv * nv) % 128 == 0 ? 3 : 2;
+                // bulk-copy ring needs whole 128-velocity rows per block (W a multiple of 128).
+                const int NS = W % 128 == 0 ? 3 : 2;
                 cudaEvent_t ev[7];
                 for (int k = 0; k <= 2 * NS; ++k) cudaEventCreate(&ev[k]);
                 cudaEventRecord(ev[0], s);
                 for (int k = 0; k < 2 * NS; ++k) {
-                    sweep1d_sched<T>(k % NS, t, g, smem, full, staged, rhs, h, jobs, active, coef, s);
+                    sweep1d_sched<T>(k % NS, t, g, smem, full, staged, rhs, h, jobs, active, coef, s, quarter);
                     cudaEventRecord(ev[k + 1], s);
                 }
                 cudaEventSynchronize(ev[2 * NS]);
@@ -908,15 +966,16 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
                 static const char* names[3] = {"staged", "register ring", "bulk-copy ring"};
                 char line[240];
                 snprintf(line, sizeof line,
-                         "sweep1d<float> nv=%d problems<=%d nodes<=%d: %s (staged %.1f us, register ring %.1f us, "
+                         "sweep1d<float>%s nv=%d problems<=%d nodes<=%d: %s (staged %.1f us, register ring %.1f us, "
                          "bulk-copy ring %.1f us)",
-                         nv, jb, nb, names[sched], 1000.0f * best[0], 1000.0f * best[1], 1000.0f * best[2]);
+                         quarter ? " orbit layout" : "", nv, jb, nb, names[sched], 1000.0f * best[0],
+                         1000.0f * best[1], 1000.0f * best[2]);
                 t.tuning->log.push_back(line);
                 g_launches += 2 * NS - 1;
                 return;
             }
         }
-        sweep1d_sched<T>(sched, t, g, smem, full, staged, rhs, h, jobs, active, coef, s);
+        sweep1d_sched<T>(sched, t, g, smem, full, staged, rhs, h, jobs, active, coef, s, quarter);
     } else {
         const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
         const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
@@ -942,11 +1001,23 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
 }
 
 template <typename T>
-void launch_moments(const DevTables& t, long cell0, int cells, const T* h, double* mom, cudaStream_t s) {
+void launch_moments(const DevTables& t, long cell0, int cells, const T* h, double* mom, cudaStream_t s,
+                    int quarter) {
     if (cells <= 0) return;
     g_launches += 1;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
     const double dv3 = t.dv * t.dv * t.dv;
+    if (quarter && sizeof(T) == 4) {
+        const float* hf = (const float*)h;
+        const float* vf = (const float*)vel;
+        switch (t.nv) {
+            case 8: k_moments_q<8><<<cells, 32, 0, s>>>(hf, vf, dv3, cell0, mom); break;
+            case 16: k_moments_q<16><<<cells, 64, 0, s>>>(hf, vf, dv3, cell0, mom); break;
+            case 24: k_moments_q<24><<<cells, 160, 0, s>>>(hf, vf, dv3, cell0, mom); break;
+            default: k_moments_q<32><<<cells, 256, 0, s>>>(hf, vf, dv3, cell0, mom); break;
+        }
+        return;
+    }
     switch (t.nv) {
         case 8: k_moments<T, 8><<<cells, 64, 0, s>>>(h, vel, dv3, cell0, mom); break;
         case 16: k_moments<T, 16><<<cells, 128, 0, s>>>(h, vel, dv3, cell0, mom); break;
@@ -966,7 +1037,7 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
 template <typename T>
 void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
                     const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state, double* hm,
-                    const double* nd) {
+                    const double* nd, int quarter) {
     if (njobs <= 0) return;
     g_launches += 1;
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
@@ -974,20 +1045,20 @@ void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const doub
     dim3 g(2 * sm_count(), njobs);
     const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
     k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1,
-                                   t.dv * t.dv * t.dv);
+                                   t.dv * t.dv * t.dv, quarter);
 }
 
 template void launch_sweep<double>(const DevTables&, int, int, int, const double*, double*,
-                                   const SweepJobDev*, const int*, const double*, cudaStream_t);
+                                   const SweepJobDev*, const int*, const double*, cudaStream_t, int);
 template void launch_sweep<float>(const DevTables&, int, int, int, const float*, float*,
-                                  const SweepJobDev*, const int*, const double*, cudaStream_t);
-template void launch_moments<double>(const DevTables&, long, int, const double*, double*, cudaStream_t);
-template void launch_moments<float>(const DevTables&, long, int, const float*, double*, cudaStream_t);
+                                  const SweepJobDev*, const int*, const double*, cudaStream_t, int);
+template void launch_moments<double>(const DevTables&, long, int, const double*, double*, cudaStream_t, int);
+template void launch_moments<float>(const DevTables&, long, int, const float*, double*, cudaStream_t, int);
 template void launch_correct<double>(const DevTables&, int, const double*, double*, const double*,
                                      const double*, const SweepJobDev*, const int*, cudaStream_t, const JobState*,
-                                     double*, const double*);
+                                     double*, const double*, int);
 template void launch_correct<float>(const DevTables&, int, const float*, float*, const double*, const float*,
                                     const SweepJobDev*, const int*, cudaStream_t, const JobState*, double*,
-                                    const double*);
+                                    const double*, int);
 
 }  // namespace lbe

@@ -13,9 +13,11 @@ struct Ctx;
 // fsm_dense.cu: tensor-core operator on the parity subspace (float in / out; mode 1 or 2)
 // hm (may be NULL): per cell the h part of G (launch_correct); with it and without Lout the
 // expand reads no h.
+// quarter (mode 2 only): h and Lplus in the orbit layout (below); then Lout must be NULL, and
+// G needs hm.
 lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h,
                         float* Lplus, float* Lout, cudaStream_t s, bool sync = true, const double* nd = nullptr,
-                        double* G = nullptr, const double* hm = nullptr);
+                        double* G = nullptr, const double* hm = nullptr, bool quarter = false);
 lbe_status tc_check(Ctx* c, DevTables* t);
 void tc_release(Ctx* c, DevTables* t);
 // refine.cu: BF16 operator inside an outer defect-correction loop
@@ -57,11 +59,18 @@ struct JobState {
     int iters, done, nan, skip;
 };
 
+// Orbit layout ("quarter"): a plate iterate is odd in v3 and even in v2, so each cell keeps one
+// value per orbit {1, R2, R3, R2 R3} -- the points with i2, i3 < nv / 2 -- at index
+// (i1 nv / 2 + i2) nv / 2 + i3 in the first nv^3 / 4 places of the cell's nv^3 (the cell stride
+// is unchanged).  h(i1, nv-1-i2, i3) = h(i1, i2, i3) and h(i1, i2, nv-1-i3) = -h(i1, i2, i3).
+// The FP32 iterations of the tensor-core operator use it for plates (1D problems).
 template <typename T>
 void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T* rhs, T* h,
-                  const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s);
+                  const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s,
+                  int quarter = 0);
 template <typename T>
-void launch_moments(const DevTables& t, long cell0, int cells, const T* h, double* mom, cudaStream_t s);
+void launch_moments(const DevTables& t, long cell0, int cells, const T* h, double* mom, cudaStream_t s,
+                    int quarter = 0);
 void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, const int* active,
                        const double* mom, const double* G, const double* coef, double* work, double* dU,
                        double* U3, JobState* state, cudaStream_t s);
@@ -71,7 +80,7 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
 template <typename T>
 void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
                     const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state = nullptr,
-                    double* hm = nullptr, const double* nd = nullptr);
+                    double* hm = nullptr, const double* nd = nullptr, int quarter = 0);
 
 // fsm_cc.cu
 void init_twiddles_cc();

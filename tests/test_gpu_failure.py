@@ -158,8 +158,11 @@ def test_cancel_queued_and_admitted():
         c.close()
 
 
-@pytest.mark.parametrize("prec", [lbe.FP64, lbe.FP32])
+@pytest.mark.parametrize("prec", [lbe.FP64, lbe.FP32, lbe.BF16])
 def test_resume_is_bitwise(ctx, prec):
+    """A solve stopped after k iterations and resumed from its h and flow rates ends exactly where
+    the uninterrupted solve ends. BF16 keeps plate iterates in the orbit layout (one value per
+    orbit of the v2 and v3 reflections), so its checkpoint round-trips through the full grid."""
     pb = small_plate(precision=prec, delta=10.0, eps=1e-9 if prec == lbe.FP64 else 1e-5)
     full, U_full, h_full = ctx.solve(pb, want_h=True)
     assert full.status == lbe.OK and full.iters > 8

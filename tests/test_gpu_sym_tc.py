@@ -183,3 +183,17 @@ def test_bf16_refined_solve_reaches_fp64(ctx):
         assert g.status == lbe.OK, (g.status, g.iters, g.refinements)
         assert abs(g.mass_flow - r.mass_flow) <= 1e-7 * abs(r.mass_flow)
         assert abs(g.heat_flow - r.heat_flow) <= 1e-7 * abs(r.heat_flow)
+
+
+def test_bf16_plate_iterate_symmetric_and_near_fp64(ctx):
+    """The plate iterate of the tensor-core path lives in the orbit layout; returned on the full
+    grid it is exactly even in v2 and odd in v3, and within 1e-4 of the FP64 iterate's scale."""
+    base = dict(dim=1, ns=30, grid_kind=1, nv=16, vmax=6.0, M=16, R=4.5, delta=3.0, scheme=lbe.SIS,
+                max_iter=300)
+    r64, _, h64 = ctx.solve(lbe.problem(**base, precision=lbe.FP64, eps=1e-10), want_h=True)
+    rb, _, hb = ctx.solve(lbe.problem(**base, precision=lbe.BF16, eps=1e-6), want_h=True)
+    assert rb.status == lbe.OK and r64.status == lbe.OK
+    assert np.array_equal(hb[:, :, ::-1, :], hb)
+    assert np.array_equal(hb[:, :, :, ::-1], -hb)
+    scale = np.abs(h64).max()
+    assert np.abs(hb - h64).max() <= 1e-4 * scale
