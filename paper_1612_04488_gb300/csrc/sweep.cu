@@ -818,51 +818,12 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
             comp = (t - sum) - y;
             sum = t;
         };
-        for (int r = threadIdx.x; r < norb; r += blockDim.x) {
-            const int i3 = r % hv;
-            int i1, i2;
-            if (plates) {
-                i2 = (r / hv) % hv;
-                i1 = r / (hv * hv);
-            } else {
-                i2 = (r / hv) % nv;
-                i1 = r / (hv * nv);
-            }
-            const int va = (i1 * nv + i2) * nv + i3;        // v3 < 0 half
-            const int vc = (i1 * nv + i2) * nv + nv - 1 - i3;  // R3
-            const int vb = (i1 * nv + nv - 1 - i2) * nv + i3;           // R2 (plates)
-            const int vd = (i1 * nv + nv - 1 - i2) * nv + nv - 1 - i3;  // R2 R3 (plates)
-            T y;
-            if (only_hm) {
-                y = plates && quarter ? dst[r] : dst[va];
-            } else if (plates && quarter) {  // orbit layout: the orbit's one stored value, at index r
-                y = (ex ? src[r] + ex[r] : src[r]) + d * vel[i3] * feq[va];
-                dst[r] = y;
-            } else {
-                T xa = src[va], xc = src[vc];
-                if (ex) {
-                    xa += ex[va];
-                    xc += ex[vc];
-                }
-                if (plates) {
-                    T xb = src[vb], xd = src[vd];
-                    if (ex) {
-                        xb += ex[vb];
-                        xd += ex[vd];
-                    }
-                    y = (T)0.25 * ((xa + xb) - (xc + xd)) + d * vel[i3] * feq[va];
-                    dst[va] = y;
-                    dst[vb] = y;
-                    dst[vc] = -y;
-                    dst[vd] = -y;
-                } else {
-                    y = (T)0.5 * (xa - xc) + d * vel[i3] * feq[va];
-                    dst[va] = y;
-                    dst[vc] = -y;
-                }
-            }
-            if (!hm) continue;
+        // the h part of the L-moments at the orbit of (i1, i2, i3) (plates) or (i1, i2, i3) and
+        // its R3 image (ducts), y the value at the representative
+        auto add_hm = [&](int i1, int i2, int i3, T y) {
+            const int va = (i1 * nv + i2) * nv + i3, vc = (i1 * nv + i2) * nv + nv - 1 - i3;
             if (plates) {  // v3 h is the same at the four points; v2 flips sign under R2
+                const int vb = (i1 * nv + nv - 1 - i2) * nv + i3, vd = (i1 * nv + nv - 1 - i2) * nv + nv - 1 - i3;
                 const float wa = ndc - dl * (float)nu1[va], wb = ndc - dl * (float)nu1[vb];
                 const float wc = ndc - dl * (float)nu1[vc], wd = ndc - dl * (float)nu1[vd];
                 const float t = (float)vel[i3] * (float)y;
@@ -873,6 +834,81 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
                 const float t = (float)vel[i3] * (float)y * w;
                 kahan(a0, c0, (float)vel[i1] * t);
                 kahan(a1, c1, (float)vel[i2] * t);
+            }
+        };
+        if (plates && quarter) {
+            // orbit layout: the orbit's one stored value sits at index r.  Four orbits per
+            // thread and pass, their loads issued together (the same order of sums as one at
+            // a time).
+            const int bd = blockDim.x;
+            for (int r0 = threadIdx.x; r0 < norb; r0 += 4 * bd) {
+                T x[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int r = r0 + k * bd;
+                    x[k] = r < norb ? (only_hm ? dst[r] : src[r]) : T(0);
+                }
+                if (ex && !only_hm)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int r = r0 + k * bd;
+                        if (r < norb) x[k] += ex[r];
+                    }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int r = r0 + k * bd;
+                    if (r >= norb) break;
+                    const int i3 = r % hv, i2 = (r / hv) % hv, i1 = r / (hv * hv);
+                    T y = x[k];
+                    if (!only_hm) {
+                        y = x[k] + d * vel[i3] * feq[(i1 * nv + i2) * nv + i3];
+                        dst[r] = y;
+                    }
+                    if (hm) add_hm(i1, i2, i3, y);
+                }
+            }
+        } else {
+            for (int r = threadIdx.x; r < norb; r += blockDim.x) {
+                const int i3 = r % hv;
+                int i1, i2;
+                if (plates) {
+                    i2 = (r / hv) % hv;
+                    i1 = r / (hv * hv);
+                } else {
+                    i2 = (r / hv) % nv;
+                    i1 = r / (hv * nv);
+                }
+                const int va = (i1 * nv + i2) * nv + i3;                    // v3 < 0 half
+                const int vc = (i1 * nv + i2) * nv + nv - 1 - i3;           // R3
+                const int vb = (i1 * nv + nv - 1 - i2) * nv + i3;           // R2 (plates)
+                const int vd = (i1 * nv + nv - 1 - i2) * nv + nv - 1 - i3;  // R2 R3 (plates)
+                T y;
+                if (only_hm) {
+                    y = dst[va];
+                } else {
+                    T xa = src[va], xc = src[vc];
+                    if (ex) {
+                        xa += ex[va];
+                        xc += ex[vc];
+                    }
+                    if (plates) {
+                        T xb = src[vb], xd = src[vd];
+                        if (ex) {
+                            xb += ex[vb];
+                            xd += ex[vd];
+                        }
+                        y = (T)0.25 * ((xa + xb) - (xc + xd)) + d * vel[i3] * feq[va];
+                        dst[va] = y;
+                        dst[vb] = y;
+                        dst[vc] = -y;
+                        dst[vd] = -y;
+                    } else {
+                        y = (T)0.5 * (xa - xc) + d * vel[i3] * feq[va];
+                        dst[va] = y;
+                        dst[vc] = -y;
+                    }
+                }
+                if (hm) add_hm(i1, i2, i3, y);
             }
         }
         if (hm) {
