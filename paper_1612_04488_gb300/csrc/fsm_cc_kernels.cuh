@@ -125,30 +125,26 @@ __global__ void __launch_bounds__(32 * WPB) k_slab2d(const TIN* __restrict__ hin
         sm[w][idx / N][idx % N] = z;
     }
     __syncwarp();
-    if (lane < N) {  // along i3: lane owns row k2 = lane
-        T re[N], im[N];
+    // along i3 (lane owns row k2 = lane), then along i2 (lane owns column i3 = lane): one loop,
+    // so the unrolled line transform is emitted once (the kernel's code stays small enough for
+    // the instruction cache)
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        if (lane < N) {
+            cplx_t<T>* p0 = pass == 0 ? &sm[w][lane][0] : &sm[w][0][lane];
+            const int st = pass == 0 ? 1 : LD;
+            T re[N], im[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            re[j] = sm[w][lane][j].x;
-            im[j] = sm[w][lane][j].y;
+            for (int j = 0; j < N; ++j) {
+                re[j] = p0[j * st].x;
+                im[j] = p0[j * st].y;
+            }
+            dft_line<T, N, INV>(re, im);
+#pragma unroll
+            for (int j = 0; j < N; ++j) p0[j * st] = mk<T>(re[j], im[j]);
         }
-        dft_line<T, N, INV>(re, im);
-#pragma unroll
-        for (int j = 0; j < N; ++j) sm[w][lane][j] = mk<T>(re[j], im[j]);
+        __syncwarp();
     }
-    __syncwarp();
-    if (lane < N) {  // along i2: lane owns column i3 = lane
-        T re[N], im[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            re[j] = sm[w][j][lane].x;
-            im[j] = sm[w][j][lane].y;
-        }
-        dft_line<T, N, INV>(re, im);
-#pragma unroll
-        for (int j = 0; j < N; ++j) sm[w][j][lane] = mk<T>(re[j], im[j]);
-    }
-    __syncwarp();
     for (int idx = lane; idx < N2; idx += 32) out[obase + idx] = sm[w][idx / N][idx % N];
 }
 
@@ -173,27 +169,10 @@ __global__ void __launch_bounds__(128) k_inv_last4(const cplx_t<T>* __restrict__
     T acc[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) acc[j] = T(0);
-    if (w == 0) {
-        const cplx_t<T>* yl = Y + (cell * (M + 1) + M) * N3 + r;
-        T re[N], im[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const cplx_t<T> z = yl[(long)j * N2];
-            re[j] = z.x;
-            im[j] = z.y;
-        }
-        dft_line<T, N, true>(re, im);
-        if (RAW) {
-#pragma unroll
-            for (int j = 0; j < N; ++j) Lout[cell * N3 + (long)j * N2 + r] = re[j];
-        } else {
-#pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] = -feq[j * N2 + r] * re[j];
-        }
-    }
-    for (int p = w; p < M; p += 4) {
+    // slots p = w, w + 4, .. of the M directions and the loss (p = M), one line transform in
+    // the loop body (emitted once)
+    for (int p = w; p <= M; p += 4) {
         const cplx_t<T>* yl = Y + (cell * (M + 1) + p) * N3 + r;
-        const cplx_t<T>* al = ab + (long)p * N3 + r;
         T re[N], im[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
@@ -202,6 +181,17 @@ __global__ void __launch_bounds__(128) k_inv_last4(const cplx_t<T>* __restrict__
             im[j] = z.y;
         }
         dft_line<T, N, true>(re, im);
+        if (p == M) {  // the loss convolution
+            if (RAW) {
+#pragma unroll
+                for (int j = 0; j < N; ++j) Lout[cell * N3 + (long)j * N2 + r] = re[j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < N; ++j) acc[j] += -feq[j * N2 + r] * re[j];
+            }
+            continue;
+        }
+        const cplx_t<T>* al = ab + (long)p * N3 + r;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             const cplx_t<T> a = al[j * N2];

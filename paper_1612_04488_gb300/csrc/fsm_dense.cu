@@ -775,7 +775,7 @@ __global__ void __launch_bounds__(8 * NV) k_expand_sub(const float* __restrict__
 // quarter's sum (v1 v3 L+ h is even under R2 and R3); G_2's summand is odd under R2, so
 // G_2 = hm_2.  The per-point arithmetic is that of k_expand_sub.
 template <int NV>
-__global__ void __launch_bounds__(8 * NV) k_expand_q(const float* __restrict__ Y, const float* __restrict__ vel,
+__global__ void __launch_bounds__(1024) k_expand_q(const float* __restrict__ Y, const float* __restrict__ vel,
                                                      const double* __restrict__ delta, float* __restrict__ Lplus,
                                                      double* __restrict__ G, double dv3,
                                                      const double* __restrict__ hm) {
@@ -837,7 +837,8 @@ void launch_expand_q(int cells, const float* Y, const float* vel, const double* 
     std::call_once(once, [smem] {
         cudaFuncSetAttribute(k_expand_q<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     });
-    k_expand_q<NV><<<cells, 8 * NV, smem, s>>>(Y, vel, delta, Lplus, G, dv3, hm);
+    constexpr int pts = NV * H * H, threads = pts >= 1024 ? 1024 : (pts + 31) / 32 * 32;  // a thread per point
+    k_expand_q<NV><<<cells, threads, smem, s>>>(Y, vel, delta, Lplus, G, dv3, hm);
 }
 
 template <int NV, int MODE>

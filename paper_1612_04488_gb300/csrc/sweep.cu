@@ -788,7 +788,7 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
 // at the orbit's index), where the projection is the identity.  hh = NULL: only hm, of the h
 // already stored (a solve resumed from a checkpoint), with the same arithmetic.
 template <typename T>
-__global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __restrict__ h,
+__global__ void __launch_bounds__(1024) k_correct(const T* __restrict__ hh, T* __restrict__ h,
                                                  const double* __restrict__ dU, const T* __restrict__ extra,
                                                  const T* __restrict__ feq,
                                                  const T* __restrict__ vel, const SweepJobDev* __restrict__ jobs,
@@ -1078,9 +1078,11 @@ void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const doub
     g_launches += 1;
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
+    // one block per cell (grid-stride over a job's cells), 1024 threads: a plate cell is
+    // 8192 orbits at 32^3
     dim3 g(2 * sm_count(), njobs);
     const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
-    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1,
+    k_correct<T><<<g, 1024, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1,
                                    t.dv * t.dv * t.dv, quarter);
 }
 
