@@ -501,33 +501,45 @@ void batch_iterate(Batch& B, bool upload, bool read) {
         const long c0 = sp.c0;
         const int nc = (int)sp.n;
         const int mode = sp.dim == 1 ? 2 : 1;
+        const bool q = B.quarter() && sp.dim == 1;  // plates in the orbit layout
         if (sizeof(T) == 8 && B.base_h) {
             // L h = L_64(h_base) + L_32(h - h_base): the increment is small, so FP32 suffices
             const long o = c0 * n3, nn = (long)nc * n3;
-            range_sub_f32((const double*)(h + o), B.base_h + o, B.inc_h + o, nn, s);
+            if (q)
+                range_sub_f32_q((const double*)(h + o), B.base_h + o, B.inc_h + o, nc, n3, s);
+            else
+                range_sub_f32((const double*)(h + o), B.base_h + o, B.inc_h + o, nn, s);
             if (B.inc_tc) {  // BF16-refined: the increment through the tensor-core operator
                 const lbe_status ts = tc_apply_sym(B.c, B.t, mode, nc, B.delta.as<double>() + c0, B.inc_h + o,
-                                                   B.inc_lp + o, B.inc_lh + o, s, false);
+                                                   B.inc_lp + o, B.inc_lh + o, s, false, nullptr, nullptr, nullptr,
+                                                   q);
                 if (ts != LBE_OK && B.op_status == LBE_OK) B.op_status = ts;
             } else {
                 fsm_cc_apply<float>(t, nc, B.delta.as<double>() + c0, B.inc_h + o, B.inc_lp + o, B.inc_lh + o,
                                     B.inc_scratch, B.inc_chunk, s, mode);
             }
-            range_add_f64(B.base_lp + o, B.inc_lp + o, (double*)(lp + o), nn, s);
-            range_add_f64(B.base_lh + o, B.inc_lh + o, (double*)(lh + o), nn, s);
+            if (q) {
+                range_add_f64_q(B.base_lp + o, B.inc_lp + o, (double*)(lp + o), nc, n3, s);
+                range_add_f64_q(B.base_lh + o, B.inc_lh + o, (double*)(lh + o), nc, n3, s);
+            } else {
+                range_add_f64(B.base_lp + o, B.inc_lp + o, (double*)(lp + o), nn, s);
+                range_add_f64(B.base_lh + o, B.inc_lh + o, (double*)(lh + o), nn, s);
+            }
         } else if (sizeof(T) == 4 && B.use_tc) {
             // L+ h and the L-moments in one pass; L h itself is not stored
             const lbe_status ts = tc_apply_sym(B.c, B.t, mode, nc, B.delta.as<double>() + c0, (const float*)(h + c0 * n3),
                                                (float*)(lp + c0 * n3), nullptr, s, false, B.nd.as<double>() + c0,
                                                B.G.as<double>() + c0 * 2, B.hmom.as<double>() + c0 * 2,
-                                               B.quarter() && sp.dim == 1);
+                                               q);
             if (ts != LBE_OK && B.op_status == LBE_OK) B.op_status = ts;
             continue;
         } else {
             fsm_cc_apply<T>(t, nc, B.delta.as<double>() + c0, h + c0 * n3, lp + c0 * n3, lh + c0 * n3,
                             B.scratch.p, B.chunk, s, mode);
         }
-        if (any_sis) lmoments<T>(t, nc, lh + c0 * n3, h + c0 * n3, B.nd.as<double>() + c0, B.G.as<double>() + c0 * 2, s);
+        if (any_sis)
+            lmoments<T>(t, nc, lh + c0 * n3, h + c0 * n3, B.nd.as<double>() + c0, B.G.as<double>() + c0 * 2, s,
+                        q ? 1 : 0);
     }
     // sweeps grouped by dimension
     std::vector<int> act1, act2;
@@ -560,13 +572,15 @@ void batch_iterate(Batch& B, bool upload, bool read) {
     }
     for (auto& sp : spans)
         launch_moments<T>(t, sp.c0, (int)sp.n, hh, B.mom.as<double>(), s, B.quarter() && sp.dim == 1);
+    int max_cells = 0;
+    for (int j : B.active) max_cells = std::max(max_cells, B.sj[j].ncell);
     launch_sis_update(t, na, B.ijobs.as<SisJobDev>(), dact, B.mom.as<double>(), B.G.as<double>(),
                       B.coef.as<double>(), B.work.as<double>(), B.dU.as<double>(), B.U3.as<double>(),
                       B.states.as<JobState>(), s);
     launch_correct<T>(t, na, hh, h, B.dU.as<double>(), B.extra.p ? B.extra.as<T>() : nullptr,
                       B.sjobs.as<SweepJobDev>(), dact, s, B.states.as<JobState>(),
                       (sizeof(T) == 4 && B.use_tc) ? B.hmom.as<double>() : nullptr, B.nd.as<double>(),
-                      B.quarter() ? 1 : 0);
+                      B.quarter() ? 1 : 0, max_cells);
     if (read) {
         cudaMemcpyAsync(B.hstate.data(), B.states.p, B.njobs * sizeof(JobState), cudaMemcpyDeviceToHost, s);
         g_d2h += B.njobs * sizeof(JobState);
@@ -801,9 +815,8 @@ int lbe_problem_cells(const lbe_problem* pb) {
     return pb->geom.dim == 1 ? pb->geom.ns + 1 : pb->geom.nx * pb->geom.ny;
 }
 
-// Host conversion between the full velocity grid and the orbit layout (sweep.h) of `cells`
-// cells: pack keeps the orbit representatives (i2, i3 < nv / 2), unpack restores the R2 and R3
-// images (even in v2, odd in v3).
+// Host: the orbit layout (sweep.h) of `cells` cells from the full velocity grid -- the orbit
+// representatives (i2, i3 < nv / 2); orbit_unpack_host (batch.h) is the inverse.
 static void orbit_pack(int nv, long cells, const double* full, float* q) {
     const int H = nv / 2;
     const long n3 = (long)nv * nv * nv;
@@ -813,19 +826,6 @@ static void orbit_pack(int nv, long cells, const double* full, float* q) {
                 for (int j3 = 0; j3 < H; ++j3)
                     q[c * n3 + ((long)i1 * H + j2) * H + j3] = (float)full[c * n3 + ((long)i1 * nv + j2) * nv + j3];
 }
-static void orbit_unpack(int nv, long cells, const float* q, double* full) {
-    const int H = nv / 2;
-    const long n3 = (long)nv * nv * nv;
-    for (long c = 0; c < cells; ++c)
-        for (int i1 = 0; i1 < nv; ++i1)
-            for (int i2 = 0; i2 < nv; ++i2)
-                for (int i3 = 0; i3 < nv; ++i3) {
-                    const int j2 = i2 < H ? i2 : nv - 1 - i2, j3 = i3 < H ? i3 : nv - 1 - i3;
-                    const double v = q[c * n3 + ((long)i1 * H + j2) * H + j3];
-                    full[c * n3 + ((long)i1 * nv + i2) * nv + i3] = i3 < H ? v : -v;
-                }
-}
-
 static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_result* outs,
                                 double* U3_out, double* h_out, const double* h_in = nullptr,
                                 const lbe_result* prev = nullptr) {
@@ -848,6 +848,7 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
         // the tensor-core operator with FP32 everything else; scale-relative stopping test
         if (B.t->sym_reps2 == 0) return bad_arg(ctx, "LBE_BF16 needs a parity-reducible direction set");
         B.use_tc = true;
+        B.orbit = true;
         for (int j = 0; j < n; ++j) B.ij[j].crit = 1;
         cudaMemcpyAsync(B.ijobs.p, B.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, ctx->stream);
         g_h2d += n * sizeof(SisJobDev);
@@ -916,8 +917,8 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
             if (B.quarter())
                 for (int j = 0; j < n; ++j)
                     if (B.geo[j].dim == 1)
-                        orbit_unpack(pbs[0].nv, B.sj[j].ncell, tmp.data() + B.cell_off[j] * n3,
-                                     h_out + B.cell_off[j] * n3);
+                        orbit_unpack_host(pbs[0].nv, B.sj[j].ncell, tmp.data() + B.cell_off[j] * n3,
+                                          h_out + B.cell_off[j] * n3);
         }
     }
     return st != LBE_OK ? st : worst;

@@ -771,14 +771,16 @@ __global__ void __launch_bounds__(8 * NV) k_expand_sub(const float* __restrict__
 }
 
 // The plate expand in the orbit layout: L+ h at the stored quarter only (i2, i3 < nv / 2, where
-// the R2 and R3 signs are +1), and G_1 = 2 sum_v v1 v3 L+ h dv^3 + hm_1 as four times the
-// quarter's sum (v1 v3 L+ h is even under R2 and R3); G_2's summand is odd under R2, so
-// G_2 = hm_2.  The per-point arithmetic is that of k_expand_sub.
+// the R2 and R3 signs are +1), optionally L h = L+ h - delta nu h (h in the orbit layout), and
+// optionally G_1 = 2 sum_v v1 v3 L+ h dv^3 + hm_1 as four times the quarter's sum (v1 v3 L+ h is
+// even under R2 and R3); G_2's summand is odd under R2, so G_2 = hm_2.  The per-point arithmetic
+// is that of k_expand_sub.
 template <int NV>
-__global__ void __launch_bounds__(1024) k_expand_q(const float* __restrict__ Y, const float* __restrict__ vel,
+__global__ void __launch_bounds__(256) k_expand_q(const float* __restrict__ Y, const float* __restrict__ vel,
                                                      const double* __restrict__ delta, float* __restrict__ Lplus,
                                                      double* __restrict__ G, double dv3,
-                                                     const double* __restrict__ hm) {
+                                                     const double* __restrict__ hm, const float* __restrict__ h,
+                                                     const float* __restrict__ nu1, float* __restrict__ Lout) {
     extern __shared__ float sY[];
     __shared__ dfloat redx[32 * 2];
     constexpr int H = NV / 2;
@@ -805,6 +807,7 @@ __global__ void __launch_bounds__(1024) k_expand_q(const float* __restrict__ Y, 
         const float y1 = sY[L.soff[2] + (j1 * H + j2) * H + j3];
         const float lp = d * (m1 ? y0 - y1 : y0 + y1);
         Lplus[c * n3 + p] = lp;
+        if (Lout) Lout[c * n3 + p] = lp - d * nu1[(i1 * NV + j2) * NV + j3] * h[c * n3 + p];
         if (G) {
             const float t = lp * vel[j3];
             const float x = vel[i1] * t - c0;
@@ -830,15 +833,15 @@ void launch_gather(int cells, int cpad, const float* h, __nv_bfloat162* xh, __nv
 
 template <int NV>
 void launch_expand_q(int cells, const float* Y, const float* vel, const double* delta, float* Lplus, double* G,
-                     double dv3, const double* hm, cudaStream_t s) {
+                     double dv3, const double* hm, const float* h, const float* nu1, float* Lout, cudaStream_t s) {
     static std::once_flag once;
     constexpr int H = NV / 2;
     const int smem = 2 * H * H * H * 4;
     std::call_once(once, [smem] {
         cudaFuncSetAttribute(k_expand_q<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     });
-    constexpr int pts = NV * H * H, threads = pts >= 1024 ? 1024 : (pts + 31) / 32 * 32;  // a thread per point
-    k_expand_q<NV><<<cells, threads, smem, s>>>(Y, vel, delta, Lplus, G, dv3, hm);
+    constexpr int pts = NV * H * H, threads = pts >= 256 ? 256 : (pts + 31) / 32 * 32;
+    k_expand_q<NV><<<cells, threads, smem, s>>>(Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout);
 }
 
 template <int NV, int MODE>
@@ -1252,7 +1255,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
                         float* Lout, cudaStream_t s, bool sync, const double* nd, double* G, const double* hm,
                         bool quarter) {
     if (mode != 1 && mode != 2) return LBE_BAD_ARG;
-    if (quarter && (mode != 2 || Lout || (G && !hm))) return LBE_BAD_ARG;
+    if (quarter && (mode != 2 || (G && (!hm || Lout)))) return LBE_BAD_ARG;
     if (cells <= 0) return LBE_OK;
     if (!t->tc) t->tc = new TcOperands();
     TcOperands& T = *t->tc;
@@ -1472,10 +1475,10 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         const double dv3 = t->dv * t->dv * t->dv;
         const bool p2 = mode == 2;
         if (quarter) switch (nv) {
-                case 8: launch_expand_q<8>(cells, Y, vel, delta, Lplus, G, dv3, hm, s); break;
-                case 16: launch_expand_q<16>(cells, Y, vel, delta, Lplus, G, dv3, hm, s); break;
-                case 24: launch_expand_q<24>(cells, Y, vel, delta, Lplus, G, dv3, hm, s); break;
-                default: launch_expand_q<32>(cells, Y, vel, delta, Lplus, G, dv3, hm, s); break;
+                case 8: launch_expand_q<8>(cells, Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout, s); break;
+                case 16: launch_expand_q<16>(cells, Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout, s); break;
+                case 24: launch_expand_q<24>(cells, Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout, s); break;
+                default: launch_expand_q<32>(cells, Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout, s); break;
             }
         else switch (nv) {
             case 8: (p2 ? launch_expand<8, 2> : launch_expand<8, 1>)(cells, Y, h, nu1, vel, delta, nd, Lplus, Lout, G, dv3, hm, s); break;

@@ -90,73 +90,119 @@ void range_residual_q(const double* h, const double* h_old, float* r, long cells
     k_range_residual_q<<<sm_count(), 256, 0, s>>>(h, h_old, r, cells, nv);
 }
 
+__global__ void k_range_sub_f32_q(const double* __restrict__ h, const double* __restrict__ b, float* __restrict__ o,
+                                  long cells, long n3) {
+    const long nq = n3 / 4, n = cells * nq;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const long i = (k / nq) * n3 + k % nq;
+        o[i] = (float)(h[i] - b[i]);
+    }
+}
+__global__ void k_range_add_f64_q(const double* __restrict__ b, const float* __restrict__ inc,
+                                  double* __restrict__ o, long cells, long n3) {
+    const long nq = n3 / 4, n = cells * nq;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const long i = (k / nq) * n3 + k % nq;
+        o[i] = b[i] + (double)inc[i];
+    }
+}
+__global__ void k_range_copy_q(const double* __restrict__ a, double* __restrict__ b, long cells, long n3) {
+    const long nq = n3 / 4, n = cells * nq;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const long i = (k / nq) * n3 + k % nq;
+        b[i] = a[i];
+    }
+}
+__global__ void k_orbit_unpack(const double* __restrict__ q, double* __restrict__ full, long cells, int nv) {
+    const long n3 = (long)nv * nv * nv, n = cells * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const long f = k % n3;
+        bool neg;
+        const double v = q[k - f + orbit_of(f, nv, &neg)];
+        full[k] = neg ? -v : v;
+    }
+}
+__global__ void k_orbit_pack(const double* __restrict__ full, double* __restrict__ q, long cells, int nv) {
+    const long n3 = (long)nv * nv * nv, nq = n3 / 4, n = cells * nq;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
+        const long c = k / nq, r = k % nq;
+        q[c * n3 + r] = full[c * n3 + full_of(r, nv)];
+    }
+}
+void range_sub_f32_q(const double* h, const double* base, float* out, long cells, long n3, cudaStream_t s) {
+    g_launches += 1;
+    k_range_sub_f32_q<<<2 * sm_count(), 256, 0, s>>>(h, base, out, cells, n3);
+}
+void range_add_f64_q(const double* base, const float* inc, double* out, long cells, long n3, cudaStream_t s) {
+    g_launches += 1;
+    k_range_add_f64_q<<<2 * sm_count(), 256, 0, s>>>(base, inc, out, cells, n3);
+}
+void range_copy_q(const double* a, double* b, long cells, long n3, cudaStream_t s) {
+    g_launches += 1;
+    k_range_copy_q<<<2 * sm_count(), 256, 0, s>>>(a, b, cells, n3);
+}
+void orbit_unpack_dev(const double* q, double* full, long cells, int nv, cudaStream_t s) {
+    g_launches += 1;
+    k_orbit_unpack<<<2 * sm_count(), 256, 0, s>>>(q, full, cells, nv);
+}
+void orbit_pack_dev(const double* full, double* q, long cells, int nv, cudaStream_t s) {
+    g_launches += 1;
+    k_orbit_pack<<<2 * sm_count(), 256, 0, s>>>(full, q, cells, nv);
+}
+
 namespace {
+
+// The per-job element-wise steps below run over the values a job's cells hold: all nv^3 of a
+// cell, or with quarter the orbit-layout prefix (nv^3 / 4) of a plate's cells (sweep.h), where
+// both sides of the step are in that layout.
+__device__ __forceinline__ long job_values(const SweepJobDev& jb, long n3, int quarter) {
+    return quarter && jb.ny == 0 ? n3 / 4 : n3;
+}
 
 // dst = src over the cells of the active jobs
 __global__ void k_copy64(const double* __restrict__ src, double* __restrict__ dst,
-                         const SweepJobDev* __restrict__ jobs, const int* __restrict__ active, long n3) {
+                         const SweepJobDev* __restrict__ jobs, const int* __restrict__ active, long n3,
+                         int quarter) {
     const SweepJobDev jb = jobs[active[blockIdx.y]];
-    const long total = (long)jb.ncell * n3, base = jb.cell_off * n3;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x)
-        dst[base + k] = src[base + k];
+    const long nq = job_values(jb, n3, quarter), total = (long)jb.ncell * nq, base = jb.cell_off * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
+        const long i = base + (k / nq) * n3 + k % nq;
+        dst[i] = src[i];
+    }
 }
 
-// r = (float)(h - h_old); r of a plate in the orbit layout when quarter (h is exactly even in
-// v2 and odd in v3: the FP64 correction step projects onto that subspace)
+// r = (float)(h - h_old)
 __global__ void k_residual(const double* __restrict__ h, const double* __restrict__ h_old, float* __restrict__ r,
-                           const SweepJobDev* __restrict__ jobs, const int* __restrict__ active, int nv,
+                           const SweepJobDev* __restrict__ jobs, const int* __restrict__ active, long n3,
                            int quarter) {
     const SweepJobDev jb = jobs[active[blockIdx.y]];
-    const long n3 = (long)nv * nv * nv, base = jb.cell_off * n3;
-    if (quarter && jb.ny == 0) {
-        const long nq = n3 / 4, total = (long)jb.ncell * nq;
-        for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-            const long c = k / nq, q = k % nq, f = base + c * n3 + full_of(q, nv);
-            r[base + c * n3 + q] = (float)(h[f] - h_old[f]);
-        }
-        return;
+    const long nq = job_values(jb, n3, quarter), total = (long)jb.ncell * nq, base = jb.cell_off * n3;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
+        const long i = base + (k / nq) * n3 + k % nq;
+        r[i] = (float)(h[i] - h_old[i]);
     }
-    const long total = (long)jb.ncell * n3;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x)
-        r[base + k] = (float)(h[base + k] - h_old[base + k]);
 }
 
-// h = h_old + e (e of a plate in the orbit layout when quarter)
+// h = h_old + e
 __global__ void k_apply_correction(const double* __restrict__ h_old, const float* __restrict__ e,
                                    double* __restrict__ h, const SweepJobDev* __restrict__ jobs,
-                                   const int* __restrict__ active, int nv, int quarter) {
+                                   const int* __restrict__ active, long n3, int quarter) {
     const SweepJobDev jb = jobs[active[blockIdx.y]];
-    const long n3 = (long)nv * nv * nv, total = (long)jb.ncell * n3, base = jb.cell_off * n3;
-    const bool q = quarter && jb.ny == 0;
+    const long nq = job_values(jb, n3, quarter), total = (long)jb.ncell * nq, base = jb.cell_off * n3;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-        double v;
-        if (q) {
-            const long f = k % n3;
-            bool neg;
-            v = (double)e[base + k - f + orbit_of(f, nv, &neg)];
-            if (neg) v = -v;
-        } else {
-            v = (double)e[base + k];
-        }
-        h[base + k] = h_old[base + k] + v;
+        const long i = base + (k / nq) * n3 + k % nq;
+        h[i] = h_old[i] + (double)e[i];
     }
 }
 
-// h = (double)e (e of a plate in the orbit layout when quarter)
+// h = (double)e
 __global__ void k_widen(const float* __restrict__ e, double* __restrict__ h, const SweepJobDev* __restrict__ jobs,
-                        const int* __restrict__ active, int nv, int quarter) {
+                        const int* __restrict__ active, long n3, int quarter) {
     const SweepJobDev jb = jobs[active[blockIdx.y]];
-    const long n3 = (long)nv * nv * nv, total = (long)jb.ncell * n3, base = jb.cell_off * n3;
-    const bool q = quarter && jb.ny == 0;
+    const long nq = job_values(jb, n3, quarter), total = (long)jb.ncell * nq, base = jb.cell_off * n3;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
-        if (q) {
-            const long f = k % n3;
-            bool neg;
-            const double v = (double)e[base + k - f + orbit_of(f, nv, &neg)];
-            h[base + k] = neg ? -v : v;
-        } else {
-            h[base + k] = (double)e[base + k];
-        }
+        const long i = base + (k / nq) * n3 + k % nq;
+        h[i] = (double)e[i];
     }
 }
 
@@ -263,27 +309,43 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
     if (st == LBE_OK) st = batch_init(I, c, pi.data(), n, &ai, s);
     if (st == LBE_OK) {  // low-precision phases test changes against the flow-rate scale
         I.use_tc = pbs[0].precision == LBE_BF16_REFINED && O.t->sym_reps2 > 0 && pbs[0].M >= 8;
+        // BF16-refined: plates in the orbit layout on both sides (sweep.h)
+        I.orbit = O.orbit = I.use_tc;
         for (int j = 0; j < n; ++j) I.ij[j].crit = 1;
         cudaMemcpyAsync(I.ijobs.p, I.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, s);
     }
-    const long n3 = (long)pbs[0].nv * pbs[0].nv * pbs[0].nv;
+    const bool q = I.orbit;
+    const int nv = pbs[0].nv;
+    const long n3 = (long)nv * nv * nv;
     const size_t vol64 = O.cells * n3 * 8, vol32 = O.cells * n3 * 4;
     int inc_chunk = 1;
     const size_t inc_scr = st == LBE_OK ? fsm_cc_scratch_bytes(*O.t, (int)O.cells, 4, &inc_chunk) : 0;
-    // h_old, r, base_h, base_lp, base_lh, inc_h, inc_lp, inc_lh, FP32 operator scratch
+    // h_old, r, base_h, base_lp, base_lh (the double-float operator's full-grid input and
+    // outputs), with q their copies in the batch's layout, inc_h, inc_lp, inc_lh, FP32
+    // operator scratch
     Arena& aw = c->refine_arena[2];
     double *h_old = nullptr, *base_h = nullptr, *base_lp = nullptr, *base_lh = nullptr;
+    double *bq_h = nullptr, *bq_lp = nullptr, *bq_lh = nullptr;
     float *r = nullptr, *inc_h = nullptr, *inc_lp = nullptr, *inc_lh = nullptr;
     void* inc_scratch = nullptr;
     if (st == LBE_OK) {
         const size_t pad = 256;
-        st = arena_reserve(c, aw, 4 * (vol64 + pad) + 4 * (vol32 + pad) + inc_scr + pad);
+        st = arena_reserve(c, aw, (q ? 7 : 4) * (vol64 + pad) + 4 * (vol32 + pad) + inc_scr + pad);
     }
     if (st == LBE_OK) {
         h_old = (double*)arena_take(aw, vol64);
         base_h = (double*)arena_take(aw, vol64);
         base_lp = (double*)arena_take(aw, vol64);
         base_lh = (double*)arena_take(aw, vol64);
+        if (q) {
+            bq_h = (double*)arena_take(aw, vol64);
+            bq_lp = (double*)arena_take(aw, vol64);
+            bq_lh = (double*)arena_take(aw, vol64);
+        } else {
+            bq_h = base_h;
+            bq_lp = base_lp;
+            bq_lh = base_lh;
+        }
         r = (float*)arena_take(aw, vol32);
         inc_h = (float*)arena_take(aw, vol32);
         inc_lp = (float*)arena_take(aw, vol32);
@@ -292,6 +354,32 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         if (!inc_scratch) st = LBE_INTERNAL;
     }
     if (st != LBE_OK) return st;
+    // The FP64-class operator of the current iterate of problems j0 .. j1 - 1 (consecutive, one
+    // geometry, contiguous cells) becomes their base: h0 = h, base_lp / base_lh = L+ h0 / L h0 in
+    // double-float arithmetic on the full grid, kept in the batch's layout.
+    auto evaluate_base = [&](int j0, int j1) {
+        long cells = 0;
+        for (int j = j0; j < j1; ++j) cells += O.sj[j].ncell;
+        const long o = O.cell_off[j0] * n3;
+        const bool plates = O.geo[j0].dim == 1;
+        const double* h = O.h.as<double>() + o;
+        if (q && plates)
+            orbit_unpack_dev(h, base_h + o, cells, nv, s);
+        else
+            range_copy(h, base_h + o, cells * n3, s);
+        fsm_df_apply(*O.t, (int)cells, O.delta.as<double>() + O.cell_off[j0], base_h + o, base_lp + o, base_lh + o,
+                     O.scratch.p, O.chunk, s, plates ? 2 : 1);
+        if (!q) return;
+        if (plates) {
+            range_copy_q(h, bq_h + o, cells, n3, s);
+            orbit_pack_dev(base_lp + o, bq_lp + o, cells, nv, s);
+            orbit_pack_dev(base_lh + o, bq_lh + o, cells, nv, s);
+        } else {
+            range_copy(base_h + o, bq_h + o, cells * n3, s);
+            range_copy(base_lp + o, bq_lp + o, cells * n3, s);
+            range_copy(base_lh + o, bq_lh + o, cells * n3, s);
+        }
+    };
     std::vector<int> outer_it(n, 0), inner_it(n, 0), refs(n, 0);
     std::vector<double> t_done(n, 0.0);
     std::vector<double> prev_rel(n, 1e300);
@@ -310,7 +398,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         for (int j = 0; j < n; ++j) inner_it[j] += I.hstate[j].iters;
         cudaMemcpyAsync(O.act.p, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, s);
         k_widen<<<dim3(sm_count(), n), blk, 0, s>>>(I.h.as<float>(), O.h.as<double>(), O.sjobs.as<SweepJobDev>(),
-                                                   O.act.as<int>(), pbs[0].nv, I.quarter() ? 1 : 0);
+                                                   O.act.as<int>(), n3, q ? 1 : 0);
         g_launches += 1;
         // from now on the inner batch solves the homogeneous correction equation
         for (int j = 0; j < n; ++j) {
@@ -324,7 +412,6 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         g_h2d += n * (sizeof(SweepJobDev) + sizeof(SisJobDev));
         // the one FP64-class collision-operator evaluation of the solve: at h0 = the FP32
         // solution; every later FP64 iteration adds the FP32 operator of the increment h - h0
-        range_copy(O.h.as<double>(), base_h, O.cells * n3, s);
         // one call per run of consecutive problems of one geometry (plates: parity mode 2,
         // ducts: mode 1); the problems' cells are contiguous in batch order
         for (int j0 = 0; j0 < n;) {
@@ -332,14 +419,12 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             long cells = O.sj[j0].ncell;
             while (j1 < n && O.geo[j1].dim == O.geo[j0].dim && O.cell_off[j1] == O.cell_off[j0] + cells)
                 cells += O.sj[j1++].ncell;
-            const long o = O.cell_off[j0] * n3;
-            fsm_df_apply(*O.t, (int)cells, O.delta.as<double>() + O.cell_off[j0], base_h + o, base_lp + o,
-                         base_lh + o, O.scratch.p, O.chunk, s, O.geo[j0].dim == 1 ? 2 : 1);
+            evaluate_base(j0, j1);
             j0 = j1;
         }
-        O.base_h = base_h;
-        O.base_lp = base_lp;
-        O.base_lh = base_lh;
+        O.base_h = bq_h;
+        O.base_lp = bq_lp;
+        O.base_lh = bq_lh;
         O.inc_h = inc_h;
         O.inc_tc = I.use_tc;  // BF16-refined: the increment h - h0 (~1e-4 of h) takes the
                               // tensor-core operator too; its 2^-16 error is ~1e-9 of h
@@ -358,23 +443,28 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         g_h2d += na * sizeof(int);
         // flow rates of the current iterate, then keep a copy of it
         {  // one launch per contiguous run of active problems' cells
-            std::vector<std::pair<long, long>> runs;
-            for (int j : active) runs.push_back({O.cell_off[j], (long)O.sj[j].ncell});
-            std::sort(runs.begin(), runs.end());
-            std::vector<std::pair<long, long>> merged;
+            struct Run {
+                long c0, n;
+                int dim;
+            };
+            std::vector<Run> runs;
+            for (int j : active) runs.push_back({O.cell_off[j], (long)O.sj[j].ncell, O.geo[j].dim});
+            std::sort(runs.begin(), runs.end(), [](const Run& a, const Run& b) { return a.c0 < b.c0; });
+            std::vector<Run> merged;
             for (auto& r : runs) {
-                if (!merged.empty() && merged.back().first + merged.back().second == r.first)
-                    merged.back().second += r.second;
+                if (!merged.empty() && merged.back().c0 + merged.back().n == r.c0 && merged.back().dim == r.dim)
+                    merged.back().n += r.n;
                 else
                     merged.push_back(r);
             }
             for (auto& r : merged)
-                launch_moments<double>(*O.t, r.first, (int)r.second, O.h.as<double>(), O.mom.as<double>(), s);
+                launch_moments<double>(*O.t, r.c0, (int)r.n, O.h.as<double>(), O.mom.as<double>(), s,
+                                       q && r.dim == 1);
         }
         k_set_rates<<<na, 32, 0, s>>>(O.ijobs.as<SisJobDev>(), O.act.as<int>(), O.mom.as<double>(),
                                       O.coef.as<double>(), O.states.as<JobState>());
         k_copy64<<<dim3(sm_count(), na), blk, 0, s>>>(O.h.as<double>(), h_old, O.sjobs.as<SweepJobDev>(),
-                                               O.act.as<int>(), n3);
+                                                     O.act.as<int>(), n3, q ? 1 : 0);
         g_launches += 2;
         // one FP64 SIS iteration: h = Phi(h_old), flags against the copy's flow rates
         O.active = active;
@@ -400,11 +490,13 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             if (plain[j] && rel > 0.9 * pr) rebase[j] = 1;  // plain steps stalled: re-centre the operator
             if (trace) {
                 const long o = O.cell_off[j] * n3, nn = (long)O.sj[j].ncell * n3;
+                const long per = q && O.geo[j].dim == 1 ? n3 / 4 : n3;  // values held per cell
                 std::vector<double> hh(nn), hb(nn);
                 cudaMemcpy(hh.data(), h_old + o, nn * 8, cudaMemcpyDeviceToHost);
-                cudaMemcpy(hb.data(), base_h + o, nn * 8, cudaMemcpyDeviceToHost);
+                cudaMemcpy(hb.data(), bq_h + o, nn * 8, cudaMemcpyDeviceToHost);
                 double dmax = 0, hmax = 0;
                 for (long k = 0; k < nn; ++k) {
+                    if (k % n3 >= per) continue;
                     dmax = std::max(dmax, std::fabs(hh[k] - hb[k]));
                     hmax = std::max(hmax, std::fabs(hh[k]));
                 }
@@ -418,18 +510,13 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         // correction solve for the unfinished problems (plain ones keep h = Phi(h_old))
         std::vector<int> corr, rb_plain;
         for (int j : active) (plain[j] ? rb_plain : corr).push_back(j);
-        for (int j : rb_plain) {
-            if (!rebase[j]) continue;
-            const long o = O.cell_off[j] * n3;
-            range_copy(O.h.as<double>() + o, base_h + o, (long)O.sj[j].ncell * n3, s);
-            fsm_df_apply(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o, base_lp + o,
-                                 base_lh + o, O.scratch.p, O.chunk, s, O.geo[j].dim == 1 ? 2 : 1);
-        }
+        for (int j : rb_plain)
+            if (rebase[j]) evaluate_base(j, j + 1);
         if (!corr.empty()) {
             const int nk = (int)corr.size();
             cudaMemcpyAsync(O.act.p, corr.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s);
             k_residual<<<dim3(sm_count(), nk), blk, 0, s>>>(O.h.as<double>(), h_old, r, O.sjobs.as<SweepJobDev>(),
-                                                           O.act.as<int>(), pbs[0].nv, I.quarter() ? 1 : 0);
+                                                           O.act.as<int>(), n3, q ? 1 : 0);
             g_launches += 1;
             for (int j : corr) {
                 cudaMemsetAsync(I.h.as<float>() + I.cell_off[j] * n3, 0, I.sj[j].ncell * n3 * 4, s);
@@ -449,16 +536,11 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             }
             cudaMemcpyAsync(O.act.p, corr.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s);
             k_apply_correction<<<dim3(sm_count(), nk), blk, 0, s>>>(h_old, I.h.as<float>(), O.h.as<double>(),
-                                                                   O.sjobs.as<SweepJobDev>(), O.act.as<int>(),
-                                                                   pbs[0].nv, I.quarter() ? 1 : 0);
+                                                                   O.sjobs.as<SweepJobDev>(), O.act.as<int>(), n3,
+                                                                   q ? 1 : 0);
             g_launches += 1;
-            for (int j : corr) {
-                if (!rebase[j]) continue;
-                const long o = O.cell_off[j] * n3;
-                range_copy(O.h.as<double>() + o, base_h + o, (long)O.sj[j].ncell * n3, s);
-                fsm_df_apply(*O.t, O.sj[j].ncell, O.delta.as<double>() + O.cell_off[j], base_h + o,
-                                     base_lp + o, base_lh + o, O.scratch.p, O.chunk, s, O.geo[j].dim == 1 ? 2 : 1);
-            }
+            for (int j : corr)
+                if (rebase[j]) evaluate_base(j, j + 1);
         }
         // drop problems that reached their iteration cap
         std::vector<int> keep2;
@@ -481,8 +563,18 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             st = cuda_status(c, cudaMemcpy(U3_out, O.U3.p, O.cells * 8, cudaMemcpyDeviceToHost), "U3");
             g_d2h += O.cells * 8;
         }
-        if (st == LBE_OK && h_out)
+        if (st == LBE_OK && h_out) {
             st = cuda_status(c, cudaMemcpy(h_out, O.h.p, vol64, cudaMemcpyDeviceToHost), "h");
+            if (st == LBE_OK && q) {  // plates back to the full grid
+                std::vector<double> hq;
+                for (int j = 0; j < n; ++j) {
+                    if (O.geo[j].dim != 1) continue;
+                    const long o = O.cell_off[j] * n3, nn = (long)O.sj[j].ncell * n3;
+                    hq.assign(h_out + o, h_out + o + nn);
+                    orbit_unpack_host(nv, O.sj[j].ncell, hq.data(), h_out + o);
+                }
+            }
+        }
     }
     return st != LBE_OK ? st : worst;
 }

@@ -335,7 +335,7 @@ static Bucket* get_bucket(Service& sv, Ctx* c, const lbe_problem& pb, int prec, 
     if (prec == LBE_FP64)
         nb->B.inc_tc = tc && inc;
     else
-        nb->B.use_tc = tc;
+        nb->B.use_tc = nb->B.orbit = tc;
     b = nb.get();
     sv.buckets.push_back(std::move(nb));
     return b;

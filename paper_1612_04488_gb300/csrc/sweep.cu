@@ -583,36 +583,57 @@ __global__ void __launch_bounds__(8 * NV) k_moments(const T* __restrict__ h, con
 // integrands are even under both reflections, so each is four times its sum over the stored
 // quarter; 2 v1 v2 v3 h is odd under R2 and sums to zero.  One thread per (j2, j3), the block
 // rounded up to whole warps.
-template <int NV>
-__global__ void __launch_bounds__(256) k_moments_q(const float* __restrict__ h, const float* __restrict__ vel,
-                                                   double dv3, long cell0, double* __restrict__ mom) {
-    __shared__ dfloat redx[32 * 4];
+template <typename T, int NV>
+__global__ void __launch_bounds__(256) k_moments_q(const T* __restrict__ h, const T* __restrict__ vel, double dv3,
+                                                   long cell0, double* __restrict__ mom) {
     constexpr int H = NV / 2;
     constexpr long n3 = (long)NV * NV * NV;
     const long cell = cell0 + blockIdx.x;
     const int p = threadIdx.x;
-    dfloat s[4] = {dfloat(0), dfloat(0), dfloat(0), dfloat(0)};
+    Acc<T> S0, S1;  // sums of h and v1^2 h over i1
+    T v2 = T(0), v3 = T(0);
     if (p < H * H) {
-        const int j2 = p / H, j3 = p % H;
-        const float* hc = h + cell * n3 + p;
-        Acc<float> S0, S1;  // sums of h and v1^2 h over i1
+        v2 = vel[p / H];
+        v3 = vel[p % H];
+        const T* hc = h + cell * n3 + p;
         for (int i1 = 0; i1 < NV; ++i1) {
-            const float v1 = vel[i1], x = hc[(long)i1 * H * H];
+            const T v1 = vel[i1], x = hc[(long)i1 * H * H];
             S0.add(x);
             S1.add(v1 * v1 * x);
         }
-        const float v2 = vel[j2];
-        const dfloat a0 = S0.pair(), a2 = S1.pair(), a3 = dfloat(v2 * v2, 0.f) * a0;
-        const dfloat w3(vel[j3], 0.f), w3s = w3 * w3;
-        s[0] = w3 * a0;
-        s[1] = w3 * ((a2 + a3) + (w3s - dfloat(2.5f, 0.f)) * a0);
-        s[2] = w3 * ((a2 + a2) - a0);
-        s[3] = w3 * ((a3 + a3) - a0);
     }
-    block_reduce_df<4>(s, redx);
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < 4; ++k) mom[cell * 5 + k] = 4.0 * (double)s[k] * dv3;
-        mom[cell * 5 + 4] = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        __shared__ dfloat redx[32 * 4];
+        dfloat s[4] = {dfloat(0), dfloat(0), dfloat(0), dfloat(0)};
+        if (p < H * H) {
+            const dfloat a0 = S0.pair(), a2 = S1.pair(), a3 = dfloat((float)(v2 * v2), 0.f) * a0;
+            const dfloat w3((float)v3, 0.f), w3s = w3 * w3;
+            s[0] = w3 * a0;
+            s[1] = w3 * ((a2 + a3) + (w3s - dfloat(2.5f, 0.f)) * a0);
+            s[2] = w3 * ((a2 + a2) - a0);
+            s[3] = w3 * ((a3 + a3) - a0);
+        }
+        block_reduce_df<4>(s, redx);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 4; ++k) mom[cell * 5 + k] = 4.0 * (double)s[k] * dv3;
+            mom[cell * 5 + 4] = 0.0;
+        }
+    } else {
+        __shared__ double red[32 * 4];
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        if (p < H * H) {
+            const double a0 = S0.value(), a2 = S1.value(), a3 = (double)v2 * (double)v2 * a0;
+            const double w3 = (double)v3;
+            s[0] = w3 * a0;
+            s[1] = w3 * (a2 + a3 + (w3 * w3 - 2.5) * a0);
+            s[2] = w3 * (2.0 * a2 - a0);
+            s[3] = w3 * (2.0 * a3 - a0);
+        }
+        block_reduce<4>(s, red);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 4; ++k) mom[cell * 5 + k] = 4.0 * s[k] * dv3;
+            mom[cell * 5 + 4] = 0.0;
+        }
     }
 }
 
@@ -788,7 +809,7 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
 // at the orbit's index), where the projection is the identity.  hh = NULL: only hm, of the h
 // already stored (a solve resumed from a checkpoint), with the same arithmetic.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_correct(const T* __restrict__ hh, T* __restrict__ h,
+__global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __restrict__ h,
                                                  const double* __restrict__ dU, const T* __restrict__ extra,
                                                  const T* __restrict__ feq,
                                                  const T* __restrict__ vel, const SweepJobDev* __restrict__ jobs,
@@ -1043,14 +1064,12 @@ void launch_moments(const DevTables& t, long cell0, int cells, const T* h, doubl
     g_launches += 1;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
     const double dv3 = t.dv * t.dv * t.dv;
-    if (quarter && sizeof(T) == 4) {
-        const float* hf = (const float*)h;
-        const float* vf = (const float*)vel;
+    if (quarter) {
         switch (t.nv) {
-            case 8: k_moments_q<8><<<cells, 32, 0, s>>>(hf, vf, dv3, cell0, mom); break;
-            case 16: k_moments_q<16><<<cells, 64, 0, s>>>(hf, vf, dv3, cell0, mom); break;
-            case 24: k_moments_q<24><<<cells, 160, 0, s>>>(hf, vf, dv3, cell0, mom); break;
-            default: k_moments_q<32><<<cells, 256, 0, s>>>(hf, vf, dv3, cell0, mom); break;
+            case 8: k_moments_q<T, 8><<<cells, 32, 0, s>>>(h, vel, dv3, cell0, mom); break;
+            case 16: k_moments_q<T, 16><<<cells, 64, 0, s>>>(h, vel, dv3, cell0, mom); break;
+            case 24: k_moments_q<T, 24><<<cells, 160, 0, s>>>(h, vel, dv3, cell0, mom); break;
+            default: k_moments_q<T, 32><<<cells, 256, 0, s>>>(h, vel, dv3, cell0, mom); break;
         }
         return;
     }
@@ -1073,16 +1092,15 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
 template <typename T>
 void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
                     const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state, double* hm,
-                    const double* nd, int quarter) {
+                    const double* nd, int quarter, int max_cells) {
     if (njobs <= 0) return;
     g_launches += 1;
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
-    // one block per cell (grid-stride over a job's cells), 1024 threads: a plate cell is
-    // 8192 orbits at 32^3
-    dim3 g(2 * sm_count(), njobs);
+    // one block per cell of the largest job (max_cells > 0), or a grid-stride loop over cells
+    dim3 g(max_cells > 0 ? max_cells : 2 * sm_count(), njobs);
     const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
-    k_correct<T><<<g, 1024, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1,
+    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1,
                                    t.dv * t.dv * t.dv, quarter);
 }
 
@@ -1094,9 +1112,9 @@ template void launch_moments<double>(const DevTables&, long, int, const double*,
 template void launch_moments<float>(const DevTables&, long, int, const float*, double*, cudaStream_t, int);
 template void launch_correct<double>(const DevTables&, int, const double*, double*, const double*,
                                      const double*, const SweepJobDev*, const int*, cudaStream_t, const JobState*,
-                                     double*, const double*, int);
+                                     double*, const double*, int, int);
 template void launch_correct<float>(const DevTables&, int, const float*, float*, const double*, const float*,
                                     const SweepJobDev*, const int*, cudaStream_t, const JobState*, double*,
-                                    const double*, int);
+                                    const double*, int, int);
 
 }  // namespace lbe

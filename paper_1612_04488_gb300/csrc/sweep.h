@@ -13,8 +13,7 @@ struct Ctx;
 // fsm_dense.cu: tensor-core operator on the parity subspace (float in / out; mode 1 or 2)
 // hm (may be NULL): per cell the h part of G (launch_correct); with it and without Lout the
 // expand reads no h.
-// quarter (mode 2 only): h and Lplus in the orbit layout (below); then Lout must be NULL, and
-// G needs hm.
+// quarter (mode 2 only): h, Lplus and Lout in the orbit layout (below); G needs hm and no Lout.
 lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h,
                         float* Lplus, float* Lout, cudaStream_t s, bool sync = true, const double* nd = nullptr,
                         double* G = nullptr, const double* hm = nullptr, bool quarter = false);
@@ -80,7 +79,7 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
 template <typename T>
 void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
                     const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state = nullptr,
-                    double* hm = nullptr, const double* nd = nullptr, int quarter = 0);
+                    double* hm = nullptr, const double* nd = nullptr, int quarter = 0, int max_cells = 0);
 
 // fsm_cc.cu
 void init_twiddles_cc();
@@ -93,6 +92,6 @@ lbe_status fsm_df_apply(const DevTables& t, int cells, const double* delta, cons
                         double* Lout, void* scratch, int chunk, cudaStream_t s, int mode = 0);
 template <typename T>
 void lmoments(const DevTables& t, int cells, const T* Lh, const T* h, const double* nd, double* G,
-              cudaStream_t s);
+              cudaStream_t s, int quarter = 0);
 
 }  // namespace lbe
