@@ -247,6 +247,24 @@ DevTables* get_tables(Ctx* c, int nv, double vmax, int M, double R, lbe_status* 
     if (s == LBE_OK) s = upload(c, &t->mult_f, to_f(h.mult), &b);
     if (s == LBE_OK) s = upload(c, &t->ab_f, to_f(h.ab), &b);
     if (s == LBE_OK) s = upload(c, &t->vel_f, to_f(h.v), &b);
+    if (s == LBE_OK) {  // orbit constants of the plate parity (the correction step)
+        const int H = nv / 2;
+        std::vector<float> orb((size_t)nv * H * H * 4, 0.f);
+        for (int i1 = 0; i1 < nv; ++i1)
+            for (int j2 = 0; j2 < H; ++j2)
+                for (int j3 = 0; j3 < H; ++j3) {
+                    const long q = ((long)i1 * H + j2) * H + j3;
+                    const long va = ((long)i1 * nv + j2) * nv + j3, vb = ((long)i1 * nv + nv - 1 - j2) * nv + j3;
+                    const long vc = ((long)i1 * nv + j2) * nv + nv - 1 - j3;
+                    const long vd = ((long)i1 * nv + nv - 1 - j2) * nv + nv - 1 - j3;
+                    orb[4 * q + 0] = (float)(h.v[j3] * h.feq[va]);
+                    orb[4 * q + 1] = (float)(h.v[i1] * h.v[j3]);
+                    orb[4 * q + 2] = (float)(h.nu1[va] + h.nu1[vb] + h.nu1[vc] + h.nu1[vd]);
+                }
+        float* of = nullptr;
+        s = upload(c, &of, orb, &b);
+        t->orb_f = reinterpret_cast<float4*>(of);
+    }
     if (s == LBE_OK) s = upload(c, &t->feq_x, to_df(h.feq), &b);
     if (s == LBE_OK) s = upload(c, &t->nu1_x, to_df(h.nu1), &b);
     if (s == LBE_OK) s = upload(c, &t->mult_x, to_df(h.mult), &b);
@@ -256,7 +274,7 @@ DevTables* get_tables(Ctx* c, int nv, double vmax, int M, double R, lbe_status* 
     if (s != LBE_OK) {  // give back what was uploaded before the failure
         for (void* p : {(void*)t->feq_d, (void*)t->nu1_d, (void*)t->mult_d, (void*)t->ab_d, (void*)t->vel_d,
                         (void*)t->feq_f, (void*)t->nu1_f, (void*)t->mult_f, (void*)t->ab_f, (void*)t->vel_f,
-                        (void*)t->feq_x, (void*)t->nu1_x, (void*)t->mult_x, (void*)t->ab_x})
+                        (void*)t->orb_f, (void*)t->feq_x, (void*)t->nu1_x, (void*)t->mult_x, (void*)t->ab_x})
             if (p) cudaFree(p);
         c->used -= std::min(b, c->used);
         delete t->tuning;
@@ -580,7 +598,7 @@ void batch_iterate(Batch& B, bool upload, bool read) {
     launch_correct<T>(t, na, hh, h, B.dU.as<double>(), B.extra.p ? B.extra.as<T>() : nullptr,
                       B.sjobs.as<SweepJobDev>(), dact, s, B.states.as<JobState>(),
                       (sizeof(T) == 4 && B.use_tc) ? B.hmom.as<double>() : nullptr, B.nd.as<double>(),
-                      B.quarter() ? 1 : 0, max_cells);
+                      B.quarter() ? 1 : 0, max_cells, act2.empty() ? 0 : 1);
     if (read) {
         cudaMemcpyAsync(B.hstate.data(), B.states.p, B.njobs * sizeof(JobState), cudaMemcpyDeviceToHost, s);
         g_d2h += B.njobs * sizeof(JobState);
@@ -797,7 +815,7 @@ lbe_status lbe_destroy(lbe_ctx* ctx) {
         t->tuning = nullptr;
         for (void* p : {(void*)t->feq_d, (void*)t->nu1_d, (void*)t->mult_d, (void*)t->ab_d, (void*)t->vel_d,
                         (void*)t->feq_f, (void*)t->nu1_f, (void*)t->mult_f, (void*)t->ab_f, (void*)t->vel_f,
-                        (void*)t->feq_x, (void*)t->nu1_x, (void*)t->mult_x, (void*)t->ab_x})
+                        (void*)t->orb_f, (void*)t->feq_x, (void*)t->nu1_x, (void*)t->mult_x, (void*)t->ab_x})
             if (p) cudaFree(p);
     }
     ctx->tables.clear();
@@ -873,7 +891,7 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
             cudaMemcpyAsync(B.act.p, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
             launch_correct<float>(*B.t, 1, nullptr, B.h.as<float>(), nullptr, nullptr, B.sjobs.as<SweepJobDev>(),
                                   B.act.as<int>(), ctx->stream, nullptr, B.hmom.as<double>(), B.nd.as<double>(),
-                                  B.quarter() ? 1 : 0);
+                                  B.quarter() ? 1 : 0, 0, B.geo[0].dim == 2 ? 1 : 0);
         }
         if (prev) {  // the flow rates the interrupted run held
             B.hstate[0].M = prev->mass_flow;

@@ -781,16 +781,22 @@ __global__ void __launch_bounds__(256) k_expand_q(const float* __restrict__ Y, c
                                                      double* __restrict__ G, double dv3,
                                                      const double* __restrict__ hm, const float* __restrict__ h,
                                                      const float* __restrict__ nu1, float* __restrict__ Lout) {
-    extern __shared__ float sY[];
+    extern __shared__ __align__(16) float sY[];
     __shared__ dfloat redx[32 * 2];
     constexpr int H = NV / 2;
     constexpr SubLayout L = sub_layout(NV, 2);  // S0, A0 (block 0), F1 (block 1)
     constexpr long n3 = (long)NV * NV * NV;
     const long c = blockIdx.x;
     const float* yc = Y + c * (long)L.rows;
+    // the cell's sub-block outputs into shared memory, 16 bytes per asynchronous copy, all in
+    // flight at once (every sub-block's length and offsets are multiples of 4 floats)
 #pragma unroll
     for (int q = 0; q < L.count; ++q)
-        for (int k = threadIdx.x; k < L.n[q]; k += blockDim.x) sY[L.soff[q] + k] = yc[L.roff[q] + k];
+        for (int k = 4 * threadIdx.x; k < L.n[q]; k += 4 * blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sY + L.soff[q] + k)),
+                         "l"(yc + L.roff[q] + k)
+                         : "memory");
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     const float d = (float)delta[c];
     float a0 = 0.f, c0 = 0.f;  // compensated sum of v1 v3 L+ h

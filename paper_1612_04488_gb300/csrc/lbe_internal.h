@@ -61,6 +61,9 @@ struct DevTables {
     // float
     float* feq_f = nullptr; float* nu1_f = nullptr; float* mult_f = nullptr; float* ab_f = nullptr;
     float* vel_f = nullptr;
+    // per orbit of the plate parity (orbit layout, sweep.h): {v3 f_eq, v1 v3, the sum of
+    // nu_eq over the orbit's four points, 0} at its representative
+    float4* orb_f = nullptr;
     // double-float (hi, lo float pairs; complex tables as re.hi, re.lo, im.hi, im.lo)
     float* feq_x = nullptr; float* nu1_x = nullptr; float* mult_x = nullptr; float* ab_x = nullptr;
     TcOperands* tc = nullptr;

@@ -676,38 +676,85 @@ __global__ void __launch_bounds__(256) k_sis_update(const SisJobDev* __restrict_
     if (jb.scheme == 0) {  // CIS: no correction
         for (int c = threadIdx.x; c < n; c += blockDim.x) du[c] = 0.0;
     } else if (jb.dim == 1) {
-        // the march is serial: the block stages 256 nodes at a time in shared memory and
-        // thread 0 walks them
-        __shared__ double sfa[256], sfb[256], sfc[256], srhs[256], sW[256], sU[256];
-        const double* fa = coef + jb.coef_off;  // block [1/fa | fb | fc | x], n each
-        const double* fb = fa + n;
-        const double* fc = fb + n;
-        const double* xs = fc + n;
-        double ym2 = 0.0, ym1 = m[0] + m[2];
-        if (threadIdx.x == 0) du[0] = 0.0;  // U(x0) = U^(k+1/2)(x0)
-        for (int w0 = 1; w0 < n; w0 += 256) {
-            const int i = w0 + threadIdx.x;
-            __syncthreads();
-            if (i < n) {
-                sfa[threadIdx.x] = fa[i];
-                sfb[threadIdx.x] = fb[i];
-                sfc[threadIdx.x] = fc[i];
-                srhs[threadIdx.x] = -jb.ndsig * xs[i] + G[(c0 + i) * 2];
-                sW[threadIdx.x] = m[i * 5 + 2];
-                sU[threadIdx.x] = m[i * 5 + 0];
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const int wn = min(256, n - w0);
-                for (int k = 0; k < wn; ++k) {
-                    const int ii = w0 + k;
-                    double r = srhs[k] - sfb[k] * ym1;
-                    if (ii >= 2) r -= sfc[k] * ym2;
-                    const double yi = r * sfa[k];
-                    du[ii] = (yi - sW[k]) - sU[k];
-                    ym2 = ym1;
-                    ym1 = yi;
+        // The march y_i = (rhs_i - fb_i y_(i-1) - fc_i y_(i-2)) / fa_i (coefficient block
+        // [1/fa | fb | fc | x]) is the affine map Y_i = A_i Y_(i-1) + b_i of Y_i = (y_i, y_(i-1)),
+        // A_i = [[-fb_i / fa_i, -fc_i / fa_i], [1, 0]], b_i = (rhs_i / fa_i, 0), from
+        // Y_0 = (U(x0) + W(x0), 0).  Warp 0 runs it as a scan, 128 nodes per pass: each lane
+        // composes the maps of its 4 consecutive nodes, a shuffle scan composes them across the
+        // lanes, and each lane applies its exclusive prefix to the carried state and walks its
+        // nodes.  du_i = y_i - W_i - U_i.
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            const double* fa = coef + jb.coef_off;
+            const double* fb = fa + n;
+            const double* fc = fb + n;
+            const double* xs = fc + n;
+            double s0y = m[0] + m[2], s1y = 0.0;  // the carried state Y_(s-1)
+            if (lane == 0) du[0] = 0.0;
+            for (int s0 = 1; s0 < n; s0 += 128) {
+                const int e0 = s0 + 4 * lane;
+                double ia[4], ib[4], ir[4];  // -fb / fa, -fc / fa, rhs / fa of the lane's nodes
+                double a00 = 1.0, a01 = 0.0, a10 = 0.0, a11 = 1.0, b0 = 0.0, b1 = 0.0;  // identity
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = e0 + k;
+                    if (i < n) {
+                        const double f = fa[i];
+                        ia[k] = -fb[i] * f;
+                        ib[k] = i >= 2 ? -fc[i] * f : 0.0;
+                        ir[k] = (-jb.ndsig * xs[i] + G[(c0 + i) * 2]) * f;
+                        // (A_i, b_i) after the maps so far
+                        const double n00 = ia[k] * a00 + ib[k] * a10, n01 = ia[k] * a01 + ib[k] * a11;
+                        const double nb0 = ia[k] * b0 + ib[k] * b1 + ir[k];
+                        a10 = a00;
+                        a11 = a01;
+                        b1 = b0;
+                        a00 = n00;
+                        a01 = n01;
+                        b0 = nb0;
+                    }
                 }
+                // inclusive scan over the lanes: this lane's maps after those of the lanes below
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const double p00 = __shfl_up_sync(0xffffffffu, a00, off), p01 = __shfl_up_sync(0xffffffffu, a01, off);
+                    const double p10 = __shfl_up_sync(0xffffffffu, a10, off), p11 = __shfl_up_sync(0xffffffffu, a11, off);
+                    const double q0 = __shfl_up_sync(0xffffffffu, b0, off), q1 = __shfl_up_sync(0xffffffffu, b1, off);
+                    if (lane >= off) {
+                        const double n00 = a00 * p00 + a01 * p10, n01 = a00 * p01 + a01 * p11;
+                        const double n10 = a10 * p00 + a11 * p10, n11 = a10 * p01 + a11 * p11;
+                        const double nb0 = a00 * q0 + a01 * q1 + b0, nb1 = a10 * q0 + a11 * q1 + b1;
+                        a00 = n00;
+                        a01 = n01;
+                        a10 = n10;
+                        a11 = n11;
+                        b0 = nb0;
+                        b1 = nb1;
+                    }
+                }
+                // state before this lane's nodes: the exclusive prefix applied to the carry
+                const double e00 = __shfl_up_sync(0xffffffffu, a00, 1), e01 = __shfl_up_sync(0xffffffffu, a01, 1);
+                const double e10 = __shfl_up_sync(0xffffffffu, a10, 1), e11 = __shfl_up_sync(0xffffffffu, a11, 1);
+                const double f0 = __shfl_up_sync(0xffffffffu, b0, 1), f1 = __shfl_up_sync(0xffffffffu, b1, 1);
+                double y1 = s0y, y2 = s1y;
+                if (lane > 0) {
+                    y1 = e00 * s0y + e01 * s1y + f0;
+                    y2 = e10 * s0y + e11 * s1y + f1;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = e0 + k;
+                    if (i < n) {
+                        const double yi = ia[k] * y1 + ib[k] * y2 + ir[k];
+                        du[i] = (yi - m[i * 5 + 2]) - m[i * 5 + 0];
+                        y2 = y1;
+                        y1 = yi;
+                    }
+                }
+                // the next pass starts from the state after all 128 nodes (lane 31's prefix)
+                const double n0 = a00 * s0y + a01 * s1y + b0, n1 = a10 * s0y + a11 * s1y + b1;
+                s0y = __shfl_sync(0xffffffffu, n0, 31);
+                s1y = __shfl_sync(0xffffffffu, n1, 31);
             }
         }
     } else {
@@ -823,6 +870,7 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
     const SweepJobDev jb = jobs[jid];
     const int n3 = nv * nv * nv, hv = nv / 2;
     const bool plates = jb.ny == 0;  // 1D: orbits {1, R2, R3, R2R3}; 2D: {1, R3}
+    if (plates && quarter == 2) return;  // plates done by k_correct_q
     const int norb = plates ? n3 / 4 : n3 / 2;
     const bool only_hm = hh == nullptr;  // hm of the stored h alone (a resumed solve); h unchanged
     for (int c = blockIdx.x; c < jb.ncell; c += gridDim.x) {
@@ -938,6 +986,82 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
             if (threadIdx.x == 0) {
                 hm[2 * (jb.cell_off + c) + 0] = 2.0 * (double)sm[0] * dv3;
                 hm[2 * (jb.cell_off + c) + 1] = 2.0 * (double)sm[1] * dv3;
+            }
+        }
+    }
+}
+
+// The correction step for plates in the orbit layout (float): the orbit's one stored value at
+// index r, y = hh + extra + 2 dU v3 f_eq, and the h part of the L-moments from the orbit
+// constants orb = {v3 f_eq, v1 v3, sum of nu_eq over the orbit}: the orbit's four points carry
+// v1 v3 y (N delta - delta nu) each, so Gh_1 = 2 sum_orbits v1 v3 y (4 N delta - delta sum nu)
+// dv^3; Gh_2 = 0 (odd under R2).  hh = NULL: only hm, of the stored h (a resumed solve).  Grid
+// sizes are compile-time constants; four orbits per thread and pass with their loads issued
+// together.
+template <int NV>
+__global__ void __launch_bounds__(256) k_correct_q(const float* __restrict__ hh, float* __restrict__ h,
+                                                   const double* __restrict__ dU, const float* __restrict__ extra,
+                                                   const float4* __restrict__ orb,
+                                                   const SweepJobDev* __restrict__ jobs,
+                                                   const int* __restrict__ active,
+                                                   const JobState* __restrict__ state, double* __restrict__ hm,
+                                                   const double* __restrict__ nd, double dv3) {
+    constexpr int H = NV / 2, NQ = NV * H * H;
+    constexpr long n3 = (long)NV * NV * NV;
+    __shared__ dfloat redx[32 * 2];
+    const int jid = active ? active[blockIdx.y] : blockIdx.y;
+    if (state && state[jid].skip) return;
+    const SweepJobDev jb = jobs[jid];
+    if (jb.ny != 0) return;  // plates only
+    const bool only_hm = hh == nullptr;
+    for (int c = blockIdx.x; c < jb.ncell; c += gridDim.x) {
+        const long g0 = (jb.cell_off + c) * n3;
+        const float d = only_hm ? 0.f : (float)(2.0 * dU[jb.cell_off + c]);
+        const float* src = only_hm ? nullptr : hh + g0;
+        float* dst = h + g0;
+        const float* ex = extra ? extra + g0 : nullptr;
+        const float ndc4 = hm ? 4.f * (float)nd[jb.cell_off + c] : 0.f, dl = (float)jb.delta;
+        float a0 = 0.f, c0 = 0.f;
+        for (int r0 = threadIdx.x; r0 < NQ; r0 += 4 * 256) {
+            float x[4];
+            float4 o[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int r = r0 + k * 256;
+                if (r < NQ) {
+                    x[k] = only_hm ? dst[r] : src[r];
+                    o[k] = orb[r];
+                }
+            }
+            if (ex && !only_hm)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int r = r0 + k * 256;
+                    if (r < NQ) x[k] += ex[r];
+                }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int r = r0 + k * 256;
+                if (r >= NQ) break;
+                float y = x[k];
+                if (!only_hm) {
+                    y = x[k] + d * o[k].x;
+                    dst[r] = y;
+                }
+                if (hm) {
+                    const float v = o[k].y * y * (ndc4 - dl * o[k].z) - c0;
+                    const float t = a0 + v;
+                    c0 = (t - a0) - v;
+                    a0 = t;
+                }
+            }
+        }
+        if (hm) {
+            dfloat sm[2] = {df_fast2sum(a0, -c0), dfloat(0)};
+            block_reduce_df<2>(sm, redx);
+            if (threadIdx.x == 0) {
+                hm[2 * (jb.cell_off + c) + 0] = 2.0 * (double)sm[0] * dv3;
+                hm[2 * (jb.cell_off + c) + 1] = 0.0;
             }
         }
     }
@@ -1092,7 +1216,7 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
 template <typename T>
 void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
                     const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state, double* hm,
-                    const double* nd, int quarter, int max_cells) {
+                    const double* nd, int quarter, int max_cells, int ducts) {
     if (njobs <= 0) return;
     g_launches += 1;
     const T* feq = sizeof(T) == 8 ? (const T*)t.feq_d : (const T*)t.feq_f;
@@ -1100,8 +1224,23 @@ void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const doub
     // one block per cell of the largest job (max_cells > 0), or a grid-stride loop over cells
     dim3 g(max_cells > 0 ? max_cells : 2 * sm_count(), njobs);
     const T* nu1 = sizeof(T) == 8 ? (const T*)t.nu1_d : (const T*)t.nu1_f;
-    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1,
-                                   t.dv * t.dv * t.dv, quarter);
+    const double dv3 = t.dv * t.dv * t.dv;
+    if (sizeof(T) == 4 && quarter) {  // plates by the orbit kernel, then any ducts
+        const float* hf = (const float*)hh;
+        float* h_ = (float*)h;
+        const float* ef = (const float*)extra;
+        switch (t.nv) {
+            case 8: k_correct_q<8><<<g, 256, 0, s>>>(hf, h_, dU, ef, t.orb_f, jobs, active, state, hm, nd, dv3); break;
+            case 16: k_correct_q<16><<<g, 256, 0, s>>>(hf, h_, dU, ef, t.orb_f, jobs, active, state, hm, nd, dv3); break;
+            case 24: k_correct_q<24><<<g, 256, 0, s>>>(hf, h_, dU, ef, t.orb_f, jobs, active, state, hm, nd, dv3); break;
+            default: k_correct_q<32><<<g, 256, 0, s>>>(hf, h_, dU, ef, t.orb_f, jobs, active, state, hm, nd, dv3); break;
+        }
+        if (!ducts) return;
+        g_launches += 1;
+        k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1, dv3, 2);
+        return;
+    }
+    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1, dv3, quarter);
 }
 
 template void launch_sweep<double>(const DevTables&, int, int, int, const double*, double*,
@@ -1112,9 +1251,9 @@ template void launch_moments<double>(const DevTables&, long, int, const double*,
 template void launch_moments<float>(const DevTables&, long, int, const float*, double*, cudaStream_t, int);
 template void launch_correct<double>(const DevTables&, int, const double*, double*, const double*,
                                      const double*, const SweepJobDev*, const int*, cudaStream_t, const JobState*,
-                                     double*, const double*, int, int);
+                                     double*, const double*, int, int, int);
 template void launch_correct<float>(const DevTables&, int, const float*, float*, const double*, const float*,
                                     const SweepJobDev*, const int*, cudaStream_t, const JobState*, double*,
-                                    const double*, int, int);
+                                    const double*, int, int, int);
 
 }  // namespace lbe

@@ -79,7 +79,8 @@ void launch_sis_update(const DevTables& t, int njobs, const SisJobDev* jobs, con
 template <typename T>
 void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const double* dU, const T* extra,
                     const SweepJobDev* jobs, const int* active, cudaStream_t s, const JobState* state = nullptr,
-                    double* hm = nullptr, const double* nd = nullptr, int quarter = 0, int max_cells = 0);
+                    double* hm = nullptr, const double* nd = nullptr, int quarter = 0, int max_cells = 0,
+                    int ducts = 1);
 
 // fsm_cc.cu
 void init_twiddles_cc();
