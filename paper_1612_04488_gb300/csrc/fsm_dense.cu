@@ -31,10 +31,12 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -1373,6 +1375,17 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     if (plan.cs == 0) {
         auto it = T.cs_choice.find(cs_key);
         if (it != T.cs_choice.end()) plan.cs = it->second;
+    }
+    if (plan.cs == 0) {
+        // LBE_GEMM_FORM fixes the form instead of timing them (for profilers, whose own overhead
+        // distorts the timing): "persistent", or a cluster size 1, 2 or 4 the work list allows
+        static const char* forced = std::getenv("LBE_GEMM_FORM");
+        if (forced) {
+            const std::string f(forced);
+            int want = f == "persistent" ? kPersistent : (f == "1" || f == "2" || f == "4" ? std::stoi(f) : 0);
+            if (want > 1 && want != kPersistent && plan.group % want != 0) want = 0;
+            if (want) plan.cs = want;
+        }
     }
     if (plan.cs == 0) {
         // autotuner: each cluster size the work list allows, twice in turn (every one computes
