@@ -47,7 +47,11 @@ namespace lbe {
 
 namespace {
 
-constexpr int kBM = 128, kBK = 32;
+// kBK: K depth of one stage.  The operands are stored interleaved, [row][slice][hi 32 | lo 32]
+// bf16, so one 128-byte row of a TMA box carries a slice's hi and lo halves.
+constexpr int kBM = 128, kBK = 32, kRowB = 4 * kBK, kHalfB = 2 * kBK;
+// index of the hi half of logical column col in an interleaved row (the lo half is 32 further)
+__host__ __device__ inline long ilv(long col) { return (col / kBK) * 2 * kBK + col % kBK; }
 constexpr int kSmemMax = 232448;  // opt-in dynamic shared memory per block
 constexpr int kTmemCols = 256;    // accumulator columns allocated (power of two >= BN)
 
@@ -175,15 +179,16 @@ __device__ __forceinline__ void emit_chunk(const float (&v)[W], int c0, int r, i
     }
 }
 
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 32 bf16), 8-row groups
-// 512 B apart.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle (rows of 64 bf16: the hi and lo
+// halves of one 32-deep K slice side by side), 8-row groups 1024 B apart.  A start address
+// 32, 64 or 96 bytes into the row selects the K16 step and the half.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)(16 >> 4) << 16;   // leading byte offset (unused by swizzled K-major)
-    d |= (uint64_t)(512 >> 4) << 32;  // stride byte offset
-    d |= (uint64_t)1 << 46;           // descriptor version
-    d |= (uint64_t)4 << 61;           // 64-byte swizzle
+    d |= (uint64_t)(16 >> 4) << 16;    // leading byte offset (unused by swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
     return d;
 }
 
@@ -210,11 +215,10 @@ struct GemmWork {
 
 template <int BN>
 __global__ void __launch_bounds__(128, 1)
-    k_dense_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-                 const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl, int Mrows,
+    k_dense_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int Mrows,
                  int ncols, const GemmWork* __restrict__ work, float* __restrict__ Y, float* __restrict__ P,
                  int* __restrict__ err, int probe, int cs) {
-    constexpr int A_BYTES = kBM * kBK * 2, X_BYTES = BN * kBK * 2, STAGE = 2 * A_BYTES + 2 * X_BYTES;
+    constexpr int A_BYTES = kBM * kRowB, X_BYTES = BN * kRowB, STAGE = A_BYTES + X_BYTES;
     constexpr int kStages = GemmCfg<BN>::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -256,19 +260,16 @@ __global__ void __launch_bounds__(128, 1)
 
     if (tid == 0) {
         auto issue = [&](int kt, int s) {  // slice kt of this CTA's K range into stage s
-            const int x = (kt0 + kt) * kBK;
+            const int x = (kt0 + kt) * 2 * kBK;  // the slice's hi | lo pair in the interleaved rows
             uint8_t* st = base + s * STAGE;
             mbar_expect_tx(&full[s], STAGE);  // the whole stage lands here, A from every CTA
             if (cs == 1) {
-                tma_load_2d(st, &tmAh, x, row0, &full[s]);
-                tma_load_2d(st + A_BYTES, &tmAl, x, row0, &full[s]);
+                tma_load_2d(st, &tmA, x, row0, &full[s]);
             } else {
                 const int rows = kBM / cs, off = (int)rank * rows;  // this CTA's slice of the A rows
-                tma_load_2d_mc(st + off * kBK * 2, &tmAh, x, row0 + off, &full[s], cmask);
-                tma_load_2d_mc(st + A_BYTES + off * kBK * 2, &tmAl, x, row0 + off, &full[s], cmask);
+                tma_load_2d_mc(st + off * kRowB, &tmA, x, row0 + off, &full[s], cmask);
             }
-            tma_load_2d(st + 2 * A_BYTES, &tmXh, x, xrow0, &full[s]);
-            tma_load_2d(st + 2 * A_BYTES + X_BYTES, &tmXl, x, xrow0, &full[s]);
+            tma_load_2d(st + A_BYTES, &tmX, x, xrow0, &full[s]);
         };
         int issued = 0;
         for (int s = 0; s < kStages && s < KT; ++s) issue(s, s), ++issued;
@@ -284,13 +285,13 @@ __global__ void __launch_bounds__(128, 1)
             }
             ++consumed;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ah = smem_u32(base + s * STAGE), al = ah + A_BYTES, xh = al + A_BYTES, xl = xh + X_BYTES;
+            const uint32_t ah = smem_u32(base + s * STAGE), al = ah + kHalfB, xh = ah + A_BYTES, xl = xh + kHalfB;
 #pragma unroll
             for (int k = 0; k < kBK / 16; ++k) {
-                const uint32_t o = 32 * k;  // 16 bf16 along K inside the 64-byte swizzled row
-                mma_bf16(tmem, sdesc_sw64(ah + o), sdesc_sw64(xh + o), IDESC, (kt > 0 || k > 0) ? 1u : 0u);
-                mma_bf16(tmem, sdesc_sw64(al + o), sdesc_sw64(xh + o), IDESC, 1u);
-                mma_bf16(tmem, sdesc_sw64(ah + o), sdesc_sw64(xl + o), IDESC, 1u);
+                const uint32_t o = 32 * k;  // 16 bf16 along K inside the row's hi or lo half
+                mma_bf16(tmem, sdesc_sw128(ah + o), sdesc_sw128(xh + o), IDESC, (kt > 0 || k > 0) ? 1u : 0u);
+                mma_bf16(tmem, sdesc_sw128(al + o), sdesc_sw128(xh + o), IDESC, 1u);
+                mma_bf16(tmem, sdesc_sw128(ah + o), sdesc_sw128(xl + o), IDESC, 1u);
             }
             if (cs > 1)
                 mma_commit_mc(&empty[s], cmask);
@@ -374,11 +375,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
-    k_dense_gemm_ws(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-                    const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl, int Mrows,
+    k_dense_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int Mrows,
                     int ncols, const GemmWork* __restrict__ work, const int* __restrict__ cta_off,
                     float* __restrict__ Y, float* __restrict__ P, int* __restrict__ err, int probe) {
-    constexpr int A_BYTES = kBM * kBK * 2, X_BYTES = BN * kBK * 2, STAGE = 2 * A_BYTES + 2 * X_BYTES;
+    constexpr int A_BYTES = kBM * kRowB, X_BYTES = BN * kRowB, STAGE = A_BYTES + X_BYTES;
     constexpr int kStages = GemmCfg<BN>::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -432,13 +432,11 @@ __global__ void __launch_bounds__(192, 1)
                         ok = false;
                         break;
                     }
-                    const int x = kt * kBK;
+                    const int x = kt * 2 * kBK;  // the slice's hi | lo pair in the interleaved rows
                     uint8_t* st = base + s * STAGE;
                     mbar_expect_tx(&full[s], STAGE);
-                    tma_load_2d(st, &tmAh, x, wk.row0, &full[s]);
-                    tma_load_2d(st + A_BYTES, &tmAl, x, wk.row0, &full[s]);
-                    tma_load_2d(st + 2 * A_BYTES, &tmXh, x, wk.xrow0, &full[s]);
-                    tma_load_2d(st + 2 * A_BYTES + X_BYTES, &tmXl, x, wk.xrow0, &full[s]);
+                    tma_load_2d(st, &tmA, x, wk.row0, &full[s]);
+                    tma_load_2d(st + A_BYTES, &tmX, x, wk.xrow0, &full[s]);
                     n_issued = g + 1;
                 }
             }
@@ -471,14 +469,14 @@ __global__ void __launch_bounds__(192, 1)
                     }
                     n_consumed = g + 1;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t ah = smem_u32(base + s * STAGE), al = ah + A_BYTES, xh = al + A_BYTES,
-                                   xl = xh + X_BYTES;
+                    const uint32_t ah = smem_u32(base + s * STAGE), al = ah + kHalfB, xh = ah + A_BYTES,
+                                   xl = xh + kHalfB;
 #pragma unroll
                     for (int k = 0; k < kBK / 16; ++k) {
                         const uint32_t o = 32 * k;
-                        mma_bf16(acc, sdesc_sw64(ah + o), sdesc_sw64(xh + o), IDESC, (kt > 0 || k > 0) ? 1u : 0u);
-                        mma_bf16(acc, sdesc_sw64(al + o), sdesc_sw64(xh + o), IDESC, 1u);
-                        mma_bf16(acc, sdesc_sw64(ah + o), sdesc_sw64(xl + o), IDESC, 1u);
+                        mma_bf16(acc, sdesc_sw128(ah + o), sdesc_sw128(xh + o), IDESC, (kt > 0 || k > 0) ? 1u : 0u);
+                        mma_bf16(acc, sdesc_sw128(al + o), sdesc_sw128(xh + o), IDESC, 1u);
+                        mma_bf16(acc, sdesc_sw128(ah + o), sdesc_sw128(xl + o), IDESC, 1u);
                     }
                     mma_commit(&empty[s]);
                 }
@@ -589,7 +587,8 @@ __host__ __device__ inline bool blk_neg(int b, int mode, bool m1, bool m2, bool 
     return neg & 1;
 }
 
-// x of every sub-block (hi / lo bf16, [sub-block][cpad][npmax]) from h (float).  Block
+// x of every sub-block (hi / lo bf16 interleaved per 32-column slice, [sub-block][cpad][2 npmax])
+// from h (float).  Block
 // coefficients: the signed average of h over the reflections that the parity leaves free --
 // plates x_b = (h(p) +- h(R1 p)) / 2, ducts x_b = (h(p) +- h(R1 p) +- h(R2 p) +- h(R1 R2 p)) / 4;
 // halves: (x_b(a, b) +- x_b(b, a)) / 2.  Each thread takes one unordered pair a <= b of (j1, j2)
@@ -598,20 +597,19 @@ __host__ __device__ inline bool blk_neg(int b, int mode, bool m1, bool m2, bool 
 // quarter (plates): h in the orbit layout, where the points read (i2, i3 < nv / 2) are stored
 // at (i1 nv / 2 + i2) nv / 2 + i3.
 template <int NV, int MODE>
-__global__ void __launch_bounds__(256) k_gather_sub(const float* __restrict__ h, __nv_bfloat162* __restrict__ xh,
-                                                    __nv_bfloat162* __restrict__ xl, int cells, int cpad,
-                                                    int quarter) {
+__global__ void __launch_bounds__(256) k_gather_sub(const float* __restrict__ h, __nv_bfloat162* __restrict__ xo,
+                                                    int cells, int cpad, int quarter) {
     constexpr int H = NV / 2, NBLK = MODE == 2 ? 2 : 4, NPAIR = H * (H + 1) / 2;
     const int rs = MODE == 2 && quarter ? H : NV;  // row length and rows per plane of the data
     constexpr SubLayout L = sub_layout(NV, MODE);
     constexpr long N3 = (long)NV * NV * NV;
     const long total = (long)cells * NPAIR * (H / 2);
-    auto put = [&](int k, long c, int idx, float2 v) {
-        const long o = (((long)k * cpad + c) * L.npmax + idx) / 2;
+    auto put = [&](int k, long c, int idx, float2 v) {  // idx even: the pair stays in one slice
+        const long o = (((long)k * cpad + c) * 2 * L.npmax + ilv(idx)) / 2;
         const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
         const float2 hf = __bfloat1622float2(hi);
-        xh[o] = hi;
-        xl[o] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+        xo[o] = hi;
+        xo[o + kBK / 2] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
     };
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < total; k += (long)gridDim.x * blockDim.x) {
         const long c = k / (NPAIR * (H / 2));
@@ -670,9 +668,9 @@ __global__ void __launch_bounds__(256) k_gather_sub(const float* __restrict__ h,
             r -= (L.np[q] - L.n[q]) / 2;
             ++q;
         }
-        const long o = (((long)q * cpad + c) * L.npmax + L.n[q] + 2 * r) / 2;
-        xh[o] = z;
-        xl[o] = z;
+        const long o = (((long)q * cpad + c) * 2 * L.npmax + ilv(L.n[q] + 2 * r)) / 2;
+        xo[o] = z;
+        xo[o + kBK / 2] = z;
     }
 }
 
@@ -834,9 +832,8 @@ __global__ void __launch_bounds__(256) k_expand_q(const float* __restrict__ Y, c
 }
 
 template <int NV, int MODE>
-void launch_gather(int cells, int cpad, const float* h, __nv_bfloat162* xh, __nv_bfloat162* xl, cudaStream_t s,
-                   int quarter) {
-    k_gather_sub<NV, MODE><<<8 * sm_count(), 256, 0, s>>>(h, xh, xl, cells, cpad, quarter);
+void launch_gather(int cells, int cpad, const float* h, __nv_bfloat162* x, cudaStream_t s, int quarter) {
+    k_gather_sub<NV, MODE><<<8 * sm_count(), 256, 0, s>>>(h, x, cells, cpad, quarter);
 }
 
 template <int NV>
@@ -911,10 +908,11 @@ __global__ void k_basis_sub(double* __restrict__ h, int g0, int nbas, int nv, in
     }
 }
 
-// Columns g0 .. g0 + nbas - 1 of the stacked sub-blocks (row-major [rows][npmax], hi / lo
-// bf16) from L+ e at the representative point of each output row.
-__global__ void k_store_sub(const double* __restrict__ Lp, __nv_bfloat16* __restrict__ Ah,
-                            __nv_bfloat16* __restrict__ Al, int g0, int nbas, int nv, int mode) {
+// Columns g0 .. g0 + nbas - 1 of the stacked sub-blocks (row-major [rows][2 npmax], hi / lo
+// bf16 interleaved per 32-column slice) from L+ e at the representative point of each output
+// row.
+__global__ void k_store_sub(const double* __restrict__ Lp, __nv_bfloat16* __restrict__ A, int g0, int nbas,
+                            int nv, int mode) {
     const SubLayout L = sub_layout(nv, mode);
     const int H = nv / 2;
     const long n3 = (long)nv * nv * nv;
@@ -931,9 +929,9 @@ __global__ void k_store_sub(const double* __restrict__ Lp, __nv_bfloat16* __rest
         sub_column(L, q, row, H, &qa, &qb, &q3);
         const double a = Lp[bb * n3 + (qa * nv + qb) * nv + q3];
         const __nv_bfloat16 hi = __float2bfloat16_rn((float)a);
-        const long idx = (long)(L.roff[q] + row) * L.npmax + col;
-        Ah[idx] = hi;
-        Al[idx] = __float2bfloat16_rn((float)(a - (double)__bfloat162float(hi)));
+        const long idx = (long)(L.roff[q] + row) * 2 * L.npmax + ilv(col);
+        A[idx] = hi;
+        A[idx + 32] = __float2bfloat16_rn((float)(a - (double)__bfloat162float(hi)));
     }
 }
 
@@ -951,17 +949,20 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
+// Tensor map of an interleaved operand [rows][2 cols] bf16 (cols: its logical width): boxes of
+// one 32-deep slice's hi | lo pair (128 bytes) by box_rows, 128-byte swizzle.
 bool make_map(CUtensorMap* m, const void* ptr, long rows, long cols, int box_rows) {
     auto enc = get_encode();
     if (!enc) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * cols), (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * kBK), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
 
 // Column tile for a call: the cells split evenly over ceil(cells / 256) tiles, rounded up to
 // the next instantiated width (808 cells: 4 x 208 = 832 columns instead of 4 x 256).
@@ -1114,8 +1115,8 @@ __global__ void k_count_diff(const float* __restrict__ a, const float* __restric
 
 // The persistent form over nprog CTAs and, when fix is set, the fix-up of the split tiles.
 template <int BN>
-cudaError_t launch_gemm_ws(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0,
-                           const CUtensorMap& b1, int nr, int cells, int nprog, const GemmWork* work,
+cudaError_t launch_gemm_ws(const CUtensorMap& a0, const CUtensorMap& b0, int nr, int cells, int nprog,
+                           const GemmWork* work,
                            const int* cta_off, int nfix, const GemmFix* fix, float* Y, float* P, int* err, int probe,
                            cudaStream_t s) {
     static std::once_flag once;
@@ -1123,7 +1124,7 @@ cudaError_t launch_gemm_ws(const CUtensorMap& a0, const CUtensorMap& a1, const C
         cudaFuncSetAttribute(k_dense_gemm_ws<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)GemmCfg<BN>::SMEM);
     });
-    k_dense_gemm_ws<BN><<<nprog, 192, GemmCfg<BN>::SMEM, s>>>(a0, a1, b0, b1, nr, cells, work, cta_off, Y, P, err,
+    k_dense_gemm_ws<BN><<<nprog, 192, GemmCfg<BN>::SMEM, s>>>(a0, b0, nr, cells, work, cta_off, Y, P, err,
                                                               probe);
     if (nfix > 0) k_gemm_fixup<BN><<<dim3((BN * kBM / 4 + 255) / 256, nfix), 256, 0, s>>>(fix, P, Y, nr, cells);
     return cudaGetLastError();
@@ -1132,7 +1133,7 @@ cudaError_t launch_gemm_ws(const CUtensorMap& a0, const CUtensorMap& a1, const C
 // The GEMM (cluster size cs; cs = 1 an ordinary launch) and, when fix is set, the fix-up of
 // the split tiles.  Returns the launch error.
 template <int BN>
-cudaError_t launch_gemm(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
+cudaError_t launch_gemm(const CUtensorMap& a0, const CUtensorMap& b0,
                         int nr, int cells, int nwork, const GemmWork* work, int nfix, const GemmFix* fix, float* Y,
                         float* P, int* err, int probe, int cs, cudaStream_t s) {
     static std::once_flag once;
@@ -1140,7 +1141,7 @@ cudaError_t launch_gemm(const CUtensorMap& a0, const CUtensorMap& a1, const CUte
         cudaFuncSetAttribute(k_dense_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GemmCfg<BN>::SMEM);
     });
     if (cs == 1) {
-        k_dense_gemm<BN><<<nwork, 128, GemmCfg<BN>::SMEM, s>>>(a0, a1, b0, b1, nr, cells, work, Y, P, err, probe, 1);
+        k_dense_gemm<BN><<<nwork, 128, GemmCfg<BN>::SMEM, s>>>(a0, b0, nr, cells, work, Y, P, err, probe, 1);
     } else {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(nwork);
@@ -1155,7 +1156,7 @@ cudaError_t launch_gemm(const CUtensorMap& a0, const CUtensorMap& a1, const CUte
         cfg.attrs = at;
         cfg.numAttrs = 1;
         const cudaError_t e =
-            cudaLaunchKernelEx(&cfg, k_dense_gemm<BN>, a0, a1, b0, b1, nr, cells, work, Y, P, err, probe, cs);
+            cudaLaunchKernelEx(&cfg, k_dense_gemm<BN>, a0, b0, nr, cells, work, Y, P, err, probe, cs);
         if (e != cudaSuccess) return e;
     }
     if (nfix > 0) k_gemm_fixup<BN><<<dim3((BN * kBM / 4 + 255) / 256, nfix), 256, 0, s>>>(fix, P, Y, nr, cells);
@@ -1168,9 +1169,8 @@ cudaError_t launch_gemm(const CUtensorMap& a0, const CUtensorMap& a1, const CUte
 struct DenseOp {
     int mode = 0, nv = 0;
     SubLayout L;
-    __nv_bfloat16* Ah = nullptr;
-    __nv_bfloat16* Al = nullptr;
-    CUtensorMap mAh[3], mAl[3];  // boxes of 128, 64 and 32 rows (cluster sizes 1, 2 and 4)
+    __nv_bfloat16* A = nullptr;  // hi / lo interleaved per 32-column slice, [rows][2 npmax]
+    CUtensorMap mA[3];           // boxes of 128, 64 and 32 rows (cluster sizes 1, 2 and 4)
     size_t bytes = 0;
 };
 
@@ -1207,13 +1207,11 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
     d.L = sub_layout(nv, mode);
     int nbas = 0;  // basis functions: every sub-block's columns
     for (int q = 0; q < d.L.count; ++q) nbas += d.L.n[q];
-    const size_t abytes = (size_t)d.L.rows * d.L.npmax * 2;
-    lbe_status st = dev_alloc(c, (void**)&d.Ah, abytes);
-    if (st == LBE_OK) st = dev_alloc(c, (void**)&d.Al, abytes);
+    const size_t abytes = (size_t)d.L.rows * 2 * d.L.npmax * 2;  // hi and lo
+    lbe_status st = dev_alloc(c, (void**)&d.A, abytes);
     if (st != LBE_OK) return st;
-    d.bytes = 2 * abytes;
-    cudaMemsetAsync(d.Ah, 0, abytes, s);  // padding rows and columns stay zero
-    cudaMemsetAsync(d.Al, 0, abytes, s);
+    d.bytes = abytes;
+    cudaMemsetAsync(d.A, 0, abytes, s);  // padding rows and columns stay zero
     // basis chunks through the double-float fast-spectral operator (delta = 1)
     const long n3 = (long)nv * nv * nv;
     const int nb = (int)std::min<long>(nbas, std::max<long>(1, (256L << 20) / (n3 * 8)));
@@ -1234,7 +1232,7 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
             k_basis_sub<<<8 * sm_count(), 256, 0, s>>>((double*)hb, g0, b, nv, mode);
             st = fsm_df_apply(*t, b, (const double*)dl, (const double*)hb, (double*)lp, (double*)lo, sc, chunk, s,
                               mode);
-            k_store_sub<<<8 * sm_count(), 256, 0, s>>>((const double*)lp, d.Ah, d.Al, g0, b, nv, mode);
+            k_store_sub<<<8 * sm_count(), 256, 0, s>>>((const double*)lp, d.A, g0, b, nv, mode);
             g_launches += 2;
         }
         if (st == LBE_OK) st = cuda_status(c, cudaStreamSynchronize(s), "dense operator build");
@@ -1247,8 +1245,7 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
     if (st != LBE_OK) return st;
     bool maps = true;
     for (int k = 0; k < 3; ++k)
-        maps = maps && make_map(&d.mAh[k], d.Ah, d.L.rows, d.L.npmax, kBM >> k) &&
-               make_map(&d.mAl[k], d.Al, d.L.rows, d.L.npmax, kBM >> k);
+        maps = maps && make_map(&d.mA[k], d.A, d.L.rows, d.L.npmax, kBM >> k);
     if (!maps) {
         c->last_error = "cuTensorMapEncodeTiled unavailable or failed";
         return LBE_INTERNAL;
@@ -1270,7 +1267,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     std::lock_guard<std::mutex> lk(T.mu);
     DenseOp& d = T.op[mode];
     lbe_status st;
-    if (!d.Ah && (st = build_dense(c, t, d, mode, s)) != LBE_OK) return st;
+    if (!d.A && (st = build_dense(c, t, d, mode, s)) != LBE_OK) return st;
     if (!T.err_dev) {
         if ((st = dev_alloc(c, (void**)&T.err_dev, 256)) != LBE_OK) return st;
         if (cudaMallocHost((void**)&T.err_host, sizeof(int)) != cudaSuccess) {
@@ -1312,31 +1309,28 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
     const size_t pb = (size_t)plan.slots * bn * kBM * 4;
     Arena& ws = T.ws[s];
     if ((st = arena_reserve(c, ws, 2 * xb + yb + pb + 4 * 256)) != LBE_OK) return st;
-    auto* xh = (__nv_bfloat16*)arena_take(ws, xb);
-    auto* xl = (__nv_bfloat16*)arena_take(ws, xb);
+    auto* xhl = (__nv_bfloat16*)arena_take(ws, 2 * xb);  // hi / lo interleaved per slice
     auto* Y = (float*)arena_take(ws, yb);
     auto* Pp = pb ? (float*)arena_take(ws, pb) : nullptr;
     if (cpad > cells)
         for (int q = 0; q < nsub; ++q) {
-            const size_t o = ((size_t)q * cpad + cells) * npmax, n = (size_t)(cpad - cells) * npmax * 2;
-            cudaMemsetAsync(xh + o, 0, n, s);
-            cudaMemsetAsync(xl + o, 0, n, s);
+            const size_t o = ((size_t)q * cpad + cells) * 2 * npmax, n = (size_t)(cpad - cells) * 2 * npmax * 2;
+            cudaMemsetAsync(xhl + o, 0, n, s);
         }
-    CUtensorMap mXh, mXl;
-    if (!make_map(&mXh, xh, nsub * cpad, npmax, bn) || !make_map(&mXl, xl, nsub * cpad, npmax, bn)) {
+    CUtensorMap mX;
+    if (!make_map(&mX, xhl, nsub * cpad, npmax, bn)) {
         c->last_error = "cuTensorMapEncodeTiled failed for the cell operand";
         return LBE_INTERNAL;
     }
     {
-        auto* xh2 = reinterpret_cast<__nv_bfloat162*>(xh);
-        auto* xl2 = reinterpret_cast<__nv_bfloat162*>(xl);
+        auto* x2 = reinterpret_cast<__nv_bfloat162*>(xhl);
         const bool p2 = mode == 2;
         const int cp = (int)cpad, qf = quarter ? 1 : 0;
         switch (nv) {
-            case 8: (p2 ? launch_gather<8, 2> : launch_gather<8, 1>)(cells, cp, h, xh2, xl2, s, qf); break;
-            case 16: (p2 ? launch_gather<16, 2> : launch_gather<16, 1>)(cells, cp, h, xh2, xl2, s, qf); break;
-            case 24: (p2 ? launch_gather<24, 2> : launch_gather<24, 1>)(cells, cp, h, xh2, xl2, s, qf); break;
-            default: (p2 ? launch_gather<32, 2> : launch_gather<32, 1>)(cells, cp, h, xh2, xl2, s, qf); break;
+            case 8: (p2 ? launch_gather<8, 2> : launch_gather<8, 1>)(cells, cp, h, x2, s, qf); break;
+            case 16: (p2 ? launch_gather<16, 2> : launch_gather<16, 1>)(cells, cp, h, x2, s, qf); break;
+            case 24: (p2 ? launch_gather<24, 2> : launch_gather<24, 1>)(cells, cp, h, x2, s, qf); break;
+            default: (p2 ? launch_gather<32, 2> : launch_gather<32, 1>)(cells, cp, h, x2, s, qf); break;
         }
     }
     // optional event timing of the GEMM alone (public synchronous calls only)
@@ -1350,7 +1344,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         if (cs == kPersistent) switch (bn) {
 #define LBE_WS(W)                                                                                                 \
     case W:                                                                                                       \
-        return launch_gemm_ws<W>(d.mAh[0], d.mAl[0], mXh, mXl, mrows, cells, plan.nprog, plan.work_p, plan.cta_off, \
+        return launch_gemm_ws<W>(d.mA[0], mX, mrows, cells, plan.nprog, plan.work_p, plan.cta_off, \
                                  nf, plan.fix, Y, Pp, T.err_dev, probe, s);
                 LBE_WS(64)
                 LBE_WS(128)
@@ -1362,13 +1356,13 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
 #undef LBE_WS
             }
         switch (bn) {
-            case 64: return launch_gemm<64>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
-            case 128: return launch_gemm<128>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
-            case 160: return launch_gemm<160>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
-            case 192: return launch_gemm<192>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
-            case 208: return launch_gemm<208>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
-            case 224: return launch_gemm<224>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
-            default: return launch_gemm<256>(d.mAh[k], d.mAl[k], mXh, mXl, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            case 64: return launch_gemm<64>(d.mA[k], mX, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            case 128: return launch_gemm<128>(d.mA[k], mX, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            case 160: return launch_gemm<160>(d.mA[k], mX, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            case 192: return launch_gemm<192>(d.mA[k], mX, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            case 208: return launch_gemm<208>(d.mA[k], mX, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            case 224: return launch_gemm<224>(d.mA[k], mX, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
+            default: return launch_gemm<256>(d.mA[k], mX, mrows, cells, plan.nwork, cs == 1 ? plan.work_t : plan.work, nf, plan.fix, Y, Pp, T.err_dev, probe, cs, s);
         }
     };
     const long long cs_key = ((long long)mrows << 20) | ((long long)bn << 8) | plan.group;
@@ -1532,8 +1526,7 @@ lbe_status tc_check(Ctx* c, DevTables* t) {
 void tc_release(Ctx* c, DevTables* t) {
     if (!t->tc) return;
     for (auto& d : t->tc->op) {
-        dev_free(c, d.Ah, d.bytes / 2);
-        dev_free(c, d.Al, d.bytes / 2);
+        dev_free(c, d.A, d.bytes);
     }
     for (auto& kv : t->tc->ws) arena_release(c, kv.second);
     for (auto& kv : t->tc->plans) {
