@@ -711,22 +711,27 @@ lbe_status batch_run(Batch& B, int max_steps) {
         if (st != LBE_OK) return st;
         std::vector<int> keep;
         const double t = host_now();
+        std::vector<int> finished;
         for (int j : B.active) {
             const JobState& js = B.hstate[j];
             // contraction per iteration from successive relative changes
             if (last[j] > 0 && js.rel > 0 && std::isfinite(js.rel))
                 B.omega[j] = std::pow(js.rel / last[j], 1.0 / K);
             last[j] = js.rel;
-            if (!js.done)
+            if (!js.done) {
                 keep.push_back(j);
-            else
+            } else {
                 B.t_done[j] = t;
+                finished.push_back(j);
+            }
         }
         B.active.swap(keep);
         steps += K;
+        if (B.on_done && !finished.empty()) B.on_done(finished);
     }
     const double t = host_now();
     for (int j : B.active) B.t_done[j] = t;
+    if (B.on_done && !B.active.empty()) B.on_done(B.active);
     return LBE_OK;
 }
 
@@ -789,7 +794,9 @@ lbe_status lbe_create(lbe_ctx** out, int device, size_t budget) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     c->budget = budget ? budget : (size_t)(0.9 * fr);
-    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    int prio_low = 0, prio_high = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if (cudaStreamCreateWithPriority(&c->own_stream, cudaStreamNonBlocking, prio_high) != cudaSuccess) {
         delete c;
         return LBE_INTERNAL;
     }
@@ -824,6 +831,7 @@ lbe_status lbe_destroy(lbe_ctx* ctx) {
     arena_release(ctx, ctx->apply_arena);
     for (auto& a : ctx->refine_arena) arena_release(ctx, a);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
     delete ctx;
     return LBE_OK;
 }

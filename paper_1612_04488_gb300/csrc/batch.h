@@ -3,6 +3,7 @@
 // batches, the refinement driver and the service.
 #pragma once
 
+#include <functional>
 #include <vector>
 
 #include "lbe_internal.h"
@@ -65,6 +66,10 @@ struct Batch {
     std::vector<int> graph_key;
     unsigned long long graph_launches = 0, graph_levals = 0;  // counters of one replay
     bool graphs_ok = true;          // false after a failed capture (then iterations are queued plainly)
+    // Called by batch_run with the problems it has just seen finish (or reach its step limit),
+    // after the host synchronised the stream: their iterates are final, and later iterations
+    // leave them untouched.
+    std::function<void(const std::vector<int>&)> on_done;
     Batch() = default;
     Batch(const Batch&) = delete;
     Batch& operator=(const Batch&) = delete;

@@ -129,7 +129,10 @@ struct Ctx {
     std::mutex tables_mu;
     std::map<std::string, std::unique_ptr<DevTables>> tables;
     cudaStream_t stream = nullptr;      // stream of the synchronous calls
-    cudaStream_t own_stream = nullptr;  // created by lbe_create
+    cudaStream_t own_stream = nullptr;  // created by lbe_create (the highest stream priority)
+    // low-priority stream for work that overlaps the synchronous calls' critical path (the
+    // refined solves' base evaluations), created at first use
+    cudaStream_t side_stream = nullptr;
     Arena solve_arena, apply_arena;
     Arena refine_arena[3];  // refined solves: FP64 batch, low-precision batch, work buffers
     // serving

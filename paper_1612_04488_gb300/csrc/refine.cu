@@ -330,8 +330,9 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
     void* inc_scratch = nullptr;
     if (st == LBE_OK) {
         const size_t pad = 256;
-        st = arena_reserve(c, aw, (q ? 7 : 4) * (vol64 + pad) + 4 * (vol32 + pad) + inc_scr + pad);
+        st = arena_reserve(c, aw, (q ? 7 : 4) * (vol64 + pad) + 4 * (vol32 + pad) + inc_scr + n * sizeof(int) + 2 * pad);
     }
+    int* ident = nullptr;  // device [n]: ident[j] = j (one-problem launches of the per-job kernels)
     if (st == LBE_OK) {
         h_old = (double*)arena_take(aw, vol64);
         base_h = (double*)arena_take(aw, vol64);
@@ -351,13 +352,21 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         inc_lp = (float*)arena_take(aw, vol32);
         inc_lh = (float*)arena_take(aw, vol32);
         inc_scratch = arena_take(aw, inc_scr);
-        if (!inc_scratch) st = LBE_INTERNAL;
+        ident = (int*)arena_take(aw, n * sizeof(int));
+        if (!inc_scratch || !ident) st = LBE_INTERNAL;
     }
     if (st != LBE_OK) return st;
+    {
+        std::vector<int> id(n);
+        for (int j = 0; j < n; ++j) id[j] = j;
+        cudaMemcpyAsync(ident, id.data(), n * sizeof(int), cudaMemcpyHostToDevice, s);
+        st = cuda_status(c, cudaStreamSynchronize(s), "refine set-up");
+        if (st != LBE_OK) return st;
+    }
     // The FP64-class operator of the current iterate of problems j0 .. j1 - 1 (consecutive, one
     // geometry, contiguous cells) becomes their base: h0 = h, base_lp / base_lh = L+ h0 / L h0 in
     // double-float arithmetic on the full grid, kept in the batch's layout.
-    auto evaluate_base = [&](int j0, int j1) {
+    auto evaluate_base = [&](int j0, int j1, cudaStream_t s) {
         long cells = 0;
         for (int j = j0; j < j1; ++j) cells += O.sj[j].ncell;
         const long o = O.cell_off[j0] * n3;
@@ -392,14 +401,51 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
     std::vector<int> active(n);
     for (int j = 0; j < n; ++j) active[j] = j;
     const dim3 blk(256);
-    // phase 0: low-precision SIS of the full problem from h = 0, widened to FP64
+    // phase 0: low-precision SIS of the full problem from h = 0.  Each problem, as soon as
+    // batch_run sees it finish, is widened to FP64 and gets its FP64-class operator evaluation
+    // (the base of the increments) on the context's low-priority side stream, overlapping the
+    // iterations of the problems still running; the main stream waits for them afterwards.
+    if (!c->side_stream) {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, lo) != cudaSuccess)
+            c->side_stream = nullptr;
+    }
+    cudaStream_t s2 = c->side_stream ? c->side_stream : s;
+    I.on_done = [&](const std::vector<int>& fin) {
+        std::vector<int> js(fin);
+        std::sort(js.begin(), js.end());
+        for (int j : js) {
+            k_widen<<<dim3(sm_count(), 1), blk, 0, s2>>>(I.h.as<float>(), O.h.as<double>(), O.sjobs.as<SweepJobDev>(),
+                                                        ident + j, n3, q ? 1 : 0);
+            g_launches += 1;
+        }
+        // one call per run of consecutive finished problems of one geometry (plates: parity
+        // mode 2, ducts: mode 1) whose cells are contiguous
+        for (size_t a = 0; a < js.size();) {
+            size_t b = a + 1;
+            long end = O.cell_off[js[a]] + O.sj[js[a]].ncell;
+            while (b < js.size() && js[b] == js[b - 1] + 1 && O.geo[js[b]].dim == O.geo[js[a]].dim &&
+                   O.cell_off[js[b]] == end)
+                end += O.sj[js[b++]].ncell;
+            evaluate_base(js[a], js[b - 1] + 1, s2);
+            a = b;
+        }
+    };
     if (st == LBE_OK) st = batch_run(I, 150);
+    I.on_done = nullptr;
+    if (s2 != s) {  // the main stream continues once every base evaluation is done
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(ev, s2);
+            cudaStreamWaitEvent(s, ev, 0);
+            cudaEventDestroy(ev);
+        } else {
+            cudaStreamSynchronize(s2);
+        }
+    }
     if (st == LBE_OK) {
         for (int j = 0; j < n; ++j) inner_it[j] += I.hstate[j].iters;
-        cudaMemcpyAsync(O.act.p, active.data(), n * sizeof(int), cudaMemcpyHostToDevice, s);
-        k_widen<<<dim3(sm_count(), n), blk, 0, s>>>(I.h.as<float>(), O.h.as<double>(), O.sjobs.as<SweepJobDev>(),
-                                                   O.act.as<int>(), n3, q ? 1 : 0);
-        g_launches += 1;
         // from now on the inner batch solves the homogeneous correction equation
         for (int j = 0; j < n; ++j) {
             I.sj[j].forcing = kForcingNone;
@@ -410,18 +456,9 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         cudaMemcpyAsync(I.sjobs.p, I.sj.data(), n * sizeof(SweepJobDev), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(I.ijobs.p, I.ij.data(), n * sizeof(SisJobDev), cudaMemcpyHostToDevice, s);
         g_h2d += n * (sizeof(SweepJobDev) + sizeof(SisJobDev));
-        // the one FP64-class collision-operator evaluation of the solve: at h0 = the FP32
-        // solution; every later FP64 iteration adds the FP32 operator of the increment h - h0
-        // one call per run of consecutive problems of one geometry (plates: parity mode 2,
-        // ducts: mode 1); the problems' cells are contiguous in batch order
-        for (int j0 = 0; j0 < n;) {
-            int j1 = j0 + 1;
-            long cells = O.sj[j0].ncell;
-            while (j1 < n && O.geo[j1].dim == O.geo[j0].dim && O.cell_off[j1] == O.cell_off[j0] + cells)
-                cells += O.sj[j1++].ncell;
-            evaluate_base(j0, j1);
-            j0 = j1;
-        }
+        // the one FP64-class collision-operator evaluation of the solve, at h0 = the phase-0
+        // solution (above); every later FP64 iteration adds the low-precision operator of the
+        // increment h - h0
         O.base_h = bq_h;
         O.base_lp = bq_lp;
         O.base_lh = bq_lh;
@@ -511,7 +548,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         std::vector<int> corr, rb_plain;
         for (int j : active) (plain[j] ? rb_plain : corr).push_back(j);
         for (int j : rb_plain)
-            if (rebase[j]) evaluate_base(j, j + 1);
+            if (rebase[j]) evaluate_base(j, j + 1, s);
         if (!corr.empty()) {
             const int nk = (int)corr.size();
             cudaMemcpyAsync(O.act.p, corr.data(), nk * sizeof(int), cudaMemcpyHostToDevice, s);
@@ -540,7 +577,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
                                                                    q ? 1 : 0);
             g_launches += 1;
             for (int j : corr)
-                if (rebase[j]) evaluate_base(j, j + 1);
+                if (rebase[j]) evaluate_base(j, j + 1, s);
         }
         // drop problems that reached their iteration cap
         std::vector<int> keep2;
