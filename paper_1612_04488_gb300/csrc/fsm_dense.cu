@@ -1395,6 +1395,8 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         } else {
             // every candidate runs with the fix-up and must reproduce the cluster-1 result bit
             // for bit (they share the work list); one that does not is never chosen
+            // work overlapping on the context's side stream would distort the timings
+            if (c->side_stream && c->side_stream != s) cudaStreamSynchronize(c->side_stream);
             std::vector<float> best(cand.size(), 1e30f);
             float* yref = nullptr;
             int* ndiff = nullptr;
@@ -1533,6 +1535,8 @@ void tc_release(Ctx* c, DevTables* t) {
         dev_free(c, kv.second.work, kv.second.nwork * sizeof(GemmWork));
         dev_free(c, kv.second.work_t, kv.second.nwork * sizeof(GemmWork));
         if (kv.second.fix) dev_free(c, kv.second.fix, kv.second.nfix * sizeof(GemmFix));
+        dev_free(c, kv.second.work_p, kv.second.nwork * sizeof(GemmWork));
+        dev_free(c, kv.second.cta_off, (kv.second.nprog + 1) * sizeof(int));
     }
     dev_free(c, t->tc->err_dev, 256);
     if (t->tc->err_host) cudaFreeHost(t->tc->err_host);
