@@ -33,6 +33,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -96,6 +97,21 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
             smem_u32(dst)),
         "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+// The same with an L2 cache policy (createpolicy): the operator and the operands are re-read by
+// many tiles and across calls, so they are kept in L2 ahead of streaming data.
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                                 uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, "
+        "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t acc) {
@@ -424,6 +440,7 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {  // producer: every K slice of every item, in order
             int g = 0;
             bool ok = true;
+            const uint64_t keep = policy_evict_last();
             for (int it = i0; ok && it < i1; ++it) {
                 const GemmWork wk = work[it];
                 for (int kt = wk.kt0; kt < wk.kt1; ++kt, ++g) {
@@ -435,8 +452,8 @@ __global__ void __launch_bounds__(192, 1)
                     const int x = kt * 2 * kBK;  // the slice's hi | lo pair in the interleaved rows
                     uint8_t* st = base + s * STAGE;
                     mbar_expect_tx(&full[s], STAGE);
-                    tma_load_2d(st, &tmA, x, wk.row0, &full[s]);
-                    tma_load_2d(st + A_BYTES, &tmX, x, wk.xrow0, &full[s]);
+                    tma_load_2d_hint(st, &tmA, x, wk.row0, &full[s], keep);
+                    tma_load_2d_hint(st + A_BYTES, &tmX, x, wk.xrow0, &full[s], keep);
                     n_issued = g + 1;
                 }
             }
@@ -985,6 +1002,9 @@ struct GemmFix {
 template <int BN>
 __global__ void __launch_bounds__(256) k_gemm_fixup(const GemmFix* __restrict__ fix, const float* __restrict__ P,
                                                     float* __restrict__ Y, int Mrows, int ncols) {
+    // launched as a programmatic dependent of the GEMM: scheduled while the GEMM drains, it
+    // waits here until the GEMM's partial tiles are complete
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const GemmFix f = fix[blockIdx.y];
     const int q = blockIdx.x * blockDim.x + threadIdx.x;  // float4 index within the tile
     if (q >= BN * kBM / 4) return;
@@ -1066,15 +1086,39 @@ GemmPlan make_plan(int cells, int bn, const SubLayout& L, int P) {
     }
     std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.kt > b.kt; });
     int W, S;
+    int ktmin = 1 << 30;
+    for (int q = 0; q < L.count; ++q) ktmin = std::min(ktmin, L.np[q] / kBK);
     if (T >= P) {
+        // the split of the tail tiles whose items the persistent form's longest-first
+        // assignment balances best (largest CTA load in K slices, 2 per item for its read-back)
         W = T / P * P;
         S = 4;
+        long best = -1;
+        for (int sc = 2; sc <= 4; ++sc) {
+            if (ktmin / sc < 4) break;
+            std::vector<int> len;
+            for (int gi = 0; gi < (int)groups.size(); ++gi)
+                for (int m = 0; m < G; ++m) {
+                    const int kt = groups[gi].kt;
+                    if (gi < W / G) {
+                        len.push_back(kt);
+                    } else {
+                        for (int p = 0; p < sc; ++p) len.push_back(kt * (p + 1) / sc - kt * p / sc);
+                    }
+                }
+            std::sort(len.begin(), len.end(), std::greater<int>());
+            std::vector<long> load(std::min<size_t>(P, len.size()), 0);
+            for (int l : len) *std::min_element(load.begin(), load.end()) += l + 2;
+            const long mx = *std::max_element(load.begin(), load.end());
+            if (best < 0 || mx < best) {
+                best = mx;
+                S = sc;
+            }
+        }
     } else {
         W = 0;
         S = std::max(1, std::min(4, P / T));
     }
-    int ktmin = 1 << 30;
-    for (int q = 0; q < L.count; ++q) ktmin = std::min(ktmin, L.np[q] / kBK);
     while (S > 1 && ktmin / S < 4) --S;
     const int Wg = S == 1 ? (int)groups.size() : W / G;  // whole groups
     for (int gi = 0; gi < (int)groups.size(); ++gi) {
@@ -1113,6 +1157,24 @@ __global__ void k_count_diff(const float* __restrict__ a, const float* __restric
     if (c) atomicAdd(out, c);
 }
 
+// The fix-up of the split tiles, launched with programmatic stream serialization behind the GEMM.
+template <int BN>
+void launch_fixup(int nfix, const GemmFix* fix, float* P, float* Y, int nr, int cells, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((BN * kBM / 4 + 255) / 256, nfix);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_gemm_fixup<BN>, (const GemmFix*)fix, (const float*)P, Y, nr, cells) != cudaSuccess) {
+        cudaGetLastError();  // without the attribute: an ordinary launch
+        k_gemm_fixup<BN><<<cfg.gridDim, 256, 0, s>>>(fix, P, Y, nr, cells);
+    }
+}
+
 // The persistent form over nprog CTAs and, when fix is set, the fix-up of the split tiles.
 template <int BN>
 cudaError_t launch_gemm_ws(const CUtensorMap& a0, const CUtensorMap& b0, int nr, int cells, int nprog,
@@ -1126,7 +1188,7 @@ cudaError_t launch_gemm_ws(const CUtensorMap& a0, const CUtensorMap& b0, int nr,
     });
     k_dense_gemm_ws<BN><<<nprog, 192, GemmCfg<BN>::SMEM, s>>>(a0, b0, nr, cells, work, cta_off, Y, P, err,
                                                               probe);
-    if (nfix > 0) k_gemm_fixup<BN><<<dim3((BN * kBM / 4 + 255) / 256, nfix), 256, 0, s>>>(fix, P, Y, nr, cells);
+    if (nfix > 0) launch_fixup<BN>(nfix, fix, P, Y, nr, cells, s);
     return cudaGetLastError();
 }
 
@@ -1159,7 +1221,7 @@ cudaError_t launch_gemm(const CUtensorMap& a0, const CUtensorMap& b0,
             cudaLaunchKernelEx(&cfg, k_dense_gemm<BN>, a0, b0, nr, cells, work, Y, P, err, probe, cs);
         if (e != cudaSuccess) return e;
     }
-    if (nfix > 0) k_gemm_fixup<BN><<<dim3((BN * kBM / 4 + 255) / 256, nfix), 256, 0, s>>>(fix, P, Y, nr, cells);
+    if (nfix > 0) launch_fixup<BN>(nfix, fix, P, Y, nr, cells, s);
     return cudaGetLastError();
 }
 
