@@ -376,10 +376,11 @@ def run_serve(args):
     return 0
 
 
-# DRAM bytes (read + write) of one k_dense_gemm launch, from an ncu capture of
-# `bench.py --op-only` (plates32x8, 808 cells), valid only while the kernel's source is the
-# one captured: the digest covers the kernel and its stage configuration.
-GEMM_TRAFFIC = {}
+# DRAM bytes (read + write) of one launch of the GEMM kernel the tuner picks (the persistent
+# k_dense_gemm_ws), from an ncu capture of `bench.py --op-only` (plates32x8, 808 cells), valid
+# only while the kernel's source is the one captured: the digest covers the kernels and their
+# stage configuration.
+GEMM_TRAFFIC = {"plates32x8": {"cells": 808, "bytes": 131834624 + 9925632, "digest": "0a6efc136065442e"}}
 
 
 def gemm_source_digest():
