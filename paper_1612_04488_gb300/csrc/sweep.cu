@@ -52,7 +52,13 @@ template <> struct Rn<float> {
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+    // the hardware reciprocal approximation (relative error below 2^-22): one instruction and
+    // deterministic, so every schedule still computes the same bits
+    static __device__ __forceinline__ float rcp(float x) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
 };
 template <> struct Rn<double> {
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
@@ -150,12 +156,32 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
     const long n3 = (long)n2 * nv;
     const int n = jb.ncell;
     const double* cg = coef + jb.coef_off;
-    T* sc = reinterpret_cast<T*>(sweep_smem);
+    // staged (float): per node and direction one float4 {a, b, c, 0} (a: the 1 / (nu + u a)
+    // coefficient, b, c: those of h_(i-1), h_(i-2)), direction 0 forward, 1 backward
+    float4* sc4 = reinterpret_cast<float4*>(sweep_smem);
+    T* sc = reinterpret_cast<T*>(sweep_smem + (size_t)2 * n * sizeof(float4));
     if (staged) {
-        for (int k = threadIdx.x; k < 6 * n; k += blockDim.x) sc[k] = (T)cg[k];
+        for (int k = threadIdx.x; k < 2 * n; k += blockDim.x) {
+            const int dir = k / n, i = k % n;
+            const double* g = cg + 3 * dir * n + i;
+            sc4[k] = make_float4((float)g[0], (float)g[n], (float)g[2 * n], 0.f);
+        }
         __syncthreads();
     }
-    auto C = [&](int a, int i) -> T { return staged ? sc[a * n + i] : (T)cg[a * n + i]; };
+    struct Co3 {
+        T a, b, c;
+    };
+    auto CO = [&](int dir, int i) -> Co3 {
+        if (staged) {
+            const float4 q = sc4[dir * n + i];
+            return {(T)q.x, (T)q.y, (T)q.z};
+        }
+        const double* g = cg + 3 * dir * n + i;
+        return {(T)g[0], (T)g[n], (T)g[2 * n]};
+    };
+    auto march_co = [&](T x, T S, T uu, const Co3& q, T m1, T m2, T nux) {
+        return march_node(x, S, uu, q.b, q.c, m1, m2, march_inv(nux, uu, q.a));
+    };
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= half * W) return;
     const int i1p = half + t / W, rem = t % W;
@@ -178,7 +204,7 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
         // every right-hand side of this thread's two columns goes in flight at once (after the
         // staged coefficients); the thread waits for its own copies only, so no barrier is
         // needed.  Layout [column][node][thread].
-        T* cp = sc + 6 * n;
+        T* cp = sc;
         T* cn = cp + (long)n * blockDim.x;
         const int tx = threadIdx.x;
         for (int i = 1; i < n; ++i) cp_async4(cp + i * blockDim.x + tx, r + (long)i * n3 + vpos);
@@ -188,8 +214,7 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
         asm volatile("cp.async.wait_group 1;" ::: "memory");
 #pragma unroll 4
         for (int i = 1; i < n; ++i) {
-            const T hi = march_node(cp[i * blockDim.x + tx], Sp, v1, C(1, i), C(2, i), hm1, hm2,
-                                    march_inv(nup, v1, C(0, i)));
+            const T hi = march_co(cp[i * blockDim.x + tx], Sp, v1, CO(0, i), hm1, hm2, nup);
             o[(long)i * n3 + vpos] = hi;
             hm2 = hm1;
             hm1 = hi;
@@ -201,8 +226,7 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
         asm volatile("cp.async.wait_group 0;" ::: "memory");
 #pragma unroll 4
         for (int i = n - 2; i >= 0; --i) {
-            const T hi = march_node(cn[i * blockDim.x + tx], Sn, u, C(4, i), C(5, i), g1, g2,
-                                    march_inv(nun, u, C(3, i)));
+            const T hi = march_co(cn[i * blockDim.x + tx], Sn, u, CO(1, i), g1, g2, nun);
             o[(long)i * n3 + vneg] = hi;
             g2 = g1;
             g1 = hi;
@@ -217,7 +241,7 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
         constexpr int HR = 16;
         const int tx = threadIdx.x;
         const int P = 2 * (n - 1), nh = (P + HR - 1) / HR;
-        T* ring = reinterpret_cast<T*>(sweep_smem + ((6 * n * sizeof(T) + 15) / 16) * 16);
+        T* ring = reinterpret_cast<T*>(sweep_smem + (size_t)2 * n * sizeof(float4));
         uint64_t* bar = reinterpret_cast<uint64_t*>(ring + 2 * HR * 128);
         const long cpos0 = vpos - tx, cneg0 = vneg - tx;  // the block's first velocity per column
         int issued = 0, landed = 0;  // halves issued (thread 0) / seen complete by every thread
@@ -254,7 +278,7 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
             const T x = ring[((k & 1) * HR + p % HR) * 128 + tx];
             if (p < n - 1) {
                 const int i = p + 1;
-                const T hi = march_node(x, Sp, v1, C(1, i), C(2, i), hm1, hm2, march_inv(nup, v1, C(0, i)));
+                const T hi = march_co(x, Sp, v1, CO(0, i), hm1, hm2, nup);
                 o[(long)i * n3 + vpos] = hi;
                 hm2 = hm1;
                 hm1 = hi;
@@ -265,7 +289,7 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
                 }
             } else {
                 const int i = n - 2 - (p - (n - 1));
-                const T hi = march_node(x, Sn, u, C(4, i), C(5, i), g1, g2, march_inv(nun, u, C(3, i)));
+                const T hi = march_co(x, Sn, u, CO(1, i), g1, g2, nun);
                 o[(long)i * n3 + vneg] = hi;
                 g2 = g1;
                 g1 = hi;
@@ -293,7 +317,7 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
                 if (i < n) {
                     const T ri = rb[k];
                     if (i + kRing < n) rb[k] = r[(long)(i + kRing) * n3 + vpos];
-                    const T hi = march_node(ri, Sp, v1, C(1, i), C(2, i), hm1, hm2, march_inv(nup, v1, C(0, i)));
+                    const T hi = march_co(ri, Sp, v1, CO(0, i), hm1, hm2, nup);
                     o[(long)i * n3 + vpos] = hi;
                     hm2 = hm1;
                     hm1 = hi;
@@ -314,7 +338,7 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
                 if (i >= 0) {
                     const T ri = rb[k];
                     if (i - kRing >= 0) rb[k] = r[(long)(i - kRing) * n3 + vneg];
-                    const T hi = march_node(ri, Sn, u, C(4, i), C(5, i), g1, g2, march_inv(nun, u, C(3, i)));
+                    const T hi = march_co(ri, Sn, u, CO(1, i), g1, g2, nun);
                     o[(long)i * n3 + vneg] = hi;
                     g2 = g1;
                     g1 = hi;
@@ -1092,7 +1116,8 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
                   const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s, int quarter) {
     if (njobs <= 0) return;
     // float sweeps stage the coefficients when the largest job's fit in 48 KB
-    const size_t sbytes = (size_t)max_coef * sizeof(T);
+    // 1D: staged coefficients are a float4 per node and direction; 2D: the plain block
+    const size_t sbytes = dim == 1 ? (size_t)(max_coef / 6) * 2 * sizeof(float4) : (size_t)max_coef * sizeof(T);
     const int staged = (sizeof(T) == 4 && max_coef > 0 && sbytes <= 48 * 1024) ? 1 : 0;
     const size_t smem = staged ? sbytes : 0;
     g_launches += 1;
