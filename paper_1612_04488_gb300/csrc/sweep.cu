@@ -38,6 +38,11 @@ __device__ __forceinline__ T source(int forcing, T v1, T v2, T v3, T f) {
 constexpr int kPre = 8;  // prefetch depth of the sweeps (nodes)
 
 // 4-byte asynchronous copy global -> shared (completes through cp.async.wait_group)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
                  "l"(gmem)
@@ -134,10 +139,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 //            threads as the registers allow;
 //   SCHED 2  (float; W a multiple of 128) a ring of node rows in shared memory filled by the
 //            bulk-copy (TMA) engine, 512 bytes per node and column, one mbarrier per half ring:
-//            up to 32 nodes in flight per block at 16 KB of shared memory.
-// The march coefficients [fa|fb|fc|ba|bb|bc] (n each) are converted to T once per block into
-// shared memory when `staged` (a double-to-float conversion per node and thread would run at
-// the FP64 rate).
+//            up to 32 nodes in flight per block at 16 KB of shared memory;
+//   SCHED 3  (float; W a multiple of 128) staged like SCHED 0, each node's 512-byte row copied by
+//            32 lanes in 16-byte pieces, then a barrier per column.
+// The march coefficients [fa|fb|fc|ba|bb|bc] (n each) are converted once per block into shared
+// memory when `staged`, as one float4 per node and direction (a double-to-float conversion per
+// node and thread would run at the FP64 rate).
 constexpr int kRing = 16;
 template <typename T, int SCHED>
 __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* __restrict__ h,
@@ -224,6 +231,46 @@ __global__ void __launch_bounds__(128) k_sweep1d(const T* __restrict__ rhs, T* _
         T g1 = hm1, g2 = hm2;
         o[(long)(n - 1) * n3 + vneg] = hm1;
         asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll 4
+        for (int i = n - 2; i >= 0; --i) {
+            const T hi = march_co(cn[i * blockDim.x + tx], Sn, u, CO(1, i), g1, g2, nun);
+            o[(long)i * n3 + vneg] = hi;
+            g2 = g1;
+            g1 = hi;
+        }
+    } else if constexpr (SCHED == 3) {
+        // as SCHED 0, but the block's 128 velocities are contiguous in both columns (W a multiple
+        // of 128, float), so each node's 512-byte row is copied by 32 lanes in 16-byte pieces:
+        // a quarter of the copy instructions, then a barrier per column.  Layout as SCHED 0.
+        T* cp = sc;
+        T* cn = cp + (long)n * blockDim.x;
+        const int tx = threadIdx.x;
+        const long cpos0 = vpos - tx, cneg0 = vneg - tx;
+        if constexpr (sizeof(T) == 4) {
+            for (int q = tx; q < (n - 1) * 32; q += blockDim.x) {  // forward rows: nodes 1 .. n-1
+                const int i = 1 + (q >> 5), pc = 4 * (q & 31);
+                cp_async16(cp + i * 128 + pc, r + (long)i * n3 + cpos0 + pc);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            for (int q = tx; q < (n - 1) * 32; q += blockDim.x) {  // backward rows: nodes 0 .. n-2
+                const int i = q >> 5, pc = 4 * (q & 31);
+                cp_async16(cn + i * 128 + pc, r + (long)i * n3 + cneg0 + pc);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+#pragma unroll 4
+        for (int i = 1; i < n; ++i) {
+            const T hi = march_co(cp[i * blockDim.x + tx], Sp, v1, CO(0, i), hm1, hm2, nup);
+            o[(long)i * n3 + vpos] = hi;
+            hm2 = hm1;
+            hm1 = hi;
+        }
+        T g1 = hm1, g2 = hm2;
+        o[(long)(n - 1) * n3 + vneg] = hm1;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
 #pragma unroll 4
         for (int i = n - 2; i >= 0; --i) {
             const T hi = march_co(cn[i * blockDim.x + tx], Sn, u, CO(1, i), g1, g2, nun);
@@ -1103,6 +1150,9 @@ static void sweep1d_sched(int sched, const DevTables& t, dim3 g, size_t smem_coe
     if (sched == 0)
         k_sweep1d<T, 0><<<g, 128, smem_full, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged,
                                                    quarter);
+    else if (sched == 3)
+        k_sweep1d<T, 3><<<g, 128, smem_full, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged,
+                                                   quarter);
     else if (sched == 2)
         k_sweep1d<T, 2><<<g, 128, (smem_coef + 15) / 16 * 16 + 2 * 16 * 128 * sizeof(T) + 16, s>>>(
             rhs, h, nu1, vel, feq, jobs, active, coef, t.nv, staged, quarter);
@@ -1134,6 +1184,7 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
             static std::once_flag attr;  // opt-in shared memory beyond 48 KB (float instance)
             std::call_once(attr, [] {
                 cudaFuncSetAttribute(k_sweep1d<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                cudaFuncSetAttribute(k_sweep1d<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             });
             int jb = 1;
             while (jb < njobs) jb *= 2;  // problems and nodes classes: the next power of two
@@ -1150,9 +1201,10 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
                 sched = 0;
             } else {
                 // every schedule twice, in turn; each writes the same h (same arithmetic).  The
-                // bulk-copy ring needs whole 128-velocity rows per block (W a multiple of 128).
-                const int NS = W % 128 == 0 ? 3 : 2;
-                cudaEvent_t ev[7];
+                // bulk-copy ring and the row-staged schedule need whole 128-velocity rows per
+                // block (W a multiple of 128).
+                const int NS = W % 128 == 0 ? 4 : 2;
+                cudaEvent_t ev[9];
                 for (int k = 0; k <= 2 * NS; ++k) cudaEventCreate(&ev[k]);
                 cudaEventRecord(ev[0], s);
                 for (int k = 0; k < 2 * NS; ++k) {
@@ -1160,22 +1212,22 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
                     cudaEventRecord(ev[k + 1], s);
                 }
                 cudaEventSynchronize(ev[2 * NS]);
-                float ms[6] = {};
+                float ms[8] = {};
                 for (int k = 0; k < 2 * NS; ++k) cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
                 for (int k = 0; k <= 2 * NS; ++k) cudaEventDestroy(ev[k]);
-                float best[3] = {0.f, 0.f, 0.f};
+                float best[4] = {0.f, 0.f, 0.f, 0.f};
                 for (int q = 0; q < NS; ++q) best[q] = std::min(ms[q], ms[q + NS]);
                 sched = 0;
                 for (int q = 1; q < NS; ++q)
                     if (best[q] < best[sched]) sched = q;
                 t.tuning->sweep[key] = sched;
-                static const char* names[3] = {"staged", "register ring", "bulk-copy ring"};
-                char line[240];
+                static const char* names[4] = {"staged", "register ring", "bulk-copy ring", "row-staged"};
+                char line[280];
                 snprintf(line, sizeof line,
                          "sweep1d<float>%s nv=%d problems<=%d nodes<=%d: %s (staged %.1f us, register ring %.1f us, "
-                         "bulk-copy ring %.1f us)",
+                         "bulk-copy ring %.1f us, row-staged %.1f us)",
                          quarter ? " orbit layout" : "", nv, jb, nb, names[sched], 1000.0f * best[0],
-                         1000.0f * best[1], 1000.0f * best[2]);
+                         1000.0f * best[1], 1000.0f * best[2], 1000.0f * best[3]);
                 t.tuning->log.push_back(line);
                 g_launches += 2 * NS - 1;
                 return;
