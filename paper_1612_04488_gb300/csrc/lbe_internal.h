@@ -48,6 +48,9 @@ struct Tuning {
     std::mutex mu;
     std::map<long long, int> sweep;  // key -> schedule (0 staged, 1 register ring, 2 shared ring)
     std::vector<std::string> log;    // one line per decision (lbe_tuning_report)
+    // the context's side stream (if any): the tuner waits for it, so that overlapping work does
+    // not distort its timings
+    cudaStream_t side = nullptr;
 };
 
 struct DevTables {

@@ -412,6 +412,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             c->side_stream = nullptr;
     }
     cudaStream_t s2 = c->side_stream ? c->side_stream : s;
+    if (I.t->tuning) I.t->tuning->side = c->side_stream;
     I.on_done = [&](const std::vector<int>& fin) {
         std::vector<int> js(fin);
         std::sort(js.begin(), js.end());

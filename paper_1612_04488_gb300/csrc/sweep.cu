@@ -1204,6 +1204,7 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
                 // bulk-copy ring and the row-staged schedule need whole 128-velocity rows per
                 // block (W a multiple of 128).
                 const int NS = W % 128 == 0 ? 4 : 2;
+                if (t.tuning->side && t.tuning->side != s) cudaStreamSynchronize(t.tuning->side);
                 cudaEvent_t ev[9];
                 for (int k = 0; k <= 2 * NS; ++k) cudaEventCreate(&ev[k]);
                 cudaEventRecord(ev[0], s);
