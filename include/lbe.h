@@ -315,10 +315,14 @@ lbe_status lbe_get_stats(lbe_stats* out);
 lbe_status lbe_set_kernel_timing(int on);
 
 /* The autotuner's decisions in this context, one text line each (for logs and benchmark
- * records): launch choices measured at first use, e.g. the schedule of the 1D float transport
- * sweep per (grid, number of problems, nodes) class.  Every schedule computes the same bits, so
- * the choices change speed only.  buf (host, cap bytes) receives a NUL-terminated string;
- * LBE_BAD_ARG if it does not fit (the text is then truncated). */
+ * records): launch choices measured at first use -- the schedule of the 1D float transport
+ * sweep per (grid, number of problems, nodes) class, and the form of the tensor-core operator's
+ * GEMM (one CTA per work item, alone or in clusters, or persistent and warp-specialised) per
+ * launch shape.  Every candidate computes the same bits, so the choices change speed only.  The
+ * environment variable LBE_GEMM_FORM ("persistent", or a cluster size 1, 2 or 4) fixes the GEMM
+ * form instead of timing it (for profilers, whose overhead distorts the timing).  buf (host, cap
+ * bytes) receives a NUL-terminated string; LBE_BAD_ARG if it does not fit (the text is then
+ * truncated). */
 lbe_status lbe_tuning_report(lbe_ctx* ctx, char* buf, size_t cap);
 
 /* Test hook for the bounded-wait failure path (0 = off, the default).  While on, every CTA of
