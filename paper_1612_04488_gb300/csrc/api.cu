@@ -519,12 +519,15 @@ void batch_iterate(Batch& B, bool upload, bool read) {
         const long c0 = sp.c0;
         const int nc = (int)sp.n;
         const int mode = sp.dim == 1 ? 2 : 1;
-        const bool q = B.quarter() && sp.dim == 1;  // plates in the orbit layout
+        // the orbit layout of this span: 1 plates (a quarter of each cell), 2 ducts (a half)
+        const int ql = B.quarter() ? (sp.dim == 1 ? 1 : 2) : 0;
+        const bool q = ql != 0;
+        const long nq = ql == 1 ? n3 / 4 : (ql == 2 ? n3 / 2 : n3);  // values a cell holds
         if (sizeof(T) == 8 && B.base_h) {
             // L h = L_64(h_base) + L_32(h - h_base): the increment is small, so FP32 suffices
             const long o = c0 * n3, nn = (long)nc * n3;
             if (q)
-                range_sub_f32_q((const double*)(h + o), B.base_h + o, B.inc_h + o, nc, n3, s);
+                range_sub_f32_q((const double*)(h + o), B.base_h + o, B.inc_h + o, nc, n3, nq, s);
             else
                 range_sub_f32((const double*)(h + o), B.base_h + o, B.inc_h + o, nn, s);
             if (B.inc_tc) {  // BF16-refined: the increment through the tensor-core operator
@@ -537,8 +540,8 @@ void batch_iterate(Batch& B, bool upload, bool read) {
                                     B.inc_scratch, B.inc_chunk, s, mode);
             }
             if (q) {
-                range_add_f64_q(B.base_lp + o, B.inc_lp + o, (double*)(lp + o), nc, n3, s);
-                range_add_f64_q(B.base_lh + o, B.inc_lh + o, (double*)(lh + o), nc, n3, s);
+                range_add_f64_q(B.base_lp + o, B.inc_lp + o, (double*)(lp + o), nc, n3, nq, s);
+                range_add_f64_q(B.base_lh + o, B.inc_lh + o, (double*)(lh + o), nc, n3, nq, s);
             } else {
                 range_add_f64(B.base_lp + o, B.inc_lp + o, (double*)(lp + o), nn, s);
                 range_add_f64(B.base_lh + o, B.inc_lh + o, (double*)(lh + o), nn, s);
@@ -556,8 +559,7 @@ void batch_iterate(Batch& B, bool upload, bool read) {
                             B.scratch.p, B.chunk, s, mode);
         }
         if (any_sis)
-            lmoments<T>(t, nc, lh + c0 * n3, h + c0 * n3, B.nd.as<double>() + c0, B.G.as<double>() + c0 * 2, s,
-                        q ? 1 : 0);
+            lmoments<T>(t, nc, lh + c0 * n3, h + c0 * n3, B.nd.as<double>() + c0, B.G.as<double>() + c0 * 2, s, ql);
     }
     // sweeps grouped by dimension
     std::vector<int> act1, act2;
@@ -585,11 +587,11 @@ void batch_iterate(Batch& B, bool upload, bool read) {
         if (tm) sweep_timing_end(s, ev, 2.0 * sizeof(T) * (double)c1 * (q1 ? n3 / 4 : n3));
         tm = !act2.empty() && sweep_timing_begin(s, ev);
         launch_sweep<T>(t, 2, (int)act2.size(), mc2, lp, hh, B.sjobs.as<SweepJobDev>(), dact + act1.size(),
-                        B.coef.as<double>(), s);
-        if (tm) sweep_timing_end(s, ev, 2.0 * sizeof(T) * (double)c2 * n3);
+                        B.coef.as<double>(), s, q1);  // ducts in the orbit layout: a half of each cell
+        if (tm) sweep_timing_end(s, ev, 2.0 * sizeof(T) * (double)c2 * (q1 ? n3 / 2 : n3));
     }
     for (auto& sp : spans)
-        launch_moments<T>(t, sp.c0, (int)sp.n, hh, B.mom.as<double>(), s, B.quarter() && sp.dim == 1);
+        launch_moments<T>(t, sp.c0, (int)sp.n, hh, B.mom.as<double>(), s, B.quarter() ? (sp.dim == 1 ? 1 : 2) : 0);
     int max_cells = 0;
     for (int j : B.active) max_cells = std::max(max_cells, B.sj[j].ncell);
     launch_sis_update(t, na, B.ijobs.as<SisJobDev>(), dact, B.mom.as<double>(), B.G.as<double>(),
@@ -843,14 +845,14 @@ int lbe_problem_cells(const lbe_problem* pb) {
 
 // Host: the orbit layout (sweep.h) of `cells` cells from the full velocity grid -- the orbit
 // representatives (i2, i3 < nv / 2); orbit_unpack_host (batch.h) is the inverse.
-static void orbit_pack(int nv, long cells, const double* full, float* q) {
-    const int H = nv / 2;
+static void orbit_pack(int nv, long cells, const double* full, float* q, int dim) {
+    const int H = nv / 2, R2 = dim == 2 ? nv : H;
     const long n3 = (long)nv * nv * nv;
     for (long c = 0; c < cells; ++c)
         for (int i1 = 0; i1 < nv; ++i1)
-            for (int j2 = 0; j2 < H; ++j2)
+            for (int j2 = 0; j2 < R2; ++j2)
                 for (int j3 = 0; j3 < H; ++j3)
-                    q[c * n3 + ((long)i1 * H + j2) * H + j3] = (float)full[c * n3 + ((long)i1 * nv + j2) * nv + j3];
+                    q[c * n3 + ((long)i1 * R2 + j2) * H + j3] = (float)full[c * n3 + ((long)i1 * nv + j2) * nv + j3];
 }
 static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int n, lbe_result* outs,
                                 double* U3_out, double* h_out, const double* h_in = nullptr,
@@ -887,7 +889,7 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
                              "h_in copy");
         } else {
             std::vector<float> tmp(h_in, h_in + nn);
-            if (B.quarter() && B.geo[0].dim == 1) orbit_pack(pbs[0].nv, B.cells, h_in, tmp.data());
+            if (B.quarter()) orbit_pack(pbs[0].nv, B.cells, h_in, tmp.data(), B.geo[0].dim);
             st = cuda_status(ctx, cudaMemcpyAsync(B.h.p, tmp.data(), nn * 4, cudaMemcpyHostToDevice, ctx->stream),
                              "h_in copy");
             if (st == LBE_OK) st = cuda_status(ctx, cudaStreamSynchronize(ctx->stream), "h_in copy");
@@ -913,7 +915,7 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
                 launch_moments<double>(*B.t, 0, (int)B.cells, B.h.as<double>(), B.mom.as<double>(), ctx->stream);
             else
                 launch_moments<float>(*B.t, 0, (int)B.cells, B.h.as<float>(), B.mom.as<double>(), ctx->stream,
-                                      B.quarter() && B.geo[0].dim == 1);
+                                      B.quarter() ? B.geo[0].dim : 0);
             launch_set_rates(1, B.ijobs.as<SisJobDev>(), B.act.as<int>(), B.mom.as<double>(), B.coef.as<double>(),
                              B.states.as<JobState>(), ctx->stream);
         }
@@ -942,9 +944,8 @@ static lbe_status lbe_solve_batch_impl(lbe_ctx* ctx, const lbe_problem* pbs, int
             for (size_t i = 0; i < tmp.size(); ++i) h_out[i] = tmp[i];
             if (B.quarter())
                 for (int j = 0; j < n; ++j)
-                    if (B.geo[j].dim == 1)
-                        orbit_unpack_host(pbs[0].nv, B.sj[j].ncell, tmp.data() + B.cell_off[j] * n3,
-                                          h_out + B.cell_off[j] * n3);
+                    orbit_unpack_host(pbs[0].nv, B.sj[j].ncell, tmp.data() + B.cell_off[j] * n3,
+                                      h_out + B.cell_off[j] * n3, B.geo[j].dim);
         }
     }
     return st != LBE_OK ? st : worst;

@@ -82,18 +82,19 @@ struct Batch {
 // part of the SIS map, used by the refinement driver's correction solves).
 constexpr int kForcingNone = 2;
 
-// Host: the full velocity grid of `cells` plate cells from their orbit layout (sweep.h; cell
-// stride nv^3), restoring the R2 images (equal) and the R3 images (negated).
+// Host: the full velocity grid of `cells` cells from their orbit layout (sweep.h; cell stride
+// nv^3; dim 1 plates, 2 ducts), restoring the R2 images (equal, plates) and the R3 images
+// (negated).
 template <typename TQ>
-inline void orbit_unpack_host(int nv, long cells, const TQ* q, double* full) {
-    const int H = nv / 2;
+inline void orbit_unpack_host(int nv, long cells, const TQ* q, double* full, int dim = 1) {
+    const int H = nv / 2, R2 = dim == 2 ? nv : H;
     const long n3 = (long)nv * nv * nv;
     for (long c = 0; c < cells; ++c)
         for (int i1 = 0; i1 < nv; ++i1)
             for (int i2 = 0; i2 < nv; ++i2)
                 for (int i3 = 0; i3 < nv; ++i3) {
-                    const int j2 = i2 < H ? i2 : nv - 1 - i2, j3 = i3 < H ? i3 : nv - 1 - i3;
-                    const double v = (double)q[c * n3 + ((long)i1 * H + j2) * H + j3];
+                    const int j2 = dim == 2 || i2 < H ? i2 : nv - 1 - i2, j3 = i3 < H ? i3 : nv - 1 - i3;
+                    const double v = (double)q[c * n3 + ((long)i1 * R2 + j2) * H + j3];
                     full[c * n3 + ((long)i1 * nv + i2) * nv + i3] = i3 < H ? v : -v;
                 }
 }
@@ -115,17 +116,20 @@ void range_residual(const double* h, const double* h_old, float* r, long n, cuda
 void range_correct(const double* h_old, const float* e, double* h, long n, cudaStream_t s);
 void range_sub_f32(const double* h, const double* base, float* out, long n, cudaStream_t s);
 void range_add_f64(const double* base, const float* inc, double* out, long n, cudaStream_t s);
-// the same steps on the orbit-layout prefix (the first nv^3 / 4 values) of `cells` cells,
-// cell stride n3
-void range_sub_f32_q(const double* h, const double* base, float* out, long cells, long n3, cudaStream_t s);
-void range_add_f64_q(const double* base, const float* inc, double* out, long cells, long n3, cudaStream_t s);
-void range_copy_q(const double* a, double* b, long cells, long n3, cudaStream_t s);
-// full grid <-> orbit layout of `cells` plate cells (FP64): unpack restores the R2 and R3 images
-void orbit_unpack_dev(const double* q, double* full, long cells, int nv, cudaStream_t s);
-void orbit_pack_dev(const double* full, double* q, long cells, int nv, cudaStream_t s);
-// the same steps for `cells` plate cells whose FP32 side is in the orbit layout (sweep.h)
-void range_widen_q(const float* e, double* h, long cells, int nv, cudaStream_t s);
-void range_correct_q(const double* h_old, const float* e, double* h, long cells, int nv, cudaStream_t s);
-void range_residual_q(const double* h, const double* h_old, float* r, long cells, int nv, cudaStream_t s);
+// the same steps on the orbit-layout prefix (the first nq values: nv^3 / 4 plates, nv^3 / 2
+// ducts) of `cells` cells, cell stride n3
+void range_sub_f32_q(const double* h, const double* base, float* out, long cells, long n3, long nq, cudaStream_t s);
+void range_add_f64_q(const double* base, const float* inc, double* out, long cells, long n3, long nq,
+                     cudaStream_t s);
+void range_copy_q(const double* a, double* b, long cells, long n3, long nq, cudaStream_t s);
+// full grid <-> orbit layout of `cells` cells (FP64; dim 1 plates, 2 ducts): unpack restores the
+// images of the orbit's representative
+void orbit_unpack_dev(const double* q, double* full, long cells, int nv, int dim, cudaStream_t s);
+void orbit_pack_dev(const double* full, double* q, long cells, int nv, int dim, cudaStream_t s);
+// the same steps for `cells` cells whose FP32 side is in the orbit layout (sweep.h; dim 1
+// plates, 2 ducts) and whose FP64 side is on the full grid
+void range_widen_q(const float* e, double* h, long cells, int nv, int dim, cudaStream_t s);
+void range_correct_q(const double* h_old, const float* e, double* h, long cells, int nv, int dim, cudaStream_t s);
+void range_residual_q(const double* h, const double* h_old, float* r, long cells, int nv, int dim, cudaStream_t s);
 
 }  // namespace lbe

@@ -56,12 +56,46 @@ __global__ void __launch_bounds__(256) k_lmoments_q(const T* __restrict__ Lh, co
     }
 }
 
+// The L-moments of a duct cell in the orbit layout (one value per orbit {1, R3}, at
+// (i1 nv + i2) nv / 2 + j3): v_j v3 (L h + nd h) is even under R3, so G_j is twice the half's
+// sum.  One thread per (i2, j3).
+template <typename T>
+__global__ void __launch_bounds__(512) k_lmoments_h(const T* __restrict__ Lh, const T* __restrict__ h,
+                                                    const double* __restrict__ nd, const T* __restrict__ vel,
+                                                    int nv, double dv3, double* __restrict__ G) {
+    __shared__ double red[32 * 2];
+    const int H = nv / 2;
+    const long cell = blockIdx.x;
+    const long n3 = (long)nv * nv * nv;
+    const T ndc = (T)nd[cell];
+    const int p = threadIdx.x;  // < nv H
+    const T v2 = vel[p / H], v3 = vel[p % H];
+    Acc<T> a0, a1;
+    for (int i1 = 0; i1 < nv; ++i1) {
+        const long idx = cell * n3 + (long)i1 * nv * H + p;
+        const T t = (Lh[idx] + ndc * h[idx]) * v3;
+        a0.add(vel[i1] * t);
+        a1.add(v2 * t);
+    }
+    double sm[2] = {a0.value(), a1.value()};
+    block_reduce<2>(sm, red);
+    if (threadIdx.x == 0) {
+        G[2 * cell + 0] = 4.0 * sm[0] * dv3;
+        G[2 * cell + 1] = 4.0 * sm[1] * dv3;
+    }
+}
+
+// quarter: 1 plates in the orbit layout, 2 ducts in the orbit layout
 template <typename T>
 void lmoments(const DevTables& t, int cells, const T* Lh, const T* h, const double* nd, double* G,
               cudaStream_t s, int quarter) {
     if (cells <= 0) return;
     g_launches += 1;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
+    if (quarter == 2) {
+        k_lmoments_h<T><<<cells, t.nv * (t.nv / 2), 0, s>>>(Lh, h, nd, vel, t.nv, t.dv * t.dv * t.dv, G);
+        return;
+    }
     if (quarter) {
         const int H = t.nv / 2, threads = (H * H + 31) / 32 * 32;
         k_lmoments_q<T><<<cells, threads, 0, s>>>(Lh, h, nd, vel, t.nv, t.dv * t.dv * t.dv, G);

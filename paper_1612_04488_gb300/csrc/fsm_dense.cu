@@ -611,13 +611,13 @@ __host__ __device__ inline bool blk_neg(int b, int mode, bool m1, bool m2, bool 
 // halves: (x_b(a, b) +- x_b(b, a)) / 2.  Each thread takes one unordered pair a <= b of (j1, j2)
 // and two neighbouring j3 (H is even): float2 loads of both orders' orbit points, bf16x2
 // stores.  A second loop writes the padding columns of every sub-block as zero.
-// quarter (plates): h in the orbit layout, where the points read (i2, i3 < nv / 2) are stored
-// at (i1 nv / 2 + i2) nv / 2 + i3.
+// quarter: h in the orbit layout, where the points read are stored at (i1 nv / 2 + i2) nv / 2 +
+// i3 (plates: i2, i3 < nv / 2) or (i1 nv + i2) nv / 2 + i3 (ducts: i3 < nv / 2).
 template <int NV, int MODE>
 __global__ void __launch_bounds__(256) k_gather_sub(const float* __restrict__ h, __nv_bfloat162* __restrict__ xo,
                                                     int cells, int cpad, int quarter) {
     constexpr int H = NV / 2, NBLK = MODE == 2 ? 2 : 4, NPAIR = H * (H + 1) / 2;
-    const int rs = MODE == 2 && quarter ? H : NV;  // row length and rows per plane of the data
+    const int R2 = MODE == 2 && quarter ? H : NV, R3 = quarter ? H : NV;  // i2, i3 values of the data
     constexpr SubLayout L = sub_layout(NV, MODE);
     constexpr long N3 = (long)NV * NV * NV;
     const long total = (long)cells * NPAIR * (H / 2);
@@ -640,14 +640,14 @@ __global__ void __launch_bounds__(256) k_gather_sub(const float* __restrict__ h,
 #pragma unroll
         for (int o = 0; o < 2; ++o) {
             const int j1 = o ? bb : aa, j2 = o ? aa : bb;
-            const float2 p0 = *reinterpret_cast<const float2*>(hc + (j1 * rs + j2) * rs + j3);
-            const float2 p1 = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * rs + j2) * rs + j3);
+            const float2 p0 = *reinterpret_cast<const float2*>(hc + (j1 * R2 + j2) * R3 + j3);
+            const float2 p1 = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * R2 + j2) * R3 + j3);
             if constexpr (MODE == 2) {
                 x[o][0] = make_float2(0.5f * (p0.x + p1.x), 0.5f * (p0.y + p1.y));
                 x[o][1] = make_float2(0.5f * (p0.x - p1.x), 0.5f * (p0.y - p1.y));
             } else {
-                const float2 p2 = *reinterpret_cast<const float2*>(hc + (j1 * NV + (NV - 1 - j2)) * NV + j3);
-                const float2 p3 = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * NV + (NV - 1 - j2)) * NV + j3);
+                const float2 p2 = *reinterpret_cast<const float2*>(hc + (j1 * R2 + (NV - 1 - j2)) * R3 + j3);
+                const float2 p3 = *reinterpret_cast<const float2*>(hc + ((NV - 1 - j1) * R2 + (NV - 1 - j2)) * R3 + j3);
                 const float2 s0 = make_float2(p0.x + p1.x, p0.y + p1.y), d0 = make_float2(p0.x - p1.x, p0.y - p1.y);
                 const float2 s1 = make_float2(p2.x + p3.x, p2.y + p3.y), d1 = make_float2(p2.x - p3.x, p2.y - p3.y);
                 x[o][0] = make_float2(0.25f * (s0.x + s1.x), 0.25f * (s0.y + s1.y));
@@ -846,6 +846,90 @@ __global__ void __launch_bounds__(256) k_expand_q(const float* __restrict__ Y, c
         G[2 * c + 0] = 8.0 * (double)sm[0] * dv3 + hm[2 * c + 0];
         G[2 * c + 1] = hm[2 * c + 1];
     }
+}
+
+// The duct expand in the orbit layout: L+ h at the stored half only (i3 < nv / 2, where the R3
+// sign is +1), optionally L h = L+ h - delta nu h (h in the orbit layout), and optionally
+// G_j = 2 sum_v v_j v3 L+ h dv^3 + hm_j as twice the half's sum (v_j v3 L+ h is even under R3).
+// The per-point arithmetic is that of k_expand_sub.
+template <int NV>
+__global__ void __launch_bounds__(256) k_expand_h(const float* __restrict__ Y, const float* __restrict__ vel,
+                                                  const double* __restrict__ delta, float* __restrict__ Lplus,
+                                                  double* __restrict__ G, double dv3,
+                                                  const double* __restrict__ hm, const float* __restrict__ h,
+                                                  const float* __restrict__ nu1, float* __restrict__ Lout) {
+    extern __shared__ __align__(16) float sY[];
+    __shared__ dfloat redx[32 * 2];
+    constexpr int H = NV / 2;
+    constexpr SubLayout L = sub_layout(NV, 1);  // S0, A0 (block 0), F1, F2, S3, A3 (block 3)
+    constexpr long n3 = (long)NV * NV * NV;
+    const long c = blockIdx.x;
+    const float* yc = Y + c * (long)L.rows;
+#pragma unroll
+    for (int q = 0; q < L.count; ++q)
+        for (int k = 4 * threadIdx.x; k < L.n[q]; k += 4 * blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sY + L.soff[q] + k)),
+                         "l"(yc + L.roff[q] + k)
+                         : "memory");
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    const float d = (float)delta[c];
+    float a0 = 0.f, c0 = 0.f, a1 = 0.f, c1 = 0.f;  // compensated sums of v1 v3 L+ h, v2 v3 L+ h
+    auto kahan = [](float& sum, float& comp, float x) {
+        const float y = x - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    };
+    for (int p = threadIdx.x; p < NV * NV * H; p += blockDim.x) {
+        const int i1 = p / (NV * H), i2 = (p / H) % NV, j3 = p % H;
+        const bool m1 = i1 >= H, m2 = i2 >= H;
+        const int j1 = m1 ? NV - 1 - i1 : i1, j2 = m2 ? NV - 1 - i2 : i2;
+        const int aa = j1 <= j2 ? j1 : j2, bb = j1 <= j2 ? j2 : j1;
+        float yb[4];
+#pragma unroll
+        for (int q = 0; q < L.count; ++q) {
+            const int b = L.blk[q];
+            if (L.kind[q] == 0) {
+                yb[b] = sY[L.soff[q] + (j1 * H + j2) * H + j3];
+            } else if (L.kind[q] == 1) {
+                yb[b] = sY[L.soff[q] + ts_idx(aa, bb) * H + j3];
+            } else if (aa != bb) {
+                const float ya = sY[L.soff[q] + ta_idx(aa, bb) * H + j3];
+                yb[b] += j1 < j2 ? ya : -ya;
+            }
+        }
+        float y = 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) y += blk_neg(b, 1, m1, m2, false) ? -yb[b] : yb[b];
+        const float lp = d * y;
+        Lplus[c * n3 + p] = lp;
+        if (Lout) Lout[c * n3 + p] = lp - d * nu1[(i1 * NV + i2) * NV + j3] * h[c * n3 + p];
+        if (G) {
+            const float t = lp * vel[j3];
+            kahan(a0, c0, vel[i1] * t);
+            kahan(a1, c1, vel[i2] * t);
+        }
+    }
+    if (!G) return;
+    dfloat sm[2] = {df_fast2sum(a0, -c0), df_fast2sum(a1, -c1)};
+    block_reduce_df<2>(sm, redx);
+    if (threadIdx.x == 0) {
+        G[2 * c + 0] = 4.0 * (double)sm[0] * dv3 + hm[2 * c + 0];
+        G[2 * c + 1] = 4.0 * (double)sm[1] * dv3 + hm[2 * c + 1];
+    }
+}
+
+template <int NV>
+void launch_expand_h(int cells, const float* Y, const float* vel, const double* delta, float* Lplus, double* G,
+                     double dv3, const double* hm, const float* h, const float* nu1, float* Lout, cudaStream_t s) {
+    static std::once_flag once;
+    constexpr int H = NV / 2;
+    const int smem = 4 * H * H * H * 4;
+    std::call_once(once, [smem] {
+        cudaFuncSetAttribute(k_expand_h<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+    k_expand_h<NV><<<cells, 256, smem, s>>>(Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout);
 }
 
 template <int NV, int MODE>
@@ -1322,7 +1406,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
                         float* Lout, cudaStream_t s, bool sync, const double* nd, double* G, const double* hm,
                         bool quarter) {
     if (mode != 1 && mode != 2) return LBE_BAD_ARG;
-    if (quarter && (mode != 2 || (G && (!hm || Lout)))) return LBE_BAD_ARG;
+    if (quarter && G && (!hm || Lout)) return LBE_BAD_ARG;
     if (cells <= 0) return LBE_OK;
     if (!t->tc) t->tc = new TcOperands();
     TcOperands& T = *t->tc;
@@ -1551,7 +1635,13 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         const float* vel = t->vel_f;
         const double dv3 = t->dv * t->dv * t->dv;
         const bool p2 = mode == 2;
-        if (quarter) switch (nv) {
+        if (quarter && !p2) switch (nv) {
+                case 8: launch_expand_h<8>(cells, Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout, s); break;
+                case 16: launch_expand_h<16>(cells, Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout, s); break;
+                case 24: launch_expand_h<24>(cells, Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout, s); break;
+                default: launch_expand_h<32>(cells, Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout, s); break;
+            }
+        else if (quarter) switch (nv) {
                 case 8: launch_expand_q<8>(cells, Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout, s); break;
                 case 16: launch_expand_q<16>(cells, Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout, s); break;
                 case 24: launch_expand_q<24>(cells, Y, vel, delta, Lplus, G, dv3, hm, h, nu1, Lout, s); break;

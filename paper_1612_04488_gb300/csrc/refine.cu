@@ -31,123 +31,129 @@ namespace lbe {
 
 namespace {
 
-// Orbit layout (sweep.h) index of the full-grid point f of a cell, and whether the point is the
-// R3 image (negated); and the full-grid index of the representative of orbit q.
-__device__ __forceinline__ long orbit_of(long f, int nv, bool* neg) {
+// Orbit layout (sweep.h; dim 1 plates, 2 ducts) index of the full-grid point f of a cell, and
+// whether the point is the R3 image (negated); and the full-grid index of the representative
+// of orbit q.
+__device__ __forceinline__ long orbit_of(long f, int nv, int dim, bool* neg) {
     const int H = nv / 2;
     const int i3 = (int)(f % nv), i2 = (int)((f / nv) % nv), i1 = (int)(f / ((long)nv * nv));
     *neg = i3 >= H;
-    const int j2 = i2 < H ? i2 : nv - 1 - i2, j3 = i3 < H ? i3 : nv - 1 - i3;
+    const int j3 = i3 < H ? i3 : nv - 1 - i3;
+    if (dim == 2) return ((long)i1 * nv + i2) * H + j3;
+    const int j2 = i2 < H ? i2 : nv - 1 - i2;
     return ((long)i1 * H + j2) * H + j3;
 }
-__device__ __forceinline__ long full_of(long q, int nv) {
+__device__ __forceinline__ long full_of(long q, int nv, int dim) {
     const int H = nv / 2;
-    const int j3 = (int)(q % H), j2 = (int)((q / H) % H), i1 = (int)(q / ((long)H * H));
+    const int R2 = dim == 2 ? nv : H;  // i2 values of the layout
+    const int j3 = (int)(q % H), j2 = (int)((q / H) % R2), i1 = (int)(q / ((long)R2 * H));
     return ((long)i1 * nv + j2) * nv + j3;
 }
+__host__ __device__ inline long orbit_values(long n3, int dim) { return dim == 2 ? n3 / 2 : n3 / 4; }
 
 }  // namespace
 
-// The element-wise steps between the FP64 iterate and the FP32 correction of a range of cells
-// whose FP32 side is in the orbit layout (plates of a tensor-core batch).
-__global__ void k_range_widen_q(const float* __restrict__ e, double* __restrict__ h, long cells, int nv) {
+// The element-wise steps between the FP64 iterate (full grid) and the FP32 correction of a range
+// of cells (orbit layout: the service's buckets).
+__global__ void k_range_widen_q(const float* __restrict__ e, double* __restrict__ h, long cells, int nv, int dim) {
     const long n3 = (long)nv * nv * nv, n = cells * n3;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
         const long f = k % n3;
         bool neg;
-        const double v = (double)e[k - f + orbit_of(f, nv, &neg)];
+        const double v = (double)e[k - f + orbit_of(f, nv, dim, &neg)];
         h[k] = neg ? -v : v;
     }
 }
 __global__ void k_range_correct_q(const double* __restrict__ h_old, const float* __restrict__ e,
-                                  double* __restrict__ h, long cells, int nv) {
+                                  double* __restrict__ h, long cells, int nv, int dim) {
     const long n3 = (long)nv * nv * nv, n = cells * n3;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
         const long f = k % n3;
         bool neg;
-        const double v = (double)e[k - f + orbit_of(f, nv, &neg)];
+        const double v = (double)e[k - f + orbit_of(f, nv, dim, &neg)];
         h[k] = h_old[k] + (neg ? -v : v);
     }
 }
 __global__ void k_range_residual_q(const double* __restrict__ h, const double* __restrict__ h_old,
-                                   float* __restrict__ r, long cells, int nv) {
-    const long n3 = (long)nv * nv * nv, nq = n3 / 4, n = cells * nq;
+                                   float* __restrict__ r, long cells, int nv, int dim) {
+    const long n3 = (long)nv * nv * nv, nq = orbit_values(n3, dim), n = cells * nq;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
-        const long c = k / nq, q = k % nq, f = c * n3 + full_of(q, nv);
+        const long c = k / nq, q = k % nq, f = c * n3 + full_of(q, nv, dim);
         r[c * n3 + q] = (float)(h[f] - h_old[f]);
     }
 }
-void range_widen_q(const float* e, double* h, long cells, int nv, cudaStream_t s) {
+void range_widen_q(const float* e, double* h, long cells, int nv, int dim, cudaStream_t s) {
     g_launches += 1;
-    k_range_widen_q<<<sm_count(), 256, 0, s>>>(e, h, cells, nv);
+    k_range_widen_q<<<sm_count(), 256, 0, s>>>(e, h, cells, nv, dim);
 }
-void range_correct_q(const double* h_old, const float* e, double* h, long cells, int nv, cudaStream_t s) {
+void range_correct_q(const double* h_old, const float* e, double* h, long cells, int nv, int dim, cudaStream_t s) {
     g_launches += 1;
-    k_range_correct_q<<<sm_count(), 256, 0, s>>>(h_old, e, h, cells, nv);
+    k_range_correct_q<<<sm_count(), 256, 0, s>>>(h_old, e, h, cells, nv, dim);
 }
-void range_residual_q(const double* h, const double* h_old, float* r, long cells, int nv, cudaStream_t s) {
+void range_residual_q(const double* h, const double* h_old, float* r, long cells, int nv, int dim, cudaStream_t s) {
     g_launches += 1;
-    k_range_residual_q<<<sm_count(), 256, 0, s>>>(h, h_old, r, cells, nv);
+    k_range_residual_q<<<sm_count(), 256, 0, s>>>(h, h_old, r, cells, nv, dim);
 }
 
 __global__ void k_range_sub_f32_q(const double* __restrict__ h, const double* __restrict__ b, float* __restrict__ o,
-                                  long cells, long n3) {
-    const long nq = n3 / 4, n = cells * nq;
+                                  long cells, long n3, long nq) {
+    const long n = cells * nq;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
         const long i = (k / nq) * n3 + k % nq;
         o[i] = (float)(h[i] - b[i]);
     }
 }
 __global__ void k_range_add_f64_q(const double* __restrict__ b, const float* __restrict__ inc,
-                                  double* __restrict__ o, long cells, long n3) {
-    const long nq = n3 / 4, n = cells * nq;
+                                  double* __restrict__ o, long cells, long n3, long nq) {
+    const long n = cells * nq;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
         const long i = (k / nq) * n3 + k % nq;
         o[i] = b[i] + (double)inc[i];
     }
 }
-__global__ void k_range_copy_q(const double* __restrict__ a, double* __restrict__ b, long cells, long n3) {
-    const long nq = n3 / 4, n = cells * nq;
+__global__ void k_range_copy_q(const double* __restrict__ a, double* __restrict__ b, long cells, long n3, long nq) {
+    const long n = cells * nq;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
         const long i = (k / nq) * n3 + k % nq;
         b[i] = a[i];
     }
 }
-__global__ void k_orbit_unpack(const double* __restrict__ q, double* __restrict__ full, long cells, int nv) {
+__global__ void k_orbit_unpack(const double* __restrict__ q, double* __restrict__ full, long cells, int nv, int dim) {
     const long n3 = (long)nv * nv * nv, n = cells * n3;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
         const long f = k % n3;
         bool neg;
-        const double v = q[k - f + orbit_of(f, nv, &neg)];
+        const double v = q[k - f + orbit_of(f, nv, dim, &neg)];
         full[k] = neg ? -v : v;
     }
 }
-__global__ void k_orbit_pack(const double* __restrict__ full, double* __restrict__ q, long cells, int nv) {
-    const long n3 = (long)nv * nv * nv, nq = n3 / 4, n = cells * nq;
+__global__ void k_orbit_pack(const double* __restrict__ full, double* __restrict__ q, long cells, int nv, int dim) {
+    const long n3 = (long)nv * nv * nv, nq = orbit_values(n3, dim), n = cells * nq;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n; k += (long)gridDim.x * blockDim.x) {
         const long c = k / nq, r = k % nq;
-        q[c * n3 + r] = full[c * n3 + full_of(r, nv)];
+        q[c * n3 + r] = full[c * n3 + full_of(r, nv, dim)];
     }
 }
-void range_sub_f32_q(const double* h, const double* base, float* out, long cells, long n3, cudaStream_t s) {
+void range_sub_f32_q(const double* h, const double* base, float* out, long cells, long n3, long nq, cudaStream_t s) {
     g_launches += 1;
-    k_range_sub_f32_q<<<2 * sm_count(), 256, 0, s>>>(h, base, out, cells, n3);
+    k_range_sub_f32_q<<<2 * sm_count(), 256, 0, s>>>(h, base, out, cells, n3, nq);
 }
-void range_add_f64_q(const double* base, const float* inc, double* out, long cells, long n3, cudaStream_t s) {
+void range_add_f64_q(const double* base, const float* inc, double* out, long cells, long n3, long nq,
+                     cudaStream_t s) {
     g_launches += 1;
-    k_range_add_f64_q<<<2 * sm_count(), 256, 0, s>>>(base, inc, out, cells, n3);
+    k_range_add_f64_q<<<2 * sm_count(), 256, 0, s>>>(base, inc, out, cells, n3, nq);
 }
-void range_copy_q(const double* a, double* b, long cells, long n3, cudaStream_t s) {
+void range_copy_q(const double* a, double* b, long cells, long n3, long nq, cudaStream_t s) {
     g_launches += 1;
-    k_range_copy_q<<<2 * sm_count(), 256, 0, s>>>(a, b, cells, n3);
+    k_range_copy_q<<<2 * sm_count(), 256, 0, s>>>(a, b, cells, n3, nq);
 }
-void orbit_unpack_dev(const double* q, double* full, long cells, int nv, cudaStream_t s) {
+void orbit_unpack_dev(const double* q, double* full, long cells, int nv, int dim, cudaStream_t s) {
     g_launches += 1;
-    k_orbit_unpack<<<2 * sm_count(), 256, 0, s>>>(q, full, cells, nv);
+    k_orbit_unpack<<<2 * sm_count(), 256, 0, s>>>(q, full, cells, nv, dim);
 }
-void orbit_pack_dev(const double* full, double* q, long cells, int nv, cudaStream_t s) {
+void orbit_pack_dev(const double* full, double* q, long cells, int nv, int dim, cudaStream_t s) {
     g_launches += 1;
-    k_orbit_pack<<<2 * sm_count(), 256, 0, s>>>(full, q, cells, nv);
+    k_orbit_pack<<<2 * sm_count(), 256, 0, s>>>(full, q, cells, nv, dim);
 }
 
 namespace {
@@ -156,7 +162,7 @@ namespace {
 // cell, or with quarter the orbit-layout prefix (nv^3 / 4) of a plate's cells (sweep.h), where
 // both sides of the step are in that layout.
 __device__ __forceinline__ long job_values(const SweepJobDev& jb, long n3, int quarter) {
-    return quarter && jb.ny == 0 ? n3 / 4 : n3;
+    return quarter ? (jb.ny == 0 ? n3 / 4 : n3 / 2) : n3;
 }
 
 // dst = src over the cells of the active jobs
@@ -370,24 +376,18 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         long cells = 0;
         for (int j = j0; j < j1; ++j) cells += O.sj[j].ncell;
         const long o = O.cell_off[j0] * n3;
-        const bool plates = O.geo[j0].dim == 1;
+        const int dim = O.geo[j0].dim;
         const double* h = O.h.as<double>() + o;
-        if (q && plates)
-            orbit_unpack_dev(h, base_h + o, cells, nv, s);
+        if (q)
+            orbit_unpack_dev(h, base_h + o, cells, nv, dim, s);
         else
             range_copy(h, base_h + o, cells * n3, s);
         fsm_df_apply(*O.t, (int)cells, O.delta.as<double>() + O.cell_off[j0], base_h + o, base_lp + o, base_lh + o,
-                     O.scratch.p, O.chunk, s, plates ? 2 : 1);
+                     O.scratch.p, O.chunk, s, dim == 1 ? 2 : 1);
         if (!q) return;
-        if (plates) {
-            range_copy_q(h, bq_h + o, cells, n3, s);
-            orbit_pack_dev(base_lp + o, bq_lp + o, cells, nv, s);
-            orbit_pack_dev(base_lh + o, bq_lh + o, cells, nv, s);
-        } else {
-            range_copy(base_h + o, bq_h + o, cells * n3, s);
-            range_copy(base_lp + o, bq_lp + o, cells * n3, s);
-            range_copy(base_lh + o, bq_lh + o, cells * n3, s);
-        }
+        range_copy_q(h, bq_h + o, cells, n3, dim == 1 ? n3 / 4 : n3 / 2, s);
+        orbit_pack_dev(base_lp + o, bq_lp + o, cells, nv, dim, s);
+        orbit_pack_dev(base_lh + o, bq_lh + o, cells, nv, dim, s);
     };
     std::vector<int> outer_it(n, 0), inner_it(n, 0), refs(n, 0);
     std::vector<double> t_done(n, 0.0);
@@ -497,7 +497,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             }
             for (auto& r : merged)
                 launch_moments<double>(*O.t, r.c0, (int)r.n, O.h.as<double>(), O.mom.as<double>(), s,
-                                       q && r.dim == 1);
+                                       q ? r.dim : 0);
         }
         k_set_rates<<<na, 32, 0, s>>>(O.ijobs.as<SisJobDev>(), O.act.as<int>(), O.mom.as<double>(),
                                       O.coef.as<double>(), O.states.as<JobState>());
@@ -528,7 +528,7 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
             if (plain[j] && rel > 0.9 * pr) rebase[j] = 1;  // plain steps stalled: re-centre the operator
             if (trace) {
                 const long o = O.cell_off[j] * n3, nn = (long)O.sj[j].ncell * n3;
-                const long per = q && O.geo[j].dim == 1 ? n3 / 4 : n3;  // values held per cell
+                const long per = q ? (O.geo[j].dim == 1 ? n3 / 4 : n3 / 2) : n3;  // values held per cell
                 std::vector<double> hh(nn), hb(nn);
                 cudaMemcpy(hh.data(), h_old + o, nn * 8, cudaMemcpyDeviceToHost);
                 cudaMemcpy(hb.data(), bq_h + o, nn * 8, cudaMemcpyDeviceToHost);
@@ -603,13 +603,12 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
         }
         if (st == LBE_OK && h_out) {
             st = cuda_status(c, cudaMemcpy(h_out, O.h.p, vol64, cudaMemcpyDeviceToHost), "h");
-            if (st == LBE_OK && q) {  // plates back to the full grid
+            if (st == LBE_OK && q) {  // back to the full grid
                 std::vector<double> hq;
                 for (int j = 0; j < n; ++j) {
-                    if (O.geo[j].dim != 1) continue;
                     const long o = O.cell_off[j] * n3, nn = (long)O.sj[j].ncell * n3;
                     hq.assign(h_out + o, h_out + o + nn);
-                    orbit_unpack_host(nv, O.sj[j].ncell, hq.data(), h_out + o);
+                    orbit_unpack_host(nv, O.sj[j].ncell, hq.data(), h_out + o, O.geo[j].dim);
                 }
             }
         }

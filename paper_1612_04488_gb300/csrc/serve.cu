@@ -512,12 +512,13 @@ static void service_main(Ctx* c) {
                     double* hold = D->aux.as<double>() + D->B.cell_off[sj->ds] * n3;
                     const float* e = F->B.h.as<float>() + F->B.cell_off[sj->fs] * n3;
                     cudaStream_t ds = D->stream;
-                    // plates of a tensor-core bucket: e in the orbit layout
-                    const bool q = F->B.quarter() && F->B.geo[sj->fs].dim == 1;
+                    // a tensor-core bucket: e in the orbit layout (plates a quarter, ducts a half)
+                    const bool q = F->B.quarter();
+                    const int dim = F->B.geo[sj->fs].dim;
                     const long nc = F->B.sj[sj->fs].ncell;
                     if (sj->phase == 1) {
                         if (q)
-                            range_widen_q(e, h, nc, F->nv, ds);
+                            range_widen_q(e, h, nc, F->nv, dim, ds);
                         else
                             range_widen(e, h, n, ds);
                         // the request's one FP64 collision-operator evaluation, at h0
@@ -535,7 +536,7 @@ static void service_main(Ctx* c) {
                                         cudaMemcpyHostToDevice, ds);
                     } else {
                         if (q)
-                            range_correct_q(hold, e, h, nc, F->nv, ds);
+                            range_correct_q(hold, e, h, nc, F->nv, dim, ds);
                         else
                             range_correct(hold, e, h, n, ds);
                         ++sj->refs;
@@ -566,8 +567,8 @@ static void service_main(Ctx* c) {
                     const double* h = D->B.h.as<double>() + D->B.cell_off[sj->ds] * n3;
                     const double* hold = D->aux.as<double>() + D->B.cell_off[sj->ds] * n3;
                     float* r = F->aux.as<float>() + F->B.cell_off[sj->fs] * n3;
-                    if (F->B.quarter() && F->B.geo[sj->fs].dim == 1)
-                        range_residual_q(h, hold, r, D->B.sj[sj->ds].ncell, F->nv, D->stream);
+                    if (F->B.quarter())
+                        range_residual_q(h, hold, r, D->B.sj[sj->ds].ncell, F->nv, F->B.geo[sj->fs].dim, D->stream);
                     else
                         range_residual(h, hold, r, n, D->stream);
                     cudaStreamSynchronize(D->stream);

@@ -401,12 +401,13 @@ __global__ void __launch_bounds__(128) k_sweep2d(const T* __restrict__ rhs, T* _
                                                  const T* __restrict__ feq,
                                                  const SweepJobDev* __restrict__ jobs,
                                                  const int* __restrict__ active,
-                                                 const double* __restrict__ coef, int nv, int staged) {
+                                                 const double* __restrict__ coef, int nv, int staged, int half) {
     extern __shared__ __align__(16) unsigned char sweep_smem[];
     const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
     const int n2 = nv * nv;
     const long n3 = (long)n2 * nv;
     const int nx = jb.nx, ny = jb.ny;
+    const int W3 = half ? nv / 2 : nv;  // i3 values of the data (half: the v3 < 0 half)
     // [xa|xb|xc] (nx each) [ya|yb|yc] (ny each), staged as in the 1D sweep
     const double* cg = coef + jb.coef_off;
     T* sc = reinterpret_cast<T*>(sweep_smem);
@@ -416,14 +417,15 @@ __global__ void __launch_bounds__(128) k_sweep2d(const T* __restrict__ rhs, T* _
     }
     auto CX = [&](int a, int i) -> T { return staged ? sc[a * nx + i] : (T)cg[a * nx + i]; };
     auto CY = [&](int a, int j) -> T { return staged ? sc[3 * nx + a * ny + j] : (T)cg[3 * nx + a * ny + j]; };
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n3) return;
-    const int i1 = v / n2, i2 = (v / nv) % nv;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;  // in the data
+    if (v >= n2 * W3) return;
+    const int i1 = v / (nv * W3), i2 = (v / W3) % nv, i3 = v % W3;
+    const int vf = (i1 * nv + i2) * nv + i3;  // in the tables
     const bool s1 = i1 >= nv / 2, s2 = i2 >= nv / 2;
     const T u1 = s1 ? vel[i1] : -vel[i1];
     const T u2 = s2 ? vel[i2] : -vel[i2];
-    const T nu = (T)jb.delta * nu1[v];
-    const T S = source<T>(jb.forcing, vel[i1], vel[i2], vel[v % nv], feq[v]);
+    const T nu = (T)jb.delta * nu1[vf];
+    const T S = source<T>(jb.forcing, vel[i1], vel[i2], vel[i3], feq[vf]);
     const T* r = rhs + jb.cell_off * n3;
     T* o = h + jb.cell_off * n3;
     const int dj = s2 ? -1 : 1;  // offset to the upwind row in j
@@ -486,7 +488,7 @@ __global__ void __launch_bounds__(32 * WR) k_sweep2d_wave(const T* __restrict__ 
                                                           const T* __restrict__ feq,
                                                           const SweepJobDev* __restrict__ jobs,
                                                           const int* __restrict__ active,
-                                                          const double* __restrict__ coef, int nv) {
+                                                          const double* __restrict__ coef, int nv, int half) {
     constexpr int D = 8;
     extern __shared__ __align__(16) unsigned char sweep_smem[];
     const SweepJobDev jb = jobs[active ? active[blockIdx.y] : blockIdx.y];
@@ -500,15 +502,17 @@ __global__ void __launch_bounds__(32 * WR) k_sweep2d_wave(const T* __restrict__ 
     const double* cg = coef + jb.coef_off;
     for (int k = threadIdx.x; k < 3 * (nx + ny); k += blockDim.x) cxs[k] = (T)cg[k];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int v = blockIdx.x * 32 + lane;
-    const bool vok = v < n3;
+    const int W3 = half ? nv / 2 : nv;  // i3 values of the data (half: the v3 < 0 half)
+    const int v = blockIdx.x * 32 + lane;  // in the data
+    const bool vok = v < n2 * W3;
     const int vv = vok ? v : 0;
-    const int i1 = vv / n2, i2 = (vv / nv) % nv;
+    const int i1 = vv / (nv * W3), i2 = (vv / W3) % nv, i3 = vv % W3;
+    const int vf = (i1 * nv + i2) * nv + i3;  // in the tables
     const bool s1 = i1 >= nv / 2, s2 = i2 >= nv / 2;
     const T u1 = s1 ? vel[i1] : -vel[i1];
     const T u2 = s2 ? vel[i2] : -vel[i2];
-    const T nu = (T)jb.delta * nu1[vv];
-    const T S = source<T>(jb.forcing, vel[i1], vel[i2], vel[vv % nv], feq[vv]);
+    const T nu = (T)jb.delta * nu1[vf];
+    const T S = source<T>(jb.forcing, vel[i1], vel[i2], vel[i3], feq[vf]);
     const T* r = rhs + jb.cell_off * n3;
     T* o = h + jb.cell_off * n3;
     __syncthreads();
@@ -705,6 +709,47 @@ __global__ void __launch_bounds__(256) k_moments_q(const T* __restrict__ h, cons
             for (int k = 0; k < 4; ++k) mom[cell * 5 + k] = 4.0 * s[k] * dv3;
             mom[cell * 5 + 4] = 0.0;
         }
+    }
+}
+
+// The same moments of a duct cell in the orbit layout (h[i1][i2][j3], j3 < nv / 2: one value per
+// orbit {1, R3} of the parity odd in v3).  All five integrands are even under R3, so each is
+// twice its sum over the stored half.  One thread per (i2, j3).
+template <typename T, int NV>
+__global__ void __launch_bounds__(512) k_moments_h(const T* __restrict__ h, const T* __restrict__ vel, double dv3,
+                                                   long cell0, double* __restrict__ mom) {
+    constexpr int H = NV / 2;
+    constexpr long n3 = (long)NV * NV * NV;
+    const long cell = cell0 + blockIdx.x;
+    const int p = threadIdx.x;  // < NV * H
+    const T v2 = vel[p / H], v3 = vel[p % H];
+    Acc<T> S0, S1, S4;  // sums of h, v1^2 h and v1 h over i1
+    const T* hc = h + cell * n3 + p;
+    for (int i1 = 0; i1 < NV; ++i1) {
+        const T v1 = vel[i1], x = hc[(long)i1 * NV * H];
+        S0.add(x);
+        S1.add(v1 * v1 * x);
+        S4.add(v1 * x);
+    }
+    if constexpr (sizeof(T) == 4) {
+        __shared__ dfloat redx[32 * 5];
+        const dfloat a0 = S0.pair(), a2 = S1.pair(), a4 = S4.pair();
+        const dfloat a3 = dfloat((float)(v2 * v2), 0.f) * a0;
+        const dfloat w3((float)v3, 0.f), w3s = w3 * w3;
+        dfloat sm[5] = {w3 * a0, w3 * ((a2 + a3) + (w3s - dfloat(2.5f, 0.f)) * a0), w3 * ((a2 + a2) - a0),
+                        w3 * ((a3 + a3) - a0), (w3 + w3) * (dfloat((float)v2, 0.f) * a4)};
+        block_reduce_df<5>(sm, redx);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 5; ++k) mom[cell * 5 + k] = 2.0 * (double)sm[k] * dv3;
+    } else {
+        __shared__ double red[32 * 5];
+        const double a0 = S0.value(), a2 = S1.value(), a4 = S4.value(), w2 = (double)v2, w3 = (double)v3;
+        const double a3 = w2 * w2 * a0;
+        double sm[5] = {w3 * a0, w3 * (a2 + a3 + (w3 * w3 - 2.5) * a0), w3 * (2.0 * a2 - a0), w3 * (2.0 * a3 - a0),
+                        2.0 * w3 * w2 * a4};
+        block_reduce<5>(sm, red);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 5; ++k) mom[cell * 5 + k] = 2.0 * sm[k] * dv3;
     }
 }
 
@@ -941,7 +986,10 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
     const SweepJobDev jb = jobs[jid];
     const int n3 = nv * nv * nv, hv = nv / 2;
     const bool plates = jb.ny == 0;  // 1D: orbits {1, R2, R3, R2R3}; 2D: {1, R3}
-    if (plates && quarter == 2) return;  // plates done by k_correct_q
+    // quarter: bit 0 plates in the orbit layout (handled here), bit 1 plates done by k_correct_q
+    // (skipped here), bit 2 ducts in the orbit layout (one value per orbit {1, R3}, at index r)
+    if (plates && (quarter & 2)) return;
+    const bool dhalf = !plates && (quarter & 4);
     const int norb = plates ? n3 / 4 : n3 / 2;
     const bool only_hm = hh == nullptr;  // hm of the stored h alone (a resumed solve); h unchanged
     for (int c = blockIdx.x; c < jb.ncell; c += gridDim.x) {
@@ -976,7 +1024,7 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
                 kahan(a1, c1, (float)vel[i2] * t);
             }
         };
-        if (plates && quarter) {
+        if (plates && (quarter & 1)) {
             // orbit layout: the orbit's one stored value sits at index r.  Four orbits per
             // thread and pass, their loads issued together (the same order of sums as one at
             // a time).
@@ -1023,7 +1071,10 @@ __global__ void __launch_bounds__(256) k_correct(const T* __restrict__ hh, T* __
                 const int vb = (i1 * nv + nv - 1 - i2) * nv + i3;           // R2 (plates)
                 const int vd = (i1 * nv + nv - 1 - i2) * nv + nv - 1 - i3;  // R2 R3 (plates)
                 T y;
-                if (only_hm) {
+                if (dhalf) {  // the orbit's one stored value at index r
+                    y = only_hm ? dst[r] : (ex ? src[r] + ex[r] : src[r]) + d * vel[i3] * feq[va];
+                    if (!only_hm) dst[r] = y;
+                } else if (only_hm) {
                     y = dst[va];
                 } else {
                     T xa = src[va], xc = src[vc];
@@ -1242,7 +1293,7 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
         // the wavefront: blocks of 32 velocities x 16 rows; shared memory holds the
         // coefficients, the 3-step ring and the strip's last two rows
         constexpr int WR = 16;
-        const int nt = nv * nv * nv;
+        const int nt = quarter ? nv * nv * (nv / 2) : nv * nv * nv;  // ducts: quarter = the half layout
         const int mcx = max_coef / 3;  // largest nx + ny of the launch's jobs
         const size_t sm2 = (size_t)(3 * mcx + 3 * WR * 32 + 2 * mcx * 32) * sizeof(T);
         static std::once_flag attr;
@@ -1251,10 +1302,10 @@ void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T*
         });
         if (sm2 <= 160 * 1024) {
             dim3 g((nt + 31) / 32, njobs);
-            k_sweep2d_wave<T, WR><<<g, 32 * WR, sm2, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv);
+            k_sweep2d_wave<T, WR><<<g, 32 * WR, sm2, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv, quarter);
         } else {
             dim3 g((nt + 127) / 128, njobs);
-            k_sweep2d<T><<<g, 128, smem, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv, staged);
+            k_sweep2d<T><<<g, 128, smem, s>>>(rhs, h, nu1, vel, feq, jobs, active, coef, nv, staged, quarter);
         }
     }
 }
@@ -1266,6 +1317,15 @@ void launch_moments(const DevTables& t, long cell0, int cells, const T* h, doubl
     g_launches += 1;
     const T* vel = sizeof(T) == 8 ? (const T*)t.vel_d : (const T*)t.vel_f;
     const double dv3 = t.dv * t.dv * t.dv;
+    if (quarter == 2) {  // ducts in the orbit layout (the half)
+        switch (t.nv) {
+            case 8: k_moments_h<T, 8><<<cells, 32, 0, s>>>(h, vel, dv3, cell0, mom); break;
+            case 16: k_moments_h<T, 16><<<cells, 128, 0, s>>>(h, vel, dv3, cell0, mom); break;
+            case 24: k_moments_h<T, 24><<<cells, 288, 0, s>>>(h, vel, dv3, cell0, mom); break;
+            default: k_moments_h<T, 32><<<cells, 512, 0, s>>>(h, vel, dv3, cell0, mom); break;
+        }
+        return;
+    }
     if (quarter) {
         switch (t.nv) {
             case 8: k_moments_q<T, 8><<<cells, 32, 0, s>>>(h, vel, dv3, cell0, mom); break;
@@ -1315,10 +1375,11 @@ void launch_correct(const DevTables& t, int njobs, const T* hh, T* h, const doub
         }
         if (!ducts) return;
         g_launches += 1;
-        k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1, dv3, 2);
+        k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1, dv3, 2 | 4);
         return;
     }
-    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1, dv3, quarter);
+    k_correct<T><<<g, 256, 0, s>>>(hh, h, dU, extra, feq, vel, jobs, active, t.nv, state, hm, nd, nu1, dv3,
+                                   quarter ? 1 | 4 : 0);
 }
 
 template void launch_sweep<double>(const DevTables&, int, int, int, const double*, double*,

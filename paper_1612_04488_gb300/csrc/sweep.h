@@ -13,7 +13,8 @@ struct Ctx;
 // fsm_dense.cu: tensor-core operator on the parity subspace (float in / out; mode 1 or 2)
 // hm (may be NULL): per cell the h part of G (launch_correct); with it and without Lout the
 // expand reads no h.
-// quarter (mode 2 only): h, Lplus and Lout in the orbit layout (below); G needs hm and no Lout.
+// quarter: h, Lplus and Lout in the orbit layout (below; plates a quarter, ducts a half); G needs
+// hm and no Lout.
 lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h,
                         float* Lplus, float* Lout, cudaStream_t s, bool sync = true, const double* nd = nullptr,
                         double* G = nullptr, const double* hm = nullptr, bool quarter = false);
@@ -58,11 +59,13 @@ struct JobState {
     int iters, done, nan, skip;
 };
 
-// Orbit layout ("quarter"): a plate iterate is odd in v3 and even in v2, so each cell keeps one
-// value per orbit {1, R2, R3, R2 R3} -- the points with i2, i3 < nv / 2 -- at index
-// (i1 nv / 2 + i2) nv / 2 + i3 in the first nv^3 / 4 places of the cell's nv^3 (the cell stride
-// is unchanged).  h(i1, nv-1-i2, i3) = h(i1, i2, i3) and h(i1, i2, nv-1-i3) = -h(i1, i2, i3).
-// The FP32 iterations of the tensor-core operator use it for plates (1D problems).
+// Orbit layout ("quarter" flags): each cell keeps one value per orbit of its problem's parity
+// group, in the first places of the cell's nv^3 (the cell stride is unchanged).
+//   plates (1D, odd in v3, even in v2): orbits {1, R2, R3, R2 R3}, the points i2, i3 < nv / 2 at
+//     (i1 nv / 2 + i2) nv / 2 + i3 (a quarter); h(i1, nv-1-i2, i3) = h(i1, i2, i3);
+//   ducts (2D, odd in v3): orbits {1, R3}, the points i3 < nv / 2 at (i1 nv + i2) nv / 2 + i3
+//     (a half);
+// and in both h(i1, i2, nv-1-i3) = -h(i1, i2, i3).  The tensor-core batches use it.
 template <typename T>
 void launch_sweep(const DevTables& t, int dim, int njobs, int max_coef, const T* rhs, T* h,
                   const SweepJobDev* jobs, const int* active, const double* coef, cudaStream_t s,

@@ -199,3 +199,17 @@ def test_bf16_plate_iterate_symmetric_and_near_fp64(ctx, prec, eps, tol):
     assert np.array_equal(hb[:, :, :, ::-1], -hb)
     scale = np.abs(h64).max()
     assert np.abs(hb - h64).max() <= tol * scale
+
+
+@pytest.mark.parametrize("prec,eps,tol", [(lbe.BF16, 1e-6, 1e-4), (lbe.BF16_REFINED, 1e-9, 1e-6)])
+def test_bf16_duct_iterate_odd_and_near_fp64(ctx, prec, eps, tol):
+    """Duct iterates of the tensor-core paths keep one value per orbit of the v3 reflection (half
+    of each cell); returned on the full grid they are exactly odd in v3 and near the FP64 iterate."""
+    base = dict(dim=2, nx=10, ny=6, width=1.6, delta=2.0, nv=16, vmax=6.0, M=16, R=4.5, scheme=lbe.SIS,
+                max_iter=300)
+    r64, _, h64 = ctx.solve(lbe.problem(**base, precision=lbe.FP64, eps=1e-10), want_h=True)
+    rb, _, hb = ctx.solve(lbe.problem(**base, precision=prec, eps=eps), want_h=True)
+    assert rb.status == lbe.OK and r64.status == lbe.OK
+    assert np.array_equal(hb[:, :, :, ::-1], -hb)
+    scale = np.abs(h64).max()
+    assert np.abs(hb - h64).max() <= tol * scale
