@@ -18,6 +18,9 @@ Plain, slow and written for reading against the paper:
                    diffusion_LBE, guided, with the N-penalty of Sec. 2.5 footnote).
 * ``eig``       -- Fourier-mode eigenvalue analysis (Sec. 2.3, Eqs. conv_iteration,
                    acceleratred_iteration).
+* ``mixture``   -- binary hard-sphere mixture (Sec. 4): the four linearized collision
+                   operators in a dense spectral form, the viscosity that fixes delta, and
+                   the SIS of Eqs. LBE2_true1 / LBE2_true2 for plates.
 
 Every floating-point quantity is float64.  Parity status of each function is stated in
 its module docstring; functions without an independent pin say "parity unpinned".
