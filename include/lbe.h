@@ -332,6 +332,80 @@ lbe_status lbe_tuning_report(lbe_ctx* ctx, char* buf, size_t cap);
  * returns, and the call returns LBE_TIMEOUT.  The context stays usable.  Process-wide. */
 lbe_status lbe_debug_expire_waits(int on);
 
+/* ---- Binary hard-sphere mixture (Sec. 4) ------------------------------------------------
+ * Species A and B: masses m_A, m_B, hard-sphere diameters d_A, d_B (collision diameter
+ * (d_a + d_b) / 2), molar fractions chi_A and chi_B = 1 - chi_A.  Velocities are in units
+ * of v_mA, the most probable speed of A, so f_a,eq = chi_a (r_a / pi)^(3/2) exp(-r_a |v|^2)
+ * with r_a = m_a / m_A (Sec. 4, Eq. Maxwell), and
+ *   L_a h = sum_b Q_ab(f_a,eq, h_b) + Q_ab(h_a, f_b,eq)        (Sec. 4, Eq. Boltzmann_lin).
+ * The paper cites its spectral method for Q_ab without writing it out; this library derives
+ * it from the collision integral.  With mu_b = m_b / (m_a + m_b) and x ⊥ y, the pre- and
+ * post-collision velocities are v* = v + x + y, v' = v + 2 mu_b x, v*' = v + (mu_b - mu_a) x + y,
+ * and hard spheres give the constant Carleman kernel d_ab^2.  The gain's kernel modes are
+ *   beta_ab(l, m) = sum_p w'_p phi((2 mu_b xi_l + (mu_b - mu_a) xi_m) . e_p) psi_p(m),
+ * with the single-species phi, psi, hemisphere rule, truncation R and Nyquist zeroing; equal
+ * masses and diameters reproduce the single-species operator exactly.  Unless the masses are
+ * equal, phi's argument mixes the two spectra, so the gain is no sum of products of
+ * transforms: the library builds the operator once per (mixture, grid) as a dense FP64
+ * matrix on the device (O(nv^6 M) work and about 8 nv^6 bytes of temporary device memory)
+ * and applies it as an FP64 GEMM.
+ * delta = p0 l / (mu v_m) with v_m = sqrt(2 kT / m), m = chi_A m_A + chi_B m_B, and mu the
+ * first Chapman-Enskog approximation of the mixture viscosity (the approximation under which
+ * the single-species nu_bar = 1.25 delta of Sec. 2.5 holds).
+ */
+typedef struct {
+    double mass_ratio;  /* m_B / m_A > 0                                                       */
+    double diam_ratio;  /* d_B / d_A > 0                                                       */
+    double chi_A;       /* molar fraction of A, 0 < chi_A < 1                                  */
+} lbe_mixture;
+
+/* Poiseuille flow of a mixture between plates (Sec. 4; S_a = v3 f_a,eq, X_P = -1): the half
+ * channel of lbe_geometry dim = 1 (ns sections, grid_kind), diffuse wall, symmetry plane. */
+typedef struct {
+    lbe_mixture mix;
+    int ns;
+    int grid_kind;
+    double delta;
+    double N_A, N_B;     /* SIS tuning; <= 0 selects N_a = int nu_a,eq f_a,eq dv / (delta chi_a)  */
+    int nv;              /* a multiple of 4, 4..32                                              */
+    double vmax;
+    int M;               /* power of two, 2..64                                                 */
+    double R;            /* Carleman truncation radius > 0                                      */
+    lbe_scheme scheme;
+    double eps;          /* stop when all four flow rates change by < eps relative; 0 = never   */
+    int max_iter;
+} lbe_mix_problem;
+
+typedef struct {
+    double M_A, M_B;     /* molecular flow rates M_a = sqrt(m / m_A) 2 int_{-1/2}^0 U_a dx1 (Sec. 4) */
+    double Q_A, Q_B;     /* heat flow rates, q_a = int (r_a |v|^2 - 5/2) v3 h_a dv                  */
+    int iters;
+    int status;
+    double N_A, N_B;     /* the tuning used                                                        */
+} lbe_mix_result;
+
+/* Tables of one mixture on one grid: out4 (host, 4 doubles) receives b_AA at delta = 1 (the
+ * hard-sphere strength per unit solid angle, B = b_ab |v - v*|, b_ab = b_AA d_ab^2 / d_A^2),
+ * N_A, N_B (Sec. 4's N_a equation) and mu1 (units m_A = kT = d_A = 1); nu_out (host,
+ * [2][nv^3] or NULL) receives nu_A, nu_B at delta = 1.  Builds (and caches) the operator. */
+lbe_status lbe_mix_info(lbe_ctx* ctx, const lbe_mixture* mix, int nv, double vmax, int M, double R,
+                        double* out4, double* nu_out);
+
+/* L+_a and L_a = L+_a - delta nu_a h_a for `cells` cells (device pointers, [cells][nv^3]
+ * double each, full velocity grid; LA, LB may be NULL) on `stream` (NULL: the context's).
+ * Asynchronous; LBE_BAD_ARG for invalid sizes, LBE_OOM when the operator does not fit. */
+lbe_status lbe_mix_apply_L(lbe_ctx* ctx, const lbe_mixture* mix, int nv, double vmax, int M, double R,
+                           int cells, double delta, const double* hA, const double* hB, double* LplusA,
+                           double* LA, double* LplusB, double* LB, void* stream);
+
+/* Solve one mixture problem in FP64 by the CIS or the SIS of Eqs. LBE2_true1 / LBE2_true2
+ * (h in the plate orbit layout on the device).  U_out (host, [2][ns + 1] or NULL) receives
+ * U_A, U_B of the last iterate; h_out (host, [2][ns + 1][nv^3] or NULL) receives h_A, h_B.
+ * Returns the result's status: LBE_OK, LBE_NOT_CONVERGED (max_iter reached or eps = 0),
+ * LBE_NAN (a non-finite flow rate), LBE_BAD_ARG, LBE_OOM. */
+lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe_mix_result* out, double* U_out,
+                         double* h_out);
+
 #ifdef __cplusplus
 }
 #endif

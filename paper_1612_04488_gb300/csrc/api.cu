@@ -817,6 +817,7 @@ lbe_status lbe_destroy(lbe_ctx* ctx) {
     if (!ctx) return LBE_BAD_ARG;
     cudaSetDevice(ctx->device);
     stop_service(ctx);
+    mix_release(ctx);
     for (auto& kv : ctx->tables) {
         DevTables* t = kv.second.get();
         tc_release(ctx, t);

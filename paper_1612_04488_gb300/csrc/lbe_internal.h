@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <complex>
 #include <condition_variable>
 #include <cstdint>
 #include <deque>
@@ -38,8 +39,17 @@ struct HostTables {
 };
 
 void build_host_tables(HostTables& t, int nv, double vmax, int M, double R);
+// pieces of the same construction (tables.cpp): phi(s) = 2 int_0^R r cos(r s) dr,
+// psi(a) = 4 pi R J1(R a) / a, the separable DFT of an n^3 array (sign -1 forward, +1 inverse,
+// no scaling), and the hemisphere rule (directions e[3 p + i], weights w[p] summing to 2 pi,
+// ring-major order)
+double carleman_phi(double s, double R);
+double carleman_psi(double a, double R);
+void host_dft3(std::vector<std::complex<double>>& a, int n, int sign);
+void hemisphere_rule(int M, std::vector<double>& e, std::vector<double>& w);
 
 struct TcOperands;  // tensor-core operands (fsm_dense.cu)
+struct MixOp;       // binary-mixture operator (mixture.cu)
 
 // Launch choices made by measurement at first use (the autotuner): the schedule of the 1D
 // float transport sweep per (grid, problems, nodes) class.  Every choice computes the same
@@ -137,6 +147,8 @@ struct Ctx {
     // refined solves' base evaluations), created at first use
     cudaStream_t side_stream = nullptr;
     Arena solve_arena, apply_arena;
+    // binary-mixture operators by (mixture, grid, layout) (mixture.cu)
+    std::map<std::string, MixOp*> mix_ops;
     Arena refine_arena[3];  // refined solves: FP64 batch, low-precision batch, work buffers
     // serving
     std::mutex mu;

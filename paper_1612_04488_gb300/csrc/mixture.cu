@@ -1,0 +1,792 @@
+// Binary hard-sphere mixture (Sec. 4): the four linearized collision operators of a mixture
+// as one dense matrix, built on the device from the Carleman form for unequal masses and
+// applied as an FP64 GEMM, and the SIS of Eqs. LBE2_true1 / LBE2_true2 for Poiseuille flow
+// between plates.
+//
+// Operator (include/lbe.h has the full statement).  For species a colliding with b,
+// mu_b = m_b / (m_a + m_b), c = mu_b - mu_a, and x ⊥ y: v* = v + x + y, v' = v + 2 mu_b x,
+// v*' = v + c x + y; hard spheres give the constant kernel d_ab^2 = 4 b_ab, so in Fourier
+// space (f_j = sum_l f^_l w^(l j), f^ = DFT / N^3)
+//   F(Q+_ab(f, g))_k = sum_{l + m = k mod N} beta_ab(l, m) f^_l g^_m,
+//   beta_ab(l, m) = sum_p 2 b_ab w_p phi((2 mu_b xi_l + c xi_m).e_p) psi_p(m),
+// with the single-species phi, psi, hemisphere rule and truncation R; Nyquist l is zeroed
+// in phi and Nyquist m in psi.  The linearized operator restricted to h_b, as a spectral
+// matrix on h^ (row k, column m, l = k - m mod N):
+//   K_ab[k, m] = f^_a(l) (beta_ab(l, m) - G_ab(m)) + [a = b] sum_c beta_ac(m, l) f^_c(l),
+//   G_ab = sum_p 2 b_ab w_p phi_p psi_p (the loss, mass independent).
+// The velocity-space matrix is F^-1 K F; separable passes along each velocity axis carry the
+// columns to the unknown's basis (the full grid, or one value per orbit of the plate parity:
+// even in v2, odd in v3) and the rows to its representatives.  L+_a = sum_b K_ab h_b and
+// L_a = L+_a - nu_a h_a with nu_a = sum_b F^-1(G_ab F f_b,eq).
+//
+// delta: b_AA = delta mu1 sqrt(2 / m) / 4 (units m_A = kT = d_A = 1, m = chi_A + chi_B m_B),
+// mu1 the first Chapman-Enskog approximation of the mixture viscosity, b_ab = b_AA d_ab^2.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbe_internal.h"
+#include "sweep.h"
+
+namespace lbe {
+
+struct MixOp {
+    int nv = 0, M = 0, layout = 0;  // layout 0: full velocity grid, 1: plate orbit layout
+    double vmax = 0, R = 0;
+    double r[2] = {1, 1}, d[2] = {1, 1}, chi[2] = {0.5, 0.5}, mbar = 1;
+    int nr = 0;               // rows (= columns) of one species block
+    double b0 = 0, mu1 = 0;   // b_AA at delta = 1, first-approximation viscosity
+    double Nal[2] = {0, 0};   // N_a of Sec. 4 (independent of delta)
+    double cU[2] = {0, 0};    // (2 r_a / chi_a) sum v3^2 f_a,eq dv^3 (discrete)
+    double cq[2] = {0, 0};    // 2 r_a sum (r_a |v|^2 - 5/2) v3^2 f_a,eq dv^3
+    double* L = nullptr;      // [2 nr][2 nr] row-major, delta = 1
+    double* nu = nullptr;     // [2][n3] nu_a at delta = 1
+    double* feq = nullptr;    // [2][n3]
+    double* vel = nullptr;    // [nv]
+    std::vector<double> nu_h; // host copy of nu
+    size_t bytes = 0;
+    DevTables tab[2];         // per species: the transport sweep's tables (vel, f_a,eq, nu_a)
+};
+
+namespace {
+
+// First Chapman-Enskog approximation of the viscosity of a binary hard-sphere mixture in
+// units m_A = kT = d_A = 1 (rigid spheres: every reduced collision integral is 1).
+double viscosity1(double mB, double dB, double xA) {
+    const double m1 = 1.0, m2 = mB, x1 = xA, x2 = 1.0 - xA, s12 = 0.5 * (1.0 + dB);
+    const double e1 = 5.0 / 16.0 * std::sqrt(m1 / M_PI);
+    const double e2 = 5.0 / 16.0 * std::sqrt(m2 / M_PI) / (dB * dB);
+    const double e12 = 5.0 / 16.0 * std::sqrt(2.0 * m1 * m2 / (M_PI * (m1 + m2))) / (s12 * s12);
+    const double q = (m1 + m2) * (m1 + m2) / (4.0 * m1 * m2);
+    const double X = x1 * x1 / e1 + 2.0 * x1 * x2 / e12 + x2 * x2 / e2;
+    const double Y = 0.6 * (x1 * x1 / e1 * (m1 / m2) + 2.0 * x1 * x2 / e12 * q * e12 * e12 / (e1 * e2) +
+                            x2 * x2 / e2 * (m2 / m1));
+    const double Z = 0.6 * (x1 * x1 * m1 / m2 + 2.0 * x1 * x2 * (q * (e12 / e1 + e12 / e2) - 1.0) +
+                            x2 * x2 * m2 / m1);
+    return (1.0 + Z) / (X + Y);
+}
+
+__device__ __forceinline__ double phi_dev(double x, double R2) {
+    // phi = 2 R^2 [sin x / x - 2 sin^2(x/2) / x^2], x = R s
+    if (fabs(x) < 1e-3) return R2 * (1.0 - x * x / 4.0 + x * x * x * x / 72.0);
+    double sh, ch;
+    sincos(0.5 * x, &sh, &ch);
+    return 2.0 * R2 * (2.0 * sh * ch / x - 2.0 * sh * sh / (x * x));
+}
+
+// beta[l n3 + m] = keep(l) sum_p wp[p] phi(R (2 mu s_p(l) + c s_p(m))) psi_p(m)
+__global__ void __launch_bounds__(256) k_mix_beta(double* __restrict__ B, const double* __restrict__ s,
+                                                  const double* __restrict__ psi, const unsigned char* __restrict__ keep,
+                                                  const double* __restrict__ wp, int M, long n3, double twomu,
+                                                  double c, double R) {
+    const long total = n3 * n3;
+    const double R2 = R * R;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const long l = t / n3, m = t - l * n3;
+        double acc = 0.0;
+        if (keep[l])
+            for (int p = 0; p < M; ++p) {
+                const double* sp = s + p * n3;
+                acc += wp[p] * phi_dev(R * (twomu * sp[l] + c * sp[m]), R2) * psi[p * n3 + m];
+            }
+        B[t] = acc;
+    }
+}
+
+// spectral matrix of block (a, b) (file header): K[k n3 + m]
+__global__ void __launch_bounds__(256) k_mix_fourier(double2* __restrict__ K, const double* __restrict__ Bab,
+                                                     const double* __restrict__ Ba0, const double* __restrict__ Ba1,
+                                                     const double2* __restrict__ fa, const double2* __restrict__ f0,
+                                                     const double2* __restrict__ f1, const double* __restrict__ Gab,
+                                                     int N, int diag) {
+    const long n3 = (long)N * N * N, total = n3 * n3;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const long k = t / n3, m = t - k * n3;
+        const int k1 = (int)(k / (N * N)), k2 = (int)(k / N % N), k3 = (int)(k % N);
+        const int m1 = (int)(m / (N * N)), m2 = (int)(m / N % N), m3 = (int)(m % N);
+        const long l = ((long)((k1 - m1 + N) % N) * N + (k2 - m2 + N) % N) * N + (k3 - m3 + N) % N;
+        const double g = Bab[l * n3 + m] - Gab[m];
+        double re = fa[l].x * g, im = fa[l].y * g;
+        if (diag) {
+            const double b0 = Ba0[m * n3 + l], b1 = Ba1[m * n3 + l];
+            re += b0 * f0[l].x + b1 * f1[l].x;
+            im += b0 * f0[l].y + b1 * f1[l].y;
+        }
+        K[t] = make_double2(re, im);
+    }
+}
+
+// Y[(o Nout + j) inner + i] = sum_a C[j Nin + a] X[(o Nin + a) inner + i]   (complex)
+__global__ void __launch_bounds__(256) k_axis_pass(const double2* __restrict__ X, double2* __restrict__ Y,
+                                                   const double2* __restrict__ C, long outer, int Nin, long inner,
+                                                   int Nout) {
+    const long total = outer * Nout * inner;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const long i = t % inner, rr = t / inner;
+        const int j = (int)(rr % Nout);
+        const long o = rr / Nout;
+        const double2* x = X + o * Nin * inner + i;
+        const double2* cj = C + (long)j * Nin;
+        double re = 0.0, im = 0.0;
+        for (int a = 0; a < Nin; ++a) {
+            const double2 cc = cj[a], xv = x[a * inner];
+            re += cc.x * xv.x - cc.y * xv.y;
+            im += cc.x * xv.y + cc.y * xv.x;
+        }
+        Y[t] = make_double2(re, im);
+    }
+}
+
+__global__ void k_mix_store(double* __restrict__ L, const double2* __restrict__ Y, long nr, long ld, long row0,
+                            long col0) {
+    const long total = nr * nr;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const long r = t / nr, c = t - r * nr;
+        L[(row0 + r) * ld + col0 + c] = Y[t].x;
+    }
+}
+
+// FP64 GEMM of the mixture operator: for species a and cell n,
+//   y_a[n cs + j] = scale sum_{b, c} L[(a nr + j) 2nr + b nr + c] h_b[n cs + c].
+// 64 x 64 output tile per block, 4 x 4 per thread, K in slices of 16.
+constexpr int kMT = 64, kNT = 64, kKT = 16;
+__global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, int nr, const double* __restrict__ hA,
+                                                  const double* __restrict__ hB, long cs, int cells, double scale,
+                                                  double* __restrict__ yA, double* __restrict__ yB) {
+    __shared__ double As[kKT][kMT + 1];
+    __shared__ double Bs[kKT][kNT + 1];
+    const int rows = 2 * nr, K = 2 * nr;
+    const int row0 = blockIdx.x * kMT, cell0 = blockIdx.y * kNT;
+    const int t = threadIdx.x, ty = t / 16, tx = t % 16;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += kKT) {
+        // A: 64 rows x 16 k, each thread 4 consecutive k of one row
+        {
+            const int r = t / 4, kq = (t % 4) * 4;
+            const int gr = row0 + r;
+            for (int q = 0; q < 4; ++q) {
+                const int gk = k0 + kq + q;
+                As[kq + q][r] = (gr < rows && gk < K) ? L[(long)gr * K + gk] : 0.0;
+            }
+        }
+        // B: 16 k x 64 cells, each thread 4 consecutive k of one cell
+        {
+            const int cc = t / 4, kq = (t % 4) * 4;
+            const int gc = cell0 + cc;
+            for (int q = 0; q < 4; ++q) {
+                const int gk = k0 + kq + q;
+                double v = 0.0;
+                if (gc < cells && gk < K) v = gk < nr ? hA[gc * cs + gk] : hB[gc * cs + gk - nr];
+                Bs[kq + q][cc] = v;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kKT; ++k) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gr = row0 + ty * 4 + i;
+        if (gr >= rows) continue;
+        double* y = gr < nr ? yA : yB;
+        const int j = gr < nr ? gr : gr - nr;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gc = cell0 + tx * 4 + q;
+            if (gc < cells) y[gc * cs + j] = scale * acc[i][q];
+        }
+    }
+}
+
+// L_a = L+_a - delta nu_a h_a over cells x n3 (full layout)
+__global__ void k_mix_loss(const double* __restrict__ lp, const double* __restrict__ h, const double* __restrict__ nu,
+                           double delta, long n3, long total, double* __restrict__ L) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x)
+        L[t] = lp[t] - delta * nu[t % n3] * h[t];
+}
+
+// ---- plate SIS kernels (orbit layout: per cell the nq = nv^3 / 4 values at the
+// representatives (i1 H + j2) H + j3, j2, j3 < H = nv / 2; cell stride nv^3) -------------------
+struct MixSisDev {
+    double r[2], chi[2], Nd[2], delta, dv3, sqm;
+    double cU[2], cq[2];
+    int nv, cells, sis;
+};
+
+// per (cell, species): mom[(a cells + n) 5 + .] = {U, q, W, P, G} of h^(k+1/2) (U, q, W, P)
+// and of L h^(k), h^(k) (G); sums over the orbit representatives times 4
+__global__ void __launch_bounds__(256) k_mix_moments(MixSisDev P, const double* __restrict__ hh,
+                                                     const double* __restrict__ h, const double* __restrict__ lp,
+                                                     const double* __restrict__ nu, const double* __restrict__ vel,
+                                                     double* __restrict__ mom) {
+    const int n = blockIdx.x, a = blockIdx.y, N = P.nv, H = N / 2, nq = N * H * H;
+    const long n3 = (long)N * N * N, off = ((long)a * P.cells + n) * n3;
+    const double r = P.r[a];
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const int i1 = q / (H * H), j2 = q / H % H, j3 = q % H;
+        const double v1 = vel[i1], v2 = vel[j2], v3 = vel[j3];
+        const double x = hh[off + q];
+        s[0] += v3 * x;
+        s[1] += (r * (v1 * v1 + v2 * v2 + v3 * v3) - 2.5) * v3 * x;
+        s[2] += (2.0 * v1 * v1 - 1.0) * v3 * x;
+        s[3] += v1 * v3 * x;
+        if (P.sis) {
+            const long vf = ((long)i1 * N + j2) * N + j3;
+            const double y = lp[off + q] + (P.Nd[a] - P.delta * nu[a * n3 + vf]) * h[off + q];
+            s[4] += v1 * v3 * y;
+        }
+    }
+    __shared__ double red[5][8];
+    for (int k = 0; k < 5; ++k) {
+        double v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double v = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        const double w4 = 4.0 * P.dv3;
+        const double scl[5] = {w4 / P.chi[a], w4, w4, 2.0 * r * w4, 2.0 * w4};
+        mom[((long)a * P.cells + n) * 5 + threadIdx.x] = v * scl[threadIdx.x];
+    }
+}
+
+// one thread per species: the once-integrated diffusion equation marched from the wall,
+// d(chi U + W)/dx1 = G - (N delta / r) P~, P~_B = P_B, P~_A = x1 - P_B; dU, the corrected U
+// and q, and the flow rates M_a = sqrt(m) sum trap U, Q_a = sqrt(m) sum trap q.
+__global__ void k_mix_march(MixSisDev P, const double* __restrict__ mom, const double* __restrict__ geo,
+                            double* __restrict__ dU, double* __restrict__ Uout, double* __restrict__ rates) {
+    const int a = threadIdx.x;
+    if (a >= 2) return;
+    const int n = P.cells;
+    const double *x = geo, *fa = geo + n, *fb = geo + 2 * n, *fc = geo + 3 * n, *trap = geo + 4 * n;
+    const double* ma = mom + (long)a * n * 5;
+    const double* mB = mom + (long)n * 5;
+    double Mr = 0.0, Qr = 0.0, y1 = 0.0, y2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double U = ma[5 * i], q = ma[5 * i + 1], W = ma[5 * i + 2];
+        double d = 0.0;
+        if (P.sis) {
+            double Y;
+            if (i == 0) {
+                Y = P.chi[a] * U + W;
+            } else {
+                const double Pt = a == 0 ? x[i] - mB[5 * i + 3] : mB[5 * i + 3];
+                double src = ma[5 * i + 4] - P.Nd[a] / P.r[a] * Pt - fb[i] * y1;
+                if (i >= 2) src -= fc[i] * y2;
+                Y = src / fa[i];
+            }
+            y2 = y1;
+            y1 = Y;
+            d = (Y - W) / P.chi[a] - U;
+        }
+        dU[a * n + i] = d;
+        const double Uc = U + d * P.cU[a], qc = q + d * P.cq[a];
+        Uout[a * n + i] = Uc;
+        Mr += trap[i] * Uc;
+        Qr += trap[i] * qc;
+    }
+    rates[a] = P.sqm * Mr;
+    rates[2 + a] = P.sqm * Qr;
+}
+
+// h_a = hh_a + 2 r_a dU_a v3 f_a,eq on the representatives
+__global__ void __launch_bounds__(256) k_mix_correct(MixSisDev P, const double* __restrict__ hh,
+                                                     double* __restrict__ h, const double* __restrict__ dU,
+                                                     const double* __restrict__ feq, const double* __restrict__ vel) {
+    const int N = P.nv, H = N / 2, nq = N * H * H;
+    const long n3 = (long)N * N * N;
+    const long total = 2L * P.cells * nq;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int q = (int)(t % nq);
+        const long an = t / nq;
+        const int a = (int)(an / P.cells);
+        const int i1 = q / (H * H), j2 = q / H % H, j3 = q % H;
+        const long vf = ((long)i1 * N + j2) * N + j3, off = an * n3 + q;
+        h[off] = hh[off] + 2.0 * P.r[a] * dU[an] * vel[j3] * feq[a * n3 + vf];
+    }
+}
+
+int grid_for(long total) {
+    const long g = (total + 255) / 256;
+    const long cap = 32L * sm_count();
+    return (int)(g < cap ? g : cap);
+}
+
+std::string mix_key(const lbe_mixture& m, int nv, double vmax, int M, double R, int layout) {
+    char b[256];
+    snprintf(b, sizeof b, "%.17g/%.17g/%.17g/%d/%.17g/%d/%.17g/%d", m.mass_ratio, m.diam_ratio, m.chi_A, nv, vmax, M,
+             R, layout);
+    return b;
+}
+
+lbe_status check_mixture(Ctx* c, const lbe_mixture* m, int nv, double vmax, int M, double R) {
+    if (!m) return bad_arg(c, "null mixture");
+    if (!(m->mass_ratio > 0) || !(m->diam_ratio > 0) || !(m->chi_A > 0 && m->chi_A < 1))
+        return bad_arg(c, "mixture: mass_ratio, diam_ratio > 0 and 0 < chi_A < 1");
+    if (nv < 4 || nv > 32 || nv % 4) return bad_arg(c, "mixture: nv must be a multiple of 4 in 4..32");
+    if (!(vmax > 0) || M < 2 || M > 64 || (M & (M - 1))) return bad_arg(c, "mixture: vmax > 0, M a power of two <= 64");
+    if (!(R > 0)) return bad_arg(c, "mixture: R must be > 0");
+    return LBE_OK;
+}
+
+void free_mixop(Ctx* c, MixOp* o) {
+    if (!o) return;
+    if (o->L) dev_free(c, o->L, sizeof(double) * 4 * (size_t)o->nr * o->nr);
+    const size_t n3 = (size_t)o->nv * o->nv * o->nv;
+    if (o->nu) dev_free(c, o->nu, sizeof(double) * 2 * n3);
+    if (o->feq) dev_free(c, o->feq, sizeof(double) * 2 * n3);
+    if (o->vel) dev_free(c, o->vel, sizeof(double) * o->nv);
+    delete o;
+}
+
+lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
+    const int N = o.nv, H = N / 2, M = o.M;
+    const long n3 = (long)N * N * N;
+    const double dv = 2.0 * o.vmax / N, dv3 = dv * dv * dv;
+    std::vector<double> v(N);
+    for (int j = 0; j < N; ++j) v[j] = -o.vmax + (j + 0.5) * dv;
+    std::vector<double> e, w;
+    hemisphere_rule(M, e, w);
+    // Maxwellians and their spectra
+    std::vector<double> feq(2 * n3);
+    std::vector<std::vector<std::complex<double>>> fh(2, std::vector<std::complex<double>>(n3));
+    for (int a = 0; a < 2; ++a) {
+        const double pre = o.chi[a] * std::pow(o.r[a] / M_PI, 1.5);
+        for (long i = 0; i < n3; ++i) {
+            const double c2 = v[i / (N * N)] * v[i / (N * N)] + v[i / N % N] * v[i / N % N] + v[i % N] * v[i % N];
+            feq[a * n3 + i] = pre * std::exp(-o.r[a] * c2);
+            fh[a][i] = feq[a * n3 + i];
+        }
+        host_dft3(fh[a], N, -1);
+        for (auto& z : fh[a]) z /= (double)n3;
+    }
+    // direction factors per mode
+    std::vector<double> xi(N);
+    for (int k = 0; k < N; ++k) xi[k] = ((k < N / 2) ? k : k - N) * M_PI / o.vmax;
+    std::vector<double> sp((size_t)M * n3), ps((size_t)M * n3), phown((size_t)M * n3);
+    std::vector<unsigned char> keep(n3);
+    for (long m = 0; m < n3; ++m) {
+        const int a1 = (int)(m / (N * N)), a2 = (int)(m / N % N), a3 = (int)(m % N);
+        keep[m] = (a1 != N / 2 && a2 != N / 2 && a3 != N / 2);
+        const double x2 = xi[a1] * xi[a1] + xi[a2] * xi[a2] + xi[a3] * xi[a3];
+        for (int p = 0; p < M; ++p) {
+            const double sv = xi[a1] * e[3 * p] + xi[a2] * e[3 * p + 1] + xi[a3] * e[3 * p + 2];
+            sp[(size_t)p * n3 + m] = sv;
+            ps[(size_t)p * n3 + m] = keep[m] ? carleman_psi(std::sqrt(std::max(x2 - sv * sv, 0.0)), o.R) : 0.0;
+            phown[(size_t)p * n3 + m] = keep[m] ? carleman_phi(sv, o.R) : 0.0;
+        }
+    }
+    auto bab = [&](int a, int b) {
+        const double dab = 0.5 * (o.d[a] + o.d[b]) / o.d[0];
+        return o.b0 * dab * dab;
+    };
+    // loss multipliers G_ab and nu_a = sum_b F^-1(G_ab F f_b)
+    std::vector<double> G(4 * n3, 0.0);
+    o.nu_h.assign(2 * n3, 0.0);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            double* g = &G[(2 * a + b) * n3];
+            for (int p = 0; p < M; ++p) {
+                const double wpp = 2.0 * bab(a, b) * w[p];
+                for (long m = 0; m < n3; ++m) g[m] += wpp * phown[(size_t)p * n3 + m] * ps[(size_t)p * n3 + m];
+            }
+            std::vector<std::complex<double>> z(n3);
+            for (long m = 0; m < n3; ++m) z[m] = g[m] * fh[b][m];
+            host_dft3(z, N, +1);
+            for (long i = 0; i < n3; ++i) o.nu_h[a * n3 + i] += z[i].real();
+        }
+    for (int a = 0; a < 2; ++a) {
+        double nb = 0, su = 0, sq = 0;
+        for (long i = 0; i < n3; ++i) {
+            const double v3 = v[i % N], c2 = v[i / (N * N)] * v[i / (N * N)] + v[i / N % N] * v[i / N % N] + v3 * v3;
+            nb += o.nu_h[a * n3 + i] * feq[a * n3 + i] * dv3;
+            su += v3 * v3 * feq[a * n3 + i] * dv3;
+            sq += (o.r[a] * c2 - 2.5) * v3 * v3 * feq[a * n3 + i] * dv3;
+        }
+        o.Nal[a] = nb / o.chi[a];
+        o.cU[a] = 2.0 * o.r[a] * su / o.chi[a];
+        o.cq[a] = 2.0 * o.r[a] * sq;
+    }
+    // separable pass tables: columns (DFT index -> basis), rows (DFT index -> representative)
+    const int co[3] = {N, o.layout ? H : N, o.layout ? H : N};
+    std::vector<std::vector<double2>> colC(3), rowC(3);
+    for (int ax = 0; ax < 3; ++ax) {
+        colC[ax].resize((size_t)co[ax] * N);
+        rowC[ax].resize((size_t)co[ax] * N);
+        for (int j = 0; j < co[ax]; ++j)
+            for (int a = 0; a < N; ++a) {
+                std::complex<double> z = std::polar(1.0, -2.0 * M_PI * ((long)a * j % N) / N);
+                if (o.layout && ax > 0) {
+                    const std::complex<double> zr = std::polar(1.0, -2.0 * M_PI * ((long)a * (N - 1 - j) % N) / N);
+                    z = ax == 1 ? z + zr : z - zr;  // even in v2, odd in v3
+                }
+                z /= (double)N;
+                colC[ax][(size_t)j * N + a] = make_double2(z.real(), z.imag());
+                const std::complex<double> y = std::polar(1.0, 2.0 * M_PI * ((long)a * j % N) / N);
+                rowC[ax][(size_t)j * N + a] = make_double2(y.real(), y.imag());
+            }
+    }
+    const long nr = (long)co[0] * co[1] * co[2];
+    o.nr = (int)nr;
+    // device buffers
+    lbe_status st = LBE_OK;
+    auto take = [&](void** p, size_t bytes) {
+        if (st == LBE_OK) st = dev_alloc(c, p, bytes);
+    };
+    void *d_s = nullptr, *d_ps = nullptr, *d_keep = nullptr, *d_fh = nullptr, *d_G = nullptr, *d_wp = nullptr;
+    void *d_B0 = nullptr, *d_B1 = nullptr, *d_K = nullptr, *d_Y = nullptr, *d_C = nullptr;
+    const size_t nn = (size_t)n3 * n3;
+    take(&d_s, sizeof(double) * M * n3);
+    take(&d_ps, sizeof(double) * M * n3);
+    take(&d_keep, n3);
+    take(&d_fh, sizeof(double2) * 2 * n3);
+    take(&d_G, sizeof(double) * 4 * n3);
+    take(&d_wp, sizeof(double) * 4 * M);
+    take(&d_C, sizeof(double2) * 6 * N * N);
+    take(&d_B0, sizeof(double) * nn);
+    take(&d_B1, sizeof(double) * nn);
+    take(&d_K, sizeof(double2) * nn);
+    take(&d_Y, sizeof(double2) * nn);
+    take((void**)&o.L, sizeof(double) * 4 * (size_t)nr * nr);
+    take((void**)&o.nu, sizeof(double) * 2 * n3);
+    take((void**)&o.feq, sizeof(double) * 2 * n3);
+    take((void**)&o.vel, sizeof(double) * N);
+    if (st == LBE_OK) {
+        std::vector<double2> fh2(2 * n3);
+        for (int a = 0; a < 2; ++a)
+            for (long m = 0; m < n3; ++m) fh2[a * n3 + m] = make_double2(fh[a][m].real(), fh[a][m].imag());
+        std::vector<double> wpv(4 * M);
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int p = 0; p < M; ++p) wpv[(2 * a + b) * M + p] = 2.0 * bab(a, b) * w[p];
+        std::vector<double2> Ct;
+        for (int ax = 0; ax < 3; ++ax) Ct.insert(Ct.end(), colC[ax].begin(), colC[ax].end());
+        for (int ax = 0; ax < 3; ++ax) Ct.insert(Ct.end(), rowC[ax].begin(), rowC[ax].end());
+        cudaMemcpyAsync(d_s, sp.data(), sizeof(double) * M * n3, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_ps, ps.data(), sizeof(double) * M * n3, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_keep, keep.data(), n3, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_fh, fh2.data(), sizeof(double2) * 2 * n3, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_G, G.data(), sizeof(double) * 4 * n3, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_wp, wpv.data(), sizeof(double) * 4 * M, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_C, Ct.data(), sizeof(double2) * Ct.size(), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(o.nu, o.nu_h.data(), sizeof(double) * 2 * n3, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(o.feq, feq.data(), sizeof(double) * 2 * n3, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(o.vel, v.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s);
+        g_h2d += sizeof(double) * (2 * M * n3 + 8 * n3 + 4 * M + N) + n3;
+        const double2* fhd = (const double2*)d_fh;
+        const double2* Cd = (const double2*)d_C;
+        // column and row tables of axis ax start at Cd + off_c[ax] / off_r[ax]
+        long off_c[3], off_r[3], acc = 0;
+        for (int ax = 0; ax < 3; ++ax) off_c[ax] = acc, acc += (long)co[ax] * N;
+        for (int ax = 0; ax < 3; ++ax) off_r[ax] = acc, acc += (long)co[ax] * N;
+        const int gb = grid_for((long)nn);
+        for (int a = 0; a < 2 && st == LBE_OK; ++a) {
+            for (int b = 0; b < 2; ++b) {
+                const double mub = o.r[b] / (o.r[a] + o.r[b]), cc = (o.r[b] - o.r[a]) / (o.r[a] + o.r[b]);
+                k_mix_beta<<<gb, 256, 0, s>>>((double*)(b ? d_B1 : d_B0), (const double*)d_s, (const double*)d_ps,
+                                              (const unsigned char*)d_keep, (const double*)d_wp + (2 * a + b) * M, M,
+                                              n3, 2.0 * mub, cc, o.R);
+            }
+            for (int b = 0; b < 2; ++b) {
+                k_mix_fourier<<<gb, 256, 0, s>>>((double2*)d_K, (const double*)(b ? d_B1 : d_B0),
+                                                 (const double*)d_B0, (const double*)d_B1, fhd + a * n3, fhd,
+                                                 fhd + n3, (const double*)d_G + (2 * a + b) * n3, N, a == b);
+                // columns: m3, m2, m1 -> basis
+                double2 *X = (double2*)d_K, *Y = (double2*)d_Y;
+                long inner = 1;
+                long outer = n3 * N * N;
+                for (int ax = 2; ax >= 0; --ax) {
+                    k_axis_pass<<<grid_for(outer * co[ax] * inner), 256, 0, s>>>(X, Y, Cd + off_c[ax], outer, N, inner,
+                                                                                   co[ax]);
+                    std::swap(X, Y);
+                    inner *= co[ax];
+                    outer /= N;
+                }
+                // rows: k3, k2, k1 -> representatives (X now holds [k][nr])
+                inner = nr;
+                outer = (long)N * N;
+                for (int ax = 2; ax >= 0; --ax) {
+                    k_axis_pass<<<grid_for(outer * co[ax] * inner), 256, 0, s>>>(X, Y, Cd + off_r[ax], outer, N, inner,
+                                                                                   co[ax]);
+                    std::swap(X, Y);
+                    inner *= co[ax];
+                    outer /= N;
+                }
+                k_mix_store<<<grid_for(nr * nr), 256, 0, s>>>(o.L, X, nr, 2 * nr, a * nr, b * nr);
+                g_launches += 9;
+            }
+            g_launches += 2;
+        }
+        st = cuda_status(c, cudaStreamSynchronize(s), "mixture operator build");
+    }
+    for (void* p : {d_B0, d_B1, d_K, d_Y})
+        if (p) dev_free(c, p, p == d_B0 || p == d_B1 ? sizeof(double) * nn : sizeof(double2) * nn);
+    if (d_s) dev_free(c, d_s, sizeof(double) * M * n3);
+    if (d_ps) dev_free(c, d_ps, sizeof(double) * M * n3);
+    if (d_keep) dev_free(c, d_keep, n3);
+    if (d_fh) dev_free(c, d_fh, sizeof(double2) * 2 * n3);
+    if (d_G) dev_free(c, d_G, sizeof(double) * 4 * n3);
+    if (d_wp) dev_free(c, d_wp, sizeof(double) * 4 * M);
+    if (d_C) dev_free(c, d_C, sizeof(double2) * 6 * N * N);
+    if (st != LBE_OK) return st;
+    for (int a = 0; a < 2; ++a) {
+        DevTables& t = o.tab[a];
+        t.nv = N;
+        t.vmax = o.vmax;
+        t.R = o.R;
+        t.dv = dv;
+        t.M = M;
+        t.vel_d = o.vel;
+        t.feq_d = o.feq + a * n3;
+        t.nu1_d = o.nu + a * n3;
+    }
+    return LBE_OK;
+}
+
+MixOp* get_mixop(Ctx* c, const lbe_mixture& m, int nv, double vmax, int M, double R, int layout, cudaStream_t s,
+                 lbe_status* st) {
+    const std::string key = mix_key(m, nv, vmax, M, R, layout);
+    auto it = c->mix_ops.find(key);
+    if (it != c->mix_ops.end()) return it->second;
+    MixOp* o = new MixOp();
+    o->nv = nv;
+    o->M = M;
+    o->layout = layout;
+    o->vmax = vmax;
+    o->R = R;
+    o->r[1] = m.mass_ratio;
+    o->d[1] = m.diam_ratio;
+    o->chi[0] = m.chi_A;
+    o->chi[1] = 1.0 - m.chi_A;
+    o->mbar = o->chi[0] + o->chi[1] * o->r[1];
+    o->mu1 = viscosity1(o->r[1], o->d[1], o->chi[0]);
+    o->b0 = o->mu1 * std::sqrt(2.0 / o->mbar) / 4.0;
+    *st = build_mixop(c, *o, s);
+    if (*st != LBE_OK) {
+        free_mixop(c, o);
+        return nullptr;
+    }
+    c->mix_ops[key] = o;
+    return o;
+}
+
+void mix_gemm(const MixOp& o, const double* hA, const double* hB, long cs, int cells, double scale, double* yA,
+              double* yB, cudaStream_t s) {
+    dim3 g((2 * o.nr + kMT - 1) / kMT, (cells + kNT - 1) / kNT);
+    k_mix_gemm<<<g, 256, 0, s>>>(o.L, o.nr, hA, hB, cs, cells, scale, yA, yB);
+    g_launches += 1;
+}
+
+cudaStream_t use_stream(Ctx* c, void* stream) { return stream ? (cudaStream_t)stream : c->stream; }
+
+}  // namespace
+
+void mix_release(Ctx* c) {
+    for (auto& kv : c->mix_ops) free_mixop(c, kv.second);
+    c->mix_ops.clear();
+}
+
+}  // namespace lbe
+
+using namespace lbe;
+
+extern "C" lbe_status lbe_mix_info(lbe_ctx* ctx, const lbe_mixture* mix, int nv, double vmax, int M, double R,
+                                   double* out4, double* nu_out) {
+    if (!ctx || !out4) return bad_arg(ctx, "null argument");
+    lbe_status st = check_mixture(ctx, mix, nv, vmax, M, R);
+    if (st != LBE_OK) return st;
+    cudaSetDevice(ctx->device);
+    MixOp* o = get_mixop(ctx, *mix, nv, vmax, M, R, 1, ctx->stream, &st);
+    if (!o) return st;
+    out4[0] = o->b0;
+    out4[1] = o->Nal[0];
+    out4[2] = o->Nal[1];
+    out4[3] = o->mu1;
+    if (nu_out) std::memcpy(nu_out, o->nu_h.data(), sizeof(double) * o->nu_h.size());
+    return LBE_OK;
+}
+
+extern "C" lbe_status lbe_mix_apply_L(lbe_ctx* ctx, const lbe_mixture* mix, int nv, double vmax, int M, double R,
+                                      int cells, double delta, const double* hA, const double* hB, double* LplusA,
+                                      double* LA, double* LplusB, double* LB, void* stream) {
+    if (!ctx || !hA || !hB || !LplusA || !LplusB) return bad_arg(ctx, "null argument");
+    lbe_status st = check_mixture(ctx, mix, nv, vmax, M, R);
+    if (st != LBE_OK) return st;
+    if (cells < 0 || !(delta >= 0)) return bad_arg(ctx, "cells >= 0 and delta >= 0");
+    if (cells == 0) return LBE_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = use_stream(ctx, stream);
+    MixOp* o = get_mixop(ctx, *mix, nv, vmax, M, R, 0, s, &st);
+    if (!o) return st;
+    const long n3 = (long)nv * nv * nv;
+    mix_gemm(*o, hA, hB, n3, cells, delta, LplusA, LplusB, s);
+    const long total = (long)cells * n3;
+    if (LA) k_mix_loss<<<grid_for(total), 256, 0, s>>>(LplusA, hA, o->nu, delta, n3, total, LA), g_launches += 1;
+    if (LB) k_mix_loss<<<grid_for(total), 256, 0, s>>>(LplusB, hB, o->nu + n3, delta, n3, total, LB), g_launches += 1;
+    g_levals += cells;
+    return cuda_status(ctx, cudaGetLastError(), "mixture apply");
+}
+
+extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe_mix_result* out, double* U_out,
+                                    double* h_out) {
+    if (!ctx || !pb || !out) return bad_arg(ctx, "null argument");
+    lbe_status st = check_mixture(ctx, &pb->mix, pb->nv, pb->vmax, pb->M, pb->R);
+    if (st != LBE_OK) return st;
+    if (pb->ns < 2 || pb->ns > 1000 || (pb->grid_kind != 0 && pb->grid_kind != 1))
+        return bad_arg(ctx, "mixture plates: 2 <= ns <= 1000, grid_kind 0 or 1");
+    if (!(pb->delta >= 0) || pb->max_iter < 1 || !(pb->eps >= 0) || (pb->scheme != LBE_CIS && pb->scheme != LBE_SIS))
+        return bad_arg(ctx, "mixture plates: delta >= 0, max_iter >= 1, eps >= 0, scheme CIS or SIS");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    MixOp* o = get_mixop(ctx, pb->mix, pb->nv, pb->vmax, pb->M, pb->R, 1, s, &st);
+    if (!o) return st;
+    lbe_problem geo{};
+    geo.geom.dim = 1;
+    geo.geom.ns = pb->ns;
+    geo.geom.grid_kind = pb->grid_kind;
+    SweepGeom g;
+    build_sweep_geom(g, geo);
+    const int n = g.cells, N = pb->nv;
+    const long n3 = (long)N * N * N, per = (long)n * n3;
+    std::vector<double> coef, geov;
+    for (auto* vv : {&g.fa, &g.fb, &g.fc, &g.ba, &g.bb, &g.bc}) coef.insert(coef.end(), vv->begin(), vv->end());
+    for (auto* vv : {&g.x, &g.fa, &g.fb, &g.fc, &g.trap}) geov.insert(geov.end(), vv->begin(), vv->end());
+    MixSisDev P{};
+    for (int a = 0; a < 2; ++a) {
+        P.r[a] = o->r[a];
+        P.chi[a] = o->chi[a];
+        const double Nin = a ? pb->N_B : pb->N_A;
+        P.Nd[a] = (Nin > 0 ? Nin : o->Nal[a]) * pb->delta;
+        P.cU[a] = o->cU[a];
+        P.cq[a] = o->cq[a];
+    }
+    P.delta = pb->delta;
+    P.dv3 = std::pow(2.0 * pb->vmax / N, 3);
+    P.sqm = std::sqrt(o->mbar);
+    P.nv = N;
+    P.cells = n;
+    P.sis = pb->scheme == LBE_SIS;
+    SweepJobDev job{};
+    job.cell_off = 0;
+    job.ncell = n;
+    job.coef_off = 0;
+    job.forcing = LBE_POISEUILLE;
+    job.delta = pb->delta;
+    // device workspace
+    const size_t b_state = sizeof(double) * 2 * per;
+    const size_t b_small = sizeof(double) * (10 * n + 4 * n + 8) + sizeof(double) * (coef.size() + geov.size());
+    void *d_h = nullptr, *d_hh = nullptr, *d_lp = nullptr, *d_small = nullptr, *d_job = nullptr;
+    auto take = [&](void** p, size_t bytes) {
+        if (st == LBE_OK) st = dev_alloc(ctx, p, bytes);
+    };
+    take(&d_h, b_state);
+    take(&d_hh, b_state);
+    take(&d_lp, b_state);
+    take(&d_small, b_small);
+    take(&d_job, sizeof job);
+    double* h = (double*)d_h;
+    double* hh = (double*)d_hh;
+    double* lp = (double*)d_lp;
+    double* mom = (double*)d_small;           // [2][n][5]
+    double* dU = mom + 10 * n;                // [2][n]
+    double* Uc = dU + 2 * n;                  // [2][n]
+    double* rates = Uc + 2 * n;               // [8]
+    double* dcoef = rates + 8;
+    double* dgeo = dcoef + coef.size();
+    double hr[4] = {0, 0, 0, 0}, old[4] = {0, 0, 0, 0};
+    int it = 0;
+    bool conv = false, bad = false;
+    if (st == LBE_OK) {
+        cudaMemsetAsync(h, 0, b_state, s);
+        cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(dgeo, geov.data(), sizeof(double) * geov.size(), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_job, &job, sizeof job, cudaMemcpyHostToDevice, s);
+        g_h2d += sizeof(double) * (coef.size() + geov.size()) + sizeof job;
+        while (it < pb->max_iter) {
+            mix_gemm(*o, h, h + per, n3, n, pb->delta, lp, lp + per, s);
+            for (int a = 0; a < 2; ++a)
+                launch_sweep<double>(o->tab[a], 1, 1, (int)coef.size(), lp + a * per, hh + a * per,
+                                     (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
+            k_mix_moments<<<dim3(n, 2), 256, 0, s>>>(P, hh, h, lp, o->nu, o->vel, mom);
+            k_mix_march<<<1, 32, 0, s>>>(P, mom, dgeo, dU, Uc, rates);
+            if (P.sis) {
+                k_mix_correct<<<grid_for(2L * n * n3 / 4), 256, 0, s>>>(P, hh, h, dU, o->feq, o->vel);
+                g_launches += 1;
+            } else {
+                std::swap(h, hh);
+            }
+            g_launches += 2;
+            g_levals += n;
+            cudaMemcpyAsync(hr, rates, sizeof hr, cudaMemcpyDeviceToHost, s);
+            g_d2h += sizeof hr;
+            if ((st = cuda_status(ctx, cudaStreamSynchronize(s), "mixture iteration")) != LBE_OK) break;
+            ++it;
+            bool fin = true, same = pb->eps > 0;
+            for (int k = 0; k < 4; ++k) {
+                fin = fin && std::isfinite(hr[k]);
+                same = same && std::fabs(hr[k] - old[k]) < pb->eps * std::fabs(hr[k]);
+                old[k] = hr[k];
+            }
+            if (!fin) {
+                bad = true;
+                break;
+            }
+            if (same) {
+                conv = true;
+                break;
+            }
+        }
+    }
+    if (st == LBE_OK && U_out) {
+        cudaMemcpy(U_out, Uc, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost);
+        g_d2h += sizeof(double) * 2 * n;
+    }
+    if (st == LBE_OK && h_out) {
+        // the orbit layout back to the full grid: even in v2, odd in v3
+        const int H = N / 2, nq = N * H * H;
+        std::vector<double> q(2 * (size_t)n * nq);
+        for (int a = 0; a < 2; ++a)
+            for (int c = 0; c < n; ++c)
+                cudaMemcpy(&q[((size_t)a * n + c) * nq], h + a * per + (long)c * n3, sizeof(double) * nq,
+                           cudaMemcpyDeviceToHost);
+        g_d2h += sizeof(double) * q.size();
+        for (size_t ac = 0; ac < 2 * (size_t)n; ++ac)
+            for (int i1 = 0; i1 < N; ++i1)
+                for (int i2 = 0; i2 < N; ++i2)
+                    for (int i3 = 0; i3 < N; ++i3) {
+                        const int j2 = i2 < H ? i2 : N - 1 - i2, j3 = i3 < H ? i3 : N - 1 - i3;
+                        const double x = q[ac * nq + ((size_t)i1 * H + j2) * H + j3];
+                        h_out[ac * n3 + ((size_t)i1 * N + i2) * N + i3] = i3 < H ? x : -x;
+                    }
+    }
+    dev_free(ctx, d_h, b_state);
+    dev_free(ctx, d_hh, b_state);
+    dev_free(ctx, d_lp, b_state);
+    dev_free(ctx, d_small, b_small);
+    dev_free(ctx, d_job, sizeof job);
+    out->M_A = hr[0];
+    out->M_B = hr[1];
+    out->Q_A = hr[2];
+    out->Q_B = hr[3];
+    out->iters = it;
+    out->N_A = P.Nd[0] / (pb->delta > 0 ? pb->delta : 1.0);
+    out->N_B = P.Nd[1] / (pb->delta > 0 ? pb->delta : 1.0);
+    out->status = st != LBE_OK ? st : bad ? LBE_NAN : conv ? LBE_OK : LBE_NOT_CONVERGED;
+    return (lbe_status)out->status;
+}

@@ -25,6 +25,8 @@ lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs
                          double* h_out);
 // serve.cu
 void stop_service(Ctx* c);
+// mixture.cu: frees the cached mixture operators
+void mix_release(Ctx* c);
 
 struct SweepJobDev {
     long cell_off;   // first cell of the job in the batched [cell][v] arrays

@@ -97,6 +97,31 @@ void dft3(std::vector<cd>& a, int n, int sign) {
 
 double default_R(double vmax) { return 0.75 * vmax; }
 
+double carleman_phi(double s, double R) { return phi_fn(s, R); }
+double carleman_psi(double a, double R) { return psi_fn(a, R); }
+void host_dft3(std::vector<std::complex<double>>& a, int n, int sign) { dft3(a, n, sign); }
+
+void hemisphere_rule(int M, std::vector<double>& e, std::vector<double>& w) {
+    int nt = 1;
+    while (nt * nt * 4 <= M) nt *= 2;  // nt = 2^floor(log2(M)/2)
+    const int na = M / nt;
+    std::vector<double> gx, gw;
+    gauss_legendre(nt, gx, gw);
+    e.resize(3 * (size_t)M);
+    w.resize(M);
+    for (int i = 0; i < nt; ++i) {
+        const double mu = 0.5 * (gx[i] + 1.0), wmu = 0.5 * gw[i], st = std::sqrt(1.0 - mu * mu);
+        for (int k = 0; k < na; ++k) {
+            const double az = (k + 0.5) * 2.0 * M_PI / na;
+            const int p = i * na + k;
+            e[3 * p + 0] = st * std::cos(az);
+            e[3 * p + 1] = st * std::sin(az);
+            e[3 * p + 2] = mu;
+            w[p] = wmu * 2.0 * M_PI / na;
+        }
+    }
+}
+
 void build_host_tables(HostTables& t, int nv, double vmax, int M, double R) {
     const int n = nv, n3 = nv * nv * nv;
     t.nv = nv;

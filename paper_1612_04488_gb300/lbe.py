@@ -35,6 +35,28 @@ class Result(C.Structure):
                 ("refinements", C.c_int)]
 
 
+class Mixture(C.Structure):
+    _fields_ = [("mass_ratio", C.c_double), ("diam_ratio", C.c_double), ("chi_A", C.c_double)]
+
+
+class MixProblem(C.Structure):
+    _fields_ = [("mix", Mixture), ("ns", C.c_int), ("grid_kind", C.c_int), ("delta", C.c_double),
+                ("N_A", C.c_double), ("N_B", C.c_double), ("nv", C.c_int), ("vmax", C.c_double),
+                ("M", C.c_int), ("R", C.c_double), ("scheme", C.c_int), ("eps", C.c_double),
+                ("max_iter", C.c_int)]
+
+
+class MixResult(C.Structure):
+    _fields_ = [("M_A", C.c_double), ("M_B", C.c_double), ("Q_A", C.c_double), ("Q_B", C.c_double),
+                ("iters", C.c_int), ("status", C.c_int), ("N_A", C.c_double), ("N_B", C.c_double)]
+
+
+def mix_problem(mass_ratio, diam_ratio, chi_A, delta=1.0, ns=20, grid_kind=0, N_A=0.0, N_B=0.0, nv=16,
+                vmax=6.0, M=16, R=4.5, scheme=SIS, eps=1e-8, max_iter=500):
+    return MixProblem(Mixture(mass_ratio, diam_ratio, chi_A), ns, grid_kind, delta, N_A, N_B, nv, vmax, M, R,
+                      scheme, eps, max_iter)
+
+
 class Stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
                 ("cell_l_evals", C.c_uint64), ("dense_gemm_timed", C.c_uint64), ("dense_gemm_ms", C.c_double),
@@ -93,6 +115,10 @@ def lib():
         L.lbe_cancel.argtypes = [vp, C.c_uint64]
         L.lbe_debug_expire_waits.argtypes = [ip]
         L.lbe_tuning_report.argtypes = [vp, C.c_char_p, C.c_size_t]
+        L.lbe_mix_info.argtypes = [vp, C.POINTER(Mixture), ip, C.c_double, ip, C.c_double, dp, dp]
+        L.lbe_mix_apply_L.argtypes = [vp, C.POINTER(Mixture), ip, C.c_double, ip, C.c_double, ip, C.c_double,
+                                      vp, vp, vp, vp, vp, vp, vp]
+        L.lbe_mix_solve.argtypes = [vp, C.POINTER(MixProblem), C.POINTER(MixResult), dp, dp]
         _lib = L
     return _lib
 
@@ -193,6 +219,29 @@ class Context:
         st = lib().lbe_apply_L_noalloc(self.h, nv, vmax, M, R, precision, cells, delta_ptr, h_ptr,
                                        lplus_ptr, l_ptr, stream)
         return self.check(st)
+
+    def mix_info(self, mix, nv, vmax, M, R, want_nu=False):
+        """lbe_mix_info: (b_AA at delta = 1, N_A, N_B, mu1) and optionally nu_A, nu_B."""
+        out = np.zeros(4)
+        nu = np.zeros(2 * nv ** 3) if want_nu else None
+        self.check(lib().lbe_mix_info(self.h, C.byref(mix), nv, vmax, M, R, _dptr(out), _dptr(nu)))
+        return out, (nu.reshape((2,) + (nv,) * 3) if want_nu else None)
+
+    def mix_apply_L(self, mix, nv, vmax, M, R, cells, delta, hA_ptr, hB_ptr, lpA_ptr, lA_ptr, lpB_ptr, lB_ptr,
+                    stream=None):
+        st = lib().lbe_mix_apply_L(self.h, C.byref(mix), nv, vmax, M, R, cells, delta, hA_ptr, hB_ptr, lpA_ptr,
+                                   lA_ptr, lpB_ptr, lB_ptr, stream)
+        return self.check(st)
+
+    def mix_solve(self, pb, want_h=False, want_U=True):
+        n = pb.ns + 1
+        U = np.zeros(2 * n) if want_U else None
+        h = np.zeros(2 * n * pb.nv ** 3) if want_h else None
+        res = MixResult()
+        st = lib().lbe_mix_solve(self.h, C.byref(pb), C.byref(res), _dptr(U), _dptr(h))
+        self.check(st, (OK, NOT_CONVERGED))
+        return (res, U.reshape(2, n) if want_U else None,
+                h.reshape((2, n) + (pb.nv,) * 3) if want_h else None)
 
     def sweep(self, pb, rhs_ptr, h_ptr, mom_ptr=None, stream=None):
         return self.check(lib().lbe_sweep(self.h, C.byref(pb), rhs_ptr, h_ptr, mom_ptr, stream))

@@ -1,0 +1,104 @@
+"""Binary-mixture path (Sec. 4) against the oracle: the four linearized operators built as
+one dense matrix on the device (lbe_mix_apply_L, full velocity grid) and the FP64 CIS / SIS
+for plates (lbe_mix_solve, plate orbit layout), element-wise on the same seeded inputs."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mixture as mx
+
+pytestmark = pytest.mark.gpu
+
+NE_AR = (39.95 / 20.18, 1.0 / 0.711)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1612_04488_gb300 import lbe
+    c = lbe.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def oracle8():
+    return mx.MixFSM(mx.Mixture(NE_AR[0], NE_AR[1], 0.5), 8, 5.0, 8, R=3.75)
+
+
+@pytest.fixture(scope="module")
+def oracle12():
+    return mx.MixFSM(mx.Mixture(2.5, 0.8, 0.3), 12, 4.5, 8, R=3.5)
+
+
+def _h(F, cells, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for a in range(2):
+        c = rng.standard_normal((cells, 10))
+        mons = [1 + 0 * F.V1, F.V1, F.V2, F.V3, F.V1 * F.V2, F.V1 * F.V3, F.V2 * F.V3, F.V1 ** 2,
+                F.V3 ** 3, F.V1 * F.V2 * F.V3]
+        h = np.einsum("ck,kijl->cijl", c, np.stack(mons)) * F.f[a]
+        out.append(h + 0.05 * rng.standard_normal(h.shape) * F.f[a])
+    return out
+
+
+@pytest.mark.parametrize("which,cells", [("8", 5), ("12", 70)])
+def test_mixture_operator_matches_oracle(ctx, oracle8, oracle12, which, cells):
+    from paper_1612_04488_gb300 import lbe
+    F = oracle8 if which == "8" else oracle12
+    mix = lbe.Mixture(F.mix.r[1], F.mix.d[1], F.mix.chi[0])
+    hA, hB = _h(F, cells, 5)
+    delta = 1.7
+    ref = F.apply(hA, hB, delta)
+    d = [torch.tensor(x, device="cuda", dtype=torch.float64) for x in (hA, hB)]
+    out = [torch.empty_like(d[0]) for _ in range(4)]
+    ctx.mix_apply_L(mix, F.nv, F.vmax, F.M, F.R, cells, delta, d[0].data_ptr(), d[1].data_ptr(),
+                    out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), out[3].data_ptr())
+    torch.cuda.synchronize()
+    for got, exp in zip(out, ref):
+        g = got.cpu().numpy()
+        assert np.max(np.abs(g - exp)) < 1e-12 * np.max(np.abs(exp))
+
+
+def test_mixture_tables_match_oracle(ctx, oracle8):
+    from paper_1612_04488_gb300 import lbe
+    F = oracle8
+    mix = lbe.Mixture(F.mix.r[1], F.mix.d[1], F.mix.chi[0])
+    info, nu = ctx.mix_info(mix, F.nv, F.vmax, F.M, F.R, want_nu=True)
+    assert abs(info[0] - F.b0) < 1e-15 * F.b0
+    assert abs(info[3] - mx.eta1(F.mix.r[1], F.mix.d[1], F.mix.chi[0])) < 1e-15
+    for a in range(2):
+        assert abs(info[1 + a] - F.N_alpha(a)) < 1e-12 * F.N_alpha(a)
+        assert np.max(np.abs(nu[a] - F.nu[a])) < 1e-13 * np.max(F.nu[a])
+
+
+@pytest.mark.parametrize("scheme", ["sis", "cis"])
+def test_mixture_solve_matches_oracle(ctx, oracle8, scheme):
+    from paper_1612_04488_gb300 import lbe
+    F = oracle8
+    iters = 6
+    kw = dict(delta=0.8, ns=7, nv=8, vmax=5.0, M=8, R=3.75, eps=0.0, max_iter=iters)
+    run = mx.MixRun(mx.MixProblem(NE_AR[0], NE_AR[1], 0.5, scheme=scheme, **kw), F=F)
+    for _ in range(iters):
+        rates = run.step()
+    pb = lbe.mix_problem(NE_AR[0], NE_AR[1], 0.5, scheme=lbe.SIS if scheme == "sis" else lbe.CIS, **kw)
+    res, U, h = ctx.mix_solve(pb, want_h=True)
+    assert res.iters == iters and res.status == lbe.NOT_CONVERGED
+    got = np.array([res.M_A, res.M_B, res.Q_A, res.Q_B])
+    assert np.max(np.abs(got - rates) / np.abs(rates)) < 1e-10
+    for a in range(2):
+        assert np.max(np.abs(U[a] - run.U[a])) < 1e-10 * np.max(np.abs(run.U[a]))
+        assert np.max(np.abs(h[a] - run.h[a])) < 1e-10 * np.max(np.abs(run.h[a]))
+    assert abs(res.N_A - run.Nd[0] / 0.8) < 1e-12 and abs(res.N_B - run.Nd[1] / 0.8) < 1e-12
+
+
+def test_mixture_solve_converges_and_rejects_bad_input(ctx):
+    from paper_1612_04488_gb300 import lbe
+    pb = lbe.mix_problem(NE_AR[0], NE_AR[1], 0.5, delta=1.0, ns=10, nv=8, vmax=5.0, M=8, R=3.75, eps=1e-10,
+                         max_iter=300)
+    res, _, _ = ctx.mix_solve(pb)
+    assert res.status == lbe.OK and res.iters < 100
+    assert res.M_A > res.M_B > 0.0
+    bad = lbe.mix_problem(NE_AR[0], NE_AR[1], 1.5, nv=8, vmax=5.0, M=8, R=3.75)
+    with pytest.raises(lbe.LbeError):
+        ctx.mix_solve(bad)

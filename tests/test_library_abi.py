@@ -59,3 +59,27 @@ def test_no_cuda_device_gives_error_not_crash(libpath):
     from paper_1612_04488_gb300 import lbe
     with pytest.raises(lbe.LbeError):
         lbe.Context(0)
+
+
+def test_mixture_struct_layouts_match_the_header(tmp_path):
+    """Offsets and sizes of the mixture structs, as a C compiler lays out include/lbe.h,
+    against the ctypes binding."""
+    import subprocess
+    from paper_1612_04488_gb300 import lbe
+    structs = {"lbe_mixture": lbe.Mixture, "lbe_mix_problem": lbe.MixProblem, "lbe_mix_result": lbe.MixResult}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbe.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%%s %%zu\\n", "%s", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%%s.%%s %%zu\\n", "%s", "%s", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.split("\n") if l)
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
