@@ -252,6 +252,105 @@ def run_reference(args):
     return 0
 
 
+MIX_NE_AR = (39.95 / 20.18, 1.0 / 0.711)   # m_Ar / m_Ne; d_Ar / d_Ne (Sec. 4: d_Ne / d_Ar = 0.711)
+FP64_NOMINAL_TFLOPS = 1.25                   # GB300 FP64, nominal
+
+
+def table4_chi05():
+    rows = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                        "table4_ne_ar_poiseuille_chi05.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            x = [float(t) for t in line.split()]
+            rows[x[0]] = x[2:]
+    return rows
+
+
+def mixture_measure(lbe, torch, device, steps, warmup, nv=24, M=32, deltas=(1.0, 10.0)):
+    """Binary-mixture SIS (Sec. 4) on Table 4's setting: Ne-Ar, chi_Ne = 0.5, plates with 100
+    clustered sections, FP64, eps 1e-8; a step solves one problem per delta.  Returns the
+    throughput, the FP64 GEMM of the dense mixture operator against the nominal FP64 rate,
+    and the flow rates against Table 4."""
+    stream = torch.cuda.Stream(device)
+    ctx = lbe.Context(device)
+    ctx.set_stream(stream.cuda_stream)
+    pbs = [lbe.mix_problem(MIX_NE_AR[0], MIX_NE_AR[1], 0.5, delta=d, ns=100, grid_kind=1, nv=nv, vmax=5.0, M=M,
+                           R=3.75, eps=1e-8, max_iter=400) for d in deltas]
+    t0 = time.perf_counter()
+    ctx.mix_info(pbs[0].mix, nv, 5.0, M, 3.75)
+    build_s = time.perf_counter() - t0
+    for _ in range(warmup):
+        for pb in pbs:
+            ctx.mix_solve(pb, want_U=False)
+    torch.cuda.synchronize()
+    s0 = lbe.stats()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    a.record(stream)
+    for _ in range(steps):
+        res = [ctx.mix_solve(pb, want_U=False)[0] for pb in pbs]
+    b.record(stream)
+    b.synchronize()
+    wall = time.perf_counter() - w0
+    s1 = lbe.stats()
+    ms = a.elapsed_time(b)
+    # the FP64 GEMM alone, timed per launch by the library during one more solve
+    lbe.set_kernel_timing(True)
+    g0 = lbe.stats()
+    ctx.mix_solve(pbs[-1], want_U=False)
+    g1 = lbe.stats()
+    lbe.set_kernel_timing(False)
+    n_t = g1["dense_gemm_timed"] - g0["dense_gemm_timed"]
+    ms_gemm = (g1["dense_gemm_ms"] - g0["dense_gemm_ms"]) / max(n_t, 1)
+    rows = 2 * nv ** 3 // 4                      # both species, one value per plate orbit
+    cells = 101
+    flops = 2.0 * rows * rows * cells
+    achieved = flops / (ms_gemm / 1000.0) / 1e12
+    T = table4_chi05()
+    t4 = {}
+    for d, r in zip(deltas, res):
+        got = [r.M_A, r.M_B, -r.Q_A / 0.5, -r.Q_B / 0.5]
+        t4[str(d)] = {"got": got, "table4": T[d], "rel": [g / p - 1.0 for g, p in zip(got, T[d])],
+                      "iters": r.iters, "status": r.status}
+    nsolve = len(pbs) * steps
+    out = {"solves_per_s": nsolve / (ms / 1000.0), "ms_per_step": ms / steps, "build_s": build_s,
+           "e2e": {"value": nsolve / wall, "unit": "solves/s",
+                   "h2d_bytes_per_step": int((s1["h2d_bytes"] - s0["h2d_bytes"]) / steps),
+                   "d2h_bytes_per_step": int((s1["d2h_bytes"] - s0["d2h_bytes"]) / steps)},
+           "gpu_launches": int(s1["kernel_launches"] - s0["kernel_launches"]),
+           "roofline": {"bound": "alu", "kernel": "k_mix_gemm (FP64 dense mixture operator, plate orbit layout, "
+                                                  "%d x %d x %d cells)" % (rows, rows, cells),
+                        "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal GB300 FP64 rate",
+                        "traffic": None, "timed_launches": int(n_t), "ms_per_launch": ms_gemm,
+                        "flops_per_launch": flops,
+                        "algorithmic_unit": "2 (2 nv^3/4)^2 flops per cell: the dense operator is the method's "
+                                            "form here (the unequal-mass gain does not factor into transforms)"},
+           "table4": t4,
+           "config": {"workload": "mix_ne_ar%d" % nv, "mixture": "Ne-Ar hard spheres, chi_Ne = 0.5",
+                      "deltas": list(deltas), "nv": nv, "M": M, "vmax": 5.0, "R": 3.75, "ns": 100,
+                      "grid": "clustered", "eps": 1e-8, "precision": "FP64"}}
+    ctx.close()
+    return out
+
+
+def run_mixture(args):
+    import torch
+    from paper_1612_04488_gb300 import lbe
+    torch.cuda.set_device(0)
+    with Clocks(0) as clk:
+        m = mixture_measure(lbe, torch, 0, args.steps, args.warmup)
+    line = {"metric": "binary-mixture SIS solves/s (Ne-Ar plates, Table 4 setting)", "value": m["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": m["config"], "roofline": m["roofline"],
+            "table4": m["table4"], "build_s": m["build_s"], "e2e": m["e2e"], "clocks": clk.summary(),
+            "gpu_launches": m["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_op_only(args):
     """Collision operator alone on the workload's cells (for profiling); prints timings.
     bf16: the tensor-core parity-subspace operator; fp32 / fp64: the fast-spectral one, over
@@ -645,6 +744,8 @@ def run_ours(args):
         line["duct64x32"] = {"solves_per_s": 2.0 / (a.elapsed_time(b) / 1000.0), "cells": 2048,
                              "iterations": dres[-1].iters, "refinements": dres[-1].refinements,
                              "status": dres[-1].status}
+        mx = mixture_measure(lbe, torch, local, 1, 1)
+        line["mixture"] = {k: mx[k] for k in ("solves_per_s", "config", "roofline", "table4", "build_s")}
         sctx = lbe.Context(local)
         line["serving"] = serve_stream(sctx, lbe, prec, args.eps, args.requests)
         line["latency_ms"] = dict(line["serving"]["latency_ms"], workload=line["serving"]["workload"])
@@ -679,7 +780,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plates32x8", choices=["plates32x8", "plates16", "duct64x32"])
+    ap.add_argument("--workload", default="plates32x8", choices=["plates32x8", "plates16", "duct64x32",
+                                                                  "mix_ne_ar24"])
     ap.add_argument("--precision", default="bf16", choices=sorted(PRECISIONS))
     ap.add_argument("--eps", type=float, default=1e-7)
     ap.add_argument("--ref-iters", type=int, default=35,
@@ -698,6 +800,8 @@ def main():
         return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "mix_ne_ar24":
+        return run_mixture(args)
     if args.op_only:
         return run_op_only(args)
     return run_ours(args)

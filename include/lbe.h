@@ -292,8 +292,9 @@ lbe_status lbe_set_stream(lbe_ctx* ctx, void* stream);
 /* Process-wide counters since the library was loaded: kernels launched by this library,
  * bytes it copied host->device and device->host, and cells passed through the collision
  * operator (one cell = one application of L to one nv^3 vector).  With kernel timing on
- * (lbe_set_kernel_timing), every tensor-core GEMM launched by lbe_apply_L_sym is bracketed
- * by CUDA events on its stream: dense_gemm_timed counts those launches and dense_gemm_ms
+ * (lbe_set_kernel_timing), every tensor-core GEMM launched by lbe_apply_L_sym, and every
+ * FP64 GEMM of the mixture operator (lbe_mix_apply_L, lbe_mix_solve), is bracketed by CUDA
+ * events on its stream: dense_gemm_timed counts those launches and dense_gemm_ms
  * sums their durations; and every transport-sweep launch of a solve (step A5, one launch per
  * geometry per iteration) likewise: sweep_timed, sweep_ms, and sweep_bytes, the algorithmic
  * bytes of those launches (right-hand side read and h written once per cell-velocity).

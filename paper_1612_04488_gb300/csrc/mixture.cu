@@ -21,6 +21,7 @@
 //
 // delta: b_AA = delta mu1 sqrt(2 / m) / 4 (units m_A = kT = d_A = 1, m = chi_A + chi_B m_B),
 // mu1 the first Chapman-Enskog approximation of the mixture viscosity, b_ab = b_AA d_ab^2.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -48,6 +49,8 @@ struct MixOp {
     std::vector<double> nu_h; // host copy of nu
     size_t bytes = 0;
     DevTables tab[2];         // per species: the transport sweep's tables (vel, f_a,eq, nu_a)
+    double* part = nullptr;   // split-K partial sums of the GEMM (grow-only)
+    size_t part_bytes = 0;
 };
 
 namespace {
@@ -76,8 +79,21 @@ __device__ __forceinline__ double phi_dev(double x, double R2) {
     return 2.0 * R2 * (2.0 * sh * ch / x - 2.0 * sh * sh / (x * x));
 }
 
-// beta[l n3 + m] = keep(l) sum_p wp[p] phi(R (2 mu s_p(l) + c s_p(m))) psi_p(m)
+// T[p n3 + m] = (sin, cos)(f s_p(m))
+__global__ void k_mix_trig(double2* __restrict__ T, const double* __restrict__ s, long total, double f) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincos(f * s[t], &sn, &cs);
+        T[t] = make_double2(sn, cs);
+    }
+}
+
+// beta[l n3 + m] = keep(l) sum_p wp[p] phi(x) psi_p(m), x = R (2 mu s_p(l) + c s_p(m)):
+// phi = 2 R^2 [sin x / x - 2 sin^2(x/2) / x^2] = 4 R^2 sin(x/2) [cos(x/2) - sin(x/2) / x] / x,
+// with sin and cos of x/2 = R mu s_p(l) + (R c / 2) s_p(m) by angle addition from the tables
+// TL = (sin, cos)(R mu s_p(l)) and TM = (sin, cos)(R c s_p(m) / 2).
 __global__ void __launch_bounds__(256) k_mix_beta(double* __restrict__ B, const double* __restrict__ s,
+                                                  const double2* __restrict__ TL, const double2* __restrict__ TM,
                                                   const double* __restrict__ psi, const unsigned char* __restrict__ keep,
                                                   const double* __restrict__ wp, int M, long n3, double twomu,
                                                   double c, double R) {
@@ -88,8 +104,17 @@ __global__ void __launch_bounds__(256) k_mix_beta(double* __restrict__ B, const 
         double acc = 0.0;
         if (keep[l])
             for (int p = 0; p < M; ++p) {
-                const double* sp = s + p * n3;
-                acc += wp[p] * phi_dev(R * (twomu * sp[l] + c * sp[m]), R2) * psi[p * n3 + m];
+                const long pl = p * n3 + l, pm = p * n3 + m;
+                const double x = R * (twomu * s[pl] + c * s[pm]);
+                double ph;
+                if (fabs(x) < 1e-3) {
+                    ph = R2 * (1.0 - x * x / 4.0 + x * x * x * x / 72.0);
+                } else {
+                    const double2 a = TL[pl], b = TM[pm];
+                    const double sh = a.x * b.y + a.y * b.x, ch = a.y * b.y - a.x * b.x, inv = 1.0 / x;
+                    ph = 4.0 * R2 * sh * inv * (ch - sh * inv);
+                }
+                acc += wp[p] * ph * psi[pm];
             }
         B[t] = acc;
     }
@@ -152,23 +177,27 @@ __global__ void k_mix_store(double* __restrict__ L, const double2* __restrict__ 
 //   y_a[n cs + j] = scale sum_{b, c} L[(a nr + j) 2nr + b nr + c] h_b[n cs + c].
 // 64 x 64 output tile per block, 4 x 4 per thread, K in slices of 16.
 constexpr int kMT = 64, kNT = 64, kKT = 16;
+// With a K split (gridDim.z > 1) slice z covers k in [z kc, (z+1) kc) and writes its unscaled
+// partial sums to part[(z cells + cell) rows + row]; k_mix_reduce adds the slices in order.
 __global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, int nr, const double* __restrict__ hA,
                                                   const double* __restrict__ hB, long cs, int cells, double scale,
-                                                  double* __restrict__ yA, double* __restrict__ yB) {
+                                                  double* __restrict__ yA, double* __restrict__ yB, int kc,
+                                                  double* __restrict__ part) {
     __shared__ double As[kKT][kMT + 1];
     __shared__ double Bs[kKT][kNT + 1];
     const int rows = 2 * nr, K = 2 * nr;
     const int row0 = blockIdx.x * kMT, cell0 = blockIdx.y * kNT;
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
     const int t = threadIdx.x, ty = t / 16, tx = t % 16;
     double acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += kKT) {
+    for (int k0 = kb; k0 < ke; k0 += kKT) {
         // A: 64 rows x 16 k, each thread 4 consecutive k of one row
         {
             const int r = t / 4, kq = (t % 4) * 4;
             const int gr = row0 + r;
             for (int q = 0; q < 4; ++q) {
                 const int gk = k0 + kq + q;
-                As[kq + q][r] = (gr < rows && gk < K) ? L[(long)gr * K + gk] : 0.0;
+                As[kq + q][r] = (gr < rows && gk < ke) ? L[(long)gr * K + gk] : 0.0;
             }
         }
         // B: 16 k x 64 cells, each thread 4 consecutive k of one cell
@@ -178,7 +207,7 @@ __global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, 
             for (int q = 0; q < 4; ++q) {
                 const int gk = k0 + kq + q;
                 double v = 0.0;
-                if (gc < cells && gk < K) v = gk < nr ? hA[gc * cs + gk] : hB[gc * cs + gk - nr];
+                if (gc < cells && gk < ke) v = gk < nr ? hA[gc * cs + gk] : hB[gc * cs + gk - nr];
                 Bs[kq + q][cc] = v;
             }
         }
@@ -197,6 +226,19 @@ __global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, 
         }
         __syncthreads();
     }
+    if (part) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int gr = row0 + ty * 4 + i;
+            if (gr >= rows) continue;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int gc = cell0 + tx * 4 + q;
+                if (gc < cells) part[((long)blockIdx.z * cells + gc) * rows + gr] = acc[i][q];
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int gr = row0 + ty * 4 + i;
@@ -208,6 +250,18 @@ __global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, 
             const int gc = cell0 + tx * 4 + q;
             if (gc < cells) y[gc * cs + j] = scale * acc[i][q];
         }
+    }
+}
+
+// y = scale * sum_z part[z] in slice order (deterministic)
+__global__ void k_mix_reduce(const double* __restrict__ part, int nsplit, int nr, int cells, long cs, double scale,
+                             double* __restrict__ yA, double* __restrict__ yB) {
+    const long rows = 2L * nr, total = rows * cells;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const long gc = t / rows, gr = t - gc * rows;
+        double v = 0.0;
+        for (int z = 0; z < nsplit; ++z) v += part[((long)z * cells + gc) * rows + gr];
+        (gr < nr ? yA : yB)[gc * cs + (gr < nr ? gr : gr - nr)] = scale * v;
     }
 }
 
@@ -352,6 +406,7 @@ void free_mixop(Ctx* c, MixOp* o) {
     if (o->nu) dev_free(c, o->nu, sizeof(double) * 2 * n3);
     if (o->feq) dev_free(c, o->feq, sizeof(double) * 2 * n3);
     if (o->vel) dev_free(c, o->vel, sizeof(double) * o->nv);
+    if (o->part) dev_free(c, o->part, o->part_bytes);
     delete o;
 }
 
@@ -450,7 +505,7 @@ lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
         if (st == LBE_OK) st = dev_alloc(c, p, bytes);
     };
     void *d_s = nullptr, *d_ps = nullptr, *d_keep = nullptr, *d_fh = nullptr, *d_G = nullptr, *d_wp = nullptr;
-    void *d_B0 = nullptr, *d_B1 = nullptr, *d_K = nullptr, *d_Y = nullptr, *d_C = nullptr;
+    void *d_B0 = nullptr, *d_B1 = nullptr, *d_K = nullptr, *d_Y = nullptr, *d_C = nullptr, *d_T = nullptr;
     const size_t nn = (size_t)n3 * n3;
     take(&d_s, sizeof(double) * M * n3);
     take(&d_ps, sizeof(double) * M * n3);
@@ -459,6 +514,7 @@ lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
     take(&d_G, sizeof(double) * 4 * n3);
     take(&d_wp, sizeof(double) * 4 * M);
     take(&d_C, sizeof(double2) * 6 * N * N);
+    take(&d_T, sizeof(double2) * 2 * M * n3);
     take(&d_B0, sizeof(double) * nn);
     take(&d_B1, sizeof(double) * nn);
     take(&d_K, sizeof(double2) * nn);
@@ -499,9 +555,15 @@ lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
         for (int a = 0; a < 2 && st == LBE_OK; ++a) {
             for (int b = 0; b < 2; ++b) {
                 const double mub = o.r[b] / (o.r[a] + o.r[b]), cc = (o.r[b] - o.r[a]) / (o.r[a] + o.r[b]);
-                k_mix_beta<<<gb, 256, 0, s>>>((double*)(b ? d_B1 : d_B0), (const double*)d_s, (const double*)d_ps,
-                                              (const unsigned char*)d_keep, (const double*)d_wp + (2 * a + b) * M, M,
-                                              n3, 2.0 * mub, cc, o.R);
+                double2* TL = (double2*)d_T;
+                double2* TM = TL + (long)M * n3;
+                k_mix_trig<<<grid_for((long)M * n3), 256, 0, s>>>(TL, (const double*)d_s, (long)M * n3, o.R * mub);
+                k_mix_trig<<<grid_for((long)M * n3), 256, 0, s>>>(TM, (const double*)d_s, (long)M * n3,
+                                                                  0.5 * o.R * cc);
+                k_mix_beta<<<gb, 256, 0, s>>>((double*)(b ? d_B1 : d_B0), (const double*)d_s, TL, TM,
+                                              (const double*)d_ps, (const unsigned char*)d_keep,
+                                              (const double*)d_wp + (2 * a + b) * M, M, n3, 2.0 * mub, cc, o.R);
+                g_launches += 2;
             }
             for (int b = 0; b < 2; ++b) {
                 k_mix_fourier<<<gb, 256, 0, s>>>((double2*)d_K, (const double*)(b ? d_B1 : d_B0),
@@ -544,6 +606,7 @@ lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
     if (d_G) dev_free(c, d_G, sizeof(double) * 4 * n3);
     if (d_wp) dev_free(c, d_wp, sizeof(double) * 4 * M);
     if (d_C) dev_free(c, d_C, sizeof(double2) * 6 * N * N);
+    if (d_T) dev_free(c, d_T, sizeof(double2) * 2 * M * n3);
     if (st != LBE_OK) return st;
     for (int a = 0; a < 2; ++a) {
         DevTables& t = o.tab[a];
@@ -586,11 +649,58 @@ MixOp* get_mixop(Ctx* c, const lbe_mixture& m, int nv, double vmax, int M, doubl
     return o;
 }
 
-void mix_gemm(const MixOp& o, const double* hA, const double* hB, long cs, int cells, double scale, double* yA,
-              double* yB, cudaStream_t s) {
+// K split: the smallest count S (slices of at least 256 k) whose S x tiles spreads over the SMs
+// within 3 % of even, else the one that comes closest.
+int mix_split(long tiles, int K) {
+    const int P = sm_count(), smax = std::max(1, K / 256);
+    int best = 1;
+    double best_eff = 0.0;
+    for (int S = 1; S <= smax; ++S) {
+        const long n = tiles * S;
+        const double eff = (double)n / (double)(((n + P - 1) / P) * P);
+        if (eff > best_eff + 1e-9) best = S, best_eff = eff;
+        if (eff >= 0.97) break;
+    }
+    return best;
+}
+
+lbe_status mix_gemm(Ctx* c, MixOp& o, const double* hA, const double* hB, long cs, int cells, double scale,
+                    double* yA, double* yB, cudaStream_t s) {
+    const int K = 2 * o.nr;
     dim3 g((2 * o.nr + kMT - 1) / kMT, (cells + kNT - 1) / kNT);
-    k_mix_gemm<<<g, 256, 0, s>>>(o.L, o.nr, hA, hB, cs, cells, scale, yA, yB);
+    int S = mix_split((long)g.x * g.y, K);
+    int kc = (K + S - 1) / S;
+    kc = (kc + kKT - 1) / kKT * kKT;
+    S = (K + kc - 1) / kc;
+    g.z = S;
+    const size_t need = S > 1 ? sizeof(double) * (size_t)S * cells * K : 0;
+    if (need > o.part_bytes) {
+        if (o.part) cudaStreamSynchronize(s), dev_free(c, o.part, o.part_bytes), o.part = nullptr, o.part_bytes = 0;
+        lbe_status st = dev_alloc(c, (void**)&o.part, need);
+        if (st != LBE_OK) return st;
+        o.part_bytes = need;
+    }
+    // with kernel timing on, each launch is bracketed by events and waited for (lbe_get_stats)
+    cudaEvent_t ev[2];
+    const bool timed = g_time_kernels.load() != 0 && cudaEventCreate(&ev[0]) == cudaSuccess &&
+                       cudaEventCreate(&ev[1]) == cudaSuccess;
+    if (timed) cudaEventRecord(ev[0], s);
+    k_mix_gemm<<<g, 256, 0, s>>>(o.L, o.nr, hA, hB, cs, cells, scale, yA, yB, kc, S > 1 ? o.part : nullptr);
     g_launches += 1;
+    if (S > 1) {
+        k_mix_reduce<<<grid_for((long)K * cells), 256, 0, s>>>(o.part, S, o.nr, cells, cs, scale, yA, yB);
+        g_launches += 1;
+    }
+    if (timed) {
+        cudaEventRecord(ev[1], s);
+        cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        add_gemm_time(ms);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
+    return LBE_OK;
 }
 
 cudaStream_t use_stream(Ctx* c, void* stream) { return stream ? (cudaStream_t)stream : c->stream; }
@@ -635,7 +745,7 @@ extern "C" lbe_status lbe_mix_apply_L(lbe_ctx* ctx, const lbe_mixture* mix, int 
     MixOp* o = get_mixop(ctx, *mix, nv, vmax, M, R, 0, s, &st);
     if (!o) return st;
     const long n3 = (long)nv * nv * nv;
-    mix_gemm(*o, hA, hB, n3, cells, delta, LplusA, LplusB, s);
+    if ((st = mix_gemm(ctx, *o, hA, hB, n3, cells, delta, LplusA, LplusB, s)) != LBE_OK) return st;
     const long total = (long)cells * n3;
     if (LA) k_mix_loss<<<grid_for(total), 256, 0, s>>>(LplusA, hA, o->nu, delta, n3, total, LA), g_launches += 1;
     if (LB) k_mix_loss<<<grid_for(total), 256, 0, s>>>(LplusB, hB, o->nu + n3, delta, n3, total, LB), g_launches += 1;
@@ -719,7 +829,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
         cudaMemcpyAsync(d_job, &job, sizeof job, cudaMemcpyHostToDevice, s);
         g_h2d += sizeof(double) * (coef.size() + geov.size()) + sizeof job;
         while (it < pb->max_iter) {
-            mix_gemm(*o, h, h + per, n3, n, pb->delta, lp, lp + per, s);
+            if ((st = mix_gemm(ctx, *o, h, h + per, n3, n, pb->delta, lp, lp + per, s)) != LBE_OK) break;
             for (int a = 0; a < 2; ++a)
                 launch_sweep<double>(o->tab[a], 1, 1, (int)coef.size(), lp + a * per, hh + a * per,
                                      (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);

@@ -102,3 +102,46 @@ def test_mixture_solve_converges_and_rejects_bad_input(ctx):
     bad = lbe.mix_problem(NE_AR[0], NE_AR[1], 1.5, nv=8, vmax=5.0, M=8, R=3.75)
     with pytest.raises(lbe.LbeError):
         ctx.mix_solve(bad)
+
+
+GOLDEN4 = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden",
+                                     "table4_ne_ar_poiseuille_chi05.txt")
+
+
+def _table4():
+    rows = {}
+    for line in open(GOLDEN4):
+        if line.strip() and not line.startswith("#"):
+            x = [float(t) for t in line.split()]
+            rows[x[0]] = x[2:]
+    return rows
+
+
+def _mix_solve(ctx, delta, nv, M=32):
+    from paper_1612_04488_gb300 import lbe
+    pb = lbe.mix_problem(NE_AR[0], NE_AR[1], 0.5, delta=delta, ns=100, grid_kind=1, nv=nv, vmax=5.0, M=M, R=3.75,
+                         eps=1e-8, max_iter=400)
+    res, _, _ = ctx.mix_solve(pb, want_U=False)
+    assert res.status == lbe.OK
+    return np.array([res.M_A, res.M_B, -res.Q_A / 0.5, -res.Q_B / 0.5])
+
+
+def test_table4_near_continuum_row(ctx):
+    """delta = 10 (Table 4, chi_Ne = 0.5) on a 24^3 grid: flow rates within 1 %, the heat
+    flows within 3 % (Ne) and 6 % (Ar, the smallest printed value, 0.039)."""
+    got = _mix_solve(ctx, 10.0, 24)
+    ref = np.array(_table4()[10.0])
+    rel = np.abs(got / ref - 1.0)
+    assert rel[0] < 0.01 and rel[1] < 0.01 and rel[2] < 0.03 and rel[3] < 0.06, (got, ref)
+
+
+def test_table4_transition_rows_approach_the_paper_as_the_velocity_grid_refines(ctx):
+    """delta = 1 and 0.1: the flow rates rise towards Table 4 monotonically from 16^3 to 32^3
+    (the velocity grid, not the scheme, limits them; the paper's grid is finer), and at
+    32^3 the delta = 1 molecular flow rates are within 3 %."""
+    T = _table4()
+    for delta in (1.0, 0.1):
+        errs = [np.abs(_mix_solve(ctx, delta, nv)[:2] / np.array(T[delta][:2]) - 1.0) for nv in (16, 24, 32)]
+        assert np.all(errs[0] > errs[1]) and np.all(errs[1] > errs[2]), (delta, errs)
+        if delta == 1.0:
+            assert np.all(errs[2] < 0.03), errs
