@@ -280,10 +280,20 @@ def mixture_measure(lbe, torch, device, steps, warmup, nv=24, M=32, deltas=(1.0,
     t0 = time.perf_counter()
     ctx.mix_info(pbs[0].mix, nv, 5.0, M, 3.75)
     build_s = time.perf_counter() - t0
+    # BF16 hi / lo operator on the tensor cores, then FP64 iterations to the same stopping test
+    rpbs = [lbe.mix_problem(MIX_NE_AR[0], MIX_NE_AR[1], 0.5, delta=d, ns=100, grid_kind=1, nv=nv, vmax=5.0, M=M,
+                            R=3.75, eps=1e-8, max_iter=400, precision=lbe.BF16_REFINED) for d in deltas]
     for _ in range(warmup):
-        for pb in pbs:
+        for pb in pbs + rpbs:
             ctx.mix_solve(pb, want_U=False)
     torch.cuda.synchronize()
+    ra, rb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ra.record(stream)
+    for _ in range(steps):
+        rres = [ctx.mix_solve(pb, want_U=False)[0] for pb in rpbs]
+    rb.record(stream)
+    rb.synchronize()
+    ms_ref = ra.elapsed_time(rb)
     s0 = lbe.stats()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     w0 = time.perf_counter()
@@ -314,7 +324,16 @@ def mixture_measure(lbe, torch, device, steps, warmup, nv=24, M=32, deltas=(1.0,
         t4[str(d)] = {"got": got, "table4": T[d], "rel": [g / p - 1.0 for g, p in zip(got, T[d])],
                       "iters": r.iters, "status": r.status}
     nsolve = len(pbs) * steps
+    rel = max(abs(x / y - 1.0) for r, q in zip(rres, res)
+              for x, y in ((r.M_A, q.M_A), (r.M_B, q.M_B), (r.Q_A, q.Q_A), (r.Q_B, q.Q_B)))
+    refined = {"solves_per_s": nsolve / (ms_ref / 1000.0), "ms_per_step": ms_ref / steps,
+               "iters": [r.iters for r in rres], "fp64_iters": [r.fp64_iters for r in rres],
+               "max_rel_err_vs_fp64": rel,
+               "what": "tcgen05 BF16 hi/lo operator (float accumulation) down to its floor, then defect "
+                       "correction: FP64 iterations (the same 1e-8 stopping test) whose errors are solved "
+                       "for by the source-free iteration on the tensor cores"}
     out = {"solves_per_s": nsolve / (ms / 1000.0), "ms_per_step": ms / steps, "build_s": build_s,
+           "refined": refined, "fp64_iters": [r.iters for r in res],
            "e2e": {"value": nsolve / wall, "unit": "solves/s",
                    "h2d_bytes_per_step": int((s1["h2d_bytes"] - s0["h2d_bytes"]) / steps),
                    "d2h_bytes_per_step": int((s1["d2h_bytes"] - s0["d2h_bytes"]) / steps)},
@@ -345,7 +364,8 @@ def run_mixture(args):
             "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": m["config"], "roofline": m["roofline"],
-            "table4": m["table4"], "build_s": m["build_s"], "e2e": m["e2e"], "clocks": clk.summary(),
+            "table4": m["table4"], "build_s": m["build_s"], "refined": m["refined"], "e2e": m["e2e"],
+            "clocks": clk.summary(),
             "gpu_launches": m["gpu_launches"]}
     print(json.dumps(line), flush=True)
     return 0
@@ -745,7 +765,7 @@ def run_ours(args):
                              "iterations": dres[-1].iters, "refinements": dres[-1].refinements,
                              "status": dres[-1].status}
         mx = mixture_measure(lbe, torch, local, 1, 1)
-        line["mixture"] = {k: mx[k] for k in ("solves_per_s", "config", "roofline", "table4", "build_s")}
+        line["mixture"] = {k: mx[k] for k in ("solves_per_s", "config", "roofline", "table4", "build_s", "refined")}
         sctx = lbe.Context(local)
         line["serving"] = serve_stream(sctx, lbe, prec, args.eps, args.requests)
         line["latency_ms"] = dict(line["serving"]["latency_ms"], workload=line["serving"]["workload"])

@@ -374,15 +374,24 @@ typedef struct {
     double R;            /* Carleman truncation radius > 0                                      */
     lbe_scheme scheme;
     double eps;          /* stop when all four flow rates change by < eps relative; 0 = never   */
-    int max_iter;
+    int max_iter;        /* cap on all iterations                                               */
+    lbe_precision precision; /* LBE_FP64; LBE_BF16: the operator as a tcgen05 BF16 hi/lo GEMM with
+                          * float accumulation (everything else FP64), stopping when the four
+                          * changes fall below eps times the larger molecular flow rate;
+                          * LBE_BF16_REFINED: such iterations down to their floor (changes below
+                          * 1e-5 of that scale, or no longer shrinking for three iterations),
+                          * then defect correction: an FP64 iteration h' = Phi(h) (its change is
+                          * the FP64 stopping test), and its error e = G (e + h' - h) solved by
+                          * the source-free iteration on the tensor cores; h = h' + e           */
 } lbe_mix_problem;
 
 typedef struct {
     double M_A, M_B;     /* molecular flow rates M_a = sqrt(m / m_A) 2 int_{-1/2}^0 U_a dx1 (Sec. 4) */
     double Q_A, Q_B;     /* heat flow rates, q_a = int (r_a |v|^2 - 5/2) v3 h_a dv                  */
-    int iters;
+    int iters;           /* all iterations                                                          */
     int status;
     double N_A, N_B;     /* the tuning used                                                        */
+    int fp64_iters;      /* iterations with the FP64 operator                                      */
 } lbe_mix_result;
 
 /* Tables of one mixture on one grid: out4 (host, 4 doubles) receives b_AA at delta = 1 (the

@@ -1399,21 +1399,14 @@ static lbe_status build_dense(Ctx* c, DevTables* t, DenseOp& d, int mode, cudaSt
     return LBE_OK;
 }
 
-// L+ h and L h on the parity subspace with the dense tensor-core operator (float in / out).
-// sync = false leaves the stream running: the GEMM's failure word is copied to pinned host
-// memory behind it and tc_check reads it after the caller's own synchronisation.
-lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h, float* Lplus,
-                        float* Lout, cudaStream_t s, bool sync, const double* nd, double* G, const double* hm,
-                        bool quarter) {
-    if (mode != 1 && mode != 2) return LBE_BAD_ARG;
-    if (quarter && G && (!hm || Lout)) return LBE_BAD_ARG;
-    if (cells <= 0) return LBE_OK;
-    if (!t->tc) t->tc = new TcOperands();
-    TcOperands& T = *t->tc;
-    std::lock_guard<std::mutex> lk(T.mu);
-    DenseOp& d = T.op[mode];
+// The GEMM of a stacked-sub-block operator d: Y ([cells][d.L.rows], FP32, in T's workspace
+// for stream s) = the sub-blocks times the cell operand, which `fill(x2, cpad)` writes into the
+// hi / lo interleaved buffer [d.L.count][cpad][2 npmax] (rows cells .. cpad are zeroed here).
+// The work plans, the workspace and the form chosen by the autotuner are kept in T; with timed,
+// ev[0] / ev[1] bracket the launch.
+static lbe_status tc_gemm(Ctx* c, TcOperands& T, DenseOp& d, Tuning* tuning, int cells, cudaStream_t s, bool timed,
+                          cudaEvent_t* ev, const std::function<void(__nv_bfloat162*, int)>& fill, float** Yout) {
     lbe_status st;
-    if (!d.A && (st = build_dense(c, t, d, mode, s)) != LBE_OK) return st;
     if (!T.err_dev) {
         if ((st = dev_alloc(c, (void**)&T.err_dev, 256)) != LBE_OK) return st;
         if (cudaMallocHost((void**)&T.err_host, sizeof(int)) != cudaSuccess) {
@@ -1423,7 +1416,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         *T.err_host = 0;
         cudaMemsetAsync(T.err_dev, 0, sizeof(int), s);
     }
-    const int nv = t->nv, nsub = d.L.count, npmax = d.L.npmax;
+    const int nsub = d.L.count, npmax = d.L.npmax;
     const int mrows = d.L.rows;  // rows of the stacked sub-blocks (and of Y per cell)
     const int bn = pick_bn(cells);
     const long cpad = (cells + bn - 1) / bn * bn;  // whole TMA boxes, zero padding rows
@@ -1468,21 +1461,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         c->last_error = "cuTensorMapEncodeTiled failed for the cell operand";
         return LBE_INTERNAL;
     }
-    {
-        auto* x2 = reinterpret_cast<__nv_bfloat162*>(xhl);
-        const bool p2 = mode == 2;
-        const int cp = (int)cpad, qf = quarter ? 1 : 0;
-        switch (nv) {
-            case 8: (p2 ? launch_gather<8, 2> : launch_gather<8, 1>)(cells, cp, h, x2, s, qf); break;
-            case 16: (p2 ? launch_gather<16, 2> : launch_gather<16, 1>)(cells, cp, h, x2, s, qf); break;
-            case 24: (p2 ? launch_gather<24, 2> : launch_gather<24, 1>)(cells, cp, h, x2, s, qf); break;
-            default: (p2 ? launch_gather<32, 2> : launch_gather<32, 1>)(cells, cp, h, x2, s, qf); break;
-        }
-    }
-    // optional event timing of the GEMM alone (public synchronous calls only)
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    const bool timed = sync && g_time_kernels.load() != 0 && cudaEventCreate(&ev[0]) == cudaSuccess &&
-                       cudaEventCreate(&ev[1]) == cudaSuccess;
+    fill(reinterpret_cast<__nv_bfloat162*>(xhl), (int)cpad);
     const int probe = g_expire_waits.load();
     auto gemm = [&](int cs, bool with_fix) -> cudaError_t {
         const int k = cs == 4 ? 2 : (cs == 2 ? 1 : 0);
@@ -1598,7 +1577,7 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
                 if (best[i] < best[bi]) bi = i;
             plan.cs = cand[bi];
             T.cs_choice[cs_key] = plan.cs;
-            if (t->tuning) {
+            if (tuning) {
                 char line[256];
                 auto name = [](int c, char* b, size_t n) {
                     if (c == kPersistent)
@@ -1619,8 +1598,8 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
                                                                        : "did not launch");
                 }
                 if (n < (int)sizeof line) snprintf(line + n, sizeof line - n, ")");
-                std::lock_guard<std::mutex> lk2(t->tuning->mu);
-                t->tuning->log.push_back(line);
+                std::lock_guard<std::mutex> lk2(tuning->mu);
+                tuning->log.push_back(line);
             }
         }
     }
@@ -1630,6 +1609,48 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
         if (ge != cudaSuccess) return cuda_status(c, ge, "dense operator GEMM launch");
     }
     if (timed) cudaEventRecord(ev[1], s);
+    *Yout = Y;
+    return LBE_OK;
+}
+
+// L+ h and L h on the parity subspace with the dense tensor-core operator (float in / out).
+// sync = false leaves the stream running: the GEMM's failure word is copied to pinned host
+// memory behind it and tc_check reads it after the caller's own synchronisation.
+lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double* delta, const float* h, float* Lplus,
+                        float* Lout, cudaStream_t s, bool sync, const double* nd, double* G, const double* hm,
+                        bool quarter) {
+    if (mode != 1 && mode != 2) return LBE_BAD_ARG;
+    if (quarter && G && (!hm || Lout)) return LBE_BAD_ARG;
+    if (cells <= 0) return LBE_OK;
+    if (!t->tc) t->tc = new TcOperands();
+    TcOperands& T = *t->tc;
+    std::lock_guard<std::mutex> lk(T.mu);
+    DenseOp& d = T.op[mode];
+    lbe_status st;
+    if (!d.A && (st = build_dense(c, t, d, mode, s)) != LBE_OK) return st;
+    // optional event timing of the GEMM alone (public synchronous calls only)
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    const bool timed = sync && g_time_kernels.load() != 0 && cudaEventCreate(&ev[0]) == cudaSuccess &&
+                       cudaEventCreate(&ev[1]) == cudaSuccess;
+    float* Y = nullptr;
+    const int nv = t->nv;
+    st = tc_gemm(c, T, d, t->tuning, cells, s, timed, ev, [&](__nv_bfloat162* x2, int cp) {
+    {
+        const bool p2 = mode == 2;
+        const int qf = quarter ? 1 : 0;
+        switch (nv) {
+            case 8: (p2 ? launch_gather<8, 2> : launch_gather<8, 1>)(cells, cp, h, x2, s, qf); break;
+            case 16: (p2 ? launch_gather<16, 2> : launch_gather<16, 1>)(cells, cp, h, x2, s, qf); break;
+            case 24: (p2 ? launch_gather<24, 2> : launch_gather<24, 1>)(cells, cp, h, x2, s, qf); break;
+            default: (p2 ? launch_gather<32, 2> : launch_gather<32, 1>)(cells, cp, h, x2, s, qf); break;
+        }
+    }
+    }, &Y);
+    if (st != LBE_OK) {
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+        return st;
+    }
     {  // L+ h (L h when asked for) and, with G, the SIS L-moments in one pass
         const float* nu1 = t->nu1_f;
         const float* vel = t->vel_f;
@@ -1677,23 +1698,158 @@ lbe_status tc_check(Ctx* c, DevTables* t) {
     return LBE_TIMEOUT;
 }
 
-void tc_release(Ctx* c, DevTables* t) {
-    if (!t->tc) return;
-    for (auto& d : t->tc->op) {
-        dev_free(c, d.A, d.bytes);
-    }
-    for (auto& kv : t->tc->ws) arena_release(c, kv.second);
-    for (auto& kv : t->tc->plans) {
+// Frees the plans, workspaces and failure words of T (not its operators).
+static void release_operands(Ctx* c, TcOperands& T) {
+    for (auto& kv : T.ws) arena_release(c, kv.second);
+    for (auto& kv : T.plans) {
         dev_free(c, kv.second.work, kv.second.nwork * sizeof(GemmWork));
         dev_free(c, kv.second.work_t, kv.second.nwork * sizeof(GemmWork));
         if (kv.second.fix) dev_free(c, kv.second.fix, kv.second.nfix * sizeof(GemmFix));
         dev_free(c, kv.second.work_p, kv.second.nwork * sizeof(GemmWork));
         dev_free(c, kv.second.cta_off, (kv.second.nprog + 1) * sizeof(int));
     }
-    dev_free(c, t->tc->err_dev, 256);
-    if (t->tc->err_host) cudaFreeHost(t->tc->err_host);
+    dev_free(c, T.err_dev, 256);
+    if (T.err_host) cudaFreeHost(T.err_host);
+    T.err_dev = nullptr;
+    T.err_host = nullptr;
+}
+
+void tc_release(Ctx* c, DevTables* t) {
+    if (!t->tc) return;
+    for (auto& d : t->tc->op) {
+        dev_free(c, d.A, d.bytes);
+    }
+    release_operands(c, *t->tc);
     delete t->tc;
     t->tc = nullptr;
+}
+
+// ---- the binary-mixture operator on the tensor cores (mixture.cu) ----------------------------
+// The dense FP64 mixture matrix ([n][n] row-major, n = both species' unknowns per cell) as one
+// sub-block of n rows and columns, padded to the 128-row tile, in BF16 hi / lo; the cell
+// operand is both species' h of a cell, hi / lo, padded with zeros.
+struct MixTc {
+    TcOperands T;
+    DenseOp d;
+};
+
+namespace {
+
+__global__ void k_mix_store_bf16(const double* __restrict__ L, int n, int np, __nv_bfloat16* __restrict__ A) {
+    const long total = (long)n * n;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const long r = t / n, col = t - r * n;
+        const double a = L[t];
+        const __nv_bfloat16 hi = __float2bfloat16_rn((float)a);
+        const long idx = r * 2 * np + ilv(col);
+        A[idx] = hi;
+        A[idx + kBK] = __float2bfloat16_rn((float)(a - (double)__bfloat162float(hi)));
+    }
+}
+
+// x2: [cells][np] columns as hi / lo pairs (k even): column k < nr is h_A[c cs + k], nr <= k < 2 nr
+// is h_B[c cs + k - nr], the rest zero
+__global__ void k_mix_gather(const double* __restrict__ hA, const double* __restrict__ hB, long cs, int nr, int np,
+                             int cells, __nv_bfloat162* __restrict__ x2) {
+    const int half = np / 2;
+    const long total = (long)cells * half;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const long c = t / half;
+        const int k = 2 * (int)(t - c * half);
+        double v[2];
+        for (int u = 0; u < 2; ++u) {
+            const int kk = k + u;
+            v[u] = kk < nr ? hA[c * cs + kk] : (kk < 2 * nr ? hB[c * cs + kk - nr] : 0.0);
+        }
+        const __nv_bfloat16 h0 = __float2bfloat16_rn((float)v[0]), h1 = __float2bfloat16_rn((float)v[1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn((float)(v[0] - (double)__bfloat162float(h0)));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn((float)(v[1] - (double)__bfloat162float(h1)));
+        const long o = (c * 2 * np + ilv(k)) / 2;
+        x2[o] = __halves2bfloat162(h0, h1);
+        x2[o + kBK / 2] = __halves2bfloat162(l0, l1);
+    }
+}
+
+// y_a[c cs + j] = scale Y[c mrows + a nr + j]
+__global__ void k_mix_readback(const float* __restrict__ Y, int mrows, int nr, int cells, long cs, double scale,
+                               double* __restrict__ yA, double* __restrict__ yB) {
+    const long total = (long)cells * 2 * nr;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const long c = t / (2 * nr);
+        const int r = (int)(t - c * 2 * nr);
+        (r < nr ? yA : yB)[c * cs + (r < nr ? r : r - nr)] = scale * (double)Y[c * mrows + r];
+    }
+}
+
+}  // namespace
+
+lbe_status mix_tc_build(Ctx* c, const double* L, int n, MixTc** out, cudaStream_t s) {
+    MixTc* m = new MixTc();
+    DenseOp& d = m->d;
+    d.mode = 0;
+    d.L.count = 1;
+    d.L.kind[0] = 0;
+    d.L.n[0] = n;
+    d.L.np[0] = pad128(n);
+    d.L.rows = d.L.np[0];
+    d.L.npmax = d.L.np[0];
+    const size_t abytes = (size_t)d.L.rows * 2 * d.L.npmax * 2;
+    lbe_status st = dev_alloc(c, (void**)&d.A, abytes);
+    if (st != LBE_OK) {
+        delete m;
+        return st;
+    }
+    d.bytes = abytes;
+    cudaMemsetAsync(d.A, 0, abytes, s);
+    k_mix_store_bf16<<<8 * sm_count(), 256, 0, s>>>(L, n, d.L.npmax, d.A);
+    g_launches += 1;
+    st = cuda_status(c, cudaStreamSynchronize(s), "mixture tensor-core operator");
+    bool maps = st == LBE_OK;
+    for (int k = 0; k < 3 && maps; ++k) maps = make_map(&d.mA[k], d.A, d.L.rows, d.L.npmax, kBM >> k);
+    if (st == LBE_OK && !maps) {
+        c->last_error = "cuTensorMapEncodeTiled unavailable or failed";
+        st = LBE_INTERNAL;
+    }
+    if (st != LBE_OK) {
+        mix_tc_release(c, m);
+        return st;
+    }
+    *out = m;
+    return LBE_OK;
+}
+
+lbe_status mix_tc_apply(Ctx* c, MixTc* m, int cells, const double* hA, const double* hB, long cs, int nr,
+                        double scale, double* yA, double* yB, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(m->T.mu);
+    float* Y = nullptr;
+    const int np = m->d.L.npmax;
+    lbe_status st = tc_gemm(c, m->T, m->d, nullptr, cells, s, false, nullptr, [&](__nv_bfloat162* x2, int) {
+        const long tot = (long)cells * (np / 2);
+        k_mix_gather<<<(int)std::min<long>((tot + 255) / 256, 32L * sm_count()), 256, 0, s>>>(hA, hB, cs, nr, np,
+                                                                                              cells, x2);
+    }, &Y);
+    if (st != LBE_OK) return st;
+    const long tot = (long)cells * 2 * nr;
+    k_mix_readback<<<(int)std::min<long>((tot + 255) / 256, 32L * sm_count()), 256, 0, s>>>(
+        Y, m->d.L.rows, nr, cells, cs, scale, yA, yB);
+    g_launches += 3;
+    cudaMemcpyAsync(m->T.err_host, m->T.err_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+    return cuda_status(c, cudaGetLastError(), "mixture tensor-core operator");
+}
+
+lbe_status mix_tc_check(Ctx* c, MixTc* m) {
+    if (!m->T.err_host || !*m->T.err_host) return LBE_OK;
+    *m->T.err_host = 0;
+    cudaMemset(m->T.err_dev, 0, sizeof(int));
+    c->last_error = "mixture tensor-core operator: a bounded wait expired";
+    return LBE_TIMEOUT;
+}
+
+void mix_tc_release(Ctx* c, MixTc* m) {
+    if (!m) return;
+    dev_free(c, m->d.A, m->d.bytes);
+    release_operands(c, m->T);
+    delete m;
 }
 
 }  // namespace lbe

@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -51,6 +52,9 @@ struct MixOp {
     DevTables tab[2];         // per species: the transport sweep's tables (vel, f_a,eq, nu_a)
     double* part = nullptr;   // split-K partial sums of the GEMM (grow-only)
     size_t part_bytes = 0;
+    MixTc* tc = nullptr;      // the same operator in BF16 hi / lo on the tensor cores (first use)
+    double* zero = nullptr;   // [n3] zeros: the source-free sweep's f_eq
+    DevTables tab0[2];        // tab with a zero source (the correction equation's sweep)
 };
 
 namespace {
@@ -69,14 +73,6 @@ double viscosity1(double mB, double dB, double xA) {
     const double Z = 0.6 * (x1 * x1 * m1 / m2 + 2.0 * x1 * x2 * (q * (e12 / e1 + e12 / e2) - 1.0) +
                             x2 * x2 * m2 / m1);
     return (1.0 + Z) / (X + Y);
-}
-
-__device__ __forceinline__ double phi_dev(double x, double R2) {
-    // phi = 2 R^2 [sin x / x - 2 sin^2(x/2) / x^2], x = R s
-    if (fabs(x) < 1e-3) return R2 * (1.0 - x * x / 4.0 + x * x * x * x / 72.0);
-    double sh, ch;
-    sincos(0.5 * x, &sh, &ch);
-    return 2.0 * R2 * (2.0 * sh * ch / x - 2.0 * sh * sh / (x * x));
 }
 
 // T[p n3 + m] = (sin, cos)(f s_p(m))
@@ -278,6 +274,7 @@ struct MixSisDev {
     double r[2], chi[2], Nd[2], delta, dv3, sqm;
     double cU[2], cq[2];
     int nv, cells, sis;
+    int src;  // 1: the problem's own iteration; 0: the source-free one of the correction equation
 };
 
 // per (cell, species): mom[(a cells + n) 5 + .] = {U, q, W, P, G} of h^(k+1/2) (U, q, W, P)
@@ -321,16 +318,25 @@ __global__ void __launch_bounds__(256) k_mix_moments(MixSisDev P, const double* 
 }
 
 // one thread per species: the once-integrated diffusion equation marched from the wall,
-// d(chi U + W)/dx1 = G - (N delta / r) P~, P~_B = P_B, P~_A = x1 - P_B; dU, the corrected U
-// and q, and the flow rates M_a = sqrt(m) sum trap U, Q_a = sqrt(m) sum trap q.
-__global__ void k_mix_march(MixSisDev P, const double* __restrict__ mom, const double* __restrict__ geo,
-                            double* __restrict__ dU, double* __restrict__ Uout, double* __restrict__ rates) {
+// d(chi U + W)/dx1 = G - (N delta / r) P~, P~_B = P_B, P~_A = x1 - P_B (P~_A = -P_B without the
+// source); dU, the corrected U and q, and the flow rates M_a = sqrt(m) sum trap U,
+// Q_a = sqrt(m) sum trap q.  The block first stages the moments and the node coefficients in
+// shared memory (the march itself is a short serial recurrence).
+constexpr int kMarchMax = 1001;
+__global__ void __launch_bounds__(256) k_mix_march(MixSisDev P, const double* __restrict__ mom,
+                                                   const double* __restrict__ geo, double* __restrict__ dU,
+                                                   double* __restrict__ Uout, double* __restrict__ rates) {
+    extern __shared__ double sm[];  // [10 n] moments, [5 n] geometry
+    const int n = P.cells;
+    for (int i = threadIdx.x; i < 10 * n; i += blockDim.x) sm[i] = mom[i];
+    for (int i = threadIdx.x; i < 5 * n; i += blockDim.x) sm[10 * n + i] = geo[i];
+    __syncthreads();
     const int a = threadIdx.x;
     if (a >= 2) return;
-    const int n = P.cells;
-    const double *x = geo, *fa = geo + n, *fb = geo + 2 * n, *fc = geo + 3 * n, *trap = geo + 4 * n;
-    const double* ma = mom + (long)a * n * 5;
-    const double* mB = mom + (long)n * 5;
+    const double *x = sm + 10 * n, *fa = x + n, *fb = x + 2 * n, *fc = x + 3 * n, *trap = x + 4 * n;
+    const double* ma = sm + a * n * 5;
+    const double* mB = sm + n * 5;
+    const double kN = P.Nd[a] / P.r[a], chi = P.chi[a], cU = P.cU[a], cq = P.cq[a];
     double Mr = 0.0, Qr = 0.0, y1 = 0.0, y2 = 0.0;
     for (int i = 0; i < n; ++i) {
         const double U = ma[5 * i], q = ma[5 * i + 1], W = ma[5 * i + 2];
@@ -338,25 +344,32 @@ __global__ void k_mix_march(MixSisDev P, const double* __restrict__ mom, const d
         if (P.sis) {
             double Y;
             if (i == 0) {
-                Y = P.chi[a] * U + W;
+                Y = chi * U + W;
             } else {
-                const double Pt = a == 0 ? x[i] - mB[5 * i + 3] : mB[5 * i + 3];
-                double src = ma[5 * i + 4] - P.Nd[a] / P.r[a] * Pt - fb[i] * y1;
-                if (i >= 2) src -= fc[i] * y2;
-                Y = src / fa[i];
+                const double Pt = a == 0 ? (P.src ? x[i] : 0.0) - mB[5 * i + 3] : mB[5 * i + 3];
+                double sr = ma[5 * i + 4] - kN * Pt - fb[i] * y1;
+                if (i >= 2) sr -= fc[i] * y2;
+                Y = sr / fa[i];
             }
             y2 = y1;
             y1 = Y;
-            d = (Y - W) / P.chi[a] - U;
+            d = (Y - W) / chi - U;
         }
         dU[a * n + i] = d;
-        const double Uc = U + d * P.cU[a], qc = q + d * P.cq[a];
+        const double Uc = U + d * cU, qc = q + d * cq;
         Uout[a * n + i] = Uc;
         Mr += trap[i] * Uc;
         Qr += trap[i] * qc;
     }
     rates[a] = P.sqm * Mr;
     rates[2 + a] = P.sqm * Qr;
+}
+
+// y = a + s b over n values
+__global__ void k_mix_axpy(const double* __restrict__ a, double s, const double* __restrict__ b, long n,
+                           double* __restrict__ y) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        y[t] = a[t] + s * b[t];
 }
 
 // h_a = hh_a + 2 r_a dU_a v3 f_a,eq on the representatives
@@ -407,6 +420,8 @@ void free_mixop(Ctx* c, MixOp* o) {
     if (o->feq) dev_free(c, o->feq, sizeof(double) * 2 * n3);
     if (o->vel) dev_free(c, o->vel, sizeof(double) * o->nv);
     if (o->part) dev_free(c, o->part, o->part_bytes);
+    if (o->tc) mix_tc_release(c, o->tc);
+    if (o->zero) dev_free(c, o->zero, sizeof(double) * n3);
     delete o;
 }
 
@@ -608,6 +623,8 @@ lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
     if (d_C) dev_free(c, d_C, sizeof(double2) * 6 * N * N);
     if (d_T) dev_free(c, d_T, sizeof(double2) * 2 * M * n3);
     if (st != LBE_OK) return st;
+    if ((st = dev_alloc(c, (void**)&o.zero, sizeof(double) * n3)) != LBE_OK) return st;
+    cudaMemsetAsync(o.zero, 0, sizeof(double) * n3, s);
     for (int a = 0; a < 2; ++a) {
         DevTables& t = o.tab[a];
         t.nv = N;
@@ -618,8 +635,10 @@ lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
         t.vel_d = o.vel;
         t.feq_d = o.feq + a * n3;
         t.nu1_d = o.nu + a * n3;
+        o.tab0[a] = t;
+        o.tab0[a].feq_d = o.zero;
     }
-    return LBE_OK;
+    return cuda_status(c, cudaStreamSynchronize(s), "mixture tables");
 }
 
 MixOp* get_mixop(Ctx* c, const lbe_mixture& m, int nv, double vmax, int M, double R, int layout, cudaStream_t s,
@@ -762,10 +781,14 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
         return bad_arg(ctx, "mixture plates: 2 <= ns <= 1000, grid_kind 0 or 1");
     if (!(pb->delta >= 0) || pb->max_iter < 1 || !(pb->eps >= 0) || (pb->scheme != LBE_CIS && pb->scheme != LBE_SIS))
         return bad_arg(ctx, "mixture plates: delta >= 0, max_iter >= 1, eps >= 0, scheme CIS or SIS");
+    if (pb->precision != LBE_FP64 && pb->precision != LBE_BF16 && pb->precision != LBE_BF16_REFINED)
+        return bad_arg(ctx, "mixture plates: precision FP64, BF16 or BF16_REFINED");
     cudaSetDevice(ctx->device);
     cudaStream_t s = ctx->stream;
     MixOp* o = get_mixop(ctx, pb->mix, pb->nv, pb->vmax, pb->M, pb->R, 1, s, &st);
     if (!o) return st;
+    bool lo = pb->precision != LBE_FP64;  // operator on the tensor cores (BF16 hi / lo)
+    if (lo && !o->tc && (st = mix_tc_build(ctx, o->L, 2 * o->nr, &o->tc, s)) != LBE_OK) return st;
     lbe_problem geo{};
     geo.geom.dim = 1;
     geo.geom.ns = pb->ns;
@@ -805,9 +828,17 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     auto take = [&](void** p, size_t bytes) {
         if (st == LBE_OK) st = dev_alloc(ctx, p, bytes);
     };
+    const bool refined = pb->precision == LBE_BF16_REFINED;
+    void *d_hp = nullptr, *d_e = nullptr, *d_x = nullptr, *d_d = nullptr;
     take(&d_h, b_state);
     take(&d_hh, b_state);
     take(&d_lp, b_state);
+    if (refined) {
+        take(&d_hp, b_state);
+        take(&d_e, b_state);
+        take(&d_x, b_state);
+        take(&d_d, b_state);
+    }
     take(&d_small, b_small);
     take(&d_job, sizeof job);
     double* h = (double*)d_h;
@@ -820,47 +851,129 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     double* dcoef = rates + 8;
     double* dgeo = dcoef + coef.size();
     double hr[4] = {0, 0, 0, 0}, old[4] = {0, 0, 0, 0};
-    int it = 0;
+    int it = 0, it64 = 0;
     bool conv = false, bad = false;
+    static std::once_flag march_attr;  // the march stages up to 15 x 1001 doubles
+    std::call_once(march_attr, [] {
+        cudaFuncSetAttribute(k_mix_march, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(15 * kMarchMax * sizeof(double)));
+    });
+    const size_t march_smem = 15 * (size_t)n * sizeof(double);
+    // one iteration hin -> hout (hout may be hin) with the operator in FP64 or on the tensor
+    // cores; homog: the source-free iteration (no S_a in the sweep, no x1 in the march); r
+    // receives the flow rates of hout
+    auto step = [&](const double* hin, double* hout, bool tc, bool homog, double* r) -> lbe_status {
+        lbe_status e = tc ? mix_tc_apply(ctx, o->tc, n, hin, hin + per, n3, o->nr, pb->delta, lp, lp + per, s)
+                          : mix_gemm(ctx, *o, hin, hin + per, n3, n, pb->delta, lp, lp + per, s);
+        if (e != LBE_OK) return e;
+        for (int a = 0; a < 2; ++a)
+            launch_sweep<double>(homog ? o->tab0[a] : o->tab[a], 1, 1, (int)coef.size(), lp + a * per, hh + a * per,
+                                 (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
+        MixSisDev Q = P;
+        Q.src = homog ? 0 : 1;
+        k_mix_moments<<<dim3(n, 2), 256, 0, s>>>(Q, hh, hin, lp, o->nu, o->vel, mom);
+        k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
+        k_mix_correct<<<grid_for(2L * n * n3 / 4), 256, 0, s>>>(Q, hh, hout, dU, o->feq, o->vel);
+        g_launches += 3;
+        g_levals += n;
+        cudaMemcpyAsync(r, rates, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        g_d2h += 4 * sizeof(double);
+        if ((e = cuda_status(ctx, cudaStreamSynchronize(s), "mixture iteration")) != LBE_OK) return e;
+        if (tc && (e = mix_tc_check(ctx, o->tc)) != LBE_OK) return e;
+        ++it;
+        if (!tc) ++it64;
+        for (int k = 0; k < 4; ++k)
+            if (!std::isfinite(r[k])) bad = true;
+        return LBE_OK;
+    };
+    auto axpy = [&](const double* x, double sc, const double* y, double* z) {
+        k_mix_axpy<<<grid_for(2 * per), 256, 0, s>>>(x, sc, y, 2 * per, z);
+        g_launches += 1;
+    };
     if (st == LBE_OK) {
         cudaMemsetAsync(h, 0, b_state, s);
+        for (void* q : {d_hp, d_e, d_x, d_d})
+            if (q) cudaMemsetAsync(q, 0, b_state, s);
         cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(dgeo, geov.data(), sizeof(double) * geov.size(), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_job, &job, sizeof job, cudaMemcpyHostToDevice, s);
         g_h2d += sizeof(double) * (coef.size() + geov.size()) + sizeof job;
+        // plain iterations: FP64 and BF16 to their stopping tests, BF16_REFINED to the
+        // low-precision floor.  FP64: every flow rate changes by < eps relative.  Tensor-core
+        // iterations (float accumulation) cannot resolve a small flow rate below the larger
+        // one's rounding, so their changes are measured against the larger molecular flow rate.
+        int rising = 0;
+        double prev = 1e300;
         while (it < pb->max_iter) {
-            if ((st = mix_gemm(ctx, *o, h, h + per, n3, n, pb->delta, lp, lp + per, s)) != LBE_OK) break;
-            for (int a = 0; a < 2; ++a)
-                launch_sweep<double>(o->tab[a], 1, 1, (int)coef.size(), lp + a * per, hh + a * per,
-                                     (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
-            k_mix_moments<<<dim3(n, 2), 256, 0, s>>>(P, hh, h, lp, o->nu, o->vel, mom);
-            k_mix_march<<<1, 32, 0, s>>>(P, mom, dgeo, dU, Uc, rates);
-            if (P.sis) {
-                k_mix_correct<<<grid_for(2L * n * n3 / 4), 256, 0, s>>>(P, hh, h, dU, o->feq, o->vel);
-                g_launches += 1;
-            } else {
-                std::swap(h, hh);
-            }
-            g_launches += 2;
-            g_levals += n;
-            cudaMemcpyAsync(hr, rates, sizeof hr, cudaMemcpyDeviceToHost, s);
-            g_d2h += sizeof hr;
-            if ((st = cuda_status(ctx, cudaStreamSynchronize(s), "mixture iteration")) != LBE_OK) break;
-            ++it;
-            bool fin = true, same = pb->eps > 0;
+            if ((st = step(h, h, lo, false, hr)) != LBE_OK || bad) break;
+            const double scale = std::max(std::fabs(hr[0]), std::fabs(hr[1]));
+            bool same = pb->eps > 0;
+            double change = 0.0;
             for (int k = 0; k < 4; ++k) {
-                fin = fin && std::isfinite(hr[k]);
-                same = same && std::fabs(hr[k] - old[k]) < pb->eps * std::fabs(hr[k]);
+                const double dk = std::fabs(hr[k] - old[k]);
+                change = std::max(change, dk);
+                same = same && dk < pb->eps * (lo ? scale : std::fabs(hr[k]));
                 old[k] = hr[k];
             }
-            if (!fin) {
-                bad = true;
-                break;
+            if (refined) {
+                // hand over at the floor: changes below 1e-5 of the scale, or no longer shrinking
+                rising = change >= prev ? rising + 1 : 0;
+                prev = change;
+                if (change < 1e-5 * scale || rising >= 3) break;
+                continue;
             }
             if (same) {
                 conv = true;
                 break;
             }
+        }
+        // defect correction (BF16_REFINED).  The iteration is affine, Phi(h) = G h + c; from h,
+        // one FP64 iteration h' = Phi(h) (its change is the stopping test), and the error of h'
+        // solves e = G (e + d), d = h' - h, which the source-free iteration on the tensor cores
+        // approximates (e_0 = 0, e_(j+1) = G_lo (e_j + d)); then h = h' + e, and the flow rates,
+        // linear in h, are those of h' plus those of e.
+        double* hp = (double*)d_hp;
+        double* ev = (double*)d_e;
+        double* xv = (double*)d_x;
+        double* dv = (double*)d_d;
+        while (refined && st == LBE_OK && !bad && it < pb->max_iter) {
+            if ((st = step(h, hp, false, false, hr)) != LBE_OK || bad) break;
+            bool same = pb->eps > 0;
+            for (int k = 0; k < 4; ++k) same = same && std::fabs(hr[k] - old[k]) < pb->eps * std::fabs(hr[k]);
+            if (same) {
+                std::swap(h, hp);
+                conv = true;
+                break;
+            }
+            axpy(hp, -1.0, h, dv);
+            cudaMemsetAsync(ev, 0, b_state, s);
+            double re[4] = {0, 0, 0, 0};
+            double pe = 1e300;
+            int up = 0;
+            for (int j = 0; j < 200 && it < pb->max_iter; ++j) {
+                axpy(ev, 1.0, dv, xv);
+                double r[4];
+                if ((st = step(xv, ev, true, true, r)) != LBE_OK || bad) break;
+                double change = 0.0;
+                for (int k = 0; k < 4; ++k) change = std::max(change, std::fabs(r[k] - re[k])), re[k] = r[k];
+                const double emag = std::max(std::fabs(re[0]), std::fabs(re[1]));
+                up = change >= pe ? up + 1 : 0;
+                pe = change;
+                if (change <= 1e-4 * emag || up >= 3) break;
+            }
+            if (st != LBE_OK || bad) break;
+            axpy(hp, 1.0, ev, h);
+            for (int k = 0; k < 4; ++k) old[k] = hr[k] + re[k];
+        }
+        if (refined && st == LBE_OK && !bad) {
+            // U and the flow rates of the returned h
+            MixSisDev Q = P;
+            Q.sis = 0;
+            k_mix_moments<<<dim3(n, 2), 256, 0, s>>>(Q, h, h, lp, o->nu, o->vel, mom);
+            k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
+            cudaMemcpyAsync(hr, rates, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+            g_launches += 2;
+            st = cuda_status(ctx, cudaStreamSynchronize(s), "mixture flow rates");
         }
     }
     if (st == LBE_OK && U_out) {
@@ -890,11 +1003,14 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     dev_free(ctx, d_lp, b_state);
     dev_free(ctx, d_small, b_small);
     dev_free(ctx, d_job, sizeof job);
+    for (void* q : {d_hp, d_e, d_x, d_d})
+        if (q) dev_free(ctx, q, b_state);
     out->M_A = hr[0];
     out->M_B = hr[1];
     out->Q_A = hr[2];
     out->Q_B = hr[3];
     out->iters = it;
+    out->fp64_iters = it64;
     out->N_A = P.Nd[0] / (pb->delta > 0 ? pb->delta : 1.0);
     out->N_B = P.Nd[1] / (pb->delta > 0 ? pb->delta : 1.0);
     out->status = st != LBE_OK ? st : bad ? LBE_NAN : conv ? LBE_OK : LBE_NOT_CONVERGED;

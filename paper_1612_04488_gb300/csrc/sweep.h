@@ -20,6 +20,16 @@ lbe_status tc_apply_sym(Ctx* c, DevTables* t, int mode, int cells, const double*
                         double* G = nullptr, const double* hm = nullptr, bool quarter = false);
 lbe_status tc_check(Ctx* c, DevTables* t);
 void tc_release(Ctx* c, DevTables* t);
+// the binary-mixture operator on the tensor cores: the FP64 matrix L ([n][n], both species)
+// in BF16 hi / lo; apply: y_a = scale (L h) for cells whose unknowns are h_A, h_B at [c cs],
+// nr per species (float accumulation); check reads the GEMM's failure word after the
+// stream's synchronisation
+struct MixTc;
+lbe_status mix_tc_build(Ctx* c, const double* L, int n, MixTc** out, cudaStream_t s);
+lbe_status mix_tc_apply(Ctx* c, MixTc* m, int cells, const double* hA, const double* hB, long cs, int nr,
+                        double scale, double* yA, double* yB, cudaStream_t s);
+lbe_status mix_tc_check(Ctx* c, MixTc* m);
+void mix_tc_release(Ctx* c, MixTc* m);
 // refine.cu: BF16 operator inside an outer defect-correction loop
 lbe_status refined_solve(Ctx* c, const lbe_problem* pbs, int n, lbe_result* outs, double* U3_out,
                          double* h_out);

@@ -43,18 +43,19 @@ class MixProblem(C.Structure):
     _fields_ = [("mix", Mixture), ("ns", C.c_int), ("grid_kind", C.c_int), ("delta", C.c_double),
                 ("N_A", C.c_double), ("N_B", C.c_double), ("nv", C.c_int), ("vmax", C.c_double),
                 ("M", C.c_int), ("R", C.c_double), ("scheme", C.c_int), ("eps", C.c_double),
-                ("max_iter", C.c_int)]
+                ("max_iter", C.c_int), ("precision", C.c_int)]
 
 
 class MixResult(C.Structure):
     _fields_ = [("M_A", C.c_double), ("M_B", C.c_double), ("Q_A", C.c_double), ("Q_B", C.c_double),
-                ("iters", C.c_int), ("status", C.c_int), ("N_A", C.c_double), ("N_B", C.c_double)]
+                ("iters", C.c_int), ("status", C.c_int), ("N_A", C.c_double), ("N_B", C.c_double),
+                ("fp64_iters", C.c_int)]
 
 
 def mix_problem(mass_ratio, diam_ratio, chi_A, delta=1.0, ns=20, grid_kind=0, N_A=0.0, N_B=0.0, nv=16,
-                vmax=6.0, M=16, R=4.5, scheme=SIS, eps=1e-8, max_iter=500):
+                vmax=6.0, M=16, R=4.5, scheme=SIS, eps=1e-8, max_iter=500, precision=FP64):
     return MixProblem(Mixture(mass_ratio, diam_ratio, chi_A), ns, grid_kind, delta, N_A, N_B, nv, vmax, M, R,
-                      scheme, eps, max_iter)
+                      scheme, eps, max_iter, precision)
 
 
 class Stats(C.Structure):

@@ -145,3 +145,25 @@ def test_table4_transition_rows_approach_the_paper_as_the_velocity_grid_refines(
         assert np.all(errs[0] > errs[1]) and np.all(errs[1] > errs[2]), (delta, errs)
         if delta == 1.0:
             assert np.all(errs[2] < 0.03), errs
+
+
+@pytest.mark.parametrize("delta", [1.0, 10.0])
+def test_mixture_tensor_core_solves_reach_fp64(ctx, delta):
+    """BF16 hi / lo operator on the tensor cores: alone within 1e-4 of the larger flow rate;
+    with defect correction (BF16_REFINED: FP64 iterations whose errors are solved for on the
+    tensor cores) the FP64 solution to 1e-8 with at most a quarter of a plain FP64 solve's
+    FP64 iterations."""
+    from paper_1612_04488_gb300 import lbe
+    kw = dict(delta=delta, ns=40, grid_kind=1, nv=16, vmax=5.0, M=16, R=3.75, max_iter=400)
+    r64, _, _ = ctx.mix_solve(lbe.mix_problem(*NE_AR, 0.5, eps=1e-10, **kw), want_U=False)
+    rr, _, _ = ctx.mix_solve(lbe.mix_problem(*NE_AR, 0.5, eps=1e-10, precision=lbe.BF16_REFINED, **kw),
+                             want_U=False)
+    rb, _, _ = ctx.mix_solve(lbe.mix_problem(*NE_AR, 0.5, eps=1e-6, precision=lbe.BF16, **kw), want_U=False)
+    assert r64.status == rr.status == rb.status == lbe.OK
+    a = np.array([r64.M_A, r64.M_B, r64.Q_A, r64.Q_B])
+    b = np.array([rr.M_A, rr.M_B, rr.Q_A, rr.Q_B])
+    c = np.array([rb.M_A, rb.M_B, rb.Q_A, rb.Q_B])
+    assert np.max(np.abs(b - a) / np.abs(a)) < 1e-8, (a, b)
+    assert np.max(np.abs(c - a)) < 1e-4 * max(abs(a[0]), abs(a[1])), (a, c)
+    assert r64.fp64_iters == r64.iters and rb.fp64_iters == 0
+    assert 0 < rr.fp64_iters <= r64.iters // 4, (rr.fp64_iters, r64.iters)
