@@ -360,12 +360,12 @@ typedef struct {
     double chi_A;       /* molar fraction of A, 0 < chi_A < 1                                  */
 } lbe_mixture;
 
-/* Poiseuille flow of a mixture between plates (Sec. 4; S_a = v3 f_a,eq, X_P = -1): the half
- * channel of lbe_geometry dim = 1 (ns sections, grid_kind), diffuse wall, symmetry plane. */
+/* Poiseuille flow of a mixture (Sec. 4; S_a = v3 f_a,eq, X_P = -1) between plates (geom.dim = 1:
+ * the half channel, ns sections, grid_kind, diffuse wall, symmetry plane) or through a
+ * rectangular duct (geom.dim = 2: nx x ny cells of [0, width] x [0, 1], diffuse walls). */
 typedef struct {
     lbe_mixture mix;
-    int ns;
-    int grid_kind;
+    lbe_geometry geom;
     double delta;
     double N_A, N_B;     /* SIS tuning; <= 0 selects N_a = int nu_a,eq f_a,eq dv / (delta chi_a)  */
     int nv;              /* a multiple of 4, 4..32                                              */
@@ -386,7 +386,8 @@ typedef struct {
 } lbe_mix_problem;
 
 typedef struct {
-    double M_A, M_B;     /* molecular flow rates M_a = sqrt(m / m_A) 2 int_{-1/2}^0 U_a dx1 (Sec. 4) */
+    double M_A, M_B;     /* molecular flow rates M_a = sqrt(m / m_A) (1/A) int U_a (Sec. 4): plates
+                          * 2 int_{-1/2}^0 U_a dx1, ducts the cell mean                          */
     double Q_A, Q_B;     /* heat flow rates, q_a = int (r_a |v|^2 - 5/2) v3 h_a dv                  */
     int iters;           /* all iterations                                                          */
     int status;
@@ -408,9 +409,12 @@ lbe_status lbe_mix_apply_L(lbe_ctx* ctx, const lbe_mixture* mix, int nv, double 
                            int cells, double delta, const double* hA, const double* hB, double* LplusA,
                            double* LA, double* LplusB, double* LB, void* stream);
 
-/* Solve one mixture problem in FP64 by the CIS or the SIS of Eqs. LBE2_true1 / LBE2_true2
- * (h in the plate orbit layout on the device).  U_out (host, [2][ns + 1] or NULL) receives
- * U_A, U_B of the last iterate; h_out (host, [2][ns + 1][nv^3] or NULL) receives h_A, h_B.
+/* Solve one mixture problem by the CIS or the SIS of Eqs. LBE2_true1 / LBE2_true2 (plates: the
+ * equations integrated once across the half channel; ducts: one Poisson equation per species,
+ * the ring of wall-adjacent cells held at the kinetic U).  On the device h keeps one value per
+ * orbit of the parity group ({1, R2, R3, R2 R3} plates, {1, R3} ducts).  U_out (host,
+ * [2][cells] or NULL) receives U_A, U_B of the returned h; h_out (host, [2][cells][nv^3] or
+ * NULL) receives h_A, h_B; cells = ns + 1 or nx ny.
  * Returns the result's status: LBE_OK, LBE_NOT_CONVERGED (max_iter reached or eps = 0),
  * LBE_NAN (a non-finite flow rate), LBE_BAD_ARG, LBE_OOM. */
 lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe_mix_result* out, double* U_out,

@@ -52,8 +52,9 @@ explicit cyclic sum equals the matrix form (M2), brute-force sigma-representatio
 of the collision integral for unequal masses (M3), collision invariants (M4), conservation
 (M5), the sign of the dissipation (M6), the viscosity closed form against a Monte Carlo
 Galerkin on the weak form of the collision integral (M7); for the SIS:
-identical species reproduce the single-species CIS iteration exactly (M8), SIS and CIS reach
-the same solution to the discretisation, as the paper reports for one species (M9).
+identical species reproduce the single-species CIS iteration exactly, between plates and in a
+duct (M8), SIS and CIS reach the same solution to the discretisation, as the paper reports for
+one species (M9).
 """
 import numpy as np
 
@@ -348,12 +349,14 @@ def mc_galerkin_viscosity(mix, n=1_000_000, chunks=2, seed=7):
 
 # ---- synthetic iterative scheme for plates (Sec. 4) ------------------------------------------
 class MixProblem:
-    """Poiseuille flow of a binary mixture between plates (Sec. 4; Table 4's setting)."""
+    """Poiseuille flow of a binary mixture between plates (dim 1, Table 4's setting) or through
+    a rectangular duct [0, width] x [0, 1] of nx x ny cells (dim 2, Table 5's setting)."""
 
     def __init__(self, mass_ratio=39.95 / 20.18, diam_ratio=1.0 / 0.711, chi_A=0.5, delta=1.0,
                  ns=20, grid="uniform", nv=12, vmax=6.0, M=16, R=0.0, N_A=0.0, N_B=0.0,
-                 scheme="sis", eps=1e-8, max_iter=500):
+                 scheme="sis", eps=1e-8, max_iter=500, dim=1, nx=8, ny=8, width=1.0):
         self.mix = Mixture(mass_ratio, diam_ratio, chi_A)
+        self.dim, self.nx, self.ny, self.width = dim, nx, ny, float(width)
         self.delta, self.ns, self.grid = float(delta), ns, grid
         self.nv, self.vmax, self.M, self.R = nv, float(vmax), M, float(R)
         self.N = (float(N_A), float(N_B))
@@ -377,6 +380,13 @@ class MixRun:
       5. Correction (Eq. guided for each species): h_a += 2 r_a (U_a^(k+1) - U_a^(k+1/2)) v3 f_a,eq.
       6. Flow rates: M_a = sqrt(m / m_A) 2 ∫_{-1/2}^0 U_a dx1, Q_a likewise with
          q_a = ∫ (r_a |v|^2 - 5/2) v3 h_a.
+    In a duct (dim 2) step 4 is Eqs. LBE2_true1 / LBE2_true2 themselves, per species,
+         chi_a lap U_a = -(N_a delta / r_a) D_a - (d11 W_a1 + 2 d12 X_a12 + d22 W_a2)
+                         + d1 G_a1 + d2 G_a2,
+    with X_a12 = F^a_111 / 4, D_B = d1 P_B13 + d2 P_B23 of h^(k+1/2) and D_A = 1 - D_B (the
+    mixture relation dP13/dx1 + dP23/dx2 = 1), the five-point Laplacian and central
+    differences on interior cells, and U_a = U_a^(k+1/2) on the wall-adjacent ring, as for one
+    species; flow rates are sqrt(m / m_A) times cell averages.
     CIS: h^(k+1) = h^(k+1/2).  Stop when the relative changes of M_A, M_B, Q_A, Q_B are all < eps.
     N_a <= 0 selects the N_alpha equation of Sec. 4."""
 
@@ -384,8 +394,11 @@ class MixRun:
         self.pb = pb
         self.F = MixFSM(pb.mix, pb.nv, pb.vmax, pb.M, pb.R if pb.R > 0 else None) if F is None else F
         F = self.F
-        self.x = transport.nodes_uniform(pb.ns) if pb.grid == "uniform" else transport.nodes_clustered(pb.ns)
-        shape = (len(self.x),) + F.V1.shape
+        if pb.dim == 1:
+            self.x = transport.nodes_uniform(pb.ns) if pb.grid == "uniform" else transport.nodes_clustered(pb.ns)
+            shape = (len(self.x),) + F.V1.shape
+        else:
+            shape = (pb.nx, pb.ny) + F.V1.shape
         self.h = [np.zeros(shape), np.zeros(shape)]
         self.S = [F.V3 * F.f[a] for a in range(2)]
         self.Nd = [(pb.N[a] if pb.N[a] > 0 else F.N_alpha(a)) * pb.delta for a in range(2)]
@@ -404,6 +417,71 @@ class MixRun:
         P = 2.0 * r * np.sum(F.V1 * F.V3 * h, axis=ax) * w
         return U, q, W, P
 
+    def moments2(self, a, h):
+        """W_a2 = F^a_021 / 4, X_a12 = F^a_111 / 4 and P_a23 (duct terms)."""
+        F, w = self.F, self.F.dv ** 3
+        ax = (-3, -2, -1)
+        W2 = np.sum((2.0 * F.V2 ** 2 - 1.0) * F.V3 * h, axis=ax) * w
+        X12 = 2.0 * np.sum(F.V1 * F.V2 * F.V3 * h, axis=ax) * w
+        P23 = 2.0 * self.pb.mix.r[a] * np.sum(F.V2 * F.V3 * h, axis=ax) * w
+        return W2, X12, P23
+
+    def poisson(self, Uh, rhs, chi):
+        """chi lap U = rhs on interior cells (five-point, dense LU), U = Uh on the ring."""
+        pb = self.pb
+        nx, ny = Uh.shape
+        dx, dy = pb.width / nx, 1.0 / ny
+        mx, my = nx - 2, ny - 2
+        A = np.zeros((mx * my, mx * my))
+        b = rhs.reshape(-1) / chi
+        for p in range(mx):
+            for q in range(my):
+                k = p * my + q
+                A[k, k] = -2.0 / dx ** 2 - 2.0 / dy ** 2
+                for dp, dq, wgt in ((1, 0, 1.0 / dx ** 2), (-1, 0, 1.0 / dx ** 2),
+                                    (0, 1, 1.0 / dy ** 2), (0, -1, 1.0 / dy ** 2)):
+                    pp, qq = p + dp, q + dq
+                    if 0 <= pp < mx and 0 <= qq < my:
+                        A[k, pp * my + qq] = wgt
+                    else:
+                        b[k] -= wgt * Uh[pp + 1, qq + 1]
+        U = Uh.copy()
+        U[1:-1, 1:-1] = np.linalg.solve(A, b).reshape(mx, my)
+        return U
+
+    def step2(self, L, hh):
+        """Steps 3-5 in a duct: returns the corrected h of both species."""
+        F, pb, mix = self.F, self.pb, self.pb.mix
+        nx, ny = pb.nx, pb.ny
+        dx, dy = pb.width / nx, 1.0 / ny
+        I, J = np.meshgrid(np.arange(1, nx - 1), np.arange(1, ny - 1), indexing="ij")
+        w = F.dv ** 3
+        ax = (-3, -2, -1)
+
+        def d1(f):
+            return (f[I + 1, J] - f[I - 1, J]) / (2.0 * dx)
+
+        def d2(f):
+            return (f[I, J + 1] - f[I, J - 1]) / (2.0 * dy)
+
+        mo = [self.moments(a, hh[a]) + self.moments2(a, hh[a]) for a in range(2)]
+        DB = d1(mo[1][3]) + d2(mo[1][6])
+        D = [1.0 - DB, DB]
+        new = []
+        for a in range(2):
+            Uh, _, W1, _, W2, X12, _ = mo[a]
+            G1 = 2.0 * np.sum(F.V1 * F.V3 * (L[a] + self.Nd[a] * self.h[a]), axis=ax) * w
+            G2 = 2.0 * np.sum(F.V2 * F.V3 * (L[a] + self.Nd[a] * self.h[a]), axis=ax) * w
+            rhs = (-self.Nd[a] / mix.r[a] * D[a]
+                   - (W1[I + 1, J] - 2.0 * W1[I, J] + W1[I - 1, J]) / dx ** 2
+                   - 2.0 * (X12[I + 1, J + 1] - X12[I + 1, J - 1] - X12[I - 1, J + 1] + X12[I - 1, J - 1])
+                   / (4.0 * dx * dy)
+                   - (W2[I, J + 1] - 2.0 * W2[I, J] + W2[I, J - 1]) / dy ** 2
+                   + d1(G1) + d2(G2))
+            Un = self.poisson(Uh, rhs, mix.chi[a])
+            new.append(hh[a] + 2.0 * mix.r[a] * (Un - Uh)[(...,) + (None,) * 3] * F.V3 * F.f[a])
+        return new
+
     def march(self, Y0, src):
         a, b, c = transport.march_coeffs(self.x)
         Y = np.zeros(len(self.x))
@@ -420,9 +498,15 @@ class MixRun:
         mix, d = pb.mix, pb.delta
         lpA, LA, lpB, LB = F.apply(self.h[0], self.h[1], d)
         lp, L = [lpA, lpB], [LA, LB]
-        hh = [transport.sweep_1d(lp[a] + self.S[a], d * F.nu[a], F.V1, self.x) for a in range(2)]
+        if pb.dim == 1:
+            hh = [transport.sweep_1d(lp[a] + self.S[a], d * F.nu[a], F.V1, self.x) for a in range(2)]
+        else:
+            hh = [transport.sweep_2d(lp[a] + self.S[a], d * F.nu[a], F.V1, F.V2, pb.nx, pb.ny, pb.width)
+                  for a in range(2)]
         if pb.scheme == "cis":
             self.h = hh
+        elif pb.dim == 2:
+            self.h = self.step2(L, hh)
         else:
             w = F.dv ** 3
             G = [2.0 * np.sum(F.V1 * F.V3 * (L[a] + self.Nd[a] * self.h[a]), axis=(-3, -2, -1)) * w
@@ -442,6 +526,9 @@ class MixRun:
         s = np.sqrt(mix.mbar)
         self.U = [mo[0][0], mo[1][0]]
         self.iters += 1
+        if pb.dim == 2:
+            return np.array([s * np.mean(mo[0][0]), s * np.mean(mo[1][0]), s * np.mean(mo[0][1]),
+                             s * np.mean(mo[1][1])])
         return np.array([s * 2.0 * np.trapezoid(mo[0][0], self.x), s * 2.0 * np.trapezoid(mo[1][0], self.x),
                          s * 2.0 * np.trapezoid(mo[0][1], self.x), s * 2.0 * np.trapezoid(mo[1][1], self.x)])
 

@@ -35,7 +35,7 @@
 namespace lbe {
 
 struct MixOp {
-    int nv = 0, M = 0, layout = 0;  // layout 0: full velocity grid, 1: plate orbit layout
+    int nv = 0, M = 0, layout = 0;  // layout 0: full velocity grid, 1: plate orbit layout, 2: duct orbit layout
     double vmax = 0, R = 0;
     double r[2] = {1, 1}, d[2] = {1, 1}, chi[2] = {0.5, 0.5}, mbar = 1;
     int nr = 0;               // rows (= columns) of one species block
@@ -274,46 +274,65 @@ struct MixSisDev {
     double r[2], chi[2], Nd[2], delta, dv3, sqm;
     double cU[2], cq[2];
     int nv, cells, sis;
-    int src;  // 1: the problem's own iteration; 0: the source-free one of the correction equation
+    int src;     // 1: the problem's own iteration; 0: the source-free one of the correction equation
+    int layout;  // 1 plates (one value per orbit of {1, R2, R3, R2 R3}), 2 ducts ({1, R3})
 };
+constexpr int kMom = 9;  // per cell: U, q, W1, P13, G1, W2, X12, P23, G2
 
-// per (cell, species): mom[(a cells + n) 5 + .] = {U, q, W, P, G} of h^(k+1/2) (U, q, W, P)
-// and of L h^(k), h^(k) (G); sums over the orbit representatives times 4
+// the representative q of the orbit layout -> (i1, i2, i3) and the orbit size
+__device__ __forceinline__ void orbit_point(int q, int N, int layout, int* i1, int* i2, int* i3) {
+    const int H = N / 2, E2 = layout == 1 ? H : N;
+    *i1 = q / (E2 * H);
+    *i2 = q / H % E2;
+    *i3 = q % H;
+}
+
+// per (cell, species): mom[(a cells + n) kMom + .] = {U, q, W1, P13, G1, W2, X12, P23, G2}: U, q,
+// W1 = F201/4, P13, W2 = F021/4, X12 = F111/4, P23 of h^(k+1/2) and G_j of L h^(k), h^(k); sums
+// over the orbit representatives times the orbit size (4 plates, 2 ducts)
 __global__ void __launch_bounds__(256) k_mix_moments(MixSisDev P, const double* __restrict__ hh,
                                                      const double* __restrict__ h, const double* __restrict__ lp,
                                                      const double* __restrict__ nu, const double* __restrict__ vel,
                                                      double* __restrict__ mom) {
-    const int n = blockIdx.x, a = blockIdx.y, N = P.nv, H = N / 2, nq = N * H * H;
+    const int n = blockIdx.x, a = blockIdx.y, N = P.nv, H = N / 2;
+    const int nq = N * (P.layout == 1 ? H : N) * H;
     const long n3 = (long)N * N * N, off = ((long)a * P.cells + n) * n3;
     const double r = P.r[a];
-    double s[5] = {0, 0, 0, 0, 0};
+    double s[kMom] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-        const int i1 = q / (H * H), j2 = q / H % H, j3 = q % H;
-        const double v1 = vel[i1], v2 = vel[j2], v3 = vel[j3];
-        const double x = hh[off + q];
-        s[0] += v3 * x;
-        s[1] += (r * (v1 * v1 + v2 * v2 + v3 * v3) - 2.5) * v3 * x;
-        s[2] += (2.0 * v1 * v1 - 1.0) * v3 * x;
-        s[3] += v1 * v3 * x;
+        int i1, i2, i3;
+        orbit_point(q, N, P.layout, &i1, &i2, &i3);
+        const double v1 = vel[i1], v2 = vel[i2], v3 = vel[i3];
+        const double x = hh[off + q] * v3;
+        s[0] += x;
+        s[1] += (r * (v1 * v1 + v2 * v2 + v3 * v3) - 2.5) * x;
+        s[2] += (2.0 * v1 * v1 - 1.0) * x;
+        s[3] += v1 * x;
+        s[5] += (2.0 * v2 * v2 - 1.0) * x;
+        s[6] += v1 * v2 * x;
+        s[7] += v2 * x;
         if (P.sis) {
-            const long vf = ((long)i1 * N + j2) * N + j3;
-            const double y = lp[off + q] + (P.Nd[a] - P.delta * nu[a * n3 + vf]) * h[off + q];
-            s[4] += v1 * v3 * y;
+            const long vf = ((long)i1 * N + i2) * N + i3;
+            const double y = (lp[off + q] + (P.Nd[a] - P.delta * nu[a * n3 + vf]) * h[off + q]) * v3;
+            s[4] += v1 * y;
+            s[8] += v2 * y;
         }
     }
-    __shared__ double red[5][8];
-    for (int k = 0; k < 5; ++k) {
+    __shared__ double red[kMom][8];
+    for (int k = 0; k < kMom; ++k) {
         double v = s[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 5) {
+    if (threadIdx.x < kMom) {
+        const int k = threadIdx.x;
         double v = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-        const double w4 = 4.0 * P.dv3;
-        const double scl[5] = {w4 / P.chi[a], w4, w4, 2.0 * r * w4, 2.0 * w4};
-        mom[((long)a * P.cells + n) * 5 + threadIdx.x] = v * scl[threadIdx.x];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[k][w];
+        const double wq = (P.layout == 1 ? 4.0 : 2.0) * P.dv3;
+        const double scl = k == 0 ? wq / P.chi[a] : (k == 3 || k == 7) ? 2.0 * r * wq
+                         : (k == 4 || k == 6 || k == 8) ? 2.0 * wq : wq;
+        mom[((long)a * P.cells + n) * kMom + k] = v * scl;
     }
 }
 
@@ -326,28 +345,28 @@ constexpr int kMarchMax = 1001;
 __global__ void __launch_bounds__(256) k_mix_march(MixSisDev P, const double* __restrict__ mom,
                                                    const double* __restrict__ geo, double* __restrict__ dU,
                                                    double* __restrict__ Uout, double* __restrict__ rates) {
-    extern __shared__ double sm[];  // [10 n] moments, [5 n] geometry
+    extern __shared__ double sm[];  // [2 kMom n] moments, [5 n] geometry
     const int n = P.cells;
-    for (int i = threadIdx.x; i < 10 * n; i += blockDim.x) sm[i] = mom[i];
-    for (int i = threadIdx.x; i < 5 * n; i += blockDim.x) sm[10 * n + i] = geo[i];
+    for (int i = threadIdx.x; i < 2 * kMom * n; i += blockDim.x) sm[i] = mom[i];
+    for (int i = threadIdx.x; i < 5 * n; i += blockDim.x) sm[2 * kMom * n + i] = geo[i];
     __syncthreads();
     const int a = threadIdx.x;
     if (a >= 2) return;
-    const double *x = sm + 10 * n, *fa = x + n, *fb = x + 2 * n, *fc = x + 3 * n, *trap = x + 4 * n;
-    const double* ma = sm + a * n * 5;
-    const double* mB = sm + n * 5;
+    const double *x = sm + 2 * kMom * n, *fa = x + n, *fb = x + 2 * n, *fc = x + 3 * n, *trap = x + 4 * n;
+    const double* ma = sm + a * n * kMom;
+    const double* mB = sm + n * kMom;
     const double kN = P.Nd[a] / P.r[a], chi = P.chi[a], cU = P.cU[a], cq = P.cq[a];
     double Mr = 0.0, Qr = 0.0, y1 = 0.0, y2 = 0.0;
     for (int i = 0; i < n; ++i) {
-        const double U = ma[5 * i], q = ma[5 * i + 1], W = ma[5 * i + 2];
+        const double U = ma[kMom * i], q = ma[kMom * i + 1], W = ma[kMom * i + 2];
         double d = 0.0;
         if (P.sis) {
             double Y;
             if (i == 0) {
                 Y = chi * U + W;
             } else {
-                const double Pt = a == 0 ? (P.src ? x[i] : 0.0) - mB[5 * i + 3] : mB[5 * i + 3];
-                double sr = ma[5 * i + 4] - kN * Pt - fb[i] * y1;
+                const double Pt = a == 0 ? (P.src ? x[i] : 0.0) - mB[kMom * i + 3] : mB[kMom * i + 3];
+                double sr = ma[kMom * i + 4] - kN * Pt - fb[i] * y1;
                 if (i >= 2) sr -= fc[i] * y2;
                 Y = sr / fa[i];
             }
@@ -365,6 +384,92 @@ __global__ void __launch_bounds__(256) k_mix_march(MixSisDev P, const double* __
     rates[2 + a] = P.sqm * Qr;
 }
 
+// Ducts: one block per species solves Eqs. LBE2_true1 / LBE2_true2 on the interior
+// mx x my = (nx - 2) x (ny - 2) cells (cell (i, j) at i ny + j), U = U^(k+1/2) on the ring:
+//   chi_a lap U_a = -(N_a delta / r_a) D_a - (d11 W1 + 2 d12 X12 + d22 W2) + d1 G1 + d2 G2,
+// D_B = d1 P_B13 + d2 P_B23, D_A = 1 - D_B (-D_B without the source), five-point Laplacian and
+// central differences; by the DST-I: U = Sx ((Sx R Sy) ./ lam) Sy (Sx, Sy orthonormal and
+// symmetric).  Then dU, the corrected U and q, and the flow rates sqrt(m) times cell means.
+struct MixDuctDev {
+    int nx, ny;
+    double dx, dy;
+};
+__global__ void __launch_bounds__(512) k_mix_poisson2d(MixSisDev P, MixDuctDev D, const double* __restrict__ mom,
+                                                       const double* __restrict__ Sx, const double* __restrict__ Sy,
+                                                       const double* __restrict__ lam, double* __restrict__ work,
+                                                       double* __restrict__ dU, double* __restrict__ Uout,
+                                                       double* __restrict__ rates) {
+    const int a = blockIdx.x, nx = D.nx, ny = D.ny, mx = nx - 2, my = ny - 2, n = P.cells;
+    const long mm = (long)mx * my;
+    double* B = work + a * 2 * mm;
+    double* T1 = B + mm;
+    auto M = [&](int sp, int i, int j, int k) { return mom[((long)sp * n + (long)i * ny + j) * kMom + k]; };
+    if (P.sis) {
+        const double dx = D.dx, dy = D.dy, kN = P.Nd[a] / P.r[a], chi = P.chi[a];
+        for (long k = threadIdx.x; k < mm; k += blockDim.x) {
+            const int p = (int)(k / my), q = (int)(k % my), i = p + 1, j = q + 1;
+            auto d1 = [&](int sp, int c) { return (M(sp, i + 1, j, c) - M(sp, i - 1, j, c)) / (2.0 * dx); };
+            auto d2 = [&](int sp, int c) { return (M(sp, i, j + 1, c) - M(sp, i, j - 1, c)) / (2.0 * dy); };
+            const double DB = d1(1, 3) + d2(1, 7);
+            const double Dd = a == 0 ? (P.src ? 1.0 : 0.0) - DB : DB;
+            double b = -kN * Dd - (M(a, i + 1, j, 2) - 2.0 * M(a, i, j, 2) + M(a, i - 1, j, 2)) / (dx * dx) -
+                       2.0 * (M(a, i + 1, j + 1, 6) - M(a, i + 1, j - 1, 6) - M(a, i - 1, j + 1, 6) +
+                              M(a, i - 1, j - 1, 6)) / (4.0 * dx * dy) -
+                       (M(a, i, j + 1, 5) - 2.0 * M(a, i, j, 5) + M(a, i, j - 1, 5)) / (dy * dy) + d1(a, 4) +
+                       d2(a, 8);
+            b /= chi;
+            if (p == 0) b -= M(a, 0, j, 0) / (dx * dx);
+            if (p == mx - 1) b -= M(a, nx - 1, j, 0) / (dx * dx);
+            if (q == 0) b -= M(a, i, 0, 0) / (dy * dy);
+            if (q == my - 1) b -= M(a, i, ny - 1, 0) / (dy * dy);
+            B[k] = b;
+        }
+        __syncthreads();
+        // T1 = Sx B; B = (T1 Sy) ./ lam; T1 = Sx B; B = T1 Sy
+        for (int stage = 0; stage < 4; ++stage) {
+            const bool left = stage % 2 == 0;
+            const double* X = left ? B : T1;
+            double* Yv = left ? T1 : B;
+            for (long k = threadIdx.x; k < mm; k += blockDim.x) {
+                const int p = (int)(k / my), q = (int)(k % my);
+                double v = 0.0;
+                if (left)
+                    for (int t = 0; t < mx; ++t) v += Sx[(long)p * mx + t] * X[(long)t * my + q];
+                else
+                    for (int t = 0; t < my; ++t) v += X[(long)p * my + t] * Sy[(long)t * my + q];
+                if (stage == 1) v /= lam[k];
+                Yv[k] = v;
+            }
+            __syncthreads();
+        }
+    }
+    double sU = 0.0, sq = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const int i = c / ny, j = c % ny;
+        const double Uh = M(a, i, j, 0), q = M(a, i, j, 1);
+        const bool in = i > 0 && i < nx - 1 && j > 0 && j < ny - 1;
+        const double d = (P.sis && in) ? B[(long)(i - 1) * my + (j - 1)] - Uh : 0.0;
+        dU[a * n + c] = d;
+        const double Uc = Uh + d * P.cU[a];
+        Uout[a * n + c] = Uc;
+        sU += Uc;
+        sq += q + d * P.cq[a];
+    }
+    __shared__ double red[2][16];
+    for (int o = 16; o > 0; o >>= 1) {
+        sU += __shfl_xor_sync(0xffffffffu, sU, o);
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[0][threadIdx.x >> 5] = sU, red[1][threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0, v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[0][w], v += red[1][w];
+        rates[a] = P.sqm * u / n;
+        rates[2 + a] = P.sqm * v / n;
+    }
+}
+
 // y = a + s b over n values
 __global__ void k_mix_axpy(const double* __restrict__ a, double s, const double* __restrict__ b, long n,
                            double* __restrict__ y) {
@@ -376,16 +481,17 @@ __global__ void k_mix_axpy(const double* __restrict__ a, double s, const double*
 __global__ void __launch_bounds__(256) k_mix_correct(MixSisDev P, const double* __restrict__ hh,
                                                      double* __restrict__ h, const double* __restrict__ dU,
                                                      const double* __restrict__ feq, const double* __restrict__ vel) {
-    const int N = P.nv, H = N / 2, nq = N * H * H;
+    const int N = P.nv, H = N / 2, nq = N * (P.layout == 1 ? H : N) * H;
     const long n3 = (long)N * N * N;
     const long total = 2L * P.cells * nq;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
         const int q = (int)(t % nq);
         const long an = t / nq;
         const int a = (int)(an / P.cells);
-        const int i1 = q / (H * H), j2 = q / H % H, j3 = q % H;
-        const long vf = ((long)i1 * N + j2) * N + j3, off = an * n3 + q;
-        h[off] = hh[off] + 2.0 * P.r[a] * dU[an] * vel[j3] * feq[a * n3 + vf];
+        int i1, i2, i3;
+        orbit_point(q, N, P.layout, &i1, &i2, &i3);
+        const long vf = ((long)i1 * N + i2) * N + i3, off = an * n3 + q;
+        h[off] = hh[off] + 2.0 * P.r[a] * dU[an] * vel[i3] * feq[a * n3 + vf];
     }
 }
 
@@ -494,7 +600,9 @@ lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
         o.cq[a] = 2.0 * o.r[a] * sq;
     }
     // separable pass tables: columns (DFT index -> basis), rows (DFT index -> representative)
-    const int co[3] = {N, o.layout ? H : N, o.layout ? H : N};
+    // layout 1 folds v2 (even) and v3 (odd), layout 2 only v3 (odd)
+    const bool fold2 = o.layout == 1, fold3 = o.layout >= 1;
+    const int co[3] = {N, fold2 ? H : N, fold3 ? H : N};
     std::vector<std::vector<double2>> colC(3), rowC(3);
     for (int ax = 0; ax < 3; ++ax) {
         colC[ax].resize((size_t)co[ax] * N);
@@ -502,7 +610,7 @@ lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
         for (int j = 0; j < co[ax]; ++j)
             for (int a = 0; a < N; ++a) {
                 std::complex<double> z = std::polar(1.0, -2.0 * M_PI * ((long)a * j % N) / N);
-                if (o.layout && ax > 0) {
+                if ((ax == 1 && fold2) || (ax == 2 && fold3)) {
                     const std::complex<double> zr = std::polar(1.0, -2.0 * M_PI * ((long)a * (N - 1 - j) % N) / N);
                     z = ax == 1 ? z + zr : z - zr;  // even in v2, odd in v3
                 }
@@ -777,29 +885,53 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     if (!ctx || !pb || !out) return bad_arg(ctx, "null argument");
     lbe_status st = check_mixture(ctx, &pb->mix, pb->nv, pb->vmax, pb->M, pb->R);
     if (st != LBE_OK) return st;
-    if (pb->ns < 2 || pb->ns > 1000 || (pb->grid_kind != 0 && pb->grid_kind != 1))
-        return bad_arg(ctx, "mixture plates: 2 <= ns <= 1000, grid_kind 0 or 1");
+    const lbe_geometry& gm = pb->geom;
+    if (gm.dim == 1 ? (gm.ns < 2 || gm.ns > 1000 || (gm.grid_kind != 0 && gm.grid_kind != 1))
+                    : (gm.dim != 2 || gm.nx < 3 || gm.ny < 3 || gm.nx > 1024 || gm.ny > 1024 || !(gm.width > 0)))
+        return bad_arg(ctx, "mixture geometry: plates 2 <= ns <= 1000, grid_kind 0 or 1; ducts 3 <= nx, ny <= 1024, "
+                            "width > 0");
     if (!(pb->delta >= 0) || pb->max_iter < 1 || !(pb->eps >= 0) || (pb->scheme != LBE_CIS && pb->scheme != LBE_SIS))
-        return bad_arg(ctx, "mixture plates: delta >= 0, max_iter >= 1, eps >= 0, scheme CIS or SIS");
+        return bad_arg(ctx, "mixture: delta >= 0, max_iter >= 1, eps >= 0, scheme CIS or SIS");
     if (pb->precision != LBE_FP64 && pb->precision != LBE_BF16 && pb->precision != LBE_BF16_REFINED)
-        return bad_arg(ctx, "mixture plates: precision FP64, BF16 or BF16_REFINED");
+        return bad_arg(ctx, "mixture: precision FP64, BF16 or BF16_REFINED");
     cudaSetDevice(ctx->device);
     cudaStream_t s = ctx->stream;
-    MixOp* o = get_mixop(ctx, pb->mix, pb->nv, pb->vmax, pb->M, pb->R, 1, s, &st);
+    const int dim = gm.dim, layout = dim == 1 ? 1 : 2;
+    MixOp* o = get_mixop(ctx, pb->mix, pb->nv, pb->vmax, pb->M, pb->R, layout, s, &st);
     if (!o) return st;
     bool lo = pb->precision != LBE_FP64;  // operator on the tensor cores (BF16 hi / lo)
     if (lo && !o->tc && (st = mix_tc_build(ctx, o->L, 2 * o->nr, &o->tc, s)) != LBE_OK) return st;
     lbe_problem geo{};
-    geo.geom.dim = 1;
-    geo.geom.ns = pb->ns;
-    geo.geom.grid_kind = pb->grid_kind;
+    geo.geom = gm;
     SweepGeom g;
     build_sweep_geom(g, geo);
     const int n = g.cells, N = pb->nv;
     const long n3 = (long)N * N * N, per = (long)n * n3;
     std::vector<double> coef, geov;
-    for (auto* vv : {&g.fa, &g.fb, &g.fc, &g.ba, &g.bb, &g.bc}) coef.insert(coef.end(), vv->begin(), vv->end());
-    for (auto* vv : {&g.x, &g.fa, &g.fb, &g.fc, &g.trap}) geov.insert(geov.end(), vv->begin(), vv->end());
+    if (dim == 1) {
+        for (auto* vv : {&g.fa, &g.fb, &g.fc, &g.ba, &g.bb, &g.bc}) coef.insert(coef.end(), vv->begin(), vv->end());
+        for (auto* vv : {&g.x, &g.fa, &g.fb, &g.fc, &g.trap}) geov.insert(geov.end(), vv->begin(), vv->end());
+    } else {
+        for (auto* vv : {&g.xa, &g.xb, &g.xc, &g.ya, &g.yb, &g.yc}) coef.insert(coef.end(), vv->begin(), vv->end());
+        // DST-I of the interior (orthonormal, symmetric) and the Laplacian's eigenvalues
+        const int mx = gm.nx - 2, my = gm.ny - 2;
+        const double dx = gm.width / gm.nx, dy = 1.0 / gm.ny;
+        geov.resize((size_t)mx * mx + (size_t)my * my + (size_t)mx * my);
+        for (int i = 0; i < mx; ++i)
+            for (int k = 0; k < mx; ++k)
+                geov[(size_t)i * mx + k] = std::sqrt(2.0 / (mx + 1)) * std::sin(M_PI * (i + 1) * (k + 1) / (mx + 1));
+        double* sy = geov.data() + (size_t)mx * mx;
+        for (int i = 0; i < my; ++i)
+            for (int k = 0; k < my; ++k)
+                sy[(size_t)i * my + k] = std::sqrt(2.0 / (my + 1)) * std::sin(M_PI * (i + 1) * (k + 1) / (my + 1));
+        double* lm = sy + (size_t)my * my;
+        for (int p = 0; p < mx; ++p)
+            for (int q = 0; q < my; ++q) {
+                const double sp = std::sin(M_PI * (p + 1) / (2.0 * (mx + 1)));
+                const double sq = std::sin(M_PI * (q + 1) / (2.0 * (my + 1)));
+                lm[(size_t)p * my + q] = -4.0 * sp * sp / (dx * dx) - 4.0 * sq * sq / (dy * dy);
+            }
+    }
     MixSisDev P{};
     for (int a = 0; a < 2; ++a) {
         P.r[a] = o->r[a];
@@ -815,15 +947,22 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     P.nv = N;
     P.cells = n;
     P.sis = pb->scheme == LBE_SIS;
+    P.layout = layout;
+    MixDuctDev D{gm.nx, gm.ny, dim == 2 ? gm.width / gm.nx : 0.0, dim == 2 ? 1.0 / gm.ny : 0.0};
+    const int nq = N * (layout == 1 ? N / 2 : N) * (N / 2);
     SweepJobDev job{};
     job.cell_off = 0;
     job.ncell = n;
+    job.nx = dim == 2 ? gm.nx : 0;
+    job.ny = dim == 2 ? gm.ny : 0;
     job.coef_off = 0;
     job.forcing = LBE_POISEUILLE;
     job.delta = pb->delta;
     // device workspace
     const size_t b_state = sizeof(double) * 2 * per;
-    const size_t b_small = sizeof(double) * (10 * n + 4 * n + 8) + sizeof(double) * (coef.size() + geov.size());
+    const size_t n_work = dim == 2 ? 4 * (size_t)(gm.nx - 2) * (gm.ny - 2) : 0;
+    const size_t b_small = sizeof(double) * (2 * kMom * n + 4 * n + 8 + n_work) +
+                           sizeof(double) * (coef.size() + geov.size());
     void *d_h = nullptr, *d_hh = nullptr, *d_lp = nullptr, *d_small = nullptr, *d_job = nullptr;
     auto take = [&](void** p, size_t bytes) {
         if (st == LBE_OK) st = dev_alloc(ctx, p, bytes);
@@ -844,21 +983,25 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     double* h = (double*)d_h;
     double* hh = (double*)d_hh;
     double* lp = (double*)d_lp;
-    double* mom = (double*)d_small;           // [2][n][5]
-    double* dU = mom + 10 * n;                // [2][n]
+    double* mom = (double*)d_small;           // [2][n][kMom]
+    double* dU = mom + 2 * kMom * n;          // [2][n]
     double* Uc = dU + 2 * n;                  // [2][n]
     double* rates = Uc + 2 * n;               // [8]
-    double* dcoef = rates + 8;
-    double* dgeo = dcoef + coef.size();
+    double* dwork = rates + 8;                // ducts: [2][2][mx my]
+    double* dcoef = dwork + n_work;
+    double* dgeo = dcoef + coef.size();       // plates: x, fa, fb, fc, trap; ducts: Sx, Sy, lam
+    const double* dSx = dgeo;
+    const double* dSy = dim == 2 ? dgeo + (size_t)(gm.nx - 2) * (gm.nx - 2) : nullptr;
+    const double* dlam = dim == 2 ? dSy + (size_t)(gm.ny - 2) * (gm.ny - 2) : nullptr;
     double hr[4] = {0, 0, 0, 0}, old[4] = {0, 0, 0, 0};
     int it = 0, it64 = 0;
     bool conv = false, bad = false;
-    static std::once_flag march_attr;  // the march stages up to 15 x 1001 doubles
+    static std::once_flag march_attr;  // the march stages up to 23 x 1001 doubles
     std::call_once(march_attr, [] {
         cudaFuncSetAttribute(k_mix_march, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(15 * kMarchMax * sizeof(double)));
+                             (int)((2 * kMom + 5) * kMarchMax * sizeof(double)));
     });
-    const size_t march_smem = 15 * (size_t)n * sizeof(double);
+    const size_t march_smem = (2 * kMom + 5) * (size_t)n * sizeof(double);
     // one iteration hin -> hout (hout may be hin) with the operator in FP64 or on the tensor
     // cores; homog: the source-free iteration (no S_a in the sweep, no x1 in the march); r
     // receives the flow rates of hout
@@ -867,13 +1010,16 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
                           : mix_gemm(ctx, *o, hin, hin + per, n3, n, pb->delta, lp, lp + per, s);
         if (e != LBE_OK) return e;
         for (int a = 0; a < 2; ++a)
-            launch_sweep<double>(homog ? o->tab0[a] : o->tab[a], 1, 1, (int)coef.size(), lp + a * per, hh + a * per,
-                                 (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
+            launch_sweep<double>(homog ? o->tab0[a] : o->tab[a], dim, 1, (int)coef.size(), lp + a * per,
+                                 hh + a * per, (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
         MixSisDev Q = P;
         Q.src = homog ? 0 : 1;
         k_mix_moments<<<dim3(n, 2), 256, 0, s>>>(Q, hh, hin, lp, o->nu, o->vel, mom);
-        k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
-        k_mix_correct<<<grid_for(2L * n * n3 / 4), 256, 0, s>>>(Q, hh, hout, dU, o->feq, o->vel);
+        if (dim == 1)
+            k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
+        else
+            k_mix_poisson2d<<<2, 512, 0, s>>>(Q, D, mom, dSx, dSy, dlam, dwork, dU, Uc, rates);
+        k_mix_correct<<<grid_for(2L * n * nq), 256, 0, s>>>(Q, hh, hout, dU, o->feq, o->vel);
         g_launches += 3;
         g_levals += n;
         cudaMemcpyAsync(r, rates, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -970,7 +1116,10 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
             MixSisDev Q = P;
             Q.sis = 0;
             k_mix_moments<<<dim3(n, 2), 256, 0, s>>>(Q, h, h, lp, o->nu, o->vel, mom);
-            k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
+            if (dim == 1)
+                k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
+            else
+                k_mix_poisson2d<<<2, 512, 0, s>>>(Q, D, mom, dSx, dSy, dlam, dwork, dU, Uc, rates);
             cudaMemcpyAsync(hr, rates, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
             g_launches += 2;
             st = cuda_status(ctx, cudaStreamSynchronize(s), "mixture flow rates");
@@ -981,8 +1130,8 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
         g_d2h += sizeof(double) * 2 * n;
     }
     if (st == LBE_OK && h_out) {
-        // the orbit layout back to the full grid: even in v2, odd in v3
-        const int H = N / 2, nq = N * H * H;
+        // the orbit layout back to the full grid: odd in v3, and for plates even in v2
+        const int H = N / 2, E2 = layout == 1 ? H : N;
         std::vector<double> q(2 * (size_t)n * nq);
         for (int a = 0; a < 2; ++a)
             for (int c = 0; c < n; ++c)
@@ -993,8 +1142,8 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
             for (int i1 = 0; i1 < N; ++i1)
                 for (int i2 = 0; i2 < N; ++i2)
                     for (int i3 = 0; i3 < N; ++i3) {
-                        const int j2 = i2 < H ? i2 : N - 1 - i2, j3 = i3 < H ? i3 : N - 1 - i3;
-                        const double x = q[ac * nq + ((size_t)i1 * H + j2) * H + j3];
+                        const int j2 = (layout == 2 || i2 < H) ? i2 : N - 1 - i2, j3 = i3 < H ? i3 : N - 1 - i3;
+                        const double x = q[ac * nq + ((size_t)i1 * E2 + j2) * H + j3];
                         h_out[ac * n3 + ((size_t)i1 * N + i2) * N + i3] = i3 < H ? x : -x;
                     }
     }

@@ -40,7 +40,7 @@ class Mixture(C.Structure):
 
 
 class MixProblem(C.Structure):
-    _fields_ = [("mix", Mixture), ("ns", C.c_int), ("grid_kind", C.c_int), ("delta", C.c_double),
+    _fields_ = [("mix", Mixture), ("geom", Geometry), ("delta", C.c_double),
                 ("N_A", C.c_double), ("N_B", C.c_double), ("nv", C.c_int), ("vmax", C.c_double),
                 ("M", C.c_int), ("R", C.c_double), ("scheme", C.c_int), ("eps", C.c_double),
                 ("max_iter", C.c_int), ("precision", C.c_int)]
@@ -53,9 +53,15 @@ class MixResult(C.Structure):
 
 
 def mix_problem(mass_ratio, diam_ratio, chi_A, delta=1.0, ns=20, grid_kind=0, N_A=0.0, N_B=0.0, nv=16,
-                vmax=6.0, M=16, R=4.5, scheme=SIS, eps=1e-8, max_iter=500, precision=FP64):
-    return MixProblem(Mixture(mass_ratio, diam_ratio, chi_A), ns, grid_kind, delta, N_A, N_B, nv, vmax, M, R,
+                vmax=6.0, M=16, R=4.5, scheme=SIS, eps=1e-8, max_iter=500, precision=FP64, dim=1, nx=0, ny=0,
+                width=1.0):
+    geom = Geometry(dim, ns if dim == 1 else 0, grid_kind if dim == 1 else 0, nx, ny, width)
+    return MixProblem(Mixture(mass_ratio, diam_ratio, chi_A), geom, delta, N_A, N_B, nv, vmax, M, R,
                       scheme, eps, max_iter, precision)
+
+
+def mix_cells(pb):
+    return pb.geom.ns + 1 if pb.geom.dim == 1 else pb.geom.nx * pb.geom.ny
 
 
 class Stats(C.Structure):
@@ -235,7 +241,7 @@ class Context:
         return self.check(st)
 
     def mix_solve(self, pb, want_h=False, want_U=True):
-        n = pb.ns + 1
+        n = mix_cells(pb)
         U = np.zeros(2 * n) if want_U else None
         h = np.zeros(2 * n * pb.nv ** 3) if want_h else None
         res = MixResult()

@@ -167,3 +167,91 @@ def test_mixture_tensor_core_solves_reach_fp64(ctx, delta):
     assert np.max(np.abs(c - a)) < 1e-4 * max(abs(a[0]), abs(a[1])), (a, c)
     assert r64.fp64_iters == r64.iters and rb.fp64_iters == 0
     assert 0 < rr.fp64_iters <= r64.iters // 4, (rr.fp64_iters, r64.iters)
+
+
+@pytest.mark.parametrize("scheme", ["sis", "cis"])
+def test_mixture_duct_solve_matches_oracle(ctx, oracle8, scheme):
+    """Ducts: the 2D sweeps, the two Poisson solves (DST-I) and the duct orbit layout of the
+    operator, against the oracle's dense-LU Poisson solves on the full grid."""
+    from paper_1612_04488_gb300 import lbe
+    F = oracle8
+    iters = 5
+    kw = dict(delta=0.8, nv=8, vmax=5.0, M=8, R=3.75, eps=0.0, max_iter=iters)
+    run = mx.MixRun(mx.MixProblem(NE_AR[0], NE_AR[1], 0.5, scheme=scheme, dim=2, nx=7, ny=5, width=1.4, **kw), F=F)
+    for _ in range(iters):
+        rates = run.step()
+    pb = lbe.mix_problem(NE_AR[0], NE_AR[1], 0.5, scheme=lbe.SIS if scheme == "sis" else lbe.CIS, dim=2, nx=7, ny=5,
+                         width=1.4, **kw)
+    res, U, h = ctx.mix_solve(pb, want_h=True)
+    assert res.iters == iters and res.status == lbe.NOT_CONVERGED
+    got = np.array([res.M_A, res.M_B, res.Q_A, res.Q_B])
+    assert np.max(np.abs(got - rates) / np.abs(rates)) < 1e-10
+    for a in range(2):
+        ref_U = run.U[a].reshape(-1)
+        assert np.max(np.abs(U[a] - ref_U)) < 1e-10 * np.max(np.abs(ref_U))
+        ref_h = run.h[a].reshape((-1,) + run.h[a].shape[2:])
+        assert np.max(np.abs(h[a] - ref_h)) < 1e-10 * np.max(np.abs(ref_h))
+
+
+def test_mixture_duct_refined_reaches_fp64(ctx):
+    from paper_1612_04488_gb300 import lbe
+    kw = dict(delta=2.0, nv=16, vmax=5.0, M=16, R=3.75, max_iter=300, dim=2, nx=20, ny=10, width=2.0, eps=1e-10)
+    r64, _, _ = ctx.mix_solve(lbe.mix_problem(*NE_AR, 0.5, **kw), want_U=False)
+    rr, _, _ = ctx.mix_solve(lbe.mix_problem(*NE_AR, 0.5, precision=lbe.BF16_REFINED, **kw), want_U=False)
+    assert r64.status == rr.status == lbe.OK
+    a = np.array([r64.M_A, r64.M_B, r64.Q_A, r64.Q_B])
+    b = np.array([rr.M_A, rr.M_B, rr.Q_A, rr.Q_B])
+    assert np.max(np.abs(b - a) / np.abs(a)) < 1e-8, (a, b)
+    assert 0 < rr.fp64_iters <= r64.iters // 4, (rr.fp64_iters, r64.iters)
+
+
+GOLDEN5 = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden", "table5_ne_ar_duct.txt")
+
+
+def _table5():
+    rows = {}
+    for line in open(GOLDEN5):
+        if line.strip() and not line.startswith("#"):
+            x = [float(t) for t in line.split()]
+            rows[(x[0], x[1])] = x[3:]
+    return rows
+
+
+def _duct(ctx, delta, aspect, nx, ny):
+    from paper_1612_04488_gb300 import lbe
+    pb = lbe.mix_problem(*NE_AR, 0.5, delta=delta, nv=24, vmax=5.0, M=32, R=3.75, eps=1e-7, max_iter=400,
+                         precision=lbe.BF16_REFINED, dim=2, nx=nx, ny=ny, width=aspect)
+    r, _, _ = ctx.mix_solve(pb, want_U=False)
+    assert r.status == lbe.OK
+    return np.array([r.M_A, r.M_B, -2.0 * r.Q_A, -2.0 * r.Q_B])
+
+
+def test_table5_duct_rows(ctx):
+    """Table 5 (square and 2:1 ducts) on 24^3 with 40 x 40 and 64 x 32 cells: molecular flow
+    rates within 4 % at delta = 1 (measured -3 %) and 6 % at delta = 10 (measured +4 %, the
+    offset discussed in test_mixture_to_single_species_ratio_is_geometry_independent)."""
+    T = _table5()
+    for aspect, (nx, ny) in ((1.0, (40, 40)), (2.0, (64, 32))):
+        for delta, tol in ((1.0, 0.04), (10.0, 0.06)):
+            got = _duct(ctx, delta, aspect, nx, ny)
+            rel = np.abs(got[:2] / np.array(T[(aspect, delta)][:2]) - 1.0)
+            assert np.all(rel < tol), (aspect, delta, got, T[(aspect, delta)])
+
+
+def test_mixture_to_single_species_ratio_is_geometry_independent(ctx):
+    """Near continuum (delta = 10) the flow rate of each species over the single-species flow
+    rate (same delta) is the same between plates and the square duct, to 1.5 %: the slip of
+    each species relative to the gas does not depend on the cross section.  (Tables 4 / 1 give
+    1.011 / 0.997 for Ne / Ar between plates; Tables 5 / 2 give 0.978 / 0.947 in the square duct.)"""
+    from paper_1612_04488_gb300 import lbe
+    sp_plate = ctx.solve(lbe.problem(dim=1, ns=100, grid_kind=1, delta=10.0, nv=24, vmax=5.0, M=32, R=3.75,
+                                     precision=lbe.FP64, eps=1e-8, max_iter=400))[0].mass_flow
+    sp_duct = ctx.solve(lbe.problem(dim=2, nx=40, ny=40, width=1.0, delta=10.0, nv=24, vmax=5.0, M=32, R=3.75,
+                                    precision=lbe.BF16_REFINED, eps=1e-7, max_iter=400))[0].mass_flow
+    mp, _, _ = ctx.mix_solve(lbe.mix_problem(*NE_AR, 0.5, delta=10.0, ns=100, grid_kind=1, nv=24, vmax=5.0, M=32,
+                                             R=3.75, eps=1e-8, max_iter=400, precision=lbe.BF16_REFINED),
+                             want_U=False)
+    md = _duct(ctx, 10.0, 1.0, 40, 40)
+    plate = np.array([mp.M_A, mp.M_B]) / sp_plate
+    duct = md[:2] / sp_duct
+    assert np.all(np.abs(duct / plate - 1.0) < 0.015), (plate, duct)

@@ -159,3 +159,14 @@ def test_M9_sis_and_cis_reach_the_same_solution(F12):
     assert np.max(np.abs(sis.rates - cis.rates) / np.abs(cis.rates)) < 1.5e-2
     assert sis.iters < cis.iters
     assert sis.rates[0] > sis.rates[1] > 0.0        # the lighter species flows faster
+
+
+def test_M8_2d_identical_species_cis_is_the_single_species_duct_cis():
+    kw = dict(delta=0.7, nv=8, vmax=6.0, M=8, scheme="cis")
+    mr = mx.MixRun(mx.MixProblem(1.0, 1.0, 0.3, dim=2, nx=5, ny=4, width=1.5, **kw))
+    sp = solver.Run(solver.Problem(dim=2, nx=5, ny=4, width=1.5, **kw))
+    for _ in range(3):
+        mr.step()
+        sp.step()
+    for a, chi in ((0, 0.3), (1, 0.7)):
+        assert np.max(np.abs(mr.h[a] - chi * sp.h)) < 1e-13 * np.max(np.abs(sp.h))
