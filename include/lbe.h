@@ -361,8 +361,9 @@ typedef struct {
 } lbe_mixture;
 
 /* Poiseuille flow of a mixture (Sec. 4; S_a = v3 f_a,eq, X_P = -1) between plates (geom.dim = 1:
- * the half channel, ns sections, grid_kind, diffuse wall, symmetry plane) or through a
- * rectangular duct (geom.dim = 2: nx x ny cells of [0, width] x [0, 1], diffuse walls). */
+ * the half channel, 2 <= ns <= 1000 sections, grid_kind, diffuse wall, symmetry plane) or through
+ * a rectangular duct (geom.dim = 2: 3 <= nx, ny <= 256 cells of [0, width] x [0, 1], diffuse
+ * walls; each species' Poisson solve runs in one thread block). */
 typedef struct {
     lbe_mixture mix;
     lbe_geometry geom;

@@ -752,6 +752,7 @@ lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
 MixOp* get_mixop(Ctx* c, const lbe_mixture& m, int nv, double vmax, int M, double R, int layout, cudaStream_t s,
                  lbe_status* st) {
     const std::string key = mix_key(m, nv, vmax, M, R, layout);
+    std::lock_guard<std::mutex> lk(c->tables_mu);
     auto it = c->mix_ops.find(key);
     if (it != c->mix_ops.end()) return it->second;
     MixOp* o = new MixOp();
@@ -887,8 +888,8 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     if (st != LBE_OK) return st;
     const lbe_geometry& gm = pb->geom;
     if (gm.dim == 1 ? (gm.ns < 2 || gm.ns > 1000 || (gm.grid_kind != 0 && gm.grid_kind != 1))
-                    : (gm.dim != 2 || gm.nx < 3 || gm.ny < 3 || gm.nx > 1024 || gm.ny > 1024 || !(gm.width > 0)))
-        return bad_arg(ctx, "mixture geometry: plates 2 <= ns <= 1000, grid_kind 0 or 1; ducts 3 <= nx, ny <= 1024, "
+                    : (gm.dim != 2 || gm.nx < 3 || gm.ny < 3 || gm.nx > 256 || gm.ny > 256 || !(gm.width > 0)))
+        return bad_arg(ctx, "mixture geometry: plates 2 <= ns <= 1000, grid_kind 0 or 1; ducts 3 <= nx, ny <= 256, "
                             "width > 0");
     if (!(pb->delta >= 0) || pb->max_iter < 1 || !(pb->eps >= 0) || (pb->scheme != LBE_CIS && pb->scheme != LBE_SIS))
         return bad_arg(ctx, "mixture: delta >= 0, max_iter >= 1, eps >= 0, scheme CIS or SIS");
