@@ -280,7 +280,23 @@ def mixture_measure(lbe, torch, device, steps, warmup, nv=24, M=32, deltas=(1.0,
     t0 = time.perf_counter()
     ctx.mix_info(pbs[0].mix, nv, 5.0, M, 3.75)
     build_s = time.perf_counter() - t0
-    # BF16 hi / lo operator on the tensor cores, then FP64 iterations to the same stopping test
+    # the operator's GEMM in double-float on the FP32 pipes (FP64-class), same stopping test
+    fpbs = [lbe.mix_problem(MIX_NE_AR[0], MIX_NE_AR[1], 0.5, delta=d, ns=100, grid_kind=1, nv=nv, vmax=5.0, M=M,
+                            R=3.75, eps=1e-8, max_iter=400, precision=lbe.DF32) for d in deltas]
+    for pb in fpbs:
+        ctx.mix_solve(pb, want_U=False)
+    fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fa.record(stream)
+    fres = [ctx.mix_solve(pb, want_U=False)[0] for pb in fpbs]
+    fb.record(stream)
+    fb.synchronize()
+    lbe.set_kernel_timing(True)
+    q0 = lbe.stats()
+    ctx.mix_solve(fpbs[-1], want_U=False)
+    q1 = lbe.stats()
+    lbe.set_kernel_timing(False)
+    ms_df = (q1["dense_gemm_ms"] - q0["dense_gemm_ms"]) / max(q1["dense_gemm_timed"] - q0["dense_gemm_timed"], 1)
+    # BF16 hi / lo operator on the tensor cores, then FP64-class iterations to the same stopping test
     rpbs = [lbe.mix_problem(MIX_NE_AR[0], MIX_NE_AR[1], 0.5, delta=d, ns=100, grid_kind=1, nv=nv, vmax=5.0, M=M,
                             R=3.75, eps=1e-8, max_iter=400, precision=lbe.BF16_REFINED) for d in deltas]
     for _ in range(warmup):
@@ -341,14 +357,21 @@ def mixture_measure(lbe, torch, device, steps, warmup, nv=24, M=32, deltas=(1.0,
     nsolve = len(pbs) * steps
     rel = max(abs(x / y - 1.0) for r, q in zip(rres, res)
               for x, y in ((r.M_A, q.M_A), (r.M_B, q.M_B), (r.Q_A, q.Q_A), (r.Q_B, q.Q_B)))
+    frel = max(abs(x / y - 1.0) for r, q in zip(fres, res)
+               for x, y in ((r.M_A, q.M_A), (r.M_B, q.M_B), (r.Q_A, q.Q_A), (r.Q_B, q.Q_B)))
+    df32 = {"solves_per_s": len(fpbs) / (fa.elapsed_time(fb) / 1000.0), "max_rel_err_vs_fp64": frel,
+            "gemm_ms_per_launch": ms_df, "gemm_fp64_equivalent_tflops": flops / (ms_df / 1000.0) / 1e12,
+            "gemm_speedup_vs_fp64": ms_gemm / ms_df,
+            "what": "the operator's GEMM in double-float arithmetic on the FP32 pipes (TwoProduct by FMA, "
+                    "TwoSum accumulation), everything else FP64"}
     refined = {"solves_per_s": nsolve / (ms_ref / 1000.0), "ms_per_step": ms_ref / steps,
                "iters": [r.iters for r in rres], "fp64_iters": [r.fp64_iters for r in rres],
                "max_rel_err_vs_fp64": rel,
                "what": "tcgen05 BF16 hi/lo operator (float accumulation) down to its floor, then defect "
-                       "correction: FP64 iterations (the same 1e-8 stopping test) whose errors are solved "
-                       "for by the source-free iteration on the tensor cores"}
+                       "correction: FP64-class (double-float GEMM) iterations, the same 1e-8 stopping test, "
+                       "whose errors are solved for by the source-free iteration on the tensor cores"}
     out = {"solves_per_s": nsolve / (ms / 1000.0), "ms_per_step": ms / steps, "build_s": build_s,
-           "refined": refined, "duct": duct, "fp64_iters": [r.iters for r in res],
+           "refined": refined, "df32": df32, "duct": duct, "fp64_iters": [r.iters for r in res],
            "e2e": {"value": nsolve / wall, "unit": "solves/s",
                    "h2d_bytes_per_step": int((s1["h2d_bytes"] - s0["h2d_bytes"]) / steps),
                    "d2h_bytes_per_step": int((s1["d2h_bytes"] - s0["d2h_bytes"]) / steps)},
@@ -379,7 +402,8 @@ def run_mixture(args):
             "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": m["config"], "roofline": m["roofline"],
-            "table4": m["table4"], "build_s": m["build_s"], "refined": m["refined"], "duct": m["duct"],
+            "table4": m["table4"], "build_s": m["build_s"], "refined": m["refined"], "df32": m["df32"],
+            "duct": m["duct"],
             "e2e": m["e2e"],
             "clocks": clk.summary(),
             "gpu_launches": m["gpu_launches"]}
@@ -782,7 +806,7 @@ def run_ours(args):
                              "status": dres[-1].status}
         mx = mixture_measure(lbe, torch, local, 1, 1)
         line["mixture"] = {k: mx[k] for k in ("solves_per_s", "config", "roofline", "table4", "build_s", "refined",
-                                              "duct")}
+                                              "df32", "duct")}
         sctx = lbe.Context(local)
         line["serving"] = serve_stream(sctx, lbe, prec, args.eps, args.requests)
         line["latency_ms"] = dict(line["serving"]["latency_ms"], workload=line["serving"]["workload"])

@@ -376,14 +376,17 @@ typedef struct {
     lbe_scheme scheme;
     double eps;          /* stop when all four flow rates change by < eps relative; 0 = never   */
     int max_iter;        /* cap on all iterations                                               */
-    lbe_precision precision; /* LBE_FP64; LBE_BF16: the operator as a tcgen05 BF16 hi/lo GEMM with
+    lbe_precision precision; /* LBE_FP64; LBE_DF32: the operator's GEMM in double-float arithmetic
+                          * on the FP32 pipes (about 1e-13 of the scale from FP64), the rest FP64;
+                          * LBE_BF16: the operator as a tcgen05 BF16 hi/lo GEMM with
                           * float accumulation (everything else FP64), stopping when the four
                           * changes fall below eps times the larger molecular flow rate;
                           * LBE_BF16_REFINED: such iterations down to their floor (changes below
                           * 1e-5 of that scale, or no longer shrinking for three iterations),
-                          * then defect correction: an FP64 iteration h' = Phi(h) (its change is
-                          * the FP64 stopping test), and its error e = G (e + h' - h) solved by
-                          * the source-free iteration on the tensor cores; h = h' + e           */
+                          * then defect correction: an FP64-class (LBE_DF32) iteration h' = Phi(h)
+                          * (its change is the FP64 stopping test), and its error
+                          * e = G (e + h' - h) solved by the source-free iteration on the tensor
+                          * cores; h = h' + e                                                   */
 } lbe_mix_problem;
 
 typedef struct {

@@ -29,6 +29,7 @@
 #include <string>
 #include <vector>
 
+#include "common.cuh"
 #include "lbe_internal.h"
 #include "sweep.h"
 
@@ -50,6 +51,7 @@ struct MixOp {
     std::vector<double> nu_h; // host copy of nu
     size_t bytes = 0;
     DevTables tab[2];         // per species: the transport sweep's tables (vel, f_a,eq, nu_a)
+    float2* Ldf = nullptr;    // L as double-float (hi, lo) pairs, built at first use
     double* part = nullptr;   // split-K partial sums of the GEMM (grow-only)
     size_t part_bytes = 0;
     MixTc* tc = nullptr;      // the same operator in BF16 hi / lo on the tensor cores (first use)
@@ -246,6 +248,88 @@ __global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, 
             const int gc = cell0 + tx * 4 + q;
             if (gc < cells) y[gc * cs + j] = scale * acc[i][q];
         }
+    }
+}
+
+// The same GEMM in double-float arithmetic on the FP32 pipes: L as (hi, lo) float pairs, h split
+// on load, each product formed exactly by FMA (TwoProduct, cross terms added) and accumulated
+// by TwoSum; the pairs are renormalised after every K slice of the tile and widened to double at
+// the end (about 1e-13 of the scale, against the FP64 kernel's rounding).
+__global__ void __launch_bounds__(256) k_mix_gemm_df(const float2* __restrict__ L, int nr,
+                                                     const double* __restrict__ hA, const double* __restrict__ hB,
+                                                     long cs, int cells, double scale, double* __restrict__ yA,
+                                                     double* __restrict__ yB, int kc, double* __restrict__ part) {
+    __shared__ float2 As[kKT][kMT + 1];
+    __shared__ float2 Bs[kKT][kNT + 1];
+    const int rows = 2 * nr, K = 2 * nr;
+    const int row0 = blockIdx.x * kMT, cell0 = blockIdx.y * kNT;
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    const int t = threadIdx.x, ty = t / 16, tx = t % 16;
+    dfloat acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = dfloat(0.f, 0.f);
+    for (int k0 = kb; k0 < ke; k0 += kKT) {
+        {
+            const int r = t / 4, kq = (t % 4) * 4;
+            const int gr = row0 + r;
+            for (int q = 0; q < 4; ++q) {
+                const int gk = k0 + kq + q;
+                As[kq + q][r] = (gr < rows && gk < ke) ? L[(long)gr * K + gk] : make_float2(0.f, 0.f);
+            }
+        }
+        {
+            const int cc = t / 4, kq = (t % 4) * 4;
+            const int gc = cell0 + cc;
+            for (int q = 0; q < 4; ++q) {
+                const int gk = k0 + kq + q;
+                double v = 0.0;
+                if (gc < cells && gk < ke) v = gk < nr ? hA[gc * cs + gk] : hB[gc * cs + gk - nr];
+                const dfloat d(v);
+                Bs[kq + q][cc] = make_float2(d.hi, d.lo);
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < kKT; ++k) {
+            dfloat a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = dfloat(As[k][ty * 4 + i].x, As[k][ty * 4 + i].y);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = dfloat(Bs[k][tx * 4 + j].x, Bs[k][tx * 4 + j].y);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = df_fast2sum(acc[i][j].hi, acc[i][j].lo);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gr = row0 + ty * 4 + i;
+        if (gr >= rows) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gc = cell0 + tx * 4 + q;
+            if (gc >= cells) continue;
+            const double v = (double)acc[i][q];
+            if (part)
+                part[((long)blockIdx.z * cells + gc) * rows + gr] = v;
+            else
+                (gr < nr ? yA : yB)[gc * cs + (gr < nr ? gr : gr - nr)] = scale * v;
+        }
+    }
+}
+
+__global__ void k_mix_to_df(const double* __restrict__ L, long n, float2* __restrict__ out) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+        const dfloat d(L[t]);
+        out[t] = make_float2(d.hi, d.lo);
     }
 }
 
@@ -526,6 +610,7 @@ void free_mixop(Ctx* c, MixOp* o) {
     if (o->feq) dev_free(c, o->feq, sizeof(double) * 2 * n3);
     if (o->vel) dev_free(c, o->vel, sizeof(double) * o->nv);
     if (o->part) dev_free(c, o->part, o->part_bytes);
+    if (o->Ldf) dev_free(c, o->Ldf, sizeof(float2) * 4 * (size_t)o->nr * o->nr);
     if (o->tc) mix_tc_release(c, o->tc);
     if (o->zero) dev_free(c, o->zero, sizeof(double) * n3);
     delete o;
@@ -793,7 +878,14 @@ int mix_split(long tiles, int K) {
 }
 
 lbe_status mix_gemm(Ctx* c, MixOp& o, const double* hA, const double* hB, long cs, int cells, double scale,
-                    double* yA, double* yB, cudaStream_t s) {
+                    double* yA, double* yB, cudaStream_t s, bool df = false) {
+    if (df && !o.Ldf) {
+        const long nn = 4L * o.nr * o.nr;
+        lbe_status st = dev_alloc(c, (void**)&o.Ldf, sizeof(float2) * nn);
+        if (st != LBE_OK) return st;
+        k_mix_to_df<<<grid_for(nn), 256, 0, s>>>(o.L, nn, o.Ldf);
+        g_launches += 1;
+    }
     const int K = 2 * o.nr;
     dim3 g((2 * o.nr + kMT - 1) / kMT, (cells + kNT - 1) / kNT);
     int S = mix_split((long)g.x * g.y, K);
@@ -813,7 +905,10 @@ lbe_status mix_gemm(Ctx* c, MixOp& o, const double* hA, const double* hB, long c
     const bool timed = g_time_kernels.load() != 0 && cudaEventCreate(&ev[0]) == cudaSuccess &&
                        cudaEventCreate(&ev[1]) == cudaSuccess;
     if (timed) cudaEventRecord(ev[0], s);
-    k_mix_gemm<<<g, 256, 0, s>>>(o.L, o.nr, hA, hB, cs, cells, scale, yA, yB, kc, S > 1 ? o.part : nullptr);
+    if (df)
+        k_mix_gemm_df<<<g, 256, 0, s>>>(o.Ldf, o.nr, hA, hB, cs, cells, scale, yA, yB, kc, S > 1 ? o.part : nullptr);
+    else
+        k_mix_gemm<<<g, 256, 0, s>>>(o.L, o.nr, hA, hB, cs, cells, scale, yA, yB, kc, S > 1 ? o.part : nullptr);
     g_launches += 1;
     if (S > 1) {
         k_mix_reduce<<<grid_for((long)K * cells), 256, 0, s>>>(o.part, S, o.nr, cells, cs, scale, yA, yB);
@@ -893,14 +988,17 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
                             "width > 0");
     if (!(pb->delta >= 0) || pb->max_iter < 1 || !(pb->eps >= 0) || (pb->scheme != LBE_CIS && pb->scheme != LBE_SIS))
         return bad_arg(ctx, "mixture: delta >= 0, max_iter >= 1, eps >= 0, scheme CIS or SIS");
-    if (pb->precision != LBE_FP64 && pb->precision != LBE_BF16 && pb->precision != LBE_BF16_REFINED)
-        return bad_arg(ctx, "mixture: precision FP64, BF16 or BF16_REFINED");
+    if (pb->precision != LBE_FP64 && pb->precision != LBE_DF32 && pb->precision != LBE_BF16 &&
+        pb->precision != LBE_BF16_REFINED)
+        return bad_arg(ctx, "mixture: precision FP64, DF32, BF16 or BF16_REFINED");
     cudaSetDevice(ctx->device);
     cudaStream_t s = ctx->stream;
     const int dim = gm.dim, layout = dim == 1 ? 1 : 2;
     MixOp* o = get_mixop(ctx, pb->mix, pb->nv, pb->vmax, pb->M, pb->R, layout, s, &st);
     if (!o) return st;
-    bool lo = pb->precision != LBE_FP64;  // operator on the tensor cores (BF16 hi / lo)
+    // operator on the tensor cores (BF16 hi / lo); the FP64-class GEMM in double-float
+    bool lo = pb->precision == LBE_BF16 || pb->precision == LBE_BF16_REFINED;
+    const bool dfg = pb->precision == LBE_DF32 || pb->precision == LBE_BF16_REFINED;
     if (lo && !o->tc && (st = mix_tc_build(ctx, o->L, 2 * o->nr, &o->tc, s)) != LBE_OK) return st;
     lbe_problem geo{};
     geo.geom = gm;
@@ -1008,7 +1106,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     // receives the flow rates of hout
     auto step = [&](const double* hin, double* hout, bool tc, bool homog, double* r) -> lbe_status {
         lbe_status e = tc ? mix_tc_apply(ctx, o->tc, n, hin, hin + per, n3, o->nr, pb->delta, lp, lp + per, s)
-                          : mix_gemm(ctx, *o, hin, hin + per, n3, n, pb->delta, lp, lp + per, s);
+                          : mix_gemm(ctx, *o, hin, hin + per, n3, n, pb->delta, lp, lp + per, s, dfg);
         if (e != LBE_OK) return e;
         for (int a = 0; a < 2; ++a)
             launch_sweep<double>(homog ? o->tab0[a] : o->tab[a], dim, 1, (int)coef.size(), lp + a * per,

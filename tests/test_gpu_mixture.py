@@ -72,8 +72,10 @@ def test_mixture_tables_match_oracle(ctx, oracle8):
         assert np.max(np.abs(nu[a] - F.nu[a])) < 1e-13 * np.max(F.nu[a])
 
 
-@pytest.mark.parametrize("scheme", ["sis", "cis"])
-def test_mixture_solve_matches_oracle(ctx, oracle8, scheme):
+@pytest.mark.parametrize("scheme,prec", [("sis", "fp64"), ("cis", "fp64"), ("sis", "df32")])
+def test_mixture_solve_matches_oracle(ctx, oracle8, scheme, prec):
+    """FP64 and double-float (the operator's GEMM on the FP32 pipes) plate solves, fixed
+    iterations, against the oracle."""
     from paper_1612_04488_gb300 import lbe
     F = oracle8
     iters = 6
@@ -81,7 +83,8 @@ def test_mixture_solve_matches_oracle(ctx, oracle8, scheme):
     run = mx.MixRun(mx.MixProblem(NE_AR[0], NE_AR[1], 0.5, scheme=scheme, **kw), F=F)
     for _ in range(iters):
         rates = run.step()
-    pb = lbe.mix_problem(NE_AR[0], NE_AR[1], 0.5, scheme=lbe.SIS if scheme == "sis" else lbe.CIS, **kw)
+    pb = lbe.mix_problem(NE_AR[0], NE_AR[1], 0.5, scheme=lbe.SIS if scheme == "sis" else lbe.CIS,
+                         precision=lbe.FP64 if prec == "fp64" else lbe.DF32, **kw)
     res, U, h = ctx.mix_solve(pb, want_h=True)
     assert res.iters == iters and res.status == lbe.NOT_CONVERGED
     got = np.array([res.M_A, res.M_B, res.Q_A, res.Q_B])
