@@ -1771,13 +1771,14 @@ __global__ void k_mix_gather(const double* __restrict__ hA, const double* __rest
 }
 
 // y_a[c cs + j] = scale Y[c mrows + a nr + j]
+template <typename T>
 __global__ void k_mix_readback(const float* __restrict__ Y, int mrows, int nr, int cells, long cs, double scale,
-                               double* __restrict__ yA, double* __restrict__ yB) {
+                               T* __restrict__ yA, T* __restrict__ yB) {
     const long total = (long)cells * 2 * nr;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
         const long c = t / (2 * nr);
         const int r = (int)(t - c * 2 * nr);
-        (r < nr ? yA : yB)[c * cs + (r < nr ? r : r - nr)] = scale * (double)Y[c * mrows + r];
+        (r < nr ? yA : yB)[c * cs + (r < nr ? r : r - nr)] = (T)(scale * (double)Y[c * mrows + r]);
     }
 }
 
@@ -1819,7 +1820,7 @@ lbe_status mix_tc_build(Ctx* c, const double* L, int n, MixTc** out, cudaStream_
 }
 
 lbe_status mix_tc_apply(Ctx* c, MixTc* m, int cells, const double* hA, const double* hB, long cs, int nr,
-                        double scale, double* yA, double* yB, cudaStream_t s) {
+                        double scale, void* yA, void* yB, bool f32, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(m->T.mu);
     float* Y = nullptr;
     const int np = m->d.L.npmax;
@@ -1830,8 +1831,11 @@ lbe_status mix_tc_apply(Ctx* c, MixTc* m, int cells, const double* hA, const dou
     }, &Y);
     if (st != LBE_OK) return st;
     const long tot = (long)cells * 2 * nr;
-    k_mix_readback<<<(int)std::min<long>((tot + 255) / 256, 32L * sm_count()), 256, 0, s>>>(
-        Y, m->d.L.rows, nr, cells, cs, scale, yA, yB);
+    const int gr = (int)std::min<long>((tot + 255) / 256, 32L * sm_count());
+    if (f32)
+        k_mix_readback<float><<<gr, 256, 0, s>>>(Y, m->d.L.rows, nr, cells, cs, scale, (float*)yA, (float*)yB);
+    else
+        k_mix_readback<double><<<gr, 256, 0, s>>>(Y, m->d.L.rows, nr, cells, cs, scale, (double*)yA, (double*)yB);
     g_launches += 3;
     cudaMemcpyAsync(m->T.err_host, m->T.err_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
     return cuda_status(c, cudaGetLastError(), "mixture tensor-core operator");

@@ -52,11 +52,15 @@ struct MixOp {
     size_t bytes = 0;
     DevTables tab[2];         // per species: the transport sweep's tables (vel, f_a,eq, nu_a)
     float2* Ldf = nullptr;    // L as double-float (hi, lo) pairs, built at first use
+    float2* Xdf = nullptr;    // the cell operand as double-float pairs (grow-only)
+    size_t xdf_bytes = 0;
     double* part = nullptr;   // split-K partial sums of the GEMM (grow-only)
     size_t part_bytes = 0;
     MixTc* tc = nullptr;      // the same operator in BF16 hi / lo on the tensor cores (first use)
     double* zero = nullptr;   // [n3] zeros: the source-free sweep's f_eq
     DevTables tab0[2];        // tab with a zero source (the correction equation's sweep)
+    float* ftab = nullptr;    // float copies for the low-precision sweeps: f_eq [2][n3], nu [2][n3],
+                              // zeros [n3], vel [nv]
 };
 
 namespace {
@@ -255,10 +259,22 @@ __global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, 
 // on load, each product formed exactly by FMA (TwoProduct, cross terms added) and accumulated
 // by TwoSum; the pairs are renormalised after every K slice of the tile and widened to double at
 // the end (about 1e-13 of the scale, against the FP64 kernel's rounding).
+// X[cell][k] = both species' h of a cell as double-float pairs (once per GEMM, so the tiles read
+// float pairs and the GEMM does no FP64 arithmetic)
+__global__ void k_mix_h_to_df(const double* __restrict__ hA, const double* __restrict__ hB, long cs, int nr,
+                              int cells, float2* __restrict__ X) {
+    const long K = 2L * nr, total = K * cells;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const long c = t / K, k = t - c * K;
+        const dfloat d(k < nr ? hA[c * cs + k] : hB[c * cs + k - nr]);
+        X[t] = make_float2(d.hi, d.lo);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_mix_gemm_df(const float2* __restrict__ L, int nr,
-                                                     const double* __restrict__ hA, const double* __restrict__ hB,
-                                                     long cs, int cells, double scale, double* __restrict__ yA,
-                                                     double* __restrict__ yB, int kc, double* __restrict__ part) {
+                                                     const float2* __restrict__ X, long cs, int cells, double scale,
+                                                     double* __restrict__ yA, double* __restrict__ yB, int kc,
+                                                     double* __restrict__ part) {
     __shared__ float2 As[kKT][kMT + 1];
     __shared__ float2 Bs[kKT][kNT + 1];
     const int rows = 2 * nr, K = 2 * nr;
@@ -284,10 +300,7 @@ __global__ void __launch_bounds__(256) k_mix_gemm_df(const float2* __restrict__ 
             const int gc = cell0 + cc;
             for (int q = 0; q < 4; ++q) {
                 const int gk = k0 + kq + q;
-                double v = 0.0;
-                if (gc < cells && gk < ke) v = gk < nr ? hA[gc * cs + gk] : hB[gc * cs + gk - nr];
-                const dfloat d(v);
-                Bs[kq + q][cc] = make_float2(d.hi, d.lo);
+                Bs[kq + q][cc] = (gc < cells && gk < ke) ? X[(long)gc * K + gk] : make_float2(0.f, 0.f);
             }
         }
         __syncthreads();
@@ -374,8 +387,9 @@ __device__ __forceinline__ void orbit_point(int q, int N, int layout, int* i1, i
 // per (cell, species): mom[(a cells + n) kMom + .] = {U, q, W1, P13, G1, W2, X12, P23, G2}: U, q,
 // W1 = F201/4, P13, W2 = F021/4, X12 = F111/4, P23 of h^(k+1/2) and G_j of L h^(k), h^(k); sums
 // over the orbit representatives times the orbit size (4 plates, 2 ducts)
-__global__ void __launch_bounds__(256) k_mix_moments(MixSisDev P, const double* __restrict__ hh,
-                                                     const double* __restrict__ h, const double* __restrict__ lp,
+template <typename T>
+__global__ void __launch_bounds__(256) k_mix_moments(MixSisDev P, const T* __restrict__ hh,
+                                                     const double* __restrict__ h, const T* __restrict__ lp,
                                                      const double* __restrict__ nu, const double* __restrict__ vel,
                                                      double* __restrict__ mom) {
     const int n = blockIdx.x, a = blockIdx.y, N = P.nv, H = N / 2;
@@ -387,7 +401,7 @@ __global__ void __launch_bounds__(256) k_mix_moments(MixSisDev P, const double* 
         int i1, i2, i3;
         orbit_point(q, N, P.layout, &i1, &i2, &i3);
         const double v1 = vel[i1], v2 = vel[i2], v3 = vel[i3];
-        const double x = hh[off + q] * v3;
+        const double x = (double)hh[off + q] * v3;
         s[0] += x;
         s[1] += (r * (v1 * v1 + v2 * v2 + v3 * v3) - 2.5) * x;
         s[2] += (2.0 * v1 * v1 - 1.0) * x;
@@ -397,7 +411,7 @@ __global__ void __launch_bounds__(256) k_mix_moments(MixSisDev P, const double* 
         s[7] += v2 * x;
         if (P.sis) {
             const long vf = ((long)i1 * N + i2) * N + i3;
-            const double y = (lp[off + q] + (P.Nd[a] - P.delta * nu[a * n3 + vf]) * h[off + q]) * v3;
+            const double y = ((double)lp[off + q] + (P.Nd[a] - P.delta * nu[a * n3 + vf]) * h[off + q]) * v3;
             s[4] += v1 * y;
             s[8] += v2 * y;
         }
@@ -436,7 +450,8 @@ __global__ void __launch_bounds__(256) k_mix_march(MixSisDev P, const double* __
     __syncthreads();
     const int a = threadIdx.x;
     if (a >= 2) return;
-    const double *x = sm + 2 * kMom * n, *fa = x + n, *fb = x + 2 * n, *fc = x + 3 * n, *trap = x + 4 * n;
+    // ia: reciprocals of the stencil's diagonal (host)
+    const double *x = sm + 2 * kMom * n, *ia = x + n, *fb = x + 2 * n, *fc = x + 3 * n, *trap = x + 4 * n;
     const double* ma = sm + a * n * kMom;
     const double* mB = sm + n * kMom;
     const double kN = P.Nd[a] / P.r[a], chi = P.chi[a], cU = P.cU[a], cq = P.cq[a];
@@ -452,7 +467,7 @@ __global__ void __launch_bounds__(256) k_mix_march(MixSisDev P, const double* __
                 const double Pt = a == 0 ? (P.src ? x[i] : 0.0) - mB[kMom * i + 3] : mB[kMom * i + 3];
                 double sr = ma[kMom * i + 4] - kN * Pt - fb[i] * y1;
                 if (i >= 2) sr -= fc[i] * y2;
-                Y = sr / fa[i];
+                Y = sr * ia[i];
             }
             y2 = y1;
             y1 = Y;
@@ -562,7 +577,8 @@ __global__ void k_mix_axpy(const double* __restrict__ a, double s, const double*
 }
 
 // h_a = hh_a + 2 r_a dU_a v3 f_a,eq on the representatives
-__global__ void __launch_bounds__(256) k_mix_correct(MixSisDev P, const double* __restrict__ hh,
+template <typename T>
+__global__ void __launch_bounds__(256) k_mix_correct(MixSisDev P, const T* __restrict__ hh,
                                                      double* __restrict__ h, const double* __restrict__ dU,
                                                      const double* __restrict__ feq, const double* __restrict__ vel) {
     const int N = P.nv, H = N / 2, nq = N * (P.layout == 1 ? H : N) * H;
@@ -575,7 +591,7 @@ __global__ void __launch_bounds__(256) k_mix_correct(MixSisDev P, const double* 
         int i1, i2, i3;
         orbit_point(q, N, P.layout, &i1, &i2, &i3);
         const long vf = ((long)i1 * N + i2) * N + i3, off = an * n3 + q;
-        h[off] = hh[off] + 2.0 * P.r[a] * dU[an] * vel[i3] * feq[a * n3 + vf];
+        h[off] = (double)hh[off] + 2.0 * P.r[a] * dU[an] * vel[i3] * feq[a * n3 + vf];
     }
 }
 
@@ -611,8 +627,10 @@ void free_mixop(Ctx* c, MixOp* o) {
     if (o->vel) dev_free(c, o->vel, sizeof(double) * o->nv);
     if (o->part) dev_free(c, o->part, o->part_bytes);
     if (o->Ldf) dev_free(c, o->Ldf, sizeof(float2) * 4 * (size_t)o->nr * o->nr);
+    if (o->Xdf) dev_free(c, o->Xdf, o->xdf_bytes);
     if (o->tc) mix_tc_release(c, o->tc);
     if (o->zero) dev_free(c, o->zero, sizeof(double) * n3);
+    if (o->ftab) dev_free(c, o->ftab, sizeof(float) * (5 * n3 + o->nv));
     delete o;
 }
 
@@ -818,6 +836,15 @@ lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
     if (st != LBE_OK) return st;
     if ((st = dev_alloc(c, (void**)&o.zero, sizeof(double) * n3)) != LBE_OK) return st;
     cudaMemsetAsync(o.zero, 0, sizeof(double) * n3, s);
+    if ((st = dev_alloc(c, (void**)&o.ftab, sizeof(float) * (5 * n3 + N))) != LBE_OK) return st;
+    {
+        std::vector<float> ft(5 * n3 + N, 0.f);
+        for (long i = 0; i < 2 * n3; ++i) ft[i] = (float)feq[i];
+        for (long i = 0; i < 2 * n3; ++i) ft[2 * n3 + i] = (float)o.nu_h[i];
+        for (int j = 0; j < N; ++j) ft[5 * n3 + j] = (float)v[j];
+        cudaMemcpy(o.ftab, ft.data(), sizeof(float) * ft.size(), cudaMemcpyHostToDevice);
+        g_h2d += sizeof(float) * ft.size();
+    }
     for (int a = 0; a < 2; ++a) {
         DevTables& t = o.tab[a];
         t.nv = N;
@@ -828,8 +855,12 @@ lbe_status build_mixop(Ctx* c, MixOp& o, cudaStream_t s) {
         t.vel_d = o.vel;
         t.feq_d = o.feq + a * n3;
         t.nu1_d = o.nu + a * n3;
+        t.feq_f = o.ftab + a * n3;
+        t.nu1_f = o.ftab + 2 * n3 + a * n3;
+        t.vel_f = o.ftab + 5 * n3;
         o.tab0[a] = t;
         o.tab0[a].feq_d = o.zero;
+        o.tab0[a].feq_f = o.ftab + 4 * n3;
     }
     return cuda_status(c, cudaStreamSynchronize(s), "mixture tables");
 }
@@ -905,8 +936,18 @@ lbe_status mix_gemm(Ctx* c, MixOp& o, const double* hA, const double* hB, long c
     const bool timed = g_time_kernels.load() != 0 && cudaEventCreate(&ev[0]) == cudaSuccess &&
                        cudaEventCreate(&ev[1]) == cudaSuccess;
     if (timed) cudaEventRecord(ev[0], s);
-    if (df)
-        k_mix_gemm_df<<<g, 256, 0, s>>>(o.Ldf, o.nr, hA, hB, cs, cells, scale, yA, yB, kc, S > 1 ? o.part : nullptr);
+    if (df) {
+        const size_t xb = sizeof(float2) * (size_t)K * cells;
+        if (xb > o.xdf_bytes) {
+            if (o.Xdf) cudaStreamSynchronize(s), dev_free(c, o.Xdf, o.xdf_bytes), o.Xdf = nullptr, o.xdf_bytes = 0;
+            lbe_status st = dev_alloc(c, (void**)&o.Xdf, xb);
+            if (st != LBE_OK) return st;
+            o.xdf_bytes = xb;
+        }
+        k_mix_h_to_df<<<grid_for((long)K * cells), 256, 0, s>>>(hA, hB, cs, o.nr, cells, o.Xdf);
+        k_mix_gemm_df<<<g, 256, 0, s>>>(o.Ldf, o.nr, o.Xdf, cs, cells, scale, yA, yB, kc, S > 1 ? o.part : nullptr);
+        g_launches += 1;
+    }
     else
         k_mix_gemm<<<g, 256, 0, s>>>(o.L, o.nr, hA, hB, cs, cells, scale, yA, yB, kc, S > 1 ? o.part : nullptr);
     g_launches += 1;
@@ -1009,7 +1050,9 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     std::vector<double> coef, geov;
     if (dim == 1) {
         for (auto* vv : {&g.fa, &g.fb, &g.fc, &g.ba, &g.bb, &g.bc}) coef.insert(coef.end(), vv->begin(), vv->end());
-        for (auto* vv : {&g.x, &g.fa, &g.fb, &g.fc, &g.trap}) geov.insert(geov.end(), vv->begin(), vv->end());
+        std::vector<double> ia(g.fa.size());
+        for (size_t i = 0; i < ia.size(); ++i) ia[i] = g.fa[i] != 0.0 ? 1.0 / g.fa[i] : 0.0;
+        for (auto* vv : {&g.x, &ia, &g.fb, &g.fc, &g.trap}) geov.insert(geov.end(), vv->begin(), vv->end());
     } else {
         for (auto* vv : {&g.xa, &g.xb, &g.xc, &g.ya, &g.yb, &g.yc}) coef.insert(coef.end(), vv->begin(), vv->end());
         // DST-I of the interior (orthonormal, symmetric) and the Laplacian's eigenvalues
@@ -1067,7 +1110,11 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
         if (st == LBE_OK) st = dev_alloc(ctx, p, bytes);
     };
     const bool refined = pb->precision == LBE_BF16_REFINED;
-    void *d_hp = nullptr, *d_e = nullptr, *d_x = nullptr, *d_d = nullptr;
+    void *d_hp = nullptr, *d_e = nullptr, *d_x = nullptr, *d_d = nullptr, *d_lp32 = nullptr, *d_hh32 = nullptr;
+    if (lo) {
+        take(&d_lp32, b_state / 2);
+        take(&d_hh32, b_state / 2);
+    }
     take(&d_h, b_state);
     take(&d_hh, b_state);
     take(&d_lp, b_state);
@@ -1105,20 +1152,37 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     // cores; homog: the source-free iteration (no S_a in the sweep, no x1 in the march); r
     // receives the flow rates of hout
     auto step = [&](const double* hin, double* hout, bool tc, bool homog, double* r) -> lbe_status {
-        lbe_status e = tc ? mix_tc_apply(ctx, o->tc, n, hin, hin + per, n3, o->nr, pb->delta, lp, lp + per, s)
-                          : mix_gemm(ctx, *o, hin, hin + per, n3, n, pb->delta, lp, lp + per, s, dfg);
-        if (e != LBE_OK) return e;
-        for (int a = 0; a < 2; ++a)
-            launch_sweep<double>(homog ? o->tab0[a] : o->tab[a], dim, 1, (int)coef.size(), lp + a * per,
-                                 hh + a * per, (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
         MixSisDev Q = P;
         Q.src = homog ? 0 : 1;
-        k_mix_moments<<<dim3(n, 2), 256, 0, s>>>(Q, hh, hin, lp, o->nu, o->vel, mom);
-        if (dim == 1)
-            k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
-        else
-            k_mix_poisson2d<<<2, 512, 0, s>>>(Q, D, mom, dSx, dSy, dlam, dwork, dU, Uc, rates);
-        k_mix_correct<<<grid_for(2L * n * nq), 256, 0, s>>>(Q, hh, hout, dU, o->feq, o->vel);
+        lbe_status e;
+        if (tc) {
+            // low precision: the tensor-core operator read back as float, float sweeps, FP64 state
+            float* lp32 = (float*)d_lp32;
+            float* hh32 = (float*)d_hh32;
+            e = mix_tc_apply(ctx, o->tc, n, hin, hin + per, n3, o->nr, pb->delta, lp32, lp32 + per, true, s);
+            if (e != LBE_OK) return e;
+            for (int a = 0; a < 2; ++a)
+                launch_sweep<float>(homog ? o->tab0[a] : o->tab[a], dim, 1, (int)coef.size(), lp32 + a * per,
+                                    hh32 + a * per, (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
+            k_mix_moments<float><<<dim3(n, 2), 256, 0, s>>>(Q, hh32, hin, lp32, o->nu, o->vel, mom);
+            if (dim == 1)
+                k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
+            else
+                k_mix_poisson2d<<<2, 512, 0, s>>>(Q, D, mom, dSx, dSy, dlam, dwork, dU, Uc, rates);
+            k_mix_correct<float><<<grid_for(2L * n * nq), 256, 0, s>>>(Q, hh32, hout, dU, o->feq, o->vel);
+        } else {
+            e = mix_gemm(ctx, *o, hin, hin + per, n3, n, pb->delta, lp, lp + per, s, dfg);
+            if (e != LBE_OK) return e;
+            for (int a = 0; a < 2; ++a)
+                launch_sweep<double>(homog ? o->tab0[a] : o->tab[a], dim, 1, (int)coef.size(), lp + a * per,
+                                     hh + a * per, (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
+            k_mix_moments<double><<<dim3(n, 2), 256, 0, s>>>(Q, hh, hin, lp, o->nu, o->vel, mom);
+            if (dim == 1)
+                k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
+            else
+                k_mix_poisson2d<<<2, 512, 0, s>>>(Q, D, mom, dSx, dSy, dlam, dwork, dU, Uc, rates);
+            k_mix_correct<double><<<grid_for(2L * n * nq), 256, 0, s>>>(Q, hh, hout, dU, o->feq, o->vel);
+        }
         g_launches += 3;
         g_levals += n;
         cudaMemcpyAsync(r, rates, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1214,7 +1278,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
             // U and the flow rates of the returned h
             MixSisDev Q = P;
             Q.sis = 0;
-            k_mix_moments<<<dim3(n, 2), 256, 0, s>>>(Q, h, h, lp, o->nu, o->vel, mom);
+            k_mix_moments<double><<<dim3(n, 2), 256, 0, s>>>(Q, h, h, lp, o->nu, o->vel, mom);
             if (dim == 1)
                 k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
             else
@@ -1253,6 +1317,8 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     dev_free(ctx, d_job, sizeof job);
     for (void* q : {d_hp, d_e, d_x, d_d})
         if (q) dev_free(ctx, q, b_state);
+    for (void* q : {d_lp32, d_hh32})
+        if (q) dev_free(ctx, q, b_state / 2);
     out->M_A = hr[0];
     out->M_B = hr[1];
     out->Q_A = hr[2];
