@@ -258,3 +258,33 @@ def test_mixture_to_single_species_ratio_is_geometry_independent(ctx):
     plate = np.array([mp.M_A, mp.M_B]) / sp_plate
     duct = md[:2] / sp_duct
     assert np.all(np.abs(duct / plate - 1.0) < 0.015), (plate, duct)
+
+
+def test_mixture_edge_cases_and_oom(ctx):
+    """Zero cells, invalid arguments, and an HBM budget too small for the operator build: the
+    call returns LBE_OOM and the context still serves a call that fits."""
+    from paper_1612_04488_gb300 import lbe
+    mix = lbe.Mixture(*NE_AR, 0.5)
+    d = torch.zeros(1, device="cuda", dtype=torch.float64)
+    assert ctx.mix_apply_L(mix, 8, 5.0, 8, 3.75, 0, 1.0, d.data_ptr(), d.data_ptr(), d.data_ptr(), None,
+                           d.data_ptr(), None) == lbe.OK
+    for bad in (lbe.Mixture(-1.0, 1.0, 0.5), lbe.Mixture(2.0, 1.0, 1.0), lbe.Mixture(2.0, 0.0, 0.5)):
+        with pytest.raises(lbe.LbeError):
+            ctx.mix_info(bad, 8, 5.0, 8, 3.75)
+    for nv, M, R in ((10, 8, 3.75), (8, 6, 3.75), (8, 8, 0.0)):
+        with pytest.raises(lbe.LbeError):
+            ctx.mix_info(mix, nv, 5.0, M, R)
+    for kw in (dict(ns=1), dict(dim=2, nx=2, ny=8), dict(dim=2, nx=300, ny=8), dict(precision=lbe.FP32)):
+        args = dict(delta=1.0, nv=8, vmax=5.0, M=8, R=3.75, max_iter=3)
+        args.update(kw)
+        with pytest.raises(lbe.LbeError):
+            ctx.mix_solve(lbe.mix_problem(*NE_AR, 0.5, **args))
+    small = lbe.Context(0, hbm_budget=64 << 20)
+    try:
+        with pytest.raises(lbe.LbeError) as e:
+            small.mix_info(mix, 16, 5.0, 8, 3.75)        # the build needs about 0.8 GB
+        assert e.value.status == lbe.OOM
+        info, _ = small.mix_info(mix, 8, 5.0, 8, 3.75)   # about 13 MB
+        assert info[0] > 0
+    finally:
+        small.close()
