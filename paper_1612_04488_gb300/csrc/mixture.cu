@@ -1,7 +1,8 @@
 // Binary hard-sphere mixture (Sec. 4): the four linearized collision operators of a mixture
 // as one dense matrix, built on the device from the Carleman form for unequal masses and
-// applied as an FP64 GEMM, and the SIS of Eqs. LBE2_true1 / LBE2_true2 for Poiseuille flow
-// between plates.
+// applied as a GEMM (FP64, double-float on the FP32 pipes, or tcgen05 BF16 hi / lo through
+// fsm_dense.cu), and the SIS of Eqs. LBE2_true1 / LBE2_true2 for Poiseuille flow between plates
+// and through rectangular ducts, with defect correction for the mixed-precision solves.
 //
 // Operator (include/lbe.h has the full statement).  For species a colliding with b,
 // mu_b = m_b / (m_a + m_b), c = mu_b - mu_a, and x ⊥ y: v* = v + x + y, v' = v + 2 mu_b x,
@@ -15,8 +16,9 @@
 //   K_ab[k, m] = f^_a(l) (beta_ab(l, m) - G_ab(m)) + [a = b] sum_c beta_ac(m, l) f^_c(l),
 //   G_ab = sum_p 2 b_ab w_p phi_p psi_p (the loss, mass independent).
 // The velocity-space matrix is F^-1 K F; separable passes along each velocity axis carry the
-// columns to the unknown's basis (the full grid, or one value per orbit of the plate parity:
-// even in v2, odd in v3) and the rows to its representatives.  L+_a = sum_b K_ab h_b and
+// columns to the unknown's basis (the full grid, or one value per orbit of the plate parity,
+// even in v2 and odd in v3, or of the duct parity, odd in v3) and the rows to its
+// representatives.  L+_a = sum_b K_ab h_b and
 // L_a = L+_a - nu_a h_a with nu_a = sum_b F^-1(G_ab F f_b,eq).
 //
 // delta: b_AA = delta mu1 sqrt(2 / m) / 4 (units m_A = kT = d_A = 1, m = chi_A + chi_B m_B),
@@ -255,10 +257,10 @@ __global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, 
     }
 }
 
-// The same GEMM in double-float arithmetic on the FP32 pipes: L as (hi, lo) float pairs, h split
-// on load, each product formed exactly by FMA (TwoProduct, cross terms added) and accumulated
-// by TwoSum; the pairs are renormalised after every K slice of the tile and widened to double at
-// the end (about 1e-13 of the scale, against the FP64 kernel's rounding).
+// The same GEMM in double-float arithmetic on the FP32 pipes: L and the cell operand as (hi, lo)
+// float pairs, each product formed exactly by FMA (TwoProduct, cross terms added) and
+// accumulated by TwoSum; the pairs are renormalised after every K slice of the tile and widened
+// to double at the end (about 1e-13 of the scale, against the FP64 kernel's rounding).
 // X[cell][k] = both species' h of a cell as double-float pairs (once per GEMM, so the tiles read
 // float pairs and the GEMM does no FP64 arithmetic)
 __global__ void k_mix_h_to_df(const double* __restrict__ hA, const double* __restrict__ hB, long cs, int nr,
@@ -365,8 +367,8 @@ __global__ void k_mix_loss(const double* __restrict__ lp, const double* __restri
         L[t] = lp[t] - delta * nu[t % n3] * h[t];
 }
 
-// ---- plate SIS kernels (orbit layout: per cell the nq = nv^3 / 4 values at the
-// representatives (i1 H + j2) H + j3, j2, j3 < H = nv / 2; cell stride nv^3) -------------------
+// ---- SIS kernels.  Orbit layouts, cell stride nv^3: plates keep the nq = nv^3 / 4 values at
+// (i1 H + j2) H + j3 with j2, j3 < H = nv / 2; ducts the nv^3 / 2 values at (i1 nv + i2) H + j3 --
 struct MixSisDev {
     double r[2], chi[2], Nd[2], delta, dv3, sqm;
     double cU[2], cq[2];
