@@ -387,6 +387,17 @@ typedef struct {
                           * (its change is the FP64 stopping test), and its error
                           * e = G (e + h' - h) solved by the source-free iteration on the tensor
                           * cores; h = h' + e                                                   */
+    double solid_fraction;   /* > 0 (ducts only, nx = ny): instead of the duct, the periodic unit
+                          * cell of a square array of cylinders -- a centred circle of this area
+                          * (below 0.78) as a staircase of solid cells, diffuse walls, periodic
+                          * sides (config of Sec. 4's porous media); the sweep takes a periodic
+                          * neighbour not yet swept from the previous sweep (a converged
+                          * iteration satisfies the periodic scheme), and the diffusion
+                          * correction acts on the fluid cells whose eight neighbours are fluid
+                          * (solved by conjugate gradients), the others held at the kinetic U.
+                          * The sweep's lag makes its last half step part of the iteration's
+                          * state, so LBE_BF16_REFINED continues there with plain FP64-class
+                          * iterations after the low-precision floor (no defect correction)     */
 } lbe_mix_problem;
 
 typedef struct {

@@ -347,6 +347,70 @@ def mc_galerkin_viscosity(mix, n=1_000_000, chunks=2, seed=7):
     return -P13 / np.sqrt(mix.mbar)
 
 
+# ---- porous cell: a square array of cylinders (the unit cell, periodic) ----------------------
+def porous_solid(n, solid_fraction):
+    """Staircase of the centred circular cylinder of area `solid_fraction` in the periodic unit
+    cell of n x n cells: cell (i, j), centre ((i + 1/2) / n, (j + 1/2) / n), is solid when its
+    centre lies inside the circle."""
+    c = (np.arange(n) + 0.5) / n - 0.5
+    X, Y = np.meshgrid(c, c, indexing="ij")
+    return X * X + Y * Y < solid_fraction / np.pi
+
+
+def upwind_porous(solid1, solid2, d):
+    """(a, b, c) of d/ds at a fluid cell from itself, its upwind neighbour and the next one
+    (spacing d).  A solid neighbour ends the line at its face, half a cell away, where the
+    diffuse wall emits h = 0: first order from the face next to a solid neighbour, three
+    points through the face one cell further up."""
+    if solid1:
+        return 2.0 / d, 0.0, 0.0
+    if solid2:
+        a, b, _ = transport.backward_coeffs(-1.5 * d, -d, 0.0)
+        return a, b, 0.0
+    return transport.backward_coeffs(-2.0 * d, -d, 0.0)
+
+
+def sweep_porous(rhs, nu, V1, V2, solid, hprev):
+    """nu h + v1 dh/dx1 + v2 dh/dx2 = rhs in the periodic unit cell with solid cells (h = 0).
+    For each quadrant of (v1, v2) the cells are swept in upwind order, rows in x2 and cells in
+    x1; a periodic neighbour that is not yet swept takes its value from `hprev`, the previous
+    sweep's result (the sweep is done in place over it), so a converged iteration satisfies the
+    periodic scheme itself."""
+    n = solid.shape[0]
+    d = 1.0 / n
+    out = hprev.copy()
+    for s1 in (1, -1):
+        for s2 in (1, -1):
+            sel = (np.sign(V1) == s1) & (np.sign(V2) == s2)
+            u1, u2, nuq = np.abs(V1[sel]), np.abs(V2[sel]), nu[sel]
+            for jj in range(n):
+                j = jj if s2 > 0 else n - 1 - jj
+                for ii in range(n):
+                    i = ii if s1 > 0 else n - 1 - ii
+                    if solid[i, j]:
+                        out[i, j][sel] = 0.0
+                        continue
+                    i1, i2 = (i - s1) % n, (i - 2 * s1) % n
+                    j1, j2 = (j - s2) % n, (j - 2 * s2) % n
+                    ax, bx, cx = upwind_porous(solid[i1, j], solid[i2, j], d)
+                    ay, by, cy = upwind_porous(solid[i, j1], solid[i, j2], d)
+                    num = (rhs[i, j][sel] - u1 * (bx * out[i1, j][sel] + cx * out[i2, j][sel])
+                           - u2 * (by * out[i, j1][sel] + cy * out[i, j2][sel]))
+                    out[i, j][sel] = num / (nuq + u1 * ax + u2 * ay)
+    return out
+
+
+def porous_interior(solid):
+    """Fluid cells whose eight neighbours (periodic) are fluid; the other fluid cells form the
+    wall-adjacent ring of the diffusion correction."""
+    fluid = ~solid
+    inner = fluid.copy()
+    for di in (-1, 0, 1):
+        for dj in (-1, 0, 1):
+            inner &= np.roll(fluid, (-di, -dj), axis=(0, 1))
+    return inner
+
+
 # ---- synthetic iterative scheme for plates (Sec. 4) ------------------------------------------
 class MixProblem:
     """Poiseuille flow of a binary mixture between plates (dim 1, Table 4's setting) or through
@@ -354,9 +418,10 @@ class MixProblem:
 
     def __init__(self, mass_ratio=39.95 / 20.18, diam_ratio=1.0 / 0.711, chi_A=0.5, delta=1.0,
                  ns=20, grid="uniform", nv=12, vmax=6.0, M=16, R=0.0, N_A=0.0, N_B=0.0,
-                 scheme="sis", eps=1e-8, max_iter=500, dim=1, nx=8, ny=8, width=1.0):
+                 scheme="sis", eps=1e-8, max_iter=500, dim=1, nx=8, ny=8, width=1.0, solid=0.0):
         self.mix = Mixture(mass_ratio, diam_ratio, chi_A)
         self.dim, self.nx, self.ny, self.width = dim, nx, ny, float(width)
+        self.solid = float(solid)  # > 0: the periodic unit cell (nx = ny) with a cylinder of this area
         self.delta, self.ns, self.grid = float(delta), ns, grid
         self.nv, self.vmax, self.M, self.R = nv, float(vmax), M, float(R)
         self.N = (float(N_A), float(N_B))
@@ -399,6 +464,10 @@ class MixRun:
             shape = (len(self.x),) + F.V1.shape
         else:
             shape = (pb.nx, pb.ny) + F.V1.shape
+            if pb.solid > 0:
+                self.solid = porous_solid(pb.nx, pb.solid)
+                self.inner = porous_interior(self.solid)
+                self.hprev = [np.zeros(shape), np.zeros(shape)]
         self.h = [np.zeros(shape), np.zeros(shape)]
         self.S = [F.V3 * F.f[a] for a in range(2)]
         self.Nd = [(pb.N[a] if pb.N[a] > 0 else F.N_alpha(a)) * pb.delta for a in range(2)]
@@ -448,6 +517,56 @@ class MixRun:
         U = Uh.copy()
         U[1:-1, 1:-1] = np.linalg.solve(A, b).reshape(mx, my)
         return U
+
+    def step_porous(self, L, hh):
+        """Steps 3-5 in the periodic unit cell: Eqs. LBE2_true1 / LBE2_true2 on the cells of
+        ``porous_interior`` with periodic central differences, U = U^(k+1/2) on the ring."""
+        F, pb, mix = self.F, self.pb, self.pb.mix
+        n = pb.nx
+        d = 1.0 / n
+        w = F.dv ** 3
+        ax = (-3, -2, -1)
+
+        def sh(f, di, dj):
+            return np.roll(f, (-di, -dj), axis=(0, 1))   # f[(i + di) % n, (j + dj) % n]
+
+        def d1(f):
+            return (sh(f, 1, 0) - sh(f, -1, 0)) / (2.0 * d)
+
+        def d2(f):
+            return (sh(f, 0, 1) - sh(f, 0, -1)) / (2.0 * d)
+
+        mo = [self.moments(a, hh[a]) + self.moments2(a, hh[a]) for a in range(2)]
+        DB = d1(mo[1][3]) + d2(mo[1][6])
+        D = [1.0 - DB, DB]
+        inner = self.inner
+        idx = -np.ones((n, n), dtype=int)
+        idx[inner] = np.arange(int(inner.sum()))
+        new = []
+        for a in range(2):
+            Uh, _, W1, _, W2, X12, _ = mo[a]
+            G1 = 2.0 * np.sum(F.V1 * F.V3 * (L[a] + self.Nd[a] * self.h[a]), axis=ax) * w
+            G2 = 2.0 * np.sum(F.V2 * F.V3 * (L[a] + self.Nd[a] * self.h[a]), axis=ax) * w
+            rhs = (-self.Nd[a] / mix.r[a] * D[a]
+                   - (sh(W1, 1, 0) - 2.0 * W1 + sh(W1, -1, 0)) / d ** 2
+                   - 2.0 * (sh(X12, 1, 1) - sh(X12, 1, -1) - sh(X12, -1, 1) + sh(X12, -1, -1)) / (4.0 * d * d)
+                   - (sh(W2, 0, 1) - 2.0 * W2 + sh(W2, 0, -1)) / d ** 2
+                   + d1(G1) + d2(G2)) / mix.chi[a]
+            m = int(inner.sum())
+            A = np.zeros((m, m))
+            b = rhs[inner].copy()
+            for (i, j), k in zip(np.argwhere(inner), range(m)):
+                A[k, k] = -4.0 / d ** 2
+                for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                    ii, jj = (i + di) % n, (j + dj) % n
+                    if inner[ii, jj]:
+                        A[k, idx[ii, jj]] = 1.0 / d ** 2
+                    else:
+                        b[k] -= Uh[ii, jj] / d ** 2
+            Un = Uh.copy()
+            Un[inner] = np.linalg.solve(A, b)
+            new.append(hh[a] + 2.0 * mix.r[a] * (Un - Uh)[(...,) + (None,) * 3] * F.V3 * F.f[a])
+        return new
 
     def step2(self, L, hh):
         """Steps 3-5 in a duct: returns the corrected h of both species."""
@@ -500,11 +619,17 @@ class MixRun:
         lp, L = [lpA, lpB], [LA, LB]
         if pb.dim == 1:
             hh = [transport.sweep_1d(lp[a] + self.S[a], d * F.nu[a], F.V1, self.x) for a in range(2)]
+        elif pb.solid > 0:
+            hh = [sweep_porous(lp[a] + self.S[a], d * F.nu[a], F.V1, F.V2, self.solid, self.hprev[a])
+                  for a in range(2)]
+            self.hprev = hh
         else:
             hh = [transport.sweep_2d(lp[a] + self.S[a], d * F.nu[a], F.V1, F.V2, pb.nx, pb.ny, pb.width)
                   for a in range(2)]
         if pb.scheme == "cis":
             self.h = hh
+        elif pb.dim == 2 and pb.solid > 0:
+            self.h = self.step_porous(L, hh)
         elif pb.dim == 2:
             self.h = self.step2(L, hh)
         else:

@@ -571,6 +571,194 @@ __global__ void __launch_bounds__(512) k_mix_poisson2d(MixSisDev P, MixDuctDev D
     }
 }
 
+// ---- the periodic unit cell with solid cells (a square array of cylinders) -----------------------
+// Upwind derivative weights along one direction of the march (spacing d): `u` a fluid line,
+// `w1` a solid upwind neighbour (first order from its face, where the diffuse wall emits h = 0),
+// `w2` a solid second neighbour (three points through that face).
+struct PorousDev {
+    int n;
+    double ua, ub, uc, w1a, w2a, w2b;
+};
+
+// One thread per velocity of the duct orbit layout (i1, i2, j3 < nv / 2): the cells in upwind
+// order of its (v1, v2) quadrant, rows in x2, cells in x1 (cell (i, j) at i n + j), in place in
+// h, so that a periodic neighbour not yet swept still holds the previous sweep's value; solid
+// cells are set to zero.  nu h + v1 dh/dx1 + v2 dh/dx2 = rhs + v3 feq (feq = 0: no source).
+template <typename T>
+__global__ void __launch_bounds__(128) k_mix_sweep_porous(const T* __restrict__ rhs, T* __restrict__ h,
+                                                          const T* __restrict__ nu1, const T* __restrict__ vel,
+                                                          const T* __restrict__ feq,
+                                                          const unsigned char* __restrict__ solid, PorousDev G,
+                                                          int nv, double delta) {
+    const int H = nv / 2, q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nv * nv * H) return;
+    const long n3 = (long)nv * nv * nv;
+    const int i1 = q / (nv * H), i2 = q / H % nv, j3 = q % H;
+    const long vf = ((long)i1 * nv + i2) * nv + j3;
+    const T v1 = vel[i1], v2 = vel[i2];
+    const int s1 = v1 > T(0) ? 1 : -1, s2 = v2 > T(0) ? 1 : -1;
+    const T u1 = v1 > T(0) ? v1 : -v1, u2 = v2 > T(0) ? v2 : -v2;
+    const T nu = (T)delta * nu1[vf], S = vel[j3] * feq[vf];
+    const int n = G.n;
+    auto at = [&](int i, int j) -> long { return ((long)i * n + j) * n3 + q; };
+    for (int jj = 0; jj < n; ++jj) {
+        const int j = s2 > 0 ? jj : n - 1 - jj;
+        const int j1 = (j - s2 + n) % n, j2 = (j - 2 * s2 + 2 * n) % n;
+        for (int ii = 0; ii < n; ++ii) {
+            const int i = s1 > 0 ? ii : n - 1 - ii;
+            if (solid[i * n + j]) {
+                h[at(i, j)] = T(0);
+                continue;
+            }
+            const int i1c = (i - s1 + n) % n, i2c = (i - 2 * s1 + 2 * n) % n;
+            T ax, bx, cx, ay, by, cy;
+            if (solid[i1c * n + j]) ax = (T)G.w1a, bx = T(0), cx = T(0);
+            else if (solid[i2c * n + j]) ax = (T)G.w2a, bx = (T)G.w2b, cx = T(0);
+            else ax = (T)G.ua, bx = (T)G.ub, cx = (T)G.uc;
+            if (solid[i * n + j1]) ay = (T)G.w1a, by = T(0), cy = T(0);
+            else if (solid[i * n + j2]) ay = (T)G.w2a, by = (T)G.w2b, cy = T(0);
+            else ay = (T)G.ua, by = (T)G.ub, cy = (T)G.uc;
+            T num = rhs[at(i, j)] + S;
+            if (bx != T(0)) num -= u1 * bx * h[at(i1c, j)];
+            if (cx != T(0)) num -= u1 * cx * h[at(i2c, j)];
+            if (by != T(0)) num -= u2 * by * h[at(i, j1)];
+            if (cy != T(0)) num -= u2 * cy * h[at(i, j2)];
+            h[at(i, j)] = num / (nu + u1 * ax + u2 * ay);
+        }
+    }
+}
+
+// One block per species: Eqs. LBE2_true1 / LBE2_true2 on the m interior cells (fluid cells whose
+// eight periodic neighbours are fluid; list `inner`, and per interior cell its four neighbours
+// `nb` as an interior index k >= 0 or a ring cell -1 - cell), the other fluid cells held at
+// U^(k+1/2), periodic central differences; solved by conjugate gradients on -lap (symmetric
+// positive definite) to a residual of 1e-13 of the right-hand side (at most 20000 steps).  Then
+// dU, the corrected U and q, and the flow rates sqrt(m) times means over all n^2 cells.
+__global__ void __launch_bounds__(1024) k_mix_poisson_porous(MixSisDev P, PorousDev G, const double* __restrict__ mom,
+                                                             const int* __restrict__ inner, const int* __restrict__ nb,
+                                                             int m, double* __restrict__ work,
+                                                             double* __restrict__ dU, double* __restrict__ Uout,
+                                                             double* __restrict__ rates, int* __restrict__ cg_steps) {
+    const int a = blockIdx.x, n = G.n, ncell = n * n;
+    const double d = 1.0 / n, id2 = 1.0 / (d * d);
+    double* x = work + (long)a * 5 * m;
+    double* r = x + m;
+    double* p = r + m;
+    double* Ap = p + m;
+    double* b = Ap + m;
+    auto M = [&](int sp, int cell, int k) { return mom[((long)sp * ncell + cell) * kMom + k]; };
+    __shared__ double red[32];
+    __shared__ double bc;
+    auto block_sum = [&](double v) -> double {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            bc = t;
+        }
+        __syncthreads();
+        return bc;
+    };
+    if (P.sis) {
+        const double kN = P.Nd[a] / P.r[a], chi = P.chi[a];
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            const int c = inner[k], i = c / n, j = c % n;
+            auto C = [&](int di, int dj) { return ((i + di + n) % n) * n + (j + dj + n) % n; };
+            auto d1 = [&](int sp, int q) { return (M(sp, C(1, 0), q) - M(sp, C(-1, 0), q)) / (2.0 * d); };
+            auto d2 = [&](int sp, int q) { return (M(sp, C(0, 1), q) - M(sp, C(0, -1), q)) / (2.0 * d); };
+            const double DB = d1(1, 3) + d2(1, 7);
+            const double Dd = a == 0 ? (P.src ? 1.0 : 0.0) - DB : DB;
+            double v = -kN * Dd - (M(a, C(1, 0), 2) - 2.0 * M(a, c, 2) + M(a, C(-1, 0), 2)) * id2 -
+                       2.0 * (M(a, C(1, 1), 6) - M(a, C(1, -1), 6) - M(a, C(-1, 1), 6) + M(a, C(-1, -1), 6)) /
+                           (4.0 * d * d) -
+                       (M(a, C(0, 1), 5) - 2.0 * M(a, c, 5) + M(a, C(0, -1), 5)) * id2 + d1(a, 4) + d2(a, 8);
+            v /= chi;
+            for (int e = 0; e < 4; ++e) {
+                const int t = nb[4 * k + e];
+                if (t < 0) v -= M(a, -1 - t, 0) * id2;
+            }
+            b[k] = -v;                   // -lap U = -rhs: positive definite
+            x[k] = M(a, c, 0);           // start from U^(k+1/2)
+        }
+        __syncthreads();
+        auto apply = [&](const double* y, double* z) {  // z = -lap y on the interior (ring terms in b)
+            for (int k = threadIdx.x; k < m; k += blockDim.x) {
+                double v = 4.0 * y[k];
+                for (int e = 0; e < 4; ++e) {
+                    const int t = nb[4 * k + e];
+                    if (t >= 0) v -= y[t];
+                }
+                z[k] = v * id2;
+            }
+            __syncthreads();
+        };
+        apply(x, Ap);
+        double rr = 0.0, bb = 0.0;
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            r[k] = b[k] - Ap[k];
+            p[k] = r[k];
+            rr += r[k] * r[k];
+            bb += b[k] * b[k];
+        }
+        rr = block_sum(rr);
+        bb = block_sum(bb);
+        int it = 0;
+        const double tol = 1e-26 * (bb > 0.0 ? bb : 1.0);
+        while (rr > tol && it < 20000) {
+            apply(p, Ap);
+            double pAp = 0.0;
+            for (int k = threadIdx.x; k < m; k += blockDim.x) pAp += p[k] * Ap[k];
+            pAp = block_sum(pAp);
+            const double al = rr / pAp;
+            double rn = 0.0;
+            for (int k = threadIdx.x; k < m; k += blockDim.x) {
+                x[k] += al * p[k];
+                r[k] -= al * Ap[k];
+                rn += r[k] * r[k];
+            }
+            rn = block_sum(rn);
+            const double be = rn / rr;
+            rr = rn;
+            for (int k = threadIdx.x; k < m; k += blockDim.x) p[k] = r[k] + be * p[k];
+            __syncthreads();
+            ++it;
+        }
+        if (threadIdx.x == 0) cg_steps[a] = it;
+    }
+    // interior cells: the solved U; everything else keeps U^(k+1/2) (solid cells hold zero)
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) dU[a * ncell + c] = 0.0;
+    __syncthreads();
+    if (P.sis)
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            const int c = inner[k];
+            dU[a * ncell + c] = x[k] - M(a, c, 0);
+        }
+    __syncthreads();
+    double sU = 0.0, sq = 0.0;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const double dd = dU[a * ncell + c];
+        const double Uc = M(a, c, 0) + dd * P.cU[a];
+        Uout[a * ncell + c] = Uc;
+        sU += Uc;
+        sq += M(a, c, 1) + dd * P.cq[a];
+    }
+    sU = block_sum(sU);
+    sq = block_sum(sq);
+    if (threadIdx.x == 0) {
+        rates[a] = P.sqm * sU / ncell;
+        rates[2 + a] = P.sqm * sq / ncell;
+    }
+}
+
+// y = x (float to double), the porous sweep's lag state when the iteration leaves float
+__global__ void k_mix_widen(const float* __restrict__ x, long n, double* __restrict__ y) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        y[t] = (double)x[t];
+}
+
 // y = a + s b over n values
 __global__ void k_mix_axpy(const double* __restrict__ a, double s, const double* __restrict__ b, long n,
                            double* __restrict__ y) {
@@ -1034,6 +1222,10 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     if (pb->precision != LBE_FP64 && pb->precision != LBE_DF32 && pb->precision != LBE_BF16 &&
         pb->precision != LBE_BF16_REFINED)
         return bad_arg(ctx, "mixture: precision FP64, DF32, BF16 or BF16_REFINED");
+    const bool porous = pb->solid_fraction > 0;
+    if (porous && (gm.dim != 2 || gm.nx != gm.ny || gm.nx < 4 || !(pb->solid_fraction < 0.78)))
+        return bad_arg(ctx, "mixture porous cell: ducts geometry with nx = ny >= 4 and 0 < solid_fraction < 0.78");
+    if (!(pb->solid_fraction >= 0)) return bad_arg(ctx, "mixture: solid_fraction >= 0");
     cudaSetDevice(ctx->device);
     cudaStream_t s = ctx->stream;
     const int dim = gm.dim, layout = dim == 1 ? 1 : 2;
@@ -1076,6 +1268,48 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
                 lm[(size_t)p * my + q] = -4.0 * sp * sp / (dx * dx) - 4.0 * sq * sq / (dy * dy);
             }
     }
+    // the periodic unit cell: solid cells, interior cells of the correction and their neighbours
+    PorousDev PG{};
+    std::vector<unsigned char> solid;
+    std::vector<int> inner, nbl;
+    if (porous) {
+        const int nn = gm.nx;
+        const double d = 1.0 / nn, R2 = pb->solid_fraction / M_PI;
+        solid.assign((size_t)nn * nn, 0);
+        for (int i = 0; i < nn; ++i)
+            for (int j = 0; j < nn; ++j) {
+                const double x = (i + 0.5) * d - 0.5, y = (j + 0.5) * d - 0.5;
+                solid[(size_t)i * nn + j] = x * x + y * y < R2;
+            }
+        auto fl = [&](int i, int j) { return !solid[(size_t)((i + nn) % nn) * nn + (j + nn) % nn]; };
+        std::vector<int> kof((size_t)nn * nn, -1);
+        for (int i = 0; i < nn; ++i)
+            for (int j = 0; j < nn; ++j) {
+                bool in = fl(i, j);
+                for (int di = -1; di <= 1; ++di)
+                    for (int dj = -1; dj <= 1; ++dj) in = in && fl(i + di, j + dj);
+                if (in) kof[(size_t)i * nn + j] = (int)inner.size(), inner.push_back(i * nn + j);
+            }
+        for (int c : inner) {
+            const int i = c / nn, j = c % nn;
+            const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+            for (int e = 0; e < 4; ++e) {
+                const int cc = ((i + di[e] + nn) % nn) * nn + (j + dj[e] + nn) % nn;
+                nbl.push_back(kof[cc] >= 0 ? kof[cc] : -1 - cc);
+            }
+        }
+        // three-point backward differences (Lagrange) on nodes x0 - h1 - h2, x0 - h1, x0
+        auto bw = [](double h1, double h2, double* a, double* b, double* c) {
+            *a = (2.0 * h1 + h2) / (h1 * (h1 + h2));
+            *b = -(h1 + h2) / (h1 * h2);
+            *c = h1 / (h2 * (h1 + h2));
+        };
+        double cdum;
+        PG.n = nn;
+        bw(d, d, &PG.ua, &PG.ub, &PG.uc);
+        PG.w1a = 2.0 / d;
+        bw(d, 0.5 * d, &PG.w2a, &PG.w2b, &cdum);
+    }
     MixSisDev P{};
     for (int a = 0; a < 2; ++a) {
         P.r[a] = o->r[a];
@@ -1104,7 +1338,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     job.delta = pb->delta;
     // device workspace
     const size_t b_state = sizeof(double) * 2 * per;
-    const size_t n_work = dim == 2 ? 4 * (size_t)(gm.nx - 2) * (gm.ny - 2) : 0;
+    const size_t n_work = porous ? 10 * inner.size() + 2 : (dim == 2 ? 4 * (size_t)(gm.nx - 2) * (gm.ny - 2) : 0);
     const size_t b_small = sizeof(double) * (2 * kMom * n + 4 * n + 8 + n_work) +
                            sizeof(double) * (coef.size() + geov.size());
     void *d_h = nullptr, *d_hh = nullptr, *d_lp = nullptr, *d_small = nullptr, *d_job = nullptr;
@@ -1128,6 +1362,13 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     }
     take(&d_small, b_small);
     take(&d_job, sizeof job);
+    void* d_por = nullptr;
+    const size_t b_por = porous ? solid.size() + sizeof(int) * (inner.size() + nbl.size() + 2) + 64 : 0;
+    if (porous) take(&d_por, b_por);
+    unsigned char* dsolid = (unsigned char*)d_por;
+    int* dinner = porous ? (int*)(((uintptr_t)d_por + solid.size() + 15) / 16 * 16) : nullptr;
+    int* dnb = porous ? dinner + inner.size() : nullptr;
+    int* dcg = porous ? dnb + nbl.size() : nullptr;
     double* h = (double*)d_h;
     double* hh = (double*)d_hh;
     double* lp = (double*)d_lp;
@@ -1163,11 +1404,20 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
             float* hh32 = (float*)d_hh32;
             e = mix_tc_apply(ctx, o->tc, n, hin, hin + per, n3, o->nr, pb->delta, lp32, lp32 + per, true, s);
             if (e != LBE_OK) return e;
-            for (int a = 0; a < 2; ++a)
-                launch_sweep<float>(homog ? o->tab0[a] : o->tab[a], dim, 1, (int)coef.size(), lp32 + a * per,
-                                    hh32 + a * per, (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
+            for (int a = 0; a < 2; ++a) {
+                const DevTables& tb = homog ? o->tab0[a] : o->tab[a];
+                if (porous)
+                    k_mix_sweep_porous<float><<<(N * N * (N / 2) + 127) / 128, 128, 0, s>>>(
+                        lp32 + a * per, hh32 + a * per, tb.nu1_f, tb.vel_f, tb.feq_f, dsolid, PG, N, pb->delta);
+                else
+                    launch_sweep<float>(tb, dim, 1, (int)coef.size(), lp32 + a * per, hh32 + a * per,
+                                        (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
+            }
             k_mix_moments<float><<<dim3(n, 2), 256, 0, s>>>(Q, hh32, hin, lp32, o->nu, o->vel, mom);
-            if (dim == 1)
+            if (porous)
+                k_mix_poisson_porous<<<2, 1024, 0, s>>>(Q, PG, mom, dinner, dnb, (int)inner.size(), dwork, dU, Uc,
+                                                        rates, dcg);
+            else if (dim == 1)
                 k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
             else
                 k_mix_poisson2d<<<2, 512, 0, s>>>(Q, D, mom, dSx, dSy, dlam, dwork, dU, Uc, rates);
@@ -1175,11 +1425,20 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
         } else {
             e = mix_gemm(ctx, *o, hin, hin + per, n3, n, pb->delta, lp, lp + per, s, dfg);
             if (e != LBE_OK) return e;
-            for (int a = 0; a < 2; ++a)
-                launch_sweep<double>(homog ? o->tab0[a] : o->tab[a], dim, 1, (int)coef.size(), lp + a * per,
-                                     hh + a * per, (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
+            for (int a = 0; a < 2; ++a) {
+                const DevTables& tb = homog ? o->tab0[a] : o->tab[a];
+                if (porous)
+                    k_mix_sweep_porous<double><<<(N * N * (N / 2) + 127) / 128, 128, 0, s>>>(
+                        lp + a * per, hh + a * per, tb.nu1_d, tb.vel_d, tb.feq_d, dsolid, PG, N, pb->delta);
+                else
+                    launch_sweep<double>(tb, dim, 1, (int)coef.size(), lp + a * per, hh + a * per,
+                                         (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
+            }
             k_mix_moments<double><<<dim3(n, 2), 256, 0, s>>>(Q, hh, hin, lp, o->nu, o->vel, mom);
-            if (dim == 1)
+            if (porous)
+                k_mix_poisson_porous<<<2, 1024, 0, s>>>(Q, PG, mom, dinner, dnb, (int)inner.size(), dwork, dU, Uc,
+                                                        rates, dcg);
+            else if (dim == 1)
                 k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
             else
                 k_mix_poisson2d<<<2, 512, 0, s>>>(Q, D, mom, dSx, dSy, dlam, dwork, dU, Uc, rates);
@@ -1203,8 +1462,17 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     };
     if (st == LBE_OK) {
         cudaMemsetAsync(h, 0, b_state, s);
+        cudaMemsetAsync(hh, 0, b_state, s);  // the porous sweep's periodic inflow starts from zero
         for (void* q : {d_hp, d_e, d_x, d_d})
             if (q) cudaMemsetAsync(q, 0, b_state, s);
+        for (void* q : {d_lp32, d_hh32})
+            if (q) cudaMemsetAsync(q, 0, b_state / 2, s);
+        if (porous) {
+            cudaMemcpyAsync(dsolid, solid.data(), solid.size(), cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(dinner, inner.data(), sizeof(int) * inner.size(), cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(dnb, nbl.data(), sizeof(int) * nbl.size(), cudaMemcpyHostToDevice, s);
+            g_h2d += solid.size() + sizeof(int) * (inner.size() + nbl.size());
+        }
         cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(dgeo, geov.data(), sizeof(double) * geov.size(), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_job, &job, sizeof job, cudaMemcpyHostToDevice, s);
@@ -1226,11 +1494,19 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
                 same = same && dk < pb->eps * (lo ? scale : std::fabs(hr[k]));
                 old[k] = hr[k];
             }
-            if (refined) {
+            if (refined && lo) {
                 // hand over at the floor: changes below 1e-5 of the scale, or no longer shrinking
                 rising = change >= prev ? rising + 1 : 0;
                 prev = change;
-                if (change < 1e-5 * scale || rising >= 3) break;
+                if (change < 1e-5 * scale || rising >= 3) {
+                    if (!porous) break;
+                    // the porous sweep's state includes its last half step (the periodic lag),
+                    // which a correction of h alone would leave behind: continue with plain
+                    // FP64-class iterations from the float half step instead
+                    lo = false;
+                    k_mix_widen<<<grid_for(2 * per), 256, 0, s>>>((const float*)d_hh32, 2 * per, hh);
+                    g_launches += 1;
+                }
                 continue;
             }
             if (same) {
@@ -1247,7 +1523,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
         double* ev = (double*)d_e;
         double* xv = (double*)d_x;
         double* dv = (double*)d_d;
-        while (refined && st == LBE_OK && !bad && it < pb->max_iter) {
+        while (refined && !porous && st == LBE_OK && !bad && it < pb->max_iter) {
             if ((st = step(h, hp, false, false, hr)) != LBE_OK || bad) break;
             bool same = pb->eps > 0;
             for (int k = 0; k < 4; ++k) same = same && std::fabs(hr[k] - old[k]) < pb->eps * std::fabs(hr[k]);
@@ -1276,12 +1552,15 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
             axpy(hp, 1.0, ev, h);
             for (int k = 0; k < 4; ++k) old[k] = hr[k] + re[k];
         }
-        if (refined && st == LBE_OK && !bad) {
+        if (refined && !porous && st == LBE_OK && !bad) {
             // U and the flow rates of the returned h
             MixSisDev Q = P;
             Q.sis = 0;
             k_mix_moments<double><<<dim3(n, 2), 256, 0, s>>>(Q, h, h, lp, o->nu, o->vel, mom);
-            if (dim == 1)
+            if (porous)
+                k_mix_poisson_porous<<<2, 1024, 0, s>>>(Q, PG, mom, dinner, dnb, (int)inner.size(), dwork, dU, Uc,
+                                                        rates, dcg);
+            else if (dim == 1)
                 k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
             else
                 k_mix_poisson2d<<<2, 512, 0, s>>>(Q, D, mom, dSx, dSy, dlam, dwork, dU, Uc, rates);
@@ -1321,6 +1600,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
         if (q) dev_free(ctx, q, b_state);
     for (void* q : {d_lp32, d_hh32})
         if (q) dev_free(ctx, q, b_state / 2);
+    if (d_por) dev_free(ctx, d_por, b_por);
     out->M_A = hr[0];
     out->M_B = hr[1];
     out->Q_A = hr[2];

@@ -43,7 +43,7 @@ class MixProblem(C.Structure):
     _fields_ = [("mix", Mixture), ("geom", Geometry), ("delta", C.c_double),
                 ("N_A", C.c_double), ("N_B", C.c_double), ("nv", C.c_int), ("vmax", C.c_double),
                 ("M", C.c_int), ("R", C.c_double), ("scheme", C.c_int), ("eps", C.c_double),
-                ("max_iter", C.c_int), ("precision", C.c_int)]
+                ("max_iter", C.c_int), ("precision", C.c_int), ("solid_fraction", C.c_double)]
 
 
 class MixResult(C.Structure):
@@ -54,10 +54,10 @@ class MixResult(C.Structure):
 
 def mix_problem(mass_ratio, diam_ratio, chi_A, delta=1.0, ns=20, grid_kind=0, N_A=0.0, N_B=0.0, nv=16,
                 vmax=6.0, M=16, R=4.5, scheme=SIS, eps=1e-8, max_iter=500, precision=FP64, dim=1, nx=0, ny=0,
-                width=1.0):
+                width=1.0, solid=0.0):
     geom = Geometry(dim, ns if dim == 1 else 0, grid_kind if dim == 1 else 0, nx, ny, width)
     return MixProblem(Mixture(mass_ratio, diam_ratio, chi_A), geom, delta, N_A, N_B, nv, vmax, M, R,
-                      scheme, eps, max_iter, precision)
+                      scheme, eps, max_iter, precision, solid)
 
 
 def mix_cells(pb):

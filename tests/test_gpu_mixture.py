@@ -288,3 +288,41 @@ def test_mixture_edge_cases_and_oom(ctx):
         assert info[0] > 0
     finally:
         small.close()
+
+
+@pytest.mark.parametrize("scheme", ["sis", "cis"])
+def test_mixture_porous_cell_matches_oracle(ctx, oracle8, scheme):
+    """The periodic unit cell with a cylinder (10 x 10 cells): the in-place periodic sweep, the
+    conjugate-gradient correction on the interior cells, against the oracle's loops and dense
+    solve."""
+    from paper_1612_04488_gb300 import lbe
+    iters = 4
+    kw = dict(delta=3.0, nv=8, vmax=5.0, M=8, R=3.75, eps=0.0, max_iter=iters)
+    run = mx.MixRun(mx.MixProblem(NE_AR[0], NE_AR[1], 0.5, scheme=scheme, dim=2, nx=10, ny=10, solid=0.4, **kw),
+                    F=oracle8)
+    for _ in range(iters):
+        rates = run.step()
+    pb = lbe.mix_problem(NE_AR[0], NE_AR[1], 0.5, scheme=lbe.SIS if scheme == "sis" else lbe.CIS, dim=2, nx=10,
+                         ny=10, solid=0.4, **kw)
+    res, U, h = ctx.mix_solve(pb, want_h=True)
+    got = np.array([res.M_A, res.M_B, res.Q_A, res.Q_B])
+    assert np.max(np.abs(got - rates) / np.abs(rates)) < 1e-10
+    for a in range(2):
+        ref_U = run.U[a].reshape(-1)
+        assert np.max(np.abs(U[a] - ref_U)) < 1e-10 * np.max(np.abs(ref_U))
+        ref_h = run.h[a].reshape((-1,) + run.h[a].shape[2:])
+        assert np.max(np.abs(h[a] - ref_h)) < 1e-10 * np.max(np.abs(ref_h))
+
+
+def test_mixture_porous_refined_reaches_fp64(ctx):
+    from paper_1612_04488_gb300 import lbe
+    kw = dict(delta=3.0, nv=16, vmax=5.0, M=16, R=3.75, max_iter=600, dim=2, nx=16, ny=16, solid=0.4, eps=1e-10)
+    r64, U, _ = ctx.mix_solve(lbe.mix_problem(*NE_AR, 0.5, **kw))
+    rr, _, _ = ctx.mix_solve(lbe.mix_problem(*NE_AR, 0.5, precision=lbe.BF16_REFINED, **kw), want_U=False)
+    assert r64.status == rr.status == lbe.OK
+    a = np.array([r64.M_A, r64.M_B, r64.Q_A, r64.Q_B])
+    b = np.array([rr.M_A, rr.M_B, rr.Q_A, rr.Q_B])
+    assert np.max(np.abs(b - a) / np.abs(a)) < 1e-8, (a, b)
+    assert rr.fp64_iters < r64.iters, (rr.fp64_iters, r64.iters)
+    Ug = U[0].reshape(16, 16)
+    assert np.max(np.abs(Ug - Ug[::-1, :])) < 1e-8 * np.max(np.abs(Ug))

@@ -170,3 +170,38 @@ def test_M8_2d_identical_species_cis_is_the_single_species_duct_cis():
         sp.step()
     for a, chi in ((0, 0.3), (1, 0.7)):
         assert np.max(np.abs(mr.h[a] - chi * sp.h)) < 1e-13 * np.max(np.abs(sp.h))
+
+
+def test_porous_sweep_exact_without_solids_and_geometry():
+    """The periodic sweep converges to the exact uniform solution h = rhs / nu when nothing is
+    solid; the staircase's solid area and the interior cells of the correction are as stated."""
+    F = fsm.FSM(8, 5.0, 8)
+    rng = np.random.default_rng(5)
+    nu = 0.5 + rng.random(F.V1.shape)
+    rhs = np.broadcast_to(rng.standard_normal(F.V1.shape), (6, 6) + F.V1.shape).copy()
+    solid = np.zeros((6, 6), dtype=bool)
+    h = np.zeros_like(rhs)
+    for _ in range(400):
+        h = mx.sweep_porous(rhs, nu, F.V1, F.V2, solid, h)
+    assert np.max(np.abs(h - rhs / nu)) < 1e-10 * np.max(np.abs(rhs / nu))
+    s = mx.porous_solid(100, 0.4)
+    assert abs(s.mean() - 0.4) < 0.01
+    inner = mx.porous_interior(s)
+    for di in (-1, 0, 1):
+        for dj in (-1, 0, 1):
+            assert not np.any(inner & np.roll(s, (-di, -dj), axis=(0, 1)))
+
+
+def test_porous_solution_is_symmetric():
+    """The converged flow in the unit cell has the cell's mirror and diagonal symmetries
+    (exactly: the periodic scheme does, whatever the sweep order), and the lighter species
+    flows faster."""
+    F = mx.MixFSM(mx.Mixture(*NE_AR, 0.5), 8, 5.0, 8, R=3.75)
+    kw = dict(delta=5.0, nv=8, vmax=5.0, M=8, R=3.75, eps=1e-11, max_iter=600, dim=2, nx=10, ny=10, solid=0.4)
+    run = mx.MixRun(mx.MixProblem(*NE_AR, 0.5, **kw), F=F)
+    assert run.solve()
+    for U in run.U:
+        s = np.max(np.abs(U))
+        for V in (U[::-1, :], U[:, ::-1], U.T):
+            assert np.max(np.abs(U - V)) < 1e-9 * s
+    assert run.rates[0] > run.rates[1] > 0.0
