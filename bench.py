@@ -354,6 +354,25 @@ def mixture_measure(lbe, torch, device, steps, warmup, nv=24, M=32, deltas=(1.0,
             "fp64_iters": dr.fp64_iters, "status": dr.status, "got": dgot, "table5": t5,
             "rel": [g / p - 1.0 for g, p in zip(dgot, t5)],
             "what": "square duct, 40 x 40 cells, delta = 10, BF16 refined, eps 1e-7"}
+    # the porous workload: the periodic unit cell of a square array of cylinders (solid fraction 0.4),
+    # 100 x 100 cells, d_B / d_A = 1 / 0.72, delta = 10; the low-precision solve and the refined one
+    por = {}
+    for tag, prec in (("bf16", lbe.BF16), ("refined", lbe.BF16_REFINED)):
+        ppb = lbe.mix_problem(MIX_NE_AR[0], 1.0 / 0.72, 0.5, delta=10.0, nv=nv, vmax=5.0, M=M, R=3.75, eps=1e-6,
+                              max_iter=400, precision=prec, dim=2, nx=100, ny=100, solid=0.4)
+        if tag == "bf16":
+            ctx.mix_solve(ppb, want_U=False)
+        pa, pbv = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pa.record(stream)
+        pr = ctx.mix_solve(ppb, want_U=False)[0]
+        pbv.record(stream)
+        pbv.synchronize()
+        por[tag] = {"solves_per_s": 1000.0 / pa.elapsed_time(pbv), "iters": pr.iters, "fp64_iters": pr.fp64_iters,
+                    "status": pr.status, "rates": [pr.M_A, pr.M_B, pr.Q_A, pr.Q_B]}
+    por["bf16_max_rel_vs_refined"] = max(abs(x / y - 1.0) for x, y in zip(por["bf16"]["rates"][:2],
+                                                                           por["refined"]["rates"][:2]))
+    por["what"] = ("periodic unit cell, centred cylinder of area 0.4 (staircase), 100 x 100 cells, Ne-Ar chi 0.5, "
+                   "d_B / d_A = 1 / 0.72, delta = 10, eps 1e-6")
     nsolve = len(pbs) * steps
     rel = max(abs(x / y - 1.0) for r, q in zip(rres, res)
               for x, y in ((r.M_A, q.M_A), (r.M_B, q.M_B), (r.Q_A, q.Q_A), (r.Q_B, q.Q_B)))
@@ -371,7 +390,7 @@ def mixture_measure(lbe, torch, device, steps, warmup, nv=24, M=32, deltas=(1.0,
                        "correction: FP64-class (double-float GEMM) iterations, the same 1e-8 stopping test, "
                        "whose errors are solved for by the source-free iteration on the tensor cores"}
     out = {"solves_per_s": nsolve / (ms / 1000.0), "ms_per_step": ms / steps, "build_s": build_s,
-           "refined": refined, "df32": df32, "duct": duct, "fp64_iters": [r.iters for r in res],
+           "refined": refined, "df32": df32, "duct": duct, "porous": por, "fp64_iters": [r.iters for r in res],
            "e2e": {"value": nsolve / wall, "unit": "solves/s",
                    "h2d_bytes_per_step": int((s1["h2d_bytes"] - s0["h2d_bytes"]) / steps),
                    "d2h_bytes_per_step": int((s1["d2h_bytes"] - s0["d2h_bytes"]) / steps)},
@@ -403,7 +422,7 @@ def run_mixture(args):
             "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": m["config"], "roofline": m["roofline"],
             "table4": m["table4"], "build_s": m["build_s"], "refined": m["refined"], "df32": m["df32"],
-            "duct": m["duct"],
+            "duct": m["duct"], "porous": m["porous"],
             "e2e": m["e2e"],
             "clocks": clk.summary(),
             "gpu_launches": m["gpu_launches"]}
@@ -806,7 +825,7 @@ def run_ours(args):
                              "status": dres[-1].status}
         mx = mixture_measure(lbe, torch, local, 1, 1)
         line["mixture"] = {k: mx[k] for k in ("solves_per_s", "config", "roofline", "table4", "build_s", "refined",
-                                              "df32", "duct")}
+                                              "df32", "duct", "porous")}
         sctx = lbe.Context(local)
         line["serving"] = serve_stream(sctx, lbe, prec, args.eps, args.requests)
         line["latency_ms"] = dict(line["serving"]["latency_ms"], workload=line["serving"]["workload"])
