@@ -395,9 +395,8 @@ typedef struct {
                           * iteration satisfies the periodic scheme), and the diffusion
                           * correction acts on the fluid cells whose eight neighbours are fluid
                           * (solved by conjugate gradients), the others held at the kinetic U.
-                          * The sweep's lag makes its last half step part of the iteration's
-                          * state, so LBE_BF16_REFINED continues there with plain FP64-class
-                          * iterations after the low-precision floor (no defect correction)     */
+                          * The sweep's lag makes its last half step g part of the iteration's
+                          * state; LBE_BF16_REFINED's correction then runs on the pair (h, g)   */
 } lbe_mix_problem;
 
 typedef struct {

@@ -759,6 +759,16 @@ __global__ void k_mix_widen(const float* __restrict__ x, long n, double* __restr
         y[t] = (double)x[t];
 }
 
+// x += y (float state plus a double increment), y += x (double plus float)
+__global__ void k_mix_add_fd(float* __restrict__ x, const double* __restrict__ y, long n) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        x[t] = (float)((double)x[t] + y[t]);
+}
+__global__ void k_mix_add_df(double* __restrict__ y, const float* __restrict__ x, long n) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        y[t] += (double)x[t];
+}
+
 // y = a + s b over n values
 __global__ void k_mix_axpy(const double* __restrict__ a, double s, const double* __restrict__ b, long n,
                            double* __restrict__ y) {
@@ -1354,11 +1364,16 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     take(&d_h, b_state);
     take(&d_hh, b_state);
     take(&d_lp, b_state);
+    void *d_gs = nullptr, *d_dg = nullptr;  // porous: the lag state before the FP64 step, its change
     if (refined) {
         take(&d_hp, b_state);
         take(&d_e, b_state);
         take(&d_x, b_state);
         take(&d_d, b_state);
+        if (porous) {
+            take(&d_gs, b_state);
+            take(&d_dg, b_state);
+        }
     }
     take(&d_small, b_small);
     take(&d_job, sizeof job);
@@ -1499,13 +1514,11 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
                 rising = change >= prev ? rising + 1 : 0;
                 prev = change;
                 if (change < 1e-5 * scale || rising >= 3) {
-                    if (!porous) break;
-                    // the porous sweep's state includes its last half step (the periodic lag),
-                    // which a correction of h alone would leave behind: continue with plain
-                    // FP64-class iterations from the float half step instead
-                    lo = false;
-                    k_mix_widen<<<grid_for(2 * per), 256, 0, s>>>((const float*)d_hh32, 2 * per, hh);
-                    g_launches += 1;
+                    if (porous) {  // the FP64 lag state starts from the float half step
+                        k_mix_widen<<<grid_for(2 * per), 256, 0, s>>>((const float*)d_hh32, 2 * per, hh);
+                        g_launches += 1;
+                    }
+                    break;
                 }
                 continue;
             }
@@ -1523,7 +1536,14 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
         double* ev = (double*)d_e;
         double* xv = (double*)d_x;
         double* dv = (double*)d_d;
-        while (refined && !porous && st == LBE_OK && !bad && it < pb->max_iter) {
+        // The porous sweep's last half step g (its periodic lag) is part of the iteration's state:
+        // the map is affine on the pair (h, g), and the same correction runs on pairs, with
+        // d_g = g' - g and e_g carried in the float lag buffer of the inner iterations.
+        float* hh32f = (float*)d_hh32;
+        double* gs = (double*)d_gs;
+        double* dg = (double*)d_dg;
+        while (refined && st == LBE_OK && !bad && it < pb->max_iter) {
+            if (porous) cudaMemcpyAsync(gs, hh, b_state, cudaMemcpyDeviceToDevice, s);
             if ((st = step(h, hp, false, false, hr)) != LBE_OK || bad) break;
             bool same = pb->eps > 0;
             for (int k = 0; k < 4; ++k) same = same && std::fabs(hr[k] - old[k]) < pb->eps * std::fabs(hr[k]);
@@ -1534,11 +1554,19 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
             }
             axpy(hp, -1.0, h, dv);
             cudaMemsetAsync(ev, 0, b_state, s);
+            if (porous) {
+                axpy(hh, -1.0, gs, dg);                       // d_g = g' - g
+                cudaMemsetAsync(hh32f, 0, b_state / 2, s);    // e_g = 0
+            }
             double re[4] = {0, 0, 0, 0};
             double pe = 1e300;
             int up = 0;
             for (int j = 0; j < 200 && it < pb->max_iter; ++j) {
                 axpy(ev, 1.0, dv, xv);
+                if (porous) {  // the sweep's lag input e_g + d_g; its output is the next e_g
+                    k_mix_add_fd<<<grid_for(2 * per), 256, 0, s>>>(hh32f, dg, 2 * per);
+                    g_launches += 1;
+                }
                 double r[4];
                 if ((st = step(xv, ev, true, true, r)) != LBE_OK || bad) break;
                 double change = 0.0;
@@ -1550,9 +1578,13 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
             }
             if (st != LBE_OK || bad) break;
             axpy(hp, 1.0, ev, h);
+            if (porous) {  // g = g' + e_g
+                k_mix_add_df<<<grid_for(2 * per), 256, 0, s>>>(hh, hh32f, 2 * per);
+                g_launches += 1;
+            }
             for (int k = 0; k < 4; ++k) old[k] = hr[k] + re[k];
         }
-        if (refined && !porous && st == LBE_OK && !bad) {
+        if (refined && st == LBE_OK && !bad) {
             // U and the flow rates of the returned h
             MixSisDev Q = P;
             Q.sis = 0;
@@ -1596,7 +1628,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     dev_free(ctx, d_lp, b_state);
     dev_free(ctx, d_small, b_small);
     dev_free(ctx, d_job, sizeof job);
-    for (void* q : {d_hp, d_e, d_x, d_d})
+    for (void* q : {d_hp, d_e, d_x, d_d, d_gs, d_dg})
         if (q) dev_free(ctx, q, b_state);
     for (void* q : {d_lp32, d_hh32})
         if (q) dev_free(ctx, q, b_state / 2);

@@ -323,6 +323,6 @@ def test_mixture_porous_refined_reaches_fp64(ctx):
     a = np.array([r64.M_A, r64.M_B, r64.Q_A, r64.Q_B])
     b = np.array([rr.M_A, rr.M_B, rr.Q_A, rr.Q_B])
     assert np.max(np.abs(b - a) / np.abs(a)) < 1e-8, (a, b)
-    assert rr.fp64_iters < r64.iters, (rr.fp64_iters, r64.iters)
+    assert rr.fp64_iters <= r64.iters // 4, (rr.fp64_iters, r64.iters)
     Ug = U[0].reshape(16, 16)
     assert np.max(np.abs(Ug - Ug[::-1, :])) < 1e-8 * np.max(np.abs(Ug))
