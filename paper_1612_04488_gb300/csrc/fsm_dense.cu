@@ -1748,18 +1748,18 @@ __global__ void k_mix_store_bf16(const double* __restrict__ L, int n, int np, __
 }
 
 // x2: [cells][np] columns as hi / lo pairs (k even): column k < nr is h_A[c cs + k], nr <= k < 2 nr
-// is h_B[c cs + k - nr], the rest zero
+// is h_B[c cs + k - nr], the rest zero; c = map[n] for GEMM column n when a cell list is given
 __global__ void k_mix_gather(const double* __restrict__ hA, const double* __restrict__ hB, long cs, int nr, int np,
-                             int cells, __nv_bfloat162* __restrict__ x2) {
+                             int cells, __nv_bfloat162* __restrict__ x2, const int* __restrict__ map) {
     const int half = np / 2;
     const long total = (long)cells * half;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const long c = t / half;
+        const long c = t / half, src = map ? map[c] : c;
         const int k = 2 * (int)(t - c * half);
         double v[2];
         for (int u = 0; u < 2; ++u) {
             const int kk = k + u;
-            v[u] = kk < nr ? hA[c * cs + kk] : (kk < 2 * nr ? hB[c * cs + kk - nr] : 0.0);
+            v[u] = kk < nr ? hA[src * cs + kk] : (kk < 2 * nr ? hB[src * cs + kk - nr] : 0.0);
         }
         const __nv_bfloat16 h0 = __float2bfloat16_rn((float)v[0]), h1 = __float2bfloat16_rn((float)v[1]);
         const __nv_bfloat16 l0 = __float2bfloat16_rn((float)(v[0] - (double)__bfloat162float(h0)));
@@ -1770,15 +1770,15 @@ __global__ void k_mix_gather(const double* __restrict__ hA, const double* __rest
     }
 }
 
-// y_a[c cs + j] = scale Y[c mrows + a nr + j]
+// y_a[c cs + j] = scale Y[n mrows + a nr + j], c = n or map[n]
 template <typename T>
 __global__ void k_mix_readback(const float* __restrict__ Y, int mrows, int nr, int cells, long cs, double scale,
-                               T* __restrict__ yA, T* __restrict__ yB) {
+                               T* __restrict__ yA, T* __restrict__ yB, const int* __restrict__ map) {
     const long total = (long)cells * 2 * nr;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const long c = t / (2 * nr);
+        const long c = t / (2 * nr), dst = map ? map[c] : c;
         const int r = (int)(t - c * 2 * nr);
-        (r < nr ? yA : yB)[c * cs + (r < nr ? r : r - nr)] = (T)(scale * (double)Y[c * mrows + r]);
+        (r < nr ? yA : yB)[dst * cs + (r < nr ? r : r - nr)] = (T)(scale * (double)Y[c * mrows + r]);
     }
 }
 
@@ -1820,22 +1820,23 @@ lbe_status mix_tc_build(Ctx* c, const double* L, int n, MixTc** out, cudaStream_
 }
 
 lbe_status mix_tc_apply(Ctx* c, MixTc* m, int cells, const double* hA, const double* hB, long cs, int nr,
-                        double scale, void* yA, void* yB, bool f32, cudaStream_t s) {
+                        double scale, void* yA, void* yB, bool f32, cudaStream_t s, const int* map) {
     std::lock_guard<std::mutex> lk(m->T.mu);
     float* Y = nullptr;
     const int np = m->d.L.npmax;
     lbe_status st = tc_gemm(c, m->T, m->d, nullptr, cells, s, false, nullptr, [&](__nv_bfloat162* x2, int) {
         const long tot = (long)cells * (np / 2);
         k_mix_gather<<<(int)std::min<long>((tot + 255) / 256, 32L * sm_count()), 256, 0, s>>>(hA, hB, cs, nr, np,
-                                                                                              cells, x2);
+                                                                                              cells, x2, map);
     }, &Y);
     if (st != LBE_OK) return st;
     const long tot = (long)cells * 2 * nr;
     const int gr = (int)std::min<long>((tot + 255) / 256, 32L * sm_count());
     if (f32)
-        k_mix_readback<float><<<gr, 256, 0, s>>>(Y, m->d.L.rows, nr, cells, cs, scale, (float*)yA, (float*)yB);
+        k_mix_readback<float><<<gr, 256, 0, s>>>(Y, m->d.L.rows, nr, cells, cs, scale, (float*)yA, (float*)yB, map);
     else
-        k_mix_readback<double><<<gr, 256, 0, s>>>(Y, m->d.L.rows, nr, cells, cs, scale, (double*)yA, (double*)yB);
+        k_mix_readback<double><<<gr, 256, 0, s>>>(Y, m->d.L.rows, nr, cells, cs, scale, (double*)yA, (double*)yB,
+                                                  map);
     g_launches += 3;
     cudaMemcpyAsync(m->T.err_host, m->T.err_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
     return cuda_status(c, cudaGetLastError(), "mixture tensor-core operator");

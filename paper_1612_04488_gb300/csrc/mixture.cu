@@ -179,14 +179,15 @@ __global__ void k_mix_store(double* __restrict__ L, const double2* __restrict__ 
 
 // FP64 GEMM of the mixture operator: for species a and cell n,
 //   y_a[n cs + j] = scale sum_{b, c} L[(a nr + j) 2nr + b nr + c] h_b[n cs + c].
-// 64 x 64 output tile per block, 4 x 4 per thread, K in slices of 16.
+// 64 x 64 output tile per block, 4 x 4 per thread, K in slices of 16.  With a cell list `map`
+// (may be null) GEMM column n is cell map[n], in h and in y (the porous cell's fluid cells).
 constexpr int kMT = 64, kNT = 64, kKT = 16;
 // With a K split (gridDim.z > 1) slice z covers k in [z kc, (z+1) kc) and writes its unscaled
 // partial sums to part[(z cells + cell) rows + row]; k_mix_reduce adds the slices in order.
 __global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, int nr, const double* __restrict__ hA,
                                                   const double* __restrict__ hB, long cs, int cells, double scale,
                                                   double* __restrict__ yA, double* __restrict__ yB, int kc,
-                                                  double* __restrict__ part) {
+                                                  double* __restrict__ part, const int* __restrict__ map) {
     __shared__ double As[kKT][kMT + 1];
     __shared__ double Bs[kKT][kNT + 1];
     const int rows = 2 * nr, K = 2 * nr;
@@ -211,7 +212,10 @@ __global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, 
             for (int q = 0; q < 4; ++q) {
                 const int gk = k0 + kq + q;
                 double v = 0.0;
-                if (gc < cells && gk < ke) v = gk < nr ? hA[gc * cs + gk] : hB[gc * cs + gk - nr];
+                if (gc < cells && gk < ke) {
+                    const long src = map ? map[gc] : gc;
+                    v = gk < nr ? hA[src * cs + gk] : hB[src * cs + gk - nr];
+                }
                 Bs[kq + q][cc] = v;
             }
         }
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int gc = cell0 + tx * 4 + q;
-            if (gc < cells) y[gc * cs + j] = scale * acc[i][q];
+            if (gc < cells) y[(long)(map ? map[gc] : gc) * cs + j] = scale * acc[i][q];
         }
     }
 }
@@ -264,10 +268,10 @@ __global__ void __launch_bounds__(256) k_mix_gemm(const double* __restrict__ L, 
 // X[cell][k] = both species' h of a cell as double-float pairs (once per GEMM, so the tiles read
 // float pairs and the GEMM does no FP64 arithmetic)
 __global__ void k_mix_h_to_df(const double* __restrict__ hA, const double* __restrict__ hB, long cs, int nr,
-                              int cells, float2* __restrict__ X) {
+                              int cells, float2* __restrict__ X, const int* __restrict__ map) {
     const long K = 2L * nr, total = K * cells;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const long c = t / K, k = t - c * K;
+        const long n = t / K, k = t - n * K, c = map ? map[n] : n;
         const dfloat d(k < nr ? hA[c * cs + k] : hB[c * cs + k - nr]);
         X[t] = make_float2(d.hi, d.lo);
     }
@@ -276,7 +280,7 @@ __global__ void k_mix_h_to_df(const double* __restrict__ hA, const double* __res
 __global__ void __launch_bounds__(256) k_mix_gemm_df(const float2* __restrict__ L, int nr,
                                                      const float2* __restrict__ X, long cs, int cells, double scale,
                                                      double* __restrict__ yA, double* __restrict__ yB, int kc,
-                                                     double* __restrict__ part) {
+                                                     double* __restrict__ part, const int* __restrict__ map) {
     __shared__ float2 As[kKT][kMT + 1];
     __shared__ float2 Bs[kKT][kNT + 1];
     const int rows = 2 * nr, K = 2 * nr;
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(256) k_mix_gemm_df(const float2* __restrict__ 
             if (part)
                 part[((long)blockIdx.z * cells + gc) * rows + gr] = v;
             else
-                (gr < nr ? yA : yB)[gc * cs + (gr < nr ? gr : gr - nr)] = scale * v;
+                (gr < nr ? yA : yB)[(long)(map ? map[gc] : gc) * cs + (gr < nr ? gr : gr - nr)] = scale * v;
         }
     }
 }
@@ -350,13 +354,13 @@ __global__ void k_mix_to_df(const double* __restrict__ L, long n, float2* __rest
 
 // y = scale * sum_z part[z] in slice order (deterministic)
 __global__ void k_mix_reduce(const double* __restrict__ part, int nsplit, int nr, int cells, long cs, double scale,
-                             double* __restrict__ yA, double* __restrict__ yB) {
+                             double* __restrict__ yA, double* __restrict__ yB, const int* __restrict__ map) {
     const long rows = 2L * nr, total = rows * cells;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
         const long gc = t / rows, gr = t - gc * rows;
         double v = 0.0;
         for (int z = 0; z < nsplit; ++z) v += part[((long)z * cells + gc) * rows + gr];
-        (gr < nr ? yA : yB)[gc * cs + (gr < nr ? gr : gr - nr)] = scale * v;
+        (gr < nr ? yA : yB)[(map ? map[gc] : gc) * cs + (gr < nr ? gr : gr - nr)] = scale * v;
     }
 }
 
@@ -580,52 +584,89 @@ struct PorousDev {
     double ua, ub, uc, w1a, w2a, w2b;
 };
 
-// One thread per velocity of the duct orbit layout (i1, i2, j3 < nv / 2): the cells in upwind
-// order of its (v1, v2) quadrant, rows in x2, cells in x1 (cell (i, j) at i n + j), in place in
-// h, so that a periodic neighbour not yet swept still holds the previous sweep's value; solid
-// cells are set to zero.  nu h + v1 dh/dx1 + v2 dh/dx2 = rhs + v3 feq (feq = 0: no source).
+// The two species' operands of one porous sweep (per species: L h, h, nu / delta, v, v3 feq).
 template <typename T>
-__global__ void __launch_bounds__(128) k_mix_sweep_porous(const T* __restrict__ rhs, T* __restrict__ h,
-                                                          const T* __restrict__ nu1, const T* __restrict__ vel,
-                                                          const T* __restrict__ feq,
-                                                          const unsigned char* __restrict__ solid, PorousDev G,
-                                                          int nv, double delta) {
-    const int H = nv / 2, q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nv * nv * H) return;
+struct PorousSweepArgs {
+    const T* rhs[2];
+    T* h[2];
+    const T* nu1[2];
+    const T* vel[2];
+    const T* feq[2];
+};
+
+constexpr int kPorousSweepWarps = 16;
+
+// nu h + v1 dh/dx1 + v2 dh/dx2 = rhs + v3 feq (feq = 0: no source) for every velocity of the duct
+// orbit layout (i1, i2, j3 < nv / 2), in place in h: the cells are taken in upwind order of the
+// velocity's (v1, v2) quadrant, so a periodic neighbour not yet swept still holds the previous
+// sweep's value; solid cells are set to zero.  In upwind coordinates (ii, jj) a cell depends on
+// (ii - 1, jj), (ii - 2, jj), (ii, jj - 1), (ii, jj - 2) of this sweep, and on wrapped
+// neighbours that lie on a later anti-diagonal ii + jj, so the anti-diagonals are swept in order
+// and the cells of one anti-diagonal in parallel: the values read are those of the sequential
+// row-by-row sweep.  Block: 32 consecutive velocities (lanes) of species blockIdx.y, its warps
+// taking the cells of each anti-diagonal in turn, a block barrier between anti-diagonals.
+template <typename T>
+__global__ void __launch_bounds__(32 * kPorousSweepWarps, 3) k_mix_sweep_porous(PorousSweepArgs<T> A,
+                                                                          const unsigned char* __restrict__ solid,
+                                                                          PorousDev G, int nv, double delta) {
+    const int H = nv / 2, sp = blockIdx.y, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int q = blockIdx.x * 32 + (threadIdx.x & 31);
+    const bool live = q < nv * nv * H;
     const long n3 = (long)nv * nv * nv;
-    const int i1 = q / (nv * H), i2 = q / H % nv, j3 = q % H;
+    const int i1 = live ? q / (nv * H) : 0, i2 = live ? q / H % nv : 0, j3 = live ? q % H : 0;
     const long vf = ((long)i1 * nv + i2) * nv + j3;
+    // species by selection, not by a runtime index into the parameter struct
+    const T* __restrict__ rhs = sp ? A.rhs[1] : A.rhs[0];
+    T* h = sp ? A.h[1] : A.h[0];
+    const T* vel = sp ? A.vel[1] : A.vel[0];
     const T v1 = vel[i1], v2 = vel[i2];
     const int s1 = v1 > T(0) ? 1 : -1, s2 = v2 > T(0) ? 1 : -1;
     const T u1 = v1 > T(0) ? v1 : -v1, u2 = v2 > T(0) ? v2 : -v2;
-    const T nu = (T)delta * nu1[vf], S = vel[j3] * feq[vf];
+    const T nu = (T)delta * (sp ? A.nu1[1] : A.nu1[0])[vf], S = vel[j3] * (sp ? A.feq[1] : A.feq[0])[vf];
     const int n = G.n;
     auto at = [&](int i, int j) -> long { return ((long)i * n + j) * n3 + q; };
-    for (int jj = 0; jj < n; ++jj) {
-        const int j = s2 > 0 ? jj : n - 1 - jj;
-        const int j1 = (j - s2 + n) % n, j2 = (j - 2 * s2 + 2 * n) % n;
-        for (int ii = 0; ii < n; ++ii) {
-            const int i = s1 > 0 ? ii : n - 1 - ii;
-            if (solid[i * n + j]) {
-                h[at(i, j)] = T(0);
-                continue;
+    for (int d = 0; d <= 2 * (n - 1); ++d) {
+        if (live)
+            for (int jj = (d > n - 1 ? d - (n - 1) : 0) + w; jj <= d && jj < n; jj += W) {
+                const int ii = d - jj;
+                const int j = s2 > 0 ? jj : n - 1 - jj, i = s1 > 0 ? ii : n - 1 - ii;
+                if (solid[i * n + j]) {
+                    h[at(i, j)] = T(0);
+                    continue;
+                }
+                const int j1 = (j - s2 + n) % n, j2 = (j - 2 * s2 + 2 * n) % n;
+                const int i1c = (i - s1 + n) % n, i2c = (i - 2 * s1 + 2 * n) % n;
+                T ax, bx, cx, ay, by, cy;
+                if (solid[i1c * n + j]) ax = (T)G.w1a, bx = T(0), cx = T(0);
+                else if (solid[i2c * n + j]) ax = (T)G.w2a, bx = (T)G.w2b, cx = T(0);
+                else ax = (T)G.ua, bx = (T)G.ub, cx = (T)G.uc;
+                if (solid[i * n + j1]) ay = (T)G.w1a, by = T(0), cy = T(0);
+                else if (solid[i * n + j2]) ay = (T)G.w2a, by = (T)G.w2b, cy = T(0);
+                else ay = (T)G.ua, by = (T)G.ub, cy = (T)G.uc;
+                T num = rhs[at(i, j)] + S;
+                if (bx != T(0)) num -= u1 * bx * h[at(i1c, j)];
+                if (cx != T(0)) num -= u1 * cx * h[at(i2c, j)];
+                if (by != T(0)) num -= u2 * by * h[at(i, j1)];
+                if (cy != T(0)) num -= u2 * cy * h[at(i, j2)];
+                h[at(i, j)] = num / (nu + u1 * ax + u2 * ay);
             }
-            const int i1c = (i - s1 + n) % n, i2c = (i - 2 * s1 + 2 * n) % n;
-            T ax, bx, cx, ay, by, cy;
-            if (solid[i1c * n + j]) ax = (T)G.w1a, bx = T(0), cx = T(0);
-            else if (solid[i2c * n + j]) ax = (T)G.w2a, bx = (T)G.w2b, cx = T(0);
-            else ax = (T)G.ua, bx = (T)G.ub, cx = (T)G.uc;
-            if (solid[i * n + j1]) ay = (T)G.w1a, by = T(0), cy = T(0);
-            else if (solid[i * n + j2]) ay = (T)G.w2a, by = (T)G.w2b, cy = T(0);
-            else ay = (T)G.ua, by = (T)G.ub, cy = (T)G.uc;
-            T num = rhs[at(i, j)] + S;
-            if (bx != T(0)) num -= u1 * bx * h[at(i1c, j)];
-            if (cx != T(0)) num -= u1 * cx * h[at(i2c, j)];
-            if (by != T(0)) num -= u2 * by * h[at(i, j1)];
-            if (cy != T(0)) num -= u2 * cy * h[at(i, j2)];
-            h[at(i, j)] = num / (nu + u1 * ax + u2 * ay);
-        }
+        __syncthreads();
     }
+}
+
+template <typename T>
+void launch_sweep_porous(const T* rhs, T* h, long per, const DevTables* tb, bool f32, const unsigned char* solid,
+                         const PorousDev& G, int nv, double delta, cudaStream_t s) {
+    PorousSweepArgs<T> A;
+    for (int a = 0; a < 2; ++a) {
+        A.rhs[a] = rhs + a * per;
+        A.h[a] = h + a * per;
+        A.nu1[a] = (const T*)(f32 ? (const void*)tb[a].nu1_f : (const void*)tb[a].nu1_d);
+        A.vel[a] = (const T*)(f32 ? (const void*)tb[a].vel_f : (const void*)tb[a].vel_d);
+        A.feq[a] = (const T*)(f32 ? (const void*)tb[a].feq_f : (const void*)tb[a].feq_d);
+    }
+    const int nq = nv * nv * (nv / 2);
+    k_mix_sweep_porous<T><<<dim3((nq + 31) / 32, 2), 32 * kPorousSweepWarps, 0, s>>>(A, solid, G, nv, delta);
 }
 
 // One block per species: Eqs. LBE2_true1 / LBE2_true2 on the m interior cells (fluid cells whose
@@ -1109,7 +1150,7 @@ int mix_split(long tiles, int K) {
 }
 
 lbe_status mix_gemm(Ctx* c, MixOp& o, const double* hA, const double* hB, long cs, int cells, double scale,
-                    double* yA, double* yB, cudaStream_t s, bool df = false) {
+                    double* yA, double* yB, cudaStream_t s, bool df = false, const int* map = nullptr) {
     if (df && !o.Ldf) {
         const long nn = 4L * o.nr * o.nr;
         lbe_status st = dev_alloc(c, (void**)&o.Ldf, sizeof(float2) * nn);
@@ -1144,15 +1185,16 @@ lbe_status mix_gemm(Ctx* c, MixOp& o, const double* hA, const double* hB, long c
             if (st != LBE_OK) return st;
             o.xdf_bytes = xb;
         }
-        k_mix_h_to_df<<<grid_for((long)K * cells), 256, 0, s>>>(hA, hB, cs, o.nr, cells, o.Xdf);
-        k_mix_gemm_df<<<g, 256, 0, s>>>(o.Ldf, o.nr, o.Xdf, cs, cells, scale, yA, yB, kc, S > 1 ? o.part : nullptr);
+        k_mix_h_to_df<<<grid_for((long)K * cells), 256, 0, s>>>(hA, hB, cs, o.nr, cells, o.Xdf, map);
+        k_mix_gemm_df<<<g, 256, 0, s>>>(o.Ldf, o.nr, o.Xdf, cs, cells, scale, yA, yB, kc, S > 1 ? o.part : nullptr,
+                                        map);
         g_launches += 1;
     }
     else
-        k_mix_gemm<<<g, 256, 0, s>>>(o.L, o.nr, hA, hB, cs, cells, scale, yA, yB, kc, S > 1 ? o.part : nullptr);
+        k_mix_gemm<<<g, 256, 0, s>>>(o.L, o.nr, hA, hB, cs, cells, scale, yA, yB, kc, S > 1 ? o.part : nullptr, map);
     g_launches += 1;
     if (S > 1) {
-        k_mix_reduce<<<grid_for((long)K * cells), 256, 0, s>>>(o.part, S, o.nr, cells, cs, scale, yA, yB);
+        k_mix_reduce<<<grid_for((long)K * cells), 256, 0, s>>>(o.part, S, o.nr, cells, cs, scale, yA, yB, map);
         g_launches += 1;
     }
     if (timed) {
@@ -1281,7 +1323,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     // the periodic unit cell: solid cells, interior cells of the correction and their neighbours
     PorousDev PG{};
     std::vector<unsigned char> solid;
-    std::vector<int> inner, nbl;
+    std::vector<int> inner, nbl, fluid;
     if (porous) {
         const int nn = gm.nx;
         const double d = 1.0 / nn, R2 = pb->solid_fraction / M_PI;
@@ -1292,6 +1334,9 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
                 solid[(size_t)i * nn + j] = x * x + y * y < R2;
             }
         auto fl = [&](int i, int j) { return !solid[(size_t)((i + nn) % nn) * nn + (j + nn) % nn]; };
+        // the operator's columns: fluid cells only (h and L h stay zero in solid cells)
+        for (int c = 0; c < nn * nn; ++c)
+            if (!solid[c]) fluid.push_back(c);
         std::vector<int> kof((size_t)nn * nn, -1);
         for (int i = 0; i < nn; ++i)
             for (int j = 0; j < nn; ++j) {
@@ -1378,12 +1423,15 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     take(&d_small, b_small);
     take(&d_job, sizeof job);
     void* d_por = nullptr;
-    const size_t b_por = porous ? solid.size() + sizeof(int) * (inner.size() + nbl.size() + 2) + 64 : 0;
+    const size_t b_por = porous ? solid.size() + sizeof(int) * (inner.size() + nbl.size() + fluid.size() + 2) + 64 : 0;
     if (porous) take(&d_por, b_por);
     unsigned char* dsolid = (unsigned char*)d_por;
     int* dinner = porous ? (int*)(((uintptr_t)d_por + solid.size() + 15) / 16 * 16) : nullptr;
     int* dnb = porous ? dinner + inner.size() : nullptr;
-    int* dcg = porous ? dnb + nbl.size() : nullptr;
+    int* dfluid = porous ? dnb + nbl.size() : nullptr;
+    int* dcg = porous ? dfluid + fluid.size() : nullptr;
+    // operator columns: all cells, or the porous cell's fluid cells through the list dfluid
+    const int ncol = porous ? (int)fluid.size() : n;
     double* h = (double*)d_h;
     double* hh = (double*)d_hh;
     double* lp = (double*)d_lp;
@@ -1417,17 +1465,18 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
             // low precision: the tensor-core operator read back as float, float sweeps, FP64 state
             float* lp32 = (float*)d_lp32;
             float* hh32 = (float*)d_hh32;
-            e = mix_tc_apply(ctx, o->tc, n, hin, hin + per, n3, o->nr, pb->delta, lp32, lp32 + per, true, s);
+            e = mix_tc_apply(ctx, o->tc, ncol, hin, hin + per, n3, o->nr, pb->delta, lp32, lp32 + per, true, s,
+                             dfluid);
             if (e != LBE_OK) return e;
-            for (int a = 0; a < 2; ++a) {
-                const DevTables& tb = homog ? o->tab0[a] : o->tab[a];
-                if (porous)
-                    k_mix_sweep_porous<float><<<(N * N * (N / 2) + 127) / 128, 128, 0, s>>>(
-                        lp32 + a * per, hh32 + a * per, tb.nu1_f, tb.vel_f, tb.feq_f, dsolid, PG, N, pb->delta);
-                else
+            if (porous)
+                launch_sweep_porous<float>(lp32, hh32, per, homog ? o->tab0 : o->tab, true, dsolid, PG, N,
+                                           pb->delta, s);
+            else
+                for (int a = 0; a < 2; ++a) {
+                    const DevTables& tb = homog ? o->tab0[a] : o->tab[a];
                     launch_sweep<float>(tb, dim, 1, (int)coef.size(), lp32 + a * per, hh32 + a * per,
                                         (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
-            }
+                }
             k_mix_moments<float><<<dim3(n, 2), 256, 0, s>>>(Q, hh32, hin, lp32, o->nu, o->vel, mom);
             if (porous)
                 k_mix_poisson_porous<<<2, 1024, 0, s>>>(Q, PG, mom, dinner, dnb, (int)inner.size(), dwork, dU, Uc,
@@ -1438,17 +1487,17 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
                 k_mix_poisson2d<<<2, 512, 0, s>>>(Q, D, mom, dSx, dSy, dlam, dwork, dU, Uc, rates);
             k_mix_correct<float><<<grid_for(2L * n * nq), 256, 0, s>>>(Q, hh32, hout, dU, o->feq, o->vel);
         } else {
-            e = mix_gemm(ctx, *o, hin, hin + per, n3, n, pb->delta, lp, lp + per, s, dfg);
+            e = mix_gemm(ctx, *o, hin, hin + per, n3, ncol, pb->delta, lp, lp + per, s, dfg, dfluid);
             if (e != LBE_OK) return e;
-            for (int a = 0; a < 2; ++a) {
-                const DevTables& tb = homog ? o->tab0[a] : o->tab[a];
-                if (porous)
-                    k_mix_sweep_porous<double><<<(N * N * (N / 2) + 127) / 128, 128, 0, s>>>(
-                        lp + a * per, hh + a * per, tb.nu1_d, tb.vel_d, tb.feq_d, dsolid, PG, N, pb->delta);
-                else
+            if (porous)
+                launch_sweep_porous<double>(lp, hh, per, homog ? o->tab0 : o->tab, false, dsolid, PG, N,
+                                            pb->delta, s);
+            else
+                for (int a = 0; a < 2; ++a) {
+                    const DevTables& tb = homog ? o->tab0[a] : o->tab[a];
                     launch_sweep<double>(tb, dim, 1, (int)coef.size(), lp + a * per, hh + a * per,
                                          (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
-            }
+                }
             k_mix_moments<double><<<dim3(n, 2), 256, 0, s>>>(Q, hh, hin, lp, o->nu, o->vel, mom);
             if (porous)
                 k_mix_poisson_porous<<<2, 1024, 0, s>>>(Q, PG, mom, dinner, dnb, (int)inner.size(), dwork, dU, Uc,
@@ -1478,6 +1527,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
     if (st == LBE_OK) {
         cudaMemsetAsync(h, 0, b_state, s);
         cudaMemsetAsync(hh, 0, b_state, s);  // the porous sweep's periodic inflow starts from zero
+        cudaMemsetAsync(lp, 0, b_state, s);  // L h in solid cells, which the operator skips
         for (void* q : {d_hp, d_e, d_x, d_d})
             if (q) cudaMemsetAsync(q, 0, b_state, s);
         for (void* q : {d_lp32, d_hh32})
@@ -1486,7 +1536,8 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
             cudaMemcpyAsync(dsolid, solid.data(), solid.size(), cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(dinner, inner.data(), sizeof(int) * inner.size(), cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(dnb, nbl.data(), sizeof(int) * nbl.size(), cudaMemcpyHostToDevice, s);
-            g_h2d += solid.size() + sizeof(int) * (inner.size() + nbl.size());
+            cudaMemcpyAsync(dfluid, fluid.data(), sizeof(int) * fluid.size(), cudaMemcpyHostToDevice, s);
+            g_h2d += solid.size() + sizeof(int) * (inner.size() + nbl.size() + fluid.size());
         }
         cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(dgeo, geov.data(), sizeof(double) * geov.size(), cudaMemcpyHostToDevice, s);

@@ -22,12 +22,13 @@ lbe_status tc_check(Ctx* c, DevTables* t);
 void tc_release(Ctx* c, DevTables* t);
 // the binary-mixture operator on the tensor cores: the FP64 matrix L ([n][n], both species)
 // in BF16 hi / lo; apply: y_a = scale (L h) for cells whose unknowns are h_A, h_B at [c cs],
-// nr per species (float accumulation; y float with f32, else double); check reads the GEMM's
-// failure word after the stream's synchronisation
+// nr per species (float accumulation; y float with f32, else double), GEMM column n being cell
+// map[n] when a cell list is given; check reads the GEMM's failure word after the stream's
+// synchronisation
 struct MixTc;
 lbe_status mix_tc_build(Ctx* c, const double* L, int n, MixTc** out, cudaStream_t s);
 lbe_status mix_tc_apply(Ctx* c, MixTc* m, int cells, const double* hA, const double* hB, long cs, int nr,
-                        double scale, void* yA, void* yB, bool f32, cudaStream_t s);
+                        double scale, void* yA, void* yB, bool f32, cudaStream_t s, const int* map = nullptr);
 lbe_status mix_tc_check(Ctx* c, MixTc* m);
 void mix_tc_release(Ctx* c, MixTc* m);
 // refine.cu: BF16 operator inside an outer defect-correction loop
