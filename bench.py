@@ -26,6 +26,11 @@ the 134 MB of tensor-core operator blocks, well above L2 (129 MB).
   cpu_baseline  the FP64 oracle on a bounded sample of the same workload (extrapolated), on
             one core and on all host cores
 
+--workload mix_ne_ar24: the binary-mixture line (Ne-Ar plates, Table 4's setting: FP64, double-float
+and BF16-refined solves, the square duct and the porous cell).  --workload mix_porous100: the
+mixture in the periodic unit cell of a square array of cylinders (100 x 100 cells, porosity 0.6,
+delta in {1, 10}, BF16-refined), with the tensor-core GEMM of its operator against the bf16 peak.
+
 --impl reference times the oracle instead (the reference arm of this repository).
 Multi-GPU: replicas only (independent solves per rank), launched by torchrun.
 """
@@ -225,6 +230,11 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload.startswith("mix_"):
+        print(json.dumps({"impl": "reference", "unavailable": "the mixture oracle forms dense spectral matrices at "
+                                                              "N^6 M cost and runs at nv <= 12 only: no bounded "
+                                                              "sample of the 24^3 workload"}), flush=True)
+        return 0
     iters = args.ref_iters
     vals = []
     for _ in range(args.warmup):
@@ -409,6 +419,102 @@ def mixture_measure(lbe, torch, device, steps, warmup, nv=24, M=32, deltas=(1.0,
                       "grid": "clustered", "eps": 1e-8, "precision": "FP64"}}
     ctx.close()
     return out
+
+
+def porous_measure(lbe, torch, device, steps, warmup, nv=24, M=32, deltas=(1.0, 10.0), eps=1e-6, n=100):
+    """Binary mixture in the periodic unit cell of a square array of cylinders: n x n cells,
+    solid fraction 0.4 (porosity 0.6), Ne-Ar chi = 0.5, d_B / d_A = 1 / 0.72, 24^3, M = 32.
+    A step solves one problem per delta with LBE_BF16_REFINED to eps.  Also: the tensor-core
+    GEMM of the mixture operator timed by the library during a BF16 solve (the kernel the
+    low-precision iterations spend on), against the measured bf16 peak."""
+    stream = torch.cuda.Stream(device)
+    ctx = lbe.Context(device)
+    ctx.set_stream(stream.cuda_stream)
+
+    def mk(d, prec):
+        return lbe.mix_problem(MIX_NE_AR[0], 1.0 / 0.72, 0.5, delta=d, nv=nv, vmax=5.0, M=M, R=3.75, eps=eps,
+                               max_iter=400, precision=prec, dim=2, nx=n, ny=n, solid=0.4)
+
+    pbs = [mk(d, lbe.BF16_REFINED) for d in deltas]
+    t0 = time.perf_counter()
+    ctx.mix_info(pbs[0].mix, nv, 5.0, M, 3.75)
+    build_s = time.perf_counter() - t0
+    for _ in range(warmup):
+        for pb in pbs:
+            ctx.mix_solve(pb, want_U=False)
+    torch.cuda.synchronize()
+    s0 = lbe.stats()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    a.record(stream)
+    for _ in range(steps):
+        res = [ctx.mix_solve(pb, want_U=False)[0] for pb in pbs]
+    b.record(stream)
+    b.synchronize()
+    wall = time.perf_counter() - w0
+    s1 = lbe.stats()
+    ms = a.elapsed_time(b)
+    # the low-precision solve alone, with the tensor-core GEMM timed launch by launch
+    bpb = mk(deltas[-1], lbe.BF16)
+    lbe.set_kernel_timing(True)
+    g0 = lbe.stats()
+    br = ctx.mix_solve(bpb, want_U=False)[0]
+    g1 = lbe.stats()
+    lbe.set_kernel_timing(False)
+    n_t = g1["dense_gemm_timed"] - g0["dense_gemm_timed"]
+    ms_gemm = (g1["dense_gemm_ms"] - g0["dense_gemm_ms"]) / max(n_t, 1)
+    # the GEMM's columns: the fluid cells, those whose centre lies outside the circle of area 0.4
+    c = (np.arange(n) + 0.5) * (1.0 / n) - 0.5
+    fluid = int((c[:, None] ** 2 + c[None, :] ** 2 >= 0.4 / np.pi).sum())
+    rows = 2 * nv ** 3 // 2                      # both species, one value per duct orbit
+    flops = 2.0 * rows * rows * fluid           # the dense operator is the method's form
+    peaks = load_peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    achieved = flops / (ms_gemm / 1000.0) / 1e12
+    ref = res[-1]
+    rel = max(abs(x / y - 1.0) for x, y in ((br.M_A, ref.M_A), (br.M_B, ref.M_B)))
+    nsolve = len(pbs) * steps
+    out = {"solves_per_s": nsolve / (ms / 1000.0), "ms_per_step": ms / steps, "build_s": build_s,
+           "solves": [{"delta": d, "iters": r.iters, "fp64_iters": r.fp64_iters, "status": r.status,
+                       "rates": [r.M_A, r.M_B, r.Q_A, r.Q_B]} for d, r in zip(deltas, res)],
+           "bf16": {"delta": deltas[-1], "iters": br.iters, "status": br.status, "max_rel_vs_refined": rel},
+           "e2e": {"value": nsolve / wall, "unit": "solves/s",
+                   "h2d_bytes_per_step": int((s1["h2d_bytes"] - s0["h2d_bytes"]) / steps),
+                   "d2h_bytes_per_step": int((s1["d2h_bytes"] - s0["d2h_bytes"]) / steps)},
+           "gpu_launches": int(s1["kernel_launches"] - s0["kernel_launches"]),
+           "roofline": {"bound": "tensor", "kernel": "k_dense_gemm (mixture operator, BF16 hi/lo, %d x %d x %d fluid "
+                                                     "cells)" % (rows, rows, fluid),
+                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "peak_source": "bf16_tflops (burst, %s)" % peaks["_source"], "traffic": None,
+                        "timed_launches": int(n_t), "ms_per_launch": ms_gemm, "flops_per_launch": flops,
+                        "executed_flops_per_launch": 3.0 * flops,
+                        "algorithmic_unit": "2 (2 nv^3/2)^2 flops per fluid cell (one product of the dense "
+                                            "operator; the hi/lo split executes three)"},
+           "config": {"workload": "mix_porous%d" % n, "mixture": "Ne-Ar hard spheres, chi_Ne = 0.5, "
+                                                               "d_B / d_A = 1 / 0.72",
+                      "geometry": "periodic unit cell, centred cylinder of area 0.4 (staircase), %d x %d cells, "
+                                  "%d fluid" % (n, n, fluid),
+                      "deltas": list(deltas), "nv": nv, "M": M, "vmax": 5.0, "R": 3.75, "eps": eps,
+                      "precision": "BF16_REFINED",
+                      "l2": "inputs larger than L2 (h: %d MB in FP64)" % (n * n * nv ** 3 * 8 // 2 ** 20)}}
+    ctx.close()
+    return out
+
+
+def run_porous(args):
+    import torch
+    from paper_1612_04488_gb300 import lbe
+    torch.cuda.set_device(0)
+    with Clocks(0) as clk:
+        m = porous_measure(lbe, torch, 0, args.steps, args.warmup)
+    line = {"metric": "binary-mixture SIS solves/s at 1e-6 flow-rate change (porous unit cell)",
+            "value": m["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPES["bf16"], "data": "synthetic", "config": m["config"],
+            "roofline": m["roofline"], "solves": m["solves"], "bf16": m["bf16"], "build_s": m["build_s"],
+            "e2e": m["e2e"], "clocks": clk.summary(), "gpu_launches": m["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_mixture(args):
@@ -861,7 +967,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plates32x8", choices=["plates32x8", "plates16", "duct64x32",
-                                                                  "mix_ne_ar24"])
+                                                                  "mix_ne_ar24", "mix_porous100"])
     ap.add_argument("--precision", default="bf16", choices=sorted(PRECISIONS))
     ap.add_argument("--eps", type=float, default=1e-7)
     ap.add_argument("--ref-iters", type=int, default=35,
@@ -882,6 +988,8 @@ def main():
         return run_reference(args)
     if args.workload == "mix_ne_ar24":
         return run_mixture(args)
+    if args.workload == "mix_porous100":
+        return run_porous(args)
     if args.op_only:
         return run_op_only(args)
     return run_ours(args)

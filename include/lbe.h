@@ -293,11 +293,12 @@ lbe_status lbe_set_stream(lbe_ctx* ctx, void* stream);
  * bytes it copied host->device and device->host, and cells passed through the collision
  * operator (one cell = one application of L to one nv^3 vector).  With kernel timing on
  * (lbe_set_kernel_timing), every tensor-core GEMM launched by lbe_apply_L_sym, and every
- * FP64 GEMM of the mixture operator (lbe_mix_apply_L, lbe_mix_solve), is bracketed by CUDA
- * events on its stream: dense_gemm_timed counts those launches and dense_gemm_ms
- * sums their durations; and every transport-sweep launch of a solve (step A5, one launch per
- * geometry per iteration) likewise: sweep_timed, sweep_ms, and sweep_bytes, the algorithmic
- * bytes of those launches (right-hand side read and h written once per cell-velocity).
+ * GEMM of the mixture operator (lbe_mix_apply_L, lbe_mix_solve: FP64, double-float or on the
+ * tensor cores), is bracketed by CUDA events on its stream and waited for: dense_gemm_timed
+ * counts those launches and dense_gemm_ms sums their durations; and every transport-sweep
+ * launch of a solve (step A5, one launch per geometry per iteration) likewise: sweep_timed,
+ * sweep_ms, and sweep_bytes, the algorithmic bytes of those launches (right-hand side read
+ * and h written once per cell-velocity).
  * Reading the counters waits for the timed sweeps to finish. */
 typedef struct {
     uint64_t kernel_launches;

@@ -1824,11 +1824,23 @@ lbe_status mix_tc_apply(Ctx* c, MixTc* m, int cells, const double* hA, const dou
     std::lock_guard<std::mutex> lk(m->T.mu);
     float* Y = nullptr;
     const int np = m->d.L.npmax;
-    lbe_status st = tc_gemm(c, m->T, m->d, nullptr, cells, s, false, nullptr, [&](__nv_bfloat162* x2, int) {
+    // with kernel timing on, the GEMM is bracketed by events and waited for (lbe_get_stats)
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    const bool timed = g_time_kernels.load() != 0 && cudaEventCreate(&ev[0]) == cudaSuccess &&
+                       cudaEventCreate(&ev[1]) == cudaSuccess;
+    lbe_status st = tc_gemm(c, m->T, m->d, nullptr, cells, s, timed, ev, [&](__nv_bfloat162* x2, int) {
         const long tot = (long)cells * (np / 2);
         k_mix_gather<<<(int)std::min<long>((tot + 255) / 256, 32L * sm_count()), 256, 0, s>>>(hA, hB, cs, nr, np,
                                                                                               cells, x2, map);
     }, &Y);
+    if (ev[0]) {
+        float ms = 0.f;
+        if (timed && st == LBE_OK && cudaEventSynchronize(ev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess)
+            add_gemm_time(ms);
+        cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+    }
     if (st != LBE_OK) return st;
     const long tot = (long)cells * 2 * nr;
     const int gr = (int)std::min<long>((tot + 255) / 256, 32L * sm_count());

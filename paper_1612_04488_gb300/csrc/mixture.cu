@@ -392,35 +392,41 @@ __device__ __forceinline__ void orbit_point(int q, int N, int layout, int* i1, i
 
 // per (cell, species): mom[(a cells + n) kMom + .] = {U, q, W1, P13, G1, W2, X12, P23, G2}: U, q,
 // W1 = F201/4, P13, W2 = F021/4, X12 = F111/4, P23 of h^(k+1/2) and G_j of L h^(k), h^(k); sums
-// over the orbit representatives times the orbit size (4 plates, 2 ducts)
+// over the orbit representatives times the orbit size (4 plates, 2 ducts).  A thread takes whole
+// rows (i1, i2) of the layout: it sums v3 x, v3^3 x (x = h^(k+1/2)) and the G integrand along
+// i3, then applies the row's (v1, v2) weights once.
 template <typename T>
 __global__ void __launch_bounds__(256) k_mix_moments(MixSisDev P, const T* __restrict__ hh,
                                                      const double* __restrict__ h, const T* __restrict__ lp,
                                                      const double* __restrict__ nu, const double* __restrict__ vel,
                                                      double* __restrict__ mom) {
     const int n = blockIdx.x, a = blockIdx.y, N = P.nv, H = N / 2;
-    const int nq = N * (P.layout == 1 ? H : N) * H;
+    const int E2 = P.layout == 1 ? H : N, rows = N * E2;
     const long n3 = (long)N * N * N, off = ((long)a * P.cells + n) * n3;
-    const double r = P.r[a];
+    const double r = P.r[a], Nd = P.Nd[a], dl = P.delta;
+    const double* __restrict__ nua = nu + a * n3;
     double s[kMom] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-        int i1, i2, i3;
-        orbit_point(q, N, P.layout, &i1, &i2, &i3);
-        const double v1 = vel[i1], v2 = vel[i2], v3 = vel[i3];
-        const double x = (double)hh[off + q] * v3;
-        s[0] += x;
-        s[1] += (r * (v1 * v1 + v2 * v2 + v3 * v3) - 2.5) * x;
-        s[2] += (2.0 * v1 * v1 - 1.0) * x;
-        s[3] += v1 * x;
-        s[5] += (2.0 * v2 * v2 - 1.0) * x;
-        s[6] += v1 * v2 * x;
-        s[7] += v2 * x;
-        if (P.sis) {
-            const long vf = ((long)i1 * N + i2) * N + i3;
-            const double y = ((double)lp[off + q] + (P.Nd[a] - P.delta * nu[a * n3 + vf]) * h[off + q]) * v3;
-            s[4] += v1 * y;
-            s[8] += v2 * y;
+    for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+        const int i1 = row / E2, i2 = row - i1 * E2;
+        const long o = off + (long)row * H, vf = ((long)i1 * N + i2) * N;
+        double A0 = 0.0, A1 = 0.0, B0 = 0.0;
+        for (int i3 = 0; i3 < H; ++i3) {
+            const double v3 = vel[i3];
+            const double x = (double)hh[o + i3] * v3;
+            A0 += x;
+            A1 += v3 * v3 * x;
+            if (P.sis) B0 += ((double)lp[o + i3] + (Nd - dl * nua[vf + i3]) * h[o + i3]) * v3;
         }
+        const double v1 = vel[i1], v2 = vel[i2];
+        s[0] += A0;
+        s[1] += (r * (v1 * v1 + v2 * v2) - 2.5) * A0 + r * A1;
+        s[2] += (2.0 * v1 * v1 - 1.0) * A0;
+        s[3] += v1 * A0;
+        s[5] += (2.0 * v2 * v2 - 1.0) * A0;
+        s[6] += v1 * v2 * A0;
+        s[7] += v2 * A0;
+        s[4] += v1 * B0;
+        s[8] += v2 * B0;
     }
     __shared__ double red[kMom][8];
     for (int k = 0; k < kMom; ++k) {
@@ -822,18 +828,28 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_mix_correct(MixSisDev P, const T* __restrict__ hh,
                                                      double* __restrict__ h, const double* __restrict__ dU,
                                                      const double* __restrict__ feq, const double* __restrict__ vel) {
+    // thread: orbit representative q; blocks in y walk the (species, cell) pairs
     const int N = P.nv, H = N / 2, nq = N * (P.layout == 1 ? H : N) * H;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
     const long n3 = (long)N * N * N;
-    const long total = 2L * P.cells * nq;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const int q = (int)(t % nq);
-        const long an = t / nq;
-        const int a = (int)(an / P.cells);
-        int i1, i2, i3;
-        orbit_point(q, N, P.layout, &i1, &i2, &i3);
-        const long vf = ((long)i1 * N + i2) * N + i3, off = an * n3 + q;
-        h[off] = (double)hh[off] + 2.0 * P.r[a] * dU[an] * vel[i3] * feq[a * n3 + vf];
+    int i1, i2, i3;
+    orbit_point(q, N, P.layout, &i1, &i2, &i3);
+    const long vf = ((long)i1 * N + i2) * N + i3;
+    const double c0 = 2.0 * P.r[0] * vel[i3] * feq[vf], c1 = 2.0 * P.r[1] * vel[i3] * feq[n3 + vf];
+    for (long an = blockIdx.y; an < 2L * P.cells; an += gridDim.y) {
+        const long off = an * n3 + q;
+        h[off] = (double)hh[off] + dU[an] * (an < P.cells ? c0 : c1);
     }
+}
+
+// h = h^(k+1/2) + 2 r_a dU v3 f_a,eq on every (species, cell) of the orbit layout
+template <typename T>
+void launch_correct(const MixSisDev& P, const T* hh, double* h, const double* dU, const double* feq,
+                    const double* vel, int nq, cudaStream_t s) {
+    const long pairs = 2L * P.cells;
+    const dim3 g((nq + 255) / 256, (unsigned)(pairs < 8192 ? pairs : 8192));
+    k_mix_correct<T><<<g, 256, 0, s>>>(P, hh, h, dU, feq, vel);
 }
 
 int grid_for(long total) {
@@ -1485,7 +1501,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
                 k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
             else
                 k_mix_poisson2d<<<2, 512, 0, s>>>(Q, D, mom, dSx, dSy, dlam, dwork, dU, Uc, rates);
-            k_mix_correct<float><<<grid_for(2L * n * nq), 256, 0, s>>>(Q, hh32, hout, dU, o->feq, o->vel);
+            launch_correct<float>(Q, hh32, hout, dU, o->feq, o->vel, nq, s);
         } else {
             e = mix_gemm(ctx, *o, hin, hin + per, n3, ncol, pb->delta, lp, lp + per, s, dfg, dfluid);
             if (e != LBE_OK) return e;
@@ -1506,7 +1522,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
                 k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
             else
                 k_mix_poisson2d<<<2, 512, 0, s>>>(Q, D, mom, dSx, dSy, dlam, dwork, dU, Uc, rates);
-            k_mix_correct<double><<<grid_for(2L * n * nq), 256, 0, s>>>(Q, hh, hout, dU, o->feq, o->vel);
+            launch_correct<double>(Q, hh, hout, dU, o->feq, o->vel, nq, s);
         }
         g_launches += 3;
         g_levals += n;
