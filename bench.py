@@ -436,9 +436,10 @@ def porous_measure(lbe, torch, device, steps, warmup, nv=24, M=32, deltas=(1.0, 
                                max_iter=400, precision=prec, dim=2, nx=n, ny=n, solid=0.4)
 
     pbs = [mk(d, lbe.BF16_REFINED) for d in deltas]
+    # the first solve builds the operator in the duct orbit layout and its tensor-core form
     t0 = time.perf_counter()
-    ctx.mix_info(pbs[0].mix, nv, 5.0, M, 3.75)
-    build_s = time.perf_counter() - t0
+    ctx.mix_solve(pbs[0], want_U=False)
+    first_s = time.perf_counter() - t0
     for _ in range(warmup):
         for pb in pbs:
             ctx.mix_solve(pb, want_U=False)
@@ -474,7 +475,7 @@ def porous_measure(lbe, torch, device, steps, warmup, nv=24, M=32, deltas=(1.0, 
     ref = res[-1]
     rel = max(abs(x / y - 1.0) for x, y in ((br.M_A, ref.M_A), (br.M_B, ref.M_B)))
     nsolve = len(pbs) * steps
-    out = {"solves_per_s": nsolve / (ms / 1000.0), "ms_per_step": ms / steps, "build_s": build_s,
+    out = {"solves_per_s": nsolve / (ms / 1000.0), "ms_per_step": ms / steps, "first_solve_s": first_s,
            "solves": [{"delta": d, "iters": r.iters, "fp64_iters": r.fp64_iters, "status": r.status,
                        "rates": [r.M_A, r.M_B, r.Q_A, r.Q_B]} for d, r in zip(deltas, res)],
            "bf16": {"delta": deltas[-1], "iters": br.iters, "status": br.status, "max_rel_vs_refined": rel},
@@ -511,7 +512,7 @@ def run_porous(args):
             "value": m["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPES["bf16"], "data": "synthetic", "config": m["config"],
-            "roofline": m["roofline"], "solves": m["solves"], "bf16": m["bf16"], "build_s": m["build_s"],
+            "roofline": m["roofline"], "solves": m["solves"], "bf16": m["bf16"], "first_solve_s": m["first_solve_s"],
             "e2e": m["e2e"], "clocks": clk.summary(), "gpu_launches": m["gpu_launches"]}
     print(json.dumps(line), flush=True)
     return 0
