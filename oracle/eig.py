@@ -9,9 +9,12 @@ the error iteration is homogeneous), and the correction of Eq. guided.  The conv
 factor omega is the modulus of the dominant eigenvalue of that linear map; the paper fits
 U3(k) = U_inf + C exp(-lambda k), omega = exp(-lambda), which power iteration reproduces.
 
-Pin: with L replaced by the linearized BGK operator delta (2 U3 v3 f_eq - h), the CIS map
-is rank one and omega = delta^2 ∫ pi^-1/2 exp(-v^2) / (delta^2 + 4 pi^2 v^2) dv
-(tests/test_oracle_eig.py).
+Pins: with L replaced by the linearized BGK operator delta (2 U3 v3 f_eq - h) (collision
+frequency 1), the CIS map is rank one and omega = delta^2 ∫ pi^-1/2 exp(-v^2) /
+(delta^2 + 4 pi^2 v^2) dv; the SIS map has rank two (its range is spanned by the half step's
+shape and v3 f_eq) and its eigenvalues solve a quadratic whose coefficients are 1D integrals
+of the same kind (tests/test_oracle_eig.py).  Both maps take the operator as an argument so
+that the pins exercise the same code as the hard-sphere analysis.
 """
 import numpy as np
 
@@ -23,15 +26,34 @@ def _lplus(F, e, delta):
     return lr + 1j * li, Lr + 1j * Li
 
 
-def cis_map(F, e, delta):
-    lp, _ = _lplus(F, e, delta)
-    return lp / (delta * F.nu + 2j * np.pi * F.V1)
+def fsm_operator(F, delta):
+    """e -> (L+ e, L e, nu) for the hard-sphere operator of the fast spectral method."""
+    def op(e):
+        lp, Le = _lplus(F, e, delta)
+        return lp, Le, F.nu
+    return op
 
 
-def sis_map(F, e, delta, N=1.25):
+def bgk_operator(F, delta):
+    """e -> (L+ e, L e, nu) for the linearized BGK operator L e = delta (2 U3(e) v3 f_eq - e),
+    U3(e) = ∫ v3 e (collision frequency 1)."""
     w = F.dv ** 3
-    lp, Le = _lplus(F, e, delta)
-    eh = lp / (delta * F.nu + 2j * np.pi * F.V1)
+
+    def op(e):
+        lp = delta * 2.0 * np.sum(F.V3 * e) * w * F.V3 * F.feq
+        return lp, lp - delta * e, 1.0
+    return op
+
+
+def cis_map(F, e, delta, op=None):
+    lp, _, nu = (op or fsm_operator(F, delta))(e)
+    return lp / (delta * nu + 2j * np.pi * F.V1)
+
+
+def sis_map(F, e, delta, N=1.25, op=None):
+    w = F.dv ** 3
+    lp, Le, nu = (op or fsm_operator(F, delta))(e)
+    eh = lp / (delta * nu + 2j * np.pi * F.V1)
     A1 = 2.0 * np.sum(F.V1 * F.V3 * (Le + N * delta * e)) * w
     A2 = np.sum((2.0 * F.V1 ** 2 - 1.0) * F.V3 * eh) * w
     Uh = np.sum(F.V3 * eh) * w
