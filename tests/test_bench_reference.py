@@ -22,3 +22,16 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+
+
+def test_reference_arm_mixture_workloads_unavailable():
+    """The mixture oracle runs at nv <= 12 only, so the reference arm of the 24^3 mixture
+    workloads prints its one-line reason and exits 0."""
+    for wl in ("mix_ne_ar24", "mix_porous100"):
+        out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                              wl], capture_output=True, text=True, timeout=120, cwd=ROOT)
+        assert out.returncode == 0, out.stderr[-2000:]
+        lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+        assert len(lines) == 1
+        d = json.loads(lines[0])
+        assert d["impl"] == "reference" and d["unavailable"]
