@@ -396,8 +396,10 @@ typedef struct {
                           * iteration satisfies the periodic scheme), and the diffusion
                           * correction acts on the fluid cells whose eight neighbours are fluid
                           * (solved by conjugate gradients), the others held at the kinetic U.
-                          * The sweep's lag makes its last half step g part of the iteration's
-                          * state; LBE_BF16_REFINED's correction then runs on the pair (h, g)   */
+                          * Solid cells hold h = 0 and U = 0; the operator acts on the fluid
+                          * cells only.  The sweep's lag makes its last half step g part of the
+                          * iteration's state; LBE_BF16_REFINED's correction then runs on the
+                          * pair (h, g)                                                        */
 } lbe_mix_problem;
 
 typedef struct {
