@@ -412,6 +412,29 @@ def porous_interior(solid):
 
 
 # ---- synthetic iterative scheme for plates (Sec. 4) ------------------------------------------
+def porous_poisson(inner, Uh, rhs):
+    """lap U = rhs on the cells of ``inner`` (five-point periodic differences on the n x n unit
+    cell, spacing 1/n), U = Uh on every other cell; dense LU.  Returns U on all cells."""
+    n = Uh.shape[0]
+    d = 1.0 / n
+    idx = -np.ones((n, n), dtype=int)
+    idx[inner] = np.arange(int(inner.sum()))
+    m = int(inner.sum())
+    A = np.zeros((m, m))
+    b = rhs[inner].copy()
+    for (i, j), k in zip(np.argwhere(inner), range(m)):
+        A[k, k] = -4.0 / d ** 2
+        for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            ii, jj = (i + di) % n, (j + dj) % n
+            if inner[ii, jj]:
+                A[k, idx[ii, jj]] = 1.0 / d ** 2
+            else:
+                b[k] -= Uh[ii, jj] / d ** 2
+    U = Uh.copy()
+    U[inner] = np.linalg.solve(A, b)
+    return U
+
+
 class MixProblem:
     """Poiseuille flow of a binary mixture between plates (dim 1, Table 4's setting) or through
     a rectangular duct [0, width] x [0, 1] of nx x ny cells (dim 2, Table 5's setting)."""
@@ -540,8 +563,6 @@ class MixRun:
         DB = d1(mo[1][3]) + d2(mo[1][6])
         D = [1.0 - DB, DB]
         inner = self.inner
-        idx = -np.ones((n, n), dtype=int)
-        idx[inner] = np.arange(int(inner.sum()))
         new = []
         for a in range(2):
             Uh, _, W1, _, W2, X12, _ = mo[a]
@@ -552,19 +573,7 @@ class MixRun:
                    - 2.0 * (sh(X12, 1, 1) - sh(X12, 1, -1) - sh(X12, -1, 1) + sh(X12, -1, -1)) / (4.0 * d * d)
                    - (sh(W2, 0, 1) - 2.0 * W2 + sh(W2, 0, -1)) / d ** 2
                    + d1(G1) + d2(G2)) / mix.chi[a]
-            m = int(inner.sum())
-            A = np.zeros((m, m))
-            b = rhs[inner].copy()
-            for (i, j), k in zip(np.argwhere(inner), range(m)):
-                A[k, k] = -4.0 / d ** 2
-                for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
-                    ii, jj = (i + di) % n, (j + dj) % n
-                    if inner[ii, jj]:
-                        A[k, idx[ii, jj]] = 1.0 / d ** 2
-                    else:
-                        b[k] -= Uh[ii, jj] / d ** 2
-            Un = Uh.copy()
-            Un[inner] = np.linalg.solve(A, b)
+            Un = porous_poisson(inner, Uh, rhs)
             new.append(hh[a] + 2.0 * mix.r[a] * (Un - Uh)[(...,) + (None,) * 3] * F.V3 * F.f[a])
         return new
 
