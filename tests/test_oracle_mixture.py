@@ -226,3 +226,20 @@ def test_porous_poisson_reproduces_a_periodic_discrete_eigenfunction():
     Uh = np.where(inner, 0.0, U)
     got = mx.porous_poisson(inner, Uh, lap)
     assert np.max(np.abs(got - U)) < 1e-12
+
+
+def test_duct_poisson_reproduces_a_quadratic():
+    """The duct correction's Poisson solve (chi lap U = rhs on the interior, U held on the ring)
+    against U = x^2 + 3 y^2 - x y, whose five-point differences are exact: lap U = 8 with
+    unequal spacings width / nx and 1 / ny."""
+    from types import SimpleNamespace
+    nx, ny, width, chi = 9, 7, 1.5, 0.37
+    x = (np.arange(nx) + 0.5) * width / nx
+    y = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, y, indexing="ij")
+    U = X ** 2 + 3 * Y ** 2 - X * Y
+    Uh = U.copy()
+    Uh[1:-1, 1:-1] = 0.0
+    rhs = np.full((nx - 2, ny - 2), 8.0 * chi)
+    got = mx.MixRun.poisson(SimpleNamespace(pb=SimpleNamespace(width=width)), Uh, rhs, chi)
+    assert np.max(np.abs(got - U)) < 1e-12
