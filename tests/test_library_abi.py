@@ -83,3 +83,26 @@ def test_mixture_struct_layouts_match_the_header(tmp_path):
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
+
+
+def test_every_entry_point_rejects_null_arguments_without_a_device(libpath):
+    """Every call that takes a context, batch or output pointer returns LBE_BAD_ARG for null
+    arguments, before any CUDA call (so this runs without a GPU)."""
+    from paper_1612_04488_gb300 import lbe
+    lib = ctypes.CDLL(libpath)
+    txt = ""
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt += re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", f)).read(), flags=re.S)
+    decls = re.findall(r"\blbe_status\s+(lbe_[A-Za-z_0-9]+)\s*\(([^)]*)\)\s*;", txt)
+    flags_only = {"lbe_set_kernel_timing", "lbe_debug_expire_waits"}   # take an int switch, nothing to reject
+    checked = 0
+    for name, params in decls:
+        if name in flags_only:
+            continue
+        nargs = len([p for p in params.split(",") if p.strip() and p.strip() != "void"])
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        assert fn(*([None] * nargs)) == lbe.BAD_ARG, name
+        checked += 1
+    assert checked >= 20
