@@ -679,13 +679,14 @@ void launch_sweep_porous(const T* rhs, T* h, long per, const DevTables* tb, bool
 // eight periodic neighbours are fluid; list `inner`, and per interior cell its four neighbours
 // `nb` as an interior index k >= 0 or a ring cell -1 - cell), the other fluid cells held at
 // U^(k+1/2), periodic central differences; solved by conjugate gradients on -lap (symmetric
-// positive definite) to a residual of 1e-13 of the right-hand side (at most 20000 steps).  Then
+// positive definite) to a residual of rtol times the right-hand side (at most 20000 steps).  Then
 // dU, the corrected U and q, and the flow rates sqrt(m) times means over all n^2 cells.
 __global__ void __launch_bounds__(1024) k_mix_poisson_porous(MixSisDev P, PorousDev G, const double* __restrict__ mom,
                                                              const int* __restrict__ inner, const int* __restrict__ nb,
                                                              int m, double* __restrict__ work,
                                                              double* __restrict__ dU, double* __restrict__ Uout,
-                                                             double* __restrict__ rates, int* __restrict__ cg_steps) {
+                                                             double* __restrict__ rates, int* __restrict__ cg_steps,
+                                                             double rtol) {
     const int a = blockIdx.x, n = G.n, ncell = n * n;
     const double d = 1.0 / n, id2 = 1.0 / (d * d);
     double* x = work + (long)a * 5 * m;
@@ -753,7 +754,7 @@ __global__ void __launch_bounds__(1024) k_mix_poisson_porous(MixSisDev P, Porous
         rr = block_sum(rr);
         bb = block_sum(bb);
         int it = 0;
-        const double tol = 1e-26 * (bb > 0.0 ? bb : 1.0);
+        const double tol = rtol * rtol * (bb > 0.0 ? bb : 1.0);
         while (rr > tol && it < 20000) {
             apply(p, Ap);
             double pAp = 0.0;
@@ -1494,9 +1495,9 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
                                         (const SweepJobDev*)d_job, nullptr, dcoef, s, 1);
                 }
             k_mix_moments<float><<<dim3(n, 2), 256, 0, s>>>(Q, hh32, hin, lp32, o->nu, o->vel, mom);
-            if (porous)
+            if (porous)  // the low-precision iteration's floor is far above 1e-9
                 k_mix_poisson_porous<<<2, 1024, 0, s>>>(Q, PG, mom, dinner, dnb, (int)inner.size(), dwork, dU, Uc,
-                                                        rates, dcg);
+                                                        rates, dcg, 1e-9);
             else if (dim == 1)
                 k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
             else
@@ -1517,7 +1518,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
             k_mix_moments<double><<<dim3(n, 2), 256, 0, s>>>(Q, hh, hin, lp, o->nu, o->vel, mom);
             if (porous)
                 k_mix_poisson_porous<<<2, 1024, 0, s>>>(Q, PG, mom, dinner, dnb, (int)inner.size(), dwork, dU, Uc,
-                                                        rates, dcg);
+                                                        rates, dcg, 1e-13);
             else if (dim == 1)
                 k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
             else
@@ -1658,7 +1659,7 @@ extern "C" lbe_status lbe_mix_solve(lbe_ctx* ctx, const lbe_mix_problem* pb, lbe
             k_mix_moments<double><<<dim3(n, 2), 256, 0, s>>>(Q, h, h, lp, o->nu, o->vel, mom);
             if (porous)
                 k_mix_poisson_porous<<<2, 1024, 0, s>>>(Q, PG, mom, dinner, dnb, (int)inner.size(), dwork, dU, Uc,
-                                                        rates, dcg);
+                                                        rates, dcg, 1e-13);
             else if (dim == 1)
                 k_mix_march<<<1, 256, march_smem, s>>>(Q, mom, dgeo, dU, Uc, rates);
             else
