@@ -243,3 +243,14 @@ def test_duct_poisson_reproduces_a_quadratic():
     rhs = np.full((nx - 2, ny - 2), 8.0 * chi)
     got = mx.MixRun.poisson(SimpleNamespace(pb=SimpleNamespace(width=width)), Uh, rhs, chi)
     assert np.max(np.abs(got - U)) < 1e-12
+
+
+def test_march_integrates_a_linear_profile_exactly():
+    """The once-integrated diffusion equation is marched from the wall with the sweep's upwind
+    differences (two points at the first node, three after), which are exact for a linear
+    profile: dY/dx = 3 with Y(x0) = 2 gives Y = 2 + 3 (x - x0) on the clustered nodes."""
+    from types import SimpleNamespace
+    from oracle import transport
+    x = transport.nodes_clustered(40)
+    Y = mx.MixRun.march(SimpleNamespace(x=x), 2.0, np.full(len(x), 3.0))
+    assert np.max(np.abs(Y - (2.0 + 3.0 * (x - x[0])))) < 1e-12
